@@ -1,0 +1,909 @@
+/*
+ * rr_oracle.c -- FP64 brute-force CPU oracle of the RadaRays polar scan.
+ *
+ * TEST INFRASTRUCTURE ONLY.  The tests, the smoke check of the package entry
+ * module and the CPU-baseline leg of the benchmark are the only callers.  The
+ * CUDA library never links, loads or calls this file, and this file shares no
+ * code, header, table or constant generator with it: every formula is written
+ * again here from the paper (Mock, Magnusson, Hertzberg: "RadaRays: Real-time
+ * Simulation of Rotating FMCW Radar for Mobile Robotics via Hardware-accelerated
+ * Ray Tracing", arXiv 2310.03505).
+ *
+ * Plain and slow on purpose:
+ *   - every quantity is a double;
+ *   - the closest hit is a loop over every triangle (Moller-Trumbore), no BVH;
+ *   - each initial ray's tree is expanded depth first with an explicit stack;
+ *   - returns are collected in a list and then summed into the polar image by
+ *     a lookup, as Sec. III-B describes.
+ *
+ * Readings of passages the paper leaves open are fixed once here and listed in
+ * the design notes of the repository (normalised Eq. 5, unpolarised Fresnel,
+ * optical range, returns deplete the reflected child, air-path capping, ...).
+ *
+ * Parity flags.  Besides the image, the oracle marks every initial ray whose
+ * tree contains a decision that FP32 arithmetic could take the other way
+ * (a hit or a near miss within 1e-5 barycentric margin of a triangle edge,
+ * a hit next to t_min or the range limit, a near tie between two triangles,
+ * a total-internal-reflection test next to the critical angle, a grazing hit,
+ * a child next to the range cut).  Returns whose range sits next to a bin edge
+ * add their energy to a per-bin slack.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_NONE 0xFFFFFFFFu
+#define ORC_AIR (-1)
+
+#define ORC_MULTIPATH 1u
+#define ORC_REFRACTION 2u
+#define ORC_SPECKLE 4u
+#define ORC_NOISE 8u
+
+/* flag thresholds of the parity protocol */
+#define FLAG_BARY 1e-5    /* barycentric margin (hits and near misses)        */
+#define FLAG_TREL 1e-6    /* relative distance for ties / range limits        */
+#define FLAG_TABS 1e-6    /* absolute distance next to t_min (metres)          */
+#define FLAG_TIR 1e-6     /* |eta^2 sin^2 - 1| next to the critical angle      */
+#define FLAG_COS 1e-6     /* grazing incidence |cos theta0|                    */
+
+/* segment flag bits (diagnostics) */
+#define SEG_EDGE 1u
+#define SEG_TMIN 2u
+#define SEG_TIE 4u
+#define SEG_TLIM 8u
+#define SEG_TIR 16u
+#define SEG_GRAZE 32u
+#define SEG_RMAX 64u
+#define SEG_VIS 128u
+#define SEG_EMIN 256u
+
+typedef struct {
+  double eps_r, loss_tangent, A, B, C;
+  int32_t pec, pad;
+} orc_material;
+
+typedef struct {
+  uint32_t n_azimuth, rays_per_beam, max_bounces, n_bins;
+  double beam_width, beam_prob, elevation, bin_size, t_min, min_energy, freq_hz;
+  double blur_sigma_bins, az_pattern_sigma, noise_sys, noise_amb;
+  uint32_t flags, seed_lo, seed_hi, scan_id;
+} orc_params;
+
+typedef struct {
+  double p[3];
+  double q[4]; /* (w, x, y, z) */
+} orc_pose;
+
+typedef struct {
+  uint32_t az, k, path, bounce, tri, flags;
+  double t, E;
+} orc_segment;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC 2011).  Ten rounds of two 32x32->64 multiplications  */
+/* with a Weyl-sequence key schedule.                                       */
+/* ------------------------------------------------------------------------ */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint64_t mul0 = 0xD2511F53u, mul1 = 0xCD9E8D57u;
+  const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t prod0 = mul0 * (uint64_t)c0;
+    uint64_t prod1 = mul1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+    uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += weyl0;
+    k1 += weyl1;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* uniform in (0,1) from the top 23 bits: (2 (x >> 9) + 1) / 2^24.  The odd
+   numerator has at most 24 significant bits, so the value is exact in float
+   as well as in double and both implementations draw identical numbers. */
+double orc_u24(uint32_t x) { return (double)(2u * (x >> 9) + 1u) * (1.0 / 16777216.0); }
+
+static void draw(const orc_params* p, uint32_t a, uint32_t b, uint32_t c, uint32_t out[4]) {
+  uint32_t ctr[4] = {p->scan_id, a, b, c};
+  uint32_t key[2] = {p->seed_lo, p->seed_hi};
+  orc_philox(ctr, key, out);
+}
+
+/* inverse error function: bisection on erf() to full double precision */
+double orc_erfinv(double y) {
+  if (!(y > -1.0 && y < 1.0)) return NAN;
+  double lo = -6.0, hi = 6.0;
+  for (int i = 0; i < 200; ++i) {
+    double mid = 0.5 * (lo + hi);
+    if (erf(mid) < y) lo = mid; else hi = mid;
+    if (hi - lo <= 0.0) break;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* Eq. 2: standard deviation of the D3 radius, sigma = (b/2) / (sqrt(2) erfinv(P)) */
+double orc_d3_sigma(double beam_width, double beam_prob) {
+  if (beam_width == 0.0) return 0.0;
+  return 0.5 * beam_width / (sqrt(2.0) * orc_erfinv(beam_prob));
+}
+
+/* ------------------------------------------------------------------------ */
+/* small vector helpers                                                     */
+/* ------------------------------------------------------------------------ */
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static void sub3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[0] - b[0];
+  o[1] = a[1] - b[1];
+  o[2] = a[2] - b[2];
+}
+static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
+static void normalize3(double a[3]) {
+  double n = norm3(a);
+  a[0] /= n;
+  a[1] /= n;
+  a[2] /= n;
+}
+/* angle between two vectors, atan2(|a x b|, a.b) */
+double orc_angle(const double a[3], const double b[3]) {
+  double c[3];
+  cross3(a, b, c);
+  return atan2(norm3(c), dot3(a, b));
+}
+
+/* rotate v by the unit quaternion q = (w, x, y, z), written as its rotation matrix */
+static void quat_rotate(const double qin[4], const double v[3], double o[3]) {
+  double n = sqrt(qin[0] * qin[0] + qin[1] * qin[1] + qin[2] * qin[2] + qin[3] * qin[3]);
+  double w = qin[0] / n, x = qin[1] / n, y = qin[2] / n, z = qin[3] / n;
+  double m[3][3] = {
+      {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+      {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+      {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+  for (int i = 0; i < 3; ++i) o[i] = m[i][0] * v[0] + m[i][1] * v[1] + m[i][2] * v[2];
+}
+
+/* beam axis of azimuth index a in the world frame */
+void orc_beam_axis(const orc_params* p, const orc_pose* pose, uint32_t a, double axis[3]) {
+  double phi = 2.0 * M_PI * (double)a / (double)p->n_azimuth;
+  double th = p->elevation;
+  double ds[3] = {cos(th) * cos(phi), cos(th) * sin(phi), sin(th)};
+  quat_rotate(pose->q, ds, axis);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. III-A, Eq. 2: D3 cone sample of initial ray k of azimuth a.          */
+/* N ~ N(0,1) by Box-Muller from two uniforms, omega ~ U[-pi, pi), r = sigma N */
+/* (d_az, d_inc) = r (cos omega, sin omega) around the beam axis.            */
+/* ------------------------------------------------------------------------ */
+void orc_d3_ray(const orc_params* p, const orc_pose* pose, uint32_t a, uint32_t k, double o[3], double d[3],
+                double* r_out, double* omega_out) {
+  uint32_t x[4];
+  draw(p, a, k, 0u, x);
+  double u0 = orc_u24(x[0]), u1 = orc_u24(x[1]), u2 = orc_u24(x[2]);
+  double gauss = sqrt(-2.0 * log(u0)) * cos(2.0 * M_PI * u1);
+  double sigma = orc_d3_sigma(p->beam_width, p->beam_prob);
+  double r = sigma * gauss;
+  double omega = M_PI * (2.0 * u2 - 1.0);
+  double phi = 2.0 * M_PI * (double)a / (double)p->n_azimuth + r * cos(omega);
+  double th = p->elevation + r * sin(omega);
+  double ds[3] = {cos(th) * cos(phi), cos(th) * sin(phi), sin(th)};
+  quat_rotate(pose->q, ds, d);
+  normalize3(d);
+  o[0] = pose->p[0];
+  o[1] = pose->p[1];
+  o[2] = pose->p[2];
+  if (r_out) *r_out = r;
+  if (omega_out) *omega_out = omega;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. III-A: Fresnel split of the incident energy E0 = E1 + E2 and Snell's */
+/* law sin(theta0)/sin(theta2) = v1/v2 = n2/n1.  Unpolarised: R = (Rs+Rp)/2. */
+/* Returns 1 on total internal reflection (R = 1, T = 0).                    */
+/* ------------------------------------------------------------------------ */
+int orc_fresnel(double n1, double n2, double cos_i, double* R, double* cos_t, double* sin2_t_out) {
+  double eta = n1 / n2;
+  double sin2_t = eta * eta * (1.0 - cos_i * cos_i);
+  if (sin2_t_out) *sin2_t_out = sin2_t;
+  if (sin2_t >= 1.0) {
+    *R = 1.0;
+    *cos_t = 0.0;
+    return 1;
+  }
+  double ct = sqrt(1.0 - sin2_t);
+  double rs = (n1 * cos_i - n2 * ct) / (n1 * cos_i + n2 * ct);
+  double rp = (n1 * ct - n2 * cos_i) / (n1 * ct + n2 * cos_i);
+  *R = 0.5 * (rs * rs + rp * rp);
+  *cos_t = ct;
+  return 0;
+}
+
+/* mirror direction about a unit normal n (theta1 = theta0) */
+void orc_reflect(const double d[3], const double n[3], double out[3]) {
+  double dn = dot3(d, n);
+  for (int i = 0; i < 3; ++i) out[i] = d[i] - 2.0 * dn * n[i];
+}
+
+/* refracted direction; n faces the incident side (d.n = -cos_i < 0), eta = n1/n2 */
+void orc_refract(const double d[3], const double n[3], double eta, double cos_i, double cos_t, double out[3]) {
+  for (int i = 0; i < 3; ++i) out[i] = eta * d[i] + (eta * cos_i - cos_t) * n[i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 3 - Eq. 5: BRDF lobe f(w) = (A + B cos w + S cos^C w) / Z on          */
+/* [-pi/2, pi/2], S = 1 - A - B, normalised so that its integral is one,     */
+/* and the beam-window fraction W(w) = integral of f over [w-b/2, w+b/2].    */
+/* ------------------------------------------------------------------------ */
+static double cospow(double x, double c) {
+  double cx = cos(x);
+  if (cx <= 0.0) return (c == 0.0) ? 1.0 : 0.0;
+  return pow(cx, c);
+}
+
+static double simpson_rec(double c, double a, double b, double fa, double fm, double fb, double whole, double eps,
+                          int depth) {
+  double m = 0.5 * (a + b);
+  double lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+  double flm = cospow(lm, c), frm = cospow(rm, c);
+  double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm);
+  double right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+  double delta = left + right - whole;
+  if (depth <= 0 || fabs(delta) <= 15.0 * eps) return left + right + delta / 15.0;
+  return simpson_rec(c, a, m, fa, flm, fm, left, 0.5 * eps, depth - 1) +
+         simpson_rec(c, m, b, fm, frm, fb, right, 0.5 * eps, depth - 1);
+}
+
+/* integral of cos^C over [lo, hi] by adaptive Simpson on 64 starting panels */
+double orc_int_cospow(double c, double lo, double hi) {
+  if (!(hi > lo)) return 0.0;
+  const int panels = 64;
+  double h = (hi - lo) / panels, sum = 0.0;
+  for (int i = 0; i < panels; ++i) {
+    double a = lo + h * i, b = (i == panels - 1) ? hi : lo + h * (i + 1);
+    double fa = cospow(a, c), fb = cospow(b, c), fm = cospow(0.5 * (a + b), c);
+    double whole = (b - a) / 6.0 * (fa + 4.0 * fm + fb);
+    sum += simpson_rec(c, a, b, fa, fm, fb, whole, 1e-16, 48);
+  }
+  return sum;
+}
+
+/* Z = A pi + 2 B + S sqrt(pi) Gamma((C+1)/2) / Gamma(C/2 + 1) */
+double orc_brdf_norm(const orc_material* m) {
+  double S = 1.0 - m->A - m->B;
+  double gr = exp(lgamma(0.5 * (m->C + 1.0)) - lgamma(0.5 * m->C + 1.0));
+  return m->A * M_PI + 2.0 * m->B + S * sqrt(M_PI) * gr;
+}
+
+double orc_brdf_density(const orc_material* m, double w) {
+  if (w < -M_PI / 2 || w > M_PI / 2) return 0.0;
+  double S = 1.0 - m->A - m->B;
+  return (m->A + m->B * cos(w) + S * cospow(w, m->C)) / orc_brdf_norm(m);
+}
+
+double orc_brdf_window(const orc_material* m, double w, double b) {
+  double lo = w - 0.5 * b, hi = w + 0.5 * b;
+  if (lo < -M_PI / 2) lo = -M_PI / 2;
+  if (hi > M_PI / 2) hi = M_PI / 2;
+  if (!(hi > lo)) return 0.0;
+  double S = 1.0 - m->A - m->B;
+  double v = m->A * (hi - lo) + m->B * (sin(hi) - sin(lo));
+  if (S != 0.0) v += S * orc_int_cospow(m->C, lo, hi);
+  return v / orc_brdf_norm(m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Moller-Trumbore ray/triangle test in double precision.  Reports the plane  */
+/* distance t and the signed barycentrics (b1 for v1, b2 for v2) even when   */
+/* the point lies outside, so the caller can see near misses.  Returns 0 if */
+/* the ray is parallel to the plane.                                         */
+/* ------------------------------------------------------------------------ */
+int orc_tri_plane(const double o[3], const double d[3], const double v0[3], const double v1[3], const double v2[3],
+                  double* t, double* b1, double* b2) {
+  double e1[3], e2[3], pv[3], tv[3], qv[3];
+  sub3(v1, v0, e1);
+  sub3(v2, v0, e2);
+  cross3(d, e2, pv);
+  double det = dot3(e1, pv);
+  if (det == 0.0) return 0;
+  double inv = 1.0 / det;
+  sub3(o, v0, tv);
+  *b1 = dot3(tv, pv) * inv;
+  cross3(tv, e1, qv);
+  *b2 = dot3(d, qv) * inv;
+  *t = dot3(e2, qv) * inv;
+  return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* scene                                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const float* vtx;
+  const uint32_t* tri;
+  const uint16_t* mat_id;
+  const orc_material* mat;
+  uint32_t nv, nt, nm;
+} scene_t;
+
+static void tri_vertices(const scene_t* s, uint32_t j, double v0[3], double v1[3], double v2[3]) {
+  const uint32_t* t = s->tri + 3 * (size_t)j;
+  for (int i = 0; i < 3; ++i) {
+    v0[i] = (double)s->vtx[3 * (size_t)t[0] + i];
+    v1[i] = (double)s->vtx[3 * (size_t)t[1] + i];
+    v2[i] = (double)s->vtx[3 * (size_t)t[2] + i];
+  }
+}
+
+/* geometric normal normalize((v1 - v0) x (v2 - v0)); triangles are wound so it
+   points out of their material */
+static void tri_normal(const scene_t* s, uint32_t j, double n[3]) {
+  double v0[3], v1[3], v2[3], e1[3], e2[3];
+  tri_vertices(s, j, v0, v1, v2);
+  sub3(v1, v0, e1);
+  sub3(v2, v0, e2);
+  cross3(e1, e2, n);
+  normalize3(n);
+}
+
+typedef struct {
+  uint32_t tri;
+  double t, margin;
+  uint32_t flags;
+} hit_t;
+
+/* Closest hit by brute force over all triangles: t > t_min, triangle != skip,
+   ties on t go to the smaller triangle id.  Flags near-edge candidates (hit or
+   miss within FLAG_BARY of an edge) that could be the closest, a near tie with
+   the second closest triangle, and hits next to t_min. */
+static hit_t closest_hit(const scene_t* s, const double o[3], const double d[3], double t_min, uint32_t skip) {
+  hit_t h = {ORC_NONE, INFINITY, 0.0, 0u};
+  double t2 = INFINITY;         /* second closest valid hit */
+  double t_edge = INFINITY;     /* nearest near-edge candidate */
+  int near_tmin = 0;
+  for (uint32_t j = 0; j < s->nt; ++j) {
+    if (j == skip) continue;
+    double v0[3], v1[3], v2[3], t, b1, b2;
+    tri_vertices(s, j, v0, v1, v2);
+    if (!orc_tri_plane(o, d, v0, v1, v2, &t, &b1, &b2)) continue;
+    double b0 = 1.0 - b1 - b2;
+    double m = b0 < b1 ? b0 : b1;
+    if (b2 < m) m = b2;
+    if (m > -FLAG_BARY && m < FLAG_BARY && t > t_min - FLAG_TABS && t < t_edge) t_edge = t;
+    if (m >= 0.0 && fabs(t - t_min) < FLAG_TABS) near_tmin = 1;
+    if (m < 0.0 || !(t > t_min)) continue;
+    if (t < h.t || (t == h.t && j < h.tri)) {
+      if (h.tri != ORC_NONE) t2 = h.t;
+      h.t = t;
+      h.tri = j;
+      h.margin = m;
+    } else if (t < t2) {
+      t2 = t;
+    }
+  }
+  if (t_edge < INFINITY && t_edge <= h.t * (1.0 + FLAG_TREL)) h.flags |= SEG_EDGE;
+  if (near_tmin) h.flags |= SEG_TMIN;
+  if (h.tri != ORC_NONE && t2 - h.t <= FLAG_TREL * h.t) h.flags |= SEG_TIE;
+  return h;
+}
+
+/* exported for the tests: closest hit of one ray by brute force */
+int orc_closest(const float* vertices, uint32_t n_vertices, const uint32_t* triangles, uint32_t n_triangles,
+                const double o[3], const double d[3], double t_min, uint32_t skip, uint32_t* tri, double* t,
+                uint32_t* flags) {
+  scene_t s = {vertices, triangles, NULL, NULL, n_vertices, n_triangles, 0};
+  hit_t h = closest_hit(&s, o, d, t_min, skip);
+  *tri = h.tri;
+  *t = h.t;
+  *flags = h.flags;
+  return h.tri != ORC_NONE;
+}
+
+/* Any hit on the open segment from p (on triangle skip) to the sensor at
+   distance dist.  Sets *flag when a triangle lies within the flag margins. */
+static int occluded(const scene_t* s, const double p[3], const double dir[3], double t_min, double dist, uint32_t skip,
+                    int* flag) {
+  int occ = 0;
+  for (uint32_t j = 0; j < s->nt; ++j) {
+    if (j == skip) continue;
+    double v0[3], v1[3], v2[3], t, b1, b2;
+    tri_vertices(s, j, v0, v1, v2);
+    if (!orc_tri_plane(p, dir, v0, v1, v2, &t, &b1, &b2)) continue;
+    double b0 = 1.0 - b1 - b2;
+    double m = b0 < b1 ? b0 : b1;
+    if (b2 < m) m = b2;
+    int inside_t = t > t_min && t < dist;
+    int near_t = fabs(t - t_min) < FLAG_TABS || fabs(t - dist) < FLAG_TREL * dist;
+    if (m > -FLAG_BARY && m < FLAG_BARY && (inside_t || near_t)) *flag = 1;
+    if (m >= 0.0 && near_t) *flag = 1;
+    if (m >= 0.0 && inside_t) occ = 1;
+  }
+  return occ;
+}
+
+/* ------------------------------------------------------------------------ */
+/* per-column work                                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double o[3], d[3], E, L;
+  int32_t medium;
+  uint32_t prev, path, bounce;
+} oray_t;
+
+typedef struct {
+  uint32_t k;
+  double range, E;
+} oret_t;
+
+typedef struct {
+  oret_t* ret;
+  size_t n_ret, cap_ret;
+  orc_segment* seg;
+  size_t n_seg, cap_seg;
+  uint8_t* flagged;   /* [Ns] */
+  double* tally;      /* [Ns][4]: returned, absorbed, escaped, terminated */
+  uint64_t queries, shadow_queries;
+} column_t;
+
+static void push_ret(column_t* c, uint32_t k, double range, double E) {
+  if (c->n_ret == c->cap_ret) {
+    c->cap_ret = c->cap_ret ? 2 * c->cap_ret : 256;
+    c->ret = (oret_t*)realloc(c->ret, c->cap_ret * sizeof(oret_t));
+  }
+  c->ret[c->n_ret].k = k;
+  c->ret[c->n_ret].range = range;
+  c->ret[c->n_ret].E = E;
+  c->n_ret++;
+}
+
+static void push_seg(column_t* c, const orc_segment* s) {
+  if (c->n_seg == c->cap_seg) {
+    c->cap_seg = c->cap_seg ? 2 * c->cap_seg : 256;
+    c->seg = (orc_segment*)realloc(c->seg, c->cap_seg * sizeof(orc_segment));
+  }
+  c->seg[c->n_seg++] = *s;
+}
+
+static double refr_index(const scene_t* s, int32_t medium) {
+  return medium == ORC_AIR ? 1.0 : sqrt(s->mat[medium].eps_r);
+}
+
+/* field attenuation constant alpha = pi sqrt(eps_r) tan(delta) / lambda, lambda = c / f */
+static double alpha_np(const scene_t* s, int32_t medium, double freq) {
+  if (medium == ORC_AIR) return 0.0;
+  const double c0 = 299792458.0;
+  const orc_material* m = &s->mat[medium];
+  return M_PI * sqrt(m->eps_r) * m->loss_tangent * freq / c0;
+}
+
+/* Gaussian receive weight of the current beam for a return arriving from p */
+static double receive_weight(const orc_params* p, const double axis[3], const double sensor[3], const double pt[3]) {
+  double sigma = orc_d3_sigma(p->beam_width, p->beam_prob);
+  if (sigma == 0.0) return 0.0;
+  double v[3];
+  sub3(pt, sensor, v);
+  double delta = orc_angle(v, axis);
+  return exp(-0.5 * delta * delta / (sigma * sigma));
+}
+
+static double speckle_factor(const orc_params* p, uint32_t a, uint32_t k, uint32_t path, uint32_t bounce, int which) {
+  uint32_t x[4];
+  draw(p, a, k, 1u | (((path << 8) | bounce) << 8), x);
+  return -log(orc_u24(x[which]));
+}
+
+/* Sec. III-A: trace the ray tree of every initial ray of azimuth a. */
+static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* pose, uint32_t a, column_t* col) {
+  const double r_max = (double)p->n_bins * p->bin_size;
+  const double r_lim = ((p->flags & ORC_MULTIPATH) ? 2.0 : 1.0) * r_max;
+  const double b = p->beam_width;
+  double axis[3];
+  orc_beam_axis(p, pose, a, axis);
+  const double* sensor = pose->p;
+
+  size_t cap = 64;
+  oray_t* stack = (oray_t*)malloc(cap * sizeof(oray_t));
+
+  for (uint32_t k = 0; k < p->rays_per_beam; ++k) {
+    double* tal = col->tally + 4 * (size_t)k;
+    int flagged = 0;
+    size_t sp = 0;
+    oray_t root;
+    orc_d3_ray(p, pose, a, k, root.o, root.d, NULL, NULL);
+    root.E = 1.0 / (double)p->rays_per_beam; /* Sec. III-A: ray energies sum to E0 = 1 */
+    root.L = 0.0;
+    root.medium = ORC_AIR;
+    root.prev = ORC_NONE;
+    root.path = 0;
+    root.bounce = 0;
+    stack[sp++] = root;
+
+    while (sp > 0) {
+      oray_t ray = stack[--sp];
+      orc_segment seg = {a, k, ray.path, ray.bounce, ORC_NONE, 0u, INFINITY, ray.E};
+      double n_cur = refr_index(s, ray.medium);
+      double t_lim = (r_lim - ray.L) / n_cur; /* past it no return can reach the image */
+      hit_t h = closest_hit(s, ray.o, ray.d, p->t_min, ray.prev);
+      col->queries++;
+      seg.flags = h.flags;
+      if (h.tri != ORC_NONE && fabs(h.t - t_lim) <= FLAG_TREL * t_lim) seg.flags |= SEG_TLIM;
+      if (h.tri == ORC_NONE || h.t >= t_lim) {
+        tal[2] += ray.E; /* escaped */
+        push_seg(col, &seg);
+        if (seg.flags) flagged = 1;
+        continue;
+      }
+      seg.tri = h.tri;
+      seg.t = h.t;
+
+      double pt[3];
+      for (int i = 0; i < 3; ++i) pt[i] = ray.o[i] + h.t * ray.d[i];
+      double L1 = ray.L + n_cur * h.t;
+      /* attenuation inside a lossy medium: E <- E exp(-2 alpha d) */
+      double E1 = ray.E;
+      if (ray.medium != ORC_AIR) {
+        E1 = ray.E * exp(-2.0 * alpha_np(s, ray.medium, p->freq_hz) * h.t);
+        tal[1] += ray.E - E1;
+      }
+
+      const uint32_t mid = s->mat_id[h.tri];
+      const orc_material* m = &s->mat[mid];
+      double n[3];
+      tri_normal(s, h.tri, n);
+      double cos_i = -dot3(ray.d, n);
+      if (fabs(cos_i) < FLAG_COS) seg.flags |= SEG_GRAZE;
+      int entering = cos_i > 0.0;
+      double n1 = n_cur, n2;
+      int32_t next_medium;
+      if (entering) {
+        n2 = sqrt(m->eps_r);
+        next_medium = (int32_t)mid;
+      } else {
+        for (int i = 0; i < 3; ++i) n[i] = -n[i];
+        cos_i = -cos_i;
+        n2 = 1.0;
+        next_medium = ORC_AIR;
+      }
+
+      double R, cos_t = 0.0, sin2_t = 0.0;
+      int tir = 0;
+      if (m->pec) {
+        R = 1.0;
+      } else {
+        tir = orc_fresnel(n1, n2, cos_i, &R, &cos_t, &sin2_t);
+        if (fabs(sin2_t - 1.0) < FLAG_TIR) seg.flags |= SEG_TIR;
+      }
+      double T = (m->pec || tir) ? 0.0 : 1.0 - R;
+      int can_refract = !m->pec && !tir;
+
+      double d_refl[3], d_refr[3] = {0, 0, 0};
+      orc_reflect(ray.d, n, d_refl);
+      normalize3(d_refl);
+      if (can_refract) {
+        orc_refract(ray.d, n, n1 / n2, cos_i, cos_t, d_refr);
+        normalize3(d_refr);
+      }
+
+      /* traveled-path return: omega = theta0 + theta1 = 2 theta0, range = L1 */
+      double dn[3];
+      for (int i = 0; i < 3; ++i) dn[i] = -n[i];
+      double theta0 = orc_angle(ray.d, dn);
+      double ret_t = E1 * R * orc_brdf_window(m, 2.0 * theta0, b);
+
+      /* air-path return (multipath), bounce >= 1 only */
+      double ret_a = 0.0, range_a = 0.0;
+      int air_uses_T = 0;
+      if ((p->flags & ORC_MULTIPATH) && ray.bounce >= 1) {
+        int candidate = 0;
+        const double* dir_out = NULL;
+        double base = 0.0, cap_a = 0.0;
+        double v[3];
+        sub3(sensor, pt, v);
+        double dist = norm3(v);
+        double side = dot3(v, n) / dist;
+        if (entering && ray.medium == ORC_AIR) {
+          candidate = 1;
+          dir_out = d_refl;
+          base = E1 * R;
+          cap_a = E1 * R - ret_t;
+          if (fabs(side) < FLAG_COS) seg.flags |= SEG_VIS;
+          if (side <= 0.0) candidate = 0;
+        } else if (!entering && ray.medium != ORC_AIR && can_refract) {
+          candidate = 1;
+          air_uses_T = 1;
+          dir_out = d_refr;
+          base = E1 * T;
+          cap_a = E1 * T;
+          if (fabs(side) < FLAG_COS) seg.flags |= SEG_VIS;
+          if (side >= 0.0) candidate = 0;
+        }
+        if (candidate) {
+          double w_a = orc_brdf_window(m, orc_angle(dir_out, v), b);
+          if (w_a > 0.0) {
+            double dir[3] = {v[0] / dist, v[1] / dist, v[2] / dist};
+            int vflag = 0;
+            int occ = occluded(s, pt, dir, p->t_min, dist, h.tri, &vflag);
+            col->shadow_queries++;
+            if (vflag) seg.flags |= SEG_VIS;
+            if (!occ) {
+              double g = receive_weight(p, axis, sensor, pt);
+              ret_a = base * w_a * g;
+              if (ret_a > cap_a) ret_a = cap_a;
+              range_a = 0.5 * (L1 + dist);
+            }
+          }
+        }
+      }
+
+      /* record the returns (Sec. III-A: collected in a list) */
+      tal[0] += ret_t + ret_a;
+      if (ret_t > 0.0) {
+        double e = ret_t;
+        if (p->flags & ORC_SPECKLE) e *= speckle_factor(p, a, k, ray.path, ray.bounce, 0);
+        push_ret(col, k, L1, e);
+      }
+      if (ret_a > 0.0) {
+        double e = ret_a;
+        if (p->flags & ORC_SPECKLE) e *= speckle_factor(p, a, k, ray.path, ray.bounce, 1);
+        push_ret(col, k, range_a, e);
+      }
+
+      /* children: the remaining energy goes on (Sec. III-A) */
+      double e_refl = E1 * R - ret_t - (air_uses_T ? 0.0 : ret_a);
+      double e_refr = E1 * T - (air_uses_T ? ret_a : 0.0);
+      if (e_refl < 0.0) e_refl = 0.0;
+      if (e_refr < 0.0) e_refr = 0.0;
+      int deeper = ray.bounce + 1 < p->max_bounces;
+      if (fabs(L1 - r_max) <= FLAG_TREL * r_max) seg.flags |= SEG_RMAX;
+      int in_range = L1 < r_max;
+      int spawn_refl = deeper && in_range && e_refl >= p->min_energy;
+      int spawn_refr = deeper && in_range && can_refract && (p->flags & ORC_REFRACTION) && e_refr >= p->min_energy;
+      if (p->min_energy > 0.0 && deeper && in_range) {
+        if (fabs(e_refl - p->min_energy) < 1e-5 * p->min_energy) seg.flags |= SEG_EMIN;
+        if (can_refract && fabs(e_refr - p->min_energy) < 1e-5 * p->min_energy) seg.flags |= SEG_EMIN;
+      }
+      if (!spawn_refl) tal[3] += e_refl;
+      if (!spawn_refr) tal[3] += e_refr;
+
+      push_seg(col, &seg);
+      if (seg.flags) flagged = 1;
+
+      if (sp + 2 > cap) {
+        cap *= 2;
+        stack = (oray_t*)realloc(stack, cap * sizeof(oray_t));
+      }
+      if (spawn_refr) {
+        oray_t c;
+        memcpy(c.o, pt, sizeof pt);
+        memcpy(c.d, d_refr, sizeof d_refr);
+        c.E = e_refr;
+        c.L = L1;
+        c.medium = next_medium;
+        c.prev = h.tri;
+        c.path = (ray.path << 1) | 1u;
+        c.bounce = ray.bounce + 1;
+        stack[sp++] = c;
+      }
+      if (spawn_refl) {
+        oray_t c;
+        memcpy(c.o, pt, sizeof pt);
+        memcpy(c.d, d_refl, sizeof d_refl);
+        c.E = e_refl;
+        c.L = L1;
+        c.medium = ray.medium;
+        c.prev = h.tri;
+        c.path = ray.path << 1;
+        c.bounce = ray.bounce + 1;
+        stack[sp++] = c;
+      }
+    }
+    col->flagged[k] = (uint8_t)flagged;
+  }
+  free(stack);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. III-B: polar image by lookup and summation, starting at 0.          */
+/* A return within a small window of a bin edge also adds its energy to the */
+/* slack of both neighbouring bins.                                          */
+/* ------------------------------------------------------------------------ */
+static void bin_column(const orc_params* p, const column_t* col, int exclude_flagged, double* img, double* slack) {
+  for (size_t i = 0; i < col->n_ret; ++i) {
+    const oret_t* r = &col->ret[i];
+    if (exclude_flagged && col->flagged[r->k]) continue;
+    double x = r->range / p->bin_size;
+    double fb = floor(x);
+    if (fb < 0.0 || fb >= (double)p->n_bins) {
+      /* out of the image; still check the last edge */
+    } else {
+      img[(size_t)fb] += r->E;
+    }
+    if (slack) {
+      double edge = floor(x + 0.5);
+      double tol = 1e-4 > 4e-6 * x ? 1e-4 : 4e-6 * x;
+      if (fabs(x - edge) < tol) {
+        long lo = (long)edge - 1, hi = (long)edge;
+        if (lo >= 0 && lo < (long)p->n_bins) slack[lo] += r->E;
+        if (hi >= 0 && hi < (long)p->n_bins) slack[hi] += r->E;
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* public scan entry                                                        */
+/* ------------------------------------------------------------------------ */
+int orc_scan(const float* vertices, uint32_t n_vertices, const uint32_t* triangles, uint32_t n_triangles,
+             const uint16_t* material_ids, const orc_material* materials, uint32_t n_materials, const orc_pose* pose,
+             const orc_params* p, const uint32_t* az_list, uint32_t n_cols, int exclude_flagged, double* image,
+             double* slack, uint8_t* ray_flags, double* tallies, orc_segment* segs, uint64_t seg_cap,
+             uint64_t* n_segs, uint64_t* counts, int n_threads) {
+  if (p->n_azimuth == 0 || p->rays_per_beam == 0 || p->n_bins == 0 || p->max_bounces == 0) return 1;
+  for (uint32_t j = 0; j < n_triangles; ++j) {
+    for (int i = 0; i < 3; ++i)
+      if (triangles[3 * (size_t)j + i] >= n_vertices) return 2;
+    if (material_ids[j] >= n_materials) return 2;
+  }
+  scene_t s = {vertices, triangles, material_ids, materials, n_vertices, n_triangles, n_materials};
+  column_t* cols = (column_t*)calloc(n_cols, sizeof(column_t));
+  const uint32_t ns = p->rays_per_beam;
+  for (uint32_t c = 0; c < n_cols; ++c) {
+    cols[c].flagged = ray_flags + (size_t)c * ns;
+    cols[c].tally = tallies + (size_t)c * ns * 4;
+    memset(cols[c].tally, 0, sizeof(double) * 4 * ns);
+  }
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int c = 0; c < (int)n_cols; ++c) {
+    uint32_t a = az_list ? az_list[c] : (uint32_t)c;
+    trace_column(&s, p, pose, a, &cols[c]);
+    bin_column(p, &cols[c], exclude_flagged, image + (size_t)c * p->n_bins,
+               slack ? slack + (size_t)c * p->n_bins : NULL);
+  }
+  uint64_t ns_out = 0, q = 0, sq = 0, nret = 0;
+  for (uint32_t c = 0; c < n_cols; ++c) {
+    for (size_t i = 0; i < cols[c].n_seg; ++i) {
+      if (segs && ns_out < seg_cap) segs[ns_out] = cols[c].seg[i];
+      ns_out++;
+    }
+    q += cols[c].queries;
+    sq += cols[c].shadow_queries;
+    nret += cols[c].n_ret;
+    free(cols[c].seg);
+    free(cols[c].ret);
+  }
+  free(cols);
+  if (n_segs) *n_segs = ns_out;
+  if (counts) {
+    counts[0] = q;
+    counts[1] = sq;
+    counts[2] = nret;
+  }
+  return (segs && ns_out > seg_cap) ? 3 : 0;
+}
+
+/* number of threads an OpenMP region would use */
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. III-C noise and the post pass.                                       */
+/*  (1) optional beam pattern across azimuths (circular Gaussian),          */
+/*  (2) measurement noise as a Gaussian blur along range (zero padded),     */
+/*  (3) additive uniform system and ambient noise.                          */
+/* Taps: exp(-j^2 / (2 sigma^2)) for |j| <= ceil(3 sigma), normalised.      */
+/* ------------------------------------------------------------------------ */
+static int gauss_taps(double sigma, double* w, int max_r) {
+  if (!(sigma > 0.0)) {
+    w[0] = 1.0;
+    return 0;
+  }
+  int r = (int)ceil(3.0 * sigma);
+  if (r > max_r) r = max_r;
+  double sum = 0.0;
+  for (int j = -r; j <= r; ++j) {
+    w[j + r] = exp(-0.5 * (double)j * (double)j / (sigma * sigma));
+    sum += w[j + r];
+  }
+  for (int j = 0; j <= 2 * r; ++j) w[j] /= sum;
+  return r;
+}
+
+/* image: [n_cols][n_bins] for the azimuth indices az_list (NULL = all).  The
+   azimuth pattern needs every column and is refused on a subset. */
+int orc_post(double* image, const orc_params* p, const uint32_t* az_list, uint32_t n_cols) {
+  const uint32_t nb = p->n_bins;
+  enum { MAXR = 4096 };
+  double* tmp = NULL;
+  if (p->az_pattern_sigma > 0.0) {
+    if (n_cols != p->n_azimuth || az_list) return 1;
+    double* w = (double*)malloc(sizeof(double) * (2 * MAXR + 1));
+    int r = gauss_taps(p->az_pattern_sigma, w, MAXR);
+    tmp = (double*)calloc((size_t)n_cols * nb, sizeof(double));
+    for (uint32_t a = 0; a < n_cols; ++a)
+      for (int j = -r; j <= r; ++j) {
+        long src = ((long)a + j) % (long)n_cols;
+        if (src < 0) src += n_cols;
+        for (uint32_t i = 0; i < nb; ++i) tmp[(size_t)a * nb + i] += w[j + r] * image[(size_t)src * nb + i];
+      }
+    memcpy(image, tmp, sizeof(double) * (size_t)n_cols * nb);
+    free(tmp);
+    free(w);
+  }
+  if (p->blur_sigma_bins > 0.0) {
+    double* wtab = (double*)malloc(sizeof(double) * (2 * MAXR + 1));
+    int r = gauss_taps(p->blur_sigma_bins, wtab, MAXR);
+    double* col = (double*)malloc(sizeof(double) * nb);
+    for (uint32_t a = 0; a < n_cols; ++a) {
+      double* img = image + (size_t)a * nb;
+      for (uint32_t i = 0; i < nb; ++i) {
+        double acc = 0.0;
+        for (int j = -r; j <= r; ++j) {
+          long src = (long)i + j;
+          if (src < 0 || src >= (long)nb) continue;
+          acc += wtab[j + r] * img[src];
+        }
+        col[i] = acc;
+      }
+      memcpy(img, col, sizeof(double) * nb);
+    }
+    free(col);
+    free(wtab);
+  }
+  if (p->flags & ORC_NOISE) {
+    for (uint32_t c = 0; c < n_cols; ++c) {
+      uint32_t a = az_list ? az_list[c] : c;
+      for (uint32_t i = 0; i < nb; ++i) {
+        uint32_t xs[4], xa[4];
+        draw(p, a, i, 2u, xs);
+        draw(p, a, i, 3u, xa);
+        image[(size_t)c * nb + i] += p->noise_sys * orc_u24(xs[0]) + p->noise_amb * orc_u24(xa[0]);
+      }
+    }
+  }
+  return 0;
+}
+
+/* Sec. III-B: L_E = 10 log10(E_R / E0), E0 = 1 per column, mapped linearly
+   from [-cutoff_db, 0] dB to [0, 255] and clamped. */
+void orc_db_u8(const double* image, uint64_t n, double cutoff_db, uint8_t* out) {
+  for (uint64_t i = 0; i < n; ++i) {
+    double e = image[i];
+    double v;
+    if (!(e > 0.0)) {
+      v = 0.0;
+    } else {
+      double le = 10.0 * log10(e);
+      v = 255.0 * (le + cutoff_db) / cutoff_db;
+      if (v < 0.0) v = 0.0;
+      if (v > 255.0) v = 255.0;
+    }
+    out[i] = (uint8_t)floor(v + 0.5);
+  }
+}

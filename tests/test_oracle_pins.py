@@ -1,0 +1,569 @@
+"""Pins of the FP64 oracle against values that the paper and the mathematics
+fix independently of the oracle: published known-answer vectors, textbook
+closed forms, library routines (scipy) and brute force on tiny inputs.
+
+Every check lives in a ``check_*`` function so that the mutation tests in
+``test_oracle_mutants.py`` can run the same checks against builds of the
+oracle with a planted mistake.  CPU only.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, ndimage, special, stats
+
+from oracle import oracle as orc
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ----------------------------------------------------------------- helpers
+def scipy_window(A, B, C, w, b):
+    """W(w) of Eq. 4 for the lobe of Eq. 5 normalised over [-pi/2, pi/2],
+    integrated by scipy's QUADPACK; Z through log-gamma."""
+    S = 1.0 - A - B
+    lo, hi = max(w - b / 2, -math.pi / 2), min(w + b / 2, math.pi / 2)
+    if hi <= lo:
+        return 0.0
+    f = lambda a: A + B * math.cos(a) + S * max(math.cos(a), 0.0) ** C
+    pts = [0.0] if lo < 0.0 < hi else None
+    v, _ = integrate.quad(f, lo, hi, epsabs=1e-15, epsrel=1e-13, limit=1000, points=pts)
+    Z = A * math.pi + 2 * B + S * math.sqrt(math.pi) * math.exp(special.gammaln((C + 1) / 2) - special.gammaln(C / 2 + 1))
+    return v / Z
+
+
+def textbook_fresnel(n1, n2, ti):
+    """Unpolarised power reflectance from the angle forms of the Fresnel equations."""
+    if ti == 0.0:
+        return ((n1 - n2) / (n1 + n2)) ** 2
+    st = n1 / n2 * math.sin(ti)
+    if st >= 1.0:
+        return 1.0
+    tt = math.asin(st)
+    rs = math.sin(ti - tt) ** 2 / math.sin(ti + tt) ** 2
+    rp = math.tan(ti - tt) ** 2 / math.tan(ti + tt) ** 2
+    return 0.5 * (rs + rp)
+
+
+def make_material(eps_r=1.0, tan_d=0.0, A=0.6, B=0.1, C=30.0, pec=False):
+    return dict(eps_r=eps_r, loss_tangent=tan_d, A=A, B=B, C=C, pec=pec)
+
+
+WALL = dict(A=0.6, B=0.1, C=30.0)
+METAL_LOBE = dict(A=0.0, B=0.0, C=2000.0)
+
+
+def base_params(**kw):
+    p = dict(n_azimuth=1, rays_per_beam=1, max_bounces=1, n_bins=2000, beam_width=math.radians(10.0),
+             beam_prob=0.9, elevation=0.0, bin_size=0.01, t_min=1e-4, min_energy=0.0, freq_hz=76.5e9,
+             blur_sigma_bins=0.0, az_pattern_sigma=0.0, noise_sys=0.0, noise_amb=0.0, multipath=False,
+             refraction=True, speckle=False, noise=False, seed=0x5EED, scan_id=0)
+    p.update(kw)
+    for k in ("beam_width", "beam_prob", "elevation", "bin_size", "t_min", "freq_hz"):
+        p[k] = float(np.float32(p[k]))
+    return p
+
+
+POSE0 = dict(p=(0.0, 0.0, 0.0), q=(1.0, 0.0, 0.0, 0.0))
+
+
+class Soup:
+    """Tiny triangle soup for pin scenes."""
+
+    def __init__(self):
+        self.v, self.t, self.m = [], [], []
+
+    def quad(self, centre, u, v, half, normal, mat):
+        c = np.asarray(centre, float)
+        u = np.asarray(u, float) * half
+        v = np.asarray(v, float) * half
+        P = [c - u - v, c + u - v, c + u + v, c - u + v]
+        for a, b, cc in ((0, 1, 2), (0, 2, 3)):
+            A, B, Cc = P[a], P[b], P[cc]
+            if np.dot(np.cross(B - A, Cc - A), normal) < 0:
+                B, Cc = Cc, B
+            n0 = len(self.v)
+            self.v += [A, B, Cc]
+            self.t.append((n0, n0 + 1, n0 + 2))
+            self.m.append(mat)
+
+    def arrays(self):
+        return (np.asarray(self.v, np.float32), np.asarray(self.t, np.uint32), np.asarray(self.m, np.uint16))
+
+
+def frame(d):
+    """Two unit vectors orthogonal to d and to each other."""
+    d = np.asarray(d, float)
+    a = np.array([0.0, 0.0, 1.0]) if abs(d[2]) < 0.9 else np.array([1.0, 0.0, 0.0])
+    u = np.cross(d, a)
+    u /= np.linalg.norm(u)
+    v = np.cross(d, u)
+    return u, v
+
+
+def plane_distance(soup, tri, o, d):
+    """Distance along d from o to the plane of triangle tri as stored (float32)."""
+    v, t, _ = soup.arrays()
+    a, b, c = (v[t[tri, i]].astype(np.float64) for i in range(3))
+    n = np.cross(b - a, c - a)
+    return float(np.dot(a - o, n) / np.dot(d, n))
+
+
+def single_return(img):
+    nz = np.nonzero(img)[0]
+    return nz, img[nz]
+
+
+# ----------------------------------------------------------------- Philox
+def check_philox_kat():
+    for row in _golden_rows("philox4x32_10_kat.txt"):
+        vals = [int(x, 16) for x in row]
+        out = orc.philox(vals[0:4], vals[4:6])
+        assert [int(x) for x in out] == vals[6:10], (row, [hex(int(x)) for x in out])
+
+
+def check_u24():
+    assert orc.u24(0) == 2.0 ** -24
+    assert orc.u24(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    rng = np.random.default_rng(1)
+    for x in rng.integers(0, 2 ** 32, size=200, dtype=np.uint64):
+        u = orc.u24(int(x))
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u               # exact in float32 as well
+        assert (u * 2 ** 24 - 1) / 2 == (int(x) >> 9)   # uses the top 23 bits
+
+
+# ----------------------------------------------------------------- D3 (Eq. 2)
+def check_d3_sigma():
+    # sqrt(2) erfinv(P) is the (1+P)/2 quantile of N(0,1)
+    q = stats.norm.ppf(0.95)
+    assert abs(math.sqrt(2) * orc.erfinv(0.9) - q) < 1e-12
+    assert abs(orc.d3_sigma(math.radians(10), 0.9) - math.radians(5) / q) < 1e-15
+    assert abs(math.degrees(orc.d3_sigma(math.radians(10), 0.9)) - 3.0397841595588) < 1e-9
+    assert orc.d3_sigma(0.0, 0.9) == 0.0
+
+
+def check_d3_statistics(n=40000):
+    p = base_params(n_azimuth=1, rays_per_beam=n)
+    sigma = orc.d3_sigma(p["beam_width"], p["beam_prob"])
+    r = np.empty(n)
+    w = np.empty(n)
+    ang = np.empty(n)
+    axis = orc.beam_axis(p, POSE0, 0)
+    for k in range(n):
+        o, d, r[k], w[k] = orc.d3_ray(p, POSE0, 0, k)
+        ang[k] = math.atan2(np.linalg.norm(np.cross(d, axis)), np.dot(d, axis))
+    assert np.allclose(axis, [1, 0, 0])
+    z = r / sigma
+    # E[r^2] = sigma^2 (4 standard errors)
+    assert abs(np.mean(z ** 2) - 1.0) < 4 * math.sqrt(2.0 / n)
+    # P(|r| <= b/2) = P
+    frac = np.mean(np.abs(r) <= p["beam_width"] / 2)
+    assert abs(frac - 0.9) < 4 * math.sqrt(0.09 / n)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    assert stats.kstest((w + math.pi) / (2 * math.pi), "uniform").pvalue > 1e-4
+    # the ray's angle to the beam axis is |r| to second order
+    assert np.max(np.abs(ang - np.abs(r))) < 0.01 * np.max(np.abs(r)) ** 2 + 1e-12
+    # each component carries half the variance: r cos w and r sin w
+    assert abs(np.mean((r * np.cos(w)) ** 2) / sigma ** 2 - 0.5) < 4 * math.sqrt(0.5 / n)
+
+
+def check_d3_pose_and_azimuth():
+    p = base_params(n_azimuth=8, elevation=math.radians(5.0), beam_width=0.0)
+    yaw = 0.3
+    pz = dict(p=(1.0, 2.0, 3.0), q=(math.cos(yaw / 2), 0.0, 0.0, math.sin(yaw / 2)))
+    for a in range(8):
+        o, d, r, _ = orc.d3_ray(p, pz, a, 0)
+        phi = 2 * math.pi * a / 8 + yaw
+        el = float(np.float32(math.radians(5.0)))
+        expect = [math.cos(el) * math.cos(phi), math.cos(el) * math.sin(phi), math.sin(el)]
+        assert r == 0.0
+        assert np.allclose(o, [1, 2, 3])
+        assert np.allclose(d, expect, atol=1e-14)
+
+
+# ----------------------------------------------------------------- Fresnel / Snell
+def check_fresnel_closed_forms():
+    for name, n1, n2, deg, R in _golden_rows("fresnel_brdf_pins.txt")[:4]:
+        n1, n2, ti, R = float(n1), float(n2), math.radians(float(deg)), float(R)
+        got, ct, tir = orc.fresnel(n1, n2, math.cos(ti))
+        assert not tir
+        assert abs(got - R) < 1e-12, name
+        assert abs(got - textbook_fresnel(n1, n2, ti)) < 1e-12, name
+    # Brewster: the p reflectance vanishes, R = Rs / 2
+    R, _, _ = orc.fresnel(1.0, 2.0, math.cos(math.atan(2.0)))
+    assert abs(R - 0.18) < 1e-12
+    # critical angle inside n = 2: 30 deg
+    assert orc.fresnel(2.0, 1.0, math.cos(math.radians(30.0) + 1e-9))[2]
+    assert not orc.fresnel(2.0, 1.0, math.cos(math.radians(30.0) - 1e-9))[2]
+    assert orc.fresnel(2.0, 1.0, math.cos(math.radians(45.0)))[0] == 1.0
+    # reciprocity: the same interface seen from both sides reflects the same
+    for deg in (5, 17, 29):
+        ti = math.radians(deg)
+        R12, ct, _ = orc.fresnel(2.0, 1.0, math.cos(ti))
+        R21, _, _ = orc.fresnel(1.0, 2.0, ct)
+        assert abs(R12 - R21) < 1e-12
+    # equal indices: no interface
+    assert orc.fresnel(1.5, 1.5, 0.3)[0] < 1e-30
+
+
+def check_snell():
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        if np.dot(d, n) > 0:
+            d = -d
+        cos_i = -np.dot(d, n)
+        n1, n2 = rng.uniform(1, 3, size=2)
+        R, cos_t, tir = orc.fresnel(n1, n2, cos_i)
+        refl = orc.reflect(d, n)
+        assert abs(np.linalg.norm(refl) - 1) < 1e-12
+        assert abs(np.dot(refl, n) - cos_i) < 1e-12                 # theta1 = theta0
+        assert abs(np.dot(np.cross(d, n), refl)) < 1e-12           # plane of incidence
+        if tir:
+            assert (n1 / n2) * math.sqrt(max(0.0, 1 - cos_i ** 2)) >= 1 - 1e-12
+            continue
+        t = orc.refract(d, n, n1 / n2, cos_i, cos_t)
+        assert abs(np.linalg.norm(t) - 1) < 1e-12
+        sin_i = np.linalg.norm(np.cross(d, n))
+        sin_t = np.linalg.norm(np.cross(t, n))
+        assert abs(n1 * sin_i - n2 * sin_t) < 1e-12                # Snell
+        assert np.dot(t, n) < 0                                    # goes through
+        assert abs(np.dot(np.cross(d, n), t)) < 1e-12              # plane of incidence
+
+
+# ----------------------------------------------------------------- BRDF (Eq. 3-5)
+def check_brdf_normalisation():
+    for A, B, C in ((0.6, 0.1, 30.0), (0.6, 0.1, 70.0), (0.01, 0.95, 1900.0), (0.0, 0.0, 2000.0),
+                    (0.2, 0.3, 2.5), (1.0, 0.0, 0.0), (0.0, 1.0, 5.0)):
+        m = make_material(A=A, B=B, C=C)
+        v, _ = integrate.quad(lambda w: orc.brdf_density(m, w), -math.pi / 2, math.pi / 2, points=[0.0],
+                              limit=2000, epsabs=1e-13, epsrel=1e-12)
+        assert abs(v - 1.0) < 1e-9, (A, B, C, v)
+        assert abs(orc.brdf_window(m, 0.0, math.pi) - 1.0) < 1e-10
+    # Wallis: integral of cos^n over [-pi/2, pi/2]
+    for nn in range(0, 12):
+        dfac = lambda k: 1 if k <= 0 else k * dfac(k - 2)
+        exact = (math.pi if nn % 2 == 0 else 2.0) * dfac(nn - 1) / dfac(nn)
+        assert abs(orc.int_cospow(nn, -math.pi / 2, math.pi / 2) - exact) < 1e-12
+
+
+def check_brdf_window_pins():
+    rows = _golden_rows("fresnel_brdf_pins.txt")[4:]
+    b10 = math.radians(10.0)
+    bt = math.radians(2.960736528512652)
+    for name, A, B, C, w10, wt in rows:
+        m = make_material(A=float(A), B=float(B), C=float(C))
+        assert abs(orc.brdf_window(m, 0.0, b10) - float(w10)) < 1e-12, name
+        assert abs(orc.brdf_window(m, 0.0, bt) - float(wt)) < 1e-12, name
+    m = make_material(**WALL)
+    for w in (-1.2, -0.3, 0.2, 0.7, 1.5):
+        assert abs(orc.brdf_window(m, w, b10) - scipy_window(0.6, 0.1, 30.0, w, b10)) < 1e-12
+        assert abs(orc.brdf_window(m, w, b10) - orc.brdf_window(m, -w, b10)) < 1e-14
+    assert orc.brdf_window(m, math.pi / 2 + b10 / 2 + 1e-9, b10) == 0.0
+    assert orc.brdf_window(m, math.pi / 2 + b10 / 2 - 1e-3, b10) > 0.0
+
+
+# ----------------------------------------------------------------- intersection
+def check_closest_brute_force():
+    """Oracle closest hit vs a different algorithm: plane solve with numpy."""
+    from paper_2310_03505_gb300 import scenes
+    sc = scenes.tiny_room()
+    V = sc.vertices.astype(np.float64)
+    T = sc.triangles
+    v0, v1, v2 = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    rng = np.random.default_rng(3)
+    for _ in range(150):
+        o = rng.uniform([-4.5, -4.5, 0.2], [4.5, 4.5, 2.8])
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        # solve o + t d = v0 + b1 (v1 - v0) + b2 (v2 - v0) for every triangle
+        M = np.stack([-np.broadcast_to(d, v0.shape), v1 - v0, v2 - v0], axis=2)
+        ok = np.abs(np.linalg.det(M)) > 1e-14
+        sol = np.full((len(T), 3), np.nan)
+        sol[ok] = np.linalg.solve(M[ok], (o - v0)[ok][..., None])[..., 0]
+        t, b1, b2 = sol[:, 0], sol[:, 1], sol[:, 2]
+        valid = ok & (t > 1e-4) & (b1 >= 0) & (b2 >= 0) & (b1 + b2 <= 1)
+        tri, tt, fl = orc.closest(sc.vertices, sc.triangles, o, d)
+        if not valid.any():
+            assert tri is None
+            continue
+        tmin = np.min(t[valid])
+        cand = np.nonzero(valid & (t <= tmin * (1 + 1e-12)))[0]
+        assert abs(tt - tmin) < 1e-9 * max(1.0, tmin)
+        if fl == 0:
+            assert tri == cand.min()
+        assert fl != 0 or len(cand) == 1
+
+
+# ----------------------------------------------------------------- scans on pin scenes
+def _scan(soup, mats, p, pose=POSE0, **kw):
+    v, t, m = soup.arrays()
+    return orc.scan(v, t, m, mats, pose, p, **kw)
+
+
+def check_normal_incidence_plane():
+    """Plane perpendicular to the drawn ray at distance D: one return at bin
+    floor(D / bin) with energy R W(0): W(0) for a perfect conductor, W(0)/9
+    for eps_r = 4."""
+    p = base_params()
+    _, d, _, _ = orc.d3_ray(p, POSE0, 0, 0)
+    u, v = frame(d)
+    D = 10.013
+    b = p["beam_width"]                     # the float32 value both sides read
+    for mat, expect in ((make_material(pec=True, **METAL_LOBE), scipy_window(0, 0, 2000, 0.0, b)),
+                        (make_material(eps_r=4.0, tan_d=0.01, **WALL), scipy_window(0.6, 0.1, 30, 0.0, b) / 9.0)):
+        s = Soup()
+        s.quad(D * d, u, v, 2.0, -d, 0)
+        r = _scan(s, [mat], p)
+        nz, e = single_return(r["image"][0])
+        assert list(nz) == [int(D / p["bin_size"])]
+        assert abs(e[0] - expect) < 1e-9 * expect
+        assert abs(r["tallies"][0, 0].sum() - 1.0) < 1e-12
+
+
+def check_oblique_plane():
+    """Plane tilted by theta0 = 20 deg: return R(20 deg) W(40 deg) at the range
+    along the ray (traveled path: omega = theta0 + theta1)."""
+    p = base_params()
+    _, d, _, _ = orc.d3_ray(p, POSE0, 0, 0)
+    u, v = frame(d)
+    th = math.radians(20.0)
+    n = -(math.cos(th) * d + math.sin(th) * u)
+    D = 7.0153
+    s = Soup()
+    nu = np.cross(n, v)
+    nu /= np.linalg.norm(nu)
+    s.quad(D * d, nu, v, 3.0, n, 0)
+    r = _scan(s, [make_material(eps_r=4.0, **WALL)], p)
+    nz, e = single_return(r["image"][0])
+    assert list(nz) == [int(D / p["bin_size"])]
+    expect = textbook_fresnel(1.0, 2.0, th) * scipy_window(0.6, 0.1, 30.0, 2 * th, p["beam_width"])
+    assert abs(e[0] - expect) < 1e-6 * expect
+
+
+def check_slab():
+    """eps_r = 4 slab of thickness t backed by a perfect conductor, normal
+    incidence, multipath off: returns at D (W(0)/9), at D + 2t (optical path;
+    (8/9) e^{-2 alpha t} W_metal(0)) and the internal multiple at D + 4t."""
+    p = base_params(max_bounces=3)
+    _, d, _, _ = orc.d3_ray(p, POSE0, 0, 0)
+    u, v = frame(d)
+    D, th = 5.0134, 0.0512
+    s = Soup()
+    s.quad(D * d, u, v, 2.0, -d, 0)                 # front face, dielectric
+    s.quad((D + th) * d, u, v, 2.0, -d, 1)          # back face, metal (faces the slab)
+    mats = [make_material(eps_r=4.0, tan_d=0.01, **WALL), make_material(pec=True, **METAL_LOBE)]
+    r = _scan(s, mats, p)
+    alpha = math.pi * 2.0 * 0.01 * p["freq_hz"] / 299792458.0
+    assert abs(alpha - 16.0336) < 1e-3                       # 1/e power depth 3.12 cm
+    t_front = plane_distance(s, 0, np.zeros(3), d)
+    att = math.exp(-2 * alpha * (plane_distance(s, 2, np.zeros(3), d) - t_front))
+    w_wall, w_metal = scipy_window(0.6, 0.1, 30, 0.0, p["beam_width"]), scipy_window(0, 0, 2000, 0.0, p["beam_width"])
+    e0 = w_wall / 9
+    e1 = 8 / 9 * att * w_metal
+    e2 = 8 / 9 * att * (1 - w_metal) * att * (1 / 9) * w_wall
+    img = r["image"][0]
+    bins = [int(D / 0.01), int((D + 2 * th) / 0.01), int((D + 4 * th) / 0.01)]
+    nz = np.nonzero(img)[0]
+    assert list(nz) == bins, (nz, bins)
+    # the third return carries 1 - W_metal(0) ~ 1e-4: quadrature error is amplified there
+    for b, e, tol in zip(bins, (e0, e1, e2), (1e-9, 1e-9, 1e-7)):
+        assert abs(img[b] - e) < tol * e, (b, img[b], e)
+    assert abs(r["tallies"][0, 0].sum() - 1.0) < 1e-12
+
+
+def check_slab_multipath():
+    """Same slab with multipath on: the exit hit at bounce 2 adds an air-path
+    return at ((D + 4t) + D) / 2 = D + 2t carrying T W(0) g_rx."""
+    p = base_params(max_bounces=3, multipath=True)
+    _, d, _, _ = orc.d3_ray(p, POSE0, 0, 0)
+    u, v = frame(d)
+    D, th = 5.0134, 0.0512
+    s = Soup()
+    s.quad(D * d, u, v, 2.0, -d, 0)
+    s.quad((D + th) * d, u, v, 2.0, -d, 1)
+    mats = [make_material(eps_r=4.0, tan_d=0.01, **WALL), make_material(pec=True, **METAL_LOBE)]
+    r = _scan(s, mats, p)
+    alpha = math.pi * 2.0 * 0.01 * p["freq_hz"] / 299792458.0
+    att = math.exp(-2 * alpha * (plane_distance(s, 2, np.zeros(3), d) - plane_distance(s, 0, np.zeros(3), d)))
+    w_wall, w_metal = scipy_window(0.6, 0.1, 30, 0.0, p["beam_width"]), scipy_window(0, 0, 2000, 0.0, p["beam_width"])
+    sigma = p["beam_width"] / 2 / stats.norm.ppf(0.95)
+    delta = math.acos(np.clip(d[0], -1, 1))                  # beam axis is +x
+    g = math.exp(-0.5 * (delta / sigma) ** 2)
+    e_in2 = 8 / 9 * att * (1 - w_metal) * att
+    e_air = e_in2 * (8 / 9) * w_wall * g
+    e1 = 8 / 9 * att * w_metal
+    b = int((D + 2 * th) / 0.01)
+    assert abs(r["image"][0][b] - (e1 + e_air)) < 1e-9 * (e1 + e_air)
+
+
+def check_corner_reflector():
+    """Perfect-conductor trihedral facing the sensor: the ray returns after
+    three bounces; the third-bounce air-path return lands at half the exact
+    round trip (path to the third hit + distance back) with energy
+    W_metal(omega_a) g_rx, omega_a the angle between the reflected direction
+    and the direction to the sensor."""
+    p = base_params(max_bounces=3, multipath=True, beam_width=math.radians(1.0), bin_size=0.005)
+    _, d, _, _ = orc.d3_ray(p, POSE0, 0, 0)
+    # local frame: faces on x=0, y=0, z=0, normals +x, +y, +z, diagonal (1,1,1)/sqrt(3) -> -x world
+    diag = np.ones(3) / math.sqrt(3)
+    e1 = np.array([1.0, -1.0, 0.0]) / math.sqrt(2)
+    e2 = np.cross(diag, e1)
+    Rm = np.stack([-np.array([1.0, 0, 0]), np.array([0, 1.0, 0]), np.array([0, 0, 1.0])], 1) @ \
+        np.stack([diag, e1, e2], 0)
+    apex = np.array([8.0, 0.0, 0.0])
+    s = Soup()
+    planes = []
+    for ax in range(3):
+        nl = np.eye(3)[ax]
+        ua, va = np.eye(3)[(ax + 1) % 3], np.eye(3)[(ax + 2) % 3]
+        c = apex + Rm @ (0.5 * ua + 0.5 * va)
+        s.quad(c, Rm @ ua, Rm @ va, 0.5, Rm @ nl, 0)
+        planes.append((Rm @ nl, apex))
+    mats = [make_material(pec=True, **METAL_LOBE)]
+    r = _scan(s, mats, p)
+    # reference path with numpy over the six stored (float32) triangles:
+    # solve o + t d = a + b1 (b - a) + b2 (c - a), keep the nearest, mirror
+    vs, ts, _ = s.arrays()
+    tri = [tuple(vs[ts[j, i]].astype(np.float64) for i in range(3)) for j in range(len(ts))]
+    o = np.zeros(3)
+    dd = d.copy()
+    L = 0.0
+    pts = []
+    skip = None
+    for _ in range(3):
+        best = None
+        for j, (a, b_, c) in enumerate(tri):
+            if j == skip:
+                continue
+            M = np.stack([-dd, b_ - a, c - a], 1)
+            t, b1, b2 = np.linalg.solve(M, o - a)
+            if t > 1e-4 and b1 >= 0 and b2 >= 0 and b1 + b2 <= 1 and (best is None or t < best[0]):
+                best = (t, j)
+        t, j = best
+        a, b_, c = tri[j]
+        n = np.cross(b_ - a, c - a)
+        n /= np.linalg.norm(n)
+        o = o + t * dd
+        L += t
+        pts.append(o)
+        dd = dd - 2 * np.dot(dd, n) * n
+        skip = j
+    # after three mirror reflections the ray is reversed
+    assert np.allclose(dd, -d, atol=1e-6)
+    p3 = pts[-1]
+    to_s = -p3
+    dist = np.linalg.norm(to_s)
+    w_a = math.atan2(np.linalg.norm(np.cross(dd, to_s)), np.dot(dd, to_s))
+    sigma = p["beam_width"] / 2 / stats.norm.ppf(0.95)
+    delta = math.atan2(np.linalg.norm(np.cross(p3, [1, 0, 0])), p3[0])
+    g = math.exp(-0.5 * (delta / sigma) ** 2)
+    expect = min(scipy_window(0.0, 0.0, 2000.0, w_a, p["beam_width"]) * g, 1.0)
+    b = int((L + dist) / 2 / p["bin_size"])
+    img = r["image"][0]
+    assert abs(img[b] - expect) < 1e-7 * expect + 1e-12, (img[b], expect)
+    assert abs((L + dist) / 2 - 8.0) < 0.05          # plane-wave picture: range of the apex
+    assert abs(r["tallies"][0, 0].sum() - 1.0) < 1e-12
+
+
+def check_lidar_like():
+    """One bounce, one ray per azimuth, b -> narrow: the image holds a single
+    return per azimuth at the plain ray-cast distance (Sec. IV-A baseline)."""
+    from paper_2310_03505_gb300 import scenes
+    sc = scenes.tiny_room()
+    p = base_params(n_azimuth=64, rays_per_beam=1, max_bounces=1, n_bins=1142, bin_size=0.0438,
+                    beam_width=math.radians(2.96), multipath=True)
+    pz = dict(p=(0.0, 0.0, 0.5), q=(1.0, 0.0, 0.0, 0.0))
+    r = orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, p)
+    V = sc.vertices.astype(np.float64)
+    T = sc.triangles
+    v0, v1, v2 = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    nrm = np.cross(v1 - v0, v2 - v0)
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    for a in range(64):
+        o, d, _, _ = orc.d3_ray(p, pz, a, 0)
+        M = np.stack([-np.broadcast_to(d, v0.shape), v1 - v0, v2 - v0], axis=2)
+        sol = np.linalg.solve(M, (o - v0)[..., None])[..., 0]
+        t, b1, b2 = sol.T
+        valid = (t > 1e-4) & (b1 >= 0) & (b2 >= 0) & (b1 + b2 <= 1)
+        j = np.nonzero(valid)[0][np.argmin(t[valid])]
+        nz = np.nonzero(r["image"][a])[0]
+        assert len(nz) <= 1
+        th = math.acos(abs(np.dot(d, nrm[j])))
+        mat = sc.materials[sc.material_ids[j]]
+        R = 1.0 if mat["pec"] else textbook_fresnel(1.0, math.sqrt(mat["eps_r"]), th)
+        e = R * scipy_window(mat["A"], mat["B"], mat["C"], 2 * th, p["beam_width"])
+        if e > 0:
+            assert list(nz) == [int(t[j] / p["bin_size"])], a
+            assert abs(r["image"][a][nz[0]] - e) < 1e-7 * e + 1e-15
+        else:
+            assert len(nz) == 0
+
+
+def check_conservation_tiny():
+    from paper_2310_03505_gb300 import scenes
+    sc, pz, s = scenes.config_tiny()
+    r = orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, s, az_list=range(0, 400, 25))
+    assert np.max(np.abs(r["tallies"].sum(-1) - 1.0 / s["rays_per_beam"])) < 1e-12
+    assert np.all(r["tallies"] >= -1e-18)
+    # every returned joule that lands in the image is in the raw image
+    assert r["raw"].sum() <= r["tallies"][..., 0].sum() + 1e-12
+
+
+def check_post_pass():
+    """Blur / beam pattern against scipy's Gaussian filter (zero padding along
+    range, wrap-around along azimuth, same truncation for sigma = 1, 2) and
+    noise bounds."""
+    rng = np.random.default_rng(5)
+    img = rng.uniform(size=(16, 50)) * (rng.uniform(size=(16, 50)) < 0.2)
+    for sig in (1.0, 2.0):
+        p = base_params(n_azimuth=16, n_bins=50, blur_sigma_bins=sig)
+        got = orc.post(img, p)
+        ref = ndimage.gaussian_filter1d(img, sig, axis=1, mode="constant", cval=0.0, truncate=3.0)
+        assert np.max(np.abs(got - ref)) < 1e-14
+        p = base_params(n_azimuth=16, n_bins=50, az_pattern_sigma=sig)
+        got = orc.post(img, p)
+        ref = ndimage.gaussian_filter1d(img, sig, axis=0, mode="wrap", truncate=3.0)
+        assert np.max(np.abs(got - ref)) < 1e-14
+    p = base_params(n_azimuth=32, n_bins=100, noise=True, noise_sys=0.3, noise_amb=0.1)
+    z = orc.post(np.zeros((32, 100)), p)
+    assert np.all(z > 0) and np.all(z < 0.4)
+    assert abs(z.mean() - 0.2) < 0.01
+    # independent uniforms for the two terms: variance (0.3^2 + 0.1^2) / 12
+    assert abs(z.var() - 0.1 / 12) < 0.0015
+
+
+def check_db_map():
+    img = np.array([1.0, 10 ** -4.0, 10 ** -2.0, 0.0, 10 ** -9.0, 2.0])
+    out = orc.db_u8(img, 40.0)
+    assert list(out) == [255, 0, 128, 0, 0, 255]
+
+
+ALL_CHECKS = [check_philox_kat, check_u24, check_d3_sigma, check_d3_pose_and_azimuth, check_fresnel_closed_forms,
+              check_snell, check_brdf_normalisation, check_brdf_window_pins, check_closest_brute_force,
+              check_normal_incidence_plane, check_oblique_plane, check_slab, check_slab_multipath,
+              check_corner_reflector, check_lidar_like, check_conservation_tiny, check_post_pass, check_db_map]
+
+
+@pytest.mark.parametrize("check", ALL_CHECKS, ids=lambda f: f.__name__[6:])
+def test_pin(check):
+    check()
+
+
+def test_d3_statistics():
+    check_d3_statistics()
