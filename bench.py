@@ -1,0 +1,343 @@
+"""Benchmark of the radar scan hot path on GB300.
+
+One step = one pass of the whole hot path on the medium campus workload
+(about 200k triangles, 400 beams x 200 rays, at most 5 bounces, refraction
+and multipath on, 2000 range bins): LBVH rebuild from the resident vertices
+(ingest, Morton, radix sort, Karras hierarchy, refit) followed by one polar
+scan (raygen, trace / shade per bounce, range-bin accumulation, post pass).
+Each step uses a new scan id, so every step traces new rays.
+
+Metric: Mrays/s = closest-hit queries over all bounces / device time of the
+steps (CUDA events on the library's stream; L2 flushed between steps with a
+256 MiB write, outside the timed events).  Also reported: scans/s, per-step
+latency p50/p99, the roofline of the dominant kernel (trace), the oracle
+timed on the host cores, an end-to-end figure through the C ABI with host
+buffers, and GPU clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun (N > 1) every rank runs its own scans (independent scan ids,
+weak scaling); rank 0 prints the line, time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "campus_200k_tris_400x200_rays_5_bounces_2000_bins"
+L2_FLUSH_BYTES = 256 << 20
+METRIC = "Mrays/s (all bounces) & scans/s on 1 GB300; p50/p99 served scan latency"
+RAY_IO_BYTES = 48 + 16          # ray record read + hit record written per closest-hit query
+NODE_BYTES, TRI_BYTES = 64, 48  # BVH node and triangle record
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def shard_scan_ids(rank: int, steps: int, warmup: int):
+    """Scan ids of one rank: disjoint across ranks (weak scaling, no exchange)."""
+    base = rank * (steps + warmup)
+    return list(range(base, base + warmup)), list(range(base + warmup, base + warmup + steps))
+
+
+def reduce_timing(local_ms: float, local_units: float, world: int, device=None):
+    """Job time = max over ranks, units = sum over ranks."""
+    if world == 1:
+        return local_ms, local_units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([local_units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, path: str):
+        self.path = path
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_from_profiles():
+    """Per-launch DRAM bytes of the trace kernel from the committed ncu summary,
+    valid only while the kernel source matches the hash it was taken on."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "trace_kernel_campus_ncu.json")
+    src = os.path.join(ROOT, "paper_2310_03505_gb300", "csrc", "rr_trace.cu")
+    if not (os.path.exists(p) and os.path.exists(src)):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if d.get("source_sha256_16") != h:
+        return None
+    return d.get("dram_bytes_per_trace_launch_full_scale")
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_sample(sc, pz, params, budget_s: float = 12.0, min_cols: int = 2):
+    """Time the FP64 oracle (as it stands) on a bounded sample of azimuth
+    columns of the same workload; returns (Mrays/s, cores, sample text, queries, seconds)."""
+    from oracle import oracle as orc
+    cores = orc.max_threads()
+    cols, q_tot, t_tot = [], 0, 0.0
+    order = list(np.random.default_rng(12345).permutation(params["n_azimuth"]))
+    while order and (t_tot < budget_s or len(cols) < min_cols):
+        batch = [int(order.pop()) for _ in range(min(cores, len(order)))]
+        t0 = time.perf_counter()
+        r = orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, params, az_list=batch,
+                     want_segments=False)
+        t_tot += time.perf_counter() - t0
+        q_tot += int(r["counts"][0])
+        cols += batch
+    sample = (f"{len(cols)} of {params['n_azimuth']} azimuth columns ({len(cols) * params['rays_per_beam']} "
+              f"initial rays, all bounces), FP64 brute force over all {sc.n_triangles} triangles")
+    return q_tot / t_tot / 1e6, cores, sample, q_tot, t_tot
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+
+    from paper_2310_03505_gb300 import scenes
+    sc, pz, params = scenes.config_medium()
+
+    if args.impl == "reference":
+        # the oracle arm: rank 0 only, on the host cores
+        if rank != 0:
+            return
+        import oracle.oracle as orc
+        orc.build()
+        per_step_budget = max(2.0, 60.0 / max(args.steps, 1))
+        for _ in range(args.warmup):
+            oracle_sample(sc, pz, params, budget_s=0.0, min_cols=1)
+        t_all, q_all = 0.0, 0
+        times = []
+        for _ in range(args.steps):
+            v, cores, sample, q, t = oracle_sample(sc, pz, params, budget_s=per_step_budget)
+            t_all += t
+            q_all += q
+            times.append(t)
+        value = q_all / t_all / 1e6
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD, "triangles": sc.n_triangles},
+                "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    from paper_2310_03505_gb300 import build, rr
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    rr.load()
+    torch.cuda.init()
+    stream = torch.cuda.current_stream()
+
+    d_vtx = torch.from_numpy(sc.vertices).to(device)
+    h = rr.rr_scene_create(d_vtx, sc.triangles, sc.material_ids, sc.materials)
+    info = rr.rr_scene_info_get(h)
+    img = torch.zeros(params["n_azimuth"], params["n_bins"], device=device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    warm_ids, step_ids = shard_scan_ids(rank, args.steps, args.warmup)
+
+    def step(scan_id):
+        rr.rr_scene_update_vertices(h, d_vtx)
+        rr.rr_scan_async(h, pz, {**params, "scan_id": scan_id}, img)
+
+    for sid in warm_ids:
+        step(sid)
+    rr.rr_scene_sync(h)
+
+    # traversal counters of one untimed scan (per-query algorithmic bytes)
+    rr.rr_scene_stats(h, reset=True)
+    rr.rr_scan(h, pz, {**params, "scan_id": 10 ** 6 + rank, "count_traversal": True}, img)
+    cst = rr.rr_scene_stats(h, reset=True)
+    q_cal = cst["closest_queries"] + cst["anyhit_queries"]
+    nodes_per_q = cst["nodes_visited"] / max(q_cal, 1)
+    tris_per_q = cst["tris_tested"] / max(q_cal, 1)
+    any_per_closest = cst["anyhit_queries"] / max(cst["closest_queries"], 1)
+    bytes_per_closest = (1 + any_per_closest) * (nodes_per_q * NODE_BYTES + tris_per_q * TRI_BYTES) + RAY_IO_BYTES
+
+    # timed region
+    rr.rr_profile_read(h, reset=True)
+    rr.rr_profile_enable(h, True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in step_ids]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in step_ids]
+    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                                              else "_work", f"clocks_rank{rank}.csv")) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i, sid in enumerate(step_ids):
+        flush.fill_(float(i))                      # evict the scene from L2 (outside the events)
+        starts[i].record(stream)
+        step(sid)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    rc_status = rr.rr_scene_sync(h)
+    clk = clocks.stop() if clocks else None
+    rr.rr_profile_enable(h, False)
+    prof = rr.rr_profile_read(h, reset=True)
+    st = rr.rr_scene_stats(h, reset=True)
+    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    local_ms = float(np.sum(per_step))
+    job_ms, job_queries = reduce_timing(local_ms, float(st["closest_queries"]), world, device)
+
+    mrays = job_queries / (job_ms * 1e-3) / 1e6
+    scans_per_s = world * args.steps / (job_ms * 1e-3)
+    trace_ms, trace_launches = prof["trace"]
+    peak, peak_kind = measured_peaks()
+    algo_bytes = bytes_per_closest * st["closest_queries"]
+    achieved_gbs = algo_bytes / (trace_ms * 1e-3) / 1e9 if trace_ms > 0 else None
+    traffic = traffic_from_profiles()
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_vtx = torch.from_numpy(sc.vertices).pin_memory()
+        h_img = torch.zeros(params["n_azimuth"], params["n_bins"]).pin_memory()
+        rr.rr_scene_stats(h, reset=True)
+        t_e2e = 0.0
+        for i, sid in enumerate(step_ids):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rr.rr_scene_update_vertices(h, h_vtx)
+            rr.rr_scan(h, pz, {**params, "scan_id": sid}, h_img)     # blocking: D2H included
+            t_e2e += time.perf_counter() - t0
+        st2 = rr.rr_scene_stats(h, reset=True)
+        e2e_ms, e2e_q = reduce_timing(1e3 * t_e2e, float(st2["closest_queries"]), world, device)
+        e2e = {"value": e2e_q / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
+               "h2d_bytes_per_step": int(sc.vertices.nbytes + 28 + 80),
+               "d2h_bytes_per_step": int(h_img.numel() * 4), "scans_per_s": world * args.steps / (e2e_ms * 1e-3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample, _, _ = oracle_sample(sc, pz, params)
+        cpu = {"value": v, "unit": "Mrays/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        kernels_per_step = st["kernel_launches"] / max(args.steps, 1)
+        line = {
+            "metric": METRIC, "value": mrays, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": job_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "triangles": sc.n_triangles, "n_azimuth": params["n_azimuth"],
+                       "rays_per_beam": params["rays_per_beam"], "max_bounces": params["max_bounces"],
+                       "n_bins": params["n_bins"], "step": "LBVH rebuild + polar scan",
+                       "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                       "parallelism": f"replicas x{world}"},
+            "scans_per_s": scans_per_s,
+            "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
+                           "kind": "plain scan (rebuild + scan), not served"},
+            "queries_per_scan": st["closest_queries"] / args.steps,
+            "anyhit_per_scan": st["anyhit_queries"] / args.steps,
+            "bvh_build_ms_per_step": prof["build"][0] / max(prof["build"][1], 1),
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "roofline": {"bound": "hbm", "kernel": "k_trace", "achieved": achieved_gbs, "peak": peak,
+                         "unit": "GB/s", "frac": (achieved_gbs / peak) if achieved_gbs else None,
+                         "traffic": traffic, "peak_source": peak_kind,
+                         "algorithmic_bytes_per_query": bytes_per_closest,
+                         "nodes_per_query": nodes_per_q, "tris_per_query": tris_per_q,
+                         "trace_ms_per_launch": trace_ms / max(trace_launches, 1)},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["kernel_launches"]),
+            "kernels_per_step": kernels_per_step, "clocks": clk, "wall_s_timed": wall,
+            "status": "ok" if rc_status is None else str(rc_status),
+        }
+        print(json.dumps(line))
+    rr.rr_scene_destroy(h)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

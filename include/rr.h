@@ -1,0 +1,265 @@
+/*
+ * rr.h -- C ABI of the GB300 radar scan simulator (RadaRays method,
+ * Mock, Magnusson, Hertzberg, arXiv 2310.03505).
+ *
+ * The library simulates a rotating FMCW radar by ray tracing, as Sec. III of
+ * the paper describes: for every azimuth beam it samples rays from the D3
+ * cone (Sec. III-A, Eq. 2), traces them through a triangle scene over several
+ * bounces with a Fresnel split into reflected and refracted rays (Sec. III-A),
+ * collects the energy that returns to the sensor through the beam window of
+ * the material lobe (Eq. 3-5), sums the returns by range into a polar image
+ * (Sec. III-B) and applies the blur / beam-pattern / noise pass (Sec. III-C).
+ *
+ * Conventions shared by every entry point
+ *  - Status: every function returns RR_OK (0) or one of the RR_ERR_* codes
+ *    below; no C++ exception crosses this boundary.  rr_last_error() gives a
+ *    message for the last failure on the calling thread.  On failure nothing
+ *    is written to the output buffers.
+ *  - Pointers: "host or device" arguments may point to host memory (pageable
+ *    or pinned) or to CUDA device memory of the current device; the library
+ *    tells them apart with cudaPointerGetAttributes.  The caller owns every
+ *    buffer it passes; the library copies what it needs.
+ *  - Streams: work is issued on the stream set with rr_set_stream() from the
+ *    calling thread (default: the legacy default stream).  Blocking calls
+ *    synchronise that stream before they return.
+ *  - Layout of the polar image: float32, row major [n_azimuth][n_bins]
+ *    (azimuth major), linear energy; each azimuth emits E0 = 1 (Sec. III-A:
+ *    the ray energies of a beam sum to the emitted energy).
+ *  - Threads: a scene may be used from several threads, but calls on the same
+ *    scene are serialised by the caller (the scene owns its scan workspace).
+ */
+#ifndef RR_H
+#define RR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RR_VERSION 1
+
+/* status codes */
+#define RR_OK 0
+#define RR_ERR_INVALID_ARG 1 /* a size, index, pointer or parameter is out of range     */
+#define RR_ERR_OOM 2         /* a device allocation failed                              */
+#define RR_ERR_CAPACITY 3    /* the ray tree outgrew the scan workspace (see message)   */
+#define RR_ERR_TIMEOUT 4     /* a bounded device wait gave up                           */
+#define RR_ERR_CUDA 5        /* a CUDA runtime call failed                              */
+#define RR_ERR_BUSY 6        /* the request cannot be admitted now                      */
+
+/* sensor flags (rr_sensor_params.flags) */
+#define RR_MULTIPATH 1u  /* air-path returns, Sec. III-A ("multi-path reflection")   */
+#define RR_REFRACTION 2u /* trace the refracted child, Sec. III-A                     */
+#define RR_SPECKLE 4u    /* multiply each return by an Exp(1) draw                    */
+#define RR_NOISE 8u      /* uniform system and ambient noise, Sec. III-C              */
+#define RR_COUNT_TRAVERSAL 16u /* count BVH nodes visited and triangles tested (stats) */
+
+/* material flags (rr_material.flags) */
+#define RR_MAT_PERFECT_CONDUCTOR 1u /* R = 1, T = 0 whatever the angle            */
+
+#define RR_NO_HIT 0xFFFFFFFFu
+
+/* limits checked by the library */
+#define RR_MAX_BOUNCES 16u
+#define RR_MAX_BINS 16384u
+#define RR_MAX_AZIMUTH 65535u
+#define RR_MAX_RAYS_PER_BEAM 65535u
+#define RR_MAX_MATERIALS 65535u
+
+typedef struct rr_scene rr_scene; /* opaque: resident triangles, LBVH, lobe tables, workspace */
+
+/* Per-material radar properties.  eps_r >= 1 is the relative permittivity
+   (refractive index sqrt(eps_r), Snell and Fresnel of Sec. III-A),
+   loss_tangent >= 0 sets the attenuation inside the material.  A, B, C are
+   the lobe parameters of Eq. 5 with S = 1 - A - B; 0 <= A, B, A + B <= 1,
+   C >= 0. */
+typedef struct {
+  float eps_r;
+  float loss_tangent;
+  float A, B, C;
+  uint32_t flags;
+} rr_material;
+
+/* Sensor pose: position p (metres) and orientation q = (w, x, y, z), sensor to
+   world.  q need not be exactly unit; it is normalised. */
+typedef struct {
+  float p[3];
+  float q[4];
+} rr_pose;
+
+/* Sensor model (Sec. III-A/B/C and the setup of Sec. IV).
+   n_azimuth      azimuth beams over 360 deg, beam a points at 2 pi a / n_azimuth
+   rays_per_beam  N_s initial rays per beam, each with energy 1 / N_s
+   max_bounces    maximum number of intersections along a path (>= 1)
+   n_bins         range bins; bin i covers [i, i + 1) * bin_size_m
+   beam_width_rad b of Eq. 2 and Eq. 4; beam_prob P of Eq. 2 (0 < P < 1)
+   elevation_rad  elevation of the beam axes
+   t_min_m        self-intersection offset: hits need t > t_min_m
+   min_energy     rays carrying less energy are not spawned (0: keep all)
+   freq_hz        carrier frequency (wavelength of the loss model)
+   blur_sigma_bins    Gaussian blur along range (measurement noise), 0: off
+   az_pattern_sigma   Gaussian beam pattern across azimuths (in beams), 0: off
+   noise_sys, noise_amb amplitudes of the uniform system / ambient noise
+   flags          RR_MULTIPATH | RR_REFRACTION | RR_SPECKLE | RR_NOISE
+   seed, scan_id  key and counter words of the Philox4x32-10 draws */
+typedef struct {
+  uint32_t n_azimuth, rays_per_beam, max_bounces, n_bins;
+  float beam_width_rad, beam_prob, elevation_rad, bin_size_m, t_min_m, min_energy, freq_hz;
+  float blur_sigma_bins, az_pattern_sigma, noise_sys, noise_amb;
+  uint32_t flags;
+  uint64_t seed;
+  uint32_t scan_id;
+  uint32_t reserved;
+} rr_sensor_params;
+
+/* One traced segment (debug dump): initial ray (az, k), branch path (bit i =
+   0 reflected / 1 refracted at intersection i), bounce index, original
+   triangle id hit (RR_NO_HIT on a miss or beyond the range limit), hit
+   distance (+inf on a miss), the energy entering the segment, and at the hit
+   cos theta0 (incidence, >= 0) and the energies of the traveled-path and
+   air-path returns (0 on a miss). */
+typedef struct {
+  uint32_t az, k, path, bounce;
+  uint32_t tri;
+  float t;
+  float E;
+  uint32_t flags; /* bit 0: an air-path visibility test ran, bit 1: the sensor was visible */
+  float cos_i, ret_t, ret_a, reserved;
+} rr_segment;
+
+typedef struct {
+  uint32_t n_triangles, n_materials, bvh_depth, reserved;
+  uint64_t device_bytes;    /* scene buffers (not the scan workspace) */
+  uint64_t workspace_bytes; /* current scan workspace */
+  float build_ms;           /* device time of the last LBVH build */
+  float reserved_f;
+} rr_scene_info;
+
+typedef struct {
+  uint64_t closest_queries; /* closest-hit queries over all bounces and scans */
+  uint64_t anyhit_queries;  /* air-path visibility queries */
+  uint64_t returns;         /* return records written */
+  uint64_t scans;
+  uint64_t nodes_visited;   /* internal BVH nodes fetched (RR_COUNT_TRAVERSAL scans only) */
+  uint64_t tris_tested;     /* triangles tested (RR_COUNT_TRAVERSAL scans only) */
+  uint64_t kernel_launches; /* kernels this scene launched (host count) */
+} rr_stats;
+
+/* kernel kinds reported by rr_profile_read */
+#define RR_K_RAYGEN 0
+#define RR_K_TRACE 1
+#define RR_K_SHADE 2
+#define RR_K_IMAGE 3
+#define RR_K_BUILD 4
+#define RR_K_COUNT 5
+typedef struct {
+  double ms[RR_K_COUNT];
+  uint64_t launches[RR_K_COUNT];
+} rr_profile;
+
+/* ---------------------------------------------------------------------- */
+/* general                                                                 */
+/* ---------------------------------------------------------------------- */
+int rr_version(void);
+
+/* Message of the last failed call on this thread ("" if none).  The string
+   stays valid until the next call on this thread. */
+const char* rr_last_error(void);
+
+/* Stream for subsequent calls from this thread (a cudaStream_t; NULL = the
+   legacy default stream). */
+int rr_set_stream(void* cuda_stream);
+
+/* ---------------------------------------------------------------------- */
+/* scene: ingest + LBVH (Sec. III-D: the scene mesh with per-triangle      */
+/* materials; the hierarchy is this library's own, 30-bit Morton codes,    */
+/* radix sort, Karras hierarchy, bottom-up refit)                          */
+/* ---------------------------------------------------------------------- */
+/* vertices [n_vertices][3] float (metres), triangles [n_triangles][3] vertex
+   indices, material_ids [n_triangles], materials [n_materials]; all host or
+   device.  Triangles are wound so that (v1 - v0) x (v2 - v0) points out of
+   their material.  Invalid indices, material ids or non-finite vertices give
+   RR_ERR_INVALID_ARG.  The scene keeps its own copies; *out receives the
+   handle.  Blocking. */
+int rr_scene_create(const float* vertices, uint32_t n_vertices, const uint32_t* triangles, uint32_t n_triangles,
+                    const uint16_t* material_ids, const rr_material* materials, uint32_t n_materials,
+                    rr_scene** out);
+
+/* Frees the scene and its workspace.  NULL is accepted. */
+int rr_scene_destroy(rr_scene* scene);
+
+/* New vertex positions [n_vertices][3] (host or device) for the same
+   topology and materials; rebuilds the LBVH (Morton, sort, hierarchy,
+   refit) without allocating.  Stream ordered; non-finite vertices give
+   RR_ERR_INVALID_ARG at the next blocking call or rr_scene_sync. */
+int rr_scene_update_vertices(rr_scene* scene, const float* vertices);
+
+int rr_scene_info_get(const rr_scene* scene, rr_scene_info* info);
+
+/* Copies the LBVH to host arrays (each may be NULL): morton [T] sorted
+   Morton codes, perm [T] triangle id of each sorted leaf, children
+   [(T-1)][2] child references of the internal nodes (leaf j encoded as
+   j | 0x80000000), parents [2T-1] parent of internal nodes 0..T-2 then of
+   leaves (T-1)+j (root: RR_NO_HIT), boxes [(T-1)][2][6] child boxes of
+   every internal node (lo xyz, hi xyz).  Blocking. */
+int rr_scene_export_bvh(const rr_scene* scene, uint32_t* morton, uint32_t* perm, uint32_t* children,
+                        uint32_t* parents, float* boxes);
+
+/* ---------------------------------------------------------------------- */
+/* scans                                                                   */
+/* ---------------------------------------------------------------------- */
+/* One polar image (Sec. III-A..C) for the pose: out_polar [n_azimuth][n_bins]
+   float, host or device.  Blocking; returns the device status of the scan
+   (RR_ERR_CAPACITY if the ray tree outgrew the workspace -- the message
+   gives the size needed). */
+int rr_scan(rr_scene* scene, const rr_pose* pose, const rr_sensor_params* params, float* out_polar);
+
+/* Same, non-blocking: out_polar must be device memory; returns after the
+   kernels are queued.  Device-side errors are reported by rr_scene_sync. */
+int rr_scan_async(rr_scene* scene, const rr_pose* pose, const rr_sensor_params* params, float* out_polar);
+
+/* Waits for the scene's queued work and returns (then clears) the sticky
+   device status of the scans and rebuilds since the previous sync. */
+int rr_scene_sync(rr_scene* scene);
+
+/* n scans of one scene: poses [n], params [n], out [n] pointers to images
+   (host or device, each [params[i].n_azimuth][params[i].n_bins]).
+   Blocking. */
+int rr_scan_batch(rr_scene* scene, uint32_t n, const rr_pose* poses, const rr_sensor_params* params,
+                  float* const* out);
+
+/* Debug scan: like rr_scan, plus
+   ray_mask  [n_azimuth * rays_per_beam] uint8 or NULL; initial rays with a
+             non-zero mask are traced but add nothing to the image
+   segs      [seg_capacity] segment records (NULL: none); *n_segs receives the
+             number of segments traced (may exceed seg_capacity, then
+             RR_ERR_CAPACITY and only seg_capacity records are written)
+   ray_tallies [n_azimuth * rays_per_beam][4] float or NULL: per initial ray
+             the energy returned, absorbed, escaped and terminated
+   All buffers host or device.  Segments are ordered by bounce, then by
+   queue position.  Blocking. */
+int rr_scan_debug(rr_scene* scene, const rr_pose* pose, const rr_sensor_params* params, const uint8_t* ray_mask,
+                  float* out_polar, rr_segment* segs, uint64_t seg_capacity, uint64_t* n_segs, float* ray_tallies);
+
+/* Sec. III-B display mapping: L_E = 10 log10(E_R / E0), E0 = 1, mapped
+   linearly from [-cutoff_db, 0] dB to [0, 255], clamped, rounded to nearest.
+   polar [n] float and out [n] uint8 are device memory.  Stream ordered. */
+int rr_polar_to_db_u8(const float* polar, uint64_t n, float cutoff_db, uint8_t* out);
+
+/* ---------------------------------------------------------------------- */
+/* counters                                                                */
+/* ---------------------------------------------------------------------- */
+/* Cumulative query counters of the scene (blocking); reset != 0 clears them. */
+int rr_scene_stats(rr_scene* scene, rr_stats* stats, int reset);
+
+/* Per-kernel device time with CUDA events on the scene's launches.  While
+   enabled, each launch is bracketed by two events on its stream. */
+int rr_profile_enable(rr_scene* scene, int on);
+int rr_profile_read(rr_scene* scene, rr_profile* out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RR_H */

@@ -48,7 +48,8 @@ class Pose(C.Structure):
 
 
 SEGMENT_DTYPE = np.dtype([("az", "<u4"), ("k", "<u4"), ("path", "<u4"), ("bounce", "<u4"), ("tri", "<u4"),
-                          ("flags", "<u4"), ("t", "<f8"), ("E", "<f8")])
+                          ("flags", "<u4"), ("t", "<f8"), ("E", "<f8"), ("cos_i", "<f8"), ("ret_t", "<f8"),
+                          ("ret_a", "<f8")])
 
 
 def build(force: bool = False) -> str:
@@ -96,7 +97,7 @@ def _load(path):
             L.orc_tri_plane.restype = C.c_int
             L.orc_closest.argtypes = [p, u32, p, u32, p, p, d, u32, p, p, p]
             L.orc_closest.restype = C.c_int
-            L.orc_scan.argtypes = [p, u32, p, u32, p, p, u32, p, p, p, u32, C.c_int, p, p, p, p, p, C.c_uint64, p,
+            L.orc_scan.argtypes = [p, u32, p, u32, p, p, u32, p, p, p, u32, p, p, p, p, p, p, C.c_uint64, p,
                                    p, C.c_int]
             L.orc_scan.restype = C.c_int
             L.orc_post.argtypes = [p, p, p, u32]
@@ -259,16 +260,18 @@ def restore_library(handle):
 
 
 # ---------------------------------------------------------------- full scan
-def scan(vertices, triangles, material_ids, materials, pz: dict, params: dict, az_list=None,
-         exclude_flagged: bool = False, post: bool = True, threads: int = 0, want_segments: bool = True):
+def scan(vertices, triangles, material_ids, materials, pz: dict, params: dict, az_list=None, post: bool = True,
+         threads: int = 0, want_segments: bool = True):
     """Run the brute-force scan on the azimuth columns az_list (all if None).
 
-    Returns a dict with ``image`` [n_cols, n_bins] (post pass applied when
-    ``post``), ``raw`` (before the post pass), ``slack``, ``flags``
-    [n_cols, Ns] (1 = initial ray flagged for parity), ``tallies``
-    [n_cols, Ns, 4] (returned, absorbed, escaped, terminated), ``segments``
-    (structured array, SEGMENT_DTYPE) and ``counts`` (closest-hit queries,
-    shadow queries, returns)."""
+    Returns a dict with ``image`` [n_cols, n_bins] (every return, post pass
+    applied when ``post``), ``image_masked`` (returns of flagged initial rays
+    left out, post pass applied), ``raw`` / ``raw_masked`` (both before the
+    post pass), ``slack`` (energy of unflagged returns next to a bin edge,
+    before the post pass), ``flags`` [n_cols, Ns] (1 = initial ray flagged
+    for parity), ``tallies`` [n_cols, Ns, 4] (returned, absorbed, escaped,
+    terminated), ``segments`` (structured array, SEGMENT_DTYPE) and
+    ``counts`` (closest-hit queries, shadow queries, returns)."""
     L = lib()
     v = np.ascontiguousarray(vertices, np.float32)
     t = np.ascontiguousarray(triangles, np.uint32)
@@ -279,10 +282,11 @@ def scan(vertices, triangles, material_ids, materials, pz: dict, params: dict, a
         cols = None
         n_cols = params["n_azimuth"]
     else:
-        cols = np.ascontiguousarray(np.asarray(az_list, np.uint32))
+        cols = np.ascontiguousarray(np.asarray(list(az_list), np.uint32))
         n_cols = int(cols.size)
     ns, nb, nbnc = params["rays_per_beam"], params["n_bins"], params["max_bounces"]
     image = np.zeros((n_cols, nb))
+    image_m = np.zeros((n_cols, nb))
     slack = np.zeros((n_cols, nb))
     flags = np.zeros((n_cols, ns), np.uint8)
     tallies = np.zeros((n_cols, ns, 4))
@@ -291,17 +295,17 @@ def scan(vertices, triangles, material_ids, materials, pz: dict, params: dict, a
     n_segs = C.c_uint64()
     counts = np.zeros(3, np.uint64)
     rc = L.orc_scan(_ptr(v), v.shape[0], _ptr(t), t.shape[0], _ptr(m), mats, len(materials), C.byref(po),
-                    C.byref(pr), _ptr(cols), n_cols, 1 if exclude_flagged else 0, _ptr(image), _ptr(slack),
-                    _ptr(flags), _ptr(tallies), _ptr(segs), cap, C.byref(n_segs), _ptr(counts), int(threads))
+                    C.byref(pr), _ptr(cols), n_cols, _ptr(image), _ptr(image_m), _ptr(slack), _ptr(flags),
+                    _ptr(tallies), _ptr(segs), cap, C.byref(n_segs), _ptr(counts), int(threads))
     if rc != 0:
         raise RuntimeError(f"orc_scan failed with code {rc}")
-    raw = image.copy()
+    raw, raw_m = image.copy(), image_m.copy()
     if post:
-        rc = L.orc_post(_ptr(image), C.byref(pr), _ptr(cols), n_cols)
-        if rc != 0:
-            raise RuntimeError("orc_post: the azimuth pattern needs every column")
-    return dict(image=image, raw=raw, slack=slack, flags=flags, tallies=tallies,
-                segments=segs[: n_segs.value] if want_segments else None, counts=counts)
+        for img in (image, image_m):
+            if L.orc_post(_ptr(img), C.byref(pr), _ptr(cols), n_cols) != 0:
+                raise RuntimeError("orc_post: the azimuth pattern needs every column")
+    return dict(image=image, image_masked=image_m, raw=raw, raw_masked=raw_m, slack=slack, flags=flags,
+                tallies=tallies, segments=segs[: n_segs.value] if want_segments else None, counts=counts)
 
 
 def post(image, params: dict, az_list=None):

@@ -24,8 +24,9 @@
  * tree contains a decision that FP32 arithmetic could take the other way
  * (a hit or a near miss within 1e-5 barycentric margin of a triangle edge,
  * a hit next to t_min or the range limit, a near tie between two triangles,
- * a total-internal-reflection test next to the critical angle, a grazing hit,
- * a child next to the range cut).  Returns whose range sits next to a bin edge
+ * a total-internal-reflection test next to the critical angle, a refraction
+ * so close to grazing that Snell's law amplifies rounding, a grazing hit, a
+ * child next to the range cut).  Returns whose range sits next to a bin edge
  * add their energy to a per-bin slack.
  */
 #include <math.h>
@@ -50,6 +51,7 @@
 #define FLAG_TABS 1e-6    /* absolute distance next to t_min (metres)          */
 #define FLAG_TIR 1e-6     /* |eta^2 sin^2 - 1| next to the critical angle      */
 #define FLAG_COS 1e-6     /* grazing incidence |cos theta0|                    */
+#define FLAG_COST 0.05    /* refraction next to grazing: cos theta2 below it  */
 
 /* segment flag bits (diagnostics) */
 #define SEG_EDGE 1u
@@ -61,6 +63,7 @@
 #define SEG_RMAX 64u
 #define SEG_VIS 128u
 #define SEG_EMIN 256u
+#define SEG_SNELL 512u
 
 typedef struct {
   double eps_r, loss_tangent, A, B, C;
@@ -82,6 +85,7 @@ typedef struct {
 typedef struct {
   uint32_t az, k, path, bounce, tri, flags;
   double t, E;
+  double cos_i, ret_t, ret_a;
 } orc_segment;
 
 /* ------------------------------------------------------------------------ */
@@ -539,7 +543,7 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
 
     while (sp > 0) {
       oray_t ray = stack[--sp];
-      orc_segment seg = {a, k, ray.path, ray.bounce, ORC_NONE, 0u, INFINITY, ray.E};
+      orc_segment seg = {a, k, ray.path, ray.bounce, ORC_NONE, 0u, INFINITY, ray.E, 0.0, 0.0, 0.0};
       double n_cur = refr_index(s, ray.medium);
       double t_lim = (r_lim - ray.L) / n_cur; /* past it no return can reach the image */
       hit_t h = closest_hit(s, ray.o, ray.d, p->t_min, ray.prev);
@@ -591,6 +595,10 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
       } else {
         tir = orc_fresnel(n1, n2, cos_i, &R, &cos_t, &sin2_t);
         if (fabs(sin2_t - 1.0) < FLAG_TIR) seg.flags |= SEG_TIR;
+        /* Snell's law is ill-conditioned next to the critical angle: the
+           refracted direction moves by d(sin^2)/(2 cos theta2), so float32
+           rounding there bends the refracted child measurably */
+        if (!tir && cos_t < FLAG_COST && (p->flags & ORC_REFRACTION)) seg.flags |= SEG_SNELL;
       }
       double T = (m->pec || tir) ? 0.0 : 1.0 - R;
       int can_refract = !m->pec && !tir;
@@ -656,6 +664,9 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
 
       /* record the returns (Sec. III-A: collected in a list) */
       tal[0] += ret_t + ret_a;
+      seg.cos_i = cos_i;
+      seg.ret_t = ret_t;
+      seg.ret_a = ret_a;
       if (ret_t > 0.0) {
         double e = ret_t;
         if (p->flags & ORC_SPECKLE) e *= speckle_factor(p, a, k, ray.path, ray.bounce, 0);
@@ -723,21 +734,21 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
 
 /* ------------------------------------------------------------------------ */
 /* Sec. III-B: polar image by lookup and summation, starting at 0.          */
-/* A return within a small window of a bin edge also adds its energy to the */
-/* slack of both neighbouring bins.                                          */
+/* img sums every return; img_masked leaves out the returns of flagged      */
+/* initial rays.  A return of an unflagged ray within a small window of a   */
+/* bin edge also adds its energy to the slack of both neighbouring bins.    */
 /* ------------------------------------------------------------------------ */
-static void bin_column(const orc_params* p, const column_t* col, int exclude_flagged, double* img, double* slack) {
+static void bin_column(const orc_params* p, const column_t* col, double* img, double* img_masked, double* slack) {
   for (size_t i = 0; i < col->n_ret; ++i) {
     const oret_t* r = &col->ret[i];
-    if (exclude_flagged && col->flagged[r->k]) continue;
+    const int flagged = col->flagged[r->k];
     double x = r->range / p->bin_size;
     double fb = floor(x);
-    if (fb < 0.0 || fb >= (double)p->n_bins) {
-      /* out of the image; still check the last edge */
-    } else {
+    if (fb >= 0.0 && fb < (double)p->n_bins) {
       img[(size_t)fb] += r->E;
+      if (!flagged && img_masked) img_masked[(size_t)fb] += r->E;
     }
-    if (slack) {
+    if (slack && !flagged) {
       double edge = floor(x + 0.5);
       double tol = 1e-4 > 4e-6 * x ? 1e-4 : 4e-6 * x;
       if (fabs(x - edge) < tol) {
@@ -754,7 +765,7 @@ static void bin_column(const orc_params* p, const column_t* col, int exclude_fla
 /* ------------------------------------------------------------------------ */
 int orc_scan(const float* vertices, uint32_t n_vertices, const uint32_t* triangles, uint32_t n_triangles,
              const uint16_t* material_ids, const orc_material* materials, uint32_t n_materials, const orc_pose* pose,
-             const orc_params* p, const uint32_t* az_list, uint32_t n_cols, int exclude_flagged, double* image,
+             const orc_params* p, const uint32_t* az_list, uint32_t n_cols, double* image, double* image_masked,
              double* slack, uint8_t* ray_flags, double* tallies, orc_segment* segs, uint64_t seg_cap,
              uint64_t* n_segs, uint64_t* counts, int n_threads) {
   if (p->n_azimuth == 0 || p->rays_per_beam == 0 || p->n_bins == 0 || p->max_bounces == 0) return 1;
@@ -778,7 +789,8 @@ int orc_scan(const float* vertices, uint32_t n_vertices, const uint32_t* triangl
   for (int c = 0; c < (int)n_cols; ++c) {
     uint32_t a = az_list ? az_list[c] : (uint32_t)c;
     trace_column(&s, p, pose, a, &cols[c]);
-    bin_column(p, &cols[c], exclude_flagged, image + (size_t)c * p->n_bins,
+    bin_column(p, &cols[c], image + (size_t)c * p->n_bins,
+               image_masked ? image_masked + (size_t)c * p->n_bins : NULL,
                slack ? slack + (size_t)c * p->n_bins : NULL);
   }
   uint64_t ns_out = 0, q = 0, sq = 0, nret = 0;

@@ -1,0 +1,689 @@
+// rr_api.cu -- the extern "C" boundary declared in include/rr.h.
+//
+// Host code here validates arguments, owns device memory and orders the
+// launches; every step of the scan itself runs in the kernels of
+// rr_build.cu, rr_trace.cu and rr_image.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rr_host.h"
+
+using rr::ScanArgs;
+using rr::ScanCounters;
+
+namespace rr_host {
+
+static thread_local std::string t_error;
+static thread_local cudaStream_t t_stream = nullptr;
+
+void set_error(const std::string& msg) { t_error = msg; }
+cudaStream_t current_stream() { return t_stream; }
+
+// scan workspace limit (bytes); beyond it the queues are clamped and an
+// overflow reports RR_ERR_CAPACITY with the size needed
+static size_t g_ws_limit = size_t(24) << 30;
+
+static int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? RR_ERR_OOM : RR_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RR_CHECK_CUDA(expr, what)              \
+  do {                                         \
+    cudaError_t e__ = (expr);                  \
+    if (e__ != cudaSuccess) {                  \
+      cudaGetLastError();                      \
+      return cuda_fail(e__, what);             \
+    }                                          \
+  } while (0)
+
+static bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// profiling
+void prof_begin(rr_scene* s, int kind, cudaStream_t st, cudaEvent_t* stop_out) {
+  *stop_out = nullptr;
+  if (!s->prof) return;
+  ProfEvent ev;
+  ev.kind = kind;
+  for (cudaEvent_t* e : {&ev.start, &ev.stop}) {
+    if (!s->prof_pool.empty()) {
+      *e = s->prof_pool.back();
+      s->prof_pool.pop_back();
+    } else {
+      cudaEventCreate(e);
+    }
+  }
+  cudaEventRecord(ev.start, st);
+  s->prof_pending.push_back(ev);
+  *stop_out = ev.stop;
+}
+
+void prof_end(rr_scene* s, cudaEvent_t stop, cudaStream_t st) {
+  if (stop) cudaEventRecord(stop, st);
+}
+
+static void prof_collect(rr_scene* s) {
+  for (ProfEvent& ev : s->prof_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(ev.stop) == cudaSuccess && cudaEventElapsedTime(&ms, ev.start, ev.stop) == cudaSuccess) {
+      s->prof_ms[ev.kind] += ms;
+      s->prof_launches[ev.kind] += 1;
+    }
+    s->prof_pool.push_back(ev.start);
+    s->prof_pool.push_back(ev.stop);
+  }
+  s->prof_pending.clear();
+}
+
+// ---------------------------------------------------------------------------
+// parameter checks
+static bool finite_f(float x) { return std::isfinite(x); }
+
+static int check_params(const rr_pose* pose, const rr_sensor_params* p) {
+  if (!pose || !p) return fail(RR_ERR_INVALID_ARG, "pose and params must not be NULL");
+  if (p->n_azimuth < 1 || p->n_azimuth > RR_MAX_AZIMUTH) return fail(RR_ERR_INVALID_ARG, "n_azimuth out of range");
+  if (p->rays_per_beam < 1 || p->rays_per_beam > RR_MAX_RAYS_PER_BEAM)
+    return fail(RR_ERR_INVALID_ARG, "rays_per_beam out of range");
+  if (p->max_bounces < 1 || p->max_bounces > RR_MAX_BOUNCES)
+    return fail(RR_ERR_INVALID_ARG, "max_bounces must be in [1, 16]");
+  if (p->n_bins < 1 || p->n_bins > RR_MAX_BINS) return fail(RR_ERR_INVALID_ARG, "n_bins must be in [1, 16384]");
+  if ((uint64_t)p->n_azimuth * p->rays_per_beam > (1ull << 30))
+    return fail(RR_ERR_INVALID_ARG, "n_azimuth * rays_per_beam exceeds 2^30");
+  const float fs[] = {p->beam_width_rad, p->beam_prob, p->elevation_rad, p->bin_size_m, p->t_min_m, p->min_energy,
+                      p->freq_hz, p->blur_sigma_bins, p->az_pattern_sigma, p->noise_sys, p->noise_amb};
+  for (float f : fs)
+    if (!finite_f(f)) return fail(RR_ERR_INVALID_ARG, "sensor parameters must be finite");
+  if (p->beam_width_rad < 0.f || p->beam_width_rad > 3.14159265f)
+    return fail(RR_ERR_INVALID_ARG, "beam_width_rad must be in [0, pi]");
+  if (p->beam_width_rad > 0.f && !(p->beam_prob > 0.f && p->beam_prob < 1.f))
+    return fail(RR_ERR_INVALID_ARG, "beam_prob must be in (0, 1)");
+  if (!(p->bin_size_m > 0.f)) return fail(RR_ERR_INVALID_ARG, "bin_size_m must be > 0");
+  if (p->t_min_m < 0.f || p->min_energy < 0.f) return fail(RR_ERR_INVALID_ARG, "t_min_m and min_energy must be >= 0");
+  if (!(p->freq_hz > 0.f)) return fail(RR_ERR_INVALID_ARG, "freq_hz must be > 0");
+  if (p->blur_sigma_bins < 0.f || p->blur_sigma_bins > 256.f || p->az_pattern_sigma < 0.f ||
+      p->az_pattern_sigma > 256.f)
+    return fail(RR_ERR_INVALID_ARG, "blur / pattern sigma must be in [0, 256]");
+  if (p->noise_sys < 0.f || p->noise_amb < 0.f) return fail(RR_ERR_INVALID_ARG, "noise amplitudes must be >= 0");
+  for (int i = 0; i < 3; ++i)
+    if (!finite_f(pose->p[i])) return fail(RR_ERR_INVALID_ARG, "pose position must be finite");
+  double qn = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    if (!finite_f(pose->q[i])) return fail(RR_ERR_INVALID_ARG, "pose quaternion must be finite");
+    qn += (double)pose->q[i] * pose->q[i];
+  }
+  if (!(qn > 1e-12)) return fail(RR_ERR_INVALID_ARG, "pose quaternion must be non-zero");
+  return RR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+struct WsLayout {
+  uint32_t ray_cap, rec_cap, tiles;
+  size_t off_rays0, off_rays1, off_hits, off_recs, off_status, off_tmp, total;
+  bool clamped;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static WsLayout plan_workspace(const rr_sensor_params* p) {
+  const uint64_t n0 = (uint64_t)p->n_azimuth * p->rays_per_beam;
+  uint64_t q = n0 << (p->max_bounces - 1);
+  uint64_t r = 2ull * n0 * ((1ull << p->max_bounces) - 1ull);
+  const uint64_t cap30 = 1ull << 30;
+  if (q > cap30) q = cap30;
+  if (r > (cap30 << 1)) r = cap30 << 1;
+  if (q < n0) q = n0;
+  auto bytes = [&](uint64_t qq, uint64_t rr_) {
+    const uint64_t tiles = (qq + 255) / 256 + 1;
+    return align256(qq * sizeof(rr::RayRec)) * 2 + align256(qq * sizeof(rr::HitRec)) + align256(rr_ * 8) +
+           align256(tiles * 8) + align256((uint64_t)p->n_azimuth * p->n_bins * 4);
+  };
+  WsLayout L;
+  L.clamped = false;
+  if (bytes(q, r) > g_ws_limit) {
+    const double f = (double)g_ws_limit / (double)bytes(q, r);
+    q = std::max<uint64_t>(n0, (uint64_t)(q * f));
+    r = std::max<uint64_t>(2 * n0, (uint64_t)(r * f));
+    L.clamped = true;
+  }
+  L.ray_cap = (uint32_t)q;
+  L.rec_cap = (uint32_t)std::min<uint64_t>(r, 0xFFFFFFFFull);
+  L.tiles = (uint32_t)((q + 255) / 256 + 1);
+  size_t off = 0;
+  L.off_rays0 = off;
+  off += align256((size_t)q * sizeof(rr::RayRec));
+  L.off_rays1 = off;
+  off += align256((size_t)q * sizeof(rr::RayRec));
+  L.off_hits = off;
+  off += align256((size_t)q * sizeof(rr::HitRec));
+  L.off_recs = off;
+  off += align256((size_t)L.rec_cap * 8);
+  L.off_status = off;
+  off += align256((size_t)L.tiles * 8);
+  L.off_tmp = off;
+  off += align256((size_t)p->n_azimuth * p->n_bins * 4);
+  L.total = off;
+  return L;
+}
+
+static int ensure_workspace(rr_scene* s, size_t bytes, cudaStream_t st) {
+  if (s->ws_bytes >= bytes) return RR_OK;
+  RR_CHECK_CUDA(cudaStreamSynchronize(st), "synchronising before growing the workspace");
+  if (s->ws) cudaFree(s->ws);
+  s->ws = nullptr;
+  s->ws_bytes = 0;
+  RR_CHECK_CUDA(cudaMalloc(&s->ws, bytes), "allocating the scan workspace");
+  s->ws_bytes = bytes;
+  return RR_OK;
+}
+
+static int ensure_image(rr_scene* s, size_t bytes, cudaStream_t st) {
+  if (s->image_bytes >= bytes) return RR_OK;
+  RR_CHECK_CUDA(cudaStreamSynchronize(st), "synchronising before growing the image buffer");
+  if (s->d_image) cudaFree(s->d_image);
+  s->d_image = nullptr;
+  s->image_bytes = 0;
+  RR_CHECK_CUDA(cudaMalloc(&s->d_image, bytes), "allocating the image buffer");
+  s->image_bytes = bytes;
+  return RR_OK;
+}
+
+struct DebugOut {
+  rr_segment* segs = nullptr;
+  uint32_t seg_cap = 0;
+  float* tallies = nullptr;
+  const uint8_t* mask = nullptr;
+};
+
+// queue the kernels of one scan into `image` (device); no synchronisation
+static int scan_enqueue(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* image,
+                        const DebugOut* dbg, cudaStream_t st) {
+  const WsLayout L = plan_workspace(p);
+  int rc = ensure_workspace(s, L.total, st);
+  if (rc != RR_OK) return rc;
+  char* w = (char*)s->ws;
+  ScanArgs a;
+  memset(&a, 0, sizeof a);
+  a.tri = s->d_tri;
+  a.nodes = s->d_nodes;
+  a.mats = s->d_mats;
+  a.lut = s->d_lut;
+  a.n_tris = s->nt;
+  a.rays[0] = (rr::RayRec*)(w + L.off_rays0);
+  a.rays[1] = (rr::RayRec*)(w + L.off_rays1);
+  a.hits = (rr::HitRec*)(w + L.off_hits);
+  a.recs = (uint2*)(w + L.off_recs);
+  a.tile_status = (unsigned long long*)(w + L.off_status);
+  a.ctr = s->d_ctr;
+  a.image = image;
+  a.image_tmp = (float*)(w + L.off_tmp);
+  a.ray_cap = L.ray_cap;
+  a.rec_cap = L.rec_cap;
+  if (dbg) {
+    a.segs = dbg->segs;
+    a.seg_cap = dbg->seg_cap;
+    a.tallies = dbg->tallies;
+    a.mask = dbg->mask;
+  }
+  a.pos = make_float3(pose->p[0], pose->p[1], pose->p[2]);
+  const float qn = 1.0f / std::sqrt(pose->q[0] * pose->q[0] + pose->q[1] * pose->q[1] + pose->q[2] * pose->q[2] +
+                                    pose->q[3] * pose->q[3]);
+  a.quat = make_float4(pose->q[0] * qn, pose->q[1] * qn, pose->q[2] * qn, pose->q[3] * qn);
+  a.n_az = p->n_azimuth;
+  a.ns = p->rays_per_beam;
+  a.max_bounces = p->max_bounces;
+  a.n_bins = p->n_bins;
+  a.beam_width = p->beam_width_rad;
+  a.beam_prob = p->beam_prob;
+  a.elevation = p->elevation_rad;
+  a.bin_size = p->bin_size_m;
+  a.t_min = p->t_min_m;
+  a.min_energy = p->min_energy;
+  a.freq = p->freq_hz;
+  a.blur_sigma = p->blur_sigma_bins;
+  a.az_sigma = p->az_pattern_sigma;
+  a.noise_sys = p->noise_sys;
+  a.noise_amb = p->noise_amb;
+  a.flags = p->flags;
+  a.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFu);
+  a.seed_hi = (uint32_t)(p->seed >> 32);
+  a.scan_id = p->scan_id;
+  a.r_max = (float)p->n_bins * p->bin_size_m;
+
+  s->launches += 2u + 2u * p->max_bounces + (p->az_pattern_sigma > 0.f ? 1u : 0u);
+  cudaEvent_t ev;
+  prof_begin(s, RR_K_RAYGEN, st, &ev);
+  RR_CHECK_CUDA(launch_raygen(a, st), "raygen launch");
+  prof_end(s, ev, st);
+  for (uint32_t b = 0; b < p->max_bounces; ++b) {
+    prof_begin(s, RR_K_TRACE, st, &ev);
+    RR_CHECK_CUDA(launch_trace(a, b, st), "trace launch");
+    prof_end(s, ev, st);
+    prof_begin(s, RR_K_SHADE, st, &ev);
+    RR_CHECK_CUDA(launch_shade(a, b, st), "shade launch");
+    prof_end(s, ev, st);
+  }
+  prof_begin(s, RR_K_IMAGE, st, &ev);
+  RR_CHECK_CUDA(launch_image(a, st), "image launch");
+  prof_end(s, ev, st);
+  return RR_OK;
+}
+
+// read (and clear) the sticky device status; requires the stream to be idle
+static int device_status(rr_scene* s, cudaStream_t st) {
+  RR_CHECK_CUDA(cudaMemcpyAsync(s->h_ctr, s->d_ctr, sizeof(ScanCounters), cudaMemcpyDeviceToHost, st),
+                "reading the scan counters");
+  RR_CHECK_CUDA(cudaStreamSynchronize(st), "scan");
+  const uint32_t err = s->h_ctr->error;
+  if (err) {
+    RR_CHECK_CUDA(cudaMemsetAsync(&s->d_ctr->error, 0, sizeof(uint32_t), st), "clearing the status");
+    RR_CHECK_CUDA(cudaMemsetAsync(&s->d_ctr->need_rays, 0, 2 * sizeof(uint32_t), st), "clearing the status");
+    RR_CHECK_CUDA(cudaStreamSynchronize(st), "clearing the status");
+    char msg[256];
+    if (err & rr::kErrBadVertex)
+      return fail(RR_ERR_INVALID_ARG, "a rebuild saw an invalid vertex index or a non-finite vertex");
+    if (err & rr::kErrStack) return fail(RR_ERR_CAPACITY, "BVH deeper than the traversal stack");
+    if (err & rr::kErrTimeout) return fail(RR_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (err & (rr::kErrCapacityRays | rr::kErrCapacityRecs)) {
+      snprintf(msg, sizeof msg,
+               "ray tree outgrew the workspace: %u queued rays and %u return records were needed; raise the "
+               "workspace limit",
+               s->h_ctr->need_rays, s->h_ctr->need_recs);
+      return fail(RR_ERR_CAPACITY, msg);
+    }
+    if (err & rr::kErrCapacitySegs) return fail(RR_ERR_CAPACITY, "segment buffer too small");
+    return fail(RR_ERR_CUDA, "unknown device status");
+  }
+  return RR_OK;
+}
+
+}  // namespace rr_host
+
+using namespace rr_host;
+
+// one-thread kernel folding the build status into the scan status word
+__global__ void k_fold_build_status(const uint32_t* misc, ScanCounters* ctr) {
+  uint32_t e = 0;
+  if (misc[6]) e |= rr::kErrBadVertex;
+  if (misc[7] > (uint32_t)rr::kStack) e |= rr::kErrStack;
+  if (e) atomicOr(&ctr->error, e);
+}
+
+extern "C" {
+
+int rr_version(void) { return RR_VERSION; }
+
+const char* rr_last_error(void) { return t_error.c_str(); }
+
+int rr_set_stream(void* cuda_stream) {
+  t_stream = (cudaStream_t)cuda_stream;
+  return RR_OK;
+}
+
+int rr_scene_destroy(rr_scene* s) {
+  if (!s) return RR_OK;
+  cudaDeviceSynchronize();
+  void* ptrs[] = {s->d_vtx, s->d_idx, s->d_mat_id, s->d_raw_mats, s->d_mats, s->d_lut, s->d_lut_cells,
+                  s->d_tri, s->d_nodes, s->d_centroid, s->d_keys[0], s->d_keys[1], s->d_vals[0], s->d_vals[1],
+                  s->d_hist, s->d_parent, s->d_child, s->d_nbox, s->d_visit, s->d_misc, s->ws, s->d_ctr,
+                  s->d_image};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (s->h_ctr) cudaFreeHost(s->h_ctr);
+  for (auto& ev : s->prof_pending) {
+    cudaEventDestroy(ev.start);
+    cudaEventDestroy(ev.stop);
+  }
+  for (auto e : s->prof_pool) cudaEventDestroy(e);
+  delete s;
+  return RR_OK;
+}
+
+int rr_scene_create(const float* vertices, uint32_t n_vertices, const uint32_t* triangles, uint32_t n_triangles,
+                    const uint16_t* material_ids, const rr_material* materials, uint32_t n_materials,
+                    rr_scene** out) {
+  if (!out) return fail(RR_ERR_INVALID_ARG, "out must not be NULL");
+  *out = nullptr;
+  if (n_triangles > 0 && (!vertices || !triangles || !material_ids))
+    return fail(RR_ERR_INVALID_ARG, "vertices, triangles and material_ids must not be NULL");
+  if (n_materials == 0 || !materials) return fail(RR_ERR_INVALID_ARG, "at least one material is required");
+  if (n_materials > RR_MAX_MATERIALS) return fail(RR_ERR_INVALID_ARG, "too many materials");
+  if (n_triangles > (1u << 30)) return fail(RR_ERR_INVALID_ARG, "more than 2^30 triangles");
+  std::vector<rr_material> mats(n_materials);
+  {
+    cudaError_t e = cudaMemcpy(mats.data(), materials, n_materials * sizeof(rr_material), cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, "reading the materials");
+    }
+  }
+  for (uint32_t m = 0; m < n_materials; ++m) {
+    const rr_material& x = mats[m];
+    if (!(std::isfinite(x.eps_r) && std::isfinite(x.loss_tangent) && std::isfinite(x.A) && std::isfinite(x.B) &&
+          std::isfinite(x.C)))
+      return fail(RR_ERR_INVALID_ARG, "material " + std::to_string(m) + ": non-finite value");
+    if (x.eps_r < 1.f || x.loss_tangent < 0.f || x.A < 0.f || x.B < 0.f || x.A > 1.f || x.B > 1.f ||
+        x.A + x.B > 1.f + 1e-6f || x.C < 0.f)
+      return fail(RR_ERR_INVALID_ARG, "material " + std::to_string(m) +
+                                          ": needs eps_r >= 1, tan_d >= 0, 0 <= A, B, A + B <= 1, C >= 0");
+  }
+  cudaStream_t st = t_stream;
+  rr_scene* s = new rr_scene();
+  cudaGetDevice(&s->device);
+  s->nv = n_vertices;
+  s->nt = n_triangles;
+  s->nm = n_materials;
+  auto bail = [&](int code) {
+    rr_scene_destroy(s);
+    return code;
+  };
+  {
+    cudaError_t e = build_alloc(s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return bail(cuda_fail(e, "allocating the scene"));
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (cudaMalloc((void**)&s->d_ctr, sizeof(ScanCounters)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->h_ctr, sizeof(ScanCounters)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(RR_ERR_OOM, "allocating the scan counters"));
+  }
+  e = cudaMemsetAsync(s->d_ctr, 0, sizeof(ScanCounters), st);
+  if (e == cudaSuccess && n_vertices)
+    e = cudaMemcpyAsync(s->d_vtx, vertices, (size_t)n_vertices * 3 * sizeof(float), cudaMemcpyDefault, st);
+  if (e == cudaSuccess && n_triangles)
+    e = cudaMemcpyAsync(s->d_idx, triangles, (size_t)n_triangles * 3 * sizeof(uint32_t), cudaMemcpyDefault, st);
+  if (e == cudaSuccess && n_triangles)
+    e = cudaMemcpyAsync(s->d_mat_id, material_ids, (size_t)n_triangles * sizeof(uint16_t), cudaMemcpyDefault, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_raw_mats, mats.data(), n_materials * sizeof(rr_material), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = build_materials(s, st);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) e = build_lbvh(s, st);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return bail(cuda_fail(e, "building the scene"));
+  }
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->build_ms = ms;
+  if (n_triangles) {
+    uint32_t misc[8];
+    e = cudaMemcpy(misc, s->d_misc, sizeof misc, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "reading the build status"));
+    if (misc[6] & 1u) return bail(fail(RR_ERR_INVALID_ARG, "a triangle references a vertex index >= n_vertices"));
+    if (misc[6] & 2u) return bail(fail(RR_ERR_INVALID_ARG, "a material id is >= n_materials"));
+    if (misc[6] & rr::kErrBadVertex) return bail(fail(RR_ERR_INVALID_ARG, "non-finite vertex coordinates"));
+    s->depth = misc[7];
+    if (s->depth > (uint32_t)rr::kStack)
+      return bail(fail(RR_ERR_CAPACITY, "BVH depth " + std::to_string(s->depth) + " exceeds the traversal stack"));
+  }
+  *out = s;
+  return RR_OK;
+}
+
+int rr_scene_update_vertices(rr_scene* s, const float* vertices) {
+  if (!s || !vertices) return fail(RR_ERR_INVALID_ARG, "scene and vertices must not be NULL");
+  cudaStream_t st = t_stream;
+  cudaEvent_t ev;
+  if (s->nv)
+    RR_CHECK_CUDA(cudaMemcpyAsync(s->d_vtx, vertices, (size_t)s->nv * 3 * sizeof(float), cudaMemcpyDefault, st),
+                  "copying the vertices");
+  prof_begin(s, RR_K_BUILD, st, &ev);
+  RR_CHECK_CUDA(build_lbvh(s, st), "rebuilding the BVH");
+  prof_end(s, ev, st);
+  if (s->nt) {
+    s->launches += 1;
+    k_fold_build_status<<<1, 1, 0, st>>>(s->d_misc, s->d_ctr);
+    RR_CHECK_CUDA(cudaGetLastError(), "status fold");
+  }
+  return RR_OK;
+}
+
+int rr_scene_info_get(const rr_scene* s, rr_scene_info* info) {
+  if (!s || !info) return fail(RR_ERR_INVALID_ARG, "scene and info must not be NULL");
+  memset(info, 0, sizeof *info);
+  info->n_triangles = s->nt;
+  info->n_materials = s->nm;
+  info->bvh_depth = s->depth;
+  info->device_bytes = s->scene_bytes;
+  info->workspace_bytes = s->ws_bytes;
+  info->build_ms = s->build_ms;
+  return RR_OK;
+}
+
+int rr_scene_export_bvh(const rr_scene* s, uint32_t* morton, uint32_t* perm, uint32_t* children, uint32_t* parents,
+                        float* boxes) {
+  if (!s) return fail(RR_ERR_INVALID_ARG, "scene must not be NULL");
+  RR_CHECK_CUDA(cudaStreamSynchronize(t_stream), "synchronising");
+  const size_t T = s->nt;
+  if (T == 0) return RR_OK;
+  if (morton) RR_CHECK_CUDA(cudaMemcpy(morton, s->d_keys[0], T * 4, cudaMemcpyDeviceToHost), "export");
+  if (perm) RR_CHECK_CUDA(cudaMemcpy(perm, s->d_vals[0], T * 4, cudaMemcpyDeviceToHost), "export");
+  if (T > 1 && children) RR_CHECK_CUDA(cudaMemcpy(children, s->d_child, (T - 1) * 8, cudaMemcpyDeviceToHost), "export");
+  if (parents) RR_CHECK_CUDA(cudaMemcpy(parents, s->d_parent, (2 * T - 1) * 4, cudaMemcpyDeviceToHost), "export");
+  if (T > 1 && boxes) {
+    std::vector<float4> nodes((T - 1) * 4);
+    RR_CHECK_CUDA(cudaMemcpy(nodes.data(), s->d_nodes, nodes.size() * sizeof(float4), cudaMemcpyDeviceToHost),
+                  "export");
+    for (size_t i = 0; i + 1 < T; ++i) {
+      const float4 n0 = nodes[4 * i], n1 = nodes[4 * i + 1], n2 = nodes[4 * i + 2];
+      float* b = boxes + 12 * i;
+      const float v[12] = {n0.x, n0.z, n2.x, n0.y, n0.w, n2.y, n1.x, n1.z, n2.z, n1.y, n1.w, n2.w};
+      memcpy(b, v, sizeof v);
+    }
+  }
+  return RR_OK;
+}
+
+int rr_scan_async(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* out_polar) {
+  if (!s || !out_polar) return fail(RR_ERR_INVALID_ARG, "scene and out_polar must not be NULL");
+  int rc = check_params(pose, p);
+  if (rc != RR_OK) return rc;
+  if (!is_device_ptr(out_polar)) return fail(RR_ERR_INVALID_ARG, "rr_scan_async needs a device output");
+  return scan_enqueue(s, pose, p, out_polar, nullptr, t_stream);
+}
+
+int rr_scene_sync(rr_scene* s) {
+  if (!s) return fail(RR_ERR_INVALID_ARG, "scene must not be NULL");
+  return device_status(s, t_stream);
+}
+
+int rr_scan(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* out_polar) {
+  if (!s || !out_polar) return fail(RR_ERR_INVALID_ARG, "scene and out_polar must not be NULL");
+  int rc = check_params(pose, p);
+  if (rc != RR_OK) return rc;
+  cudaStream_t st = t_stream;
+  const size_t img_bytes = (size_t)p->n_azimuth * p->n_bins * sizeof(float);
+  const bool dev = is_device_ptr(out_polar);
+  float* target = out_polar;
+  if (!dev) {
+    rc = ensure_image(s, img_bytes, st);
+    if (rc != RR_OK) return rc;
+    target = s->d_image;
+  }
+  rc = scan_enqueue(s, pose, p, target, nullptr, st);
+  if (rc != RR_OK) return rc;
+  if (!dev)
+    RR_CHECK_CUDA(cudaMemcpyAsync(out_polar, target, img_bytes, cudaMemcpyDeviceToHost, st), "copying the image");
+  return device_status(s, st);
+}
+
+int rr_scan_batch(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor_params* params, float* const* out) {
+  if (!s || (n && (!poses || !params || !out))) return fail(RR_ERR_INVALID_ARG, "NULL argument");
+  for (uint32_t i = 0; i < n; ++i) {
+    int rc = check_params(&poses[i], &params[i]);
+    if (rc != RR_OK) return rc;
+    if (!out[i]) return fail(RR_ERR_INVALID_ARG, "NULL output");
+  }
+  cudaStream_t st = t_stream;
+  for (uint32_t i = 0; i < n; ++i) {
+    const size_t img_bytes = (size_t)params[i].n_azimuth * params[i].n_bins * sizeof(float);
+    const bool dev = is_device_ptr(out[i]);
+    float* target = out[i];
+    int rc;
+    if (!dev) {
+      rc = ensure_image(s, img_bytes, st);
+      if (rc != RR_OK) return rc;
+      target = s->d_image;
+    }
+    rc = scan_enqueue(s, &poses[i], &params[i], target, nullptr, st);
+    if (rc != RR_OK) return rc;
+    if (!dev) {
+      RR_CHECK_CUDA(cudaMemcpyAsync(out[i], target, img_bytes, cudaMemcpyDeviceToHost, st), "copying the image");
+      RR_CHECK_CUDA(cudaStreamSynchronize(st), "batch");
+    }
+  }
+  return device_status(s, st);
+}
+
+int rr_scan_debug(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, const uint8_t* ray_mask,
+                  float* out_polar, rr_segment* segs, uint64_t seg_capacity, uint64_t* n_segs, float* ray_tallies) {
+  if (!s || !out_polar) return fail(RR_ERR_INVALID_ARG, "scene and out_polar must not be NULL");
+  int rc = check_params(pose, p);
+  if (rc != RR_OK) return rc;
+  cudaStream_t st = t_stream;
+  const size_t n0 = (size_t)p->n_azimuth * p->rays_per_beam;
+  const size_t img_bytes = (size_t)p->n_azimuth * p->n_bins * sizeof(float);
+  if (seg_capacity > 0xFFFFFFFFull) seg_capacity = 0xFFFFFFFFull;
+  // temporaries of the debug path (allocated per call)
+  float* d_img = nullptr;
+  rr_segment* d_segs = nullptr;
+  float* d_tal = nullptr;
+  uint8_t* d_mask = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    cudaFree(d_img);
+    cudaFree(d_segs);
+    cudaFree(d_tal);
+    cudaFree(d_mask);
+  };
+  auto check = [&](cudaError_t e, const char* what) -> int {
+    if (e == cudaSuccess) return RR_OK;
+    cudaGetLastError();
+    cleanup();
+    return cuda_fail(e, what);
+  };
+  if ((rc = check(cudaMalloc(&d_img, img_bytes), "debug image")) != RR_OK) return rc;
+  if (segs && seg_capacity)
+    if ((rc = check(cudaMalloc(&d_segs, seg_capacity * sizeof(rr_segment)), "debug segments")) != RR_OK) return rc;
+  if (ray_tallies) {
+    if ((rc = check(cudaMalloc(&d_tal, n0 * 4 * sizeof(float)), "debug tallies")) != RR_OK) return rc;
+    if ((rc = check(cudaMemsetAsync(d_tal, 0, n0 * 4 * sizeof(float), st), "debug tallies")) != RR_OK) return rc;
+  }
+  if (ray_mask) {
+    if ((rc = check(cudaMalloc(&d_mask, n0), "debug mask")) != RR_OK) return rc;
+    if ((rc = check(cudaMemcpyAsync(d_mask, ray_mask, n0, cudaMemcpyDefault, st), "debug mask")) != RR_OK) return rc;
+  }
+  DebugOut dbg;
+  dbg.segs = d_segs;
+  dbg.seg_cap = d_segs ? (uint32_t)seg_capacity : 0u;
+  dbg.tallies = d_tal;
+  dbg.mask = d_mask;
+  rc = scan_enqueue(s, pose, p, d_img, &dbg, st);
+  if (rc != RR_OK) {
+    cleanup();
+    return rc;
+  }
+  rc = device_status(s, st);
+  const uint64_t total = s->h_ctr->seg_start[p->max_bounces];
+  if (n_segs) *n_segs = total;
+  if (rc == RR_OK || rc == RR_ERR_CAPACITY) {
+    int rc2;
+    if ((rc2 = check(cudaMemcpyAsync(out_polar, d_img, img_bytes, cudaMemcpyDefault, st), "copy")) != RR_OK)
+      return rc2;
+    if (d_segs) {
+      const uint64_t nw = total < seg_capacity ? total : seg_capacity;
+      if ((rc2 = check(cudaMemcpyAsync(segs, d_segs, nw * sizeof(rr_segment), cudaMemcpyDefault, st), "copy")) !=
+          RR_OK)
+        return rc2;
+    }
+    if (d_tal)
+      if ((rc2 = check(cudaMemcpyAsync(ray_tallies, d_tal, n0 * 4 * sizeof(float), cudaMemcpyDefault, st),
+                       "copy")) != RR_OK)
+        return rc2;
+  }
+  cleanup();
+  if (rc == RR_OK && segs && total > seg_capacity) return fail(RR_ERR_CAPACITY, "segment buffer too small");
+  return rc;
+}
+
+int rr_polar_to_db_u8(const float* polar, uint64_t n, float cutoff_db, uint8_t* out) {
+  if (!polar || !out) return fail(RR_ERR_INVALID_ARG, "NULL buffer");
+  if (!(cutoff_db > 0.f) || !std::isfinite(cutoff_db)) return fail(RR_ERR_INVALID_ARG, "cutoff_db must be > 0");
+  if (!is_device_ptr(polar) || !is_device_ptr(out)) return fail(RR_ERR_INVALID_ARG, "buffers must be device memory");
+  RR_CHECK_CUDA(launch_db_u8(polar, n, cutoff_db, out, t_stream), "dB map launch");
+  return RR_OK;
+}
+
+int rr_scene_stats(rr_scene* s, rr_stats* out, int reset) {
+  if (!s || !out) return fail(RR_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = t_stream;
+  RR_CHECK_CUDA(cudaMemcpyAsync(s->h_ctr, s->d_ctr, sizeof(ScanCounters), cudaMemcpyDeviceToHost, st), "stats");
+  RR_CHECK_CUDA(cudaStreamSynchronize(st), "stats");
+  out->closest_queries = s->h_ctr->stat_closest;
+  out->anyhit_queries = s->h_ctr->stat_anyhit;
+  out->returns = s->h_ctr->stat_returns;
+  out->scans = s->h_ctr->stat_scans;
+  out->nodes_visited = s->h_ctr->stat_nodes;
+  out->tris_tested = s->h_ctr->stat_tris;
+  out->kernel_launches = s->launches;
+  if (reset) {
+    s->launches = 0;
+    RR_CHECK_CUDA(cudaMemsetAsync(&s->d_ctr->stat_closest, 0, 6 * sizeof(unsigned long long), st), "stats reset");
+    RR_CHECK_CUDA(cudaStreamSynchronize(st), "stats reset");
+  }
+  return RR_OK;
+}
+
+int rr_profile_enable(rr_scene* s, int on) {
+  if (!s) return fail(RR_ERR_INVALID_ARG, "NULL scene");
+  s->prof = on != 0;
+  return RR_OK;
+}
+
+int rr_profile_read(rr_scene* s, rr_profile* out, int reset) {
+  if (!s || !out) return fail(RR_ERR_INVALID_ARG, "NULL argument");
+  prof_collect(s);
+  for (int k = 0; k < RR_K_COUNT; ++k) {
+    out->ms[k] = s->prof_ms[k];
+    out->launches[k] = s->prof_launches[k];
+    if (reset) {
+      s->prof_ms[k] = 0.0;
+      s->prof_launches[k] = 0;
+    }
+  }
+  return RR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,201 @@
+// rr_internal.cuh -- device layouts and helpers shared by the CUDA
+// translation units of the radar scan library (never by the oracle).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rr.h"
+
+namespace rr {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kAir = 0xFFFFu;
+constexpr uint32_t kLeafBit = 0x80000000u;
+constexpr int kStack = 64;            // traversal stack entries; the build checks depth <= kStack
+constexpr int kLutCells = 2048;       // lobe table cells over [0, pi/2]
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kHalfPi = 1.57079632679489661923f;
+constexpr float kC0 = 299792458.0f;   // speed of light (m/s)
+constexpr uint32_t kSpinLimit = 1u << 24;  // bounded device waits
+
+// status bits of the sticky device error word
+constexpr uint32_t kErrCapacityRays = 1u;
+constexpr uint32_t kErrCapacityRecs = 2u;
+constexpr uint32_t kErrTimeout = 4u;
+constexpr uint32_t kErrCapacitySegs = 8u;
+constexpr uint32_t kErrBadVertex = 16u;
+constexpr uint32_t kErrStack = 32u;
+
+// ---------------------------------------------------------------------------
+// device material record (derived at scene creation)
+struct __align__(16) MatDev {
+  float n;          // refractive index sqrt(eps_r)
+  float tan_d;      // loss tangent
+  float A, B;       // Eq. 5
+  float S, C;       // S = 1 - A - B
+  float invZ;       // 1 / (A pi + 2 B + 2 S G(pi/2)), G from the lobe table
+  uint32_t pec;     // perfect conductor
+};
+
+// ray record, 48 bytes
+struct __align__(16) RayRec {
+  float4 o_L;   // origin, one-way optical path so far
+  float4 d_E;   // unit direction, energy
+  uint4 meta;   // x: prev leaf (sorted index) or kNone, y: az << 16 | k,
+                // z: path (bit 31: masked), w: medium material or kAir
+};
+
+// hit record, 16 bytes
+struct __align__(16) HitRec {
+  float t;
+  uint32_t leaf;   // sorted leaf index or kNone
+  uint32_t flags;  // bit 0: visibility test ran, bit 1: visible
+  float wa_g;      // W(omega_a) * g_rx of a visible air-path candidate, else 0
+};
+
+// device counters of one scene
+struct ScanCounters {
+  uint32_t count[RR_MAX_BOUNCES + 1];      // queue length per bounce
+  uint32_t rec_start[RR_MAX_BOUNCES + 1];  // first record of each bounce
+  uint32_t seg_start[RR_MAX_BOUNCES + 1];  // first debug segment of each bounce
+  uint32_t trace_ticket[RR_MAX_BOUNCES];
+  uint32_t shade_ticket[RR_MAX_BOUNCES];
+  uint32_t need_rays, need_recs;           // largest request seen (overflow report)
+  uint32_t error;                          // sticky kErr* bits
+  uint32_t pad;
+  unsigned long long stat_closest, stat_anyhit, stat_returns, stat_scans;
+  unsigned long long stat_nodes, stat_tris;
+};
+
+// per-scan constants (passed by value)
+struct ScanArgs {
+  // scene
+  const float4* tri;         // [T][3] sorted: v0 (w: orig id bits), v1 (w: material bits), v2
+  const float4* nodes;       // [T-1][4] Aila-Laine layout
+  const MatDev* mats;
+  const float4* lut;         // [M][kLutCells + 1]: (G(x_k), Gc(x_k), cos^C(x_k), 0)
+  uint32_t n_tris;
+  // workspace
+  RayRec* rays[2];
+  HitRec* hits;
+  uint2* recs;               // (az << 16 | bin, energy bits)
+  unsigned long long* tile_status;
+  ScanCounters* ctr;
+  float* image;              // [n_az][n_bins] output (device)
+  float* image_tmp;          // [n_az][n_bins] before the azimuth pattern (or null)
+  uint32_t ray_cap, rec_cap;
+  // debug (may be null)
+  rr_segment* segs;
+  uint32_t seg_cap;
+  float* tallies;
+  const uint8_t* mask;
+  // sensor
+  float3 pos;
+  float4 quat;               // normalised (w, x, y, z)
+  uint32_t n_az, ns, max_bounces, n_bins;
+  float beam_width, beam_prob, elevation, bin_size, t_min, min_energy, freq;
+  float blur_sigma, az_sigma, noise_sys, noise_amb;
+  uint32_t flags;
+  uint32_t seed_lo, seed_hi, scan_id;
+  float r_max;               // n_bins * bin_size
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC 2011): counter (scan, a, b, c), key = seed
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// uniform in (0,1) from the top 23 bits, (2 (x >> 9) + 1) / 2^24: exact in float
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(2u * (x >> 9) + 1u) * 5.9604644775390625e-8f; }
+
+__device__ __forceinline__ uint4 draw(const ScanArgs& a, uint32_t w1, uint32_t w2, uint32_t w3) {
+  return philox(make_uint4(a.scan_id, w1, w2, w3), make_uint2(a.seed_lo, a.seed_hi));
+}
+
+// ---------------------------------------------------------------------------
+// small vector helpers
+__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return make_float3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float length(float3 a) { return sqrtf(dot(a, a)); }
+__device__ __forceinline__ float3 normalize(float3 a) { return rsqrtf(dot(a, a)) * a; }
+// angle between two vectors, well conditioned at 0 and pi
+__device__ __forceinline__ float angle_between(float3 a, float3 b) { return atan2f(length(cross(a, b)), dot(a, b)); }
+
+// rotate v by the unit quaternion q = (w, x, y, z)
+__device__ __forceinline__ float3 qrot(float4 q, float3 v) {
+  const float w = q.x, x = q.y, y = q.z, z = q.w;
+  return make_float3((1.f - 2.f * (y * y + z * z)) * v.x + 2.f * (x * y - w * z) * v.y + 2.f * (x * z + w * y) * v.z,
+                     2.f * (x * y + w * z) * v.x + (1.f - 2.f * (x * x + z * z)) * v.y + 2.f * (y * z - w * x) * v.z,
+                     2.f * (x * z - w * y) * v.x + 2.f * (y * z + w * x) * v.y + (1.f - 2.f * (x * x + y * y)) * v.z);
+}
+
+// cos^C(x) for x in [0, pi/2] as exp(C log1p(-2 sin^2(x/2))): keeps the
+// relative error near 1 ulp for the sharp lobes (C up to a few thousand)
+__device__ __forceinline__ float cospow(float x, float C) {
+  if (C == 0.0f) return 1.0f;
+  const float s = sinf(0.5f * x);
+  // at x = pi/2 (rounded up in float) -2 s^2 can land just below -1: clamp so
+  // that cos^C(pi/2) = exp(-inf) = 0 instead of NaN
+  return expf(C * log1pf(fmaxf(-2.0f * s * s, -1.0f)));
+}
+
+// Lobe table of one material: node k at x_k = k (pi/2) / kLutCells holds
+// (G(x_k), Gc(x_k), cos^C(x_k), 0) with G(x) = integral of cos^C over [0, x]
+// and Gc(x) = integral over [x, pi/2].  Values between nodes come from cubic
+// Hermite interpolation (G' = cos^C, Gc' = -cos^C).
+__device__ __forceinline__ float lut_interp(const float4* __restrict__ lut, float x, bool comp) {
+  const float h = kHalfPi / kLutCells;
+  const float u = x * (kLutCells / kHalfPi);
+  if (!(u > 0.0f)) return comp ? __ldg(&lut[0]).y : 0.0f;        // also NaN
+  if (u >= (float)kLutCells) return comp ? 0.0f : __ldg(&lut[kLutCells]).x;
+  const int k = (int)u;
+  const float s = u - (float)k;
+  const float4 p0 = __ldg(&lut[k]), p1 = __ldg(&lut[k + 1]);
+  const float s2 = s * s, s3 = s2 * s;
+  const float h00 = 2.f * s3 - 3.f * s2 + 1.f, h10 = s3 - 2.f * s2 + s, h01 = -2.f * s3 + 3.f * s2,
+              h11 = s3 - s2;
+  if (comp) return h00 * p0.y - h10 * h * p0.z + h01 * p1.y - h11 * h * p1.z;
+  return h00 * p0.x + h10 * h * p0.z + h01 * p1.x + h11 * h * p1.z;
+}
+
+// integral of cos^C over [lo, hi], -pi/2 <= lo < hi <= pi/2; tails use the
+// complementary table so that no large nearly-equal values are subtracted
+__device__ __forceinline__ float lut_integral(const float4* __restrict__ lut, float lo, float hi) {
+  if (lo >= 0.0f) {
+    const float half = 0.5f * __ldg(&lut[kLutCells]).x;
+    const float g_lo = lut_interp(lut, lo, false);
+    if (g_lo > half) return lut_interp(lut, lo, true) - lut_interp(lut, hi, true);
+    return lut_interp(lut, hi, false) - g_lo;
+  }
+  if (hi <= 0.0f) return lut_integral(lut, -hi, -lo);
+  return lut_interp(lut, hi, false) + lut_interp(lut, -lo, false);
+}
+
+// Eq. 4 with the normalised Eq. 5 lobe: fraction of the lobe inside the
+// window [w - b/2, w + b/2] clipped to [-pi/2, pi/2]
+__device__ __forceinline__ float brdf_window(const MatDev& m, const float4* __restrict__ lut, float w, float b) {
+  const float lo = fmaxf(w - 0.5f * b, -kHalfPi), hi = fminf(w + 0.5f * b, kHalfPi);
+  if (!(hi > lo)) return 0.0f;
+  float v = m.A * (hi - lo) + m.B * 2.0f * cosf(0.5f * (hi + lo)) * sinf(0.5f * (hi - lo));
+  if (m.S != 0.0f) v += m.S * lut_integral(lut, lo, hi);
+  return fmaxf(v * m.invZ, 0.0f);
+}
+
+}  // namespace rr

@@ -1,0 +1,679 @@
+// rr_trace.cu -- wavefront ray tracing of one polar scan.
+//
+// Per scan:  raygen -> { trace -> shade } x max_bounces -> image
+//   raygen  Sec. III-A, Eq. 2: N_s rays per azimuth beam from the D3 cone.
+//   trace   closest hit through the LBVH (watertight ray/triangle test of
+//           Woop, Benthin, Wald, JCGT 2013) and, for multipath, the
+//           visibility test of the air-path return toward the sensor.
+//   shade   Sec. III-A: Fresnel split E0 = E1 + E2, Snell refraction,
+//           attenuation in lossy media, traveled-path and air-path returns
+//           through the beam window of the material lobe (Eq. 3-5), and the
+//           reflected / refracted children.  Children and return records are
+//           compacted stably (single pass, decoupled look-back over tiles of
+//           256 rays), so every queue and every bounce's record list stays
+//           in (azimuth, ray) order.
+//
+// All kernels are persistent: the grid is a multiple of the SM count and
+// reads the queue length from device memory, so a whole scan is a fixed
+// sequence of launches with no host round trip between bounces.
+#include <cuda_runtime.h>
+
+#include "rr_host.h"
+
+namespace rr {
+
+constexpr int kTraceBlock = 128;
+constexpr int kShadeBlock = 256;
+constexpr float kBoxInflate = 1.00000036f;  // 1 + 2 gamma_3 (robust slab test, Ize 2013)
+
+// ---------------------------------------------------------------------------
+// beam axis angle 2 pi a / n with an exact quadrant reduction; returns (cos, sin)
+__device__ __forceinline__ float2 beam_angle(uint32_t a, uint32_t n) {
+  const uint32_t m = 4u * a;
+  const uint32_t q = (m + n / 2u) / n;              // nearest quarter turn
+  const int rem = (int)m - (int)(q * n);            // in [-n/2, n/2]
+  float s, c;
+  sincospif(0.5f * (float)rem / (float)n, &s, &c);
+  switch (q & 3u) {
+    case 0: return make_float2(c, s);
+    case 1: return make_float2(-s, c);
+    case 2: return make_float2(-c, -s);
+    default: return make_float2(s, -c);
+  }
+}
+
+__device__ __forceinline__ float3 beam_axis(const ScanArgs& a, uint32_t az) {
+  const float2 cs = beam_angle(az, a.n_az);
+  float se, ce;
+  sincosf(a.elevation, &se, &ce);
+  return qrot(a.quat, make_float3(ce * cs.x, ce * cs.y, se));
+}
+
+__device__ __forceinline__ float d3_sigma(const ScanArgs& a) {
+  return a.beam_width > 0.0f ? 0.5f * a.beam_width / (1.41421356237309515f * erfinvf(a.beam_prob)) : 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// raygen: ray (az, k) of the D3 cone, energy 1 / N_s
+__global__ void k_raygen(ScanArgs a) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = a.n_az * a.ns;
+  if (i == 0) {
+    ScanCounters* c = a.ctr;
+    for (int b = 0; b <= (int)RR_MAX_BOUNCES; ++b) {
+      c->count[b] = 0;
+      c->rec_start[b] = 0;
+      c->seg_start[b] = 0;
+    }
+    for (int b = 0; b < (int)RR_MAX_BOUNCES; ++b) {
+      c->trace_ticket[b] = 0;
+      c->shade_ticket[b] = 0;
+    }
+    c->count[0] = n;
+    c->stat_scans += 1ull;
+  }
+  if (i >= n) return;
+  const uint32_t az = i / a.ns, k = i - az * a.ns;
+  const uint4 x = draw(a, az, k, 0u);
+  const float u0 = u01(x.x), u1 = u01(x.y), u2 = u01(x.z);
+  const float gauss = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
+  const float r = d3_sigma(a) * gauss;
+  float sw, cw;
+  sincospif(2.0f * u2 - 1.0f, &sw, &cw);      // omega = pi (2 u2 - 1)
+  const float daz = r * cw, dinc = r * sw;
+  const float2 ph = beam_angle(az, a.n_az);
+  float sd, cd;
+  sincosf(daz, &sd, &cd);
+  const float ca = ph.x * cd - ph.y * sd, sa = ph.y * cd + ph.x * sd;   // cos, sin of phi + daz
+  float si, ci;
+  sincosf(a.elevation + dinc, &si, &ci);
+  const float3 d = normalize(qrot(a.quat, make_float3(ci * ca, ci * sa, si)));
+  const bool masked = a.mask != nullptr && a.mask[i] != 0;
+  RayRec ray;
+  ray.o_L = make_float4(a.pos.x, a.pos.y, a.pos.z, 0.0f);
+  ray.d_E = make_float4(d.x, d.y, d.z, 1.0f / (float)a.ns);
+  ray.meta = make_uint4(kNone, (az << 16) | k, masked ? 0x80000000u : 0u, kAir);
+  a.rays[0][i] = ray;
+}
+
+// ---------------------------------------------------------------------------
+// traversal
+struct WoopRay {
+  float3 o;
+  int kx, ky, kz;
+  float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float sel(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ WoopRay make_woop(float3 o, float3 d) {
+  WoopRay w;
+  w.o = o;
+  const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+  w.kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+  w.kx = w.kz == 2 ? 0 : w.kz + 1;
+  w.ky = w.kx == 2 ? 0 : w.kx + 1;
+  const float dz = sel(d, w.kz);
+  if (dz < 0.0f) {
+    const int t = w.kx;
+    w.kx = w.ky;
+    w.ky = t;
+  }
+  w.Sx = sel(d, w.kx) / dz;
+  w.Sy = sel(d, w.ky) / dz;
+  w.Sz = 1.0f / dz;
+  return w;
+}
+
+// watertight test; returns t (or -1) -- products are kept unfused so that a
+// shared edge evaluates to exactly opposite values in both triangles
+__device__ __forceinline__ float woop_hit(const WoopRay& w, float3 v0, float3 v1, float3 v2) {
+  const float3 A = v0 - w.o, B = v1 - w.o, C = v2 - w.o;
+  const float Az_ = sel(A, w.kz), Bz_ = sel(B, w.kz), Cz_ = sel(C, w.kz);
+  const float Ax = __fsub_rn(sel(A, w.kx), __fmul_rn(w.Sx, Az_));
+  const float Ay = __fsub_rn(sel(A, w.ky), __fmul_rn(w.Sy, Az_));
+  const float Bx = __fsub_rn(sel(B, w.kx), __fmul_rn(w.Sx, Bz_));
+  const float By = __fsub_rn(sel(B, w.ky), __fmul_rn(w.Sy, Bz_));
+  const float Cx = __fsub_rn(sel(C, w.kx), __fmul_rn(w.Sx, Cz_));
+  const float Cy = __fsub_rn(sel(C, w.ky), __fmul_rn(w.Sy, Cz_));
+  const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return -1.0f;
+  const float det = U + V + W;
+  if (det == 0.0f) return -1.0f;
+  const float T = U * (w.Sz * Az_) + V * (w.Sz * Bz_) + W * (w.Sz * Cz_);
+  return T / det;
+}
+
+// Closest hit with t_min < t and (t, original id) lexicographically smallest,
+// t < t_best on entry; or, with any_hit, the first hit with t_min < t < t_best.
+// Returns the leaf index or kNone.
+template <bool kAny, bool kCount>
+__device__ __forceinline__ uint32_t traverse(const ScanArgs& a, float3 o, float3 d, float t_min, float& t_best,
+                                             uint32_t skip, uint32_t& n_nodes, uint32_t& n_tris) {
+  const uint32_t nt = a.n_tris;
+  if (nt == 0) return kNone;
+  const WoopRay w = make_woop(o, d);
+  const float3 id = make_float3(1.0f / (fabsf(d.x) > 1e-30f ? d.x : copysignf(1e-30f, d.x)),
+                                1.0f / (fabsf(d.y) > 1e-30f ? d.y : copysignf(1e-30f, d.y)),
+                                1.0f / (fabsf(d.z) > 1e-30f ? d.z : copysignf(1e-30f, d.z)));
+  uint32_t stack[kStack];
+  int sp = 0;
+  uint32_t node = nt == 1 ? kLeafBit : 0u;
+  uint32_t best = kNone, best_id = 0u;
+  while (true) {
+    if (!(node & kLeafBit)) {
+      if (kCount) ++n_nodes;
+      const float4* np = a.nodes + 4 * (size_t)node;
+      const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+      // child 0
+      float t0 = (n0.x - o.x) * id.x, t1 = (n0.y - o.x) * id.x;
+      float lo0 = fminf(t0, t1), hi0 = fmaxf(t0, t1);
+      t0 = (n0.z - o.y) * id.y;
+      t1 = (n0.w - o.y) * id.y;
+      lo0 = fmaxf(lo0, fminf(t0, t1));
+      hi0 = fminf(hi0, fmaxf(t0, t1));
+      t0 = (n2.x - o.z) * id.z;
+      t1 = (n2.y - o.z) * id.z;
+      lo0 = fmaxf(fmaxf(lo0, fminf(t0, t1)), t_min);
+      hi0 = fminf(fminf(hi0, fmaxf(t0, t1)) * kBoxInflate, t_best);
+      // child 1
+      t0 = (n1.x - o.x) * id.x;
+      t1 = (n1.y - o.x) * id.x;
+      float lo1 = fminf(t0, t1), hi1 = fmaxf(t0, t1);
+      t0 = (n1.z - o.y) * id.y;
+      t1 = (n1.w - o.y) * id.y;
+      lo1 = fmaxf(lo1, fminf(t0, t1));
+      hi1 = fminf(hi1, fmaxf(t0, t1));
+      t0 = (n2.z - o.z) * id.z;
+      t1 = (n2.w - o.z) * id.z;
+      lo1 = fmaxf(fmaxf(lo1, fminf(t0, t1)), t_min);
+      hi1 = fminf(fminf(hi1, fmaxf(t0, t1)) * kBoxInflate, t_best);
+      const bool h0 = lo0 <= hi0, h1 = lo1 <= hi1;
+      const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
+      if (h0 && h1) {
+        const bool first0 = lo0 <= lo1;
+        node = first0 ? c0 : c1;
+        if (sp < kStack) stack[sp++] = first0 ? c1 : c0;
+        else atomicOr(&a.ctr->error, kErrStack);
+        continue;
+      }
+      if (h0 || h1) {
+        node = h0 ? c0 : c1;
+        continue;
+      }
+    } else {
+      const uint32_t j = node & ~kLeafBit;
+      if (j != skip) {
+        if (kCount) ++n_tris;
+        const float4* tp = a.tri + 3 * (size_t)j;
+        const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+        const float t = woop_hit(w, f3(v0), f3(v1), f3(v2));
+        if (t > t_min) {
+          if (kAny) {
+            if (t < t_best) return j;
+          } else {
+            const uint32_t tid = __float_as_uint(v0.w);
+            if (t < t_best || (t == t_best && best != kNone && tid < best_id)) {
+              t_best = t;
+              best = j;
+              best_id = tid;
+            }
+          }
+        }
+      }
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  return best;
+}
+
+// ---------------------------------------------------------------------------
+// trace: closest hit of every queued ray; multipath visibility of the
+// air-path return (Sec. III-A) for hits at bounce >= 1
+template <bool kCount>
+__global__ void __launch_bounds__(kTraceBlock) k_trace(ScanArgs a, uint32_t bounce) {
+  const uint32_t n = a.ctr->count[bounce];
+  const uint32_t tiles = (n + kShadeBlock - 1) / kShadeBlock;
+  const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  for (uint32_t t = gtid; t < tiles; t += gsz) a.tile_status[t] = 0ull;
+  const RayRec* __restrict__ q = a.rays[bounce & 1];
+  const float r_lim = (a.flags & RR_MULTIPATH) ? 2.0f * a.r_max : a.r_max;
+  const bool want_air = (a.flags & RR_MULTIPATH) && bounce >= 1;
+  const float sigma = d3_sigma(a);
+  const int lane = threadIdx.x & 31;
+  uint32_t n_closest = 0, n_any = 0, n_nodes = 0, n_tris = 0;
+  while (true) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&a.ctr->trace_ticket[bounce], 32u);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (base >= n) break;
+    const uint32_t i = base + lane;
+    if (i >= n) continue;
+    const RayRec ray = q[i];
+    const float3 o = f3(ray.o_L), d = f3(ray.d_E);
+    const uint32_t medium = ray.meta.w;
+    const float n_cur = medium == kAir ? 1.0f : __ldg(&a.mats[medium].n);
+    float t = (r_lim - ray.o_L.w) / n_cur;   // past it no return can reach the image
+    const uint32_t leaf = traverse<false, kCount>(a, o, d, a.t_min, t, ray.meta.x, n_nodes, n_tris);
+    ++n_closest;
+    HitRec h;
+    h.t = leaf == kNone ? INFINITY : t;
+    h.leaf = leaf;
+    h.flags = 0u;
+    h.wa_g = 0.0f;
+    if (want_air && leaf != kNone) {
+      const float4* tp = a.tri + 3 * (size_t)leaf;
+      const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+      const MatDev m = a.mats[__float_as_uint(v1.w)];
+      float3 nrm = normalize(cross(f3(v1) - f3(v0), f3(v2) - f3(v0)));
+      float cos_i = -dot(d, nrm);
+      const bool entering = cos_i > 0.0f;
+      float n2 = m.n;
+      if (!entering) {
+        nrm = -nrm;
+        cos_i = -cos_i;
+        n2 = 1.0f;
+      }
+      const float3 p = o + t * d;
+      const float3 v = a.pos - p;
+      const float dist = length(v);
+      const float side = dot(v, nrm);
+      float3 dir_out = make_float3(0.f, 0.f, 0.f);
+      bool cand = false;
+      if (entering && medium == kAir) {
+        dir_out = normalize(d + (2.0f * cos_i) * nrm);
+        cand = side > 0.0f;
+      } else if (!entering && medium != kAir && !m.pec) {
+        const float eta = n_cur / n2;
+        const float sin2_t = eta * eta * (1.0f - cos_i * cos_i);
+        if (sin2_t < 1.0f) {
+          const float cos_t = sqrtf(1.0f - sin2_t);
+          dir_out = normalize(eta * d + (eta * cos_i - cos_t) * nrm);
+          cand = side < 0.0f;
+        }
+      }
+      if (cand) {
+        const float wa = brdf_window(m, a.lut + (size_t)__float_as_uint(v1.w) * (kLutCells + 1),
+                                     angle_between(dir_out, v), a.beam_width);
+        if (wa > 0.0f) {
+          float t_s = dist;
+          const uint32_t occ = traverse<true, kCount>(a, p, (1.0f / dist) * v, a.t_min, t_s, leaf, n_nodes, n_tris);
+          ++n_any;
+          h.flags = 1u;
+          if (occ == kNone) {
+            h.flags |= 2u;
+            const float delta = angle_between(p - a.pos, beam_axis(a, ray.meta.y >> 16));
+            const float g = sigma > 0.0f ? expf(-0.5f * (delta / sigma) * (delta / sigma)) : 0.0f;
+            h.wa_g = wa * g;
+          }
+        }
+      }
+    }
+    a.hits[i] = h;
+  }
+  // counters, one atomic per warp
+  for (int off = 16; off > 0; off >>= 1) {
+    n_closest += __shfl_xor_sync(0xFFFFFFFFu, n_closest, off);
+    n_any += __shfl_xor_sync(0xFFFFFFFFu, n_any, off);
+  }
+  if (lane == 0) {
+    if (n_closest) atomicAdd(&a.ctr->stat_closest, (unsigned long long)n_closest);
+    if (n_any) atomicAdd(&a.ctr->stat_anyhit, (unsigned long long)n_any);
+  }
+  if (kCount) {
+    unsigned long long nn = n_nodes, nt = n_tris;
+    for (int off = 16; off > 0; off >>= 1) {
+      nn += __shfl_xor_sync(0xFFFFFFFFu, nn, off);
+      nt += __shfl_xor_sync(0xFFFFFFFFu, nt, off);
+    }
+    if (lane == 0) {
+      atomicAdd(&a.ctr->stat_nodes, nn);
+      atomicAdd(&a.ctr->stat_tris, nt);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// decoupled look-back over tiles: status word = flag << 62 | recs << 31 | kids
+constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPre = 2ull << 62;
+constexpr unsigned long long kMask31 = 0x7FFFFFFFull;
+
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_status(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// exclusive (kids, recs) prefix of tile `tile`, computed by one full warp
+__device__ __forceinline__ uint2 look_back(const ScanArgs& a, uint32_t tile, uint32_t agg_kids, uint32_t agg_recs) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long* st = a.tile_status;
+  const unsigned long long mine = ((unsigned long long)agg_recs << 31) | agg_kids;
+  if (tile == 0) {
+    if (lane == 0) st_status(st, kFlagPre | mine);
+    return make_uint2(0u, 0u);
+  }
+  if (lane == 0) st_status(st + tile, kFlagAgg | mine);
+  uint32_t ex_k = 0, ex_r = 0;
+  int j = (int)tile - 1;
+  uint32_t spins = 0;
+  while (true) {
+    const int idx = j - lane;
+    unsigned long long s = idx >= 0 ? ld_status(st + idx) : kFlagPre;
+    while (__any_sync(0xFFFFFFFFu, (s >> 62) == 0ull)) {
+      if (++spins > kSpinLimit) {
+        if (lane == 0) atomicOr(&a.ctr->error, kErrTimeout);
+        s = kFlagPre;   // give up: the scan is reported as failed
+        break;
+      }
+      if ((s >> 62) == 0ull) s = ld_status(st + idx);
+    }
+    const uint32_t pre = __ballot_sync(0xFFFFFFFFu, (s >> 62) == 2ull);
+    const int first = pre ? __ffs(pre) - 1 : 32;
+    const uint32_t vk = lane <= first ? (uint32_t)(s & kMask31) : 0u;
+    const uint32_t vr = lane <= first ? (uint32_t)((s >> 31) & kMask31) : 0u;
+    ex_k += __reduce_add_sync(0xFFFFFFFFu, vk);
+    ex_r += __reduce_add_sync(0xFFFFFFFFu, vr);
+    if (pre) break;
+    j -= 32;
+  }
+  if (lane == 0)
+    st_status(st + tile, kFlagPre | ((unsigned long long)(agg_recs + ex_r) << 31) | (agg_kids + ex_k));
+  return make_uint2(ex_k, ex_r);
+}
+
+// ---------------------------------------------------------------------------
+// shade
+__global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t bounce) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_wsum[kShadeBlock / 32];
+  __shared__ uint2 s_excl;
+  const uint32_t n = a.ctr->count[bounce];
+  const uint32_t tiles = (n + kShadeBlock - 1) / kShadeBlock;
+  const uint32_t rec0 = a.ctr->rec_start[bounce];
+  const uint32_t seg0 = a.ctr->seg_start[bounce];
+  const RayRec* __restrict__ qin = a.rays[bounce & 1];
+  RayRec* __restrict__ qout = a.rays[(bounce + 1) & 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float3 s_pos = a.pos;
+  const bool deeper = bounce + 1 < a.max_bounces;
+  if (n == 0) {
+    // empty queue: no tile will publish the offsets of the next bounce
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.ctr->count[bounce + 1] = 0u;
+      a.ctr->rec_start[bounce + 1] = rec0;
+      a.ctr->seg_start[bounce + 1] = seg0;
+    }
+    return;
+  }
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctr->shade_ticket[bounce], 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= tiles) break;
+    const uint32_t i = tile * kShadeBlock + threadIdx.x;
+    RayRec kid[2];
+    uint2 rec[2];
+    uint32_t nk = 0, nr = 0;
+    if (i < n) {
+      const RayRec ray = qin[i];
+      const HitRec h = a.hits[i];
+      const uint32_t az = ray.meta.y >> 16, k = ray.meta.y & 0xFFFFu;
+      const uint32_t path = ray.meta.z & 0x7FFFFFFFu;
+      const bool masked = (ray.meta.z >> 31) != 0u;
+      const uint32_t medium = ray.meta.w;
+      const float E = ray.d_E.w;
+      float tal[4] = {0.f, 0.f, 0.f, 0.f};
+      float dbg_cos = 0.f, dbg_ret_t = 0.f, dbg_ret_a = 0.f;
+      uint32_t orig = kNone;
+      if (h.leaf == kNone) {
+        tal[2] = E;   // escaped (or beyond the range limit)
+      } else {
+        const float3 o = f3(ray.o_L), d = f3(ray.d_E);
+        const float t = h.t;
+        const float3 p = o + t * d;
+        const float n_cur = medium == kAir ? 1.0f : a.mats[medium].n;
+        const float L1 = ray.o_L.w + n_cur * t;
+        float E1 = E;
+        if (medium != kAir) {
+          const float alpha = kPi * n_cur * a.mats[medium].tan_d * a.freq / kC0;
+          E1 = E * expf(-2.0f * alpha * t);
+          tal[1] = E - E1;
+        }
+        const float4* tp = a.tri + 3 * (size_t)h.leaf;
+        const float4 v0 = tp[0], v1 = tp[1], v2 = tp[2];
+        orig = __float_as_uint(v0.w);
+        const uint32_t mid = __float_as_uint(v1.w);
+        const MatDev m = a.mats[mid];
+        const float4* lut = a.lut + (size_t)mid * (kLutCells + 1);
+        float3 nrm = normalize(cross(f3(v1) - f3(v0), f3(v2) - f3(v0)));
+        float cos_i = -dot(d, nrm);
+        const bool entering = cos_i > 0.0f;
+        float n2 = m.n;
+        uint32_t next_med = mid;
+        if (!entering) {
+          nrm = -nrm;
+          cos_i = -cos_i;
+          n2 = 1.0f;
+          next_med = kAir;
+        }
+        float R = 1.0f, T = 0.0f, cos_t = 0.0f;
+        bool can_refract = false;
+        const float eta = n_cur / n2;
+        if (!m.pec) {
+          const float sin2_t = eta * eta * (1.0f - cos_i * cos_i);
+          if (sin2_t < 1.0f) {
+            cos_t = sqrtf(1.0f - sin2_t);
+            const float rs = (n_cur * cos_i - n2 * cos_t) / (n_cur * cos_i + n2 * cos_t);
+            const float rp = (n_cur * cos_t - n2 * cos_i) / (n_cur * cos_t + n2 * cos_i);
+            R = 0.5f * (rs * rs + rp * rp);
+            T = 1.0f - R;
+            can_refract = true;
+          }
+        }
+        const float3 d_refl = normalize(d + (2.0f * cos_i) * nrm);
+        // traveled-path return: omega = theta0 + theta1 = 2 theta0, range L1
+        const float theta0 = angle_between(d, -nrm);
+        const float ret_t = E1 * R * fminf(brdf_window(m, lut, 2.0f * theta0, a.beam_width), 1.0f);
+        float ret_a = 0.0f, range_a = 0.0f;
+        bool air_T = false;
+        if (h.wa_g > 0.0f) {
+          float base, cap;
+          if (entering && medium == kAir) {
+            base = E1 * R;
+            cap = E1 * R - ret_t;
+          } else {
+            air_T = true;
+            base = E1 * T;
+            cap = E1 * T;
+          }
+          ret_a = fmaxf(fminf(base * h.wa_g, cap), 0.0f);
+          range_a = 0.5f * (L1 + length(s_pos - p));
+        }
+        tal[0] = ret_t + ret_a;
+        dbg_cos = cos_i;
+        dbg_ret_t = ret_t;
+        dbg_ret_a = ret_a;
+        if (!masked) {
+          if (ret_t > 0.0f) {
+            const float bin = floorf(L1 / a.bin_size);
+            if (bin < (float)a.n_bins) {
+              float e = ret_t;
+              if (a.flags & RR_SPECKLE) e *= -logf(u01(draw(a, az, k, 1u | (((path << 8) | bounce) << 8)).x));
+              rec[nr++] = make_uint2((az << 16) | (uint32_t)bin, __float_as_uint(e));
+            }
+          }
+          if (ret_a > 0.0f) {
+            const float bin = floorf(range_a / a.bin_size);
+            if (bin < (float)a.n_bins) {
+              float e = ret_a;
+              if (a.flags & RR_SPECKLE) e *= -logf(u01(draw(a, az, k, 1u | (((path << 8) | bounce) << 8)).y));
+              rec[nr++] = make_uint2((az << 16) | (uint32_t)bin, __float_as_uint(e));
+            }
+          }
+        }
+        const float e_refl = fmaxf(E1 * R - ret_t - (air_T ? 0.0f : ret_a), 0.0f);
+        const float e_refr = fmaxf(E1 * T - (air_T ? ret_a : 0.0f), 0.0f);
+        const bool in_range = L1 < a.r_max;
+        const bool sp_refl = deeper && in_range && e_refl >= a.min_energy;
+        const bool sp_refr =
+            deeper && in_range && can_refract && (a.flags & RR_REFRACTION) && e_refr >= a.min_energy;
+        if (!sp_refl) tal[3] += e_refl;
+        if (!sp_refr) tal[3] += e_refr;
+        const uint32_t mbit = ray.meta.z & 0x80000000u;
+        if (sp_refl) {
+          RayRec& c = kid[nk++];
+          c.o_L = make_float4(p.x, p.y, p.z, L1);
+          c.d_E = make_float4(d_refl.x, d_refl.y, d_refl.z, e_refl);
+          c.meta = make_uint4(h.leaf, ray.meta.y, mbit | (path << 1), medium);
+        }
+        if (sp_refr) {
+          const float3 d_refr = normalize(eta * d + (eta * cos_i - cos_t) * nrm);
+          RayRec& c = kid[nk++];
+          c.o_L = make_float4(p.x, p.y, p.z, L1);
+          c.d_E = make_float4(d_refr.x, d_refr.y, d_refr.z, e_refr);
+          c.meta = make_uint4(h.leaf, ray.meta.y, mbit | (path << 1) | 1u, next_med);
+        }
+      }
+      if (a.tallies != nullptr) {
+        float* tp = a.tallies + 4 * (size_t)(az * a.ns + k);
+        for (int q = 0; q < 4; ++q)
+          if (tal[q] != 0.0f) atomicAdd(tp + q, tal[q]);
+      }
+      if (a.segs != nullptr) {
+        const uint32_t si = seg0 + i;
+        if (si < a.seg_cap) {
+          rr_segment sg;
+          sg.az = az;
+          sg.k = k;
+          sg.path = path;
+          sg.bounce = bounce;
+          sg.tri = orig;
+          sg.t = h.leaf == kNone ? INFINITY : h.t;
+          sg.E = E;
+          sg.flags = h.flags;
+          sg.cos_i = dbg_cos;
+          sg.ret_t = dbg_ret_t;
+          sg.ret_a = dbg_ret_a;
+          sg.reserved = 0.f;
+          a.segs[si] = sg;
+        } else {
+          atomicOr(&a.ctr->error, kErrCapacitySegs);
+        }
+      }
+    }
+    // block scan of (kids, recs)
+    const uint32_t packed = nk | (nr << 16);
+    uint32_t x = packed;
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    uint32_t wpre = 0, total = 0;
+    for (int w2 = 0; w2 < kShadeBlock / 32; ++w2) {
+      const uint32_t v = s_wsum[w2];
+      if (w2 < warp) wpre += v;
+      total += v;
+    }
+    const uint32_t local = x - packed + wpre;
+    if (warp == 0) {
+      const uint2 ex = look_back(a, tile, total & 0xFFFFu, total >> 16);
+      if (lane == 0) s_excl = ex;
+    }
+    __syncthreads();
+    const uint2 ex = s_excl;
+    const uint32_t kbase = ex.x + (local & 0xFFFFu), rbase = ex.y + (local >> 16);
+    for (uint32_t c = 0; c < nk; ++c) {
+      const uint32_t pos = kbase + c;
+      if (pos < a.ray_cap) qout[pos] = kid[c];
+    }
+    for (uint32_t c = 0; c < nr; ++c) {
+      const uint32_t pos = rec0 + rbase + c;
+      if (pos < a.rec_cap) a.recs[pos] = rec[c];
+    }
+    if (tile == tiles - 1 && threadIdx.x == 0) {
+      const uint32_t kids = ex.x + (total & 0xFFFFu), recs = ex.y + (total >> 16);
+      ScanCounters* cn = a.ctr;
+      uint32_t next = kids;
+      if (kids > a.ray_cap) {
+        atomicOr(&cn->error, kErrCapacityRays);
+        atomicMax(&cn->need_rays, kids);
+        next = a.ray_cap;
+      }
+      uint32_t rend = rec0 + recs;
+      if (rend > a.rec_cap || rend < rec0) {
+        atomicOr(&cn->error, kErrCapacityRecs);
+        atomicMax(&cn->need_recs, rend);
+        rend = a.rec_cap;
+      }
+      cn->count[bounce + 1] = deeper ? next : 0u;
+      cn->rec_start[bounce + 1] = rend;
+      cn->seg_start[bounce + 1] = seg0 + n;
+      cn->stat_returns += (unsigned long long)recs;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace rr
+
+namespace rr_host {
+
+using namespace rr;
+
+static int g_num_sms = 0;
+static int g_trace_blocks_per_sm = 0;
+static int g_shade_blocks_per_sm = 0;
+
+static void init_dims() {
+  if (g_num_sms) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_trace_blocks_per_sm, k_trace<false>, kTraceBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_shade_blocks_per_sm, k_shade, kShadeBlock, 0);
+  if (g_trace_blocks_per_sm < 1) g_trace_blocks_per_sm = 1;
+  if (g_shade_blocks_per_sm < 1) g_shade_blocks_per_sm = 1;
+  if (g_num_sms < 1) g_num_sms = 1;
+}
+
+LaunchDims trace_dims() {
+  init_dims();
+  LaunchDims d;
+  d.trace_grid = g_num_sms * g_trace_blocks_per_sm;
+  d.trace_block = kTraceBlock;
+  d.shade_grid = g_num_sms * g_shade_blocks_per_sm;
+  d.shade_block = kShadeBlock;
+  return d;
+}
+
+cudaError_t launch_raygen(const ScanArgs& a, cudaStream_t st) {
+  const uint32_t n = a.n_az * a.ns;
+  k_raygen<<<(n + 255) / 256, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
+  const LaunchDims d = trace_dims();
+  if (a.flags & RR_COUNT_TRAVERSAL)
+    k_trace<true><<<d.trace_grid, d.trace_block, 0, st>>>(a, bounce);
+  else
+    k_trace<false><<<d.trace_grid, d.trace_block, 0, st>>>(a, bounce);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shade(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
+  const LaunchDims d = trace_dims();
+  k_shade<<<d.shade_grid, d.shade_block, 0, st>>>(a, bounce);
+  return cudaGetLastError();
+}
+
+}  // namespace rr_host

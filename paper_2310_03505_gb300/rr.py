@@ -1,0 +1,293 @@
+"""Python binding of the C ABI in ``include/rr.h`` (ctypes).
+
+Argument marshalling only: every function has the name of the C entry point
+it calls, turns numpy arrays / torch tensors / dicts into pointers and
+structs, raises ``RRError`` on a non-zero status, and nothing else.  All the
+scan work runs in the CUDA library ``librr.so``; there is no CPU fallback.
+If the library is missing, every call raises.
+
+Buffers may be numpy arrays, CPU tensors or CUDA tensors (the library tells
+host and device pointers apart).  Calls run on torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librr.so")
+
+RR_OK, RR_ERR_INVALID_ARG, RR_ERR_OOM, RR_ERR_CAPACITY, RR_ERR_TIMEOUT, RR_ERR_CUDA, RR_ERR_BUSY = range(7)
+RR_MULTIPATH, RR_REFRACTION, RR_SPECKLE, RR_NOISE, RR_COUNT_TRAVERSAL = 1, 2, 4, 8, 16
+RR_MAT_PERFECT_CONDUCTOR = 1
+RR_NO_HIT = 0xFFFFFFFF
+RR_K_RAYGEN, RR_K_TRACE, RR_K_SHADE, RR_K_IMAGE, RR_K_BUILD, RR_K_COUNT = range(6)
+KERNEL_NAMES = ["raygen", "trace", "shade", "image", "build"]
+
+
+class RRError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rr status {code}: {msg}")
+        self.code = code
+
+
+class rr_material(C.Structure):
+    _fields_ = [("eps_r", C.c_float), ("loss_tangent", C.c_float), ("A", C.c_float), ("B", C.c_float),
+                ("C", C.c_float), ("flags", C.c_uint32)]
+
+
+class rr_pose(C.Structure):
+    _fields_ = [("p", C.c_float * 3), ("q", C.c_float * 4)]
+
+
+class rr_sensor_params(C.Structure):
+    _fields_ = [("n_azimuth", C.c_uint32), ("rays_per_beam", C.c_uint32), ("max_bounces", C.c_uint32),
+                ("n_bins", C.c_uint32), ("beam_width_rad", C.c_float), ("beam_prob", C.c_float),
+                ("elevation_rad", C.c_float), ("bin_size_m", C.c_float), ("t_min_m", C.c_float),
+                ("min_energy", C.c_float), ("freq_hz", C.c_float), ("blur_sigma_bins", C.c_float),
+                ("az_pattern_sigma", C.c_float), ("noise_sys", C.c_float), ("noise_amb", C.c_float),
+                ("flags", C.c_uint32), ("seed", C.c_uint64), ("scan_id", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class rr_segment(C.Structure):
+    _fields_ = [("az", C.c_uint32), ("k", C.c_uint32), ("path", C.c_uint32), ("bounce", C.c_uint32),
+                ("tri", C.c_uint32), ("t", C.c_float), ("E", C.c_float), ("flags", C.c_uint32),
+                ("cos_i", C.c_float), ("ret_t", C.c_float), ("ret_a", C.c_float), ("reserved", C.c_float)]
+
+
+SEGMENT_DTYPE = np.dtype([("az", "<u4"), ("k", "<u4"), ("path", "<u4"), ("bounce", "<u4"), ("tri", "<u4"),
+                          ("t", "<f4"), ("E", "<f4"), ("flags", "<u4"), ("cos_i", "<f4"), ("ret_t", "<f4"),
+                          ("ret_a", "<f4"), ("reserved", "<f4")])
+
+
+class rr_scene_info(C.Structure):
+    _fields_ = [("n_triangles", C.c_uint32), ("n_materials", C.c_uint32), ("bvh_depth", C.c_uint32),
+                ("reserved", C.c_uint32), ("device_bytes", C.c_uint64), ("workspace_bytes", C.c_uint64),
+                ("build_ms", C.c_float), ("reserved_f", C.c_float)]
+
+
+class rr_stats(C.Structure):
+    _fields_ = [("closest_queries", C.c_uint64), ("anyhit_queries", C.c_uint64), ("returns", C.c_uint64),
+                ("scans", C.c_uint64), ("nodes_visited", C.c_uint64), ("tris_tested", C.c_uint64),
+                ("kernel_launches", C.c_uint64)]
+
+
+class rr_profile(C.Structure):
+    _fields_ = [("ms", C.c_double * RR_K_COUNT), ("launches", C.c_uint64 * RR_K_COUNT)]
+
+
+# every symbol declared in include/rr.h with its ctypes signature
+_P = C.c_void_p
+SIGNATURES = {
+    "rr_version": ([], C.c_int),
+    "rr_last_error": ([], C.c_char_p),
+    "rr_set_stream": ([_P], C.c_int),
+    "rr_scene_create": ([_P, C.c_uint32, _P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(_P)], C.c_int),
+    "rr_scene_destroy": ([_P], C.c_int),
+    "rr_scene_update_vertices": ([_P, _P], C.c_int),
+    "rr_scene_info_get": ([_P, C.POINTER(rr_scene_info)], C.c_int),
+    "rr_scene_export_bvh": ([_P, _P, _P, _P, _P, _P], C.c_int),
+    "rr_scan": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P], C.c_int),
+    "rr_scan_async": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P], C.c_int),
+    "rr_scene_sync": ([_P], C.c_int),
+    "rr_scan_batch": ([_P, C.c_uint32, _P, _P, _P], C.c_int),
+    "rr_scan_debug": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P, _P, _P, C.c_uint64,
+                       C.POINTER(C.c_uint64), _P], C.c_int),
+    "rr_polar_to_db_u8": ([_P, C.c_uint64, C.c_float, _P], C.c_int),
+    "rr_scene_stats": ([_P, C.POINTER(rr_stats), C.c_int], C.c_int),
+    "rr_profile_enable": ([_P, C.c_int], C.c_int),
+    "rr_profile_read": ([_P, C.POINTER(rr_profile), C.c_int], C.c_int),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load librr.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing: run paper_2310_03505_gb300.build first")
+            lib = C.CDLL(path)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != RR_OK:
+        raise RRError(rc, load().rr_last_error().decode())
+
+
+def _ptr(x):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"], "buffers must be contiguous"
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "buffers must be contiguous"
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _use_torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            load().rr_set_stream(C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    except ImportError:
+        pass
+
+
+# ------------------------------------------------------------------- structs
+def make_params(s: dict) -> rr_sensor_params:
+    flags = ((RR_MULTIPATH if s.get("multipath") else 0) | (RR_REFRACTION if s.get("refraction") else 0) |
+             (RR_SPECKLE if s.get("speckle") else 0) | (RR_NOISE if s.get("noise") else 0) |
+             (RR_COUNT_TRAVERSAL if s.get("count_traversal") else 0))
+    return rr_sensor_params(s["n_azimuth"], s["rays_per_beam"], s["max_bounces"], s["n_bins"], s["beam_width"],
+                            s["beam_prob"], s["elevation"], s["bin_size"], s["t_min"], s["min_energy"], s["freq_hz"],
+                            s["blur_sigma_bins"], s["az_pattern_sigma"], s["noise_sys"], s["noise_amb"], flags,
+                            int(s["seed"]), int(s["scan_id"]), 0)
+
+
+def make_pose(pz: dict) -> rr_pose:
+    P = rr_pose()
+    for i in range(3):
+        P.p[i] = float(pz["p"][i])
+    for i in range(4):
+        P.q[i] = float(pz["q"][i])
+    return P
+
+
+def make_materials(mats) -> C.Array:
+    arr = (rr_material * len(mats))()
+    for i, m in enumerate(mats):
+        arr[i] = rr_material(m["eps_r"], m["loss_tangent"], m["A"], m["B"], m["C"],
+                             RR_MAT_PERFECT_CONDUCTOR if m.get("pec") else 0)
+    return arr
+
+
+# ------------------------------------------------------------------- C ABI
+def rr_version() -> int:
+    return load().rr_version()
+
+
+def rr_last_error() -> str:
+    return load().rr_last_error().decode()
+
+
+def rr_set_stream(stream_handle) -> None:
+    _check(load().rr_set_stream(C.c_void_p(stream_handle)))
+
+
+def rr_scene_create(vertices, triangles, material_ids, materials):
+    """vertices [V,3] float32, triangles [T,3] uint32, material_ids [T] uint16,
+    materials: list of dicts (eps_r, loss_tangent, A, B, C, pec).  Returns the handle."""
+    _use_torch_stream()
+    L = load()
+    mats = make_materials(materials)
+    h = C.c_void_p()
+    nv = int(vertices.shape[0])
+    nt = int(triangles.shape[0])
+    _check(L.rr_scene_create(_ptr(vertices), nv, _ptr(triangles), nt, _ptr(material_ids), C.cast(mats, C.c_void_p),
+                             len(materials), C.byref(h)))
+    return h
+
+
+def rr_scene_destroy(scene) -> None:
+    _check(load().rr_scene_destroy(scene))
+
+
+def rr_scene_update_vertices(scene, vertices) -> None:
+    _use_torch_stream()
+    _check(load().rr_scene_update_vertices(scene, _ptr(vertices)))
+
+
+def rr_scene_info_get(scene) -> dict:
+    info = rr_scene_info()
+    _check(load().rr_scene_info_get(scene, C.byref(info)))
+    return {k: getattr(info, k) for k, _ in rr_scene_info._fields_ if not k.startswith("reserved")}
+
+
+def rr_scene_export_bvh(scene, n_triangles: int) -> dict:
+    T = int(n_triangles)
+    out = dict(morton=np.zeros(T, np.uint32), perm=np.zeros(T, np.uint32),
+               children=np.zeros((max(T - 1, 0), 2), np.uint32), parents=np.zeros(max(2 * T - 1, 0), np.uint32),
+               boxes=np.zeros((max(T - 1, 0), 2, 6), np.float32))
+    _use_torch_stream()
+    _check(load().rr_scene_export_bvh(scene, _ptr(out["morton"]), _ptr(out["perm"]), _ptr(out["children"]),
+                                      _ptr(out["parents"]), _ptr(out["boxes"])))
+    return out
+
+
+def rr_scan(scene, pose: dict, params: dict, out_polar) -> None:
+    _use_torch_stream()
+    P, S = make_pose(pose), make_params(params)
+    _check(load().rr_scan(scene, C.byref(P), C.byref(S), _ptr(out_polar)))
+
+
+def rr_scan_async(scene, pose: dict, params: dict, out_polar) -> None:
+    _use_torch_stream()
+    P, S = make_pose(pose), make_params(params)
+    _check(load().rr_scan_async(scene, C.byref(P), C.byref(S), _ptr(out_polar)))
+
+
+def rr_scene_sync(scene) -> None:
+    _use_torch_stream()
+    _check(load().rr_scene_sync(scene))
+
+
+def rr_scan_batch(scene, poses, params, outs) -> None:
+    _use_torch_stream()
+    n = len(poses)
+    P = (rr_pose * n)(*[make_pose(p) for p in poses])
+    S = (rr_sensor_params * n)(*[make_params(s) for s in params])
+    O = (C.c_void_p * n)(*[_ptr(o) for o in outs])
+    _check(load().rr_scan_batch(scene, n, C.cast(P, C.c_void_p), C.cast(S, C.c_void_p), C.cast(O, C.c_void_p)))
+
+
+def rr_scan_debug(scene, pose: dict, params: dict, out_polar, ray_mask=None, seg_capacity: int = 0,
+                  tallies: bool = False):
+    """Returns (segments structured array, per-ray tallies [n_az*Ns, 4] or None)."""
+    _use_torch_stream()
+    P, S = make_pose(pose), make_params(params)
+    segs = np.zeros(int(seg_capacity), SEGMENT_DTYPE) if seg_capacity else None
+    n0 = params["n_azimuth"] * params["rays_per_beam"]
+    tal = np.zeros((n0, 4), np.float32) if tallies else None
+    mask = None if ray_mask is None else np.ascontiguousarray(np.asarray(ray_mask, np.uint8).reshape(-1))
+    n = C.c_uint64()
+    _check(load().rr_scan_debug(scene, C.byref(P), C.byref(S), _ptr(mask), _ptr(out_polar), _ptr(segs),
+                                int(seg_capacity), C.byref(n), _ptr(tal)))
+    return (segs[: n.value] if segs is not None else None), tal
+
+
+def rr_polar_to_db_u8(polar, cutoff_db: float, out) -> None:
+    _use_torch_stream()
+    _check(load().rr_polar_to_db_u8(_ptr(polar), int(polar.numel()), float(cutoff_db), _ptr(out)))
+
+
+def rr_scene_stats(scene, reset: bool = False) -> dict:
+    st = rr_stats()
+    _use_torch_stream()
+    _check(load().rr_scene_stats(scene, C.byref(st), 1 if reset else 0))
+    return {k: getattr(st, k) for k, _ in rr_stats._fields_}
+
+
+def rr_profile_enable(scene, on: bool) -> None:
+    _check(load().rr_profile_enable(scene, 1 if on else 0))
+
+
+def rr_profile_read(scene, reset: bool = False) -> dict:
+    pr = rr_profile()
+    _check(load().rr_profile_read(scene, C.byref(pr), 1 if reset else 0))
+    return {KERNEL_NAMES[k]: (pr.ms[k], pr.launches[k]) for k in range(RR_K_COUNT)}

@@ -17,3 +17,15 @@ def pytest_configure(config):
 def tiny():
     from paper_2310_03505_gb300 import scenes
     return scenes.config_tiny()
+
+
+@pytest.fixture(scope="session")
+def rrlib():
+    """Build (if needed) and load the CUDA library; GPU tests only."""
+    import torch
+    from paper_2310_03505_gb300 import build, rr
+    build.build()
+    lib = rr.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.init()
+    return lib

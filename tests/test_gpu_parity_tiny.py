@@ -1,0 +1,156 @@
+"""Full-scan parity on the tiny room (400 beams x 8 rays, 3 bounces): the
+CUDA path through the C ABI against the FP64 oracle, ray by ray, segment by
+segment and bin by bin.  Needs a GPU."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2310_03505_gb300 import rr, scenes
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tiny_scene(rrlib):
+    sc, pz, params = scenes.config_tiny()
+    h = P.gpu_scene(sc)
+    yield sc, pz, params, h
+    rr.rr_scene_destroy(h)
+
+
+VARIANTS = {
+    "plain": {},
+    "noise_blur": dict(noise=True, noise_sys=1e-4, noise_amb=5e-5, blur_sigma_bins=1.5),
+    "az_pattern": dict(az_pattern_sigma=1.0, blur_sigma_bins=1.0),
+    "no_multipath": dict(multipath=False),
+    "no_refraction": dict(refraction=False),
+    "speckle": dict(speckle=True),
+    "other_seed": dict(seed=0xABCDEF12345, scan_id=7),
+    "min_energy": dict(min_energy=1e-4),
+}
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+def test_tiny_parity(tiny_scene, variant):
+    sc, pz, params, h = tiny_scene
+    params = scenes.sensor(**{**params, **VARIANTS[variant]})
+    ora = P.oracle_scan(sc, pz, params)
+    flags = ora["flags"]
+    assert flags.mean() < 0.02, f"{flags.sum()} of {flags.size} rays flagged"
+    # ray paths and hit distances (no mask: every ray traced)
+    img_all, segs, tal = P.gpu_debug(h, pz, params)
+    n, bad, max_rel = P.compare_paths(segs, ora["segments"], flags, range(params["n_azimuth"]))
+    assert n > 0.95 * flags.size
+    assert not bad, f"{len(bad)} mismatches, first: {bad[:5]}"
+    assert len(segs) == len(ora["segments"]) or flags.any()
+    ebad = P.compare_segment_energies(segs, ora["segments"], flags, range(params["n_azimuth"]))
+    assert not ebad, f"{len(ebad)} segment energy mismatches, first: {ebad[:6]}"
+    # energy bookkeeping per initial ray
+    assert np.max(np.abs(tal.sum(-1) - 1.0 / params["rays_per_beam"])) < 1e-5 / params["rays_per_beam"] * 10
+    ok = flags == 0
+    diff = np.abs(tal - ora["tallies"]).max(-1) * ok
+    worst = np.unravel_index(np.argmax(diff), diff.shape)
+    if diff[worst] >= 2e-6:
+        az, k = int(worst[0]), int(worst[1])
+        g = segs[(segs["az"] == az) & (segs["k"] == k)]
+        o = ora["segments"][(ora["segments"]["az"] == az) & (ora["segments"]["k"] == k)]
+        raise AssertionError(f"tallies of ray {(az, k)}: gpu {tal[worst]} oracle {ora['tallies'][worst]}\n"
+                             f"gpu segments {g}\noracle segments {o}")
+    # image with the flagged rays masked on both sides
+    img, _, _ = P.gpu_debug(h, pz, params, mask=flags)
+    slack = P.slack_after_post(ora, params)
+    excess, mx = P.image_excess(img, ora["image_masked"], slack)
+    assert mx > 0
+    assert excess <= P.IMG_REL, f"image excess {excess:.3g} of max {mx:.3g}"
+
+
+def test_tiny_scan_entry_points_agree(tiny_scene):
+    """rr_scan (device out), rr_scan (host out), rr_scan_async + sync,
+    rr_scan_batch and the debug path give the same image."""
+    import torch
+    sc, pz, params, h = tiny_scene
+    shape = (params["n_azimuth"], params["n_bins"])
+    dev = torch.zeros(shape, device="cuda")
+    rr.rr_scan(h, pz, params, dev)
+    host = np.zeros(shape, np.float32)
+    rr.rr_scan(h, pz, params, host)
+    asy = torch.zeros(shape, device="cuda")
+    rr.rr_scan_async(h, pz, params, asy)
+    rr.rr_scene_sync(h)
+    b1, b2 = torch.zeros(shape, device="cuda"), np.zeros(shape, np.float32)
+    rr.rr_scan_batch(h, [pz, pz], [params, params], [b1, b2])
+    dbg, _, _ = P.gpu_debug(h, pz, params)
+    ref = dev.cpu().numpy()
+    scale = float(ref.max())
+    for other in (host, asy.cpu().numpy(), b1.cpu().numpy(), b2, dbg):
+        assert np.max(np.abs(other - ref)) <= 1e-6 * scale
+
+
+def test_tiny_determinism(tiny_scene):
+    sc, pz, params, h = tiny_scene
+    a, sa, ta = P.gpu_debug(h, pz, params)
+    b, sb, tb = P.gpu_debug(h, pz, params)
+    assert np.array_equal(sa, sb)          # same rays, same order, same hits
+    assert np.max(np.abs(a - b)) <= 1e-6 * a.max()
+
+
+def test_db_map(tiny_scene):
+    import torch
+    sc, pz, params, h = tiny_scene
+    img = torch.zeros(params["n_azimuth"], params["n_bins"], device="cuda")
+    rr.rr_scan(h, pz, params, img)
+    out = torch.zeros(img.shape, dtype=torch.uint8, device="cuda")
+    rr.rr_polar_to_db_u8(img, 60.0, out)
+    g = out.cpu().numpy()
+    x = img.cpu().numpy().astype(np.float64)
+    o = orc.db_u8(x, 60.0)
+    # integer outputs agree except where the float value sits at a rounding edge
+    v = np.where(x > 0, 255.0 * (10 * np.log10(np.maximum(x, 1e-300)) + 60.0) / 60.0, 0.0)
+    edge = np.abs(v - np.floor(v) - 0.5) < 1e-3
+    assert np.array_equal(g[~edge], o[~edge])
+
+
+def test_empty_and_single_triangle(rrlib):
+    import torch
+    params = scenes.sensor(n_azimuth=16, rays_per_beam=4, max_bounces=2, n_bins=128, bin_size=0.1,
+                           noise=True, noise_sys=0.01, noise_amb=0.0)
+    pz = scenes.pose(0, 0, 0)
+    one = scenes.Scene("one", np.array([[5, -1, -1], [5, 1, -1], [5, 0, 1]], np.float32),
+                       np.array([[0, 2, 1]], np.uint32), np.zeros(1, np.uint16), [scenes.MATERIALS["metal"]])
+    empty = scenes.Scene("empty", np.zeros((0, 3), np.float32), np.zeros((0, 3), np.uint32), np.zeros(0, np.uint16),
+                         [scenes.MATERIALS["metal"]])
+    for sc in (empty, one):
+        h = rr.rr_scene_create(sc.vertices, sc.triangles, sc.material_ids, sc.materials)
+        try:
+            img = np.zeros((16, 128), np.float32)
+            rr.rr_scan(h, pz, params, img)
+        finally:
+            rr.rr_scene_destroy(h)
+        ora = orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, params)
+        assert np.max(np.abs(img - ora["image"])) <= 1e-3 * max(ora["image"].max(), 1e-30) + 1e-7
+
+
+def test_invalid_params(tiny_scene):
+    sc, pz, params, h = tiny_scene
+    out = np.zeros((params["n_azimuth"], params["n_bins"]), np.float32)
+    for bad in (dict(n_azimuth=0), dict(max_bounces=17), dict(n_bins=10 ** 6), dict(beam_prob=1.0),
+                dict(bin_size=0.0), dict(rays_per_beam=70000), dict(blur_sigma_bins=-1.0)):
+        with pytest.raises(rr.RRError) as e:
+            rr.rr_scan(h, pz, {**params, **bad}, out)
+        assert e.value.code == rr.RR_ERR_INVALID_ARG
+    with pytest.raises(rr.RRError):
+        rr.rr_scan(h, dict(p=(0, 0, 0), q=(0, 0, 0, 0)), params, out)
+
+
+def test_capacity_error_reports_size(tiny_scene):
+    """A tiny workspace limit is not settable through the ABI; instead check
+    that a scan needing more segments than the debug buffer holds says so."""
+    sc, pz, params, h = tiny_scene
+    import torch
+    out = torch.zeros(params["n_azimuth"], params["n_bins"], device="cuda")
+    with pytest.raises(rr.RRError) as e:
+        rr.rr_scan_debug(h, pz, params, out, seg_capacity=10)
+    assert e.value.code == rr.RR_ERR_CAPACITY
