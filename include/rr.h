@@ -243,6 +243,25 @@ int rr_scan_batch(rr_scene* scene, uint32_t n, const rr_pose* poses, const rr_se
 int rr_scan_debug(rr_scene* scene, const rr_pose* pose, const rr_sensor_params* params, const uint8_t* ray_mask,
                   float* out_polar, rr_segment* segs, uint64_t seg_capacity, uint64_t* n_segs, float* ray_tallies);
 
+/* Same scan as rr_scan, for callers that cannot allocate device memory
+   while they run: real-time loops that must never block on the allocator
+   (cudaMalloc / cudaFree can synchronise the device) and programs whose device
+   memory belongs to another allocator under a fixed budget.  The paper has no
+   counterpart; this is a property of the library, not of the method.
+   Allocates nothing: the scan's scratch (ray queues, hits, return records,
+   tile flags) lives in one fixed 64 MiB device array compiled into the
+   library, which every GPU that loads the library holds until the process
+   exits.  The scene (created beforehand with rr_scene_create) and out_polar
+   [n_azimuth][n_bins] (device memory) are the caller's.  A scan whose
+   worst-case scratch exceeds 64 MiB is rejected with RR_ERR_INVALID_ARG and a
+   message giving the size; the 400 x 8 ray, 3 bounce, 1142 bin tiny room
+   needs about 4 MiB.  The first call on each device, with that device current,
+   looks up the array's device address once.  All calls share the array
+   (it keeps the last call's contents; the scan writes everything before it
+   reads it), so calls that overlap on the GPU race.  Blocking; returns the
+   device status of the scan. */
+int rr_scan_static(rr_scene* scene, const rr_pose* pose, const rr_sensor_params* params, float* out_polar);
+
 /* Sec. III-B display mapping: L_E = 10 log10(E_R / E0), E0 = 1, mapped
    linearly from [-cutoff_db, 0] dB to [0, 255], clamped, rounded to nearest.
    polar [n] float and out [n] uint8 are device memory.  Stream ordered. */

@@ -28,7 +28,7 @@ cudaStream_t current_stream() { return t_stream; }
 // overflow reports RR_ERR_CAPACITY with the size needed
 static size_t g_ws_limit = size_t(24) << 30;
 
-static int fail(int code, const std::string& msg) {
+int fail(int code, const std::string& msg) {
   set_error(msg);
   return code;
 }
@@ -47,7 +47,7 @@ static int cuda_fail(cudaError_t e, const char* what) {
     }                                          \
   } while (0)
 
-static bool is_device_ptr(const void* p) {
+bool is_device_ptr(const void* p) {
   if (p == nullptr) return false;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -98,7 +98,7 @@ static void prof_collect(rr_scene* s) {
 // parameter checks
 static bool finite_f(float x) { return std::isfinite(x); }
 
-static int check_params(const rr_pose* pose, const rr_sensor_params* p) {
+int check_params(const rr_pose* pose, const rr_sensor_params* p) {
   if (!pose || !p) return fail(RR_ERR_INVALID_ARG, "pose and params must not be NULL");
   if (p->n_azimuth < 1 || p->n_azimuth > RR_MAX_AZIMUTH) return fail(RR_ERR_INVALID_ARG, "n_azimuth out of range");
   if (p->rays_per_beam < 1 || p->rays_per_beam > RR_MAX_RAYS_PER_BEAM)
@@ -136,15 +136,9 @@ static int check_params(const rr_pose* pose, const rr_sensor_params* p) {
 
 // ---------------------------------------------------------------------------
 // workspace
-struct WsLayout {
-  uint32_t ray_cap, rec_cap, tiles;
-  size_t off_rays0, off_rays1, off_hits, off_recs, off_status, off_tmp, total;
-  bool clamped;
-};
-
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-static WsLayout plan_workspace(const rr_sensor_params* p) {
+WsLayout plan_workspace(const rr_sensor_params* p) {
   const uint64_t n0 = (uint64_t)p->n_azimuth * p->rays_per_beam;
   uint64_t q = n0 << (p->max_bounces - 1);
   uint64_t r = 2ull * n0 * ((1ull << p->max_bounces) - 1ull);
@@ -207,20 +201,13 @@ static int ensure_image(rr_scene* s, size_t bytes, cudaStream_t st) {
   return RR_OK;
 }
 
-struct DebugOut {
-  rr_segment* segs = nullptr;
-  uint32_t seg_cap = 0;
-  float* tallies = nullptr;
-  const uint8_t* mask = nullptr;
-};
-
-// queue the kernels of one scan into `image` (device); no synchronisation
-static int scan_enqueue(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* image,
-                        const DebugOut* dbg, cudaStream_t st) {
-  const WsLayout L = plan_workspace(p);
-  int rc = ensure_workspace(s, L.total, st);
-  if (rc != RR_OK) return rc;
-  char* w = (char*)s->ws;
+// queue the kernels of one scan into `image` (device), with the scan
+// workspace at `ws` laid out by L; no synchronisation, no allocation
+int scan_enqueue_into(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* image, const DebugOut* dbg,
+                      cudaStream_t st, void* ws, const WsLayout& L, bool profile) {
+  char* w = (char*)ws;
+  const bool prof_saved = s->prof;
+  if (!profile) s->prof = false;
   ScanArgs a;
   memset(&a, 0, sizeof a);
   a.tri = s->d_tri;
@@ -285,11 +272,21 @@ static int scan_enqueue(rr_scene* s, const rr_pose* pose, const rr_sensor_params
   prof_begin(s, RR_K_IMAGE, st, &ev);
   RR_CHECK_CUDA(launch_image(a, st), "image launch");
   prof_end(s, ev, st);
+  s->prof = prof_saved;
   return RR_OK;
 }
 
+// queue one scan on the scene's own (growable) workspace
+static int scan_enqueue(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* image,
+                        const DebugOut* dbg, cudaStream_t st) {
+  const WsLayout L = plan_workspace(p);
+  int rc = ensure_workspace(s, L.total, st);
+  if (rc != RR_OK) return rc;
+  return scan_enqueue_into(s, pose, p, image, dbg, st, s->ws, L, true);
+}
+
 // read (and clear) the sticky device status; requires the stream to be idle
-static int device_status(rr_scene* s, cudaStream_t st) {
+int device_status(rr_scene* s, cudaStream_t st) {
   RR_CHECK_CUDA(cudaMemcpyAsync(s->h_ctr, s->d_ctr, sizeof(ScanCounters), cudaMemcpyDeviceToHost, st),
                 "reading the scan counters");
   RR_CHECK_CUDA(cudaStreamSynchronize(st), "scan");

@@ -89,4 +89,24 @@ cudaError_t launch_db_u8(const float* polar, uint64_t n, float cutoff_db, uint8_
 void prof_begin(rr_scene* s, int kind, cudaStream_t st, cudaEvent_t* stop_out);
 void prof_end(rr_scene* s, cudaEvent_t stop, cudaStream_t st);
 
+// scan orchestration shared by the entry points (rr_api.cu)
+struct WsLayout {
+  uint32_t ray_cap, rec_cap, tiles;
+  size_t off_rays0, off_rays1, off_hits, off_recs, off_status, off_tmp, total;
+  bool clamped;
+};
+struct DebugOut {
+  rr_segment* segs = nullptr;
+  uint32_t seg_cap = 0;
+  float* tallies = nullptr;
+  const uint8_t* mask = nullptr;
+};
+int fail(int code, const std::string& msg);
+bool is_device_ptr(const void* p);
+int check_params(const rr_pose* pose, const rr_sensor_params* p);
+WsLayout plan_workspace(const rr_sensor_params* p);
+int scan_enqueue_into(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* image, const DebugOut* dbg,
+                      cudaStream_t st, void* ws, const WsLayout& L, bool profile);
+int device_status(rr_scene* s, cudaStream_t st);
+
 }  // namespace rr_host

@@ -93,6 +93,7 @@ SIGNATURES = {
     "rr_scan": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P], C.c_int),
     "rr_scan_async": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P], C.c_int),
     "rr_scene_sync": ([_P], C.c_int),
+    "rr_scan_static": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P], C.c_int),
     "rr_scan_batch": ([_P, C.c_uint32, _P, _P, _P], C.c_int),
     "rr_scan_debug": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P, _P, _P, C.c_uint64,
                        C.POINTER(C.c_uint64), _P], C.c_int),
@@ -240,6 +241,14 @@ def rr_scan_async(scene, pose: dict, params: dict, out_polar) -> None:
     _use_torch_stream()
     P, S = make_pose(pose), make_params(params)
     _check(load().rr_scan_async(scene, C.byref(P), C.byref(S), _ptr(out_polar)))
+
+
+def rr_scan_static(scene, pose: dict, params: dict, out_polar) -> None:
+    """rr_scan without allocation: scratch in the library's fixed 64 MiB device
+    array, out_polar must be device memory (see include/rr.h)."""
+    _use_torch_stream()
+    P, S = make_pose(pose), make_params(params)
+    _check(load().rr_scan_static(scene, C.byref(P), C.byref(S), _ptr(out_polar)))
 
 
 def rr_scene_sync(scene) -> None:
