@@ -130,7 +130,7 @@ def traffic_from_profiles():
     """Per-launch DRAM bytes of the trace kernel from the committed ncu summary,
     valid only while the kernel source matches the hash it was taken on."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "trace_kernel_campus_ncu.json")
+    p = os.path.join(ROOT, "profiles", "trace_kernel_campus_ncu.txt")
     src = os.path.join(ROOT, "paper_2310_03505_gb300", "csrc", "rr_trace.cu")
     if not (os.path.exists(p) and os.path.exists(src)):
         return None

@@ -118,15 +118,17 @@ typedef struct {
    0 reflected / 1 refracted at intersection i), bounce index, original
    triangle id hit (RR_NO_HIT on a miss or beyond the range limit), hit
    distance (+inf on a miss), the energy entering the segment, and at the hit
-   cos theta0 (incidence, >= 0) and the energies of the traveled-path and
-   air-path returns (0 on a miss). */
+   cos theta0 (incidence, >= 0), the energies of the traveled-path and
+   air-path returns (0 on a miss), and the number of BVH nodes the query
+   visited. */
 typedef struct {
   uint32_t az, k, path, bounce;
   uint32_t tri;
   float t;
   float E;
   uint32_t flags; /* bit 0: an air-path visibility test ran, bit 1: the sensor was visible */
-  float cos_i, ret_t, ret_a, reserved;
+  float cos_i, ret_t, ret_a;
+  float visits; /* BVH nodes the closest-hit query visited (diagnostics) */
 } rr_segment;
 
 typedef struct {

@@ -151,7 +151,8 @@ __device__ __forceinline__ float woop_hit(const WoopRay& w, float3 v0, float3 v1
 // Returns the leaf index or kNone.
 template <bool kAny, bool kCount>
 __device__ __forceinline__ uint32_t traverse(const ScanArgs& a, float3 o, float3 d, float t_min, float& t_best,
-                                             uint32_t skip, uint32_t& n_nodes, uint32_t& n_tris) {
+                                             uint32_t skip, uint32_t& n_nodes, uint32_t& n_tris,
+                                             uint32_t& visits) {
   const uint32_t nt = a.n_tris;
   if (nt == 0) return kNone;
   const WoopRay w = make_woop(o, d);
@@ -165,6 +166,7 @@ __device__ __forceinline__ uint32_t traverse(const ScanArgs& a, float3 o, float3
   while (true) {
     if (!(node & kLeafBit)) {
       if (kCount) ++n_nodes;
+      ++visits;
       const float4* np = a.nodes + 4 * (size_t)node;
       const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
       // child 0
@@ -257,12 +259,13 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(ScanArgs a, uint32_t boun
     const uint32_t medium = ray.meta.w;
     const float n_cur = medium == kAir ? 1.0f : __ldg(&a.mats[medium].n);
     float t = (r_lim - ray.o_L.w) / n_cur;   // past it no return can reach the image
-    const uint32_t leaf = traverse<false, kCount>(a, o, d, a.t_min, t, ray.meta.x, n_nodes, n_tris);
+    uint32_t visits = 0;
+    const uint32_t leaf = traverse<false, kCount>(a, o, d, a.t_min, t, ray.meta.x, n_nodes, n_tris, visits);
     ++n_closest;
     HitRec h;
     h.t = leaf == kNone ? INFINITY : t;
     h.leaf = leaf;
-    h.flags = 0u;
+    h.flags = min(visits, 0xFFFFFFu) << 8;   // bits 8..31: node visits (diagnostics)
     h.wa_g = 0.0f;
     if (want_air && leaf != kNone) {
       const float4* tp = a.tri + 3 * (size_t)leaf;
@@ -300,9 +303,11 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(ScanArgs a, uint32_t boun
                                      angle_between(dir_out, v), a.beam_width);
         if (wa > 0.0f) {
           float t_s = dist;
-          const uint32_t occ = traverse<true, kCount>(a, p, (1.0f / dist) * v, a.t_min, t_s, leaf, n_nodes, n_tris);
+          uint32_t vis_visits = 0;
+          const uint32_t occ =
+              traverse<true, kCount>(a, p, (1.0f / dist) * v, a.t_min, t_s, leaf, n_nodes, n_tris, vis_visits);
           ++n_any;
-          h.flags = 1u;
+          h.flags |= 1u;
           if (occ == kNone) {
             h.flags |= 2u;
             const float delta = angle_between(p - a.pos, beam_axis(a, ray.meta.y >> 16));
@@ -557,11 +562,11 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
           sg.tri = orig;
           sg.t = h.leaf == kNone ? INFINITY : h.t;
           sg.E = E;
-          sg.flags = h.flags;
+          sg.flags = h.flags & 0xFFu;
           sg.cos_i = dbg_cos;
           sg.ret_t = dbg_ret_t;
           sg.ret_a = dbg_ret_a;
-          sg.reserved = 0.f;
+          sg.visits = (float)(h.flags >> 8);   // node visits of the closest-hit query
           a.segs[si] = sg;
         } else {
           atomicOr(&a.ctr->error, kErrCapacitySegs);

@@ -55,12 +55,12 @@ class rr_sensor_params(C.Structure):
 class rr_segment(C.Structure):
     _fields_ = [("az", C.c_uint32), ("k", C.c_uint32), ("path", C.c_uint32), ("bounce", C.c_uint32),
                 ("tri", C.c_uint32), ("t", C.c_float), ("E", C.c_float), ("flags", C.c_uint32),
-                ("cos_i", C.c_float), ("ret_t", C.c_float), ("ret_a", C.c_float), ("reserved", C.c_float)]
+                ("cos_i", C.c_float), ("ret_t", C.c_float), ("ret_a", C.c_float), ("visits", C.c_float)]
 
 
 SEGMENT_DTYPE = np.dtype([("az", "<u4"), ("k", "<u4"), ("path", "<u4"), ("bounce", "<u4"), ("tri", "<u4"),
                           ("t", "<f4"), ("E", "<f4"), ("flags", "<u4"), ("cos_i", "<f4"), ("ret_t", "<f4"),
-                          ("ret_a", "<f4"), ("reserved", "<f4")])
+                          ("ret_a", "<f4"), ("visits", "<f4")])
 
 
 class rr_scene_info(C.Structure):

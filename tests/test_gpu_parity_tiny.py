@@ -93,7 +93,14 @@ def test_tiny_determinism(tiny_scene):
     sc, pz, params, h = tiny_scene
     a, sa, ta = P.gpu_debug(h, pz, params)
     b, sb, tb = P.gpu_debug(h, pz, params)
-    assert np.array_equal(sa, sb)          # same rays, same order, same hits
+    # segments are appended in completion order: compare them sorted by ray, bounce and branch
+    key = lambda x: np.lexsort((x["path"], x["bounce"], x["k"], x["az"]))
+    sa, sb = sa[key(sa)], sb[key(sb)]
+    # same rays, same hits, same energies; the node-visit count is a
+    # diagnostic that depends on which rays share a warp
+    for f in sa.dtype.names:
+        if f != "visits":
+            assert np.array_equal(sa[f], sb[f]), f
     assert np.max(np.abs(a - b)) <= 1e-6 * a.max()
 
 
