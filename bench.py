@@ -27,6 +27,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -250,8 +251,8 @@ def main():
     rr.rr_profile_enable(h, True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in step_ids]
     ends = [torch.cuda.Event(enable_timing=True) for _ in step_ids]
-    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                                              else "_work", f"clocks_rank{rank}.csv")) if rank == 0 else None
+    clock_csv = os.environ.get("RR_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(), f"rr_clocks_rank{rank}.csv")
+    clocks = ClockSampler(local, clock_csv) if rank == 0 else None
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
