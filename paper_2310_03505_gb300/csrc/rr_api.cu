@@ -321,7 +321,6 @@ using namespace rr_host;
 __global__ void k_fold_build_status(const uint32_t* misc, ScanCounters* ctr) {
   uint32_t e = 0;
   if (misc[6]) e |= rr::kErrBadVertex;
-  if (misc[7] > (uint32_t)rr::kStack) e |= rr::kErrStack;
   if (e) atomicOr(&ctr->error, e);
 }
 
@@ -420,7 +419,7 @@ int rr_scene_create(const float* vertices, uint32_t n_vertices, const uint32_t* 
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-  if (e == cudaSuccess) e = build_lbvh(s, st);
+  if (e == cudaSuccess) e = build_lbvh(s, st, true);
   if (e == cudaSuccess) e = cudaEventRecord(e1, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -457,7 +456,7 @@ int rr_scene_update_vertices(rr_scene* s, const float* vertices) {
     RR_CHECK_CUDA(cudaMemcpyAsync(s->d_vtx, vertices, (size_t)s->nv * 3 * sizeof(float), cudaMemcpyDefault, st),
                   "copying the vertices");
   prof_begin(s, RR_K_BUILD, st, &ev);
-  RR_CHECK_CUDA(build_lbvh(s, st), "rebuilding the BVH");
+  RR_CHECK_CUDA(build_lbvh(s, st, false), "rebuilding the BVH");
   prof_end(s, ev, st);
   if (s->nt) {
     s->launches += 1;

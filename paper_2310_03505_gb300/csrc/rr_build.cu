@@ -17,6 +17,7 @@
 // with a child reference i for internal node i and j | 0x80000000 for leaf j.
 // Leaves are the triangles in sorted order: tri[3j..3j+2] = v0, v1, v2 with
 // v0.w = original triangle id, v1.w = material id (bit patterns).
+#include <cuda/atomic>
 #include <cuda_runtime.h>
 
 #include "rr_host.h"
@@ -138,36 +139,54 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n, int 
   hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of n counters with one block of 1024 threads
+// exclusive scan of n counters (n a multiple of 4, 16-byte aligned) with one
+// block: chunks of blockDim x 4 counters, one coalesced uint4 per thread,
+// carried from chunk to chunk
 __global__ void k_scan_single(uint32_t* __restrict__ data, uint32_t n) {
   __shared__ uint32_t s_warp[32];
-  const uint32_t t = threadIdx.x, seg = (n + blockDim.x - 1) / blockDim.x;
-  const uint32_t start = min(t * seg, n), end = min(start + seg, n);
-  uint32_t sum = 0;
-  for (uint32_t i = start; i < end; ++i) sum += data[i];
-  // block exclusive scan of the per-thread sums
-  const int lane = t & 31, warp = t >> 5;
-  uint32_t x = sum;
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
-    if (lane >= off) x += y;
-  }
-  if (lane == 31) s_warp[warp] = x;
+  __shared__ uint32_t s_carry;
+  const uint32_t t = threadIdx.x;
+  const int lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  if (t == 0) s_carry = 0u;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t w = s_warp[lane];
+  uint4* d4 = reinterpret_cast<uint4*>(data);
+  const uint32_t n4 = n / 4u;
+  for (uint32_t base = 0; base < n4; base += blockDim.x) {
+    const uint32_t i = base + t;
+    uint4 v = i < n4 ? d4[i] : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t sum = v.x + v.y + v.z + v.w;
+    uint32_t x = sum;
     for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, off);
-      if (lane >= off) w += y;
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+      if (lane >= off) x += y;
     }
-    s_warp[lane] = w;
-  }
-  __syncthreads();
-  uint32_t run = x - sum + (warp > 0 ? s_warp[warp - 1] : 0u);
-  for (uint32_t i = start; i < end; ++i) {
-    const uint32_t v = data[i];
-    data[i] = run;
-    run += v;
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = lane < nw ? s_warp[lane] : 0u;
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, off);
+        if (lane >= off) w += y;
+      }
+      s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t carry = s_carry;
+    uint32_t run = carry + x - sum + (warp > 0 ? s_warp[warp - 1] : 0u);
+    if (i < n4) {
+      uint4 o;
+      o.x = run;
+      run += v.x;
+      o.y = run;
+      run += v.y;
+      o.z = run;
+      run += v.z;
+      o.w = run;
+      d4[i] = o;
+    }
+    __syncthreads();
+    if (t == 0) s_carry = carry + s_warp[nw - 1];
+    __syncthreads();
   }
 }
 
@@ -290,9 +309,9 @@ __global__ void k_refit(uint32_t n, const uint32_t* __restrict__ child, const ui
   if (j >= n) return;
   uint32_t p = parent[n - 1 + j];
   while (p != kNone) {
-    __threadfence();
-    if (atomicAdd(&visit[p], 1u) == 0u) return;
-    __threadfence();
+    // acquire-release: the second arrival sees the first one's box
+    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> cnt(visit[p]);
+    if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == 0u) return;
     const uint32_t c0 = child[2 * p], c1 = child[2 * p + 1];
     const float* b0p = nbox + 6 * (size_t)node_slot(c0, n);
     const float* b1p = nbox + 6 * (size_t)node_slot(c1, n);
@@ -442,7 +461,7 @@ cudaError_t build_materials(rr_scene* s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t build_lbvh(rr_scene* s, cudaStream_t st) {
+cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth) {
   const uint32_t n = s->nt;
   if (n == 0) return cudaSuccess;
   // bounds reset: min slots to all ones, max slots, error and depth to zero
@@ -450,7 +469,7 @@ cudaError_t build_lbvh(rr_scene* s, cudaStream_t st) {
   RR_TRY(cudaMemsetAsync(s->d_misc + 3, 0, 5 * sizeof(uint32_t), st));
   const int B = 256;
   const uint32_t g = (n + B - 1) / B;
-  s->launches += (n > 1) ? 18u : 15u;
+  s->launches += (n > 1) ? (with_depth ? 18u : 17u) : 15u;
   k_ingest<<<g, B, 0, st>>>(s->d_vtx, s->d_idx, s->d_mat_id, s->nv, n, s->nm, s->d_centroid, s->d_misc);
   RR_TRY(cudaGetLastError());
   k_morton<<<g, B, 0, st>>>(s->d_centroid, s->d_misc, n, s->d_keys[0], s->d_vals[0]);
@@ -476,8 +495,12 @@ cudaError_t build_lbvh(rr_scene* s, cudaStream_t st) {
     RR_TRY(cudaGetLastError());
     k_refit<<<g, B, 0, st>>>(n, s->d_child, s->d_parent, s->d_visit, s->d_nbox, s->d_nodes);
     RR_TRY(cudaGetLastError());
-    k_depth<<<g, B, 0, st>>>(n, s->d_parent, s->d_misc);
-    RR_TRY(cudaGetLastError());
+    if (with_depth) {
+      // the stack bound is checked once at creation; on rebuilds the
+      // traversal's own stack check reports a deeper tree
+      k_depth<<<g, B, 0, st>>>(n, s->d_parent, s->d_misc);
+      RR_TRY(cudaGetLastError());
+    }
   } else {
     RR_TRY(cudaMemsetAsync(s->d_parent, 0xFF, sizeof(uint32_t), st));
   }

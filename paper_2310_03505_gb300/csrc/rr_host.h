@@ -69,7 +69,7 @@ namespace rr_host {
 
 // rr_build.cu
 cudaError_t build_alloc(rr_scene* s);
-cudaError_t build_lbvh(rr_scene* s, cudaStream_t st);   // a1..a5 on s->d_vtx; counts its launches
+cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth);   // a1..a5 on s->d_vtx; counts its launches
 cudaError_t build_materials(rr_scene* s, cudaStream_t st);
 
 // rr_trace.cu
