@@ -226,11 +226,73 @@ int rr_scan_async(rr_scene* scene, const rr_pose* pose, const rr_sensor_params* 
    device status of the scans and rebuilds since the previous sync. */
 int rr_scene_sync(rr_scene* scene);
 
-/* n scans of one scene: poses [n], params [n], out [n] pointers to images
-   (host or device, each [params[i].n_azimuth][params[i].n_bins]).
-   Blocking. */
+/* n scans of one scene, each with its own pose and sensor model (ray counts,
+   bounce limits, bins and flags may all differ): poses [n], params [n],
+   out [n] pointers to images (host or device, each
+   [params[i].n_azimuth][params[i].n_bins]).  The scans are traced together:
+   consecutive scans whose worst-case ray trees fit the workspace limit
+   (rr_batch_config) share one launch sequence -- ray generation, the
+   trace/shade wavefront of every bounce and the image pass -- so small scans
+   fill the GPU together.  Each image equals the scan run alone up to the
+   rounding of the float sums (the order in which returns are added to a bin
+   is not fixed).  Blocking; returns the device status of the batch. */
 int rr_scan_batch(rr_scene* scene, uint32_t n, const rr_pose* poses, const rr_sensor_params* params,
                   float* const* out);
+
+/* Same, non-blocking: every out[i] must be device memory; returns once the
+   work is queued.  Device-side errors are reported by rr_scene_sync. */
+int rr_scan_batch_async(rr_scene* scene, uint32_t n, const rr_pose* poses, const rr_sensor_params* params,
+                        float* const* out);
+
+/* Launch parameters of the batched path (per scene).  The paper has no
+   counterpart; they trade memory and occupancy for throughput only and never
+   change a result beyond float summation order.
+   wavefront_rays       most initial rays traced in one launch sequence
+                        (0: as many as the workspace limit allows)
+   trace_block          threads per block of the trace kernel: 64, 128 or 256
+   trace_blocks_per_sm  resident trace blocks per SM (0: the occupancy maximum)
+   use_graph            1: each launch sequence is captured once in a CUDA
+                        graph and replayed while its arguments stay the same
+   workspace_limit      bytes of scan workspace; a launch sequence is sized
+                        for its worst-case ray tree (every hit spawning both
+                        children) within this limit (0: 24 GiB) */
+typedef struct {
+  uint32_t wavefront_rays;
+  uint32_t trace_block;
+  uint32_t trace_blocks_per_sm;
+  uint32_t use_graph;
+  uint64_t workspace_limit;
+} rr_batch_config;
+
+int rr_batch_config_get(const rr_scene* scene, rr_batch_config* out);
+/* RR_ERR_INVALID_ARG for a trace_block other than 64/128/256, more than 64
+   blocks per SM, use_graph > 1 or a workspace limit below 1 MiB. */
+int rr_batch_config_set(rr_scene* scene, const rr_batch_config* config);
+
+/* How rr_scan_batch would cut scans params[0..n) into launch sequences under
+   config (NULL: the defaults), computed on the host only (no device work,
+   usable without a GPU).  first [cap] receives the index of each sequence's
+   first scan (a sequence runs to the next one's first scan), *n_groups the
+   number of sequences (only min(cap, *n_groups) entries are written) and
+   *max_workspace the workspace bytes of the largest sequence.  A sequence
+   holds at most 65535 scans, 2^18 azimuth columns, 2^30 initial rays and
+   fewer than 2^32 pixels of beam-pattern images,
+   at most wavefront_rays initial rays and a worst-case workspace within
+   workspace_limit, except a single scan, which is sized down to the limit
+   (and may then report RR_ERR_CAPACITY when it runs). */
+int rr_batch_plan(uint32_t n, const rr_sensor_params* params, const rr_batch_config* config, uint32_t* first,
+                  uint32_t cap, uint32_t* n_groups, uint64_t* max_workspace);
+
+/* Autotuner: runs the batch (poses, params as for rr_scan_batch, images kept
+   on the device and discarded) under a sequence of launch configurations --
+   wavefront size, then trace block size, then trace blocks per SM, then
+   graph replay, keeping the best of each -- each timed with CUDA events as
+   the mean of reps passes after one warm-up pass.  Sets the fastest on the
+   scene and returns it in *best (may be NULL) with its time in *best_ms and
+   the time of the configuration it started from in *start_ms (each may be
+   NULL).  Blocking; allocates the images of one pass. */
+int rr_autotune(rr_scene* scene, uint32_t n, const rr_pose* poses, const rr_sensor_params* params, uint32_t reps,
+                rr_batch_config* best, float* best_ms, float* start_ms);
 
 /* Debug scan: like rr_scan, plus
    ray_mask  [n_azimuth * rays_per_beam] uint8 or NULL; initial rays with a

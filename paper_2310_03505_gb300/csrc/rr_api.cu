@@ -1,4 +1,5 @@
-// rr_api.cu -- the extern "C" boundary declared in include/rr.h.
+// rr_api.cu -- the extern "C" boundary declared in include/rr.h (scene,
+// single scans, debug, counters; batches are in rr_batch.cu).
 //
 // Host code here validates arguments, owns device memory and orders the
 // launches; every step of the scan itself runs in the kernels of
@@ -24,16 +25,12 @@ static thread_local cudaStream_t t_stream = nullptr;
 void set_error(const std::string& msg) { t_error = msg; }
 cudaStream_t current_stream() { return t_stream; }
 
-// scan workspace limit (bytes); beyond it the queues are clamped and an
-// overflow reports RR_ERR_CAPACITY with the size needed
-static size_t g_ws_limit = size_t(24) << 30;
-
 int fail(int code, const std::string& msg) {
   set_error(msg);
   return code;
 }
 
-static int cuda_fail(cudaError_t e, const char* what) {
+int cuda_fail(cudaError_t e, const char* what) {
   return fail(e == cudaErrorMemoryAllocation ? RR_ERR_OOM : RR_ERR_CUDA,
               std::string(what) + ": " + cudaGetErrorString(e));
 }
@@ -134,157 +131,6 @@ int check_params(const rr_pose* pose, const rr_sensor_params* p) {
   return RR_OK;
 }
 
-// ---------------------------------------------------------------------------
-// workspace
-static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-WsLayout plan_workspace(const rr_sensor_params* p) {
-  const uint64_t n0 = (uint64_t)p->n_azimuth * p->rays_per_beam;
-  uint64_t q = n0 << (p->max_bounces - 1);
-  uint64_t r = 2ull * n0 * ((1ull << p->max_bounces) - 1ull);
-  const uint64_t cap30 = 1ull << 30;
-  if (q > cap30) q = cap30;
-  if (r > (cap30 << 1)) r = cap30 << 1;
-  if (q < n0) q = n0;
-  auto bytes = [&](uint64_t qq, uint64_t rr_) {
-    const uint64_t tiles = (qq + 255) / 256 + 1;
-    return align256(qq * sizeof(rr::RayRec)) * 2 + align256(qq * sizeof(rr::HitRec)) + align256(rr_ * 8) +
-           align256(tiles * 8) + align256((uint64_t)p->n_azimuth * p->n_bins * 4);
-  };
-  WsLayout L;
-  L.clamped = false;
-  if (bytes(q, r) > g_ws_limit) {
-    const double f = (double)g_ws_limit / (double)bytes(q, r);
-    q = std::max<uint64_t>(n0, (uint64_t)(q * f));
-    r = std::max<uint64_t>(2 * n0, (uint64_t)(r * f));
-    L.clamped = true;
-  }
-  L.ray_cap = (uint32_t)q;
-  L.rec_cap = (uint32_t)std::min<uint64_t>(r, 0xFFFFFFFFull);
-  L.tiles = (uint32_t)((q + 255) / 256 + 1);
-  size_t off = 0;
-  L.off_rays0 = off;
-  off += align256((size_t)q * sizeof(rr::RayRec));
-  L.off_rays1 = off;
-  off += align256((size_t)q * sizeof(rr::RayRec));
-  L.off_hits = off;
-  off += align256((size_t)q * sizeof(rr::HitRec));
-  L.off_recs = off;
-  off += align256((size_t)L.rec_cap * 8);
-  L.off_status = off;
-  off += align256((size_t)L.tiles * 8);
-  L.off_tmp = off;
-  off += align256((size_t)p->n_azimuth * p->n_bins * 4);
-  L.total = off;
-  return L;
-}
-
-static int ensure_workspace(rr_scene* s, size_t bytes, cudaStream_t st) {
-  if (s->ws_bytes >= bytes) return RR_OK;
-  RR_CHECK_CUDA(cudaStreamSynchronize(st), "synchronising before growing the workspace");
-  if (s->ws) cudaFree(s->ws);
-  s->ws = nullptr;
-  s->ws_bytes = 0;
-  RR_CHECK_CUDA(cudaMalloc(&s->ws, bytes), "allocating the scan workspace");
-  s->ws_bytes = bytes;
-  return RR_OK;
-}
-
-static int ensure_image(rr_scene* s, size_t bytes, cudaStream_t st) {
-  if (s->image_bytes >= bytes) return RR_OK;
-  RR_CHECK_CUDA(cudaStreamSynchronize(st), "synchronising before growing the image buffer");
-  if (s->d_image) cudaFree(s->d_image);
-  s->d_image = nullptr;
-  s->image_bytes = 0;
-  RR_CHECK_CUDA(cudaMalloc(&s->d_image, bytes), "allocating the image buffer");
-  s->image_bytes = bytes;
-  return RR_OK;
-}
-
-// queue the kernels of one scan into `image` (device), with the scan
-// workspace at `ws` laid out by L; no synchronisation, no allocation
-int scan_enqueue_into(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* image, const DebugOut* dbg,
-                      cudaStream_t st, void* ws, const WsLayout& L, bool profile) {
-  char* w = (char*)ws;
-  const bool prof_saved = s->prof;
-  if (!profile) s->prof = false;
-  ScanArgs a;
-  memset(&a, 0, sizeof a);
-  a.tri = s->d_tri;
-  a.nodes = s->d_nodes;
-  a.mats = s->d_mats;
-  a.lut = s->d_lut;
-  a.n_tris = s->nt;
-  a.rays[0] = (rr::RayRec*)(w + L.off_rays0);
-  a.rays[1] = (rr::RayRec*)(w + L.off_rays1);
-  a.hits = (rr::HitRec*)(w + L.off_hits);
-  a.recs = (uint2*)(w + L.off_recs);
-  a.tile_status = (unsigned long long*)(w + L.off_status);
-  a.ctr = s->d_ctr;
-  a.image = image;
-  a.image_tmp = (float*)(w + L.off_tmp);
-  a.ray_cap = L.ray_cap;
-  a.rec_cap = L.rec_cap;
-  if (dbg) {
-    a.segs = dbg->segs;
-    a.seg_cap = dbg->seg_cap;
-    a.tallies = dbg->tallies;
-    a.mask = dbg->mask;
-  }
-  a.pos = make_float3(pose->p[0], pose->p[1], pose->p[2]);
-  const float qn = 1.0f / std::sqrt(pose->q[0] * pose->q[0] + pose->q[1] * pose->q[1] + pose->q[2] * pose->q[2] +
-                                    pose->q[3] * pose->q[3]);
-  a.quat = make_float4(pose->q[0] * qn, pose->q[1] * qn, pose->q[2] * qn, pose->q[3] * qn);
-  a.n_az = p->n_azimuth;
-  a.ns = p->rays_per_beam;
-  a.max_bounces = p->max_bounces;
-  a.n_bins = p->n_bins;
-  a.beam_width = p->beam_width_rad;
-  a.beam_prob = p->beam_prob;
-  a.elevation = p->elevation_rad;
-  a.bin_size = p->bin_size_m;
-  a.t_min = p->t_min_m;
-  a.min_energy = p->min_energy;
-  a.freq = p->freq_hz;
-  a.blur_sigma = p->blur_sigma_bins;
-  a.az_sigma = p->az_pattern_sigma;
-  a.noise_sys = p->noise_sys;
-  a.noise_amb = p->noise_amb;
-  a.flags = p->flags;
-  a.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFu);
-  a.seed_hi = (uint32_t)(p->seed >> 32);
-  a.scan_id = p->scan_id;
-  a.r_max = (float)p->n_bins * p->bin_size_m;
-
-  s->launches += 2u + 2u * p->max_bounces + (p->az_pattern_sigma > 0.f ? 1u : 0u);
-  cudaEvent_t ev;
-  prof_begin(s, RR_K_RAYGEN, st, &ev);
-  RR_CHECK_CUDA(launch_raygen(a, st), "raygen launch");
-  prof_end(s, ev, st);
-  for (uint32_t b = 0; b < p->max_bounces; ++b) {
-    prof_begin(s, RR_K_TRACE, st, &ev);
-    RR_CHECK_CUDA(launch_trace(a, b, st), "trace launch");
-    prof_end(s, ev, st);
-    prof_begin(s, RR_K_SHADE, st, &ev);
-    RR_CHECK_CUDA(launch_shade(a, b, st), "shade launch");
-    prof_end(s, ev, st);
-  }
-  prof_begin(s, RR_K_IMAGE, st, &ev);
-  RR_CHECK_CUDA(launch_image(a, st), "image launch");
-  prof_end(s, ev, st);
-  s->prof = prof_saved;
-  return RR_OK;
-}
-
-// queue one scan on the scene's own (growable) workspace
-static int scan_enqueue(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* image,
-                        const DebugOut* dbg, cudaStream_t st) {
-  const WsLayout L = plan_workspace(p);
-  int rc = ensure_workspace(s, L.total, st);
-  if (rc != RR_OK) return rc;
-  return scan_enqueue_into(s, pose, p, image, dbg, st, s->ws, L, true);
-}
-
 // read (and clear) the sticky device status; requires the stream to be idle
 int device_status(rr_scene* s, cudaStream_t st) {
   RR_CHECK_CUDA(cudaMemcpyAsync(s->h_ctr, s->d_ctr, sizeof(ScanCounters), cudaMemcpyDeviceToHost, st),
@@ -345,6 +191,10 @@ int rr_scene_destroy(rr_scene* s) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->h_ctr) cudaFreeHost(s->h_ctr);
+  if (s->h_stage) cudaFreeHost(s->h_stage);
+  if (s->stage_ev) cudaEventDestroy(s->stage_ev);
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   for (auto& ev : s->prof_pending) {
     cudaEventDestroy(ev.start);
     cudaEventDestroy(ev.stop);
@@ -507,7 +357,8 @@ int rr_scan_async(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, f
   int rc = check_params(pose, p);
   if (rc != RR_OK) return rc;
   if (!is_device_ptr(out_polar)) return fail(RR_ERR_INVALID_ARG, "rr_scan_async needs a device output");
-  return scan_enqueue(s, pose, p, out_polar, nullptr, t_stream);
+  float* const images[1] = {out_polar};
+  return batch_run(s, pose, p, images, 1, nullptr, t_stream);
 }
 
 int rr_scene_sync(rr_scene* s) {
@@ -528,38 +379,11 @@ int rr_scan(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* 
     if (rc != RR_OK) return rc;
     target = s->d_image;
   }
-  rc = scan_enqueue(s, pose, p, target, nullptr, st);
+  float* const images[1] = {target};
+  rc = batch_run(s, pose, p, images, 1, nullptr, st);
   if (rc != RR_OK) return rc;
   if (!dev)
     RR_CHECK_CUDA(cudaMemcpyAsync(out_polar, target, img_bytes, cudaMemcpyDeviceToHost, st), "copying the image");
-  return device_status(s, st);
-}
-
-int rr_scan_batch(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor_params* params, float* const* out) {
-  if (!s || (n && (!poses || !params || !out))) return fail(RR_ERR_INVALID_ARG, "NULL argument");
-  for (uint32_t i = 0; i < n; ++i) {
-    int rc = check_params(&poses[i], &params[i]);
-    if (rc != RR_OK) return rc;
-    if (!out[i]) return fail(RR_ERR_INVALID_ARG, "NULL output");
-  }
-  cudaStream_t st = t_stream;
-  for (uint32_t i = 0; i < n; ++i) {
-    const size_t img_bytes = (size_t)params[i].n_azimuth * params[i].n_bins * sizeof(float);
-    const bool dev = is_device_ptr(out[i]);
-    float* target = out[i];
-    int rc;
-    if (!dev) {
-      rc = ensure_image(s, img_bytes, st);
-      if (rc != RR_OK) return rc;
-      target = s->d_image;
-    }
-    rc = scan_enqueue(s, &poses[i], &params[i], target, nullptr, st);
-    if (rc != RR_OK) return rc;
-    if (!dev) {
-      RR_CHECK_CUDA(cudaMemcpyAsync(out[i], target, img_bytes, cudaMemcpyDeviceToHost, st), "copying the image");
-      RR_CHECK_CUDA(cudaStreamSynchronize(st), "batch");
-    }
-  }
   return device_status(s, st);
 }
 
@@ -606,7 +430,8 @@ int rr_scan_debug(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, c
   dbg.seg_cap = d_segs ? (uint32_t)seg_capacity : 0u;
   dbg.tallies = d_tal;
   dbg.mask = d_mask;
-  rc = scan_enqueue(s, pose, p, d_img, &dbg, st);
+  float* const images[1] = {d_img};
+  rc = batch_run(s, pose, p, images, 1, &dbg, st);
   if (rc != RR_OK) {
     cleanup();
     return rc;

@@ -20,6 +20,15 @@ struct ProfEvent {
   cudaEvent_t start, stop;
 };
 
+// tunables of the batched launch sequence (rr_batch_config)
+struct LaunchCfg {
+  uint32_t wavefront_rays = 0;        // most initial rays per launch sequence, 0: workspace limit only
+  uint32_t trace_block = 128;         // 64, 128 or 256
+  uint32_t trace_blocks_per_sm = 0;   // 0: occupancy maximum
+  uint32_t use_graph = 1;             // capture each launch sequence once and replay it
+  uint64_t ws_limit = uint64_t(24) << 30;
+};
+
 }  // namespace rr_host
 
 struct rr_scene {
@@ -56,6 +65,16 @@ struct rr_scene {
   rr::ScanCounters* h_ctr = nullptr;   // pinned mirror
   float* d_image = nullptr;            // internal image for host outputs
   size_t image_bytes = 0;
+  // batched path
+  rr_host::LaunchCfg cfg;
+  void* h_stage = nullptr;             // pinned staging of the scan descriptors
+  size_t stage_bytes = 0;
+  cudaEvent_t stage_ev = nullptr;      // the last upload from h_stage has been read
+  bool stage_used = false;
+  cudaStream_t cap_stream = nullptr;   // stream used only to capture graphs
+  cudaGraphExec_t gexec = nullptr;     // last captured launch sequence
+  std::vector<unsigned char> gkey;     // what gexec was captured for
+  uint32_t gnodes = 0;
   // profiling
   bool prof = false;
   std::vector<rr_host::ProfEvent> prof_pending;
@@ -73,26 +92,26 @@ cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth);   // a1..
 cudaError_t build_materials(rr_scene* s, cudaStream_t st);
 
 // rr_trace.cu
-struct LaunchDims {
-  int trace_grid, trace_block, shade_grid, shade_block;
-};
-LaunchDims trace_dims();
+int num_sms();
+int trace_max_blocks_per_sm(uint32_t block);
 cudaError_t launch_raygen(const rr::ScanArgs& a, cudaStream_t st);
-cudaError_t launch_trace(const rr::ScanArgs& a, uint32_t bounce, cudaStream_t st);
+cudaError_t launch_trace(const rr::ScanArgs& a, uint32_t bounce, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_shade(const rr::ScanArgs& a, uint32_t bounce, cudaStream_t st);
 
 // rr_image.cu
-cudaError_t launch_image(const rr::ScanArgs& a, cudaStream_t st);
+void init_image_attrs();
+cudaError_t launch_image(const rr::ScanArgs& a, bool pattern, cudaStream_t st);
 cudaError_t launch_db_u8(const float* polar, uint64_t n, float cutoff_db, uint8_t* out, cudaStream_t st);
 
 // profiling helpers (rr_api.cu)
 void prof_begin(rr_scene* s, int kind, cudaStream_t st, cudaEvent_t* stop_out);
 void prof_end(rr_scene* s, cudaEvent_t stop, cudaStream_t st);
 
-// scan orchestration shared by the entry points (rr_api.cu)
+// scan orchestration shared by the entry points (rr_batch.cu)
 struct WsLayout {
-  uint32_t ray_cap, rec_cap, tiles;
-  size_t off_rays0, off_rays1, off_hits, off_recs, off_status, off_tmp, total;
+  uint32_t ray_cap, rec_cap, tiles, n_desc;
+  size_t off_rays0, off_rays1, off_hits, off_recs, off_status, off_tmp, off_desc, total;
+  size_t tmp_floats;
   bool clamped;
 };
 struct DebugOut {
@@ -101,12 +120,31 @@ struct DebugOut {
   float* tallies = nullptr;
   const uint8_t* mask = nullptr;
 };
+// one launch sequence: scans [first, first + count) of a request
+struct Group {
+  uint32_t first = 0, count = 0;
+  WsLayout L;
+};
 int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
 bool is_device_ptr(const void* p);
 int check_params(const rr_pose* pose, const rr_sensor_params* p);
-WsLayout plan_workspace(const rr_sensor_params* p);
-int scan_enqueue_into(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* image, const DebugOut* dbg,
-                      cudaStream_t st, void* ws, const WsLayout& L, bool profile);
+// worst-case workspace of scans ps[0..n) traced together, clamped to limit
+WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit);
+// split n scans into launch sequences that respect the limits of cfg
+std::vector<Group> plan_groups(const rr_sensor_params* ps, uint32_t n, const LaunchCfg& cfg);
+// queue the launch sequence of scans poses/ps[0..n) writing images[i]
+// (device); the workspace at ws is laid out by L.  host_desc: where the
+// descriptors are staged (NULL: the scene's pinned staging).  No allocation
+// unless allow_graph.
+int batch_enqueue(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps, float* const* images, uint32_t n,
+                  const DebugOut* dbg, cudaStream_t st, void* ws, const WsLayout& L, bool profile, bool allow_graph,
+                  const LaunchCfg& cfg, void* host_desc);
+int ensure_workspace(rr_scene* s, size_t bytes, cudaStream_t st);
+int ensure_image(rr_scene* s, size_t bytes, cudaStream_t st);
 int device_status(rr_scene* s, cudaStream_t st);
+// whole request on the scene's workspace: images[i] device pointers
+int batch_run(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps, float* const* images, uint32_t n,
+              const DebugOut* dbg, cudaStream_t st);
 
 }  // namespace rr_host

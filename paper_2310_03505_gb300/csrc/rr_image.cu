@@ -5,7 +5,8 @@
 // noise as a Gaussian blur along range, a beam pattern across azimuths,
 // additive uniform system and ambient noise.
 //
-// One CTA owns one azimuth column: it finds the column's records in every
+// One CTA owns one image column (one azimuth of one scan of the batch; the
+// batch's columns are numbered scan by scan): it finds the column's records in every
 // bounce's record list (each list is in azimuth order, so two binary
 // searches per bounce), accumulates them into a shared-memory histogram with
 // warp-aggregated adds (lanes that hit the same bin are summed with shuffles
@@ -40,27 +41,33 @@ __device__ __forceinline__ int gauss_taps(float sigma, float* w) {
   return R;
 }
 
-__device__ __forceinline__ uint32_t lower_az(const uint2* __restrict__ recs, uint32_t lo, uint32_t hi, uint32_t az) {
+// first record in [lo, hi) whose column is >= col (records are in column order)
+__device__ __forceinline__ uint32_t lower_col(const uint2* __restrict__ recs, uint32_t lo, uint32_t hi, uint32_t col) {
   while (lo < hi) {
     const uint32_t mid = lo + ((hi - lo) >> 1);
-    if ((__ldg(&recs[mid].x) >> 16) < az) lo = mid + 1;
+    if ((__ldg(&recs[mid].x) >> kBinBits) < col) lo = mid + 1;
     else hi = mid;
   }
   return lo;
 }
 
-__device__ __forceinline__ float noise_at(const ScanArgs& a, uint32_t az, uint32_t bin) {
-  return a.noise_sys * u01(draw(a, az, bin, 2u).x) + a.noise_amb * u01(draw(a, az, bin, 3u).x);
+// Sec. III-C: uniform system and ambient noise of one pixel
+__device__ __forceinline__ float noise_at(uint4 rng, float4 post, uint32_t az, uint32_t bin) {
+  return post.z * u01(draw(rng, az, bin, 2u).x) + post.w * u01(draw(rng, az, bin, 3u).x);
 }
 
 __global__ void __launch_bounds__(kImgBlock) k_bin_column(ScanArgs a) {
   extern __shared__ float sm[];
   float* hist = sm;                     // [n_bins]
-  float* col = sm + a.n_bins;           // [n_bins]
+  float* col = sm + a.max_bins;         // [n_bins]
   __shared__ float taps[kMaxTaps];
   __shared__ uint32_t s_rng[2 * RR_MAX_BOUNCES];
-  const uint32_t az = blockIdx.x;
-  const uint32_t nb = a.n_bins;
+  const uint32_t c = blockIdx.x;
+  const uint32_t scan = owner_of(a.col0, a.n_scans, c);
+  const ScanDesc* sd = a.desc + scan;
+  const uint32_t az = c - __ldg(&a.col0[scan]);
+  const uint32_t nb = __ldg(&sd->dims.w);
+  const float4 post = __ldg(&sd->post);   // blur sigma, pattern sigma, noise_sys, noise_amb
   const int lane = threadIdx.x & 31;
   for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0.0f;
   // record range of this column in every bounce's list: lane 2b / 2b+1
@@ -68,7 +75,7 @@ __global__ void __launch_bounds__(kImgBlock) k_bin_column(ScanArgs a) {
     const uint32_t b = (uint32_t)lane >> 1;
     if (b < a.max_bounces) {
       const uint32_t lo = a.ctr->rec_start[b], hi = a.ctr->rec_start[b + 1];
-      s_rng[lane] = lower_az(a.recs, lo, hi, az + (lane & 1));
+      s_rng[lane] = lower_col(a.recs, lo, hi, c + (lane & 1));
     }
   }
   __syncthreads();
@@ -82,7 +89,7 @@ __global__ void __launch_bounds__(kImgBlock) k_bin_column(ScanArgs a) {
       float e = 0.0f;
       if (valid) {
         const uint2 rc = __ldg(&a.recs[r]);
-        bin = rc.x & 0xFFFFu;
+        bin = rc.x & kBinMask;
         e = __uint_as_float(rc.y);
         valid = bin < nb;   // records always carry bin < n_bins; a failed scan may leave stale slots
       }
@@ -95,8 +102,8 @@ __global__ void __launch_bounds__(kImgBlock) k_bin_column(ScanArgs a) {
   }
   __syncthreads();
   const float* src = hist;
-  if (a.blur_sigma > 0.0f) {
-    const int R = gauss_taps(a.blur_sigma, taps);
+  if (post.x > 0.0f) {
+    const int R = gauss_taps(post.x, taps);
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
       float acc = 0.0f;
       for (int j = -R; j <= R; ++j) {
@@ -108,31 +115,42 @@ __global__ void __launch_bounds__(kImgBlock) k_bin_column(ScanArgs a) {
     __syncthreads();
     src = col;
   }
-  if (a.az_sigma > 0.0f) {
-    float* out = a.image_tmp + (size_t)az * nb;
+  if (post.y > 0.0f) {
+    float* out = a.image_tmp + __ldg(&sd->offs.z) + (size_t)az * nb;
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) out[i] = src[i];
   } else {
-    float* out = a.image + (size_t)az * nb;
-    const bool noise = (a.flags & RR_NOISE) != 0u;
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) out[i] = src[i] + (noise ? noise_at(a, az, i) : 0.0f);
+    float* out = sd->image + (size_t)az * nb;
+    const uint4 rng = __ldg(&sd->rng);
+    const bool noise = (rng.w & RR_NOISE) != 0u;
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
+      out[i] = src[i] + (noise ? noise_at(rng, post, az, i) : 0.0f);
   }
 }
 
-// beam pattern across azimuths (circular), then noise
+// beam pattern across the azimuths of a scan (circular), then noise; one
+// block row per image column, scans without a pattern return at once
 __global__ void __launch_bounds__(kImgBlock) k_az_pattern(ScanArgs a) {
   __shared__ float taps[kMaxTaps];
-  const int R = gauss_taps(a.az_sigma, taps);
-  const uint32_t az = blockIdx.y;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_bins) return;
+  const uint32_t c = blockIdx.x;   // column on x: a batch may hold more than 65535
+  const uint32_t scan = owner_of(a.col0, a.n_scans, c);
+  const ScanDesc* sd = a.desc + scan;
+  const float4 post = __ldg(&sd->post);
+  if (!(post.y > 0.0f)) return;   // uniform over the block
+  const int R = gauss_taps(post.y, taps);
+  const uint32_t az = c - __ldg(&a.col0[scan]);
+  const uint32_t n_az = __ldg(&sd->dims.x), nb = __ldg(&sd->dims.w);
+  const uint32_t i = blockIdx.y * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  const float* tmp = a.image_tmp + __ldg(&sd->offs.z);
   float acc = 0.0f;
   for (int j = -R; j <= R; ++j) {
-    int s = ((int)az + j) % (int)a.n_az;
-    if (s < 0) s += (int)a.n_az;
-    acc += taps[j + R] * a.image_tmp[(size_t)s * a.n_bins + i];
+    int s = ((int)az + j) % (int)n_az;
+    if (s < 0) s += (int)n_az;
+    acc += taps[j + R] * tmp[(size_t)s * nb + i];
   }
-  if (a.flags & RR_NOISE) acc += noise_at(a, az, i);
-  a.image[(size_t)az * a.n_bins + i] = acc;
+  const uint4 rng = __ldg(&sd->rng);
+  if (rng.w & RR_NOISE) acc += noise_at(rng, post, az, i);
+  sd->image[(size_t)az * nb + i] = acc;
 }
 
 // Sec. III-B display mapping
@@ -151,19 +169,23 @@ namespace rr_host {
 
 using namespace rr;
 
-cudaError_t launch_image(const ScanArgs& a, cudaStream_t st) {
-  const size_t smem = 2 * (size_t)a.n_bins * sizeof(float);
+void init_image_attrs() {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_bin_column, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          2 * RR_MAX_BINS * (int)sizeof(float));
     attr_set = true;
   }
-  k_bin_column<<<a.n_az, kImgBlock, smem, st>>>(a);
+}
+
+cudaError_t launch_image(const ScanArgs& a, bool pattern, cudaStream_t st) {
+  init_image_attrs();
+  const size_t smem = 2 * (size_t)a.max_bins * sizeof(float);
+  k_bin_column<<<a.n_cols, kImgBlock, smem, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (a.az_sigma > 0.0f) {
-    dim3 grid((a.n_bins + kImgBlock - 1) / kImgBlock, a.n_az);
+  if (pattern) {
+    dim3 grid(a.n_cols, (a.max_bins + kImgBlock - 1) / kImgBlock);
     k_az_pattern<<<grid, kImgBlock, 0, st>>>(a);
     e = cudaGetLastError();
   }

@@ -43,7 +43,7 @@ struct __align__(16) RayRec {
   float4 o_L;   // origin, one-way optical path so far
   float4 d_E;   // unit direction, energy
   uint4 meta;   // x: prev leaf (sorted index) or kNone, y: az << 16 | k,
-                // z: path (bit 31: masked), w: medium material or kAir
+                // z: path (bit 31: masked), w: scan << 16 | (medium material or kAir)
 };
 
 // hit record, 16 bytes
@@ -68,38 +68,80 @@ struct ScanCounters {
   unsigned long long stat_nodes, stat_tris;
 };
 
-// per-scan constants (passed by value)
+// Return record key: global image column (scan's first column + azimuth)
+// and range bin.  Records of one bounce are in column order.
+constexpr int kBinBits = 14;                       // n_bins <= RR_MAX_BINS = 2^14
+constexpr uint32_t kBinMask = (1u << kBinBits) - 1u;
+constexpr uint32_t kMaxColumns = 1u << (32 - kBinBits);   // columns of one launch sequence
+constexpr uint32_t kMaxBatchScans = 0xFFFFu;       // scan index lives in 16 bits of RayRec.meta.w
+constexpr uint32_t kMediumMask = 0xFFFFu;
+
+// Per-scan constants of a batch (one pose and sensor model), 144 bytes.
+// Kernels read the fields of the scan each ray belongs to.
+struct __align__(16) ScanDesc {
+  float4 pos_rmax;   // sensor position, r_max = n_bins * bin_size
+  float4 quat;       // normalised (w, x, y, z), sensor to world
+  uint4 dims;        // n_az, ns, max_bounces, n_bins
+  float4 beam;       // beam_width b, beam_prob P, elevation, bin_size
+  float4 phys;       // t_min, min_energy, freq, r_lim (range limit of a closest-hit query)
+  float4 post;       // blur_sigma, az_sigma, noise_sys, noise_amb
+  uint4 rng;         // seed_lo, seed_hi, scan_id, flags
+  uint4 offs;        // first initial ray, first column, first float of image_tmp (or kNone), 0
+  float* image;      // [n_az][n_bins] output (device)
+  unsigned long long pad;
+};
+
+// Launch-sequence constants of one batch (passed by value)
 struct ScanArgs {
   // scene
   const float4* tri;         // [T][3] sorted: v0 (w: orig id bits), v1 (w: material bits), v2
   const float4* nodes;       // [T-1][4] Aila-Laine layout
   const MatDev* mats;
   const float4* lut;         // [M][kLutCells + 1]: (G(x_k), Gc(x_k), cos^C(x_k), 0)
-  uint32_t n_tris;
+  uint32_t n_tris, n_mats;
+  // batch
+  const ScanDesc* desc;      // [n_scans]
+  const uint32_t* ray0;      // [n_scans + 1] prefix of n_az * ns
+  const uint32_t* col0;      // [n_scans + 1] prefix of n_az
+  uint32_t n_scans, n_rays0, n_cols;
+  uint32_t max_bounces;      // over the batch
+  uint32_t max_bins;         // over the batch
+  uint32_t any_flags;        // union of the scans' flags
   // workspace
   RayRec* rays[2];
   HitRec* hits;
-  uint2* recs;               // (az << 16 | bin, energy bits)
+  uint2* recs;               // (column << kBinBits | bin, energy bits)
   unsigned long long* tile_status;
   ScanCounters* ctr;
-  float* image;              // [n_az][n_bins] output (device)
-  float* image_tmp;          // [n_az][n_bins] before the azimuth pattern (or null)
+  float* image_tmp;          // images before the azimuth pattern (or null)
   uint32_t ray_cap, rec_cap;
   // debug (may be null)
   rr_segment* segs;
   uint32_t seg_cap;
-  float* tallies;
-  const uint8_t* mask;
-  // sensor
-  float3 pos;
-  float4 quat;               // normalised (w, x, y, z)
-  uint32_t n_az, ns, max_bounces, n_bins;
-  float beam_width, beam_prob, elevation, bin_size, t_min, min_energy, freq;
-  float blur_sigma, az_sigma, noise_sys, noise_amb;
-  uint32_t flags;
-  uint32_t seed_lo, seed_hi, scan_id;
-  float r_max;               // n_bins * bin_size
+  float* tallies;            // [n_rays0][4]
+  const uint8_t* mask;       // [n_rays0]
 };
+
+// scan and medium of a queued ray; a slot left stale by a failed step (the
+// scan then reports an error) still maps to valid table entries
+__device__ __forceinline__ uint2 ray_scan_medium(const ScanArgs& a, uint32_t w) {
+  uint32_t scan = w >> 16, medium = w & kMediumMask;
+  if (scan >= a.n_scans) scan = 0;
+  if (medium != kAir && medium >= a.n_mats) medium = kAir;
+  return make_uint2(scan, medium);
+}
+
+// index of the scan owning item i of a prefix array p[0..n] (p[0] = 0,
+// non-decreasing, i < p[n]): the last s with p[s] <= i
+__device__ __forceinline__ uint32_t owner_of(const uint32_t* __restrict__ p, uint32_t n, uint32_t i) {
+  uint32_t lo = 0, hi = n;   // invariant: p[lo] <= i < p[hi]
+  while (hi - lo > 1u) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(&p[mid]) <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC 2011): counter (scan, a, b, c), key = seed
@@ -118,8 +160,9 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
 // uniform in (0,1) from the top 23 bits, (2 (x >> 9) + 1) / 2^24: exact in float
 __device__ __forceinline__ float u01(uint32_t x) { return (float)(2u * (x >> 9) + 1u) * 5.9604644775390625e-8f; }
 
-__device__ __forceinline__ uint4 draw(const ScanArgs& a, uint32_t w1, uint32_t w2, uint32_t w3) {
-  return philox(make_uint4(a.scan_id, w1, w2, w3), make_uint2(a.seed_lo, a.seed_hi));
+// draw of a scan whose rng words are (seed_lo, seed_hi, scan_id, flags)
+__device__ __forceinline__ uint4 draw(uint4 rng, uint32_t w1, uint32_t w2, uint32_t w3) {
+  return philox(make_uint4(rng.z, w1, w2, w3), make_uint2(rng.x, rng.y));
 }
 
 // ---------------------------------------------------------------------------

@@ -66,7 +66,7 @@ extern "C" int rr_scan_static(rr_scene* s, const rr_pose* pose, const rr_sensor_
   int rc = check_params(pose, p);
   if (rc != RR_OK) return rc;
   if (!is_device_ptr(out_polar)) return fail(RR_ERR_INVALID_ARG, "rr_scan_static needs a device output");
-  const WsLayout L = plan_workspace(p);
+  const WsLayout L = plan_workspace(p, 1, kStaticScratchBytes);
   if (L.total > kStaticScratchBytes || L.clamped)
     return fail(RR_ERR_INVALID_ARG, "rr_scan_static: this scan needs " + std::to_string(L.total) +
                                         " bytes of scratch, more than the fixed " +
@@ -75,7 +75,13 @@ extern "C" int rr_scan_static(rr_scene* s, const rr_pose* pose, const rr_sensor_
   rc = scratch_address(&scratch);
   if (rc != RR_OK) return rc;
   cudaStream_t st = current_stream();
-  rc = scan_enqueue_into(s, pose, p, out_polar, nullptr, st, scratch, L, false);
+  // the scan descriptor is staged from this stack buffer (a pageable copy
+  // returns once the source has been read), so nothing is allocated
+  alignas(16) unsigned char desc[sizeof(rr::ScanDesc) + 2 * 2 * sizeof(uint32_t)];
+  float* const images[1] = {out_polar};
+  LaunchCfg cfg = s->cfg;
+  cfg.use_graph = 0;
+  rc = batch_enqueue(s, pose, p, images, 1, nullptr, st, scratch, L, false, false, cfg, desc);
   if (rc != RR_OK) return rc;
   return device_status(s, st);
 }

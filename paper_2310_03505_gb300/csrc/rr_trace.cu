@@ -1,6 +1,9 @@
-// rr_trace.cu -- wavefront ray tracing of one polar scan.
+// rr_trace.cu -- wavefront ray tracing of a batch of polar scans.
 //
-// Per scan:  raygen -> { trace -> shade } x max_bounces -> image
+// Per batch: raygen -> { trace -> shade } x max_bounces -> image
+// A batch is one or more scans of the same scene, each with its own pose and
+// sensor model (ScanDesc); every ray carries the index of its scan, so scans
+// of uneven ray counts and bounce limits share every launch.
 //   raygen  Sec. III-A, Eq. 2: N_s rays per azimuth beam from the D3 cone.
 //   trace   closest hit through the LBVH (watertight ray/triangle test of
 //           Woop, Benthin, Wald, JCGT 2013) and, for multipath, the
@@ -14,7 +17,7 @@
 //           in (azimuth, ray) order.
 //
 // All kernels are persistent: the grid is a multiple of the SM count and
-// reads the queue length from device memory, so a whole scan is a fixed
+// reads the queue length from device memory, so a whole batch is a fixed
 // sequence of launches with no host round trip between bounces.
 #include <cuda_runtime.h>
 
@@ -22,7 +25,6 @@
 
 namespace rr {
 
-constexpr int kTraceBlock = 128;
 constexpr int kShadeBlock = 256;
 constexpr float kBoxInflate = 1.00000036f;  // 1 + 2 gamma_3 (robust slab test, Ize 2013)
 
@@ -42,22 +44,23 @@ __device__ __forceinline__ float2 beam_angle(uint32_t a, uint32_t n) {
   }
 }
 
-__device__ __forceinline__ float3 beam_axis(const ScanArgs& a, uint32_t az) {
-  const float2 cs = beam_angle(az, a.n_az);
+// world direction of beam az's axis for a scan
+__device__ __forceinline__ float3 beam_axis(const ScanDesc* sd, uint32_t az) {
+  const float2 cs = beam_angle(az, __ldg(&sd->dims.x));
   float se, ce;
-  sincosf(a.elevation, &se, &ce);
-  return qrot(a.quat, make_float3(ce * cs.x, ce * cs.y, se));
+  sincosf(__ldg(&sd->beam.z), &se, &ce);
+  return qrot(__ldg(&sd->quat), make_float3(ce * cs.x, ce * cs.y, se));
 }
 
-__device__ __forceinline__ float d3_sigma(const ScanArgs& a) {
-  return a.beam_width > 0.0f ? 0.5f * a.beam_width / (1.41421356237309515f * erfinvf(a.beam_prob)) : 0.0f;
+// Eq. 2: sigma = (b / 2) / (sqrt(2) erfinv(P))
+__device__ __forceinline__ float d3_sigma(float b, float P) {
+  return b > 0.0f ? 0.5f * b / (1.41421356237309515f * erfinvf(P)) : 0.0f;
 }
 
 // ---------------------------------------------------------------------------
-// raygen: ray (az, k) of the D3 cone, energy 1 / N_s
+// raygen: ray (az, k) of the D3 cone of its scan, energy 1 / N_s
 __global__ void k_raygen(ScanArgs a) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t n = a.n_az * a.ns;
   if (i == 0) {
     ScanCounters* c = a.ctr;
     for (int b = 0; b <= (int)RR_MAX_BOUNCES; ++b) {
@@ -69,30 +72,36 @@ __global__ void k_raygen(ScanArgs a) {
       c->trace_ticket[b] = 0;
       c->shade_ticket[b] = 0;
     }
-    c->count[0] = n;
-    c->stat_scans += 1ull;
+    c->count[0] = a.n_rays0;
+    c->stat_scans += (unsigned long long)a.n_scans;
   }
-  if (i >= n) return;
-  const uint32_t az = i / a.ns, k = i - az * a.ns;
-  const uint4 x = draw(a, az, k, 0u);
+  if (i >= a.n_rays0) return;
+  const uint32_t scan = owner_of(a.ray0, a.n_scans, i);
+  const ScanDesc* sd = a.desc + scan;
+  const uint32_t ns = __ldg(&sd->dims.y);
+  const uint32_t local = i - __ldg(&a.ray0[scan]);
+  const uint32_t az = local / ns, k = local - az * ns;
+  const float4 beam = __ldg(&sd->beam);
+  const uint4 x = draw(__ldg(&sd->rng), az, k, 0u);
   const float u0 = u01(x.x), u1 = u01(x.y), u2 = u01(x.z);
   const float gauss = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
-  const float r = d3_sigma(a) * gauss;
+  const float r = d3_sigma(beam.x, beam.y) * gauss;
   float sw, cw;
   sincospif(2.0f * u2 - 1.0f, &sw, &cw);      // omega = pi (2 u2 - 1)
   const float daz = r * cw, dinc = r * sw;
-  const float2 ph = beam_angle(az, a.n_az);
-  float sd, cd;
-  sincosf(daz, &sd, &cd);
-  const float ca = ph.x * cd - ph.y * sd, sa = ph.y * cd + ph.x * sd;   // cos, sin of phi + daz
+  const float2 ph = beam_angle(az, __ldg(&sd->dims.x));
+  float sd_, cd;
+  sincosf(daz, &sd_, &cd);
+  const float ca = ph.x * cd - ph.y * sd_, sa = ph.y * cd + ph.x * sd_;   // cos, sin of phi + daz
   float si, ci;
-  sincosf(a.elevation + dinc, &si, &ci);
-  const float3 d = normalize(qrot(a.quat, make_float3(ci * ca, ci * sa, si)));
+  sincosf(beam.z + dinc, &si, &ci);
+  const float3 d = normalize(qrot(__ldg(&sd->quat), make_float3(ci * ca, ci * sa, si)));
   const bool masked = a.mask != nullptr && a.mask[i] != 0;
+  const float4 pr = __ldg(&sd->pos_rmax);
   RayRec ray;
-  ray.o_L = make_float4(a.pos.x, a.pos.y, a.pos.z, 0.0f);
-  ray.d_E = make_float4(d.x, d.y, d.z, 1.0f / (float)a.ns);
-  ray.meta = make_uint4(kNone, (az << 16) | k, masked ? 0x80000000u : 0u, kAir);
+  ray.o_L = make_float4(pr.x, pr.y, pr.z, 0.0f);
+  ray.d_E = make_float4(d.x, d.y, d.z, 1.0f / (float)ns);
+  ray.meta = make_uint4(kNone, (az << 16) | k, masked ? 0x80000000u : 0u, (scan << 16) | kAir);
   a.rays[0][i] = ray;
 }
 
@@ -235,16 +244,13 @@ __device__ __forceinline__ uint32_t traverse(const ScanArgs& a, float3 o, float3
 // ---------------------------------------------------------------------------
 // trace: closest hit of every queued ray; multipath visibility of the
 // air-path return (Sec. III-A) for hits at bounce >= 1
-template <bool kCount>
-__global__ void __launch_bounds__(kTraceBlock) k_trace(ScanArgs a, uint32_t bounce) {
+template <bool kCount, int kBlock>
+__global__ void __launch_bounds__(kBlock) k_trace(ScanArgs a, uint32_t bounce) {
   const uint32_t n = a.ctr->count[bounce];
   const uint32_t tiles = (n + kShadeBlock - 1) / kShadeBlock;
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   for (uint32_t t = gtid; t < tiles; t += gsz) a.tile_status[t] = 0ull;
   const RayRec* __restrict__ q = a.rays[bounce & 1];
-  const float r_lim = (a.flags & RR_MULTIPATH) ? 2.0f * a.r_max : a.r_max;
-  const bool want_air = (a.flags & RR_MULTIPATH) && bounce >= 1;
-  const float sigma = d3_sigma(a);
   const int lane = threadIdx.x & 31;
   uint32_t n_closest = 0, n_any = 0, n_nodes = 0, n_tris = 0;
   while (true) {
@@ -256,18 +262,22 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(ScanArgs a, uint32_t boun
     if (i >= n) continue;
     const RayRec ray = q[i];
     const float3 o = f3(ray.o_L), d = f3(ray.d_E);
-    const uint32_t medium = ray.meta.w;
+    const uint2 sm = ray_scan_medium(a, ray.meta.w);
+    const uint32_t medium = sm.y;
+    const ScanDesc* sd = a.desc + sm.x;
+    const float4 phys = __ldg(&sd->phys);   // t_min, min_energy, freq, r_lim
+    const uint32_t flags = __ldg(&sd->rng.w);
     const float n_cur = medium == kAir ? 1.0f : __ldg(&a.mats[medium].n);
-    float t = (r_lim - ray.o_L.w) / n_cur;   // past it no return can reach the image
+    float t = (phys.w - ray.o_L.w) / n_cur;   // past it no return can reach the image
     uint32_t visits = 0;
-    const uint32_t leaf = traverse<false, kCount>(a, o, d, a.t_min, t, ray.meta.x, n_nodes, n_tris, visits);
+    const uint32_t leaf = traverse<false, kCount>(a, o, d, phys.x, t, ray.meta.x, n_nodes, n_tris, visits);
     ++n_closest;
     HitRec h;
     h.t = leaf == kNone ? INFINITY : t;
     h.leaf = leaf;
     h.flags = min(visits, 0xFFFFFFu) << 8;   // bits 8..31: node visits (diagnostics)
     h.wa_g = 0.0f;
-    if (want_air && leaf != kNone) {
+    if ((flags & RR_MULTIPATH) && bounce >= 1 && leaf != kNone) {
       const float4* tp = a.tri + 3 * (size_t)leaf;
       const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
       const MatDev m = a.mats[__float_as_uint(v1.w)];
@@ -281,7 +291,8 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(ScanArgs a, uint32_t boun
         n2 = 1.0f;
       }
       const float3 p = o + t * d;
-      const float3 v = a.pos - p;
+      const float3 s_pos = f3(__ldg(&sd->pos_rmax));
+      const float3 v = s_pos - p;
       const float dist = length(v);
       const float side = dot(v, nrm);
       float3 dir_out = make_float3(0.f, 0.f, 0.f);
@@ -299,18 +310,20 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(ScanArgs a, uint32_t boun
         }
       }
       if (cand) {
+        const float4 beam = __ldg(&sd->beam);
         const float wa = brdf_window(m, a.lut + (size_t)__float_as_uint(v1.w) * (kLutCells + 1),
-                                     angle_between(dir_out, v), a.beam_width);
+                                     angle_between(dir_out, v), beam.x);
         if (wa > 0.0f) {
           float t_s = dist;
           uint32_t vis_visits = 0;
           const uint32_t occ =
-              traverse<true, kCount>(a, p, (1.0f / dist) * v, a.t_min, t_s, leaf, n_nodes, n_tris, vis_visits);
+              traverse<true, kCount>(a, p, (1.0f / dist) * v, phys.x, t_s, leaf, n_nodes, n_tris, vis_visits);
           ++n_any;
           h.flags |= 1u;
           if (occ == kNone) {
             h.flags |= 2u;
-            const float delta = angle_between(p - a.pos, beam_axis(a, ray.meta.y >> 16));
+            const float sigma = d3_sigma(beam.x, beam.y);
+            const float delta = angle_between(p - s_pos, beam_axis(sd, ray.meta.y >> 16));
             const float g = sigma > 0.0f ? expf(-0.5f * (delta / sigma) * (delta / sigma)) : 0.0f;
             h.wa_g = wa * g;
           }
@@ -406,8 +419,6 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
   const RayRec* __restrict__ qin = a.rays[bounce & 1];
   RayRec* __restrict__ qout = a.rays[(bounce + 1) & 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float3 s_pos = a.pos;
-  const bool deeper = bounce + 1 < a.max_bounces;
   if (n == 0) {
     // empty queue: no tile will publish the offsets of the next bounce
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -432,7 +443,11 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
       const uint32_t az = ray.meta.y >> 16, k = ray.meta.y & 0xFFFFu;
       const uint32_t path = ray.meta.z & 0x7FFFFFFFu;
       const bool masked = (ray.meta.z >> 31) != 0u;
-      const uint32_t medium = ray.meta.w;
+      const uint2 sm = ray_scan_medium(a, ray.meta.w);
+      const uint32_t scan = sm.x, medium = sm.y;
+      const ScanDesc* sd = a.desc + scan;
+      const uint4 dims = __ldg(&sd->dims);   // n_az, ns, max_bounces, n_bins
+      const uint4 offs = __ldg(&sd->offs);   // first ray, first column
       const float E = ray.d_E.w;
       float tal[4] = {0.f, 0.f, 0.f, 0.f};
       float dbg_cos = 0.f, dbg_ret_t = 0.f, dbg_ret_a = 0.f;
@@ -441,13 +456,19 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
         tal[2] = E;   // escaped (or beyond the range limit)
       } else {
         const float3 o = f3(ray.o_L), d = f3(ray.d_E);
+        const float4 pr = __ldg(&sd->pos_rmax);
+        const float4 beam = __ldg(&sd->beam);   // b, P, elevation, bin_size
+        const float4 phys = __ldg(&sd->phys);   // t_min, min_energy, freq, r_lim
+        const uint4 rng = __ldg(&sd->rng);
+        const float3 s_pos = f3(pr);
+        const bool deeper = bounce + 1 < dims.z;
         const float t = h.t;
         const float3 p = o + t * d;
         const float n_cur = medium == kAir ? 1.0f : a.mats[medium].n;
         const float L1 = ray.o_L.w + n_cur * t;
         float E1 = E;
         if (medium != kAir) {
-          const float alpha = kPi * n_cur * a.mats[medium].tan_d * a.freq / kC0;
+          const float alpha = kPi * n_cur * a.mats[medium].tan_d * phys.z / kC0;
           E1 = E * expf(-2.0f * alpha * t);
           tal[1] = E - E1;
         }
@@ -485,7 +506,7 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
         const float3 d_refl = normalize(d + (2.0f * cos_i) * nrm);
         // traveled-path return: omega = theta0 + theta1 = 2 theta0, range L1
         const float theta0 = angle_between(d, -nrm);
-        const float ret_t = E1 * R * fminf(brdf_window(m, lut, 2.0f * theta0, a.beam_width), 1.0f);
+        const float ret_t = E1 * R * fminf(brdf_window(m, lut, 2.0f * theta0, beam.x), 1.0f);
         float ret_a = 0.0f, range_a = 0.0f;
         bool air_T = false;
         if (h.wa_g > 0.0f) {
@@ -507,28 +528,27 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
         dbg_ret_a = ret_a;
         if (!masked) {
           if (ret_t > 0.0f) {
-            const float bin = floorf(L1 / a.bin_size);
-            if (bin < (float)a.n_bins) {
+            const float bin = floorf(L1 / beam.w);
+            if (bin < (float)dims.w) {
               float e = ret_t;
-              if (a.flags & RR_SPECKLE) e *= -logf(u01(draw(a, az, k, 1u | (((path << 8) | bounce) << 8)).x));
-              rec[nr++] = make_uint2((az << 16) | (uint32_t)bin, __float_as_uint(e));
+              if (rng.w & RR_SPECKLE) e *= -logf(u01(draw(rng, az, k, 1u | (((path << 8) | bounce) << 8)).x));
+              rec[nr++] = make_uint2(((offs.y + az) << kBinBits) | (uint32_t)bin, __float_as_uint(e));
             }
           }
           if (ret_a > 0.0f) {
-            const float bin = floorf(range_a / a.bin_size);
-            if (bin < (float)a.n_bins) {
+            const float bin = floorf(range_a / beam.w);
+            if (bin < (float)dims.w) {
               float e = ret_a;
-              if (a.flags & RR_SPECKLE) e *= -logf(u01(draw(a, az, k, 1u | (((path << 8) | bounce) << 8)).y));
-              rec[nr++] = make_uint2((az << 16) | (uint32_t)bin, __float_as_uint(e));
+              if (rng.w & RR_SPECKLE) e *= -logf(u01(draw(rng, az, k, 1u | (((path << 8) | bounce) << 8)).y));
+              rec[nr++] = make_uint2(((offs.y + az) << kBinBits) | (uint32_t)bin, __float_as_uint(e));
             }
           }
         }
         const float e_refl = fmaxf(E1 * R - ret_t - (air_T ? 0.0f : ret_a), 0.0f);
         const float e_refr = fmaxf(E1 * T - (air_T ? ret_a : 0.0f), 0.0f);
-        const bool in_range = L1 < a.r_max;
-        const bool sp_refl = deeper && in_range && e_refl >= a.min_energy;
-        const bool sp_refr =
-            deeper && in_range && can_refract && (a.flags & RR_REFRACTION) && e_refr >= a.min_energy;
+        const bool in_range = L1 < pr.w;
+        const bool sp_refl = deeper && in_range && e_refl >= phys.y;
+        const bool sp_refr = deeper && in_range && can_refract && (rng.w & RR_REFRACTION) && e_refr >= phys.y;
         if (!sp_refl) tal[3] += e_refl;
         if (!sp_refr) tal[3] += e_refr;
         const uint32_t mbit = ray.meta.z & 0x80000000u;
@@ -536,18 +556,18 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
           RayRec& c = kid[nk++];
           c.o_L = make_float4(p.x, p.y, p.z, L1);
           c.d_E = make_float4(d_refl.x, d_refl.y, d_refl.z, e_refl);
-          c.meta = make_uint4(h.leaf, ray.meta.y, mbit | (path << 1), medium);
+          c.meta = make_uint4(h.leaf, ray.meta.y, mbit | (path << 1), (scan << 16) | medium);
         }
         if (sp_refr) {
           const float3 d_refr = normalize(eta * d + (eta * cos_i - cos_t) * nrm);
           RayRec& c = kid[nk++];
           c.o_L = make_float4(p.x, p.y, p.z, L1);
           c.d_E = make_float4(d_refr.x, d_refr.y, d_refr.z, e_refr);
-          c.meta = make_uint4(h.leaf, ray.meta.y, mbit | (path << 1) | 1u, next_med);
+          c.meta = make_uint4(h.leaf, ray.meta.y, mbit | (path << 1) | 1u, (scan << 16) | next_med);
         }
       }
       if (a.tallies != nullptr) {
-        float* tp = a.tallies + 4 * (size_t)(az * a.ns + k);
+        float* tp = a.tallies + 4 * ((size_t)offs.x + (size_t)az * dims.y + k);
         for (int q = 0; q < 4; ++q)
           if (tal[q] != 0.0f) atomicAdd(tp + q, tal[q]);
       }
@@ -619,7 +639,7 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
         atomicMax(&cn->need_recs, rend);
         rend = a.rec_cap;
       }
-      cn->count[bounce + 1] = deeper ? next : 0u;
+      cn->count[bounce + 1] = next;   // rays past their scan's bounce limit spawn no children
       cn->rec_start[bounce + 1] = rend;
       cn->seg_start[bounce + 1] = seg0 + n;
       cn->stat_returns += (unsigned long long)recs;
@@ -635,49 +655,71 @@ namespace rr_host {
 using namespace rr;
 
 static int g_num_sms = 0;
-static int g_trace_blocks_per_sm = 0;
-static int g_shade_blocks_per_sm = 0;
+static int g_trace_occ[2][3] = {{0}};   // [counting][block 64 / 128 / 256]
+static int g_shade_occ = 0;
 
-static void init_dims() {
-  if (g_num_sms) return;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_trace_blocks_per_sm, k_trace<false>, kTraceBlock, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_shade_blocks_per_sm, k_shade, kShadeBlock, 0);
-  if (g_trace_blocks_per_sm < 1) g_trace_blocks_per_sm = 1;
-  if (g_shade_blocks_per_sm < 1) g_shade_blocks_per_sm = 1;
-  if (g_num_sms < 1) g_num_sms = 1;
+static int block_index(uint32_t block) { return block <= 64u ? 0 : (block <= 128u ? 1 : 2); }
+
+template <bool kCount, int kBlock>
+static void occ_of(int* out) {
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_trace<kCount, kBlock>, kBlock, 0);
+  if (*out < 1) *out = 1;
 }
 
-LaunchDims trace_dims() {
+void init_dims() {
+  if (g_num_sms) return;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  occ_of<false, 64>(&g_trace_occ[0][0]);
+  occ_of<false, 128>(&g_trace_occ[0][1]);
+  occ_of<false, 256>(&g_trace_occ[0][2]);
+  occ_of<true, 64>(&g_trace_occ[1][0]);
+  occ_of<true, 128>(&g_trace_occ[1][1]);
+  occ_of<true, 256>(&g_trace_occ[1][2]);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_shade_occ, k_shade, kShadeBlock, 0);
+  if (g_shade_occ < 1) g_shade_occ = 1;
+  g_num_sms = sms < 1 ? 1 : sms;
+}
+
+int num_sms() {
   init_dims();
-  LaunchDims d;
-  d.trace_grid = g_num_sms * g_trace_blocks_per_sm;
-  d.trace_block = kTraceBlock;
-  d.shade_grid = g_num_sms * g_shade_blocks_per_sm;
-  d.shade_block = kShadeBlock;
-  return d;
+  return g_num_sms;
+}
+
+int trace_max_blocks_per_sm(uint32_t block) {
+  init_dims();
+  return g_trace_occ[0][block_index(block)];
 }
 
 cudaError_t launch_raygen(const ScanArgs& a, cudaStream_t st) {
-  const uint32_t n = a.n_az * a.ns;
-  k_raygen<<<(n + 255) / 256, 256, 0, st>>>(a);
+  const uint32_t n = a.n_rays0;
+  k_raygen<<<n ? (n + 255) / 256 : 1, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_trace(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
-  const LaunchDims d = trace_dims();
-  if (a.flags & RR_COUNT_TRAVERSAL)
-    k_trace<true><<<d.trace_grid, d.trace_block, 0, st>>>(a, bounce);
-  else
-    k_trace<false><<<d.trace_grid, d.trace_block, 0, st>>>(a, bounce);
+template <bool kCount>
+static void trace_launch(const ScanArgs& a, uint32_t bounce, int bi, int grid, cudaStream_t st) {
+  if (bi == 0) k_trace<kCount, 64><<<grid, 64, 0, st>>>(a, bounce);
+  else if (bi == 1) k_trace<kCount, 128><<<grid, 128, 0, st>>>(a, bounce);
+  else k_trace<kCount, 256><<<grid, 256, 0, st>>>(a, bounce);
+}
+
+cudaError_t launch_trace(const ScanArgs& a, uint32_t bounce, const LaunchCfg& c, cudaStream_t st) {
+  init_dims();
+  const bool count = (a.any_flags & RR_COUNT_TRAVERSAL) != 0u;
+  const int bi = block_index(c.trace_block);
+  int per_sm = g_trace_occ[count ? 1 : 0][bi];
+  if (c.trace_blocks_per_sm > 0 && (int)c.trace_blocks_per_sm < per_sm) per_sm = (int)c.trace_blocks_per_sm;
+  const int grid = g_num_sms * per_sm;
+  if (count) trace_launch<true>(a, bounce, bi, grid, st);
+  else trace_launch<false>(a, bounce, bi, grid, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_shade(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
-  const LaunchDims d = trace_dims();
-  k_shade<<<d.shade_grid, d.shade_block, 0, st>>>(a, bounce);
+  init_dims();
+  k_shade<<<g_num_sms * g_shade_occ, kShadeBlock, 0, st>>>(a, bounce);
   return cudaGetLastError();
 }
 

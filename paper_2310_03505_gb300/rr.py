@@ -79,6 +79,11 @@ class rr_profile(C.Structure):
     _fields_ = [("ms", C.c_double * RR_K_COUNT), ("launches", C.c_uint64 * RR_K_COUNT)]
 
 
+class rr_batch_config(C.Structure):
+    _fields_ = [("wavefront_rays", C.c_uint32), ("trace_block", C.c_uint32), ("trace_blocks_per_sm", C.c_uint32),
+                ("use_graph", C.c_uint32), ("workspace_limit", C.c_uint64)]
+
+
 # every symbol declared in include/rr.h with its ctypes signature
 _P = C.c_void_p
 SIGNATURES = {
@@ -95,6 +100,13 @@ SIGNATURES = {
     "rr_scene_sync": ([_P], C.c_int),
     "rr_scan_static": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P], C.c_int),
     "rr_scan_batch": ([_P, C.c_uint32, _P, _P, _P], C.c_int),
+    "rr_scan_batch_async": ([_P, C.c_uint32, _P, _P, _P], C.c_int),
+    "rr_batch_config_get": ([_P, C.POINTER(rr_batch_config)], C.c_int),
+    "rr_batch_config_set": ([_P, C.POINTER(rr_batch_config)], C.c_int),
+    "rr_batch_plan": ([C.c_uint32, _P, C.POINTER(rr_batch_config), _P, C.c_uint32, C.POINTER(C.c_uint32),
+                       C.POINTER(C.c_uint64)], C.c_int),
+    "rr_autotune": ([_P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(rr_batch_config), C.POINTER(C.c_float),
+                     C.POINTER(C.c_float)], C.c_int),
     "rr_scan_debug": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P, _P, _P, C.c_uint64,
                        C.POINTER(C.c_uint64), _P], C.c_int),
     "rr_polar_to_db_u8": ([_P, C.c_uint64, C.c_float, _P], C.c_int),
@@ -256,13 +268,74 @@ def rr_scene_sync(scene) -> None:
     _check(load().rr_scene_sync(scene))
 
 
-def rr_scan_batch(scene, poses, params, outs) -> None:
-    _use_torch_stream()
+def _batch_arrays(poses, params, outs=None):
     n = len(poses)
+    if len(params) != n or (outs is not None and len(outs) != n):
+        raise ValueError("poses, params and outputs must have the same length")
     P = (rr_pose * n)(*[make_pose(p) for p in poses])
     S = (rr_sensor_params * n)(*[make_params(s) for s in params])
-    O = (C.c_void_p * n)(*[_ptr(o) for o in outs])
+    O = (C.c_void_p * n)(*[_ptr(o) for o in outs]) if outs is not None else None
+    return n, P, S, O
+
+
+def rr_scan_batch(scene, poses, params, outs) -> None:
+    _use_torch_stream()
+    n, P, S, O = _batch_arrays(poses, params, outs)
     _check(load().rr_scan_batch(scene, n, C.cast(P, C.c_void_p), C.cast(S, C.c_void_p), C.cast(O, C.c_void_p)))
+
+
+def rr_scan_batch_async(scene, poses, params, outs) -> None:
+    """outs: device buffers; errors surface at rr_scene_sync."""
+    _use_torch_stream()
+    n, P, S, O = _batch_arrays(poses, params, outs)
+    _check(load().rr_scan_batch_async(scene, n, C.cast(P, C.c_void_p), C.cast(S, C.c_void_p),
+                                      C.cast(O, C.c_void_p)))
+
+
+def rr_batch_config_get(scene) -> dict:
+    c = rr_batch_config()
+    _check(load().rr_batch_config_get(scene, C.byref(c)))
+    return {k: getattr(c, k) for k, _ in rr_batch_config._fields_}
+
+
+def rr_batch_config_set(scene, **cfg) -> None:
+    """Keyword arguments override the scene's current configuration."""
+    cur = rr_batch_config_get(scene)
+    unknown = set(cfg) - set(cur)
+    if unknown:
+        raise ValueError(f"unknown batch config keys {sorted(unknown)}")
+    cur.update(cfg)
+    c = rr_batch_config(*[int(cur[k]) for k, _ in rr_batch_config._fields_])
+    _check(load().rr_batch_config_set(scene, C.byref(c)))
+
+
+def rr_batch_plan(params, config: dict | None = None):
+    """Host-only: (first scan of every launch sequence, largest workspace bytes)."""
+    n = len(params)
+    S = (rr_sensor_params * n)(*[make_params(s) for s in params])
+    cfg = None
+    if config is not None:
+        full = dict(wavefront_rays=0, trace_block=128, trace_blocks_per_sm=0, use_graph=1, workspace_limit=0)
+        full.update(config)
+        cfg = C.byref(rr_batch_config(*[int(full[k]) for k, _ in rr_batch_config._fields_]))
+    cap = max(n, 1)
+    first = np.zeros(cap, np.uint32)
+    ng, mx = C.c_uint32(), C.c_uint64()
+    _check(load().rr_batch_plan(n, C.cast(S, C.c_void_p), cfg, _ptr(first), cap, C.byref(ng), C.byref(mx)))
+    return first[: ng.value].copy(), mx.value
+
+
+def rr_autotune(scene, poses, params, reps: int = 2) -> dict:
+    """Returns the chosen configuration with 'best_ms' and 'start_ms'."""
+    _use_torch_stream()
+    n, P, S, _ = _batch_arrays(poses, params)
+    c = rr_batch_config()
+    best, start = C.c_float(), C.c_float()
+    _check(load().rr_autotune(scene, n, C.cast(P, C.c_void_p), C.cast(S, C.c_void_p), int(reps), C.byref(c),
+                              C.byref(best), C.byref(start)))
+    out = {k: getattr(c, k) for k, _ in rr_batch_config._fields_}
+    out.update(best_ms=best.value, start_ms=start.value)
+    return out
 
 
 def rr_scan_debug(scene, pose: dict, params: dict, out_polar, ray_mask=None, seg_capacity: int = 0,

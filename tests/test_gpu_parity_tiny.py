@@ -153,11 +153,29 @@ def test_invalid_params(tiny_scene):
 
 
 def test_capacity_error_reports_size(tiny_scene):
-    """A tiny workspace limit is not settable through the ABI; instead check
-    that a scan needing more segments than the debug buffer holds says so."""
+    """A workspace limit below the worst-case ray tree sizes the queues down;
+    a scan whose tree then outgrows them fails with RR_ERR_CAPACITY and says
+    how much it needed (the kernels drop what does not fit, nothing is
+    written out of bounds).  A debug scan with too small a segment buffer
+    fails the same way."""
     sc, pz, params, h = tiny_scene
     import torch
     out = torch.zeros(params["n_azimuth"], params["n_bins"], device="cuda")
     with pytest.raises(rr.RRError) as e:
         rr.rr_scan_debug(h, pz, params, out, seg_capacity=10)
     assert e.value.code == rr.RR_ERR_CAPACITY
+    saved = rr.rr_batch_config_get(h)
+    try:
+        # 64 rays per beam: the queues shrink to the 25,600 initial rays,
+        # while nearly every ray hits a dielectric wall of the closed room and
+        # spawns two children
+        rr.rr_batch_config_set(h, workspace_limit=1 << 20)
+        with pytest.raises(rr.RRError) as e:
+            rr.rr_scan(h, pz, {**params, "rays_per_beam": 64}, out)
+        assert e.value.code == rr.RR_ERR_CAPACITY
+        assert "were needed" in str(e.value)
+    finally:
+        rr.rr_batch_config_set(h, **saved)
+    # the scene stays usable
+    rr.rr_scan(h, pz, params, out)
+    assert float(out.max()) > 0
