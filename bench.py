@@ -163,6 +163,83 @@ def oracle_sample(sc, pz, params, budget_s: float = 12.0, min_cols: int = 2):
     return q_tot / t_tot / 1e6, cores, sample, q_tot, t_tot
 
 
+# ------------------------------------------------------------------ batched
+BATCHED_WORKLOAD = "campus_1M_tris_256_poses_random_walk_400_beams_32_512_rays_5_bounces_2000_bins"
+
+
+def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: int = 0):
+    """The batched workload: 256 poses along a random walk through a ~1M
+    triangle campus, rays per beam uneven per pose (32..512).  One step = the
+    256 scans through rr_scan_batch_async after the autotuner chose the launch
+    configuration (untimed), BVH resident (no rebuild); every step new scan
+    ids.  The same scans through the per-scan path (one rr_scan_async each,
+    default configuration) are timed beside it."""
+    import torch
+    from paper_2310_03505_gb300 import rr, scenes
+    sc, poses, params = scenes.config_batched()
+    h = rr.rr_scene_create(torch.from_numpy(sc.vertices).to(device), sc.triangles, sc.material_ids, sc.materials)
+    n = len(params)
+    outs = [torch.zeros(p["n_azimuth"], p["n_bins"], device=device) for p in params]
+    n0 = sum(p["n_azimuth"] * p["rays_per_beam"] for p in params)
+
+    def with_ids(step):
+        base = (rank * 1000 + step) * n
+        return [{**p, "scan_id": base + i} for i, p in enumerate(params)]
+
+    default_cfg = rr.rr_batch_config_get(h)
+    t0 = time.perf_counter()
+    tuned = rr.rr_autotune(h, poses, with_ids(999), reps=1)
+    tune_s = time.perf_counter() - t0
+    first, ws_bytes = rr.rr_batch_plan(params, {k: tuned[k] for k in default_cfg})
+
+    def timed(run, tag):
+        for w in range(warmup):
+            run(with_ids(100 + w))
+        rr.rr_scene_sync(h)
+        rr.rr_scene_stats(h, reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            run(with_ids(200 + i))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        status = rr.rr_scene_sync(h)
+        st = rr.rr_scene_stats(h, reset=True)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        tot = float(np.sum(ms))
+        return {"value": st["closest_queries"] / (tot * 1e-3) / 1e6, "unit": "Mrays/s",
+                "scans_per_s": steps * n / (tot * 1e-3), "ms_per_step": tot / steps,
+                "queries_per_step": st["closest_queries"] / steps,
+                "anyhit_per_step": st["anyhit_queries"] / steps,
+                "gpu_launches": int(st["kernel_launches"]), "status": "ok" if status is None else str(status)}
+
+    batched = timed(lambda ps: rr.rr_scan_batch_async(h, poses, ps, outs), "batched")
+    tuned_cfg = rr.rr_batch_config_get(h)
+    rr.rr_batch_config_set(h, **default_cfg)
+
+    def per_scan(ps):
+        for pz, p, o in zip(poses, ps, outs):
+            rr.rr_scan_async(h, pz, p, o)
+
+    single = timed(per_scan, "per_scan")
+    rr.rr_scene_destroy(h)
+    ns = [p["rays_per_beam"] for p in params]
+    return {
+        "workload": BATCHED_WORKLOAD, **batched,
+        "config": {"triangles": sc.n_triangles, "n_scans": n, "n_azimuth": 400,
+                   "rays_per_beam": {"min": int(min(ns)), "max": int(max(ns)), "mean": float(np.mean(ns))},
+                   "initial_rays_per_step": n0, "max_bounces": 5, "n_bins": 2000, "node_format": "fp32 2-wide",
+                   "step": "256 scans, resident BVH (no rebuild)",
+                   "l2": "flushed between steps (256 MiB write, outside the timed events)"},
+        "steps": steps, "warmup": warmup,
+        "launch_sequences": int(len(first)), "workspace_bytes": int(ws_bytes),
+        "autotune": {"chosen": tuned_cfg, "best_ms": tuned["best_ms"], "start_ms": tuned["start_ms"],
+                     "seconds": tune_s},
+        "per_scan_path": single, "speedup_vs_per_scan": batched["value"] / single["value"],
+    }
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -172,6 +249,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=3)
     args = ap.parse_args()
     world, rank, local = dist_env()
 
@@ -301,6 +380,10 @@ def main():
                "h2d_bytes_per_step": int(sc.vertices.nbytes + 28 + 80),
                "d2h_bytes_per_step": int(h_img.numel() * 4), "scans_per_s": world * args.steps / (e2e_ms * 1e-3)}
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_bench(device, stream, flush, steps=args.batched_steps, rank=rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample, _, _ = oracle_sample(sc, pz, params)
@@ -330,6 +413,7 @@ def main():
                          "algorithmic_bytes_per_query": bytes_per_closest,
                          "nodes_per_query": nodes_per_q, "tris_per_query": tris_per_q,
                          "trace_ms_per_launch": trace_ms / max(trace_launches, 1)},
+            "batched": batched,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["kernel_launches"]),
             "kernels_per_step": kernels_per_step, "clocks": clk, "wall_s_timed": wall,
             "status": "ok" if rc_status is None else str(rc_status),

@@ -71,6 +71,8 @@ class Scene:
     triangles: np.ndarray       # uint32  [T, 3]
     material_ids: np.ndarray    # uint16  [T]
     materials: list = field(default_factory=list)   # dicts, see material()
+    # axis-aligned boxes (lo, hi) of the solid objects, for placing sensors
+    obstacles: list = field(default_factory=list)
 
     @property
     def n_triangles(self) -> int:
@@ -285,7 +287,43 @@ def campus(seed: int = 0x5EED0001, target_tris: int = 200_000, n_buildings: int 
     g = max(1, int(round(math.sqrt(max(target_tris - others, 2) / 2.0))))
     mesh.quad_grid((-extent, -extent, 0.0), (2 * extent, 0, 0), (0, 2 * extent, 0), g, g, (0, 0, 1), idx["asphalt"])
     mats = [MATERIALS[n] for n in CAMPUS_MATS]
-    return mesh.build("campus", mats)
+    sc = mesh.build("campus", mats)
+    sc.obstacles = [(lo, hi) for lo, hi, _ in boxes] + list(cyl)
+    return sc
+
+
+def trajectory(sc: Scene, n: int, step: float = 0.25, seed: int = 0x5EED0003, height: float = 1.8,
+               turn_sigma_deg: float = 10.0, clearance: float = 1.0, extent: float = 140.0) -> list:
+    """Seeded random walk of n sensor poses, step metres apart: the heading
+    changes by N(0, turn_sigma) per step; a step that would come within
+    clearance of an obstacle's footprint or leave [-extent, extent]^2 is
+    redrawn with a fresh heading.  Starts at the origin (kept clear of
+    obstacles by the generators)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    foot = np.array([[lo[0], lo[1], hi[0], hi[1]] for lo, hi in sc.obstacles], np.float64).reshape(-1, 4)
+
+    def free(x, y):
+        if abs(x) > extent or abs(y) > extent:
+            return False
+        if not len(foot):
+            return True
+        inside = ((x > foot[:, 0] - clearance) & (x < foot[:, 2] + clearance) &
+                  (y > foot[:, 1] - clearance) & (y < foot[:, 3] + clearance))
+        return not bool(inside.any())
+
+    x, y = 0.0, 0.0
+    heading = float(rng.uniform(-math.pi, math.pi))
+    out = []
+    for _ in range(n):
+        out.append(pose(x, y, height, yaw=heading))
+        for attempt in range(1000):
+            h = heading + math.radians(turn_sigma_deg) * float(rng.standard_normal()) if attempt == 0 else \
+                float(rng.uniform(-math.pi, math.pi))
+            nx, ny = x + step * math.cos(h), y + step * math.sin(h)
+            if free(nx, ny):
+                x, y, heading = nx, ny, h
+                break
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -397,6 +435,21 @@ def config_medium(**kw):
     s = sensor(n_azimuth=400, rays_per_beam=200, max_bounces=5, n_bins=2000, bin_size=0.0438,
                beam_width=math.radians(10.0), **kw)
     return campus(), pose(0.0, 0.0, 1.8), s
+
+
+def config_batched(n_scans: int = 256, seed: int = 0x5EED0003, **kw):
+    """Batched scans: n_scans poses every 0.25 m along a seeded random walk
+    through a ~1M-triangle scene of the campus generator, 400 beams each with
+    rays per beam drawn uniformly from {32, ..., 512} per pose; otherwise the
+    medium sensor (<= 5 bounces, refraction on, 2000 bins to 87.6 m).
+    Returns (scene, poses, params)."""
+    sc = campus(target_tris=1_000_000)
+    poses = trajectory(sc, n_scans, step=0.25, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    ns = rng.integers(32, 513, size=n_scans)
+    params = [sensor(n_azimuth=400, rays_per_beam=int(ns[i]), max_bounces=5, n_bins=2000, bin_size=0.0438,
+                     beam_width=math.radians(10.0), scan_id=i, **kw) for i in range(n_scans)]
+    return sc, poses, params
 
 
 def config_large(**kw):
