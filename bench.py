@@ -229,7 +229,7 @@ def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: 
         "workload": BATCHED_WORKLOAD, **batched,
         "config": {"triangles": sc.n_triangles, "n_scans": n, "n_azimuth": 400,
                    "rays_per_beam": {"min": int(min(ns)), "max": int(max(ns)), "mean": float(np.mean(ns))},
-                   "initial_rays_per_step": n0, "max_bounces": 5, "n_bins": 2000, "node_format": "fp32 2-wide",
+                   "initial_rays_per_step": n0, "max_bounces": 5, "n_bins": 2000, "node_format": "wide8_q8" if tuned_cfg["node_format"] == rr.RR_NODES_WIDE8 else "binary_fp32",
                    "step": "256 scans, resident BVH (no rebuild)",
                    "l2": "flushed between steps (256 MiB write, outside the timed events)"},
         "steps": steps, "warmup": warmup,
@@ -250,6 +250,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--node-format", default="auto", choices=["auto", "wide", "binary"],
+                    help="BVH node format of the plain scan (auto: the library default)")
     ap.add_argument("--batched-steps", type=int, default=3)
     args = ap.parse_args()
     world, rank, local = dist_env()
@@ -302,6 +304,10 @@ def main():
 
     d_vtx = torch.from_numpy(sc.vertices).to(device)
     h = rr.rr_scene_create(d_vtx, sc.triangles, sc.material_ids, sc.materials)
+    if args.node_format != "auto":
+        rr.rr_batch_config_set(h, node_format=rr.RR_NODES_WIDE8 if args.node_format == "wide" else rr.RR_NODES_BINARY)
+    node_format = "wide8_q8" if rr.rr_batch_config_get(h)["node_format"] == rr.RR_NODES_WIDE8 else "binary_fp32"
+    node_bytes = rr.WIDE_NODE_BYTES if node_format == "wide8_q8" else NODE_BYTES
     info = rr.rr_scene_info_get(h)
     img = torch.zeros(params["n_azimuth"], params["n_bins"], device=device)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
@@ -319,11 +325,13 @@ def main():
     rr.rr_scene_stats(h, reset=True)
     rr.rr_scan(h, pz, {**params, "scan_id": 10 ** 6 + rank, "count_traversal": True}, img)
     cst = rr.rr_scene_stats(h, reset=True)
-    q_cal = cst["closest_queries"] + cst["anyhit_queries"]
-    nodes_per_q = cst["nodes_visited"] / max(q_cal, 1)
-    tris_per_q = cst["tris_tested"] / max(q_cal, 1)
-    any_per_closest = cst["anyhit_queries"] / max(cst["closest_queries"], 1)
-    bytes_per_closest = (1 + any_per_closest) * (nodes_per_q * NODE_BYTES + tris_per_q * TRI_BYTES) + RAY_IO_BYTES
+    # the dominant kernel is the closest-hit query: its algorithmic bytes are
+    # the nodes and triangles it fetches plus its ray and hit records
+    nodes_per_q = cst["nodes_visited"] / max(cst["closest_queries"], 1)
+    tris_per_q = cst["tris_tested"] / max(cst["closest_queries"], 1)
+    any_nodes_per_q = cst["anyhit_nodes_visited"] / max(cst["anyhit_queries"], 1)
+    any_tris_per_q = cst["anyhit_tris_tested"] / max(cst["anyhit_queries"], 1)
+    bytes_per_closest = nodes_per_q * node_bytes + tris_per_q * TRI_BYTES + RAY_IO_BYTES
 
     # timed region
     rr.rr_profile_read(h, reset=True)
@@ -397,7 +405,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "triangles": sc.n_triangles, "n_azimuth": params["n_azimuth"],
                        "rays_per_beam": params["rays_per_beam"], "max_bounces": params["max_bounces"],
-                       "n_bins": params["n_bins"], "step": "LBVH rebuild + polar scan",
+                       "n_bins": params["n_bins"], "node_format": node_format,
+                       "wide_nodes": info["n_wide_nodes"], "step": "LBVH rebuild + polar scan",
                        "l2": "flushed between steps (256 MiB write, outside the timed events)",
                        "parallelism": f"replicas x{world}"},
             "scans_per_s": scans_per_s,
@@ -407,12 +416,14 @@ def main():
             "anyhit_per_scan": st["anyhit_queries"] / args.steps,
             "bvh_build_ms_per_step": prof["build"][0] / max(prof["build"][1], 1),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-            "roofline": {"bound": "hbm", "kernel": "k_trace", "achieved": achieved_gbs, "peak": peak,
-                         "unit": "GB/s", "frac": (achieved_gbs / peak) if achieved_gbs else None,
+            "roofline": {"bound": "hbm", "kernel": "k_query (closest hit)", "achieved": achieved_gbs,
+                         "peak": peak, "unit": "GB/s", "frac": (achieved_gbs / peak) if achieved_gbs else None,
                          "traffic": traffic, "peak_source": peak_kind,
                          "algorithmic_bytes_per_query": bytes_per_closest,
                          "nodes_per_query": nodes_per_q, "tris_per_query": tris_per_q,
-                         "trace_ms_per_launch": trace_ms / max(trace_launches, 1)},
+                         "launches_per_step": trace_launches / max(args.steps, 1),
+                         "ms_per_launch": trace_ms / max(trace_launches, 1)},
+            "visibility_queries": {"nodes_per_query": any_nodes_per_q, "tris_per_query": any_tris_per_q},
             "batched": batched,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["kernel_launches"]),
             "kernels_per_step": kernels_per_step, "clocks": clk, "wall_s_timed": wall,

@@ -132,7 +132,8 @@ typedef struct {
 } rr_segment;
 
 typedef struct {
-  uint32_t n_triangles, n_materials, bvh_depth, reserved;
+  uint32_t n_triangles, n_materials, bvh_depth;
+  uint32_t n_wide_nodes;    /* nodes of the 8-wide quantised BVH (0 until it is first used) */
   uint64_t device_bytes;    /* scene buffers (not the scan workspace) */
   uint64_t workspace_bytes; /* current scan workspace */
   float build_ms;           /* device time of the last LBVH build */
@@ -144,18 +145,21 @@ typedef struct {
   uint64_t anyhit_queries;  /* air-path visibility queries */
   uint64_t returns;         /* return records written */
   uint64_t scans;
-  uint64_t nodes_visited;   /* internal BVH nodes fetched (RR_COUNT_TRAVERSAL scans only) */
-  uint64_t tris_tested;     /* triangles tested (RR_COUNT_TRAVERSAL scans only) */
+  uint64_t nodes_visited;   /* BVH nodes the closest-hit queries fetched (RR_COUNT_TRAVERSAL scans only) */
+  uint64_t tris_tested;     /* triangles the closest-hit queries tested (RR_COUNT_TRAVERSAL scans only) */
   uint64_t kernel_launches; /* kernels this scene launched (host count) */
+  uint64_t anyhit_nodes_visited; /* the same for the visibility queries */
+  uint64_t anyhit_tris_tested;
 } rr_stats;
 
 /* kernel kinds reported by rr_profile_read */
 #define RR_K_RAYGEN 0
-#define RR_K_TRACE 1
+#define RR_K_TRACE 1 /* closest-hit queries */
 #define RR_K_SHADE 2
 #define RR_K_IMAGE 3
-#define RR_K_BUILD 4
-#define RR_K_COUNT 5
+#define RR_K_BUILD 4 /* LBVH build and the 8-wide collapse */
+#define RR_K_VIS 5   /* air-path candidates and their visibility queries */
+#define RR_K_COUNT 6
 typedef struct {
   double ms[RR_K_COUNT];
   uint64_t launches[RR_K_COUNT];
@@ -198,6 +202,8 @@ int rr_scene_destroy(rr_scene* scene);
    RR_ERR_INVALID_ARG at the next blocking call or rr_scene_sync. */
 int rr_scene_update_vertices(rr_scene* scene, const float* vertices);
 
+/* Sizes of the scene and its latest build.  Blocking (reads the wide node
+   count of the latest build). */
 int rr_scene_info_get(const rr_scene* scene, rr_scene_info* info);
 
 /* Copies the LBVH to host arrays (each may be NULL): morton [T] sorted
@@ -208,6 +214,23 @@ int rr_scene_info_get(const rr_scene* scene, rr_scene_info* info);
    every internal node (lo xyz, hi xyz).  Blocking. */
 int rr_scene_export_bvh(const rr_scene* scene, uint32_t* morton, uint32_t* perm, uint32_t* children,
                         uint32_t* parents, float* boxes);
+
+/* Copies the 8-wide quantised BVH to host arrays (each may be NULL): nodes
+   [n_wide_nodes][80 bytes] in the layout below and tris [T][3][4] float, the
+   triangles in wide-leaf order (v0, v1, v2 with w = original triangle id,
+   material id as bit patterns).  Node layout, five 16-byte words:
+     w0 = P.x, P.y, P.z (float), ex | ey << 8 | ez << 16 | imask << 24
+     w1 = first internal child, first triangle, valid slot mask, 0 (uint32)
+     w2..w4 = child bounds as bytes: qlo.x[8], qlo.y[8], qlo.z[8], qhi.x[8],
+              qhi.y[8], qhi.z[8]
+   Slot k's bound on axis a is P.a + (2^23 + q) 2^(e_a - 127), an exact
+   float; internal slots (imask) are children first_child + (number of
+   internal slots below k), leaf slots triangles first_triangle + (number of
+   leaf slots below k).  Node 0 is the root.  *n_nodes receives the node
+   count; at most cap nodes are written.  The wide BVH is collapsed from the
+   binary one when first needed after a build (a scan with RR_NODES_WIDE8 or
+   this call).  Blocking. */
+int rr_scene_export_wide(rr_scene* scene, void* nodes, uint32_t cap, uint32_t* n_nodes, float* tris);
 
 /* ---------------------------------------------------------------------- */
 /* scans                                                                   */
@@ -253,20 +276,33 @@ int rr_scan_batch_async(rr_scene* scene, uint32_t n, const rr_pose* poses, const
    trace_blocks_per_sm  resident trace blocks per SM (0: the occupancy maximum)
    use_graph            1: each launch sequence is captured once in a CUDA
                         graph and replayed while its arguments stay the same
+   node_format          RR_NODES_BINARY (default): traverse the binary LBVH
+                        with float boxes; RR_NODES_WIDE8: the 8-wide BVH with
+                        8-bit quantised child boxes.  Both give the same
+                        closest hit for every query (the quantised boxes are
+                        rounded outward onto exact float bounds).
+   refill_threshold     the query kernels keep their lanes busy by handing a
+                        warp's idle lanes new queries once at least this many
+                        of its 32 lanes are idle (1..32; 0 = 8)
    workspace_limit      bytes of scan workspace; a launch sequence is sized
                         for its worst-case ray tree (every hit spawning both
                         children) within this limit (0: 24 GiB) */
+#define RR_NODES_WIDE8 0u
+#define RR_NODES_BINARY 1u
 typedef struct {
   uint32_t wavefront_rays;
   uint32_t trace_block;
   uint32_t trace_blocks_per_sm;
   uint32_t use_graph;
+  uint32_t node_format;
+  uint32_t refill_threshold;
   uint64_t workspace_limit;
 } rr_batch_config;
 
 int rr_batch_config_get(const rr_scene* scene, rr_batch_config* out);
 /* RR_ERR_INVALID_ARG for a trace_block other than 64/128/256, more than 64
-   blocks per SM, use_graph > 1 or a workspace limit below 1 MiB. */
+   blocks per SM, use_graph > 1, an unknown node_format, a refill_threshold
+   above 32 or a workspace limit below 1 MiB. */
 int rr_batch_config_set(rr_scene* scene, const rr_batch_config* config);
 
 /* How rr_scan_batch would cut scans params[0..n) into launch sequences under
@@ -285,8 +321,9 @@ int rr_batch_plan(uint32_t n, const rr_sensor_params* params, const rr_batch_con
 
 /* Autotuner: runs the batch (poses, params as for rr_scan_batch, images kept
    on the device and discarded) under a sequence of launch configurations --
-   wavefront size, then trace block size, then trace blocks per SM, then
-   graph replay, keeping the best of each -- each timed with CUDA events as
+   node format, then wavefront size, then trace block size, then trace blocks
+   per SM, then the refill threshold, then graph replay, keeping the best of
+   each -- each timed with CUDA events as
    the mean of reps passes after one warm-up pass.  Sets the fastest on the
    scene and returns it in *best (may be NULL) with its time in *best_ms and
    the time of the configuration it started from in *start_ms (each may be

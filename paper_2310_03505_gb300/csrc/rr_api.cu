@@ -6,6 +6,7 @@
 // rr_build.cu, rr_trace.cu and rr_image.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -144,6 +145,7 @@ int device_status(rr_scene* s, cudaStream_t st) {
     char msg[256];
     if (err & rr::kErrBadVertex)
       return fail(RR_ERR_INVALID_ARG, "a rebuild saw an invalid vertex index or a non-finite vertex");
+    if (err & rr::kErrBvh) return fail(RR_ERR_CUDA, "the wide BVH build failed; nothing was traced");
     if (err & rr::kErrStack) return fail(RR_ERR_CAPACITY, "BVH deeper than the traversal stack");
     if (err & rr::kErrTimeout) return fail(RR_ERR_TIMEOUT, "a bounded device wait gave up");
     if (err & (rr::kErrCapacityRays | rr::kErrCapacityRecs)) {
@@ -164,9 +166,10 @@ int device_status(rr_scene* s, cudaStream_t st) {
 using namespace rr_host;
 
 // one-thread kernel folding the build status into the scan status word
-__global__ void k_fold_build_status(const uint32_t* misc, ScanCounters* ctr) {
+__global__ void k_fold_build_status(const uint32_t* misc, const uint32_t* wctr, ScanCounters* ctr) {
   uint32_t e = 0;
   if (misc[6]) e |= rr::kErrBadVertex;
+  if (wctr[4]) e |= rr::kErrBvh;
   if (e) atomicOr(&ctr->error, e);
 }
 
@@ -187,7 +190,7 @@ int rr_scene_destroy(rr_scene* s) {
   void* ptrs[] = {s->d_vtx, s->d_idx, s->d_mat_id, s->d_raw_mats, s->d_mats, s->d_lut, s->d_lut_cells,
                   s->d_tri, s->d_nodes, s->d_centroid, s->d_keys[0], s->d_keys[1], s->d_vals[0], s->d_vals[1],
                   s->d_hist, s->d_parent, s->d_child, s->d_nbox, s->d_visit, s->d_misc, s->ws, s->d_ctr,
-                  s->d_image};
+                  s->d_image, s->d_cut, s->d_wnodes, s->d_wtri, s->d_wsrc, s->d_wrec, s->d_wctr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->h_ctr) cudaFreeHost(s->h_ctr);
@@ -310,7 +313,7 @@ int rr_scene_update_vertices(rr_scene* s, const float* vertices) {
   prof_end(s, ev, st);
   if (s->nt) {
     s->launches += 1;
-    k_fold_build_status<<<1, 1, 0, st>>>(s->d_misc, s->d_ctr);
+    k_fold_build_status<<<1, 1, 0, st>>>(s->d_misc, s->d_wctr, s->d_ctr);
     RR_CHECK_CUDA(cudaGetLastError(), "status fold");
   }
   return RR_OK;
@@ -322,6 +325,12 @@ int rr_scene_info_get(const rr_scene* s, rr_scene_info* info) {
   info->n_triangles = s->nt;
   info->n_materials = s->nm;
   info->bvh_depth = s->depth;
+  if (s->nt && !s->wide_stale) {   // the count of the latest collapse
+    uint32_t n = 0;
+    RR_CHECK_CUDA(cudaStreamSynchronize(t_stream), "synchronising");
+    RR_CHECK_CUDA(cudaMemcpy(&n, s->d_wctr + 1, sizeof n, cudaMemcpyDeviceToHost), "reading the wide node count");
+    info->n_wide_nodes = n;
+  }
   info->device_bytes = s->scene_bytes;
   info->workspace_bytes = s->ws_bytes;
   info->build_ms = s->build_ms;
@@ -349,6 +358,23 @@ int rr_scene_export_bvh(const rr_scene* s, uint32_t* morton, uint32_t* perm, uin
       memcpy(b, v, sizeof v);
     }
   }
+  return RR_OK;
+}
+
+int rr_scene_export_wide(rr_scene* s, void* nodes, uint32_t cap, uint32_t* n_nodes, float* tris) {
+  if (!s) return fail(RR_ERR_INVALID_ARG, "scene must not be NULL");
+  if (s->nt && s->wide_stale) RR_CHECK_CUDA(build_wide(s, t_stream), "collapsing the wide BVH");
+  RR_CHECK_CUDA(cudaStreamSynchronize(t_stream), "synchronising");
+  uint32_t wctr[8] = {0};
+  if (s->nt) RR_CHECK_CUDA(cudaMemcpy(wctr, s->d_wctr, sizeof wctr, cudaMemcpyDeviceToHost), "export");
+  if (wctr[4]) return fail(RR_ERR_CUDA, "the wide BVH build failed");
+  if (n_nodes) *n_nodes = wctr[1];
+  const size_t nn = std::min<size_t>(wctr[1], cap);
+  if (nodes && nn)
+    RR_CHECK_CUDA(cudaMemcpy(nodes, s->d_wnodes, nn * rr::kWideNodeWords * sizeof(float4), cudaMemcpyDeviceToHost),
+                  "export");
+  if (tris && s->nt)
+    RR_CHECK_CUDA(cudaMemcpy(tris, s->d_wtri, (size_t)s->nt * 3 * sizeof(float4), cudaMemcpyDeviceToHost), "export");
   return RR_OK;
 }
 
@@ -479,9 +505,11 @@ int rr_scene_stats(rr_scene* s, rr_stats* out, int reset) {
   out->nodes_visited = s->h_ctr->stat_nodes;
   out->tris_tested = s->h_ctr->stat_tris;
   out->kernel_launches = s->launches;
+  out->anyhit_nodes_visited = s->h_ctr->stat_nodes_any;
+  out->anyhit_tris_tested = s->h_ctr->stat_tris_any;
   if (reset) {
     s->launches = 0;
-    RR_CHECK_CUDA(cudaMemsetAsync(&s->d_ctr->stat_closest, 0, 6 * sizeof(unsigned long long), st), "stats reset");
+    RR_CHECK_CUDA(cudaMemsetAsync(&s->d_ctr->stat_closest, 0, 8 * sizeof(unsigned long long), st), "stats reset");
     RR_CHECK_CUDA(cudaStreamSynchronize(st), "stats reset");
   }
   return RR_OK;

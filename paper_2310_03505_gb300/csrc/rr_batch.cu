@@ -222,10 +222,17 @@ static cudaError_t launch_sequence(rr_scene* s, const ScanArgs& a, bool pattern,
   if (profile) prof_begin(s, RR_K_RAYGEN, st, &ev);
   if ((e = launch_raygen(a, st)) != cudaSuccess) return e;
   if (profile) prof_end(s, ev, st);
+  const bool vis = (a.any_flags & RR_MULTIPATH) != 0u;
   for (uint32_t b = 0; b < a.max_bounces; ++b) {
     if (profile) prof_begin(s, RR_K_TRACE, st, &ev);
-    if ((e = launch_trace(a, b, cfg, st)) != cudaSuccess) return e;
+    if ((e = launch_query(a, b, false, cfg, st)) != cudaSuccess) return e;
     if (profile) prof_end(s, ev, st);
+    if (b >= 1 && vis) {   // air-path visibility (Sec. III-A) from bounce 1 on
+      if (profile) prof_begin(s, RR_K_VIS, st, &ev);
+      if ((e = launch_vis_prep(a, b, st)) != cudaSuccess) return e;
+      if ((e = launch_query(a, b, true, cfg, st)) != cudaSuccess) return e;
+      if (profile) prof_end(s, ev, st);
+    }
     if (profile) prof_begin(s, RR_K_SHADE, st, &ev);
     if ((e = launch_shade(a, b, st)) != cudaSuccess) return e;
     if (profile) prof_end(s, ev, st);
@@ -240,7 +247,7 @@ static cudaError_t launch_sequence(rr_scene* s, const ScanArgs& a, bool pattern,
 static int graph_launch(rr_scene* s, const ScanArgs& a, bool pattern, const LaunchCfg& cfg, cudaStream_t st) {
   std::vector<unsigned char> key(sizeof(ScanArgs) + 4 * sizeof(uint32_t));
   memcpy(key.data(), &a, sizeof(ScanArgs));
-  const uint32_t extra[4] = {pattern ? 1u : 0u, cfg.trace_block, cfg.trace_blocks_per_sm, 0u};
+  const uint32_t extra[4] = {pattern ? 1u : 0u, cfg.trace_block, cfg.trace_blocks_per_sm, cfg.refill};
   memcpy(key.data() + sizeof(ScanArgs), extra, sizeof extra);
   if (!(s->gexec && key == s->gkey)) {
     if (!s->cap_stream) {
@@ -343,12 +350,26 @@ int batch_enqueue(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps,
 
   ScanArgs a;
   memset(&a, 0, sizeof a);
-  a.tri = s->d_tri;
-  a.nodes = s->d_nodes;
+  const bool wide = cfg.node_format == RR_NODES_WIDE8 && s->nt > 0;
+  if (wide && s->wide_stale) {   // collapse the 8-wide BVH on first use after a build
+    cudaEvent_t ev;
+    if (profile) prof_begin(s, RR_K_BUILD, st, &ev);
+    e = build_wide(s, st);
+    if (profile) prof_end(s, ev, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, "collapsing the wide BVH");
+    }
+  }
+  a.tri = wide ? s->d_wtri : s->d_tri;
+  a.nodes = wide ? s->d_wnodes : s->d_nodes;
   a.mats = s->d_mats;
   a.lut = s->d_lut;
   a.n_tris = s->nt;
   a.n_mats = s->nm;
+  a.wide = wide ? 1u : 0u;
+  a.node_cap = wide ? s->wcap : (s->nt > 1 ? s->nt - 1 : 0u);
+  a.bvh_status = wide ? s->d_wctr + 4 : nullptr;
   a.desc = (const ScanDesc*)(w + L.off_desc);
   a.ray0 = (const uint32_t*)(w + L.off_desc + (size_t)n * sizeof(ScanDesc));
   a.col0 = a.ray0 + (n + 1);
@@ -358,6 +379,7 @@ int batch_enqueue(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps,
   a.max_bounces = maxb;
   a.max_bins = maxbins;
   a.any_flags = any_flags;
+  a.refill = cfg.refill;
   a.rays[0] = (rr::RayRec*)(w + L.off_rays0);
   a.rays[1] = (rr::RayRec*)(w + L.off_rays1);
   a.hits = (rr::HitRec*)(w + L.off_hits);
@@ -373,7 +395,8 @@ int batch_enqueue(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps,
     a.tallies = dbg->tallies;
     a.mask = dbg->mask;
   }
-  s->launches += 2u + 2u * maxb + (pattern ? 1u : 0u);
+  s->launches += 2u + 2u * maxb + ((any_flags & RR_MULTIPATH) && maxb > 1 ? 2u * (maxb - 1u) : 0u) +
+                 (pattern ? 1u : 0u);
   const bool prof = profile && s->prof;
   if (!prof && allow_graph && cfg.use_graph && !dbg) return graph_launch(s, a, pattern, cfg, st);
   e = launch_sequence(s, a, pattern, cfg, prof, st);
@@ -416,6 +439,9 @@ static int cfg_check(const rr_batch_config* c) {
     return fail(RR_ERR_INVALID_ARG, "trace_block must be 64, 128 or 256");
   if (c->trace_blocks_per_sm > 64) return fail(RR_ERR_INVALID_ARG, "trace_blocks_per_sm must be <= 64");
   if (c->use_graph > 1) return fail(RR_ERR_INVALID_ARG, "use_graph must be 0 or 1");
+  if (c->node_format != RR_NODES_WIDE8 && c->node_format != RR_NODES_BINARY)
+    return fail(RR_ERR_INVALID_ARG, "node_format must be RR_NODES_WIDE8 or RR_NODES_BINARY");
+  if (c->refill_threshold > 32) return fail(RR_ERR_INVALID_ARG, "refill_threshold must be in [0, 32]");
   if (c->workspace_limit != 0 && c->workspace_limit < (uint64_t(1) << 20))
     return fail(RR_ERR_INVALID_ARG, "workspace_limit must be 0 or at least 1 MiB");
   return RR_OK;
@@ -427,6 +453,8 @@ static void cfg_to_abi(const LaunchCfg& c, rr_batch_config* o) {
   o->trace_block = c.trace_block;
   o->trace_blocks_per_sm = c.trace_blocks_per_sm;
   o->use_graph = c.use_graph;
+  o->node_format = c.node_format;
+  o->refill_threshold = c.refill;
   o->workspace_limit = c.ws_limit;
 }
 
@@ -436,6 +464,8 @@ static LaunchCfg cfg_from_abi(const rr_batch_config* c) {
   o.trace_block = c->trace_block;
   o.trace_blocks_per_sm = c->trace_blocks_per_sm;
   o.use_graph = c->use_graph;
+  o.node_format = c->node_format;
+  o.refill = c->refill_threshold ? c->refill_threshold : 8u;
   if (c->workspace_limit) o.ws_limit = c->workspace_limit;
   return o;
 }
@@ -593,7 +623,14 @@ int rr_autotune(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor_p
   float best_t = 0.f;
   rc = time_cfg(best, &best_t);
   const float first_t = best_t;
-  // coordinate descent: wavefront size, trace block, trace blocks per SM, graph
+  // coordinate descent: node format, wavefront size, trace block, trace blocks per SM, graph
+  if (rc == RR_OK) {
+    LaunchCfg c = best;
+    c.node_format = best.node_format == RR_NODES_WIDE8 ? RR_NODES_BINARY : RR_NODES_WIDE8;
+    float t = 0.f;
+    rc = time_cfg(c, &t);
+    if (rc == RR_OK && t < best_t) best_t = t, best = c;
+  }
   if (rc == RR_OK) {
     std::vector<uint32_t> waves = {0u};
     for (uint32_t w = 1u << 19; w < rays && w <= (1u << 26); w <<= 1) waves.push_back(w);
@@ -618,11 +655,21 @@ int rr_autotune(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor_p
     }
   }
   if (rc == RR_OK) {
-    const uint32_t mx = (uint32_t)trace_max_blocks_per_sm(best.trace_block);
+    const uint32_t mx = (uint32_t)trace_max_blocks_per_sm(best.trace_block, best.node_format == RR_NODES_WIDE8);
     for (uint32_t k : {mx / 2u, (3u * mx) / 4u}) {
       if (k == 0 || k == mx || k == best.trace_blocks_per_sm) continue;
       LaunchCfg c = best;
       c.trace_blocks_per_sm = k;
+      float t = 0.f;
+      if ((rc = time_cfg(c, &t)) != RR_OK) break;
+      if (t < best_t) best_t = t, best = c;
+    }
+  }
+  if (rc == RR_OK) {
+    for (uint32_t r : {1u, 4u, 8u, 16u, 32u}) {
+      if (r == best.refill) continue;
+      LaunchCfg c = best;
+      c.refill = r;
       float t = 0.f;
       if ((rc = time_cfg(c, &t)) != RR_OK) break;
       if (t < best_t) best_t = t, best = c;

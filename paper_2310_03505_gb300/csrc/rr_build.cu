@@ -17,6 +17,7 @@
 // with a child reference i for internal node i and j | 0x80000000 for leaf j.
 // Leaves are the triangles in sorted order: tri[3j..3j+2] = v0, v1, v2 with
 // v0.w = original triangle id, v1.w = material id (bit patterns).
+#include <algorithm>
 #include <cuda/atomic>
 #include <cuda_runtime.h>
 
@@ -349,6 +350,283 @@ __global__ void k_depth(uint32_t n, const uint32_t* __restrict__ parent, uint32_
 // ---------------------------------------------------------------------------
 // lobe tables: cell integrals of cos^C by 8-point Gauss-Legendre, then a
 // compensated prefix per material
+// ---------------------------------------------------------------------------
+// a6: 8-wide BVH with 8-bit quantised child boxes, collapsed from the binary
+// LBVH (wide node layout in rr_internal.cuh).
+//
+// A: every binary internal node b computes the cut it would have as the root
+//    of a wide node: starting from its two children, the internal member of
+//    largest surface area is replaced by its two children until there are 8
+//    members or only leaves.  Members get slots by octant: slot bit k is set
+//    when the member lies on the high side of axis k (greedy assignment by
+//    the centroid offset from the node centre), so that a ray visiting slots
+//    in the order k ^ octant(direction) meets near members first.
+__device__ __forceinline__ float box_area(const float* b) {
+  const float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
+  return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_wide_cut(uint32_t n, const uint32_t* __restrict__ child, const float* __restrict__ nbox,
+                           uint32_t* __restrict__ cut, uint32_t* __restrict__ wctr) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == 0) {   // counters of pass B: ticket, allocated (the root), done, triangles, error
+    wctr[0] = 0u;
+    wctr[1] = 1u;
+    wctr[2] = 0u;
+    wctr[3] = 0u;
+    wctr[4] = 0u;
+  }
+  if (b + 1 >= n) return;
+  uint32_t c[8];
+  float bx[8][6];
+  c[0] = __ldg(&child[2 * b]);
+  c[1] = __ldg(&child[2 * b + 1]);
+  int m = 2;
+  for (int k = 0; k < 2; ++k)
+    for (int q = 0; q < 6; ++q) bx[k][q] = __ldg(&nbox[6 * (size_t)node_slot(c[k], n) + q]);
+  while (m < 8) {
+    int best = -1;
+    float best_a = -1.0f;
+    for (int k = 0; k < m; ++k) {
+      if (c[k] & kLeafBit) continue;
+      const float a = box_area(bx[k]);
+      if (a > best_a) {
+        best_a = a;
+        best = k;
+      }
+    }
+    if (best < 0) break;
+    const uint32_t p = c[best];
+    const uint32_t c0 = __ldg(&child[2 * p]), c1 = __ldg(&child[2 * p + 1]);
+    c[best] = c0;
+    c[m] = c1;
+    for (int q = 0; q < 6; ++q) {
+      bx[best][q] = __ldg(&nbox[6 * (size_t)node_slot(c0, n) + q]);
+      bx[m][q] = __ldg(&nbox[6 * (size_t)node_slot(c1, n) + q]);
+    }
+    ++m;
+  }
+  // octant slots
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int k = 0; k < m; ++k)
+    for (int q = 0; q < 3; ++q) {
+      lo[q] = fminf(lo[q], bx[k][q]);
+      hi[q] = fmaxf(hi[q], bx[k][3 + q]);
+    }
+  float off[8][3];
+  for (int k = 0; k < m; ++k)
+    for (int q = 0; q < 3; ++q) off[k][q] = (bx[k][q] + bx[k][3 + q]) - (lo[q] + hi[q]);
+  uint32_t out[8];
+  for (int sl = 0; sl < 8; ++sl) out[sl] = kNone;
+  uint32_t free_slots = 0xFFu, todo = (1u << m) - 1u;
+  for (int r = 0; r < m; ++r) {
+    float best_sc = -INFINITY;
+    int bk = 0, bs = 0;
+    for (int k = 0; k < m; ++k) {
+      if (!(todo >> k & 1u)) continue;
+      for (int sl = 0; sl < 8; ++sl) {
+        if (!(free_slots >> sl & 1u)) continue;
+        const float sc = ((sl & 1) ? off[k][0] : -off[k][0]) + ((sl & 2) ? off[k][1] : -off[k][1]) +
+                         ((sl & 4) ? off[k][2] : -off[k][2]);
+        if (sc > best_sc) {
+          best_sc = sc;
+          bk = k;
+          bs = sl;
+        }
+      }
+    }
+    out[bs] = c[bk];
+    free_slots &= ~(1u << bs);
+    todo &= ~(1u << bk);
+  }
+  uint4* o = reinterpret_cast<uint4*>(cut + 8 * (size_t)b);
+  o[0] = make_uint4(out[0], out[1], out[2], out[3]);
+  o[1] = make_uint4(out[4], out[5], out[6], out[7]);
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// members of the cut of binary node b in slot order (kNone: empty slot); a
+// one-triangle scene has a root with one leaf member
+__device__ __forceinline__ void load_cut(uint32_t n, const uint32_t* __restrict__ cut, uint32_t b, uint32_t out[8]) {
+  if (n == 1) {
+    out[0] = kLeafBit;
+    for (int k = 1; k < 8; ++k) out[k] = kNone;
+    return;
+  }
+  const uint4* p = reinterpret_cast<const uint4*>(cut + 8 * (size_t)b);
+  const uint4 a = p[0], c = p[1];
+  out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+  out[4] = c.x; out[5] = c.y; out[6] = c.z; out[7] = c.w;
+}
+
+// B: wide nodes are numbered top down.  Wide node 0 is the binary root; the
+// node that processes wide node w allocates consecutive numbers for the
+// internal members of its cut (wctr[1]) and consecutive triangle slots for
+// its leaf members (wctr[3]), and publishes each internal member's binary
+// node as (epoch << 32 | b) in wsrc.  Threads take wide node numbers from a
+// ticket (wctr[0]) and wait (bounded) until their number is published or
+// the tree is complete: every node allocated has been processed
+// (wctr[2] == wctr[1]).  A thread only waits for a number allocated by a
+// thread that already holds an earlier ticket, so the waits always end.
+constexpr uint32_t kWideSpinLimit = 1u << 22;
+constexpr uint32_t kWideErr = 1u;
+
+__global__ void __launch_bounds__(128) k_wide_alloc(uint32_t n, const uint32_t* __restrict__ cut,
+                                                    unsigned long long* __restrict__ wsrc,
+                                                    uint4* __restrict__ wrec, uint32_t* __restrict__ wctr,
+                                                    uint32_t epoch, uint32_t wcap) {
+  while (true) {
+    const uint32_t i = atomicAdd(&wctr[0], 1u);
+    uint32_t b = 0;
+    if (i > 0) {
+      // poll the own slot; the shared counters only now and then, so that
+      // waiting threads do not crowd the lines the producers update
+      uint32_t spins = 0, nap = 32;
+      while (true) {
+        if (i < wcap) {
+          const unsigned long long v = ld_acquire_u64(&wsrc[i]);
+          if ((uint32_t)(v >> 32) == epoch) {
+            b = (uint32_t)v;
+            break;
+          }
+        }
+        if ((spins & 15u) == 15u) {
+          const uint32_t done = ld_acquire_u32(&wctr[2]);
+          const uint32_t alloc = ld_acquire_u32(&wctr[1]);
+          if (i >= alloc && done == alloc) return;   // the tree is complete
+          if (ld_acquire_u32(&wctr[4])) return;
+        }
+        if (++spins > kWideSpinLimit) {
+          atomicOr(&wctr[4], kWideErr);
+          return;
+        }
+        __nanosleep(nap);
+        if (nap < 256) nap <<= 1;
+      }
+    }
+    uint32_t m[8];
+    load_cut(n, cut, b, m);
+    uint32_t ni = 0, nl = 0;
+    for (int k = 0; k < 8; ++k) {
+      if (m[k] == kNone) continue;
+      if (m[k] & kLeafBit) ++nl;
+      else ++ni;
+    }
+    const uint32_t cb = ni ? atomicAdd(&wctr[1], ni) : 0u;
+    const uint32_t tb = nl ? atomicAdd(&wctr[3], nl) : 0u;
+    if ((ni && cb + ni > wcap) || tb + nl > n) {
+      atomicOr(&wctr[4], kWideErr);
+      return;
+    }
+    uint32_t r = 0;
+    for (int k = 0; k < 8; ++k)
+      if (m[k] != kNone && !(m[k] & kLeafBit))
+        st_release_u64(&wsrc[cb + r++], ((unsigned long long)epoch << 32) | m[k]);
+    wrec[i] = make_uint4(b, cb, tb, 0u);
+    __threadfence();
+    atomicAdd(&wctr[2], 1u);
+  }
+}
+
+// C: quantised boxes and the triangle copies of every wide node.  Per axis
+// the node stores an exponent e and an origin P on the grid of s = 2^e with
+// |P / s| + 255 <= 2^23; child bounds are P + q s, q in [0, 255], rounded
+// outward (q_lo = floor, q_hi = ceil).  Every such bound is a float exactly,
+// so the decoded box contains the child's box and the traversal's slab test
+// keeps its rounding guarantees.  The node keeps P - 2^23 s, so that the
+// bound is the exact fma(float(2^23 + q), s, P - 2^23 s) where the bits of
+// float(2^23 + q) are 0x4B000000 | q.
+__device__ __forceinline__ int ceil_log2(double x) {   // x > 0
+  int ex;
+  const double m = frexp(x, &ex);   // x = m 2^ex, m in [0.5, 1)
+  return m == 0.5 ? ex - 1 : ex;
+}
+
+__global__ void __launch_bounds__(128) k_wide_write(uint32_t n, const uint32_t* __restrict__ cut,
+                                                    const float* __restrict__ nbox,
+                                                    const float4* __restrict__ tri, const uint4* __restrict__ wrec,
+                                                    const uint32_t* __restrict__ wctr, uint32_t wcap,
+                                                    float4* __restrict__ wnodes, float4* __restrict__ wtri) {
+  if (wctr[4]) return;   // pass B failed: the records are incomplete (traversal is refused)
+  const uint32_t count = min(wctr[1], wcap);
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < count; w += gridDim.x * blockDim.x) {
+    const uint4 rec = wrec[w];
+    uint32_t m[8];
+    load_cut(n, cut, rec.x, m);
+    float bx[8][6];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    uint32_t valid = 0, imask = 0;
+    for (int k = 0; k < 8; ++k) {
+      if (m[k] == kNone) continue;
+      valid |= 1u << k;
+      if (!(m[k] & kLeafBit)) imask |= 1u << k;
+      for (int q = 0; q < 6; ++q) bx[k][q] = nbox[6 * (size_t)node_slot(m[k], n) + q];
+      for (int q = 0; q < 3; ++q) {
+        lo[q] = fmin(lo[q], (double)bx[k][q]);
+        hi[q] = fmax(hi[q], (double)bx[k][3 + q]);
+      }
+    }
+    float pp[3];
+    uint32_t eb[3];
+    uint32_t qw[6][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}};   // lo x y z, hi x y z
+    const double two23 = 8388608.0;
+    for (int a = 0; a < 3; ++a) {
+      int e = -126;
+      if (hi[a] > lo[a]) e = max(e, ceil_log2((hi[a] - lo[a]) / 255.0));
+      const double mag = fmax(fabs(lo[a]), fabs(hi[a]));
+      if (mag > 0.0) e = max(e, ceil_log2(mag) - 22);
+      double s = 0.0, k0 = 0.0;
+      for (int it = 0; it < 64; ++it, ++e) {
+        s = ldexp(1.0, e);
+        k0 = floor(lo[a] / s);
+        if (fabs(k0) + 255.0 <= two23 && (k0 + 255.0) * s >= hi[a]) break;
+      }
+      pp[a] = (float)((k0 - two23) * s);
+      eb[a] = (uint32_t)(e + 127);
+      for (int k = 0; k < 8; ++k) {
+        uint32_t ql = 255u, qh = 0u;   // empty slot: an inverted box
+        if (valid >> k & 1u) {
+          ql = (uint32_t)(floor((double)bx[k][a] / s) - k0);
+          qh = (uint32_t)(ceil((double)bx[k][3 + a] / s) - k0);
+        }
+        qw[a][k >> 2] |= ql << (8 * (k & 3));
+        qw[3 + a][k >> 2] |= qh << (8 * (k & 3));
+      }
+    }
+    float4* o = wnodes + 5 * (size_t)w;
+    o[0] = make_float4(pp[0], pp[1], pp[2], __uint_as_float(eb[0] | (eb[1] << 8) | (eb[2] << 16) | (imask << 24)));
+    o[1] = make_float4(__uint_as_float(rec.y), __uint_as_float(rec.z), __uint_as_float(valid), 0.0f);
+    o[2] = make_float4(__uint_as_float(qw[0][0]), __uint_as_float(qw[0][1]), __uint_as_float(qw[1][0]),
+                       __uint_as_float(qw[1][1]));
+    o[3] = make_float4(__uint_as_float(qw[2][0]), __uint_as_float(qw[2][1]), __uint_as_float(qw[3][0]),
+                       __uint_as_float(qw[3][1]));
+    o[4] = make_float4(__uint_as_float(qw[4][0]), __uint_as_float(qw[4][1]), __uint_as_float(qw[5][0]),
+                       __uint_as_float(qw[5][1]));
+    uint32_t r = 0;
+    for (int k = 0; k < 8; ++k) {
+      if (m[k] == kNone || !(m[k] & kLeafBit)) continue;
+      const uint32_t j = m[k] & ~kLeafBit;
+      const size_t dst = 3 * (size_t)(rec.z + r++);
+      wtri[dst] = tri[3 * (size_t)j];
+      wtri[dst + 1] = tri[3 * (size_t)j + 1];
+      wtri[dst + 2] = tri[3 * (size_t)j + 2];
+    }
+  }
+}
+
 __global__ void k_lut_cells(const rr_material* __restrict__ raw, uint32_t nm, float* __restrict__ cells) {
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nm * (uint32_t)kLutCells) return;
@@ -448,6 +726,18 @@ cudaError_t build_alloc(rr_scene* s) {
   RR_TRY(alloc((void**)&s->d_nbox, (T ? 2 * T - 1 : 1) * 6 * sizeof(float)));
   RR_TRY(alloc((void**)&s->d_visit, (T > 1 ? T - 1 : 1) * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_misc, 8 * sizeof(uint32_t)));
+  // wide BVH: at most T - 1 wide nodes (each owns a distinct binary internal node)
+  s->wcap = T > 1 ? (uint32_t)(T - 1) : 1u;
+  if (T) {
+    RR_TRY(alloc((void**)&s->d_cut, (size_t)s->wcap * 8 * sizeof(uint32_t)));
+    RR_TRY(alloc((void**)&s->d_wnodes, (size_t)s->wcap * kWideNodeWords * sizeof(float4)));
+    RR_TRY(alloc((void**)&s->d_wtri, T * 3 * sizeof(float4)));
+    RR_TRY(alloc((void**)&s->d_wsrc, (size_t)s->wcap * sizeof(unsigned long long)));
+    RR_TRY(alloc((void**)&s->d_wrec, (size_t)s->wcap * sizeof(uint4)));
+    RR_TRY(alloc((void**)&s->d_wctr, 8 * sizeof(uint32_t)));
+    RR_TRY(cudaMemset(s->d_wsrc, 0, (size_t)s->wcap * sizeof(unsigned long long)));   // epoch 0: nothing published
+    RR_TRY(cudaMemset(s->d_wctr, 0, 8 * sizeof(uint32_t)));
+  }
   s->scene_bytes = bytes;
   return cudaSuccess;
 }
@@ -504,7 +794,30 @@ cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth) {
   } else {
     RR_TRY(cudaMemsetAsync(s->d_parent, 0xFF, sizeof(uint32_t), st));
   }
+  s->wide_stale = true;   // the 8-wide BVH is collapsed when a scan first needs it
   return cudaSuccess;
+}
+
+// a6: the 8-wide quantised BVH, collapsed from the current binary LBVH
+cudaError_t build_wide(rr_scene* s, cudaStream_t st) {
+  const uint32_t n = s->nt;
+  s->wide_stale = false;
+  if (n == 0) return cudaSuccess;
+  s->launches += 3u;
+  s->wide_epoch += 1u;
+  if (s->wide_epoch == 0u) s->wide_epoch = 1u;   // 0 marks "never published"
+  k_wide_cut<<<n > 1 ? (n - 1 + 127) / 128 : 1, 128, 0, st>>>(n, s->d_child, s->d_nbox, s->d_cut, s->d_wctr);
+  RR_TRY(cudaGetLastError());
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t alloc_threads = 2u * 128u * (uint32_t)sms;
+  const uint32_t alloc_grid = (std::min<uint32_t>(alloc_threads, s->wcap + 128u) + 127u) / 128u;
+  k_wide_alloc<<<alloc_grid, 128, 0, st>>>(n, s->d_cut, s->d_wsrc, s->d_wrec, s->d_wctr, s->wide_epoch, s->wcap);
+  RR_TRY(cudaGetLastError());
+  k_wide_write<<<std::min<uint32_t>((s->wcap + 127u) / 128u, 8u * (uint32_t)sms), 128, 0, st>>>(
+      n, s->d_cut, s->d_nbox, s->d_tri, s->d_wrec, s->d_wctr, s->wcap, s->d_wnodes, s->d_wtri);
+  return cudaGetLastError();
 }
 
 }  // namespace rr_host

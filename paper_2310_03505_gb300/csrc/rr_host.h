@@ -26,6 +26,8 @@ struct LaunchCfg {
   uint32_t trace_block = 128;         // 64, 128 or 256
   uint32_t trace_blocks_per_sm = 0;   // 0: occupancy maximum
   uint32_t use_graph = 1;             // capture each launch sequence once and replay it
+  uint32_t node_format = RR_NODES_BINARY;
+  uint32_t refill = 8;                // idle lanes that trigger a refill (1..32)
   uint64_t ws_limit = uint64_t(24) << 30;
 };
 
@@ -44,6 +46,16 @@ struct rr_scene {
   float* d_lut_cells = nullptr;    // [M][kLutCells]
   float4* d_tri = nullptr;         // [T][3] sorted leaves
   float4* d_nodes = nullptr;       // [T-1][4]
+  // 8-wide quantised BVH (collapsed from the binary one at every build)
+  uint32_t wcap = 0;               // wide node capacity (T - 1, at least 1)
+  uint32_t wide_epoch = 0;         // build counter tagging the published work items
+  bool wide_stale = true;          // the binary LBVH changed since the last collapse
+  uint32_t* d_cut = nullptr;       // [T-1][8] cut of every binary internal node, slot order
+  float4* d_wnodes = nullptr;      // [wcap][kWideNodeWords]
+  float4* d_wtri = nullptr;        // [T][3] triangles in wide-leaf order
+  unsigned long long* d_wsrc = nullptr;   // [wcap] epoch << 32 | binary node of each wide node
+  uint4* d_wrec = nullptr;         // [wcap] (binary node, first child, first triangle, 0)
+  uint32_t* d_wctr = nullptr;      // [8] ticket, allocated, done, triangles, error
   // build temporaries (kept for rebuilds)
   float4* d_centroid = nullptr;    // [T]
   uint32_t* d_keys[2] = {nullptr, nullptr};
@@ -90,12 +102,14 @@ namespace rr_host {
 cudaError_t build_alloc(rr_scene* s);
 cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth);   // a1..a5 on s->d_vtx; counts its launches
 cudaError_t build_materials(rr_scene* s, cudaStream_t st);
+cudaError_t build_wide(rr_scene* s, cudaStream_t st);      // a6, stream ordered after the LBVH
 
 // rr_trace.cu
 int num_sms();
-int trace_max_blocks_per_sm(uint32_t block);
+int trace_max_blocks_per_sm(uint32_t block, bool wide);
 cudaError_t launch_raygen(const rr::ScanArgs& a, cudaStream_t st);
-cudaError_t launch_trace(const rr::ScanArgs& a, uint32_t bounce, const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_query(const rr::ScanArgs& a, uint32_t bounce, bool any, const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_vis_prep(const rr::ScanArgs& a, uint32_t bounce, cudaStream_t st);
 cudaError_t launch_shade(const rr::ScanArgs& a, uint32_t bounce, cudaStream_t st);
 
 // rr_image.cu

@@ -26,6 +26,7 @@ constexpr uint32_t kErrTimeout = 4u;
 constexpr uint32_t kErrCapacitySegs = 8u;
 constexpr uint32_t kErrBadVertex = 16u;
 constexpr uint32_t kErrStack = 32u;
+constexpr uint32_t kErrBvh = 64u;      // the BVH build failed (traversal refused)
 
 // ---------------------------------------------------------------------------
 // device material record (derived at scene creation)
@@ -61,12 +62,27 @@ struct ScanCounters {
   uint32_t seg_start[RR_MAX_BOUNCES + 1];  // first debug segment of each bounce
   uint32_t trace_ticket[RR_MAX_BOUNCES];
   uint32_t shade_ticket[RR_MAX_BOUNCES];
+  uint32_t vis_count[RR_MAX_BOUNCES];      // visibility jobs per bounce
+  uint32_t vis_ticket[RR_MAX_BOUNCES];
   uint32_t need_rays, need_recs;           // largest request seen (overflow report)
   uint32_t error;                          // sticky kErr* bits
   uint32_t pad;
   unsigned long long stat_closest, stat_anyhit, stat_returns, stat_scans;
   unsigned long long stat_nodes, stat_tris;
+  unsigned long long stat_nodes_any, stat_tris_any;
 };
+
+// 8-wide BVH node with 8-bit quantised child boxes, 5 float4 (80 bytes):
+//   w0 = (P.x, P.y, P.z, ex | ey << 8 | ez << 16 | imask << 24)
+//   w1 = (first internal child, first triangle, valid mask, 0)      (bits)
+//   w2 = (qlo.x[0..3], qlo.x[4..7], qlo.y[0..3], qlo.y[4..7])       (bytes)
+//   w3 = (qlo.z[0..3], qlo.z[4..7], qhi.x[0..3], qhi.x[4..7])
+//   w4 = (qhi.y[0..3], qhi.y[4..7], qhi.z[0..3], qhi.z[4..7])
+// Slot k of an axis has bounds fma(float(2^23 + q), s, P) with s = 2^(e - 127)
+// (exact floats that contain the child's box).  Internal children are stored
+// consecutively from the first child in slot order, leaf slots (one
+// triangle each) likewise from the first triangle.
+constexpr int kWideNodeWords = 5;
 
 // Return record key: global image column (scan's first column + azimuth)
 // and range bin.  Records of one bounce are in column order.
@@ -99,6 +115,9 @@ struct ScanArgs {
   const MatDev* mats;
   const float4* lut;         // [M][kLutCells + 1]: (G(x_k), Gc(x_k), cos^C(x_k), 0)
   uint32_t n_tris, n_mats;
+  uint32_t wide;             // nodes are 8-wide quantised (tri in wide-leaf order), else binary
+  uint32_t node_cap;         // nodes in the node array (traversal bound)
+  const uint32_t* bvh_status;   // non-zero: the last build failed, nothing may be traced
   // batch
   const ScanDesc* desc;      // [n_scans]
   const uint32_t* ray0;      // [n_scans + 1] prefix of n_az * ns
@@ -107,6 +126,7 @@ struct ScanArgs {
   uint32_t max_bounces;      // over the batch
   uint32_t max_bins;         // over the batch
   uint32_t any_flags;        // union of the scans' flags
+  uint32_t refill;           // a warp hands out new queries once this many lanes are idle (1..32)
   // workspace
   RayRec* rays[2];
   HitRec* hits;

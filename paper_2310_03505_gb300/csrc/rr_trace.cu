@@ -21,6 +21,8 @@
 // sequence of launches with no host round trip between bounces.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "rr_host.h"
 
 namespace rr {
@@ -71,6 +73,8 @@ __global__ void k_raygen(ScanArgs a) {
     for (int b = 0; b < (int)RR_MAX_BOUNCES; ++b) {
       c->trace_ticket[b] = 0;
       c->shade_ticket[b] = 0;
+      c->vis_count[b] = 0;
+      c->vis_ticket[b] = 0;
     }
     c->count[0] = a.n_rays0;
     c->stat_scans += (unsigned long long)a.n_scans;
@@ -155,201 +159,437 @@ __device__ __forceinline__ float woop_hit(const WoopRay& w, float3 v0, float3 v1
   return T / det;
 }
 
-// Closest hit with t_min < t and (t, original id) lexicographically smallest,
-// t < t_best on entry; or, with any_hit, the first hit with t_min < t < t_best.
-// Returns the leaf index or kNone.
-template <bool kAny, bool kCount>
-__device__ __forceinline__ uint32_t traverse(const ScanArgs& a, float3 o, float3 d, float t_min, float& t_best,
-                                             uint32_t skip, uint32_t& n_nodes, uint32_t& n_tris,
-                                             uint32_t& visits) {
-  const uint32_t nt = a.n_tris;
-  if (nt == 0) return kNone;
-  const WoopRay w = make_woop(o, d);
-  const float3 id = make_float3(1.0f / (fabsf(d.x) > 1e-30f ? d.x : copysignf(1e-30f, d.x)),
-                                1.0f / (fabsf(d.y) > 1e-30f ? d.y : copysignf(1e-30f, d.y)),
-                                1.0f / (fabsf(d.z) > 1e-30f ? d.z : copysignf(1e-30f, d.z)));
-  uint32_t stack[kStack];
-  int sp = 0;
-  uint32_t node = nt == 1 ? kLeafBit : 0u;
-  uint32_t best = kNone, best_id = 0u;
-  while (true) {
-    if (!(node & kLeafBit)) {
-      if (kCount) ++n_nodes;
-      ++visits;
-      const float4* np = a.nodes + 4 * (size_t)node;
-      const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
-      // child 0
-      float t0 = (n0.x - o.x) * id.x, t1 = (n0.y - o.x) * id.x;
-      float lo0 = fminf(t0, t1), hi0 = fmaxf(t0, t1);
-      t0 = (n0.z - o.y) * id.y;
-      t1 = (n0.w - o.y) * id.y;
-      lo0 = fmaxf(lo0, fminf(t0, t1));
-      hi0 = fminf(hi0, fmaxf(t0, t1));
-      t0 = (n2.x - o.z) * id.z;
-      t1 = (n2.y - o.z) * id.z;
-      lo0 = fmaxf(fmaxf(lo0, fminf(t0, t1)), t_min);
-      hi0 = fminf(fminf(hi0, fmaxf(t0, t1)) * kBoxInflate, t_best);
-      // child 1
-      t0 = (n1.x - o.x) * id.x;
-      t1 = (n1.y - o.x) * id.x;
-      float lo1 = fminf(t0, t1), hi1 = fmaxf(t0, t1);
-      t0 = (n1.z - o.y) * id.y;
-      t1 = (n1.w - o.y) * id.y;
-      lo1 = fmaxf(lo1, fminf(t0, t1));
-      hi1 = fminf(hi1, fmaxf(t0, t1));
-      t0 = (n2.z - o.z) * id.z;
-      t1 = (n2.w - o.z) * id.z;
-      lo1 = fmaxf(fmaxf(lo1, fminf(t0, t1)), t_min);
-      hi1 = fminf(fminf(hi1, fmaxf(t0, t1)) * kBoxInflate, t_best);
-      const bool h0 = lo0 <= hi0, h1 = lo1 <= hi1;
-      const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
-      if (h0 && h1) {
-        const bool first0 = lo0 <= lo1;
-        node = first0 ? c0 : c1;
-        if (sp < kStack) stack[sp++] = first0 ? c1 : c0;
-        else atomicOr(&a.ctr->error, kErrStack);
-        continue;
-      }
-      if (h0 || h1) {
-        node = h0 ? c0 : c1;
-        continue;
+// ---------------------------------------------------------------------------
+// Resumable traversal.  A query (closest hit, or any hit for visibility) is
+// advanced one step at a time -- one node visit or one triangle test -- so
+// that a lane whose query has ended can take the next one while the other
+// lanes of its warp go on.
+//
+// Closest hit: t_min < t < t_best on entry, (t, original id)
+// lexicographically smallest.  Any hit: the first t_min < t < t_best.  The
+// leaf `skip` (the one the ray starts on) is never reported.
+struct Trav {
+  WoopRay w;            // origin and the watertight-test frame
+  float3 id;            // 1 / direction, zero components replaced by +-1e-30
+  float t_min, t_best;
+  uint32_t skip;
+  uint32_t node;        // binary: next node; both: kNone once the query has ended
+  uint32_t best, best_id, visits;
+  uint32_t oct;                               // wide: direction octant
+  uint32_t g_base, g_bits, t_base, t_bits;    // wide: node group, triangle group
+  int sp;
+};
+
+__device__ __forceinline__ void trav_begin(Trav& s, float3 o, float3 d, float t_min, float t_best, uint32_t skip,
+                                           uint32_t n_tris, bool wide) {
+  s.w = make_woop(o, d);
+  s.id = make_float3(1.0f / (fabsf(d.x) > 1e-30f ? d.x : copysignf(1e-30f, d.x)),
+                     1.0f / (fabsf(d.y) > 1e-30f ? d.y : copysignf(1e-30f, d.y)),
+                     1.0f / (fabsf(d.z) > 1e-30f ? d.z : copysignf(1e-30f, d.z)));
+  s.t_min = t_min;
+  s.t_best = t_best;
+  s.skip = skip;
+  s.best = kNone;
+  s.best_id = 0u;
+  s.visits = 0u;
+  s.sp = 0;
+  if (wide) {
+    s.oct = (s.id.x < 0.0f ? 1u : 0u) | (s.id.y < 0.0f ? 2u : 0u) | (s.id.z < 0.0f ? 4u : 0u);
+    s.g_base = 0u;
+    s.g_bits = (1u << 8) | (1u << s.oct);   // the root: internal slot 0 of a virtual group
+    s.t_base = 0u;
+    s.t_bits = 0u;
+    s.node = n_tris ? 0u : kNone;
+  } else {
+    s.node = n_tris == 0 ? kNone : (n_tris == 1 ? kLeafBit : 0u);
+  }
+}
+
+// triangle j against the query; returns true when an any-hit query is answered
+template <bool kAny>
+__device__ __forceinline__ bool trav_tri(Trav& s, const ScanArgs& a, uint32_t j, uint32_t& n_tris, bool count) {
+  if (j == s.skip) return false;
+  if (count) ++n_tris;
+  const float4* tp = a.tri + 3 * (size_t)j;
+  const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+  const float t = woop_hit(s.w, f3(v0), f3(v1), f3(v2));
+  if (t > s.t_min) {
+    if (kAny) {
+      if (t < s.t_best) {
+        s.best = j;
+        return true;
       }
     } else {
-      const uint32_t j = node & ~kLeafBit;
-      if (j != skip) {
-        if (kCount) ++n_tris;
-        const float4* tp = a.tri + 3 * (size_t)j;
-        const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-        const float t = woop_hit(w, f3(v0), f3(v1), f3(v2));
-        if (t > t_min) {
-          if (kAny) {
-            if (t < t_best) return j;
-          } else {
-            const uint32_t tid = __float_as_uint(v0.w);
-            if (t < t_best || (t == t_best && best != kNone && tid < best_id)) {
-              t_best = t;
-              best = j;
-              best_id = tid;
-            }
-          }
-        }
+      const uint32_t tid = __float_as_uint(v0.w);
+      if (t < s.t_best || (t == s.t_best && s.best != kNone && tid < s.best_id)) {
+        s.t_best = t;
+        s.best = j;
+        s.best_id = tid;
       }
     }
-    if (sp == 0) break;
-    node = stack[--sp];
   }
-  return best;
+  return false;
+}
+
+// one step over the binary LBVH (both children tested, nearer first)
+template <bool kAny>
+__device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const ScanArgs& a, uint32_t& n_nodes,
+                                            uint32_t& n_tris, bool count) {
+  const uint32_t node = s.node;
+  if (!(node & kLeafBit)) {
+    if (count) ++n_nodes;
+    ++s.visits;
+    const float3 o = s.w.o, id = s.id;
+    const float4* np = a.nodes + 4 * (size_t)node;
+    const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+    // child 0
+    float t0 = (n0.x - o.x) * id.x, t1 = (n0.y - o.x) * id.x;
+    float lo0 = fminf(t0, t1), hi0 = fmaxf(t0, t1);
+    t0 = (n0.z - o.y) * id.y;
+    t1 = (n0.w - o.y) * id.y;
+    lo0 = fmaxf(lo0, fminf(t0, t1));
+    hi0 = fminf(hi0, fmaxf(t0, t1));
+    t0 = (n2.x - o.z) * id.z;
+    t1 = (n2.y - o.z) * id.z;
+    lo0 = fmaxf(fmaxf(lo0, fminf(t0, t1)), s.t_min);
+    hi0 = fminf(fminf(hi0, fmaxf(t0, t1)) * kBoxInflate, s.t_best);
+    // child 1
+    t0 = (n1.x - o.x) * id.x;
+    t1 = (n1.y - o.x) * id.x;
+    float lo1 = fminf(t0, t1), hi1 = fmaxf(t0, t1);
+    t0 = (n1.z - o.y) * id.y;
+    t1 = (n1.w - o.y) * id.y;
+    lo1 = fmaxf(lo1, fminf(t0, t1));
+    hi1 = fminf(hi1, fmaxf(t0, t1));
+    t0 = (n2.z - o.z) * id.z;
+    t1 = (n2.w - o.z) * id.z;
+    lo1 = fmaxf(fmaxf(lo1, fminf(t0, t1)), s.t_min);
+    hi1 = fminf(fminf(hi1, fmaxf(t0, t1)) * kBoxInflate, s.t_best);
+    const bool h0 = lo0 <= hi0, h1 = lo1 <= hi1;
+    const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
+    if (h0 && h1) {
+      const bool first0 = lo0 <= lo1;
+      s.node = first0 ? c0 : c1;
+      if (s.sp < kStack) stack[s.sp++] = first0 ? c1 : c0;
+      else atomicOr(&a.ctr->error, kErrStack);
+      return;
+    }
+    if (h0 || h1) {
+      s.node = h0 ? c0 : c1;
+      return;
+    }
+  } else if (trav_tri<kAny>(s, a, node & ~kLeafBit, n_tris, count)) {
+    s.node = kNone;
+    return;
+  }
+  s.node = s.sp ? stack[--s.sp] : kNone;
+}
+
+// One step over the 8-wide quantised BVH: a triangle of the current
+// triangle group, else the next child of the current node group, else a
+// group from the stack.  Children are visited in slot order k ^ octant
+// (near first) through node groups as in Ylitie, Karras, Laine, "Efficient
+// incoherent ray traversal on GPUs through compressed wide BVHs" (HPG 2017):
+// a group is (first child, internal-slot mask << 8 | hit children still to
+// visit, bit k for slot k ^ octant), so one stack entry stands for up to 7
+// pending children.  Slot boxes are decoded exactly (see kWideNodeWords) and
+// tested with the same slab test as the binary nodes, so a query finds the
+// same closest hit in either BVH.
+template <bool kAny>
+__device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs& a, uint32_t& n_nodes,
+                                          uint32_t& n_tris, bool count) {
+  const uint32_t oct = s.oct;
+  if (s.t_bits & 0xFFu) {
+    const uint32_t k = __ffs(s.t_bits & 0xFFu) - 1u;
+    s.t_bits &= ~(1u << k);
+    const uint32_t slot = k ^ oct;
+    const uint32_t j = s.t_base + __popc((s.t_bits >> 8) & ((1u << slot) - 1u));
+    if (j < a.n_tris && trav_tri<kAny>(s, a, j, n_tris, count)) s.node = kNone;
+    return;
+  }
+  if (s.g_bits & 0xFFu) {
+    const uint32_t k = __ffs(s.g_bits & 0xFFu) - 1u;
+    s.g_bits &= ~(1u << k);
+    const uint32_t slot = k ^ oct;
+    const uint32_t node = s.g_base + __popc((s.g_bits >> 8) & ((1u << slot) - 1u));
+    if (s.g_bits & 0xFFu) {
+      if (s.sp < kStack) stack[s.sp++] = make_uint2(s.g_base, s.g_bits);
+      else atomicOr(&a.ctr->error, kErrStack);
+    }
+    if (node >= a.node_cap) {   // only a failed build can get here
+      atomicOr(&a.ctr->error, kErrBvh);
+      s.node = kNone;
+      return;
+    }
+    if (count) ++n_nodes;
+    ++s.visits;
+    const float3 o = s.w.o, id = s.id;
+    const bool neg_x = id.x < 0.0f, neg_y = id.y < 0.0f, neg_z = id.z < 0.0f;
+    const uint4* np = reinterpret_cast<const uint4*>(a.nodes) + kWideNodeWords * (size_t)node;
+    const uint4 w0 = __ldg(np), w1 = __ldg(np + 1), w2 = __ldg(np + 2), w3 = __ldg(np + 3), w4 = __ldg(np + 4);
+    const float px = __uint_as_float(w0.x), py = __uint_as_float(w0.y), pz = __uint_as_float(w0.z);
+    const float sx = __uint_as_float((w0.w & 0xFFu) << 23), sy = __uint_as_float(((w0.w >> 8) & 0xFFu) << 23),
+                sz = __uint_as_float(((w0.w >> 16) & 0xFFu) << 23);
+    const uint32_t imask = w0.w >> 24, valid = w1.z;
+    // near and far plane bytes per axis: (lo, hi) for a positive direction, swapped otherwise
+    const uint32_t nx0 = neg_x ? w3.z : w2.x, nx1 = neg_x ? w3.w : w2.y;
+    const uint32_t fx0 = neg_x ? w2.x : w3.z, fx1 = neg_x ? w2.y : w3.w;
+    const uint32_t ny0 = neg_y ? w4.x : w2.z, ny1 = neg_y ? w4.y : w2.w;
+    const uint32_t fy0 = neg_y ? w2.z : w4.x, fy1 = neg_y ? w2.w : w4.y;
+    const uint32_t nz0 = neg_z ? w4.z : w3.x, nz1 = neg_z ? w4.w : w3.y;
+    const uint32_t fz0 = neg_z ? w3.x : w4.z, fz1 = neg_z ? w3.y : w4.w;
+    uint32_t hit_i = 0u, hit_l = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      // bits 0x4B0000qq = 2^23 + q (byte q of the word), decoded to P + q s exactly
+      const uint32_t sel = 0x7440u | (uint32_t)(j & 3);
+      const float bnx = fmaf(__uint_as_float(__byte_perm(j < 4 ? nx0 : nx1, 0x4B000000u, sel)), sx, px);
+      const float bfx = fmaf(__uint_as_float(__byte_perm(j < 4 ? fx0 : fx1, 0x4B000000u, sel)), sx, px);
+      const float bny = fmaf(__uint_as_float(__byte_perm(j < 4 ? ny0 : ny1, 0x4B000000u, sel)), sy, py);
+      const float bfy = fmaf(__uint_as_float(__byte_perm(j < 4 ? fy0 : fy1, 0x4B000000u, sel)), sy, py);
+      const float bnz = fmaf(__uint_as_float(__byte_perm(j < 4 ? nz0 : nz1, 0x4B000000u, sel)), sz, pz);
+      const float bfz = fmaf(__uint_as_float(__byte_perm(j < 4 ? fz0 : fz1, 0x4B000000u, sel)), sz, pz);
+      const float lo = fmaxf(fmaxf((bnx - o.x) * id.x, (bny - o.y) * id.y), fmaxf((bnz - o.z) * id.z, s.t_min));
+      const float hi =
+          fminf(fminf(fminf((bfx - o.x) * id.x, (bfy - o.y) * id.y), (bfz - o.z) * id.z) * kBoxInflate, s.t_best);
+      if (lo <= hi && (valid >> j & 1u)) {
+        const uint32_t bit = 1u << (j ^ oct);
+        if (imask >> j & 1u) hit_i |= bit;
+        else hit_l |= bit;
+      }
+    }
+    s.g_base = w1.x;
+    s.g_bits = (imask << 8) | hit_i;
+    s.t_base = w1.y;
+    s.t_bits = ((valid & ~imask) << 8) | hit_l;
+    return;
+  }
+  if (s.sp) {
+    const uint2 e = stack[--s.sp];
+    s.g_base = e.x;
+    s.g_bits = e.y;
+  } else {
+    s.node = kNone;
+  }
 }
 
 // ---------------------------------------------------------------------------
-// trace: closest hit of every queued ray; multipath visibility of the
-// air-path return (Sec. III-A) for hits at bounce >= 1
-template <bool kCount, int kBlock>
-__global__ void __launch_bounds__(kBlock) k_trace(ScanArgs a, uint32_t bounce) {
-  const uint32_t n = a.ctr->count[bounce];
-  const uint32_t tiles = (n + kShadeBlock - 1) / kShadeBlock;
+// Queries of one bounce.  kAny = false: the closest hit of every queued ray.
+// kAny = true: the visibility test of the air-path return (Sec. III-A) for the
+// jobs k_vis_prep listed.  Persistent: a warp claims jobs in chunks and hands
+// them to its idle lanes once at least `refill` lanes are idle (or all are),
+// so the lanes stay busy however uneven the query lengths are.
+constexpr uint32_t kClaim = 32;
+
+template <bool kAny, int kBlock, bool kWide>
+__global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
+  typedef typename std::conditional<kWide, uint2, uint32_t>::type StackEntry;
+  ScanCounters* C = a.ctr;
+  const uint32_t n = kAny ? C->vis_count[bounce] : C->count[bounce];
+  uint32_t* ticket = kAny ? &C->vis_ticket[bounce] : &C->trace_ticket[bounce];
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
-  for (uint32_t t = gtid; t < tiles; t += gsz) a.tile_status[t] = 0ull;
+  if (!kAny) {
+    const uint32_t tiles = (n + kShadeBlock - 1) / kShadeBlock;
+    for (uint32_t t = gtid; t < tiles; t += gsz) a.tile_status[t] = 0ull;
+  }
   const RayRec* __restrict__ q = a.rays[bounce & 1];
+  const uint2* __restrict__ jobs = reinterpret_cast<const uint2*>(a.rays[(bounce + 1) & 1]);
+  // after a failed build every query ends at once as a miss and the scan fails
+  const bool bvh_ok = a.bvh_status == nullptr || *a.bvh_status == 0u;
+  if (!bvh_ok && gtid == 0) atomicOr(&C->error, kErrBvh);
+  const bool count = (a.any_flags & RR_COUNT_TRAVERSAL) != 0u;
   const int lane = threadIdx.x & 31;
-  uint32_t n_closest = 0, n_any = 0, n_nodes = 0, n_tris = 0;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t refill = a.refill;
+  Trav s;
+  s.node = kNone;
+  StackEntry stack[kStack];
+  uint32_t ray_i = kNone;   // ray of the lane's query (kNone: idle)
+  uint32_t tag = 0u;        // any hit: azimuth << 16 | scan
+  float wa = 0.0f;          // any hit: W(omega_a) of the candidate
+  uint32_t c_base = 0u, c_end = 0u;   // claimed, unassigned jobs (warp-uniform)
+  bool exhausted = false;             // the job list is used up (warp-uniform)
+  uint32_t n_done = 0, n_nodes = 0, n_tris = 0;
   while (true) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&a.ctr->trace_ticket[bounce], 32u);
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (base >= n) break;
-    const uint32_t i = base + lane;
-    if (i >= n) continue;
-    const RayRec ray = q[i];
-    const float3 o = f3(ray.o_L), d = f3(ray.d_E);
-    const uint2 sm = ray_scan_medium(a, ray.meta.w);
-    const uint32_t medium = sm.y;
-    const ScanDesc* sd = a.desc + sm.x;
-    const float4 phys = __ldg(&sd->phys);   // t_min, min_energy, freq, r_lim
-    const uint32_t flags = __ldg(&sd->rng.w);
-    const float n_cur = medium == kAir ? 1.0f : __ldg(&a.mats[medium].n);
-    float t = (phys.w - ray.o_L.w) / n_cur;   // past it no return can reach the image
-    uint32_t visits = 0;
-    const uint32_t leaf = traverse<false, kCount>(a, o, d, phys.x, t, ray.meta.x, n_nodes, n_tris, visits);
-    ++n_closest;
-    HitRec h;
-    h.t = leaf == kNone ? INFINITY : t;
-    h.leaf = leaf;
-    h.flags = min(visits, 0xFFFFFFu) << 8;   // bits 8..31: node visits (diagnostics)
-    h.wa_g = 0.0f;
-    if ((flags & RR_MULTIPATH) && bounce >= 1 && leaf != kNone) {
-      const float4* tp = a.tri + 3 * (size_t)leaf;
-      const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-      const MatDev m = a.mats[__float_as_uint(v1.w)];
-      float3 nrm = normalize(cross(f3(v1) - f3(v0), f3(v2) - f3(v0)));
-      float cos_i = -dot(d, nrm);
-      const bool entering = cos_i > 0.0f;
-      float n2 = m.n;
-      if (!entering) {
-        nrm = -nrm;
-        cos_i = -cos_i;
-        n2 = 1.0f;
-      }
-      const float3 p = o + t * d;
-      const float3 s_pos = f3(__ldg(&sd->pos_rmax));
-      const float3 v = s_pos - p;
-      const float dist = length(v);
-      const float side = dot(v, nrm);
-      float3 dir_out = make_float3(0.f, 0.f, 0.f);
-      bool cand = false;
-      if (entering && medium == kAir) {
-        dir_out = normalize(d + (2.0f * cos_i) * nrm);
-        cand = side > 0.0f;
-      } else if (!entering && medium != kAir && !m.pec) {
-        const float eta = n_cur / n2;
-        const float sin2_t = eta * eta * (1.0f - cos_i * cos_i);
-        if (sin2_t < 1.0f) {
-          const float cos_t = sqrtf(1.0f - sin2_t);
-          dir_out = normalize(eta * d + (eta * cos_i - cos_t) * nrm);
-          cand = side < 0.0f;
+    const bool idle = ray_i == kNone;
+    const uint32_t im = __ballot_sync(0xFFFFFFFFu, idle);
+    if (im != 0u && !exhausted && ((uint32_t)__popc(im) >= refill || im == 0xFFFFFFFFu)) {
+      const uint32_t need = (uint32_t)__popc(im), rank = (uint32_t)__popc(im & lt);
+      const uint32_t avail = c_end - c_base;
+      uint32_t job = kNone;
+      if (idle && rank < avail) job = c_base + rank;
+      if (need <= avail) {
+        c_base += need;
+      } else {
+        c_base = c_end;
+        const uint32_t more = need - avail, chunk = max(more, kClaim);
+        uint32_t b = 0;
+        if (lane == 0) b = atomicAdd(ticket, chunk);
+        b = __shfl_sync(0xFFFFFFFFu, b, 0);
+        if (b >= n) {
+          exhausted = true;
+        } else {
+          const uint32_t e = (n - b > chunk) ? b + chunk : n;
+          if (idle && rank >= avail && b + (rank - avail) < e) job = b + (rank - avail);
+          c_base = min(b + more, e);
+          c_end = e;
         }
       }
-      if (cand) {
-        const float4 beam = __ldg(&sd->beam);
-        const float wa = brdf_window(m, a.lut + (size_t)__float_as_uint(v1.w) * (kLutCells + 1),
-                                     angle_between(dir_out, v), beam.x);
-        if (wa > 0.0f) {
-          float t_s = dist;
-          uint32_t vis_visits = 0;
-          const uint32_t occ =
-              traverse<true, kCount>(a, p, (1.0f / dist) * v, phys.x, t_s, leaf, n_nodes, n_tris, vis_visits);
-          ++n_any;
-          h.flags |= 1u;
-          if (occ == kNone) {
-            h.flags |= 2u;
-            const float sigma = d3_sigma(beam.x, beam.y);
-            const float delta = angle_between(p - s_pos, beam_axis(sd, ray.meta.y >> 16));
-            const float g = sigma > 0.0f ? expf(-0.5f * (delta / sigma) * (delta / sigma)) : 0.0f;
-            h.wa_g = wa * g;
-          }
+      if (job != kNone) {
+        if (kAny) {
+          const uint2 jb = jobs[job];
+          ray_i = jb.x;
+          wa = __uint_as_float(jb.y);
+          const RayRec ray = q[ray_i];
+          const HitRec h = a.hits[ray_i];
+          const uint2 sm = ray_scan_medium(a, ray.meta.w);
+          const ScanDesc* sd = a.desc + sm.x;
+          const float3 o = f3(ray.o_L), d = f3(ray.d_E);
+          const float3 p = o + h.t * d;
+          const float3 v = f3(__ldg(&sd->pos_rmax)) - p;
+          const float dist = length(v);
+          trav_begin(s, p, (1.0f / dist) * v, __ldg(&sd->phys.x), dist, h.leaf, a.n_tris, kWide);
+          tag = (ray.meta.y & 0xFFFF0000u) | sm.x;
+        } else {
+          ray_i = job;
+          const RayRec ray = q[ray_i];
+          const uint2 sm = ray_scan_medium(a, ray.meta.w);
+          const float4 phys = __ldg(&a.desc[sm.x].phys);   // t_min, min_energy, freq, r_lim
+          const float n_cur = sm.y == kAir ? 1.0f : __ldg(&a.mats[sm.y].n);
+          // past t_lim no return can reach the image
+          trav_begin(s, f3(ray.o_L), f3(ray.d_E), phys.x, (phys.w - ray.o_L.w) / n_cur, ray.meta.x, a.n_tris,
+                     kWide);
         }
+        if (!bvh_ok) s.node = kNone;
       }
     }
-    a.hits[i] = h;
+    const bool busy = ray_i != kNone;
+    if (!__any_sync(0xFFFFFFFFu, busy)) {
+      if (exhausted) break;
+      continue;
+    }
+    if (busy) {
+      if (s.node != kNone) {
+        if (kWide) step_wide<kAny>(s, reinterpret_cast<uint2*>(stack), a, n_nodes, n_tris, count);
+        else step_binary<kAny>(s, reinterpret_cast<uint32_t*>(stack), a, n_nodes, n_tris, count);
+      }
+      if (s.node == kNone) {   // the query has ended
+        if (kAny) {
+          HitRec* hp = a.hits + ray_i;
+          uint32_t fl = hp->flags | 1u;
+          float wag = 0.0f;
+          if (s.best == kNone) {   // the sensor is visible from the hit point
+            fl |= 2u;
+            const ScanDesc* sd = a.desc + (tag & 0xFFFFu);
+            const float4 beam = __ldg(&sd->beam);
+            const float sigma = d3_sigma(beam.x, beam.y);
+            const float3 p = s.w.o;
+            const float delta = angle_between(p - f3(__ldg(&sd->pos_rmax)), beam_axis(sd, tag >> 16));
+            const float g = sigma > 0.0f ? expf(-0.5f * (delta / sigma) * (delta / sigma)) : 0.0f;
+            wag = wa * g;
+          }
+          hp->flags = fl;
+          hp->wa_g = wag;
+        } else {
+          HitRec h;
+          h.t = s.best == kNone ? INFINITY : s.t_best;
+          h.leaf = s.best;
+          h.flags = min(s.visits, 0xFFFFFFu) << 8;   // bits 8..31: node visits (diagnostics)
+          h.wa_g = 0.0f;
+          a.hits[ray_i] = h;
+        }
+        ++n_done;
+        ray_i = kNone;
+      }
+    }
   }
   // counters, one atomic per warp
-  for (int off = 16; off > 0; off >>= 1) {
-    n_closest += __shfl_xor_sync(0xFFFFFFFFu, n_closest, off);
-    n_any += __shfl_xor_sync(0xFFFFFFFFu, n_any, off);
-  }
-  if (lane == 0) {
-    if (n_closest) atomicAdd(&a.ctr->stat_closest, (unsigned long long)n_closest);
-    if (n_any) atomicAdd(&a.ctr->stat_anyhit, (unsigned long long)n_any);
-  }
-  if (kCount) {
+  for (int off = 16; off > 0; off >>= 1) n_done += __shfl_xor_sync(0xFFFFFFFFu, n_done, off);
+  if (lane == 0 && n_done) atomicAdd(kAny ? &C->stat_anyhit : &C->stat_closest, (unsigned long long)n_done);
+  if (count) {
     unsigned long long nn = n_nodes, nt = n_tris;
     for (int off = 16; off > 0; off >>= 1) {
       nn += __shfl_xor_sync(0xFFFFFFFFu, nn, off);
       nt += __shfl_xor_sync(0xFFFFFFFFu, nt, off);
     }
     if (lane == 0) {
-      atomicAdd(&a.ctr->stat_nodes, nn);
-      atomicAdd(&a.ctr->stat_tris, nt);
+      atomicAdd(kAny ? &C->stat_nodes_any : &C->stat_nodes, nn);
+      atomicAdd(kAny ? &C->stat_tris_any : &C->stat_tris, nt);
+    }
+  }
+}
+
+// Candidates of the air-path return (Sec. III-A) at bounce >= 1: the mean
+// reflection direction (or, leaving a medium into air, the refracted one)
+// against the direction to the sensor, through the beam window of the lobe.
+// Rays whose window is open become jobs (ray, W) of the visibility query,
+// appended with one atomic per warp into the free ray buffer of the next
+// bounce (order does not matter: each job names its ray).
+__global__ void __launch_bounds__(256) k_vis_prep(ScanArgs a, uint32_t bounce) {
+  ScanCounters* C = a.ctr;
+  const uint32_t n = C->count[bounce];
+  const RayRec* __restrict__ q = a.rays[bounce & 1];
+  uint2* __restrict__ jobs = reinterpret_cast<uint2*>(a.rays[(bounce + 1) & 1]);
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u, wstride = gridDim.x * blockDim.x;
+  for (uint32_t base = warp0; base < n; base += wstride) {
+    const uint32_t i = base + lane;
+    bool want = false;
+    float wa = 0.0f;
+    if (i < n) {
+      const HitRec h = a.hits[i];
+      if (h.leaf != kNone && h.leaf < a.n_tris) {
+        const RayRec ray = q[i];
+        const uint2 sm = ray_scan_medium(a, ray.meta.w);
+        const uint32_t medium = sm.y;
+        const ScanDesc* sd = a.desc + sm.x;
+        if (__ldg(&sd->rng.w) & RR_MULTIPATH) {
+          const float3 o = f3(ray.o_L), d = f3(ray.d_E);
+          const float n_cur = medium == kAir ? 1.0f : __ldg(&a.mats[medium].n);
+          const float4* tp = a.tri + 3 * (size_t)h.leaf;
+          const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+          const MatDev m = a.mats[__float_as_uint(v1.w)];
+          float3 nrm = normalize(cross(f3(v1) - f3(v0), f3(v2) - f3(v0)));
+          float cos_i = -dot(d, nrm);
+          const bool entering = cos_i > 0.0f;
+          float n2 = m.n;
+          if (!entering) {
+            nrm = -nrm;
+            cos_i = -cos_i;
+            n2 = 1.0f;
+          }
+          const float3 p = o + h.t * d;
+          const float3 v = f3(__ldg(&sd->pos_rmax)) - p;
+          const float side = dot(v, nrm);
+          float3 dir_out = make_float3(0.f, 0.f, 0.f);
+          bool cand = false;
+          if (entering && medium == kAir) {
+            dir_out = normalize(d + (2.0f * cos_i) * nrm);
+            cand = side > 0.0f;
+          } else if (!entering && medium != kAir && !m.pec) {
+            const float eta = n_cur / n2;
+            const float sin2_t = eta * eta * (1.0f - cos_i * cos_i);
+            if (sin2_t < 1.0f) {
+              const float cos_t = sqrtf(1.0f - sin2_t);
+              dir_out = normalize(eta * d + (eta * cos_i - cos_t) * nrm);
+              cand = side < 0.0f;
+            }
+          }
+          if (cand) {
+            wa = brdf_window(m, a.lut + (size_t)__float_as_uint(v1.w) * (kLutCells + 1), angle_between(dir_out, v),
+                             __ldg(&sd->beam.x));
+            want = wa > 0.0f;
+          }
+        }
+      }
+    }
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
+    if (m) {
+      uint32_t b = 0;
+      if (lane == __ffs(m) - 1) b = atomicAdd(&C->vis_count[bounce], (uint32_t)__popc(m));
+      b = __shfl_sync(0xFFFFFFFFu, b, __ffs(m) - 1);
+      if (want) jobs[b + __popc(m & lt)] = make_uint2(i, __float_as_uint(wa));
     }
   }
 }
@@ -452,8 +692,8 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
       float tal[4] = {0.f, 0.f, 0.f, 0.f};
       float dbg_cos = 0.f, dbg_ret_t = 0.f, dbg_ret_a = 0.f;
       uint32_t orig = kNone;
-      if (h.leaf == kNone) {
-        tal[2] = E;   // escaped (or beyond the range limit)
+      if (h.leaf == kNone || h.leaf >= a.n_tris) {
+        tal[2] = E;   // escaped (or beyond the range limit); an index past the triangles only after a failed step
       } else {
         const float3 o = f3(ray.o_L), d = f3(ray.d_E);
         const float4 pr = __ldg(&sd->pos_rmax);
@@ -655,15 +895,25 @@ namespace rr_host {
 using namespace rr;
 
 static int g_num_sms = 0;
-static int g_trace_occ[2][3] = {{0}};   // [counting][block 64 / 128 / 256]
+static int g_query_occ[2][2][3] = {{{0}}};   // [wide][any][block 64 / 128 / 256]
 static int g_shade_occ = 0;
 
 static int block_index(uint32_t block) { return block <= 64u ? 0 : (block <= 128u ? 1 : 2); }
 
-template <bool kCount, int kBlock>
+template <bool kAny, int kBlock, bool kWide>
 static void occ_of(int* out) {
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_trace<kCount, kBlock>, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_query<kAny, kBlock, kWide>, kBlock, 0);
   if (*out < 1) *out = 1;
+}
+
+template <bool kWide>
+static void occ_all(int (*o)[3]) {
+  occ_of<false, 64, kWide>(&o[0][0]);
+  occ_of<false, 128, kWide>(&o[0][1]);
+  occ_of<false, 256, kWide>(&o[0][2]);
+  occ_of<true, 64, kWide>(&o[1][0]);
+  occ_of<true, 128, kWide>(&o[1][1]);
+  occ_of<true, 256, kWide>(&o[1][2]);
 }
 
 void init_dims() {
@@ -671,12 +921,8 @@ void init_dims() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  occ_of<false, 64>(&g_trace_occ[0][0]);
-  occ_of<false, 128>(&g_trace_occ[0][1]);
-  occ_of<false, 256>(&g_trace_occ[0][2]);
-  occ_of<true, 64>(&g_trace_occ[1][0]);
-  occ_of<true, 128>(&g_trace_occ[1][1]);
-  occ_of<true, 256>(&g_trace_occ[1][2]);
+  occ_all<false>(g_query_occ[0]);
+  occ_all<true>(g_query_occ[1]);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_shade_occ, k_shade, kShadeBlock, 0);
   if (g_shade_occ < 1) g_shade_occ = 1;
   g_num_sms = sms < 1 ? 1 : sms;
@@ -687,9 +933,9 @@ int num_sms() {
   return g_num_sms;
 }
 
-int trace_max_blocks_per_sm(uint32_t block) {
+int trace_max_blocks_per_sm(uint32_t block, bool wide) {
   init_dims();
-  return g_trace_occ[0][block_index(block)];
+  return g_query_occ[wide ? 1 : 0][0][block_index(block)];
 }
 
 cudaError_t launch_raygen(const ScanArgs& a, cudaStream_t st) {
@@ -698,22 +944,33 @@ cudaError_t launch_raygen(const ScanArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <bool kCount>
-static void trace_launch(const ScanArgs& a, uint32_t bounce, int bi, int grid, cudaStream_t st) {
-  if (bi == 0) k_trace<kCount, 64><<<grid, 64, 0, st>>>(a, bounce);
-  else if (bi == 1) k_trace<kCount, 128><<<grid, 128, 0, st>>>(a, bounce);
-  else k_trace<kCount, 256><<<grid, 256, 0, st>>>(a, bounce);
+template <bool kAny, bool kWide>
+static void query_launch(const ScanArgs& a, uint32_t bounce, int bi, int grid, cudaStream_t st) {
+  if (bi == 0) k_query<kAny, 64, kWide><<<grid, 64, 0, st>>>(a, bounce);
+  else if (bi == 1) k_query<kAny, 128, kWide><<<grid, 128, 0, st>>>(a, bounce);
+  else k_query<kAny, 256, kWide><<<grid, 256, 0, st>>>(a, bounce);
 }
 
-cudaError_t launch_trace(const ScanArgs& a, uint32_t bounce, const LaunchCfg& c, cudaStream_t st) {
+cudaError_t launch_query(const ScanArgs& a, uint32_t bounce, bool any, const LaunchCfg& c, cudaStream_t st) {
   init_dims();
-  const bool count = (a.any_flags & RR_COUNT_TRAVERSAL) != 0u;
+  const bool wide = a.wide != 0u;
   const int bi = block_index(c.trace_block);
-  int per_sm = g_trace_occ[count ? 1 : 0][bi];
+  int per_sm = g_query_occ[wide ? 1 : 0][any ? 1 : 0][bi];
   if (c.trace_blocks_per_sm > 0 && (int)c.trace_blocks_per_sm < per_sm) per_sm = (int)c.trace_blocks_per_sm;
   const int grid = g_num_sms * per_sm;
-  if (count) trace_launch<true>(a, bounce, bi, grid, st);
-  else trace_launch<false>(a, bounce, bi, grid, st);
+  if (wide) {
+    if (any) query_launch<true, true>(a, bounce, bi, grid, st);
+    else query_launch<false, true>(a, bounce, bi, grid, st);
+  } else {
+    if (any) query_launch<true, false>(a, bounce, bi, grid, st);
+    else query_launch<false, false>(a, bounce, bi, grid, st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vis_prep(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
+  init_dims();
+  k_vis_prep<<<g_num_sms * 8, 256, 0, st>>>(a, bounce);
   return cudaGetLastError();
 }
 

@@ -24,8 +24,8 @@ RR_OK, RR_ERR_INVALID_ARG, RR_ERR_OOM, RR_ERR_CAPACITY, RR_ERR_TIMEOUT, RR_ERR_C
 RR_MULTIPATH, RR_REFRACTION, RR_SPECKLE, RR_NOISE, RR_COUNT_TRAVERSAL = 1, 2, 4, 8, 16
 RR_MAT_PERFECT_CONDUCTOR = 1
 RR_NO_HIT = 0xFFFFFFFF
-RR_K_RAYGEN, RR_K_TRACE, RR_K_SHADE, RR_K_IMAGE, RR_K_BUILD, RR_K_COUNT = range(6)
-KERNEL_NAMES = ["raygen", "trace", "shade", "image", "build"]
+RR_K_RAYGEN, RR_K_TRACE, RR_K_SHADE, RR_K_IMAGE, RR_K_BUILD, RR_K_VIS, RR_K_COUNT = range(7)
+KERNEL_NAMES = ["raygen", "trace", "shade", "image", "build", "vis"]
 
 
 class RRError(RuntimeError):
@@ -65,14 +65,15 @@ SEGMENT_DTYPE = np.dtype([("az", "<u4"), ("k", "<u4"), ("path", "<u4"), ("bounce
 
 class rr_scene_info(C.Structure):
     _fields_ = [("n_triangles", C.c_uint32), ("n_materials", C.c_uint32), ("bvh_depth", C.c_uint32),
-                ("reserved", C.c_uint32), ("device_bytes", C.c_uint64), ("workspace_bytes", C.c_uint64),
+                ("n_wide_nodes", C.c_uint32), ("device_bytes", C.c_uint64), ("workspace_bytes", C.c_uint64),
                 ("build_ms", C.c_float), ("reserved_f", C.c_float)]
 
 
 class rr_stats(C.Structure):
     _fields_ = [("closest_queries", C.c_uint64), ("anyhit_queries", C.c_uint64), ("returns", C.c_uint64),
                 ("scans", C.c_uint64), ("nodes_visited", C.c_uint64), ("tris_tested", C.c_uint64),
-                ("kernel_launches", C.c_uint64)]
+                ("kernel_launches", C.c_uint64), ("anyhit_nodes_visited", C.c_uint64),
+                ("anyhit_tris_tested", C.c_uint64)]
 
 
 class rr_profile(C.Structure):
@@ -81,7 +82,12 @@ class rr_profile(C.Structure):
 
 class rr_batch_config(C.Structure):
     _fields_ = [("wavefront_rays", C.c_uint32), ("trace_block", C.c_uint32), ("trace_blocks_per_sm", C.c_uint32),
-                ("use_graph", C.c_uint32), ("workspace_limit", C.c_uint64)]
+                ("use_graph", C.c_uint32), ("node_format", C.c_uint32), ("refill_threshold", C.c_uint32),
+                ("workspace_limit", C.c_uint64)]
+
+
+RR_NODES_WIDE8, RR_NODES_BINARY = 0, 1
+WIDE_NODE_BYTES = 80
 
 
 # every symbol declared in include/rr.h with its ctypes signature
@@ -95,6 +101,7 @@ SIGNATURES = {
     "rr_scene_update_vertices": ([_P, _P], C.c_int),
     "rr_scene_info_get": ([_P, C.POINTER(rr_scene_info)], C.c_int),
     "rr_scene_export_bvh": ([_P, _P, _P, _P, _P, _P], C.c_int),
+    "rr_scene_export_wide": ([_P, _P, C.c_uint32, C.POINTER(C.c_uint32), _P], C.c_int),
     "rr_scan": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P], C.c_int),
     "rr_scan_async": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P], C.c_int),
     "rr_scene_sync": ([_P], C.c_int),
@@ -243,6 +250,18 @@ def rr_scene_export_bvh(scene, n_triangles: int) -> dict:
     return out
 
 
+def rr_scene_export_wide(scene, n_triangles: int) -> dict:
+    """nodes: [n, 80] uint8 raw node records, tris: [T, 3, 4] float32 in wide-leaf order."""
+    _use_torch_stream()
+    L = load()
+    n = C.c_uint32()
+    _check(L.rr_scene_export_wide(scene, None, 0, C.byref(n), None))
+    nodes = np.zeros((n.value, WIDE_NODE_BYTES), np.uint8)
+    tris = np.zeros((int(n_triangles), 3, 4), np.float32)
+    _check(L.rr_scene_export_wide(scene, _ptr(nodes), n.value, C.byref(n), _ptr(tris)))
+    return {"nodes": nodes, "tris": tris}
+
+
 def rr_scan(scene, pose: dict, params: dict, out_polar) -> None:
     _use_torch_stream()
     P, S = make_pose(pose), make_params(params)
@@ -315,7 +334,8 @@ def rr_batch_plan(params, config: dict | None = None):
     S = (rr_sensor_params * n)(*[make_params(s) for s in params])
     cfg = None
     if config is not None:
-        full = dict(wavefront_rays=0, trace_block=128, trace_blocks_per_sm=0, use_graph=1, workspace_limit=0)
+        full = dict(wavefront_rays=0, trace_block=128, trace_blocks_per_sm=0, use_graph=1, node_format=1,
+                    refill_threshold=8, workspace_limit=0)
         full.update(config)
         cfg = C.byref(rr_batch_config(*[int(full[k]) for k, _ in rr_batch_config._fields_]))
     cap = max(n, 1)

@@ -52,6 +52,8 @@ int main(void) {
          sizeof(rr_segment), sizeof(rr_scene_info), sizeof(rr_stats), sizeof(rr_profile));
   printf("%zu %zu %zu\n", offsetof(rr_sensor_params, seed), offsetof(rr_sensor_params, scan_id),
          offsetof(rr_sensor_params, flags));
+  printf("%zu %zu %zu\n", sizeof(rr_batch_config), offsetof(rr_batch_config, node_format),
+         offsetof(rr_batch_config, workspace_limit));
   return 0;
 }
 '''
@@ -65,8 +67,10 @@ int main(void) {
     assert sizes == [C.sizeof(rr.rr_material), C.sizeof(rr.rr_pose), C.sizeof(rr.rr_sensor_params),
                      C.sizeof(rr.rr_segment), C.sizeof(rr.rr_scene_info), C.sizeof(rr.rr_stats),
                      C.sizeof(rr.rr_profile)]
-    assert [int(x) for x in out[7:]] == [rr.rr_sensor_params.seed.offset, rr.rr_sensor_params.scan_id.offset,
-                                        rr.rr_sensor_params.flags.offset]
+    assert [int(x) for x in out[7:10]] == [rr.rr_sensor_params.seed.offset, rr.rr_sensor_params.scan_id.offset,
+                                          rr.rr_sensor_params.flags.offset]
+    assert [int(x) for x in out[10:13]] == [C.sizeof(rr.rr_batch_config), rr.rr_batch_config.node_format.offset,
+                                           rr.rr_batch_config.workspace_limit.offset]
     assert rr.SEGMENT_DTYPE.itemsize == C.sizeof(rr.rr_segment)
 
 

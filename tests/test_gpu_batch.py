@@ -159,8 +159,10 @@ def test_batch_counters(tiny_scene):
     rr.rr_scan_batch(h, poses, params, device_outputs(params))
     st = rr.rr_scene_stats(h)
     assert st["scans"] == len(params)
-    # one launch sequence: raygen, trace + shade per bounce, bin columns, pattern
-    assert st["kernel_launches"] == 2 + 2 * max(p["max_bounces"] for p in params) + 1
+    # one launch sequence: raygen, closest-hit query + shade per bounce,
+    # visibility preparation + any-hit query from bounce 1 on, bin columns, pattern
+    mb = max(p["max_bounces"] for p in params)
+    assert st["kernel_launches"] == 2 + 2 * mb + 2 * (mb - 1) + 1
     n0 = sum(p["n_azimuth"] * p["rays_per_beam"] for p in params)
     assert st["closest_queries"] >= n0
 
