@@ -240,6 +240,106 @@ def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: 
     }
 
 
+# ------------------------------------------------------------------ served
+SERVED_WORKLOAD = "4_scenes_50k_200k_1M_5M_tris_64_robots_poisson_16_512_rays_3_8_bounces_500_4000_bins"
+
+
+def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: int = 0):
+    """Scan requests from 64 simulated robots over 4 resident scenes (50k and
+    200k-triangle campuses, the 1M-triangle campus, the 5M-triangle city),
+    Poisson arrivals at each rate for `seconds`; every request draws a free
+    random pose of its robot's scene, rays per beam U{16..512}, bounces
+    U{3..8} and bins U{500..4000}.  Served by the continuous-batching server
+    (4 slots) and, for comparison, by a server that runs one request at a time
+    (the plain per-scan path).  Latency = submit to completion as the server
+    records it; Mrays/s = closest-hit queries / window (arrivals + drain).
+    The configured rates are 30, 60 and 120 requests/s; 240 is added to show
+    the servers near saturation."""
+    import torch
+    from paper_2310_03505_gb300 import rr, scenes
+    scs = [(scenes.campus(target_tris=50_000, seed=0x5EED0004, n_buildings=60, n_cylinders=150, extent=80.0), 70.0),
+           (scenes.campus(), 140.0), (scenes.campus(target_tris=1_000_000), 140.0), (scenes.city(), 290.0)]
+    hs = [rr.rr_scene_create(torch.from_numpy(sc.vertices).to(device), sc.triangles, sc.material_ids, sc.materials)
+          for sc, _ in scs]
+    torch.cuda.synchronize()
+    max_img = 400 * 4000
+    pool = torch.zeros(256, max_img, device=device)
+
+    def request(rng, robot, sid):
+        si = robot % len(scs)
+        sc, ext = scs[si]
+        p = scenes.sensor(n_azimuth=400, rays_per_beam=int(rng.integers(16, 513)),
+                          max_bounces=int(rng.integers(3, 9)), n_bins=int(rng.integers(500, 4001)),
+                          bin_size=0.0438, beam_width=math.radians(10.0), seed=0x5EED0005 + robot, scan_id=sid)
+        return si, scenes.random_pose(sc, rng, 1.8, ext), p
+
+    def run(cfg, rate, seed):
+        sv = rr.rr_serve_create(**cfg)
+        rng = np.random.default_rng(seed)
+        try:
+            # warm-up: one request per scene
+            for si in range(len(scs)):
+                _, pz, p = request(rng, si, 10 ** 6 + si)
+                t = rr.rr_serve_submit(sv, hs[si], pz, p, pool[0, :p["n_azimuth"] * p["n_bins"]])
+                rr.rr_serve_wait(sv, t, 120_000)
+                rr.rr_serve_result(sv, t)
+            rr.rr_serve_stats_get(sv, reset=True)
+            free = list(range(256))
+            live = {}
+            n_sub = n_busy = 0
+            t0 = time.perf_counter()
+            next_t = t0 + rng.exponential(1.0 / rate)
+            while True:
+                now = time.perf_counter()
+                if now - t0 >= seconds:
+                    break
+                for t in [t for t in live if rr.rr_serve_poll(sv, t)]:
+                    free.append(live.pop(t))
+                    rr.rr_serve_result(sv, t)
+                if now < next_t:
+                    time.sleep(min(next_t - now, 0.0005))
+                    continue
+                next_t += rng.exponential(1.0 / rate)
+                if not free:
+                    n_busy += 1
+                    continue
+                robot = int(rng.integers(0, 64))
+                si, pz, p = request(rng, robot, n_sub)
+                b = free.pop()
+                try:
+                    t = rr.rr_serve_submit(sv, hs[si], pz, p, pool[b, :p["n_azimuth"] * p["n_bins"]])
+                    live[t] = b
+                    n_sub += 1
+                except rr.RRError:
+                    free.append(b)
+                    n_busy += 1
+            for t in list(live):
+                rr.rr_serve_wait(sv, t, 600_000)
+                rr.rr_serve_result(sv, t)
+            st = rr.rr_serve_stats_get(sv)
+        finally:
+            rr.rr_serve_destroy(sv)
+        win = st["elapsed_ms"] * 1e-3
+        return {"offered_req_per_s": rate, "submitted": int(st["submitted"]), "completed": int(st["completed"]),
+                "failed": int(st["failed"]), "refused": int(st["rejected_busy"] + n_busy),
+                "p50_ms": st["latency_p50_ms"], "p99_ms": st["latency_p99_ms"], "mean_ms": st["latency_mean_ms"],
+                "max_ms": st["latency_max_ms"], "mrays_per_s": st["closest_queries"] / win / 1e6,
+                "busy_fraction": st["busy_ms"] / max(st["elapsed_ms"], 1e-9), "batches": int(st["batches"]),
+                "window_s": win}
+
+    served = dict(slots=4, memory_budget=96 << 30, max_batch_scans=64, max_batch_rays=8 << 20)
+    plain = dict(slots=1, memory_budget=24 << 30, max_batch_scans=1)
+    out = {"workload": SERVED_WORKLOAD, "seconds_per_rate": seconds,
+           "scenes_triangles": [sc.n_triangles for sc, _ in scs], "robots": 64,
+           "server": {k: int(v) for k, v in served.items()}, "rates": [], "per_scan_path": []}
+    for k, rate in enumerate(rates):
+        out["rates"].append(run(served, rate, 1000 + k))
+        out["per_scan_path"].append(run(plain, rate, 1000 + k))
+    for h in hs:
+        rr.rr_scene_destroy(h)
+    return out
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -253,6 +353,9 @@ def main():
     ap.add_argument("--node-format", default="auto", choices=["auto", "wide", "binary"],
                     help="BVH node format of the plain scan (auto: the library default)")
     ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-seconds", type=float, default=10.0,
+                    help="arrival window per request rate of the served workload")
     args = ap.parse_args()
     world, rank, local = dist_env()
 
@@ -391,6 +494,9 @@ def main():
     batched = None
     if not args.no_batched:
         batched = batched_bench(device, stream, flush, steps=args.batched_steps, rank=rank)
+    served = None
+    if not args.no_served and rank == 0:
+        served = served_bench(device, seconds=args.served_seconds, rank=rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -424,7 +530,7 @@ def main():
                          "launches_per_step": trace_launches / max(args.steps, 1),
                          "ms_per_launch": trace_ms / max(trace_launches, 1)},
             "visibility_queries": {"nodes_per_query": any_nodes_per_q, "tris_per_query": any_tris_per_q},
-            "batched": batched,
+            "batched": batched, "served": served,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["kernel_launches"]),
             "kernels_per_step": kernels_per_step, "clocks": clk, "wall_s_timed": wall,
             "status": "ok" if rc_status is None else str(rc_status),

@@ -369,6 +369,95 @@ int rr_scan_static(rr_scene* scene, const rr_pose* pose, const rr_sensor_params*
 int rr_polar_to_db_u8(const float* polar, uint64_t n, float cutoff_db, uint8_t* out);
 
 /* ---------------------------------------------------------------------- */
+/* serving: resident scenes, requests from many clients, continuous        */
+/* batching (the paper has no counterpart; it serves the same scans)       */
+/* ---------------------------------------------------------------------- */
+typedef struct rr_server rr_server; /* opaque */
+
+/* memory_budget    device bytes the server holds for work in flight, split
+                    evenly into one fixed arena per slot when the server is
+                    created (0: 16 GiB); nothing is allocated while serving
+   slots            launch sequences in flight at once, each on its own
+                    stream (1..16; 0: 4)
+   max_batch_scans  most requests per launch sequence (0: 64)
+   max_batch_rays   most initial rays per launch sequence (0: 4 Mi); a
+                    single larger request still runs alone
+   max_queue        most requests waiting for a slot (0: 4096); beyond it
+                    rr_serve_submit returns RR_ERR_BUSY
+   node_format, refill_threshold   as in rr_batch_config */
+typedef struct {
+  uint64_t memory_budget;
+  uint32_t slots;
+  uint32_t max_batch_scans;
+  uint32_t max_batch_rays;
+  uint32_t max_queue;
+  uint32_t node_format;
+  uint32_t refill_threshold;
+} rr_serve_config;
+
+/* request states */
+#define RR_REQ_QUEUED 0
+#define RR_REQ_RUNNING 1
+#define RR_REQ_DONE 2
+#define RR_REQ_FAILED 3
+
+/* One request: state, status (RR_OK or the failure), times in ms of the
+   host steady clock since the server was created: submitted, launched,
+   completed (observed by the server), and the number of requests of the
+   launch sequence it ran in. */
+typedef struct {
+  int32_t state;
+  int32_t status;
+  double submit_ms, start_ms, done_ms;
+  uint32_t batch_size;
+  uint32_t reserved;
+} rr_serve_record;
+
+/* Since the last reset: requests submitted / completed / failed / refused
+   (queue full), launch sequences, closest-hit and visibility queries traced,
+   initial rays, wall time with work in flight (busy_ms) and elapsed, the
+   requests still queued, and the latency (submit to completion) of the
+   completed requests: median, 99th percentile (nearest rank), mean, max. */
+typedef struct {
+  uint64_t submitted, completed, failed, rejected_busy;
+  uint64_t batches, closest_queries, anyhit_queries, initial_rays;
+  uint64_t queued;
+  double busy_ms, elapsed_ms;
+  double latency_p50_ms, latency_p99_ms, latency_mean_ms, latency_max_ms;
+} rr_serve_stats;
+
+/* Starts a server (its worker thread and slots) on the current device.
+   config may be NULL (all defaults).  Scenes are the caller's: they must stay
+   alive, and unchanged, while requests on them are unfinished. */
+int rr_serve_create(const rr_serve_config* config, rr_server** out);
+
+/* Finishes the requests already submitted, then frees the server.  Records
+   not yet read are lost.  NULL is accepted. */
+int rr_serve_destroy(rr_server* server);
+
+/* Queues one scan (the same as rr_scan of the scene with pose and params)
+   writing out_polar [n_azimuth][n_bins] (host or device; it must stay valid
+   until the request finishes).  Returns at once with a ticket.
+   RR_ERR_INVALID_ARG for bad parameters or a request whose worst-case scratch
+   exceeds a slot's arena, RR_ERR_BUSY when the queue is full. */
+int rr_serve_submit(rr_server* server, rr_scene* scene, const rr_pose* pose, const rr_sensor_params* params,
+                    float* out_polar, uint64_t* ticket);
+
+/* *done = 1 once the request has finished (completed or failed), else 0.
+   Non-blocking. */
+int rr_serve_poll(rr_server* server, uint64_t ticket, int* done);
+
+/* Waits up to timeout_ms for the request; returns its status (RR_OK when it
+   completed), or RR_ERR_TIMEOUT if it is still unfinished. */
+int rr_serve_wait(rr_server* server, uint64_t ticket, uint32_t timeout_ms);
+
+/* The request's record; a finished request's ticket is then forgotten. */
+int rr_serve_result(rr_server* server, uint64_t ticket, rr_serve_record* out);
+
+/* Server statistics (see rr_serve_stats); reset != 0 starts a new window. */
+int rr_serve_stats_get(rr_server* server, rr_serve_stats* out, int reset);
+
+/* ---------------------------------------------------------------------- */
 /* counters                                                                */
 /* ---------------------------------------------------------------------- */
 /* Cumulative query counters of the scene (blocking); reset != 0 clears them. */

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librr.so")
-SOURCES = ["rr_build.cu", "rr_trace.cu", "rr_image.cu", "rr_api.cu", "rr_batch.cu", "rr_static.cu"]
+SOURCES = ["rr_build.cu", "rr_trace.cu", "rr_image.cu", "rr_api.cu", "rr_batch.cu", "rr_serve.cu", "rr_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-rdc=false"]
 

@@ -132,15 +132,15 @@ int check_params(const rr_pose* pose, const rr_sensor_params* p) {
   return RR_OK;
 }
 
-// read (and clear) the sticky device status; requires the stream to be idle
-int device_status(rr_scene* s, cudaStream_t st) {
-  RR_CHECK_CUDA(cudaMemcpyAsync(s->h_ctr, s->d_ctr, sizeof(ScanCounters), cudaMemcpyDeviceToHost, st),
+// read (and clear) the sticky device status of a context; waits for the stream
+int device_status(ExecCtx* x, cudaStream_t st) {
+  RR_CHECK_CUDA(cudaMemcpyAsync(x->h_ctr, x->d_ctr, sizeof(ScanCounters), cudaMemcpyDeviceToHost, st),
                 "reading the scan counters");
   RR_CHECK_CUDA(cudaStreamSynchronize(st), "scan");
-  const uint32_t err = s->h_ctr->error;
+  const uint32_t err = x->h_ctr->error;
   if (err) {
-    RR_CHECK_CUDA(cudaMemsetAsync(&s->d_ctr->error, 0, sizeof(uint32_t), st), "clearing the status");
-    RR_CHECK_CUDA(cudaMemsetAsync(&s->d_ctr->need_rays, 0, 2 * sizeof(uint32_t), st), "clearing the status");
+    RR_CHECK_CUDA(cudaMemsetAsync(&x->d_ctr->error, 0, sizeof(uint32_t), st), "clearing the status");
+    RR_CHECK_CUDA(cudaMemsetAsync(&x->d_ctr->need_rays, 0, 2 * sizeof(uint32_t), st), "clearing the status");
     RR_CHECK_CUDA(cudaStreamSynchronize(st), "clearing the status");
     char msg[256];
     if (err & rr::kErrBadVertex)
@@ -152,13 +152,33 @@ int device_status(rr_scene* s, cudaStream_t st) {
       snprintf(msg, sizeof msg,
                "ray tree outgrew the workspace: %u queued rays and %u return records were needed; raise the "
                "workspace limit",
-               s->h_ctr->need_rays, s->h_ctr->need_recs);
+               x->h_ctr->need_rays, x->h_ctr->need_recs);
       return fail(RR_ERR_CAPACITY, msg);
     }
     if (err & rr::kErrCapacitySegs) return fail(RR_ERR_CAPACITY, "segment buffer too small");
     return fail(RR_ERR_CUDA, "unknown device status");
   }
   return RR_OK;
+}
+
+cudaError_t ctx_init(ExecCtx* x, cudaStream_t st) {
+  cudaError_t e = cudaMalloc((void**)&x->d_ctr, sizeof(ScanCounters));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&x->h_ctr, sizeof(ScanCounters));
+  if (e == cudaSuccess) memset(x->h_ctr, 0, sizeof(ScanCounters));   // the mirror starts equal to the device
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->d_ctr, 0, sizeof(ScanCounters), st);
+  return e;
+}
+
+void ctx_free(ExecCtx* x) {
+  if (x->d_ctr) cudaFree(x->d_ctr);
+  if (x->h_ctr) cudaFreeHost(x->h_ctr);
+  if (x->ws) cudaFree(x->ws);
+  if (x->d_image) cudaFree(x->d_image);
+  if (x->h_stage) cudaFreeHost(x->h_stage);
+  if (x->stage_ev) cudaEventDestroy(x->stage_ev);
+  if (x->gexec) cudaGraphExecDestroy(x->gexec);
+  if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
+  *x = ExecCtx();
 }
 
 }  // namespace rr_host
@@ -189,15 +209,12 @@ int rr_scene_destroy(rr_scene* s) {
   cudaDeviceSynchronize();
   void* ptrs[] = {s->d_vtx, s->d_idx, s->d_mat_id, s->d_raw_mats, s->d_mats, s->d_lut, s->d_lut_cells,
                   s->d_tri, s->d_nodes, s->d_centroid, s->d_keys[0], s->d_keys[1], s->d_vals[0], s->d_vals[1],
-                  s->d_hist, s->d_parent, s->d_child, s->d_nbox, s->d_visit, s->d_misc, s->ws, s->d_ctr,
-                  s->d_image, s->d_cut, s->d_wnodes, s->d_wtri, s->d_wsrc, s->d_wrec, s->d_wctr};
+                  s->d_hist, s->d_parent, s->d_child, s->d_nbox, s->d_visit, s->d_misc,
+                  s->d_cut, s->d_wnodes, s->d_wtri, s->d_wsrc, s->d_wrec, s->d_wctr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  if (s->h_ctr) cudaFreeHost(s->h_ctr);
-  if (s->h_stage) cudaFreeHost(s->h_stage);
-  if (s->stage_ev) cudaEventDestroy(s->stage_ev);
-  if (s->gexec) cudaGraphExecDestroy(s->gexec);
-  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  ctx_free(&s->main);
+  if (s->wide_ready) cudaEventDestroy(s->wide_ready);
   for (auto& ev : s->prof_pending) {
     cudaEventDestroy(ev.start);
     cudaEventDestroy(ev.stop);
@@ -253,12 +270,11 @@ int rr_scene_create(const float* vertices, uint32_t n_vertices, const uint32_t* 
     }
   }
   cudaError_t e = cudaSuccess;
-  if (cudaMalloc((void**)&s->d_ctr, sizeof(ScanCounters)) != cudaSuccess ||
-      cudaMallocHost((void**)&s->h_ctr, sizeof(ScanCounters)) != cudaSuccess) {
+  e = ctx_init(&s->main, st);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return bail(fail(RR_ERR_OOM, "allocating the scan counters"));
   }
-  e = cudaMemsetAsync(s->d_ctr, 0, sizeof(ScanCounters), st);
   if (e == cudaSuccess && n_vertices)
     e = cudaMemcpyAsync(s->d_vtx, vertices, (size_t)n_vertices * 3 * sizeof(float), cudaMemcpyDefault, st);
   if (e == cudaSuccess && n_triangles)
@@ -313,7 +329,7 @@ int rr_scene_update_vertices(rr_scene* s, const float* vertices) {
   prof_end(s, ev, st);
   if (s->nt) {
     s->launches += 1;
-    k_fold_build_status<<<1, 1, 0, st>>>(s->d_misc, s->d_wctr, s->d_ctr);
+    k_fold_build_status<<<1, 1, 0, st>>>(s->d_misc, s->d_wctr, s->main.d_ctr);
     RR_CHECK_CUDA(cudaGetLastError(), "status fold");
   }
   return RR_OK;
@@ -332,7 +348,7 @@ int rr_scene_info_get(const rr_scene* s, rr_scene_info* info) {
     info->n_wide_nodes = n;
   }
   info->device_bytes = s->scene_bytes;
-  info->workspace_bytes = s->ws_bytes;
+  info->workspace_bytes = s->main.ws_bytes;
   info->build_ms = s->build_ms;
   return RR_OK;
 }
@@ -384,12 +400,12 @@ int rr_scan_async(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, f
   if (rc != RR_OK) return rc;
   if (!is_device_ptr(out_polar)) return fail(RR_ERR_INVALID_ARG, "rr_scan_async needs a device output");
   float* const images[1] = {out_polar};
-  return batch_run(s, pose, p, images, 1, nullptr, t_stream);
+  return batch_run(s, &s->main, pose, p, images, 1, nullptr, t_stream, s->cfg);
 }
 
 int rr_scene_sync(rr_scene* s) {
   if (!s) return fail(RR_ERR_INVALID_ARG, "scene must not be NULL");
-  return device_status(s, t_stream);
+  return device_status(&s->main, t_stream);
 }
 
 int rr_scan(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* out_polar) {
@@ -401,16 +417,16 @@ int rr_scan(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* 
   const bool dev = is_device_ptr(out_polar);
   float* target = out_polar;
   if (!dev) {
-    rc = ensure_image(s, img_bytes, st);
+    rc = ensure_image(&s->main, img_bytes, st);
     if (rc != RR_OK) return rc;
-    target = s->d_image;
+    target = s->main.d_image;
   }
   float* const images[1] = {target};
-  rc = batch_run(s, pose, p, images, 1, nullptr, st);
+  rc = batch_run(s, &s->main, pose, p, images, 1, nullptr, st, s->cfg);
   if (rc != RR_OK) return rc;
   if (!dev)
     RR_CHECK_CUDA(cudaMemcpyAsync(out_polar, target, img_bytes, cudaMemcpyDeviceToHost, st), "copying the image");
-  return device_status(s, st);
+  return device_status(&s->main, st);
 }
 
 int rr_scan_debug(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, const uint8_t* ray_mask,
@@ -457,13 +473,13 @@ int rr_scan_debug(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, c
   dbg.tallies = d_tal;
   dbg.mask = d_mask;
   float* const images[1] = {d_img};
-  rc = batch_run(s, pose, p, images, 1, &dbg, st);
+  rc = batch_run(s, &s->main, pose, p, images, 1, &dbg, st, s->cfg);
   if (rc != RR_OK) {
     cleanup();
     return rc;
   }
-  rc = device_status(s, st);
-  const uint64_t total = s->h_ctr->seg_start[p->max_bounces];
+  rc = device_status(&s->main, st);
+  const uint64_t total = s->main.h_ctr->seg_start[p->max_bounces];
   if (n_segs) *n_segs = total;
   if (rc == RR_OK || rc == RR_ERR_CAPACITY) {
     int rc2;
@@ -496,20 +512,20 @@ int rr_polar_to_db_u8(const float* polar, uint64_t n, float cutoff_db, uint8_t* 
 int rr_scene_stats(rr_scene* s, rr_stats* out, int reset) {
   if (!s || !out) return fail(RR_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t st = t_stream;
-  RR_CHECK_CUDA(cudaMemcpyAsync(s->h_ctr, s->d_ctr, sizeof(ScanCounters), cudaMemcpyDeviceToHost, st), "stats");
+  RR_CHECK_CUDA(cudaMemcpyAsync(s->main.h_ctr, s->main.d_ctr, sizeof(ScanCounters), cudaMemcpyDeviceToHost, st), "stats");
   RR_CHECK_CUDA(cudaStreamSynchronize(st), "stats");
-  out->closest_queries = s->h_ctr->stat_closest;
-  out->anyhit_queries = s->h_ctr->stat_anyhit;
-  out->returns = s->h_ctr->stat_returns;
-  out->scans = s->h_ctr->stat_scans;
-  out->nodes_visited = s->h_ctr->stat_nodes;
-  out->tris_tested = s->h_ctr->stat_tris;
+  out->closest_queries = s->main.h_ctr->stat_closest;
+  out->anyhit_queries = s->main.h_ctr->stat_anyhit;
+  out->returns = s->main.h_ctr->stat_returns;
+  out->scans = s->main.h_ctr->stat_scans;
+  out->nodes_visited = s->main.h_ctr->stat_nodes;
+  out->tris_tested = s->main.h_ctr->stat_tris;
   out->kernel_launches = s->launches;
-  out->anyhit_nodes_visited = s->h_ctr->stat_nodes_any;
-  out->anyhit_tris_tested = s->h_ctr->stat_tris_any;
+  out->anyhit_nodes_visited = s->main.h_ctr->stat_nodes_any;
+  out->anyhit_tris_tested = s->main.h_ctr->stat_tris_any;
   if (reset) {
     s->launches = 0;
-    RR_CHECK_CUDA(cudaMemsetAsync(&s->d_ctr->stat_closest, 0, 8 * sizeof(unsigned long long), st), "stats reset");
+    RR_CHECK_CUDA(cudaMemsetAsync(&s->main.d_ctr->stat_closest, 0, 8 * sizeof(unsigned long long), st), "stats reset");
     RR_CHECK_CUDA(cudaStreamSynchronize(st), "stats reset");
   }
   return RR_OK;

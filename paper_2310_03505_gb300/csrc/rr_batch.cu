@@ -125,73 +125,74 @@ std::vector<Group> plan_groups(const rr_sensor_params* ps, uint32_t n, const Lau
   return out;
 }
 
-int ensure_workspace(rr_scene* s, size_t bytes, cudaStream_t st) {
-  if (s->ws_bytes >= bytes) return RR_OK;
+int ensure_workspace(ExecCtx* x, size_t bytes, cudaStream_t st) {
+  if (x->ws_bytes >= bytes) return RR_OK;
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(e, "synchronising before growing the workspace");
   }
-  if (s->ws) cudaFree(s->ws);
-  s->ws = nullptr;
-  s->ws_bytes = 0;
-  e = cudaMalloc(&s->ws, bytes);
+  if (x->ws) cudaFree(x->ws);
+  x->ws = nullptr;
+  x->ws_bytes = 0;
+  x->gkey.clear();   // a captured graph points into the old workspace
+  e = cudaMalloc(&x->ws, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(e, "allocating the scan workspace");
   }
-  s->ws_bytes = bytes;
+  x->ws_bytes = bytes;
   return RR_OK;
 }
 
-int ensure_image(rr_scene* s, size_t bytes, cudaStream_t st) {
-  if (s->image_bytes >= bytes) return RR_OK;
+int ensure_image(ExecCtx* x, size_t bytes, cudaStream_t st) {
+  if (x->image_bytes >= bytes) return RR_OK;
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(e, "synchronising before growing the image buffer");
   }
-  if (s->d_image) cudaFree(s->d_image);
-  s->d_image = nullptr;
-  s->image_bytes = 0;
-  e = cudaMalloc(&s->d_image, bytes);
+  if (x->d_image) cudaFree(x->d_image);
+  x->d_image = nullptr;
+  x->image_bytes = 0;
+  e = cudaMalloc(&x->d_image, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(e, "allocating the image buffer");
   }
-  s->image_bytes = bytes;
+  x->image_bytes = bytes;
   return RR_OK;
 }
 
 // pinned staging for the descriptors; waits until the previous upload from
 // it has been read by the device
-static int stage_acquire(rr_scene* s, size_t bytes) {
-  if (s->stage_used) {
-    cudaError_t e = cudaEventSynchronize(s->stage_ev);
+static int stage_acquire(ExecCtx* x, size_t bytes) {
+  if (x->stage_used) {
+    cudaError_t e = cudaEventSynchronize(x->stage_ev);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return cuda_fail(e, "waiting for the descriptor staging");
     }
-    s->stage_used = false;
+    x->stage_used = false;
   }
-  if (!s->stage_ev) {
-    cudaError_t e = cudaEventCreateWithFlags(&s->stage_ev, cudaEventDisableTiming);
+  if (!x->stage_ev) {
+    cudaError_t e = cudaEventCreateWithFlags(&x->stage_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return cuda_fail(e, "creating the staging event");
     }
   }
-  if (s->stage_bytes < bytes) {
-    if (s->h_stage) cudaFreeHost(s->h_stage);
-    s->h_stage = nullptr;
-    s->stage_bytes = 0;
+  if (x->stage_bytes < bytes) {
+    if (x->h_stage) cudaFreeHost(x->h_stage);
+    x->h_stage = nullptr;
+    x->stage_bytes = 0;
     const size_t want = std::max<size_t>(bytes, 4096);
-    cudaError_t e = cudaMallocHost(&s->h_stage, want);
+    cudaError_t e = cudaMallocHost(&x->h_stage, want);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return cuda_fail(e, "allocating the descriptor staging");
     }
-    s->stage_bytes = want;
+    x->stage_bytes = want;
   }
   return RR_OK;
 }
@@ -244,14 +245,15 @@ static cudaError_t launch_sequence(rr_scene* s, const ScanArgs& a, bool pattern,
 }
 
 // replay (capturing first when the arguments changed) the launch sequence
-static int graph_launch(rr_scene* s, const ScanArgs& a, bool pattern, const LaunchCfg& cfg, cudaStream_t st) {
+static int graph_launch(rr_scene* s, ExecCtx* x, const ScanArgs& a, bool pattern, const LaunchCfg& cfg,
+                        cudaStream_t st) {
   std::vector<unsigned char> key(sizeof(ScanArgs) + 4 * sizeof(uint32_t));
   memcpy(key.data(), &a, sizeof(ScanArgs));
   const uint32_t extra[4] = {pattern ? 1u : 0u, cfg.trace_block, cfg.trace_blocks_per_sm, cfg.refill};
   memcpy(key.data() + sizeof(ScanArgs), extra, sizeof extra);
-  if (!(s->gexec && key == s->gkey)) {
-    if (!s->cap_stream) {
-      cudaError_t e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+  if (!(x->gexec && key == x->gkey)) {
+    if (!x->cap_stream) {
+      cudaError_t e = cudaStreamCreateWithFlags(&x->cap_stream, cudaStreamNonBlocking);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(e, "creating the capture stream");
@@ -260,41 +262,41 @@ static int graph_launch(rr_scene* s, const ScanArgs& a, bool pattern, const Laun
     // one-time attribute and occupancy queries stay outside the capture
     num_sms();
     init_image_attrs();
-    cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(x->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return cuda_fail(e, "beginning the graph capture");
     }
-    const cudaError_t le = launch_sequence(s, a, pattern, cfg, false, s->cap_stream);
+    const cudaError_t le = launch_sequence(s, a, pattern, cfg, false, x->cap_stream);
     cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(s->cap_stream, &g);
+    e = cudaStreamEndCapture(x->cap_stream, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
       cudaGetLastError();
       if (g) cudaGraphDestroy(g);
       return cuda_fail(le != cudaSuccess ? le : e, "capturing the launch sequence");
     }
-    if (s->gexec) {
+    if (x->gexec) {
       cudaGraphExecUpdateResultInfo info;
-      if (cudaGraphExecUpdate(s->gexec, g, &info) != cudaSuccess) {
+      if (cudaGraphExecUpdate(x->gexec, g, &info) != cudaSuccess) {
         cudaGetLastError();
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
+        cudaGraphExecDestroy(x->gexec);
+        x->gexec = nullptr;
       }
     }
-    if (!s->gexec) {
-      e = cudaGraphInstantiate(&s->gexec, g, 0);
+    if (!x->gexec) {
+      e = cudaGraphInstantiate(&x->gexec, g, 0);
       if (e != cudaSuccess) {
         cudaGetLastError();
         cudaGraphDestroy(g);
-        s->gexec = nullptr;
-        s->gkey.clear();
+        x->gexec = nullptr;
+        x->gkey.clear();
         return cuda_fail(e, "instantiating the launch graph");
       }
     }
     cudaGraphDestroy(g);
-    s->gkey = key;
+    x->gkey = key;
   }
-  cudaError_t e = cudaGraphLaunch(s->gexec, st);
+  cudaError_t e = cudaGraphLaunch(x->gexec, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(e, "launching the graph");
@@ -302,18 +304,18 @@ static int graph_launch(rr_scene* s, const ScanArgs& a, bool pattern, const Laun
   return RR_OK;
 }
 
-int batch_enqueue(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps, float* const* images, uint32_t n,
-                  const DebugOut* dbg, cudaStream_t st, void* ws, const WsLayout& L, bool profile, bool allow_graph,
-                  const LaunchCfg& cfg, void* host_desc) {
+int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor_params* ps, float* const* images,
+                  uint32_t n, const DebugOut* dbg, cudaStream_t st, void* ws, const WsLayout& L, bool profile,
+                  bool allow_graph, const LaunchCfg& cfg, void* host_desc) {
   if (n == 0) return RR_OK;
   if (n != L.n_desc) return fail(RR_ERR_INVALID_ARG, "internal: layout planned for another batch");
   char* w = (char*)ws;
   const size_t dbytes = desc_bytes(n);
   void* hd = host_desc;
   if (!hd) {
-    const int rc = stage_acquire(s, dbytes);
+    const int rc = stage_acquire(x, dbytes);
     if (rc != RR_OK) return rc;
-    hd = s->h_stage;
+    hd = x->h_stage;
   }
   ScanDesc* D = (ScanDesc*)hd;
   uint32_t* R0 = (uint32_t*)(D + n);
@@ -340,8 +342,8 @@ int batch_enqueue(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps,
   if (tmp > L.tmp_floats) return fail(RR_ERR_INVALID_ARG, "internal: pattern buffer planned too small");
   cudaError_t e = cudaMemcpyAsync(w + L.off_desc, hd, dbytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !host_desc) {
-    e = cudaEventRecord(s->stage_ev, st);
-    s->stage_used = e == cudaSuccess;
+    e = cudaEventRecord(x->stage_ev, st);
+    x->stage_used = e == cudaSuccess;
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -351,11 +353,21 @@ int batch_enqueue(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps,
   ScanArgs a;
   memset(&a, 0, sizeof a);
   const bool wide = cfg.node_format == RR_NODES_WIDE8 && s->nt > 0;
-  if (wide && s->wide_stale) {   // collapse the 8-wide BVH on first use after a build
-    cudaEvent_t ev;
-    if (profile) prof_begin(s, RR_K_BUILD, st, &ev);
-    e = build_wide(s, st);
-    if (profile) prof_end(s, ev, st);
+  if (wide) {
+    // collapse the 8-wide BVH on first use after a build; streams other than
+    // the one that collapsed it wait for it
+    std::lock_guard<std::mutex> guard(s->lock);
+    if (s->wide_stale) {
+      cudaEvent_t ev;
+      const bool prof = profile && s->prof;
+      if (prof) prof_begin(s, RR_K_BUILD, st, &ev);
+      e = build_wide(s, st);
+      if (prof) prof_end(s, ev, st);
+      if (e == cudaSuccess && !s->wide_ready) e = cudaEventCreateWithFlags(&s->wide_ready, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(s->wide_ready, st);
+    } else if (s->wide_ready) {
+      e = cudaStreamWaitEvent(st, s->wide_ready, 0);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       return cuda_fail(e, "collapsing the wide BVH");
@@ -385,7 +397,7 @@ int batch_enqueue(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps,
   a.hits = (rr::HitRec*)(w + L.off_hits);
   a.recs = (uint2*)(w + L.off_recs);
   a.tile_status = (unsigned long long*)(w + L.off_status);
-  a.ctr = s->d_ctr;
+  a.ctr = x->d_ctr;
   a.image_tmp = pattern ? (float*)(w + L.off_tmp) : nullptr;
   a.ray_cap = L.ray_cap;
   a.rec_cap = L.rec_cap;
@@ -398,7 +410,7 @@ int batch_enqueue(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps,
   s->launches += 2u + 2u * maxb + ((any_flags & RR_MULTIPATH) && maxb > 1 ? 2u * (maxb - 1u) : 0u) +
                  (pattern ? 1u : 0u);
   const bool prof = profile && s->prof;
-  if (!prof && allow_graph && cfg.use_graph && !dbg) return graph_launch(s, a, pattern, cfg, st);
+  if (!prof && allow_graph && cfg.use_graph && !dbg) return graph_launch(s, x, a, pattern, cfg, st);
   e = launch_sequence(s, a, pattern, cfg, prof, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -407,17 +419,17 @@ int batch_enqueue(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps,
   return RR_OK;
 }
 
-int batch_run(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps, float* const* images, uint32_t n,
-              const DebugOut* dbg, cudaStream_t st) {
-  const std::vector<Group> groups = plan_groups(ps, n, s->cfg);
+int batch_run(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor_params* ps, float* const* images,
+              uint32_t n, const DebugOut* dbg, cudaStream_t st, const LaunchCfg& cfg) {
+  const std::vector<Group> groups = plan_groups(ps, n, cfg);
   if (dbg && groups.size() != 1) return fail(RR_ERR_INVALID_ARG, "internal: a debug scan is one group");
   size_t need = 0;
   for (const Group& g : groups) need = std::max(need, g.L.total);
-  int rc = ensure_workspace(s, need, st);
+  int rc = ensure_workspace(x, need, st);
   if (rc != RR_OK) return rc;
   for (const Group& g : groups) {
-    rc = batch_enqueue(s, poses + g.first, ps + g.first, images + g.first, g.count, dbg, st, s->ws, g.L, true, true,
-                       s->cfg, nullptr);
+    rc = batch_enqueue(s, x, poses + g.first, ps + g.first, images + g.first, g.count, dbg, st, x->ws, g.L, true,
+                       true, cfg, nullptr);
     if (rc != RR_OK) return rc;
   }
   return RR_OK;
@@ -483,7 +495,7 @@ int rr_scan_batch(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor
   const std::vector<Group> groups = plan_groups(params, n, s->cfg);
   size_t need = 0;
   for (const Group& g : groups) need = std::max(need, g.L.total);
-  rc = ensure_workspace(s, need, st);
+  rc = ensure_workspace(&s->main, need, st);
   if (rc != RR_OK) return rc;
   std::vector<float*> images(n);
   std::vector<bool> on_dev(n);
@@ -494,7 +506,7 @@ int rr_scan_batch(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor
     for (uint32_t i = g.first; i < g.first + g.count; ++i)
       if (!on_dev[i]) host_bytes += (size_t)params[i].n_azimuth * params[i].n_bins * sizeof(float);
     if (host_bytes) {
-      rc = ensure_image(s, host_bytes, st);
+      rc = ensure_image(&s->main, host_bytes, st);
       if (rc != RR_OK) return rc;
     }
     size_t off = 0;
@@ -502,12 +514,12 @@ int rr_scan_batch(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor
       if (on_dev[i]) {
         images[i] = out[i];
       } else {
-        images[i] = s->d_image + off / sizeof(float);
+        images[i] = s->main.d_image + off / sizeof(float);
         off += (size_t)params[i].n_azimuth * params[i].n_bins * sizeof(float);
       }
     }
-    rc = batch_enqueue(s, poses + g.first, params + g.first, images.data() + g.first, g.count, nullptr, st, s->ws,
-                       g.L, true, true, s->cfg, nullptr);
+    rc = batch_enqueue(s, &s->main, poses + g.first, params + g.first, images.data() + g.first, g.count, nullptr, st,
+                       s->main.ws, g.L, true, true, s->cfg, nullptr);
     if (rc != RR_OK) return rc;
     for (uint32_t i = g.first; i < g.first + g.count; ++i) {
       if (on_dev[i]) continue;
@@ -519,7 +531,7 @@ int rr_scan_batch(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor
       }
     }
   }
-  return device_status(s, st);
+  return device_status(&s->main, st);
 }
 
 int rr_scan_batch_async(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor_params* params,
@@ -529,7 +541,7 @@ int rr_scan_batch_async(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_
   for (uint32_t i = 0; i < n; ++i)
     if (!is_device_ptr(out[i]))
       return fail(RR_ERR_INVALID_ARG, "scan " + std::to_string(i) + ": rr_scan_batch_async needs device outputs");
-  return batch_run(s, poses, params, out, n, nullptr, current_stream());
+  return batch_run(s, &s->main, poses, params, out, n, nullptr, current_stream(), s->cfg);
 }
 
 int rr_batch_config_get(const rr_scene* s, rr_batch_config* out) {
@@ -606,13 +618,14 @@ int rr_autotune(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor_p
   // mean device time of one pass over the batch with configuration c
   auto time_cfg = [&](const LaunchCfg& c, float* ms) -> int {
     s->cfg = c;
-    int r = batch_run(s, poses, params, images.data(), n, nullptr, st);   // warm-up (and capture)
+    int r = batch_run(s, &s->main, poses, params, images.data(), n, nullptr, st, s->cfg);   // warm-up (and capture)
     if (r != RR_OK) return r;
     cudaEventRecord(e0, st);
-    for (uint32_t k = 0; k < reps && r == RR_OK; ++k) r = batch_run(s, poses, params, images.data(), n, nullptr, st);
+    for (uint32_t k = 0; k < reps && r == RR_OK; ++k)
+      r = batch_run(s, &s->main, poses, params, images.data(), n, nullptr, st, s->cfg);
     cudaEventRecord(e1, st);
     if (r != RR_OK) return r;
-    r = device_status(s, st);
+    r = device_status(&s->main, st);
     if (r != RR_OK) return r;
     float t = 0.f;
     cudaEventElapsedTime(&t, e0, e1);

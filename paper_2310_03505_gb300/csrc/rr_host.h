@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -30,6 +32,29 @@ struct LaunchCfg {
   uint32_t refill = 8;                // idle lanes that trigger a refill (1..32)
   uint64_t ws_limit = uint64_t(24) << 30;
 };
+
+// What one stream of scans needs besides the scene: device counters and
+// status, the scan workspace, an image buffer for host outputs, pinned
+// staging of the scan descriptors and the captured launch graph.  A scene owns
+// one for its own entry points; a server owns one per slot, so launch
+// sequences on different streams never share scratch.
+struct ExecCtx {
+  rr::ScanCounters* d_ctr = nullptr;
+  rr::ScanCounters* h_ctr = nullptr;   // pinned mirror
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  float* d_image = nullptr;            // device images of host outputs
+  size_t image_bytes = 0;
+  void* h_stage = nullptr;             // pinned staging of the scan descriptors
+  size_t stage_bytes = 0;
+  cudaEvent_t stage_ev = nullptr;      // the last upload from h_stage has been read
+  bool stage_used = false;
+  cudaStream_t cap_stream = nullptr;   // stream used only to capture graphs
+  cudaGraphExec_t gexec = nullptr;     // last captured launch sequence
+  std::vector<unsigned char> gkey;     // what gexec was captured for
+};
+cudaError_t ctx_init(ExecCtx* x, cudaStream_t st);   // counters (zeroed)
+void ctx_free(ExecCtx* x);
 
 }  // namespace rr_host
 
@@ -70,30 +95,18 @@ struct rr_scene {
   uint32_t depth = 0;
   float build_ms = 0.f;
   size_t scene_bytes = 0;
-  // scan workspace
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  rr::ScanCounters* d_ctr = nullptr;
-  rr::ScanCounters* h_ctr = nullptr;   // pinned mirror
-  float* d_image = nullptr;            // internal image for host outputs
-  size_t image_bytes = 0;
-  // batched path
+  // execution state of the scene's own entry points
+  rr_host::ExecCtx main;
   rr_host::LaunchCfg cfg;
-  void* h_stage = nullptr;             // pinned staging of the scan descriptors
-  size_t stage_bytes = 0;
-  cudaEvent_t stage_ev = nullptr;      // the last upload from h_stage has been read
-  bool stage_used = false;
-  cudaStream_t cap_stream = nullptr;   // stream used only to capture graphs
-  cudaGraphExec_t gexec = nullptr;     // last captured launch sequence
-  std::vector<unsigned char> gkey;     // what gexec was captured for
-  uint32_t gnodes = 0;
+  std::mutex lock;                     // lazy wide collapse and launch counting across threads
+  cudaEvent_t wide_ready = nullptr;    // recorded after the latest collapse
   // profiling
   bool prof = false;
   std::vector<rr_host::ProfEvent> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
   double prof_ms[RR_K_COUNT] = {0};
   uint64_t prof_launches[RR_K_COUNT] = {0};
-  uint64_t launches = 0;  // kernels launched by this scene
+  std::atomic<uint64_t> launches{0};  // kernels launched for this scene (any stream)
 };
 
 namespace rr_host {
@@ -151,14 +164,14 @@ std::vector<Group> plan_groups(const rr_sensor_params* ps, uint32_t n, const Lau
 // (device); the workspace at ws is laid out by L.  host_desc: where the
 // descriptors are staged (NULL: the scene's pinned staging).  No allocation
 // unless allow_graph.
-int batch_enqueue(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps, float* const* images, uint32_t n,
-                  const DebugOut* dbg, cudaStream_t st, void* ws, const WsLayout& L, bool profile, bool allow_graph,
-                  const LaunchCfg& cfg, void* host_desc);
-int ensure_workspace(rr_scene* s, size_t bytes, cudaStream_t st);
-int ensure_image(rr_scene* s, size_t bytes, cudaStream_t st);
-int device_status(rr_scene* s, cudaStream_t st);
-// whole request on the scene's workspace: images[i] device pointers
-int batch_run(rr_scene* s, const rr_pose* poses, const rr_sensor_params* ps, float* const* images, uint32_t n,
-              const DebugOut* dbg, cudaStream_t st);
+int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor_params* ps, float* const* images,
+                  uint32_t n, const DebugOut* dbg, cudaStream_t st, void* ws, const WsLayout& L, bool profile,
+                  bool allow_graph, const LaunchCfg& cfg, void* host_desc);
+int ensure_workspace(ExecCtx* x, size_t bytes, cudaStream_t st);
+int ensure_image(ExecCtx* x, size_t bytes, cudaStream_t st);
+int device_status(ExecCtx* x, cudaStream_t st);
+// whole request on the context's workspace (grown as needed): images[i] device pointers
+int batch_run(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor_params* ps, float* const* images,
+              uint32_t n, const DebugOut* dbg, cudaStream_t st, const LaunchCfg& cfg);
 
 }  // namespace rr_host

@@ -81,7 +81,7 @@ extern "C" int rr_scan_static(rr_scene* s, const rr_pose* pose, const rr_sensor_
   float* const images[1] = {out_polar};
   LaunchCfg cfg = s->cfg;
   cfg.use_graph = 0;
-  rc = batch_enqueue(s, pose, p, images, 1, nullptr, st, scratch, L, false, false, cfg, desc);
+  rc = batch_enqueue(s, &s->main, pose, p, images, 1, nullptr, st, scratch, L, false, false, cfg, desc);
   if (rc != RR_OK) return rc;
-  return device_status(s, st);
+  return device_status(&s->main, st);
 }

@@ -88,6 +88,26 @@ class rr_batch_config(C.Structure):
 
 RR_NODES_WIDE8, RR_NODES_BINARY = 0, 1
 WIDE_NODE_BYTES = 80
+RR_REQ_QUEUED, RR_REQ_RUNNING, RR_REQ_DONE, RR_REQ_FAILED = range(4)
+
+
+class rr_serve_config(C.Structure):
+    _fields_ = [("memory_budget", C.c_uint64), ("slots", C.c_uint32), ("max_batch_scans", C.c_uint32),
+                ("max_batch_rays", C.c_uint32), ("max_queue", C.c_uint32), ("node_format", C.c_uint32),
+                ("refill_threshold", C.c_uint32)]
+
+
+class rr_serve_record(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("submit_ms", C.c_double), ("start_ms", C.c_double),
+                ("done_ms", C.c_double), ("batch_size", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class rr_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("rejected_busy", C.c_uint64), ("batches", C.c_uint64), ("closest_queries", C.c_uint64),
+                ("anyhit_queries", C.c_uint64), ("initial_rays", C.c_uint64), ("queued", C.c_uint64),
+                ("busy_ms", C.c_double), ("elapsed_ms", C.c_double), ("latency_p50_ms", C.c_double),
+                ("latency_p99_ms", C.c_double), ("latency_mean_ms", C.c_double), ("latency_max_ms", C.c_double)]
 
 
 # every symbol declared in include/rr.h with its ctypes signature
@@ -114,6 +134,14 @@ SIGNATURES = {
                        C.POINTER(C.c_uint64)], C.c_int),
     "rr_autotune": ([_P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(rr_batch_config), C.POINTER(C.c_float),
                      C.POINTER(C.c_float)], C.c_int),
+    "rr_serve_create": ([C.POINTER(rr_serve_config), C.POINTER(_P)], C.c_int),
+    "rr_serve_destroy": ([_P], C.c_int),
+    "rr_serve_submit": ([_P, _P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P, C.POINTER(C.c_uint64)],
+                        C.c_int),
+    "rr_serve_poll": ([_P, C.c_uint64, C.POINTER(C.c_int)], C.c_int),
+    "rr_serve_wait": ([_P, C.c_uint64, C.c_uint32], C.c_int),
+    "rr_serve_result": ([_P, C.c_uint64, C.POINTER(rr_serve_record)], C.c_int),
+    "rr_serve_stats_get": ([_P, C.POINTER(rr_serve_stats), C.c_int], C.c_int),
     "rr_scan_debug": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P, _P, _P, C.c_uint64,
                        C.POINTER(C.c_uint64), _P], C.c_int),
     "rr_polar_to_db_u8": ([_P, C.c_uint64, C.c_float, _P], C.c_int),
@@ -356,6 +384,52 @@ def rr_autotune(scene, poses, params, reps: int = 2) -> dict:
     out = {k: getattr(c, k) for k, _ in rr_batch_config._fields_}
     out.update(best_ms=best.value, start_ms=start.value)
     return out
+
+
+def rr_serve_create(**config):
+    """Keyword arguments: the rr_serve_config fields (missing ones: library defaults)."""
+    unknown = set(config) - {k for k, _ in rr_serve_config._fields_}
+    if unknown:
+        raise ValueError(f"unknown server config keys {sorted(unknown)}")
+    _use_torch_stream()
+    c = rr_serve_config(**{k: int(v) for k, v in config.items()})
+    h = C.c_void_p()
+    _check(load().rr_serve_create(C.byref(c), C.byref(h)))
+    return h
+
+
+def rr_serve_destroy(server) -> None:
+    _check(load().rr_serve_destroy(server))
+
+
+def rr_serve_submit(server, scene, pose: dict, params: dict, out_polar) -> int:
+    """Returns the ticket; out_polar must stay alive until the request finishes."""
+    P, S = make_pose(pose), make_params(params)
+    t = C.c_uint64()
+    _check(load().rr_serve_submit(server, scene, C.byref(P), C.byref(S), _ptr(out_polar), C.byref(t)))
+    return t.value
+
+
+def rr_serve_poll(server, ticket: int) -> bool:
+    d = C.c_int()
+    _check(load().rr_serve_poll(server, int(ticket), C.byref(d)))
+    return bool(d.value)
+
+
+def rr_serve_wait(server, ticket: int, timeout_ms: int = 60_000) -> None:
+    _check(load().rr_serve_wait(server, int(ticket), int(timeout_ms)))
+
+
+def rr_serve_result(server, ticket: int) -> dict:
+    r = rr_serve_record()
+    _check(load().rr_serve_result(server, int(ticket), C.byref(r)))
+    return {k: getattr(r, k) for k, _ in rr_serve_record._fields_ if k != "reserved"}
+
+
+def rr_serve_stats_get(server, reset: bool = False) -> dict:
+    st = rr_serve_stats()
+    _check(load().rr_serve_stats_get(server, C.byref(st), 1 if reset else 0))
+    return {k: getattr(st, k) for k, _ in rr_serve_stats._fields_}
 
 
 def rr_scan_debug(scene, pose: dict, params: dict, out_polar, ray_mask=None, seg_capacity: int = 0,

@@ -292,6 +292,31 @@ def campus(seed: int = 0x5EED0001, target_tris: int = 200_000, n_buildings: int 
     return sc
 
 
+def _free(foot, x, y, clearance, extent):
+    if abs(x) > extent or abs(y) > extent:
+        return False
+    if not len(foot):
+        return True
+    inside = ((x > foot[:, 0] - clearance) & (x < foot[:, 2] + clearance) &
+              (y > foot[:, 1] - clearance) & (y < foot[:, 3] + clearance))
+    return not bool(inside.any())
+
+
+def _footprints(sc: Scene) -> np.ndarray:
+    return np.array([[lo[0], lo[1], hi[0], hi[1]] for lo, hi in sc.obstacles], np.float64).reshape(-1, 4)
+
+
+def random_pose(sc: Scene, rng, height: float = 1.8, extent: float = 100.0, clearance: float = 1.0) -> dict:
+    """A seeded sensor pose uniform over [-extent, extent]^2 at the given
+    height, clear of every obstacle footprint, with a uniform heading."""
+    foot = _footprints(sc)
+    for _ in range(10000):
+        x, y = (float(v) for v in rng.uniform(-extent, extent, size=2))
+        if _free(foot, x, y, clearance, extent):
+            return pose(x, y, height, yaw=float(rng.uniform(-math.pi, math.pi)))
+    raise RuntimeError("no free sensor position found")
+
+
 def trajectory(sc: Scene, n: int, step: float = 0.25, seed: int = 0x5EED0003, height: float = 1.8,
                turn_sigma_deg: float = 10.0, clearance: float = 1.0, extent: float = 140.0) -> list:
     """Seeded random walk of n sensor poses, step metres apart: the heading
@@ -300,16 +325,10 @@ def trajectory(sc: Scene, n: int, step: float = 0.25, seed: int = 0x5EED0003, he
     redrawn with a fresh heading.  Starts at the origin (kept clear of
     obstacles by the generators)."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    foot = np.array([[lo[0], lo[1], hi[0], hi[1]] for lo, hi in sc.obstacles], np.float64).reshape(-1, 4)
+    foot = _footprints(sc)
 
     def free(x, y):
-        if abs(x) > extent or abs(y) > extent:
-            return False
-        if not len(foot):
-            return True
-        inside = ((x > foot[:, 0] - clearance) & (x < foot[:, 2] + clearance) &
-                  (y > foot[:, 1] - clearance) & (y < foot[:, 3] + clearance))
-        return not bool(inside.any())
+        return _free(foot, x, y, clearance, extent)
 
     x, y = 0.0, 0.0
     heading = float(rng.uniform(-math.pi, math.pi))
@@ -343,6 +362,7 @@ def city(seed: int = 0x5EED0002, target_tris: int = 5_000_000, blocks: int = 12,
     idx = {n: i for i, n in enumerate(CITY_MATS)}
     lot = 2 * extent / blocks
     street = 14.0
+    obstacles = []
     for bi in range(blocks):
         for bj in range(blocks):
             x0 = -extent + bi * lot + street / 2
@@ -359,6 +379,7 @@ def city(seed: int = 0x5EED0002, target_tris: int = 5_000_000, blocks: int = 12,
                     hi = lo + np.array([w, w, h + 0.5])
                     mat = "brick" if rng.uniform() < 0.5 else "concrete"
                     mesh.box(lo, hi, idx[mat], cell=1.5)
+                    obstacles.append((lo.copy(), hi.copy()))
                     # glass panels 5 cm in front of the +x / -x facades
                     for side in (0, 1):
                         xf = hi[0] + 0.05 if side else lo[0] - 0.05
@@ -377,13 +398,18 @@ def city(seed: int = 0x5EED0002, target_tris: int = 5_000_000, blocks: int = 12,
                 lo = np.array([cx - 2.2, cy - 0.9, 0.15])
                 hi = np.array([cx + 2.2, cy + 0.9, 1.5])
                 mesh.box(lo, hi, idx["metal" if rng.uniform() < 0.7 else "plastic"])
+                obstacles.append((lo, hi))
             for c in range(int(size // 20)):
                 mesh.cylinder(x0 + 10 + c * 20, y0 - 5.5, -0.2, 6.0, 0.12, 16, idx["metal"])
+                px, py = x0 + 10 + c * 20, y0 - 5.5
+                obstacles.append((np.array([px - 0.12, py - 0.12, -0.2]), np.array([px + 0.12, py + 0.12, 6.0])))
     others = len(mesh.t)
     g = max(1, int(round(math.sqrt(max(target_tris - others, 2) / 2.0))))
     mesh.quad_grid((-extent, -extent, 0.0), (2 * extent, 0, 0), (0, 2 * extent, 0), g, g, (0, 0, 1), idx["asphalt"])
     mats = [MATERIALS[n] for n in CITY_MATS]
-    return mesh.build("city", mats)
+    sc = mesh.build("city", mats)
+    sc.obstacles = obstacles
+    return sc
 
 
 # --------------------------------------------------------------------------
