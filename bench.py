@@ -128,10 +128,11 @@ def measured_peaks():
 
 
 def traffic_from_profiles():
-    """Per-launch DRAM bytes of the trace kernel from the committed ncu summary,
-    valid only while the kernel source matches the hash it was taken on."""
+    """Per-launch DRAM bytes of the closest-hit query kernel from the committed
+    ncu summary, valid only while the kernel source matches the hash it was
+    taken on."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "trace_kernel_campus_ncu.txt")
+    p = os.path.join(ROOT, "profiles", "query_kernel_campus_ncu.txt")
     src = os.path.join(ROOT, "paper_2310_03505_gb300", "csrc", "rr_trace.cu")
     if not (os.path.exists(p) and os.path.exists(src)):
         return None
@@ -139,7 +140,7 @@ def traffic_from_profiles():
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if d.get("source_sha256_16") != h:
         return None
-    return d.get("dram_bytes_per_trace_launch_full_scale")
+    return d.get("dram_bytes_per_closest_launch")
 
 
 # ------------------------------------------------------------------ oracle arm

@@ -363,6 +363,17 @@ int rr_scan_debug(rr_scene* scene, const rr_pose* pose, const rr_sensor_params* 
    device status of the scan. */
 int rr_scan_static(rr_scene* scene, const rr_pose* pose, const rr_sensor_params* params, float* out_polar);
 
+/* Range-bin accumulation alone (Sec. III-B): the image pass of a scan run on
+   caller-given returns.  Return k adds energy[k] to pixel (column[k],
+   bin[k]) of out [n_columns][n_bins]; there is no blur, pattern or noise.
+   The sums are FP32 with compensated (Neumaier) summation, the same kernel as
+   in every scan.  column [n] must be non-decreasing and below n_columns (else
+   RR_ERR_INVALID_ARG); returns with bin >= n_bins are dropped; n_columns <=
+   2^18, n_bins <= 16384.
+   All buffers host or device.  Blocking. */
+int rr_accumulate_returns(const uint32_t* column, const uint32_t* bin, const float* energy, uint64_t n,
+                          uint32_t n_columns, uint32_t n_bins, float* out);
+
 /* Sec. III-B display mapping: L_E = 10 log10(E_R / E0), E0 = 1, mapped
    linearly from [-cutoff_db, 0] dB to [0, 255], clamped, rounded to nearest.
    polar [n] float and out [n] uint8 are device memory.  Stream ordered. */

@@ -318,6 +318,22 @@ def post(image, params: dict, az_list=None):
     return img
 
 
+def bin_returns(column, bin_, energy, n_columns: int, n_bins: int):
+    """Sec. III-B: every return adds its energy to the pixel (column, bin) of
+    an image that starts at zero; returns past the last bin are dropped.  Each
+    pixel is the correctly rounded (double) value of the exact sum of its
+    returns (math.fsum, Shewchuk's exact partial sums)."""
+    import math
+    groups = {}
+    for c, b, e in zip(np.asarray(column).tolist(), np.asarray(bin_).tolist(), np.asarray(energy).tolist()):
+        if b < n_bins:
+            groups.setdefault((c, b), []).append(e)
+    out = np.zeros((n_columns, n_bins), np.float64)
+    for (c, b), es in groups.items():
+        out[c, b] = math.fsum(es)
+    return out
+
+
 def db_u8(image, cutoff_db: float):
     img = np.ascontiguousarray(np.asarray(image, np.float64))
     out = np.zeros(img.shape, np.uint8)

@@ -12,7 +12,15 @@
 // warp-aggregated adds (lanes that hit the same bin are summed with shuffles
 // and added once), blurs the column in shared memory, adds the noise and
 // writes the column once, coalesced.  No global atomics, no memset.
+//
+// The sums are compensated (Neumaier's improvement of Kahan summation,
+// ZAMM 54, 1974): every bin holds a float pair (sum, correction) updated with
+// a 64-bit compare-and-swap, and lanes that share a bin combine their values
+// the same way first, so a bin's error stays within a few units in the last
+// place of its value however many returns it receives and in whatever order.
 #include <cuda_runtime.h>
+
+#include <cstring>
 
 #include "rr_host.h"
 
@@ -56,10 +64,30 @@ __device__ __forceinline__ float noise_at(uint4 rng, float4 post, uint32_t az, u
   return post.z * u01(draw(rng, az, bin, 2u).x) + post.w * u01(draw(rng, az, bin, 3u).x);
 }
 
+// (s, c) + (x, cx) with the rounding error of s + x carried into c
+__device__ __forceinline__ float2 neumaier(float2 acc, float x, float cx) {
+  const float t = acc.x + x;
+  const float e = fabsf(acc.x) >= fabsf(x) ? (acc.x - t) + x : (x - t) + acc.x;
+  return make_float2(t, acc.y + (e + cx));
+}
+
+__device__ __forceinline__ void bin_add(unsigned long long* cell, float x, float cx) {
+  unsigned long long old = *cell, seen;
+  do {
+    seen = old;
+    const float2 cur = make_float2(__uint_as_float((uint32_t)seen), __uint_as_float((uint32_t)(seen >> 32)));
+    const float2 nxt = neumaier(cur, x, cx);
+    const unsigned long long v = (unsigned long long)__float_as_uint(nxt.x) |
+                                 ((unsigned long long)__float_as_uint(nxt.y) << 32);
+    old = atomicCAS(cell, seen, v);
+  } while (old != seen);
+}
+
 __global__ void __launch_bounds__(kImgBlock) k_bin_column(ScanArgs a) {
-  extern __shared__ float sm[];
-  float* hist = sm;                     // [n_bins]
-  float* col = sm + a.max_bins;         // [n_bins]
+  extern __shared__ unsigned long long sm64[];
+  unsigned long long* cells = sm64;                             // [n_bins] (sum, correction)
+  float* hist = reinterpret_cast<float*>(sm64 + a.max_bins);    // [n_bins] the compensated sums
+  float* col = reinterpret_cast<float*>(sm64);                  // [n_bins] after the blur (reuses cells)
   __shared__ float taps[kMaxTaps];
   __shared__ uint32_t s_rng[2 * RR_MAX_BOUNCES];
   const uint32_t c = blockIdx.x;
@@ -69,7 +97,7 @@ __global__ void __launch_bounds__(kImgBlock) k_bin_column(ScanArgs a) {
   const uint32_t nb = __ldg(&sd->dims.w);
   const float4 post = __ldg(&sd->post);   // blur sigma, pattern sigma, noise_sys, noise_amb
   const int lane = threadIdx.x & 31;
-  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0.0f;
+  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) cells[i] = 0ull;
   // record range of this column in every bounce's list: lane 2b / 2b+1
   if (threadIdx.x < 32) {
     const uint32_t b = (uint32_t)lane >> 1;
@@ -95,10 +123,15 @@ __global__ void __launch_bounds__(kImgBlock) k_bin_column(ScanArgs a) {
       }
       const uint32_t tag = valid ? bin : 0x10000u + (uint32_t)lane;
       const uint32_t peers = __match_any_sync(0xFFFFFFFFu, tag);
-      float sum = 0.0f;
-      for (uint32_t m = peers; m; m &= m - 1u) sum += __shfl_sync(peers, e, __ffs(m) - 1);
-      if (valid && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], sum);
+      float2 acc = make_float2(0.0f, 0.0f);
+      for (uint32_t m = peers; m; m &= m - 1u) acc = neumaier(acc, __shfl_sync(peers, e, __ffs(m) - 1), 0.0f);
+      if (valid && lane == __ffs(peers) - 1) bin_add(&cells[bin], acc.x, acc.y);
     }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
+    const unsigned long long v = cells[i];
+    hist[i] = __uint_as_float((uint32_t)v) + __uint_as_float((uint32_t)(v >> 32));
   }
   __syncthreads();
   const float* src = hist;
@@ -153,6 +186,20 @@ __global__ void __launch_bounds__(kImgBlock) k_az_pattern(ScanArgs a) {
   sd->image[(size_t)az * nb + i] = acc;
 }
 
+// records of caller-given returns: (column << kBinBits | bin, energy); flags
+// a column that decreases or lies past the image
+__global__ void k_pack_returns(const uint32_t* __restrict__ column, const uint32_t* __restrict__ bin,
+                               const float* __restrict__ energy, uint32_t n, uint32_t n_columns, uint32_t n_bins,
+                               uint2* __restrict__ recs, uint32_t* __restrict__ bad) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const uint32_t c = column[k], b = bin[k];
+  if ((k > 0 && column[k - 1] > c) || c >= n_columns) atomicOr(bad, 1u);
+  // a bin past the image contributes nothing
+  const bool in = b < n_bins;
+  recs[k] = make_uint2(((c < n_columns ? c : 0u) << kBinBits) | (in ? b : 0u), in ? __float_as_uint(energy[k]) : 0u);
+}
+
 // Sec. III-B display mapping
 __global__ void k_db_u8(const float* __restrict__ polar, uint64_t n, float cutoff_db, uint8_t* __restrict__ out) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -169,19 +216,21 @@ namespace rr_host {
 
 using namespace rr;
 
+// dynamic shared memory of k_bin_column: (sum, correction) pairs (later the
+// blurred column), sums
+static size_t bin_smem(uint32_t n_bins) { return (size_t)n_bins * (sizeof(unsigned long long) + sizeof(float)); }
+
 void init_image_attrs() {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_bin_column, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         2 * RR_MAX_BINS * (int)sizeof(float));
+    cudaFuncSetAttribute(k_bin_column, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem(RR_MAX_BINS));
     attr_set = true;
   }
 }
 
 cudaError_t launch_image(const ScanArgs& a, bool pattern, cudaStream_t st) {
   init_image_attrs();
-  const size_t smem = 2 * (size_t)a.max_bins * sizeof(float);
-  k_bin_column<<<a.n_cols, kImgBlock, smem, st>>>(a);
+  k_bin_column<<<a.n_cols, kImgBlock, bin_smem(a.max_bins), st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (pattern) {
@@ -199,3 +248,94 @@ cudaError_t launch_db_u8(const float* polar, uint64_t n, float cutoff_db, uint8_
 }
 
 }  // namespace rr_host
+
+using namespace rr_host;
+
+extern "C" int rr_accumulate_returns(const uint32_t* column, const uint32_t* bin, const float* energy, uint64_t n,
+                                     uint32_t n_columns, uint32_t n_bins, float* out) {
+  if (!out || (n && (!column || !bin || !energy))) return fail(RR_ERR_INVALID_ARG, "NULL buffer");
+  if (n_columns < 1 || n_columns > kMaxColumns) return fail(RR_ERR_INVALID_ARG, "n_columns must be in [1, 2^18]");
+  if (n_bins < 1 || n_bins > RR_MAX_BINS) return fail(RR_ERR_INVALID_ARG, "n_bins must be in [1, 16384]");
+  if (n >= (1ull << 31)) return fail(RR_ERR_INVALID_ARG, "at most 2^31 - 1 returns");
+  cudaStream_t st = current_stream();
+  const size_t img_bytes = (size_t)n_columns * n_bins * sizeof(float);
+  // device scratch of this call: inputs, records, a counter block, one scan
+  // descriptor with its prefix arrays, the image
+  uint32_t *d_col = nullptr, *d_bin = nullptr, *d_bad = nullptr;
+  float *d_e = nullptr, *d_img = nullptr;
+  uint2* d_recs = nullptr;
+  ScanCounters* d_ctr = nullptr;
+  ScanDesc* d_desc = nullptr;
+  uint32_t* d_pre = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    for (void* p : {(void*)d_col, (void*)d_bin, (void*)d_bad, (void*)d_e, (void*)d_img, (void*)d_recs, (void*)d_ctr,
+                    (void*)d_desc, (void*)d_pre})
+      if (p) cudaFree(p);
+  };
+  cudaError_t e = cudaSuccess;
+  const size_t nn = n ? n : 1;
+  if (e == cudaSuccess) e = cudaMalloc(&d_col, nn * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d_bin, nn * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d_e, nn * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d_recs, nn * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&d_bad, 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d_img, img_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&d_ctr, sizeof(ScanCounters));
+  if (e == cudaSuccess) e = cudaMalloc(&d_desc, sizeof(ScanDesc));
+  if (e == cudaSuccess) e = cudaMalloc(&d_pre, 4 * sizeof(uint32_t));
+  if (e == cudaSuccess && n) e = cudaMemcpyAsync(d_col, column, n * 4, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && n) e = cudaMemcpyAsync(d_bin, bin, n * 4, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && n) e = cudaMemcpyAsync(d_e, energy, n * 4, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, sizeof(ScanCounters), st);
+  ScanDesc desc;
+  memset(&desc, 0, sizeof desc);
+  desc.dims = make_uint4(n_columns, 1u, 1u, n_bins);
+  desc.offs = make_uint4(0u, 0u, kNone, 0u);
+  desc.image = d_img;
+  const uint32_t pre[4] = {0u, 0u, 0u, n_columns};   // ray prefix (unused) and column prefix
+  const uint32_t starts[2] = {0u, (uint32_t)n};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_desc, &desc, sizeof desc, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_pre, pre, sizeof pre, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&d_ctr->rec_start[0], starts, sizeof starts, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && n) {
+    k_pack_returns<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_col, d_bin, d_e, (uint32_t)n, n_columns, n_bins,
+                                                                 d_recs, d_bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host copies above came from the stack
+  uint32_t bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return cuda_fail(e, "accumulating the returns");
+  }
+  if (bad) {
+    cleanup();
+    return fail(RR_ERR_INVALID_ARG, "column must be non-decreasing and below n_columns");
+  }
+  ScanArgs a;
+  memset(&a, 0, sizeof a);
+  a.desc = d_desc;
+  a.ray0 = d_pre;
+  a.col0 = d_pre + 2;
+  a.n_scans = 1;
+  a.n_cols = n_columns;
+  a.max_bounces = 1;
+  a.max_bins = n_bins;
+  a.recs = d_recs;
+  a.ctr = d_ctr;
+  a.rec_cap = (uint32_t)nn;
+  e = launch_image(a, false, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_img, img_bytes, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return cuda_fail(e, "accumulating the returns");
+  }
+  cleanup();
+  return RR_OK;
+}

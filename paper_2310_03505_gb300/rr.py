@@ -144,6 +144,7 @@ SIGNATURES = {
     "rr_serve_stats_get": ([_P, C.POINTER(rr_serve_stats), C.c_int], C.c_int),
     "rr_scan_debug": ([_P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P, _P, _P, C.c_uint64,
                        C.POINTER(C.c_uint64), _P], C.c_int),
+    "rr_accumulate_returns": ([_P, _P, _P, C.c_uint64, C.c_uint32, C.c_uint32, _P], C.c_int),
     "rr_polar_to_db_u8": ([_P, C.c_uint64, C.c_float, _P], C.c_int),
     "rr_scene_stats": ([_P, C.POINTER(rr_stats), C.c_int], C.c_int),
     "rr_profile_enable": ([_P, C.c_int], C.c_int),
@@ -445,6 +446,15 @@ def rr_scan_debug(scene, pose: dict, params: dict, out_polar, ray_mask=None, seg
     _check(load().rr_scan_debug(scene, C.byref(P), C.byref(S), _ptr(mask), _ptr(out_polar), _ptr(segs),
                                 int(seg_capacity), C.byref(n), _ptr(tal)))
     return (segs[: n.value] if segs is not None else None), tal
+
+
+def rr_accumulate_returns(column, bin_, energy, n_columns: int, n_bins: int, out) -> None:
+    """column, bin_ [n] uint32 (column non-decreasing), energy [n] float32;
+    out [n_columns, n_bins] float32 (host or device)."""
+    _use_torch_stream()
+    n = int(column.shape[0])
+    _check(load().rr_accumulate_returns(_ptr(column), _ptr(bin_), _ptr(energy), n, int(n_columns), int(n_bins),
+                                        _ptr(out)))
 
 
 def rr_polar_to_db_u8(polar, cutoff_db: float, out) -> None:

@@ -54,6 +54,8 @@ int main(void) {
          offsetof(rr_sensor_params, flags));
   printf("%zu %zu %zu\n", sizeof(rr_batch_config), offsetof(rr_batch_config, node_format),
          offsetof(rr_batch_config, workspace_limit));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(rr_serve_config), sizeof(rr_serve_record), sizeof(rr_serve_stats),
+         offsetof(rr_serve_stats, busy_ms), offsetof(rr_serve_record, submit_ms));
   return 0;
 }
 '''
@@ -71,6 +73,9 @@ int main(void) {
                                           rr.rr_sensor_params.flags.offset]
     assert [int(x) for x in out[10:13]] == [C.sizeof(rr.rr_batch_config), rr.rr_batch_config.node_format.offset,
                                            rr.rr_batch_config.workspace_limit.offset]
+    assert [int(x) for x in out[13:18]] == [C.sizeof(rr.rr_serve_config), C.sizeof(rr.rr_serve_record),
+                                           C.sizeof(rr.rr_serve_stats), rr.rr_serve_stats.busy_ms.offset,
+                                           rr.rr_serve_record.submit_ms.offset]
     assert rr.SEGMENT_DTYPE.itemsize == C.sizeof(rr.rr_segment)
 
 

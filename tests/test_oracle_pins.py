@@ -567,3 +567,24 @@ def test_pin(check):
 
 def test_d3_statistics():
     check_d3_statistics()
+
+
+def test_bin_returns_is_the_exactly_rounded_sum():
+    """Sec. III-B binning in the oracle: each pixel equals the exact rational
+    sum of its returns rounded once, whatever the order; returns past the
+    last bin are dropped."""
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    n = 4000
+    col = np.sort(rng.integers(0, 3, n)).astype(np.uint32)
+    b = rng.integers(0, 6, n).astype(np.uint32)   # bin 5 lies past a 5-bin image
+    e = (10.0 ** rng.uniform(-9, 0, n)).astype(np.float32)
+    out = orc.bin_returns(col, b, e, 3, 5)
+    for c in range(3):
+        for k in range(5):
+            sel = (col == c) & (b == k)
+            exact = sum((Fraction(float(x)) for x in e[sel]), Fraction(0))
+            assert out[c, k] == float(exact)
+    # a cancelling sum that naive left-to-right addition gets wrong
+    vals = np.array([1e16, 1.0, -1e16, 1.0], np.float64)
+    assert orc.bin_returns(np.zeros(4, np.uint32), np.zeros(4, np.uint32), vals, 1, 1)[0, 0] == 2.0
