@@ -55,6 +55,7 @@ extern "C" {
 #define RR_SPECKLE 4u    /* multiply each return by an Exp(1) draw                    */
 #define RR_NOISE 8u      /* uniform system and ambient noise, Sec. III-C              */
 #define RR_COUNT_TRAVERSAL 16u /* count BVH nodes visited and triangles tested (stats) */
+#define RR_NOISE_PERLIN 32u    /* with RR_NOISE: Perlin instead of uniform noise, Sec. III-C */
 
 /* material flags (rr_material.flags) */
 #define RR_MAT_PERFECT_CONDUCTOR 1u /* R = 1, T = 0 whatever the angle            */
@@ -102,8 +103,15 @@ typedef struct {
    blur_sigma_bins    Gaussian blur along range (measurement noise), 0: off
    az_pattern_sigma   Gaussian beam pattern across azimuths (in beams), 0: off
    noise_sys, noise_amb amplitudes of the uniform system / ambient noise
-   flags          RR_MULTIPATH | RR_REFRACTION | RR_SPECKLE | RR_NOISE
-   seed, scan_id  key and counter words of the Philox4x32-10 draws */
+   flags          RR_MULTIPATH | RR_REFRACTION | RR_SPECKLE | RR_NOISE | RR_NOISE_PERLIN
+   seed, scan_id  key and counter words of the Philox4x32-10 draws
+   beam_aspect    elliptic beams (Sec. III-A: the cone stretched along an
+                  axis): the inclination offsets of the D3 cone are scaled by
+                  this factor and the receive weight of the air path follows
+                  the same elliptic Gaussian; 0 or 1: circular
+   noise_cell_az, noise_cell_bins  Perlin lattice spacing in azimuth beams and
+                  range bins (0: 8 and 32); the lattice wraps around the circle
+                  with round(n_azimuth / noise_cell_az) cells */
 typedef struct {
   uint32_t n_azimuth, rays_per_beam, max_bounces, n_bins;
   float beam_width_rad, beam_prob, elevation_rad, bin_size_m, t_min_m, min_energy, freq_hz;
@@ -111,7 +119,8 @@ typedef struct {
   uint32_t flags;
   uint64_t seed;
   uint32_t scan_id;
-  uint32_t reserved;
+  float beam_aspect;
+  float noise_cell_az, noise_cell_bins;
 } rr_sensor_params;
 
 /* One traced segment (debug dump): initial ray (az, k), branch path (bit i =

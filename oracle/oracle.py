@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MULTIPATH, REFRACTION, SPECKLE, NOISE = 1, 2, 4, 8
+MULTIPATH, REFRACTION, SPECKLE, NOISE, NOISE_PERLIN = 1, 2, 4, 8, 32
 NONE = 0xFFFFFFFF
 
 
@@ -40,7 +40,8 @@ class Params(C.Structure):
                 ("bin_size", C.c_double), ("t_min", C.c_double), ("min_energy", C.c_double), ("freq_hz", C.c_double),
                 ("blur_sigma_bins", C.c_double), ("az_pattern_sigma", C.c_double), ("noise_sys", C.c_double),
                 ("noise_amb", C.c_double),
-                ("flags", C.c_uint32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("scan_id", C.c_uint32)]
+                ("flags", C.c_uint32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("scan_id", C.c_uint32),
+                ("beam_aspect", C.c_double), ("noise_cell_az", C.c_double), ("noise_cell_bins", C.c_double)]
 
 
 class Pose(C.Structure):
@@ -103,6 +104,10 @@ def _load(path):
             L.orc_post.argtypes = [p, p, p, u32]
             L.orc_post.restype = C.c_int
             L.orc_db_u8.argtypes = [p, C.c_uint64, d, p]
+            L.orc_perlin.argtypes = [p, u32, u32, u32]
+            L.orc_perlin.restype = d
+            L.orc_receive_weight.argtypes = [p, p, u32, p]
+            L.orc_receive_weight.restype = d
             L.orc_max_threads.restype = C.c_int
     return L
 
@@ -131,12 +136,15 @@ def make_material(m: dict) -> Material:
 
 def make_params(s: dict) -> Params:
     flags = ((MULTIPATH if s.get("multipath") else 0) | (REFRACTION if s.get("refraction") else 0) |
-             (SPECKLE if s.get("speckle") else 0) | (NOISE if s.get("noise") else 0))
+             (SPECKLE if s.get("speckle") else 0) | (NOISE if s.get("noise") else 0) |
+             (NOISE_PERLIN if s.get("perlin") else 0))
     seed = int(s["seed"])
+    # 0 selects the defaults: a circular cone, Perlin cells of 8 beams x 32 bins
     return Params(s["n_azimuth"], s["rays_per_beam"], s["max_bounces"], s["n_bins"],
                   s["beam_width"], s["beam_prob"], s["elevation"], s["bin_size"], s["t_min"], s["min_energy"],
                   s["freq_hz"], s["blur_sigma_bins"], s["az_pattern_sigma"], s["noise_sys"], s["noise_amb"],
-                  flags, seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(s["scan_id"]))
+                  flags, seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(s["scan_id"]),
+                  s.get("beam_aspect") or 1.0, s.get("noise_cell_az") or 8.0, s.get("noise_cell_bins") or 32.0)
 
 
 def make_pose(pz: dict) -> Pose:
@@ -332,6 +340,17 @@ def bin_returns(column, bin_, energy, n_columns: int, n_bins: int):
     for (c, b), es in groups.items():
         out[c, b] = math.fsum(es)
     return out
+
+
+def receive_weight(params: dict, pz: dict, a: int, pt) -> float:
+    """Sec. III-A receive weight of beam a for a return from point pt."""
+    return lib().orc_receive_weight(C.byref(make_params(params)), C.byref(make_pose(pz)), a,
+                                    _ptr(np.asarray(pt, np.float64)))
+
+
+def perlin(params: dict, a: int, b: int, purpose: int) -> float:
+    """Sec. III-C Perlin noise value in [0, 1] of pixel (a, b); purpose 4 system, 5 ambient."""
+    return lib().orc_perlin(C.byref(make_params(params)), a, b, purpose)
 
 
 def db_u8(image, cutoff_db: float):

@@ -44,6 +44,7 @@
 #define ORC_REFRACTION 2u
 #define ORC_SPECKLE 4u
 #define ORC_NOISE 8u
+#define ORC_NOISE_PERLIN 32u
 
 /* flag thresholds of the parity protocol */
 #define FLAG_BARY 1e-5    /* barycentric margin (hits and near misses)        */
@@ -75,6 +76,8 @@ typedef struct {
   double beam_width, beam_prob, elevation, bin_size, t_min, min_energy, freq_hz;
   double blur_sigma_bins, az_pattern_sigma, noise_sys, noise_amb;
   uint32_t flags, seed_lo, seed_hi, scan_id;
+  double beam_aspect;                   /* elevation / azimuth spread of the D3 cone (1: circular) */
+  double noise_cell_az, noise_cell_bins; /* Perlin lattice spacing (beams, bins) */
 } orc_params;
 
 typedef struct {
@@ -197,7 +200,9 @@ void orc_beam_axis(const orc_params* p, const orc_pose* pose, uint32_t a, double
 /* ------------------------------------------------------------------------ */
 /* Sec. III-A, Eq. 2: D3 cone sample of initial ray k of azimuth a.          */
 /* N ~ N(0,1) by Box-Muller from two uniforms, omega ~ U[-pi, pi), r = sigma N */
-/* (d_az, d_inc) = r (cos omega, sin omega) around the beam axis.            */
+/* (d_az, d_inc) = r (cos omega, a sin omega) around the beam axis: a = 1 is */
+/* the circular cone, a != 1 the cone stretched along the elevation axis     */
+/* (elliptic beams, Sec. III-A).                                             */
 /* ------------------------------------------------------------------------ */
 void orc_d3_ray(const orc_params* p, const orc_pose* pose, uint32_t a, uint32_t k, double o[3], double d[3],
                 double* r_out, double* omega_out) {
@@ -209,7 +214,7 @@ void orc_d3_ray(const orc_params* p, const orc_pose* pose, uint32_t a, uint32_t 
   double r = sigma * gauss;
   double omega = M_PI * (2.0 * u2 - 1.0);
   double phi = 2.0 * M_PI * (double)a / (double)p->n_azimuth + r * cos(omega);
-  double th = p->elevation + r * sin(omega);
+  double th = p->elevation + p->beam_aspect * r * sin(omega);
   double ds[3] = {cos(th) * cos(phi), cos(th) * sin(phi), sin(th)};
   quat_rotate(pose->q, ds, d);
   normalize3(d);
@@ -499,14 +504,39 @@ static double alpha_np(const scene_t* s, int32_t medium, double freq) {
   return M_PI * sqrt(m->eps_r) * m->loss_tangent * freq / c0;
 }
 
-/* Gaussian receive weight of the current beam for a return arriving from p */
-static double receive_weight(const orc_params* p, const double axis[3], const double sensor[3], const double pt[3]) {
+/* Gaussian receive weight of beam a for a return arriving from pt: the
+   transmit density of the D3 cone read as the receive pattern.  delta is the
+   angle between pt - sensor and the beam axis; for an elliptic beam (aspect
+   a != 1) the spread along the offset's direction psi around the axis
+   (psi = 0 along increasing azimuth, pi/2 along increasing elevation) is
+   sigma / sqrt(cos^2 psi + sin^2 psi / a^2). */
+static double receive_weight(const orc_params* p, const orc_pose* pose, uint32_t a, const double axis[3],
+                             const double sensor[3], const double pt[3]) {
   double sigma = orc_d3_sigma(p->beam_width, p->beam_prob);
   if (sigma == 0.0) return 0.0;
   double v[3];
   sub3(pt, sensor, v);
   double delta = orc_angle(v, axis);
-  return exp(-0.5 * delta * delta / (sigma * sigma));
+  double f = 1.0;
+  if (p->beam_aspect != 1.0) {
+    double phi = 2.0 * M_PI * (double)a / (double)p->n_azimuth, th = p->elevation;
+    double ea_s[3] = {-sin(phi), cos(phi), 0.0};
+    double ee_s[3] = {-sin(th) * cos(phi), -sin(th) * sin(phi), cos(th)};
+    double ea[3], ee[3];
+    quat_rotate(pose->q, ea_s, ea);
+    quat_rotate(pose->q, ee_s, ee);
+    double ca = dot3(v, ea), ce = dot3(v, ee);
+    double perp2 = ca * ca + ce * ce;
+    if (perp2 > 0.0) f = (ca * ca + ce * ce / (p->beam_aspect * p->beam_aspect)) / perp2;
+  }
+  return exp(-0.5 * delta * delta * f / (sigma * sigma));
+}
+
+/* the receive weight of beam a of the pose for a return from pt (exported for the pins) */
+double orc_receive_weight(const orc_params* p, const orc_pose* pose, uint32_t a, const double pt[3]) {
+  double axis[3];
+  orc_beam_axis(p, pose, a, axis);
+  return receive_weight(p, pose, a, axis, pose->p, pt);
 }
 
 static double speckle_factor(const orc_params* p, uint32_t a, uint32_t k, uint32_t path, uint32_t bounce, int which) {
@@ -575,6 +605,10 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
       tri_normal(s, h.tri, n);
       double cos_i = -dot3(ray.d, n);
       if (fabs(cos_i) < FLAG_COS) seg.flags |= SEG_GRAZE;
+      /* a segment inside a medium that ends at grazing incidence: its length,
+         and the energy the medium absorbs over it, moves by the float32
+         resolution of its start point amplified by 1 / |cos theta0| */
+      if (ray.medium != ORC_AIR && fabs(cos_i) < FLAG_COST) seg.flags |= SEG_GRAZE;
       int entering = cos_i > 0.0;
       double n1 = n_cur, n2;
       int32_t next_medium;
@@ -653,7 +687,7 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
             col->shadow_queries++;
             if (vflag) seg.flags |= SEG_VIS;
             if (!occ) {
-              double g = receive_weight(p, axis, sensor, pt);
+              double g = receive_weight(p, pose, a, axis, sensor, pt);
               ret_a = base * w_a * g;
               if (ret_a > cap_a) ret_a = cap_a;
               range_a = 0.5 * (L1 + dist);
@@ -847,6 +881,50 @@ static int gauss_taps(double sigma, double* w, int max_r) {
   return r;
 }
 
+/* Sec. III-C, the Perlin noise model of ambient and system noise: gradient
+   noise (Perlin, "Improving noise", SIGGRAPH 2002) over the polar image.  The
+   lattice has P = max(1, round(n_az / cell_az)) cells around the circle
+   (periodic) and cells of cell_bins bins along range: pixel (a, bin) sits at
+   x = a P / n_az, y = bin / cell_bins.  Lattice point (I, J) carries the
+   unit gradient of angle 2 pi u, u the uniform of Philox counter
+   (scan_id, I, J, purpose) -- purpose 4 for system, 5 for ambient noise.
+   The four corner ramps are blended with the fade 6t^5 - 15t^4 + 10t^3; the
+   noise n lies in [-1/sqrt(2), 1/sqrt(2)] and is mapped to 1/2 + n/sqrt(2)
+   in [0, 1]. */
+static double perlin_fade(double t) { return t * t * t * (t * (6.0 * t - 15.0) + 10.0); }
+
+static void perlin_grad(const orc_params* p, uint32_t I, uint32_t J, uint32_t purpose, double g[2]) {
+  uint32_t x[4];
+  draw(p, I, J, purpose, x);
+  double th = 2.0 * M_PI * orc_u24(x[0]);
+  g[0] = cos(th);
+  g[1] = sin(th);
+}
+
+double orc_perlin(const orc_params* p, uint32_t a, uint32_t bin, uint32_t purpose) {
+  long P = lround((double)p->n_azimuth / p->noise_cell_az);
+  if (P < 1) P = 1;
+  double x = (double)a * (double)P / (double)p->n_azimuth;
+  double y = (double)bin / p->noise_cell_bins;
+  double xf = floor(x), yf = floor(y);
+  uint32_t i0 = (uint32_t)xf % (uint32_t)P, i1 = (i0 + 1u) % (uint32_t)P;
+  uint32_t j0 = (uint32_t)yf, j1 = j0 + 1u;
+  double fx = x - xf, fy = y - yf;
+  double g00[2], g10[2], g01[2], g11[2];
+  perlin_grad(p, i0, j0, purpose, g00);
+  perlin_grad(p, i1, j0, purpose, g10);
+  perlin_grad(p, i0, j1, purpose, g01);
+  perlin_grad(p, i1, j1, purpose, g11);
+  double n00 = g00[0] * fx + g00[1] * fy;
+  double n10 = g10[0] * (fx - 1.0) + g10[1] * fy;
+  double n01 = g01[0] * fx + g01[1] * (fy - 1.0);
+  double n11 = g11[0] * (fx - 1.0) + g11[1] * (fy - 1.0);
+  double sx = perlin_fade(fx), sy = perlin_fade(fy);
+  double nx0 = n00 + sx * (n10 - n00), nx1 = n01 + sx * (n11 - n01);
+  double n = nx0 + sy * (nx1 - nx0);
+  return 0.5 + n / sqrt(2.0);
+}
+
 /* image: [n_cols][n_bins] for the azimuth indices az_list (NULL = all).  The
    azimuth pattern needs every column and is refused on a subset. */
 int orc_post(double* image, const orc_params* p, const uint32_t* az_list, uint32_t n_cols) {
@@ -892,10 +970,18 @@ int orc_post(double* image, const orc_params* p, const uint32_t* az_list, uint32
     for (uint32_t c = 0; c < n_cols; ++c) {
       uint32_t a = az_list ? az_list[c] : c;
       for (uint32_t i = 0; i < nb; ++i) {
-        uint32_t xs[4], xa[4];
-        draw(p, a, i, 2u, xs);
-        draw(p, a, i, 3u, xa);
-        image[(size_t)c * nb + i] += p->noise_sys * orc_u24(xs[0]) + p->noise_amb * orc_u24(xa[0]);
+        double vs, va;
+        if (p->flags & ORC_NOISE_PERLIN) {
+          vs = orc_perlin(p, a, i, 4u);
+          va = orc_perlin(p, a, i, 5u);
+        } else {
+          uint32_t xs[4], xa[4];
+          draw(p, a, i, 2u, xs);
+          draw(p, a, i, 3u, xa);
+          vs = orc_u24(xs[0]);
+          va = orc_u24(xa[0]);
+        }
+        image[(size_t)c * nb + i] += p->noise_sys * vs + p->noise_amb * va;
       }
     }
   }

@@ -59,8 +59,40 @@ __device__ __forceinline__ uint32_t lower_col(const uint2* __restrict__ recs, ui
   return lo;
 }
 
-// Sec. III-C: uniform system and ambient noise of one pixel
-__device__ __forceinline__ float noise_at(uint4 rng, float4 post, uint32_t az, uint32_t bin) {
+// Sec. III-C Perlin noise (Perlin, "Improving noise", SIGGRAPH 2002) of
+// pixel (a, bin): gradient noise over a lattice of P = round(n_az / cell_az)
+// cells around the circle (periodic) and cells of cell_bins bins along range;
+// lattice point (I, J) has the unit gradient at angle 2 pi u, u the uniform of
+// Philox counter (scan_id, I, J, purpose); quintic fade; value 1/2 + n/sqrt(2)
+__device__ __forceinline__ float perlin_at(uint4 rng, uint32_t n_az, float cell_az, float cell_bins, uint32_t a,
+                                          uint32_t bin, uint32_t purpose) {
+  const int P = max(1, (int)roundf((float)n_az / cell_az));
+  const float x = (float)a * (float)P / (float)n_az, y = (float)bin / cell_bins;
+  const float xf = floorf(x), yf = floorf(y);
+  const uint32_t i0 = (uint32_t)xf % (uint32_t)P, i1 = (i0 + 1u) % (uint32_t)P;
+  const uint32_t j0 = (uint32_t)yf, j1 = j0 + 1u;
+  const float fx = x - xf, fy = y - yf;
+  float s00, c00, s10, c10, s01, c01, s11, c11;
+  sincospif(2.0f * u01(draw(rng, i0, j0, purpose).x), &s00, &c00);
+  sincospif(2.0f * u01(draw(rng, i1, j0, purpose).x), &s10, &c10);
+  sincospif(2.0f * u01(draw(rng, i0, j1, purpose).x), &s01, &c01);
+  sincospif(2.0f * u01(draw(rng, i1, j1, purpose).x), &s11, &c11);
+  const float n00 = c00 * fx + s00 * fy, n10 = c10 * (fx - 1.0f) + s10 * fy;
+  const float n01 = c01 * fx + s01 * (fy - 1.0f), n11 = c11 * (fx - 1.0f) + s11 * (fy - 1.0f);
+  const float sx = fx * fx * fx * (fx * (6.0f * fx - 15.0f) + 10.0f);
+  const float sy = fy * fy * fy * (fy * (6.0f * fy - 15.0f) + 10.0f);
+  const float nx0 = n00 + sx * (n10 - n00), nx1 = n01 + sx * (n11 - n01);
+  return 0.5f + (nx0 + sy * (nx1 - nx0)) * 0.70710678118654752f;
+}
+
+// Sec. III-C: system and ambient noise of one pixel, uniform or Perlin
+__device__ __forceinline__ float noise_at(const ScanDesc* sd, uint4 rng, float4 post, uint32_t az, uint32_t bin) {
+  if (rng.w & RR_NOISE_PERLIN) {
+    const float4 ext = __ldg(&sd->ext);
+    const uint32_t n_az = __ldg(&sd->dims.x);
+    return post.z * perlin_at(rng, n_az, ext.y, ext.z, az, bin, 4u) +
+           post.w * perlin_at(rng, n_az, ext.y, ext.z, az, bin, 5u);
+  }
   return post.z * u01(draw(rng, az, bin, 2u).x) + post.w * u01(draw(rng, az, bin, 3u).x);
 }
 
@@ -156,7 +188,7 @@ __global__ void __launch_bounds__(kImgBlock) k_bin_column(ScanArgs a) {
     const uint4 rng = __ldg(&sd->rng);
     const bool noise = (rng.w & RR_NOISE) != 0u;
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
-      out[i] = src[i] + (noise ? noise_at(rng, post, az, i) : 0.0f);
+      out[i] = src[i] + (noise ? noise_at(sd, rng, post, az, i) : 0.0f);
   }
 }
 
@@ -182,7 +214,7 @@ __global__ void __launch_bounds__(kImgBlock) k_az_pattern(ScanArgs a) {
     acc += taps[j + R] * tmp[(size_t)s * nb + i];
   }
   const uint4 rng = __ldg(&sd->rng);
-  if (rng.w & RR_NOISE) acc += noise_at(rng, post, az, i);
+  if (rng.w & RR_NOISE) acc += noise_at(sd, rng, post, az, i);
   sd->image[(size_t)az * nb + i] = acc;
 }
 

@@ -92,7 +92,7 @@ constexpr uint32_t kMaxColumns = 1u << (32 - kBinBits);   // columns of one laun
 constexpr uint32_t kMaxBatchScans = 0xFFFFu;       // scan index lives in 16 bits of RayRec.meta.w
 constexpr uint32_t kMediumMask = 0xFFFFu;
 
-// Per-scan constants of a batch (one pose and sensor model), 144 bytes.
+// Per-scan constants of a batch (one pose and sensor model), 160 bytes.
 // Kernels read the fields of the scan each ray belongs to.
 struct __align__(16) ScanDesc {
   float4 pos_rmax;   // sensor position, r_max = n_bins * bin_size
@@ -103,6 +103,7 @@ struct __align__(16) ScanDesc {
   float4 post;       // blur_sigma, az_sigma, noise_sys, noise_amb
   uint4 rng;         // seed_lo, seed_hi, scan_id, flags
   uint4 offs;        // first initial ray, first column, first float of image_tmp (or kNone), 0
+  float4 ext;        // beam aspect (elliptic beams), Perlin cell in beams, Perlin cell in bins, 0
   float* image;      // [n_az][n_bins] output (device)
   unsigned long long pad;
 };

@@ -92,7 +92,7 @@ __global__ void k_raygen(ScanArgs a) {
   const float r = d3_sigma(beam.x, beam.y) * gauss;
   float sw, cw;
   sincospif(2.0f * u2 - 1.0f, &sw, &cw);      // omega = pi (2 u2 - 1)
-  const float daz = r * cw, dinc = r * sw;
+  const float daz = r * cw, dinc = r * sw * __ldg(&sd->ext.x);   // elliptic beams: inclination stretched
   const float2 ph = beam_angle(az, __ldg(&sd->dims.x));
   float sd_, cd;
   sincosf(daz, &sd_, &cd);
@@ -484,8 +484,24 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
             const float4 beam = __ldg(&sd->beam);
             const float sigma = d3_sigma(beam.x, beam.y);
             const float3 p = s.w.o;
-            const float delta = angle_between(p - f3(__ldg(&sd->pos_rmax)), beam_axis(sd, tag >> 16));
-            const float g = sigma > 0.0f ? expf(-0.5f * (delta / sigma) * (delta / sigma)) : 0.0f;
+            const float3 v = p - f3(__ldg(&sd->pos_rmax));
+            const uint32_t az = tag >> 16;
+            const float delta = angle_between(v, beam_axis(sd, az));
+            float q = (delta / sigma) * (delta / sigma);
+            const float aspect = __ldg(&sd->ext.x);
+            if (aspect != 1.0f) {
+              // elliptic beam: the spread along the offset's direction around the axis
+              const float2 cs = beam_angle(az, __ldg(&sd->dims.x));
+              float se, ce;
+              sincosf(beam.z, &se, &ce);
+              const float4 qt = __ldg(&sd->quat);
+              const float3 ea = qrot(qt, make_float3(-cs.y, cs.x, 0.0f));
+              const float3 ee = qrot(qt, make_float3(-se * cs.x, -se * cs.y, ce));
+              const float c_a = dot(v, ea), c_e = dot(v, ee);
+              const float perp2 = c_a * c_a + c_e * c_e;
+              if (perp2 > 0.0f) q *= (c_a * c_a + c_e * c_e / (aspect * aspect)) / perp2;
+            }
+            const float g = sigma > 0.0f ? expf(-0.5f * q) : 0.0f;
             wag = wa * g;
           }
           hp->flags = fl;

@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librr.so")
 
 RR_OK, RR_ERR_INVALID_ARG, RR_ERR_OOM, RR_ERR_CAPACITY, RR_ERR_TIMEOUT, RR_ERR_CUDA, RR_ERR_BUSY = range(7)
-RR_MULTIPATH, RR_REFRACTION, RR_SPECKLE, RR_NOISE, RR_COUNT_TRAVERSAL = 1, 2, 4, 8, 16
+RR_MULTIPATH, RR_REFRACTION, RR_SPECKLE, RR_NOISE, RR_COUNT_TRAVERSAL, RR_NOISE_PERLIN = 1, 2, 4, 8, 16, 32
 RR_MAT_PERFECT_CONDUCTOR = 1
 RR_NO_HIT = 0xFFFFFFFF
 RR_K_RAYGEN, RR_K_TRACE, RR_K_SHADE, RR_K_IMAGE, RR_K_BUILD, RR_K_VIS, RR_K_COUNT = range(7)
@@ -49,7 +49,8 @@ class rr_sensor_params(C.Structure):
                 ("elevation_rad", C.c_float), ("bin_size_m", C.c_float), ("t_min_m", C.c_float),
                 ("min_energy", C.c_float), ("freq_hz", C.c_float), ("blur_sigma_bins", C.c_float),
                 ("az_pattern_sigma", C.c_float), ("noise_sys", C.c_float), ("noise_amb", C.c_float),
-                ("flags", C.c_uint32), ("seed", C.c_uint64), ("scan_id", C.c_uint32), ("reserved", C.c_uint32)]
+                ("flags", C.c_uint32), ("seed", C.c_uint64), ("scan_id", C.c_uint32), ("beam_aspect", C.c_float),
+                ("noise_cell_az", C.c_float), ("noise_cell_bins", C.c_float)]
 
 
 class rr_segment(C.Structure):
@@ -202,11 +203,12 @@ def _use_torch_stream():
 def make_params(s: dict) -> rr_sensor_params:
     flags = ((RR_MULTIPATH if s.get("multipath") else 0) | (RR_REFRACTION if s.get("refraction") else 0) |
              (RR_SPECKLE if s.get("speckle") else 0) | (RR_NOISE if s.get("noise") else 0) |
-             (RR_COUNT_TRAVERSAL if s.get("count_traversal") else 0))
+             (RR_COUNT_TRAVERSAL if s.get("count_traversal") else 0) | (RR_NOISE_PERLIN if s.get("perlin") else 0))
     return rr_sensor_params(s["n_azimuth"], s["rays_per_beam"], s["max_bounces"], s["n_bins"], s["beam_width"],
                             s["beam_prob"], s["elevation"], s["bin_size"], s["t_min"], s["min_energy"], s["freq_hz"],
                             s["blur_sigma_bins"], s["az_pattern_sigma"], s["noise_sys"], s["noise_amb"], flags,
-                            int(s["seed"]), int(s["scan_id"]), 0)
+                            int(s["seed"]), int(s["scan_id"]), s.get("beam_aspect", 0.0),
+                            s.get("noise_cell_az", 0.0), s.get("noise_cell_bins", 0.0))
 
 
 def make_pose(pz: dict) -> rr_pose:

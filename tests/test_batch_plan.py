@@ -31,7 +31,7 @@ def worst_case_bytes(ps):
     r = sum(2 * p["n_azimuth"] * p["rays_per_beam"] * ((1 << p["max_bounces"]) - 1) for p in ps)
     tmp = sum(p["n_azimuth"] * p["n_bins"] for p in ps if p["az_pattern_sigma"] > 0)
     tiles = (q + 255) // 256 + 1
-    desc = len(ps) * 144 + 2 * (len(ps) + 1) * 4
+    desc = len(ps) * 160 + 2 * (len(ps) + 1) * 4
     return 2 * a256(q * 48) + a256(q * 16) + a256(r * 8) + a256(tiles * 8) + a256(tmp * 4) + a256(desc)
 
 

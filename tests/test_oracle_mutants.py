@@ -37,8 +37,16 @@ MUTANTS = {
     "blur_clamp_edges": ("if (src < 0 || src >= (long)nb) continue;",
                          "if (src < 0) src = 0;\n          if (src >= (long)nb) src = nb - 1;"),
     "no_depletion": ("double e_refl = E1 * R - ret_t - (air_uses_T ? 0.0 : ret_a);", "double e_refl = E1 * R;"),
-    "receive_weight": ("exp(-0.5 * delta * delta / (sigma * sigma))", "exp(-delta * delta / (sigma * sigma))"),
-    "noise_same_uniform": ("p->noise_amb * orc_u24(xa[0])", "p->noise_amb * orc_u24(xs[0])"),
+    "receive_weight": ("exp(-0.5 * delta * delta * f / (sigma * sigma))", "exp(-delta * delta * f / (sigma * sigma))"),
+    "noise_same_uniform": ("va = orc_u24(xa[0]);", "va = orc_u24(xs[0]);"),
+    "elliptic_ignored": ("double th = p->elevation + p->beam_aspect * r * sin(omega);",
+                         "double th = p->elevation + r * sin(omega);"),
+    "elliptic_weight_inverted": ("ce * ce / (p->beam_aspect * p->beam_aspect)",
+                                 "ce * ce * (p->beam_aspect * p->beam_aspect)"),
+    "perlin_smoothstep": ("return t * t * t * (t * (6.0 * t - 15.0) + 10.0);", "return t * t * (3.0 - 2.0 * t);"),
+    "perlin_corner_swap": ("perlin_grad(p, i1, j0, purpose, g10);", "perlin_grad(p, i0, j1, purpose, g10);"),
+    "perlin_not_periodic": ("i1 = (i0 + 1u) % (uint32_t)P;", "i1 = i0 + 1u;"),
+    "perlin_scale": ("return 0.5 + n / sqrt(2.0);", "return 0.5 + n;"),
     "air_side": ("          if (side <= 0.0) candidate = 0;", "          if (side >= 0.0) candidate = 0;"),
     "traveled_range_half": ("push_ret(col, k, L1, e);", "push_ret(col, k, 0.5 * L1, e);"),
     "bin_off_by_one": ("img[(size_t)fb] += r->E;", "img[(size_t)fb + 1] += r->E;"),

@@ -68,9 +68,9 @@ def base_params(**kw):
     p = dict(n_azimuth=1, rays_per_beam=1, max_bounces=1, n_bins=2000, beam_width=math.radians(10.0),
              beam_prob=0.9, elevation=0.0, bin_size=0.01, t_min=1e-4, min_energy=0.0, freq_hz=76.5e9,
              blur_sigma_bins=0.0, az_pattern_sigma=0.0, noise_sys=0.0, noise_amb=0.0, multipath=False,
-             refraction=True, speckle=False, noise=False, seed=0x5EED, scan_id=0)
+             refraction=True, speckle=False, noise=False, seed=0x5EED, scan_id=0, beam_aspect=1.0)
     p.update(kw)
-    for k in ("beam_width", "beam_prob", "elevation", "bin_size", "t_min", "freq_hz"):
+    for k in ("beam_width", "beam_prob", "elevation", "bin_size", "t_min", "freq_hz", "beam_aspect"):
         p[k] = float(np.float32(p[k]))
     return p
 
@@ -554,10 +554,77 @@ def check_db_map():
     assert list(out) == [255, 0, 128, 0, 0, 255]
 
 
+def check_elliptic_beam():
+    """Elliptic beams (Sec. III-A, the cone stretched along an axis): with
+    aspect a the inclination offsets of the D3 rays spread a times wider than
+    the azimuth offsets, and the receive weight falls off as
+    exp(-delta^2 / 2 sigma^2) along azimuth, exp(-delta^2 / 2 (a sigma)^2)
+    along elevation; a = 1 is the circular cone."""
+    n = 20000
+    for aspect in (1.0, 2.0):
+        p = base_params(n_azimuth=1, rays_per_beam=n, beam_aspect=aspect)
+        daz = np.empty(n)
+        dinc = np.empty(n)
+        for k in range(n):
+            _, d, _, _ = orc.d3_ray(p, POSE0, 0, k)
+            daz[k] = math.atan2(d[1], d[0])
+            dinc[k] = math.asin(max(-1.0, min(1.0, d[2])))
+        ratio = np.var(dinc) / np.var(daz)
+        assert abs(ratio / aspect ** 2 - 1.0) < 0.08, (aspect, ratio)
+        sigma = orc.d3_sigma(p["beam_width"], p["beam_prob"])
+        for delta in (0.5 * sigma, sigma, 2.0 * sigma):
+            g_az = orc.receive_weight(p, POSE0, 0, [10 * math.cos(delta), 10 * math.sin(delta), 0.0])
+            g_el = orc.receive_weight(p, POSE0, 0, [10 * math.cos(delta), 0.0, 10 * math.sin(delta)])
+            assert abs(g_az - math.exp(-0.5 * (delta / sigma) ** 2)) < 1e-12
+            assert abs(g_el - math.exp(-0.5 * (delta / (aspect * sigma)) ** 2)) < 1e-12
+        assert abs(orc.receive_weight(p, POSE0, 0, [5.0, 0.0, 0.0]) - 1.0) < 1e-15
+
+
+def _perlin_gradient(p, I, J, purpose):
+    """Lattice gradient of the reading: unit vector at angle 2 pi u, u the
+    uniform of Philox counter (scan_id, I, J, purpose) (generator pinned by
+    the known-answer vectors)."""
+    key = (p["seed"] & 0xFFFFFFFF, p["seed"] >> 32)
+    x = orc.philox((p["scan_id"], I, J, purpose), key)
+    th = 2.0 * math.pi * orc.u24(x[0])
+    return math.cos(th), math.sin(th)
+
+
+def check_perlin():
+    """Perlin noise (Sec. III-C) has value 1/2 at the lattice points, slope
+    there equal to the lattice gradient (from both sides), a second derivative
+    that is continuous across cell borders (the quintic fade), continuity
+    across the 360 degree seam, and values in [0, 1]."""
+    cell = 1024
+    p = base_params(n_azimuth=8 * cell, n_bins=4 * cell, noise=True, perlin=True, noise_cell_az=cell,
+                    noise_cell_bins=cell, seed=0x1234ABCD5678, scan_id=3)
+    v = lambda a, b, pu=4: orc.perlin(p, a % (8 * cell), b, pu)
+    h = 1.0 / cell
+    for pu in (4, 5):
+        for I, J in ((1, 1), (5, 2), (0, 1)):
+            A, B = I * cell, J * cell
+            assert abs(v(A, B, pu) - 0.5) < 1e-15
+            gx, gy = _perlin_gradient(p, I, J, pu)
+            right = (v(A + 1, B, pu) - v(A, B, pu)) / h
+            left = (v(A, B, pu) - v(A - 1, B, pu)) / h   # I = 0: across the seam
+            up = (v(A, B + 1, pu) - v(A, B, pu)) / h
+            down = (v(A, B, pu) - v(A, B - 1, pu)) / h
+            for d_, g_ in ((right, gx), (left, gx), (up, gy), (down, gy)):
+                assert abs(d_ - g_ / math.sqrt(2.0)) < 5e-3, (pu, I, J, d_, g_)
+            # second derivative on both sides of the lattice line x = I (off the line y = J)
+            Bq = B + cell // 3
+            d2l = (v(A - 2, Bq, pu) - 2 * v(A - 1, Bq, pu) + v(A, Bq, pu)) / h ** 2
+            d2r = (v(A, Bq, pu) - 2 * v(A + 1, Bq, pu) + v(A + 2, Bq, pu)) / h ** 2
+            assert abs(d2l - d2r) < 0.5, (pu, I, J, d2l, d2r)
+    vals = [orc.perlin(p, a, b, 4) for a in range(0, 8 * cell, 97) for b in range(0, 4 * cell, 89)]
+    assert 0.0 <= min(vals) and max(vals) <= 1.0 and np.std(vals) > 0.05
+
+
 ALL_CHECKS = [check_philox_kat, check_u24, check_d3_sigma, check_d3_pose_and_azimuth, check_fresnel_closed_forms,
               check_snell, check_brdf_normalisation, check_brdf_window_pins, check_closest_brute_force,
               check_normal_incidence_plane, check_oblique_plane, check_slab, check_slab_multipath,
-              check_corner_reflector, check_lidar_like, check_conservation_tiny, check_post_pass, check_db_map]
+              check_corner_reflector, check_lidar_like, check_conservation_tiny, check_post_pass, check_db_map,
+              check_elliptic_beam, check_perlin]
 
 
 @pytest.mark.parametrize("check", ALL_CHECKS, ids=lambda f: f.__name__[6:])
