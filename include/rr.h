@@ -59,6 +59,16 @@ extern "C" {
 
 /* material flags (rr_material.flags) */
 #define RR_MAT_PERFECT_CONDUCTOR 1u /* R = 1, T = 0 whatever the angle            */
+/* Lobe of the beam window (Eq. 4) other than Eq. 5 (Sec. III-A: user-defined
+   BRDFs per material).  The lobe is a symmetric density over the deviation w
+   from the mirror direction on [-pi/2, pi/2], normalised to unit integral. */
+#define RR_MAT_COOK_TORRANCE 2u  /* the microfacet lobe of the paper's Sec. IV: A = diffuse
+                                    amount kd, B = Beckmann roughness m > 0; f(w) = kd cos(w)/2
+                                    + (1 - kd) D(w/2) / Zw, D the Beckmann distribution of the
+                                    half-vector angle w/2, Zw its integral (closed form) */
+#define RR_MAT_TABULATED_LOBE 4u /* the density set by rr_scene_set_lobe (until then Eq. 5 with
+                                    A, B, C) */
+#define RR_LOBE_SAMPLES 4097u    /* samples of a tabulated lobe: density at j (pi/2) / 4096 */
 
 #define RR_NO_HIT 0xFFFFFFFFu
 
@@ -214,6 +224,14 @@ int rr_scene_update_vertices(rr_scene* scene, const float* vertices);
 /* Sizes of the scene and its latest build.  Blocking (reads the wide node
    count of the latest build). */
 int rr_scene_info_get(const rr_scene* scene, rr_scene_info* info);
+
+/* Sets the lobe of material `material` (created with RR_MAT_TABULATED_LOBE)
+   to the symmetric density given at RR_LOBE_SAMPLES points x_j = j (pi/2) /
+   (RR_LOBE_SAMPLES - 1) of [0, pi/2] (host or device; finite, >= 0, not all
+   zero).  The density between samples is the quadratic through each triple
+   (x_2k, x_2k+1, x_2k+2); it is normalised to unit integral over
+   [-pi/2, pi/2].  Rebuilds the scene's lobe tables (stream ordered). */
+int rr_scene_set_lobe(rr_scene* scene, uint32_t material, const float* density);
 
 /* Copies the LBVH to host arrays (each may be NULL): morton [T] sorted
    Morton codes, perm [T] triangle id of each sorted leaf, children

@@ -28,9 +28,15 @@ MULTIPATH, REFRACTION, SPECKLE, NOISE, NOISE_PERLIN = 1, 2, 4, 8, 32
 NONE = 0xFFFFFFFF
 
 
+LOBE_EQ5, LOBE_COOK_TORRANCE, LOBE_TABLE = 0, 1, 2
+LOBE_CELLS = 2048
+LOBE_SAMPLES = 2 * LOBE_CELLS + 1
+_LOBE_KINDS = {"eq5": LOBE_EQ5, "cook_torrance": LOBE_COOK_TORRANCE, "table": LOBE_TABLE}
+
+
 class Material(C.Structure):
     _fields_ = [("eps_r", C.c_double), ("loss_tangent", C.c_double), ("A", C.c_double), ("B", C.c_double),
-                ("C", C.c_double), ("pec", C.c_int32), ("pad", C.c_int32)]
+                ("C", C.c_double), ("pec", C.c_int32), ("lobe", C.c_int32), ("table", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -104,6 +110,10 @@ def _load(path):
             L.orc_post.argtypes = [p, p, p, u32]
             L.orc_post.restype = C.c_int
             L.orc_db_u8.argtypes = [p, C.c_uint64, d, p]
+            L.orc_beckmann.argtypes = [d, d]
+            L.orc_beckmann.restype = d
+            L.orc_beckmann_norm.argtypes = [d]
+            L.orc_beckmann_norm.restype = d
             L.orc_perlin.argtypes = [p, u32, u32, u32]
             L.orc_perlin.restype = d
             L.orc_receive_weight.argtypes = [p, p, u32, p]
@@ -130,8 +140,18 @@ def _vec(x):
 
 # ---------------------------------------------------------------- conversions
 def make_material(m: dict) -> Material:
-    return Material(float(m["eps_r"]), float(m["loss_tangent"]), float(m["A"]), float(m["B"]), float(m["C"]),
-                    1 if m.get("pec") else 0, 0)
+    """Material dict: eps_r, loss_tangent, A, B, C, pec, lobe ("eq5",
+    "cook_torrance" or "table") and, for "table", lobe_table (LOBE_SAMPLES
+    densities over [0, pi/2])."""
+    kind = _LOBE_KINDS[m.get("lobe", "eq5")]
+    table = None
+    if kind == LOBE_TABLE:
+        table = np.ascontiguousarray(np.asarray(m["lobe_table"], np.float64))
+        assert table.shape == (LOBE_SAMPLES,)
+    out = Material(float(m["eps_r"]), float(m["loss_tangent"]), float(m["A"]), float(m["B"]), float(m["C"]),
+                   1 if m.get("pec") else 0, kind, table.ctypes.data if table is not None else None)
+    out._table = table   # keeps the samples alive as long as the struct
+    return out
 
 
 def make_params(s: dict) -> Params:
@@ -284,7 +304,8 @@ def scan(vertices, triangles, material_ids, materials, pz: dict, params: dict, a
     v = np.ascontiguousarray(vertices, np.float32)
     t = np.ascontiguousarray(triangles, np.uint32)
     m = np.ascontiguousarray(material_ids, np.uint16)
-    mats = (Material * len(materials))(*[make_material(x) for x in materials])
+    made = [make_material(x) for x in materials]   # holds the lobe tables during the call
+    mats = (Material * len(materials))(*made)
     pr, po = make_params(params), make_pose(pz)
     if az_list is None:
         cols = None
@@ -305,6 +326,7 @@ def scan(vertices, triangles, material_ids, materials, pz: dict, params: dict, a
     rc = L.orc_scan(_ptr(v), v.shape[0], _ptr(t), t.shape[0], _ptr(m), mats, len(materials), C.byref(po),
                     C.byref(pr), _ptr(cols), n_cols, _ptr(image), _ptr(image_m), _ptr(slack), _ptr(flags),
                     _ptr(tallies), _ptr(segs), cap, C.byref(n_segs), _ptr(counts), int(threads))
+    del made
     if rc != 0:
         raise RuntimeError(f"orc_scan failed with code {rc}")
     raw, raw_m = image.copy(), image_m.copy()
@@ -312,7 +334,10 @@ def scan(vertices, triangles, material_ids, materials, pz: dict, params: dict, a
         for img in (image, image_m):
             if L.orc_post(_ptr(img), C.byref(pr), _ptr(cols), n_cols) != 0:
                 raise RuntimeError("orc_post: the azimuth pattern needs every column")
-    return dict(image=image, image_masked=image_m, raw=raw, raw_masked=raw_m, slack=slack, flags=flags,
+    # bit 0: a decision float32 can take the other way (paths, energies,
+    # images); bit 1: only the per-ray tallies can move past their tolerance
+    return dict(image=image, image_masked=image_m, raw=raw, raw_masked=raw_m, slack=slack,
+                flags=(flags & 1).astype(np.uint8), tally_flags=(flags != 0).astype(np.uint8),
                 tallies=tallies, segments=segs[: n_segs.value] if want_segments else None, counts=counts)
 
 
@@ -340,6 +365,14 @@ def bin_returns(column, bin_, energy, n_columns: int, n_bins: int):
     for (c, b), es in groups.items():
         out[c, b] = math.fsum(es)
     return out
+
+
+def beckmann(t: float, m: float) -> float:
+    return lib().orc_beckmann(float(t), float(m))
+
+
+def beckmann_norm(m: float) -> float:
+    return lib().orc_beckmann_norm(float(m))
 
 
 def receive_weight(params: dict, pz: dict, a: int, pt) -> float:

@@ -53,6 +53,7 @@
 #define FLAG_TIR 1e-6     /* |eta^2 sin^2 - 1| next to the critical angle      */
 #define FLAG_COS 1e-6     /* grazing incidence |cos theta0|                    */
 #define FLAG_COST 0.05    /* refraction next to grazing: cos theta2 below it  */
+#define FLAG_TALLY 1e-6   /* energy a tally may move by (half its tolerance)  */
 
 /* segment flag bits (diagnostics) */
 #define SEG_EDGE 1u
@@ -65,10 +66,19 @@
 #define SEG_VIS 128u
 #define SEG_EMIN 256u
 #define SEG_SNELL 512u
+#define SEG_TALLY 1024u   /* affects only the per-ray energy tallies */
+
+/* lobe kinds of a material (Sec. III-A: user-defined BRDFs per material) */
+#define ORC_LOBE_EQ5 0           /* Eq. 5 with A, B, C                                  */
+#define ORC_LOBE_COOK_TORRANCE 1 /* microfacet lobe, A = diffuse amount, B = roughness  */
+#define ORC_LOBE_TABLE 2         /* tabulated density, table[ORC_LOBE_SAMPLES]          */
+#define ORC_LOBE_CELLS 2048
+#define ORC_LOBE_SAMPLES (2 * ORC_LOBE_CELLS + 1)
 
 typedef struct {
   double eps_r, loss_tangent, A, B, C;
-  int32_t pec, pad;
+  int32_t pec, lobe;
+  const double* table; /* ORC_LOBE_TABLE: density at x_j = j (pi/2) / (2 ORC_LOBE_CELLS) */
 } orc_material;
 
 typedef struct {
@@ -296,8 +306,106 @@ double orc_int_cospow(double c, double lo, double hi) {
   return sum;
 }
 
-/* Z = A pi + 2 B + S sqrt(pi) Gamma((C+1)/2) / Gamma(C/2 + 1) */
+/* ------------------------------------------------------------------------ */
+/* Cook-Torrance lobe (the microfacet model the paper uses as a user BRDF,   */
+/* Sec. IV; Cook & Torrance 1982, Walter et al. 2007).  Read on the same     */
+/* 1-D domain as Eq. 5: w is the deviation of the return from the mirror     */
+/* direction, whose half vector deviates from the normal by w/2.  The lobe  */
+/* is a diffuse part cos(w)/2 plus a Beckmann microfacet part, each of unit  */
+/* integral over [-pi/2, pi/2]:                                              */
+/*   f(w) = kd cos(w)/2 + (1 - kd) D(w/2) / Zw,                              */
+/*   D(t) = exp(-tan^2 t / m^2) / (pi m^2 cos^4 t),  kd = A, m = B,          */
+/*   Zw = integral of D(w/2) over [-pi/2, pi/2] = 2 integral of D over       */
+/*        [-pi/4, pi/4] = 2 [m sqrt(pi) erf(1/m) (1 + m^2/2) - m^2 e^(-1/m^2)] */
+/*        / (pi m^2)   (substituting u = tan t).                             */
+/* ------------------------------------------------------------------------ */
+double orc_beckmann(double t, double m) {
+  double c = cos(t), tt = tan(t);
+  return exp(-tt * tt / (m * m)) / (M_PI * m * m * c * c * c * c);
+}
+
+double orc_beckmann_norm(double m) {
+  return 2.0 * (m * sqrt(M_PI) * erf(1.0 / m) * (1.0 + 0.5 * m * m) - m * m * exp(-1.0 / (m * m))) / (M_PI * m * m);
+}
+
+static double ct_density(const orc_material* m, double w) {
+  return m->A * 0.5 * cos(w) + (1.0 - m->A) * orc_beckmann(0.5 * w, m->B) / orc_beckmann_norm(m->B);
+}
+
+/* adaptive Simpson of the Cook-Torrance density over [a, b] */
+static double ct_rec(const orc_material* m, double a, double b, double fa, double fm, double fb, double whole,
+                     double eps, int depth) {
+  double c = 0.5 * (a + b), lm = 0.5 * (a + c), rm = 0.5 * (c + b);
+  double flm = ct_density(m, lm), frm = ct_density(m, rm);
+  double left = (c - a) / 6.0 * (fa + 4.0 * flm + fm), right = (b - c) / 6.0 * (fm + 4.0 * frm + fb);
+  double delta = left + right - whole;
+  if (depth <= 0 || fabs(delta) <= 15.0 * eps) return left + right + delta / 15.0;
+  return ct_rec(m, a, c, fa, flm, fm, left, 0.5 * eps, depth - 1) +
+         ct_rec(m, c, b, fm, frm, fb, right, 0.5 * eps, depth - 1);
+}
+
+static double ct_integral(const orc_material* m, double lo, double hi) {
+  const int panels = 256;
+  double h = (hi - lo) / panels, sum = 0.0;
+  for (int i = 0; i < panels; ++i) {
+    double a = lo + h * i, b = (i == panels - 1) ? hi : lo + h * (i + 1);
+    double fa = ct_density(m, a), fb = ct_density(m, b), fm = ct_density(m, 0.5 * (a + b));
+    sum += ct_rec(m, a, b, fa, fm, fb, (b - a) / 6.0 * (fa + 4.0 * fm + fb), 1e-17, 48);
+  }
+  return sum;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tabulated lobe (Sec. III-A: a user-defined BRDF per material): a          */
+/* symmetric density given at x_j = j h, h = (pi/2) / (2 ORC_LOBE_CELLS),    */
+/* read as the quadratic through (x_2k, x_2k+1, x_2k+2) on every cell, so    */
+/* that Simpson's rule integrates each cell exactly.  Normalised to unit     */
+/* integral over [-pi/2, pi/2].                                              */
+/* ------------------------------------------------------------------------ */
+/* integral of cell k's quadratic from its start to local coordinate s in [0, 2] (units of h) */
+static double table_cell_prim(const double* t, int k, double s) {
+  double f0 = t[2 * k], f1 = t[2 * k + 1], f2 = t[2 * k + 2];
+  double s2 = s * s, s3 = s2 * s;
+  return f0 * (s3 / 6.0 - 0.75 * s2 + s) - f1 * (s3 / 3.0 - s2) + f2 * (s3 / 6.0 - 0.25 * s2);
+}
+
+/* integral of the tabulated density over [0, x], 0 <= x <= pi/2 */
+static double table_prim(const double* t, double x) {
+  const double h = 0.5 * M_PI / (2.0 * ORC_LOBE_CELLS);
+  double u = x / (2.0 * h);   /* in cells */
+  if (u <= 0.0) return 0.0;
+  if (u > ORC_LOBE_CELLS) u = ORC_LOBE_CELLS;
+  int k = (int)floor(u);
+  if (k >= ORC_LOBE_CELLS) k = ORC_LOBE_CELLS - 1;
+  double sum = 0.0;
+  for (int c = 0; c < k; ++c) sum += table_cell_prim(t, c, 2.0);
+  sum += table_cell_prim(t, k, 2.0 * (u - k));
+  return h * sum;
+}
+
+static double table_value(const double* t, double x) {
+  const double h = 0.5 * M_PI / (2.0 * ORC_LOBE_CELLS);
+  x = fabs(x);
+  double u = x / (2.0 * h);
+  int k = (int)floor(u);
+  if (k >= ORC_LOBE_CELLS) k = ORC_LOBE_CELLS - 1;
+  double s = 2.0 * (u - k);
+  double f0 = t[2 * k], f1 = t[2 * k + 1], f2 = t[2 * k + 2];
+  return f0 * (s - 1.0) * (s - 2.0) * 0.5 - f1 * s * (s - 2.0) + f2 * s * (s - 1.0) * 0.5;
+}
+
+/* signed-range integral of the symmetric tabulated density over [lo, hi] */
+static double table_integral(const double* t, double lo, double hi) {
+  if (lo >= 0.0) return table_prim(t, hi) - table_prim(t, lo);
+  if (hi <= 0.0) return table_prim(t, -lo) - table_prim(t, -hi);
+  return table_prim(t, hi) + table_prim(t, -lo);
+}
+
+/* Z = A pi + 2 B + S sqrt(pi) Gamma((C+1)/2) / Gamma(C/2 + 1) for Eq. 5;
+   the integral of the density over [-pi/2, pi/2] for the other lobes */
 double orc_brdf_norm(const orc_material* m) {
+  if (m->lobe == ORC_LOBE_COOK_TORRANCE) return 1.0;
+  if (m->lobe == ORC_LOBE_TABLE) return 2.0 * table_prim(m->table, M_PI / 2);
   double S = 1.0 - m->A - m->B;
   double gr = exp(lgamma(0.5 * (m->C + 1.0)) - lgamma(0.5 * m->C + 1.0));
   return m->A * M_PI + 2.0 * m->B + S * sqrt(M_PI) * gr;
@@ -305,6 +413,8 @@ double orc_brdf_norm(const orc_material* m) {
 
 double orc_brdf_density(const orc_material* m, double w) {
   if (w < -M_PI / 2 || w > M_PI / 2) return 0.0;
+  if (m->lobe == ORC_LOBE_COOK_TORRANCE) return ct_density(m, w);
+  if (m->lobe == ORC_LOBE_TABLE) return table_value(m->table, w) / orc_brdf_norm(m);
   double S = 1.0 - m->A - m->B;
   return (m->A + m->B * cos(w) + S * cospow(w, m->C)) / orc_brdf_norm(m);
 }
@@ -314,6 +424,8 @@ double orc_brdf_window(const orc_material* m, double w, double b) {
   if (lo < -M_PI / 2) lo = -M_PI / 2;
   if (hi > M_PI / 2) hi = M_PI / 2;
   if (!(hi > lo)) return 0.0;
+  if (m->lobe == ORC_LOBE_COOK_TORRANCE) return ct_integral(m, lo, hi);
+  if (m->lobe == ORC_LOBE_TABLE) return table_integral(m->table, lo, hi) / orc_brdf_norm(m);
   double S = 1.0 - m->A - m->B;
   double v = m->A * (hi - lo) + m->B * (sin(hi) - sin(lo));
   if (S != 0.0) v += S * orc_int_cospow(m->C, lo, hi);
@@ -583,7 +695,8 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
       if (h.tri == ORC_NONE || h.t >= t_lim) {
         tal[2] += ray.E; /* escaped */
         push_seg(col, &seg);
-        if (seg.flags) flagged = 1;
+        if (seg.flags & ~SEG_TALLY) flagged |= 1;
+        if (seg.flags & SEG_TALLY) flagged |= 2;
         continue;
       }
       seg.tri = h.tri;
@@ -605,10 +718,16 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
       tri_normal(s, h.tri, n);
       double cos_i = -dot3(ray.d, n);
       if (fabs(cos_i) < FLAG_COS) seg.flags |= SEG_GRAZE;
-      /* a segment inside a medium that ends at grazing incidence: its length,
-         and the energy the medium absorbs over it, moves by the float32
-         resolution of its start point amplified by 1 / |cos theta0| */
-      if (ray.medium != ORC_AIR && fabs(cos_i) < FLAG_COST) seg.flags |= SEG_GRAZE;
+      /* a segment inside a medium that ends at grazing incidence: its length
+         moves by the float32 resolution of its start point amplified by
+         1 / |cos theta0|, and the energy the medium absorbs over it by
+         2 alpha E_end as much; flagged for the per-ray tallies when that can
+         reach half their tolerance */
+      if (ray.medium != ORC_AIR && fabs(cos_i) < FLAG_COST) {
+        double omax = fmax(fmax(fabs(ray.o[0]), fabs(ray.o[1])), fmax(fabs(ray.o[2]), 1.0));
+        double dt = 8.0 * omax * 0x1p-24 / fmax(fabs(cos_i), 1e-12);
+        if (2.0 * alpha_np(s, ray.medium, p->freq_hz) * E1 * dt > FLAG_TALLY) seg.flags |= SEG_TALLY;
+      }
       int entering = cos_i > 0.0;
       double n1 = n_cur, n2;
       int32_t next_medium;
@@ -730,7 +849,8 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
       if (!spawn_refr) tal[3] += e_refr;
 
       push_seg(col, &seg);
-      if (seg.flags) flagged = 1;
+      if (seg.flags & ~SEG_TALLY) flagged |= 1;   /* bit 0: paths, energies, images */
+      if (seg.flags & SEG_TALLY) flagged |= 2;    /* bit 1: the tallies only */
 
       if (sp + 2 > cap) {
         cap *= 2;
@@ -775,7 +895,7 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
 static void bin_column(const orc_params* p, const column_t* col, double* img, double* img_masked, double* slack) {
   for (size_t i = 0; i < col->n_ret; ++i) {
     const oret_t* r = &col->ret[i];
-    const int flagged = col->flagged[r->k];
+    const int flagged = col->flagged[r->k] & 1;
     double x = r->range / p->bin_size;
     double fb = floor(x);
     if (fb >= 0.0 && fb < (double)p->n_bins) {

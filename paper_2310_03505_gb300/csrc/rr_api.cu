@@ -216,7 +216,8 @@ int rr_scene_destroy(rr_scene* s) {
   void* ptrs[] = {s->d_vtx, s->d_idx, s->d_mat_id, s->d_raw_mats, s->d_mats, s->d_lut, s->d_lut_cells,
                   s->d_tri, s->d_nodes, s->d_centroid, s->d_keys[0], s->d_keys[1], s->d_vals[0], s->d_vals[1],
                   s->d_hist, s->d_parent, s->d_child, s->d_nbox, s->d_visit, s->d_misc,
-                  s->d_cut, s->d_wnodes, s->d_wtri, s->d_wsrc, s->d_wrec, s->d_wctr};
+                  s->d_cut, s->d_wnodes, s->d_wtri, s->d_wsrc, s->d_wrec, s->d_wctr, s->d_lobe_kind,
+                  s->d_lobe_samples};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ctx_free(&s->main);
@@ -253,10 +254,18 @@ int rr_scene_create(const float* vertices, uint32_t n_vertices, const uint32_t* 
     if (!(std::isfinite(x.eps_r) && std::isfinite(x.loss_tangent) && std::isfinite(x.A) && std::isfinite(x.B) &&
           std::isfinite(x.C)))
       return fail(RR_ERR_INVALID_ARG, "material " + std::to_string(m) + ": non-finite value");
-    if (x.eps_r < 1.f || x.loss_tangent < 0.f || x.A < 0.f || x.B < 0.f || x.A > 1.f || x.B > 1.f ||
-        x.A + x.B > 1.f + 1e-6f || x.C < 0.f)
+    const bool ct = (x.flags & RR_MAT_COOK_TORRANCE) != 0u, tab = (x.flags & RR_MAT_TABULATED_LOBE) != 0u;
+    if (ct && tab) return fail(RR_ERR_INVALID_ARG, "material " + std::to_string(m) + ": one lobe kind only");
+    if (x.eps_r < 1.f || x.loss_tangent < 0.f)
+      return fail(RR_ERR_INVALID_ARG, "material " + std::to_string(m) + ": needs eps_r >= 1, tan_d >= 0");
+    if (ct) {
+      if (x.A < 0.f || x.A > 1.f || !(x.B >= 1e-3f && x.B <= 10.f))
+        return fail(RR_ERR_INVALID_ARG, "material " + std::to_string(m) +
+                                            ": Cook-Torrance needs 0 <= A (diffuse) <= 1, 1e-3 <= B (roughness) <= 10");
+    } else if (x.A < 0.f || x.B < 0.f || x.A > 1.f || x.B > 1.f || x.A + x.B > 1.f + 1e-6f || x.C < 0.f) {
       return fail(RR_ERR_INVALID_ARG, "material " + std::to_string(m) +
-                                          ": needs eps_r >= 1, tan_d >= 0, 0 <= A, B, A + B <= 1, C >= 0");
+                                          ": needs 0 <= A, B, A + B <= 1, C >= 0");
+    }
   }
   cudaStream_t st = t_stream;
   rr_scene* s = new rr_scene();
@@ -264,6 +273,11 @@ int rr_scene_create(const float* vertices, uint32_t n_vertices, const uint32_t* 
   s->nv = n_vertices;
   s->nt = n_triangles;
   s->nm = n_materials;
+  s->lobe_kind.resize(n_materials);
+  for (uint32_t m = 0; m < n_materials; ++m)   // a tabulated lobe is Eq. 5 until it is set
+    s->lobe_kind[m] = (mats[m].flags & RR_MAT_COOK_TORRANCE) ? (uint8_t)rr::kLobeCookTorrance : (uint8_t)rr::kLobeEq5;
+  s->raw_flags.resize(n_materials);
+  for (uint32_t m = 0; m < n_materials; ++m) s->raw_flags[m] = mats[m].flags;
   auto bail = [&](int code) {
     rr_scene_destroy(s);
     return code;
@@ -380,6 +394,33 @@ int rr_scene_export_bvh(const rr_scene* s, uint32_t* morton, uint32_t* perm, uin
       memcpy(b, v, sizeof v);
     }
   }
+  return RR_OK;
+}
+
+int rr_scene_set_lobe(rr_scene* s, uint32_t material, const float* density) {
+  if (!s || !density) return fail(RR_ERR_INVALID_ARG, "scene and density must not be NULL");
+  if (material >= s->nm) return fail(RR_ERR_INVALID_ARG, "material index out of range");
+  if (!(s->raw_flags[material] & RR_MAT_TABULATED_LOBE))
+    return fail(RR_ERR_INVALID_ARG, "the material was not created with RR_MAT_TABULATED_LOBE");
+  std::vector<float> h(rr::kLobeSamples);
+  RR_CHECK_CUDA(cudaMemcpy(h.data(), density, h.size() * sizeof(float), cudaMemcpyDefault), "reading the lobe");
+  double total = 0.0;
+  for (float v : h) {
+    if (!std::isfinite(v) || v < 0.f) return fail(RR_ERR_INVALID_ARG, "lobe samples must be finite and >= 0");
+    total += v;
+  }
+  if (!(total > 0.0)) return fail(RR_ERR_INVALID_ARG, "lobe samples must not all be zero");
+  cudaStream_t st = t_stream;
+  if (!s->d_lobe_samples) {
+    const size_t bytes = (size_t)s->nm * rr::kLobeSamples * sizeof(float);
+    RR_CHECK_CUDA(cudaMalloc(&s->d_lobe_samples, bytes), "allocating the lobe samples");
+    RR_CHECK_CUDA(cudaMemsetAsync(s->d_lobe_samples, 0, bytes, st), "clearing the lobe samples");
+  }
+  RR_CHECK_CUDA(cudaMemcpyAsync(s->d_lobe_samples + (size_t)material * rr::kLobeSamples, h.data(),
+                                h.size() * sizeof(float), cudaMemcpyHostToDevice, st),
+                "copying the lobe samples");
+  s->lobe_kind[material] = (uint8_t)rr::kLobeTable;
+  RR_CHECK_CUDA(build_materials(s, st), "rebuilding the lobe tables");   // synchronises (h stays alive)
   return RR_OK;
 }
 

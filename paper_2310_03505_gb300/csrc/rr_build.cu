@@ -627,40 +627,85 @@ __global__ void __launch_bounds__(128) k_wide_write(uint32_t n, const uint32_t* 
   }
 }
 
-__global__ void k_lut_cells(const rr_material* __restrict__ raw, uint32_t nm, float* __restrict__ cells) {
+// Lobe density g(x) of a material on [0, pi/2], up to normalisation: cos^C
+// (the S term of Eq. 5; A and B are integrated in closed form), the
+// Cook-Torrance lobe, or the user's samples (Sec. III-A)
+struct LobeShape {
+  uint32_t kind;
+  float C;          // Eq. 5
+  float kd, m, zw;  // Cook-Torrance: diffuse amount, roughness, integral of D(w/2)
+};
+
+__device__ __forceinline__ LobeShape lobe_shape(const rr_material& r, uint32_t kind) {
+  LobeShape ls;
+  ls.kind = kind;
+  ls.C = r.C;
+  ls.kd = r.A;
+  ls.m = r.B;
+  ls.zw = 0.f;
+  if (kind == kLobeCookTorrance) {
+    const float m = r.B;
+    ls.zw = 2.0f * (m * 1.77245385090551603f * erff(1.0f / m) * (1.0f + 0.5f * m * m) - m * m * expf(-1.0f / (m * m))) /
+            (kPi * m * m);
+  }
+  return ls;
+}
+
+__device__ __forceinline__ float lobe_value(const LobeShape& ls, float x) {
+  if (ls.kind == kLobeCookTorrance) {
+    const float t = 0.5f * x, c = cosf(t), tt = tanf(t);
+    const float d = expf(-tt * tt / (ls.m * ls.m)) / (kPi * ls.m * ls.m * c * c * c * c);
+    return ls.kd * 0.5f * cosf(x) + (1.0f - ls.kd) * d / ls.zw;
+  }
+  return cospow(x, ls.C);
+}
+
+__global__ void k_lut_cells(const rr_material* __restrict__ raw, const uint8_t* __restrict__ kinds, uint32_t nm,
+                            const float* __restrict__ samples, float* __restrict__ cells) {
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nm * (uint32_t)kLutCells) return;
   const uint32_t m = g / kLutCells, j = g % kLutCells;
-  const float C = raw[m].C;
   const float h = kHalfPi / kLutCells;
+  if (kinds[m] == kLobeTable) {   // Simpson: exact for the quadratic through the cell's three samples
+    const float* t = samples + (size_t)m * kLobeSamples + 2 * j;
+    cells[g] = (t[0] + 4.0f * t[1] + t[2]) * (h / 6.0f);
+    return;
+  }
+  const LobeShape ls = lobe_shape(raw[m], kinds[m]);
   const float a = h * (float)j, mid = a + 0.5f * h, half = 0.5f * h;
   // Gauss-Legendre nodes and weights of order 8 (roots of P8)
   const float xg[4] = {0.18343464249564980f, 0.52553240991632899f, 0.79666647741362674f, 0.96028985649753623f};
   const float wg[4] = {0.36268378337836198f, 0.31370664587788729f, 0.22238103445337447f, 0.10122853629037626f};
   float s = 0.f;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) s += wg[q] * (cospow(mid - half * xg[q], C) + cospow(mid + half * xg[q], C));
+  for (int q = 0; q < 4; ++q) s += wg[q] * (lobe_value(ls, mid - half * xg[q]) + lobe_value(ls, mid + half * xg[q]));
   cells[g] = s * half;
 }
 
-__global__ void k_lut_prefix(const rr_material* __restrict__ raw, uint32_t nm, const float* __restrict__ cells,
+__global__ void k_lut_prefix(const rr_material* __restrict__ raw, const uint8_t* __restrict__ kinds, uint32_t nm,
+                             const float* __restrict__ samples, const float* __restrict__ cells,
                              float4* __restrict__ lut, MatDev* __restrict__ mats) {
   const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= nm) return;
   const rr_material r = raw[m];
+  const uint32_t kind = kinds[m];
+  const LobeShape ls = lobe_shape(r, kind);
+  const float* tab = samples + (size_t)m * kLobeSamples;
+  // the density at node k (the slope of the integral table)
+  auto node = [&](int k, float x) { return kind == kLobeTable ? tab[2 * k] : lobe_value(ls, x); };
   const float h = kHalfPi / kLutCells;
   const float* cm = cells + (size_t)m * kLutCells;
   float4* L = lut + (size_t)m * (kLutCells + 1);
   // forward prefix G and backward prefix Gc, both Kahan-compensated
   float sum = 0.f, comp = 0.f;
-  L[0] = make_float4(0.f, 0.f, cospow(0.f, r.C), 0.f);
+  L[0] = make_float4(0.f, 0.f, node(0, 0.f), 0.f);
   for (int j = 0; j < kLutCells; ++j) {
     const float y = cm[j] - comp;
     const float t = sum + y;
     comp = (t - sum) - y;
     sum = t;
     const float x = (j + 1 == kLutCells) ? kHalfPi : h * (float)(j + 1);
-    L[j + 1] = make_float4(sum, 0.f, cospow(x, r.C), 0.f);
+    L[j + 1] = make_float4(sum, 0.f, node(j + 1, x), 0.f);
   }
   float csum = 0.f, ccomp = 0.f;
   for (int j = kLutCells - 1; j >= 0; --j) {
@@ -673,11 +718,12 @@ __global__ void k_lut_prefix(const rr_material* __restrict__ raw, uint32_t nm, c
   MatDev d;
   d.n = sqrtf(r.eps_r);
   d.tan_d = r.loss_tangent;
-  d.A = r.A;
-  d.B = r.B;
-  d.S = 1.0f - r.A - r.B;
+  const bool eq5 = kind == kLobeEq5;   // other lobes live entirely in the table
+  d.A = eq5 ? r.A : 0.0f;
+  d.B = eq5 ? r.B : 0.0f;
+  d.S = eq5 ? 1.0f - r.A - r.B : 1.0f;
   d.C = r.C;
-  d.invZ = 1.0f / (r.A * kPi + 2.0f * r.B + 2.0f * d.S * sum);
+  d.invZ = 1.0f / (d.A * kPi + 2.0f * d.B + 2.0f * d.S * sum);
   d.pec = (r.flags & RR_MAT_PERFECT_CONDUCTOR) ? 1u : 0u;
   mats[m] = d;
 }
@@ -713,6 +759,7 @@ cudaError_t build_alloc(rr_scene* s) {
   RR_TRY(alloc((void**)&s->d_mats, M * sizeof(MatDev)));
   RR_TRY(alloc((void**)&s->d_lut, M * (kLutCells + 1) * sizeof(float4)));
   RR_TRY(alloc((void**)&s->d_lut_cells, M * kLutCells * sizeof(float)));
+  RR_TRY(alloc((void**)&s->d_lobe_kind, M * sizeof(uint8_t)));
   RR_TRY(alloc((void**)&s->d_tri, T * 3 * sizeof(float4)));
   RR_TRY(alloc((void**)&s->d_nodes, (T > 1 ? T - 1 : 0) * 4 * sizeof(float4)));
   RR_TRY(alloc((void**)&s->d_centroid, T * sizeof(float4)));
@@ -744,11 +791,15 @@ cudaError_t build_alloc(rr_scene* s) {
 
 cudaError_t build_materials(rr_scene* s, cudaStream_t st) {
   if (s->nm == 0) return cudaSuccess;
+  RR_TRY(cudaMemcpyAsync(s->d_lobe_kind, s->lobe_kind.data(), s->nm, cudaMemcpyHostToDevice, st));
   const uint32_t cells = s->nm * kLutCells;
-  k_lut_cells<<<(cells + 255) / 256, 256, 0, st>>>(s->d_raw_mats, s->nm, s->d_lut_cells);
+  k_lut_cells<<<(cells + 255) / 256, 256, 0, st>>>(s->d_raw_mats, s->d_lobe_kind, s->nm, s->d_lobe_samples,
+                                                     s->d_lut_cells);
   RR_TRY(cudaGetLastError());
-  k_lut_prefix<<<(s->nm + 63) / 64, 64, 0, st>>>(s->d_raw_mats, s->nm, s->d_lut_cells, s->d_lut, s->d_mats);
-  return cudaGetLastError();
+  k_lut_prefix<<<(s->nm + 63) / 64, 64, 0, st>>>(s->d_raw_mats, s->d_lobe_kind, s->nm, s->d_lobe_samples,
+                                                   s->d_lut_cells, s->d_lut, s->d_mats);
+  RR_TRY(cudaGetLastError());
+  return cudaStreamSynchronize(st);   // the host copy of the kinds must outlive the upload
 }
 
 cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth) {

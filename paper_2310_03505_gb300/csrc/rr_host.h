@@ -69,6 +69,10 @@ struct rr_scene {
   rr::MatDev* d_mats = nullptr;    // [M]
   float4* d_lut = nullptr;         // [M][kLutCells + 1]
   float* d_lut_cells = nullptr;    // [M][kLutCells]
+  uint8_t* d_lobe_kind = nullptr;  // [M] kLobeEq5 / kLobeCookTorrance / kLobeTable
+  std::vector<uint8_t> lobe_kind;  // host copy
+  std::vector<uint32_t> raw_flags; // rr_material.flags of every material
+  float* d_lobe_samples = nullptr; // [M][kLobeSamples] tabulated lobes (allocated on first use)
   float4* d_tri = nullptr;         // [T][3] sorted leaves
   float4* d_nodes = nullptr;       // [T-1][4]
   // 8-wide quantised BVH (collapsed from the binary one at every build)

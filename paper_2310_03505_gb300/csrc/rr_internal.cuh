@@ -14,6 +14,8 @@ constexpr uint32_t kAir = 0xFFFFu;
 constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr int kStack = 64;            // traversal stack entries; the build checks depth <= kStack
 constexpr int kLutCells = 2048;       // lobe table cells over [0, pi/2]
+constexpr int kLobeSamples = 2 * kLutCells + 1;   // samples of a tabulated lobe (RR_LOBE_SAMPLES)
+constexpr uint32_t kLobeEq5 = 0, kLobeCookTorrance = 1, kLobeTable = 2;
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kHalfPi = 1.57079632679489661923f;
 constexpr float kC0 = 299792458.0f;   // speed of light (m/s)

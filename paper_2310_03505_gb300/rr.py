@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(_HERE, "librr.so")
 
 RR_OK, RR_ERR_INVALID_ARG, RR_ERR_OOM, RR_ERR_CAPACITY, RR_ERR_TIMEOUT, RR_ERR_CUDA, RR_ERR_BUSY = range(7)
 RR_MULTIPATH, RR_REFRACTION, RR_SPECKLE, RR_NOISE, RR_COUNT_TRAVERSAL, RR_NOISE_PERLIN = 1, 2, 4, 8, 16, 32
-RR_MAT_PERFECT_CONDUCTOR = 1
+RR_MAT_PERFECT_CONDUCTOR, RR_MAT_COOK_TORRANCE, RR_MAT_TABULATED_LOBE = 1, 2, 4
+RR_LOBE_SAMPLES = 4097
 RR_NO_HIT = 0xFFFFFFFF
 RR_K_RAYGEN, RR_K_TRACE, RR_K_SHADE, RR_K_IMAGE, RR_K_BUILD, RR_K_VIS, RR_K_COUNT = range(7)
 KERNEL_NAMES = ["raygen", "trace", "shade", "image", "build", "vis"]
@@ -120,6 +121,7 @@ SIGNATURES = {
     "rr_scene_create": ([_P, C.c_uint32, _P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(_P)], C.c_int),
     "rr_scene_destroy": ([_P], C.c_int),
     "rr_scene_update_vertices": ([_P, _P], C.c_int),
+    "rr_scene_set_lobe": ([_P, C.c_uint32, _P], C.c_int),
     "rr_scene_info_get": ([_P, C.POINTER(rr_scene_info)], C.c_int),
     "rr_scene_export_bvh": ([_P, _P, _P, _P, _P, _P], C.c_int),
     "rr_scene_export_wide": ([_P, _P, C.c_uint32, C.POINTER(C.c_uint32), _P], C.c_int),
@@ -223,8 +225,11 @@ def make_pose(pz: dict) -> rr_pose:
 def make_materials(mats) -> C.Array:
     arr = (rr_material * len(mats))()
     for i, m in enumerate(mats):
-        arr[i] = rr_material(m["eps_r"], m["loss_tangent"], m["A"], m["B"], m["C"],
-                             RR_MAT_PERFECT_CONDUCTOR if m.get("pec") else 0)
+        lobe = m.get("lobe", "eq5")
+        flags = ((RR_MAT_PERFECT_CONDUCTOR if m.get("pec") else 0) |
+                 (RR_MAT_COOK_TORRANCE if lobe == "cook_torrance" else 0) |
+                 (RR_MAT_TABULATED_LOBE if lobe == "table" else 0))
+        arr[i] = rr_material(m["eps_r"], m["loss_tangent"], m["A"], m["B"], m["C"], flags)
     return arr
 
 
@@ -262,6 +267,17 @@ def rr_scene_destroy(scene) -> None:
 def rr_scene_update_vertices(scene, vertices) -> None:
     _use_torch_stream()
     _check(load().rr_scene_update_vertices(scene, _ptr(vertices)))
+
+
+def rr_scene_set_lobe(scene, material: int, density) -> None:
+    """density: RR_LOBE_SAMPLES floats over [0, pi/2] (host or device)."""
+    _use_torch_stream()
+    d = density
+    if isinstance(d, (list, tuple)) or (isinstance(d, np.ndarray) and d.dtype != np.float32):
+        d = np.ascontiguousarray(np.asarray(d, np.float32))
+    if int(np.prod(d.shape)) != RR_LOBE_SAMPLES:
+        raise ValueError(f"a lobe has {RR_LOBE_SAMPLES} samples")
+    _check(load().rr_scene_set_lobe(scene, int(material), _ptr(d)))
 
 
 def rr_scene_info_get(scene) -> dict:

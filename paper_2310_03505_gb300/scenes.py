@@ -51,6 +51,27 @@ def material(eps_r=1.0, loss_tangent=0.0, brdf="wall", pec=False, name=""):
 
 # relative permittivity and loss tangent of the synthetic materials (proposed;
 # the configurations only bound eps_r to 1..10)
+def cook_torrance(eps_r, loss_tangent, diffuse, roughness, name=""):
+    """A material with the Cook-Torrance lobe (diffuse amount, Beckmann
+    roughness; the paper's setting in Sec. IV is diffuse 0.2, roughness 0.5).
+    Its Fresnel split and losses come from eps_r and the loss tangent as for
+    every material."""
+    return dict(name=name, eps_r=float(eps_r), loss_tangent=float(loss_tangent), A=float(diffuse),
+                B=float(roughness), C=0.0, pec=False, lobe="cook_torrance")
+
+
+LOBE_SAMPLES = 4097
+
+
+def tabulated(eps_r, loss_tangent, density, name=""):
+    """A material with a user lobe: density(x) sampled at the 4097 points
+    x_j = j (pi/2) / 4096 of [0, pi/2] (float32)."""
+    x = np.arange(LOBE_SAMPLES) * (0.5 * math.pi / (LOBE_SAMPLES - 1))
+    t = np.asarray(density(x), np.float32).astype(np.float64)
+    return dict(name=name, eps_r=float(eps_r), loss_tangent=float(loss_tangent), A=0.6, B=0.1, C=30.0, pec=False,
+                lobe="table", lobe_table=t)
+
+
 MATERIALS = {
     "metal": material(pec=True, brdf="metal", name="metal"),
     "dielectric": material(4.0, 0.01, "wall", name="dielectric"),

@@ -40,6 +40,32 @@ VARIANTS = {
 def test_tiny_parity(tiny_scene, variant):
     sc, pz, params, h = tiny_scene
     params = scenes.sensor(**{**params, **VARIANTS[variant]})
+    check_parity(sc, pz, params, h)
+
+
+# lobes other than Eq. 5 (Sec. III-A user BRDFs): the room's dielectric
+# with the paper's Cook-Torrance lobe (diffuse 0.2, roughness 0.5) or a
+# sharper one, or with a tabulated lobe
+LOBE_VARIANTS = {
+    "cook_torrance": lambda mats: [mats[0], scenes.cook_torrance(4.0, 0.01, 0.2, 0.5, name="ct")],
+    "cook_torrance_sharp": lambda mats: [mats[0], scenes.cook_torrance(4.0, 0.01, 0.1, 0.08, name="ct")],
+    "tabulated": lambda mats: [mats[0], scenes.tabulated(
+        4.0, 0.01, lambda x: 0.3 + np.exp(-0.5 * (x / 0.12) ** 2) + 0.2 * np.cos(x) ** 4, name="tab")],
+}
+
+
+@pytest.mark.parametrize("variant", sorted(LOBE_VARIANTS))
+def test_tiny_parity_lobes(rrlib, variant):
+    sc, pz, params = scenes.config_tiny()
+    sc = scenes.Scene(sc.name, sc.vertices, sc.triangles, sc.material_ids, LOBE_VARIANTS[variant](sc.materials))
+    h = P.gpu_scene(sc)
+    try:
+        check_parity(sc, pz, params, h)
+    finally:
+        rr.rr_scene_destroy(h)
+
+
+def check_parity(sc, pz, params, h):
     ora = P.oracle_scan(sc, pz, params)
     flags = ora["flags"]
     assert flags.mean() < 0.02, f"{flags.sum()} of {flags.size} rays flagged"
@@ -53,7 +79,7 @@ def test_tiny_parity(tiny_scene, variant):
     assert not ebad, f"{len(ebad)} segment energy mismatches, first: {ebad[:6]}"
     # energy bookkeeping per initial ray
     assert np.max(np.abs(tal.sum(-1) - 1.0 / params["rays_per_beam"])) < 1e-5 / params["rays_per_beam"] * 10
-    ok = flags == 0
+    ok = ora["tally_flags"] == 0
     diff = np.abs(tal - ora["tallies"]).max(-1) * ok
     worst = np.unravel_index(np.argmax(diff), diff.shape)
     if diff[worst] >= 2e-6:
@@ -182,3 +208,22 @@ def test_capacity_error_reports_size(tiny_scene):
     # the scene stays usable
     rr.rr_scan(h, pz, params, out)
     assert float(out.max()) > 0
+
+
+def test_set_lobe_checks_its_arguments(rrlib):
+    sc, _, _ = scenes.config_tiny()
+    mats = [sc.materials[0], scenes.tabulated(4.0, 0.01, lambda x: np.cos(x), name="tab")]
+    h = P.gpu_scene(scenes.Scene(sc.name, sc.vertices, sc.triangles, sc.material_ids, mats))
+    try:
+        good = np.cos(np.linspace(0, np.pi / 2, rr.RR_LOBE_SAMPLES)).astype(np.float32)
+        with pytest.raises(rr.RRError):   # material 0 is not tabulated
+            rr.rr_scene_set_lobe(h, 0, good)
+        with pytest.raises(rr.RRError):
+            rr.rr_scene_set_lobe(h, 2, good)
+        with pytest.raises(rr.RRError):
+            rr.rr_scene_set_lobe(h, 1, -good)
+        with pytest.raises(rr.RRError):
+            rr.rr_scene_set_lobe(h, 1, np.zeros(rr.RR_LOBE_SAMPLES, np.float32))
+        rr.rr_scene_set_lobe(h, 1, good)
+    finally:
+        rr.rr_scene_destroy(h)

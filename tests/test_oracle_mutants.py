@@ -47,6 +47,12 @@ MUTANTS = {
     "perlin_corner_swap": ("perlin_grad(p, i1, j0, purpose, g10);", "perlin_grad(p, i0, j1, purpose, g10);"),
     "perlin_not_periodic": ("i1 = (i0 + 1u) % (uint32_t)P;", "i1 = i0 + 1u;"),
     "perlin_scale": ("return 0.5 + n / sqrt(2.0);", "return 0.5 + n;"),
+    "ct_diffuse_norm": ("return m->A * 0.5 * cos(w)", "return m->A * cos(w)"),
+    "ct_half_angle": ("orc_beckmann(0.5 * w, m->B)", "orc_beckmann(w, m->B)"),
+    "beckmann_norm_term": ("(1.0 + 0.5 * m * m)", "(1.0 + m * m)"),
+    "table_prim_coeff": ("f0 * (s3 / 6.0 - 0.75 * s2 + s)", "f0 * (s3 / 6.0 - 0.5 * s2 + s)"),
+    "table_symmetry": ("return table_prim(t, hi) + table_prim(t, -lo);",
+                       "return table_prim(t, hi) - table_prim(t, -lo);"),
     "air_side": ("          if (side <= 0.0) candidate = 0;", "          if (side >= 0.0) candidate = 0;"),
     "traveled_range_half": ("push_ret(col, k, L1, e);", "push_ret(col, k, 0.5 * L1, e);"),
     "bin_off_by_one": ("img[(size_t)fb] += r->E;", "img[(size_t)fb + 1] += r->E;"),

@@ -620,11 +620,62 @@ def check_perlin():
     assert 0.0 <= min(vals) and max(vals) <= 1.0 and np.std(vals) > 0.05
 
 
+def check_cook_torrance_lobe():
+    """Cook-Torrance lobe (the paper's microfacet user BRDF, Sec. IV): the
+    Beckmann normalisation against scipy's quadrature; unit integral; a
+    purely diffuse lobe gives (sin hi - sin lo) / 2; for small roughness m
+    the microfacet part tends to a Gaussian in w of variance 2 m^2, so
+    W(0, b) -> erf(b / (4 m))."""
+    for m in (0.1, 0.3, 0.5, 1.0):
+        ref = 2.0 * integrate.quad(lambda t: orc.beckmann(t, m), -math.pi / 4, math.pi / 4, epsabs=1e-13,
+                                   epsrel=1e-12, limit=400)[0]
+        assert abs(orc.beckmann_norm(m) / ref - 1.0) < 1e-9, m
+    for kd, m in ((0.2, 0.5), (0.0, 0.1), (1.0, 0.3)):
+        mat = make_material(A=kd, B=m, C=0.0)
+        mat["lobe"] = "cook_torrance"
+        assert abs(orc.brdf_window(mat, 0.0, math.pi) - 1.0) < 1e-9
+        assert abs(orc.brdf_window(mat, 0.3, 0.2) - orc.brdf_window(mat, -0.3, 0.2)) < 1e-12
+    mat = make_material(A=1.0, B=0.3, C=0.0)
+    mat["lobe"] = "cook_torrance"
+    for w, b in ((0.0, 0.3), (0.7, 0.5), (-1.4, 0.6)):
+        lo, hi = max(w - b / 2, -math.pi / 2), min(w + b / 2, math.pi / 2)
+        assert abs(orc.brdf_window(mat, w, b) - 0.5 * (math.sin(hi) - math.sin(lo))) < 1e-12
+    m = 0.01
+    mat = make_material(A=0.0, B=m, C=0.0)
+    mat["lobe"] = "cook_torrance"
+    for b in (0.01745, 0.03, 0.06):
+        assert abs(orc.brdf_window(mat, 0.0, b) - math.erf(b / (4 * m))) < 2e-3, b
+
+
+def check_tabulated_lobe():
+    """Tabulated lobe (Sec. III-A, a user-defined BRDF per material): a
+    quadratic density is reproduced exactly (closed-form windows, also across
+    w = 0), and the Eq. 5 wall lobe tabulated gives the Eq. 5 windows."""
+    x = np.arange(orc.LOBE_SAMPLES) * (0.5 * math.pi / (orc.LOBE_SAMPLES - 1))
+    mat = make_material()
+    mat.update(lobe="table", lobe_table=1.0 + x * x)
+    P = lambda u: u + u ** 3 / 3.0                      # integral of 1 + x^2 from 0
+    Z = 2.0 * P(math.pi / 2)
+    for w, b in ((0.0, 0.4), (0.5, 0.3), (-0.9, 0.2), (1.4, 0.5), (-0.05, 0.2)):
+        lo, hi = max(w - b / 2, -math.pi / 2), min(w + b / 2, math.pi / 2)
+        exact = (P(hi) - P(lo)) / Z if lo >= 0 or hi <= 0 else (P(hi) + P(-lo)) / Z
+        if hi <= 0:
+            exact = (P(-lo) - P(-hi)) / Z
+        assert abs(orc.brdf_window(mat, w, b) - exact) < 1e-12, (w, b)
+    A, B, Cc = WALL["A"], WALL["B"], WALL["C"]
+    tab = make_material()
+    tab.update(lobe="table", lobe_table=A + B * np.cos(x) + (1 - A - B) * np.cos(x) ** Cc)
+    eq5 = make_material(**WALL)
+    for w in (0.0, 0.1, 0.5, -1.0):
+        for b in (0.05, math.radians(10.0)):
+            assert abs(orc.brdf_window(tab, w, b) - orc.brdf_window(eq5, w, b)) < 1e-7, (w, b)
+
+
 ALL_CHECKS = [check_philox_kat, check_u24, check_d3_sigma, check_d3_pose_and_azimuth, check_fresnel_closed_forms,
               check_snell, check_brdf_normalisation, check_brdf_window_pins, check_closest_brute_force,
               check_normal_incidence_plane, check_oblique_plane, check_slab, check_slab_multipath,
               check_corner_reflector, check_lidar_like, check_conservation_tiny, check_post_pass, check_db_map,
-              check_elliptic_beam, check_perlin]
+              check_elliptic_beam, check_perlin, check_cook_torrance_lobe, check_tabulated_lobe]
 
 
 @pytest.mark.parametrize("check", ALL_CHECKS, ids=lambda f: f.__name__[6:])
