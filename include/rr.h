@@ -313,7 +313,13 @@ int rr_scan_batch_async(rr_scene* scene, uint32_t n, const rr_pose* poses, const
                         of its 32 lanes are idle (1..32; 0 = 8)
    workspace_limit      bytes of scan workspace; a launch sequence is sized
                         for its worst-case ray tree (every hit spawning both
-                        children) within this limit (0: 24 GiB) */
+                        children) within this limit (0: 24 GiB)
+   split_streams        rr_scan / rr_scan_async trace a scan as this many
+                        azimuth ranges, each on its own stream, so that the
+                        slow queries closing one range's bounce overlap the
+                        other ranges' work (1..4; 0: the default, 3).  Scans
+                        with a beam pattern run whole.  The image is the same
+                        up to the rounding of the bin sums. */
 #define RR_NODES_WIDE8 0u
 #define RR_NODES_BINARY 1u
 typedef struct {
@@ -324,12 +330,14 @@ typedef struct {
   uint32_t node_format;
   uint32_t refill_threshold;
   uint64_t workspace_limit;
+  uint32_t split_streams;
+  uint32_t reserved;
 } rr_batch_config;
 
 int rr_batch_config_get(const rr_scene* scene, rr_batch_config* out);
 /* RR_ERR_INVALID_ARG for a trace_block other than 64/128/256, more than 64
    blocks per SM, use_graph > 1, an unknown node_format, a refill_threshold
-   above 32 or a workspace limit below 1 MiB. */
+   above 32, split_streams above 4 or a workspace limit below 1 MiB. */
 int rr_batch_config_set(rr_scene* scene, const rr_batch_config* config);
 
 /* How rr_scan_batch would cut scans params[0..n) into launch sequences under

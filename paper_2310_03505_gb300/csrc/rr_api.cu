@@ -167,6 +167,15 @@ int device_status(ExecCtx* x, cudaStream_t st) {
   return RR_OK;
 }
 
+int scene_status(rr_scene* s, cudaStream_t st) {
+  int rc = device_status(&s->main, st);   // st has joined the split lanes' work
+  for (uint32_t k = 0; k < s->split_used; ++k) {
+    const int r = device_status(&s->split[k].ctx, s->split[k].stream);
+    if (rc == RR_OK) rc = r;
+  }
+  return rc;
+}
+
 cudaError_t ctx_init(ExecCtx* x, cudaStream_t st) {
   cudaError_t e = cudaMalloc((void**)&x->d_ctr, sizeof(ScanCounters));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&x->h_ctr, sizeof(ScanCounters));
@@ -221,6 +230,12 @@ int rr_scene_destroy(rr_scene* s) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ctx_free(&s->main);
+  for (SplitLane& ln : s->split) {
+    ctx_free(&ln.ctx);
+    if (ln.join) cudaEventDestroy(ln.join);
+    if (ln.stream) cudaStreamDestroy(ln.stream);
+  }
+  if (s->fork) cudaEventDestroy(s->fork);
   if (s->wide_ready) cudaEventDestroy(s->wide_ready);
   for (auto& ev : s->prof_pending) {
     cudaEventDestroy(ev.start);
@@ -446,13 +461,12 @@ int rr_scan_async(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, f
   int rc = check_params(pose, p);
   if (rc != RR_OK) return rc;
   if (!is_device_ptr(out_polar)) return fail(RR_ERR_INVALID_ARG, "rr_scan_async needs a device output");
-  float* const images[1] = {out_polar};
-  return batch_run(s, &s->main, pose, p, images, 1, nullptr, t_stream, s->cfg);
+  return scan_split(s, pose, p, out_polar, t_stream, true);
 }
 
 int rr_scene_sync(rr_scene* s) {
   if (!s) return fail(RR_ERR_INVALID_ARG, "scene must not be NULL");
-  return device_status(&s->main, t_stream);
+  return scene_status(s, t_stream);
 }
 
 int rr_scan(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* out_polar) {
@@ -468,12 +482,11 @@ int rr_scan(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* 
     if (rc != RR_OK) return rc;
     target = s->main.d_image;
   }
-  float* const images[1] = {target};
-  rc = batch_run(s, &s->main, pose, p, images, 1, nullptr, st, s->cfg);
+  rc = scan_split(s, pose, p, target, st, true);
   if (rc != RR_OK) return rc;
   if (!dev)
     RR_CHECK_CUDA(cudaMemcpyAsync(out_polar, target, img_bytes, cudaMemcpyDeviceToHost, st), "copying the image");
-  return device_status(&s->main, st);
+  return scene_status(s, st);
 }
 
 int rr_scan_debug(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, const uint8_t* ray_mask,
@@ -559,21 +572,27 @@ int rr_polar_to_db_u8(const float* polar, uint64_t n, float cutoff_db, uint8_t* 
 int rr_scene_stats(rr_scene* s, rr_stats* out, int reset) {
   if (!s || !out) return fail(RR_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t st = t_stream;
-  RR_CHECK_CUDA(cudaMemcpyAsync(s->main.h_ctr, s->main.d_ctr, sizeof(ScanCounters), cudaMemcpyDeviceToHost, st), "stats");
+  memset(out, 0, sizeof *out);
+  // the scene's own context and the lanes of split scans (joined into st)
+  std::vector<ExecCtx*> xs = {&s->main};
+  for (uint32_t k = 0; k < s->split_used; ++k) xs.push_back(&s->split[k].ctx);
   RR_CHECK_CUDA(cudaStreamSynchronize(st), "stats");
-  out->closest_queries = s->main.h_ctr->stat_closest;
-  out->anyhit_queries = s->main.h_ctr->stat_anyhit;
-  out->returns = s->main.h_ctr->stat_returns;
-  out->scans = s->main.h_ctr->stat_scans;
-  out->nodes_visited = s->main.h_ctr->stat_nodes;
-  out->tris_tested = s->main.h_ctr->stat_tris;
+  for (ExecCtx* x : xs) {
+    RR_CHECK_CUDA(cudaMemcpy(x->h_ctr, x->d_ctr, sizeof(ScanCounters), cudaMemcpyDeviceToHost), "stats");
+    out->closest_queries += x->h_ctr->stat_closest;
+    out->anyhit_queries += x->h_ctr->stat_anyhit;
+    out->returns += x->h_ctr->stat_returns;
+    out->nodes_visited += x->h_ctr->stat_nodes;
+    out->tris_tested += x->h_ctr->stat_tris;
+    out->anyhit_nodes_visited += x->h_ctr->stat_nodes_any;
+    out->anyhit_tris_tested += x->h_ctr->stat_tris_any;
+  }
+  out->scans = s->main.h_ctr->stat_scans;   // a split scan counts once (its first range)
   out->kernel_launches = s->launches;
-  out->anyhit_nodes_visited = s->main.h_ctr->stat_nodes_any;
-  out->anyhit_tris_tested = s->main.h_ctr->stat_tris_any;
   if (reset) {
     s->launches = 0;
-    RR_CHECK_CUDA(cudaMemsetAsync(&s->main.d_ctr->stat_closest, 0, 8 * sizeof(unsigned long long), st), "stats reset");
-    RR_CHECK_CUDA(cudaStreamSynchronize(st), "stats reset");
+    for (ExecCtx* x : xs)
+      RR_CHECK_CUDA(cudaMemset(&x->d_ctr->stat_closest, 0, 8 * sizeof(unsigned long long)), "stats reset");
   }
   return RR_OK;
 }

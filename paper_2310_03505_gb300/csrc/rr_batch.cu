@@ -35,14 +35,16 @@ struct Need {
   uint64_t r = 0;      // return records: sum of 2 n0 (2^bounces - 1)
   uint64_t tmp = 0;    // floats of the images before the azimuth pattern
   uint64_t n = 0;      // scans
-  void add(const rr_sensor_params& p) {
-    const uint64_t s0 = (uint64_t)p.n_azimuth * p.rays_per_beam;
+  // a scan of n_az columns (all azimuths of p, or a range of them)
+  void add(const rr_sensor_params& p, uint32_t n_az) {
+    const uint64_t s0 = (uint64_t)n_az * p.rays_per_beam;
     n0 += s0;
     q += s0 << (p.max_bounces - 1);
     r += 2ull * s0 * ((1ull << p.max_bounces) - 1ull);
     if (p.az_pattern_sigma > 0.f) tmp += (uint64_t)p.n_azimuth * p.n_bins;
     n += 1;
   }
+  void add(const rr_sensor_params& p) { add(p, p.n_azimuth); }
 };
 
 static size_t desc_bytes(uint64_t n) { return (size_t)n * sizeof(ScanDesc) + 2 * (size_t)(n + 1) * sizeof(uint32_t); }
@@ -89,9 +91,9 @@ static WsLayout layout_of(const Need& nd, uint64_t limit) {
   return L;
 }
 
-WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit) {
+WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit, const uint32_t* az_count) {
   Need nd;
-  for (uint32_t i = 0; i < n; ++i) nd.add(ps[i]);
+  for (uint32_t i = 0; i < n; ++i) nd.add(ps[i], az_count ? az_count[i] : ps[i].n_azimuth);
   return layout_of(nd, limit);
 }
 
@@ -199,7 +201,7 @@ static int stage_acquire(ExecCtx* x, size_t bytes) {
 
 // descriptor of one scan (the same float arithmetic for every entry point)
 static void fill_desc(ScanDesc& d, const rr_pose& pose, const rr_sensor_params& p, float* image, uint32_t ray0,
-                      uint32_t col0, uint32_t tmp0) {
+                      uint32_t col0, uint32_t tmp0, uint32_t az_begin) {
   memset(&d, 0, sizeof d);
   const float qn = 1.0f / std::sqrt(pose.q[0] * pose.q[0] + pose.q[1] * pose.q[1] + pose.q[2] * pose.q[2] +
                                     pose.q[3] * pose.q[3]);
@@ -211,7 +213,7 @@ static void fill_desc(ScanDesc& d, const rr_pose& pose, const rr_sensor_params& 
   d.phys = make_float4(p.t_min_m, p.min_energy, p.freq_hz, (p.flags & RR_MULTIPATH) ? 2.0f * r_max : r_max);
   d.post = make_float4(p.blur_sigma_bins, p.az_pattern_sigma, p.noise_sys, p.noise_amb);
   d.rng = make_uint4((uint32_t)(p.seed & 0xFFFFFFFFu), (uint32_t)(p.seed >> 32), p.scan_id, p.flags);
-  d.offs = make_uint4(ray0, col0, tmp0, 0u);
+  d.offs = make_uint4(ray0, col0, tmp0, az_begin);
   d.ext = make_float4(p.beam_aspect > 0.f ? p.beam_aspect : 1.0f, p.noise_cell_az > 0.f ? p.noise_cell_az : 8.0f,
                       p.noise_cell_bins > 0.f ? p.noise_cell_bins : 32.0f, 0.0f);
   d.image = image;
@@ -308,7 +310,7 @@ static int graph_launch(rr_scene* s, ExecCtx* x, const ScanArgs& a, bool pattern
 
 int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor_params* ps, float* const* images,
                   uint32_t n, const DebugOut* dbg, cudaStream_t st, void* ws, const WsLayout& L, bool profile,
-                  bool allow_graph, const LaunchCfg& cfg, void* host_desc) {
+                  bool allow_graph, const LaunchCfg& cfg, void* host_desc, const uint32_t* az_range) {
   if (n == 0) return RR_OK;
   if (n != L.n_desc) return fail(RR_ERR_INVALID_ARG, "internal: layout planned for another batch");
   char* w = (char*)ws;
@@ -328,11 +330,12 @@ int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor
   for (uint32_t i = 0; i < n; ++i) {
     const rr_sensor_params& p = ps[i];
     const bool pat = p.az_pattern_sigma > 0.f;
-    fill_desc(D[i], poses[i], p, images[i], rays, cols, pat ? (uint32_t)tmp : rr::kNone);
+    const uint32_t az0 = az_range ? az_range[2 * i] : 0u, naz = az_range ? az_range[2 * i + 1] : p.n_azimuth;
+    fill_desc(D[i], poses[i], p, images[i], rays, cols, pat ? (uint32_t)tmp : rr::kNone, az0);
     R0[i] = rays;
     C0[i] = cols;
-    rays += p.n_azimuth * p.rays_per_beam;
-    cols += p.n_azimuth;
+    rays += naz * p.rays_per_beam;
+    cols += naz;
     if (pat) tmp += (uint64_t)p.n_azimuth * p.n_bins;
     maxb = std::max(maxb, p.max_bounces);
     maxbins = std::max(maxbins, p.n_bins);
@@ -431,8 +434,61 @@ int batch_run(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor_par
   if (rc != RR_OK) return rc;
   for (const Group& g : groups) {
     rc = batch_enqueue(s, x, poses + g.first, ps + g.first, images + g.first, g.count, dbg, st, x->ws, g.L, true,
-                       true, cfg, nullptr);
+                       true, cfg, nullptr, nullptr);
     if (rc != RR_OK) return rc;
+  }
+  return RR_OK;
+}
+
+// One scan as split_streams azimuth ranges, each a launch sequence of its own
+// on its own stream and execution context: the bounces of the ranges no
+// longer wait for each other, so the tail of one range's bounce (its slowest
+// queries) overlaps the others' work.  Forked from and joined back to st.
+// Scans with a beam pattern (which needs every column) run whole.
+int scan_split(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* image, cudaStream_t st,
+               bool profile) {
+  uint32_t k_n = std::min<uint32_t>(s->cfg.split, p->n_azimuth);
+  if (k_n <= 1 || p->az_pattern_sigma > 0.f) {
+    float* const images[1] = {image};
+    return batch_run(s, &s->main, pose, p, images, 1, nullptr, st, s->cfg);
+  }
+  cudaError_t e = cudaSuccess;
+  for (uint32_t k = 1; k < k_n; ++k) {
+    SplitLane& ln = s->split[k - 1];
+    if (!ln.stream) {
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ln.join, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = ctx_init(&ln.ctx, ln.stream);
+    }
+  }
+  if (e == cudaSuccess && !s->fork) e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(s->fork, st);
+  for (uint32_t k = 1; k < k_n && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(s->split[k - 1].stream, s->fork, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "forking the split scan");
+  }
+  s->split_used = std::max<uint32_t>(s->split_used, k_n - 1);
+  for (uint32_t k = 0; k < k_n; ++k) {
+    const uint32_t a0 = (uint32_t)((uint64_t)p->n_azimuth * k / k_n);
+    const uint32_t a1 = (uint32_t)((uint64_t)p->n_azimuth * (k + 1) / k_n);
+    const uint32_t range[2] = {a0, a1 - a0};
+    ExecCtx* x = k == 0 ? &s->main : &s->split[k - 1].ctx;
+    cudaStream_t sk = k == 0 ? st : s->split[k - 1].stream;
+    const WsLayout L = plan_workspace(p, 1, s->cfg.ws_limit, &range[1]);
+    int rc = ensure_workspace(x, L.total, sk);
+    if (rc != RR_OK) return rc;
+    float* const images[1] = {image};
+    rc = batch_enqueue(s, x, pose, p, images, 1, nullptr, sk, x->ws, L, profile, true, s->cfg, nullptr, range);
+    if (rc != RR_OK) return rc;
+  }
+  for (uint32_t k = 1; k < k_n && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(s->split[k - 1].join, s->split[k - 1].stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->split[k - 1].join, 0);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "joining the split scan");
   }
   return RR_OK;
 }
@@ -456,6 +512,7 @@ static int cfg_check(const rr_batch_config* c) {
   if (c->node_format != RR_NODES_WIDE8 && c->node_format != RR_NODES_BINARY)
     return fail(RR_ERR_INVALID_ARG, "node_format must be RR_NODES_WIDE8 or RR_NODES_BINARY");
   if (c->refill_threshold > 32) return fail(RR_ERR_INVALID_ARG, "refill_threshold must be in [0, 32]");
+  if (c->split_streams > kMaxSplit) return fail(RR_ERR_INVALID_ARG, "split_streams must be in [0, 4]");
   if (c->workspace_limit != 0 && c->workspace_limit < (uint64_t(1) << 20))
     return fail(RR_ERR_INVALID_ARG, "workspace_limit must be 0 or at least 1 MiB");
   return RR_OK;
@@ -470,6 +527,7 @@ static void cfg_to_abi(const LaunchCfg& c, rr_batch_config* o) {
   o->node_format = c.node_format;
   o->refill_threshold = c.refill;
   o->workspace_limit = c.ws_limit;
+  o->split_streams = c.split;
 }
 
 static LaunchCfg cfg_from_abi(const rr_batch_config* c) {
@@ -481,6 +539,7 @@ static LaunchCfg cfg_from_abi(const rr_batch_config* c) {
   o.node_format = c->node_format;
   o.refill = c->refill_threshold ? c->refill_threshold : 8u;
   if (c->workspace_limit) o.ws_limit = c->workspace_limit;
+  o.split = c->split_streams ? c->split_streams : 3u;
   return o;
 }
 
@@ -521,7 +580,7 @@ int rr_scan_batch(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor
       }
     }
     rc = batch_enqueue(s, &s->main, poses + g.first, params + g.first, images.data() + g.first, g.count, nullptr, st,
-                       s->main.ws, g.L, true, true, s->cfg, nullptr);
+                       s->main.ws, g.L, true, true, s->cfg, nullptr, nullptr);
     if (rc != RR_OK) return rc;
     for (uint32_t i = g.first; i < g.first + g.count; ++i) {
       if (on_dev[i]) continue;

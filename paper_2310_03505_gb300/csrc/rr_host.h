@@ -30,8 +30,11 @@ struct LaunchCfg {
   uint32_t use_graph = 1;             // capture each launch sequence once and replay it
   uint32_t node_format = RR_NODES_BINARY;
   uint32_t refill = 8;                // idle lanes that trigger a refill (1..32)
+  uint32_t split = 3;                 // a single scan as this many azimuth ranges on their own streams
   uint64_t ws_limit = uint64_t(24) << 30;
 };
+
+constexpr uint32_t kMaxSplit = 4;
 
 // What one stream of scans needs besides the scene: device counters and
 // status, the scan workspace, an image buffer for host outputs, pinned
@@ -55,6 +58,13 @@ struct ExecCtx {
 };
 cudaError_t ctx_init(ExecCtx* x, cudaStream_t st);   // counters (zeroed)
 void ctx_free(ExecCtx* x);
+
+// an extra stream of a split scan with its execution context
+struct SplitLane {
+  ExecCtx ctx;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t join = nullptr;
+};
 
 }  // namespace rr_host
 
@@ -101,6 +111,9 @@ struct rr_scene {
   size_t scene_bytes = 0;
   // execution state of the scene's own entry points
   rr_host::ExecCtx main;
+  rr_host::SplitLane split[rr_host::kMaxSplit - 1];   // the other azimuth ranges of split scans
+  uint32_t split_used = 0;                           // lanes that have run work (status, statistics)
+  cudaEvent_t fork = nullptr;
   rr_host::LaunchCfg cfg;
   std::mutex lock;                     // lazy wide collapse and launch counting across threads
   cudaEvent_t wide_ready = nullptr;    // recorded after the latest collapse
@@ -161,7 +174,7 @@ int cuda_fail(cudaError_t e, const char* what);
 bool is_device_ptr(const void* p);
 int check_params(const rr_pose* pose, const rr_sensor_params* p);
 // worst-case workspace of scans ps[0..n) traced together, clamped to limit
-WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit);
+WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit, const uint32_t* az_count = nullptr);
 // split n scans into launch sequences that respect the limits of cfg
 std::vector<Group> plan_groups(const rr_sensor_params* ps, uint32_t n, const LaunchCfg& cfg);
 // queue the launch sequence of scans poses/ps[0..n) writing images[i]
@@ -170,7 +183,12 @@ std::vector<Group> plan_groups(const rr_sensor_params* ps, uint32_t n, const Lau
 // unless allow_graph.
 int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor_params* ps, float* const* images,
                   uint32_t n, const DebugOut* dbg, cudaStream_t st, void* ws, const WsLayout& L, bool profile,
-                  bool allow_graph, const LaunchCfg& cfg, void* host_desc);
+                  bool allow_graph, const LaunchCfg& cfg, void* host_desc, const uint32_t* az_range = nullptr);
+// one scan, split into azimuth ranges on several streams when the scene's configuration asks for it
+int scan_split(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* image, cudaStream_t st,
+               bool profile);
+// device status of the scene's contexts (main and split lanes); waits for st
+int scene_status(rr_scene* s, cudaStream_t st);
 int ensure_workspace(ExecCtx* x, size_t bytes, cudaStream_t st);
 int ensure_image(ExecCtx* x, size_t bytes, cudaStream_t st);
 int device_status(ExecCtx* x, cudaStream_t st);

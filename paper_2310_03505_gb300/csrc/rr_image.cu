@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kImgBlock) k_bin_column(ScanArgs a) {
   const uint32_t c = blockIdx.x;
   const uint32_t scan = owner_of(a.col0, a.n_scans, c);
   const ScanDesc* sd = a.desc + scan;
-  const uint32_t az = c - __ldg(&a.col0[scan]);
+  const uint32_t az = __ldg(&sd->offs.w) + (c - __ldg(&a.col0[scan]));   // the scan's first azimuth + column
   const uint32_t nb = __ldg(&sd->dims.w);
   const float4 post = __ldg(&sd->post);   // blur sigma, pattern sigma, noise_sys, noise_amb
   const int lane = threadIdx.x & 31;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kImgBlock) k_az_pattern(ScanArgs a) {
   const float4 post = __ldg(&sd->post);
   if (!(post.y > 0.0f)) return;   // uniform over the block
   const int R = gauss_taps(post.y, taps);
-  const uint32_t az = c - __ldg(&a.col0[scan]);
+  const uint32_t az = __ldg(&sd->offs.w) + (c - __ldg(&a.col0[scan]));   // pattern scans are never split: offs.w = 0
   const uint32_t n_az = __ldg(&sd->dims.x), nb = __ldg(&sd->dims.w);
   const uint32_t i = blockIdx.y * blockDim.x + threadIdx.x;
   if (i >= nb) return;

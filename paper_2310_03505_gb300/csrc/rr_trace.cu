@@ -84,7 +84,8 @@ __global__ void k_raygen(ScanArgs a) {
   const ScanDesc* sd = a.desc + scan;
   const uint32_t ns = __ldg(&sd->dims.y);
   const uint32_t local = i - __ldg(&a.ray0[scan]);
-  const uint32_t az = local / ns, k = local - az * ns;
+  const uint32_t az_l = local / ns, k = local - az_l * ns;
+  const uint32_t az = __ldg(&sd->offs.w) + az_l;   // a scan may trace a range of the azimuths
   const float4 beam = __ldg(&sd->beam);
   const uint4 x = draw(__ldg(&sd->rng), az, k, 0u);
   const float u0 = u01(x.x), u1 = u01(x.y), u2 = u01(x.z);
@@ -788,7 +789,7 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
             if (bin < (float)dims.w) {
               float e = ret_t;
               if (rng.w & RR_SPECKLE) e *= -logf(u01(draw(rng, az, k, 1u | (((path << 8) | bounce) << 8)).x));
-              rec[nr++] = make_uint2(((offs.y + az) << kBinBits) | (uint32_t)bin, __float_as_uint(e));
+              rec[nr++] = make_uint2(((offs.y + az - offs.w) << kBinBits) | (uint32_t)bin, __float_as_uint(e));
             }
           }
           if (ret_a > 0.0f) {
@@ -796,7 +797,7 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
             if (bin < (float)dims.w) {
               float e = ret_a;
               if (rng.w & RR_SPECKLE) e *= -logf(u01(draw(rng, az, k, 1u | (((path << 8) | bounce) << 8)).y));
-              rec[nr++] = make_uint2(((offs.y + az) << kBinBits) | (uint32_t)bin, __float_as_uint(e));
+              rec[nr++] = make_uint2(((offs.y + az - offs.w) << kBinBits) | (uint32_t)bin, __float_as_uint(e));
             }
           }
         }
@@ -823,7 +824,7 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
         }
       }
       if (a.tallies != nullptr) {
-        float* tp = a.tallies + 4 * ((size_t)offs.x + (size_t)az * dims.y + k);
+        float* tp = a.tallies + 4 * ((size_t)offs.x + (size_t)(az - offs.w) * dims.y + k);
         for (int q = 0; q < 4; ++q)
           if (tal[q] != 0.0f) atomicAdd(tp + q, tal[q]);
       }

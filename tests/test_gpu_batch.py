@@ -217,3 +217,32 @@ def test_medium_uneven_batch_equals_alone(medium_scene):
     rr.rr_scan_batch(h, poses, params, outs)
     for i, (p, q, o) in enumerate(zip(poses, params, outs)):
         assert_close(o.cpu().numpy(), alone(h, p, q), f"campus scan {i}")
+
+
+@pytest.mark.parametrize("variant", ["plain", "noise_blur", "pattern"])
+def test_split_scan_equals_whole(tiny_scene, variant):
+    """rr_scan / rr_scan_async with split_streams = 2..4 trace the azimuth
+    ranges on separate streams: the same image up to the bin sums' rounding
+    and exactly the same queries (a beam-pattern scan runs whole)."""
+    import torch
+    _, pz, base, h = tiny_scene
+    extra = {"plain": {}, "noise_blur": dict(noise=True, noise_sys=1e-4, noise_amb=5e-5, blur_sigma_bins=1.5),
+             "pattern": dict(az_pattern_sigma=1.0)}[variant]
+    p = scenes.sensor(**{**base, **extra, "n_azimuth": 397, "rays_per_beam": 5})
+    saved = rr.rr_batch_config_get(h)
+    try:
+        rr.rr_scene_stats(h, reset=True)
+        ref = alone(h, pz, p)
+        q_ref = rr.rr_scene_stats(h, reset=True)["closest_queries"]
+        for k in (2, 3, 4):
+            rr.rr_batch_config_set(h, split_streams=k)
+            img = alone(h, pz, p)
+            assert rr.rr_scene_stats(h, reset=True)["closest_queries"] == q_ref
+            assert_close(img, ref, f"split {k}")
+            out = torch.zeros(p["n_azimuth"], p["n_bins"], device="cuda")
+            rr.rr_scan_async(h, pz, p, out)
+            rr.rr_scene_sync(h)
+            assert_close(out.cpu().numpy(), ref, f"async split {k}")
+            rr.rr_scene_stats(h, reset=True)
+    finally:
+        rr.rr_batch_config_set(h, **saved)
