@@ -128,9 +128,9 @@ def measured_peaks():
 
 
 def traffic_from_profiles():
-    """Per-launch DRAM bytes of the closest-hit query kernel from the committed
-    ncu summary, valid only while the kernel source matches the hash it was
-    taken on."""
+    """DRAM bytes of the closest-hit query kernel per bounce (all azimuth
+    ranges of the bounce) from the committed ncu summary, valid only while the
+    kernel source matches the hash it was taken on."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "query_kernel_campus_ncu.txt")
     src = os.path.join(ROOT, "paper_2310_03505_gb300", "csrc", "rr_trace.cu")
@@ -140,7 +140,7 @@ def traffic_from_profiles():
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if d.get("source_sha256_16") != h:
         return None
-    return d.get("dram_bytes_per_closest_launch")
+    return d.get("dram_bytes_per_closest_bounce")
 
 
 # ------------------------------------------------------------------ oracle arm
@@ -467,10 +467,14 @@ def main():
 
     mrays = job_queries / (job_ms * 1e-3) / 1e6
     scans_per_s = world * args.steps / (job_ms * 1e-3)
-    trace_ms, trace_launches = prof["trace"]
+    trace_ms, trace_launches, trace_busy = prof["trace"]
     peak, peak_kind = measured_peaks()
     algo_bytes = bytes_per_closest * st["closest_queries"]
-    achieved_gbs = algo_bytes / (trace_ms * 1e-3) / 1e9 if trace_ms > 0 else None
+    # the split ranges' closest-hit launches of a bounce run at the same time on
+    # their streams: the kernel's rate is its bytes over the time any of them ran
+    achieved_gbs = algo_bytes / (trace_busy * 1e-3) / 1e9 if trace_busy > 0 else None
+    per_launch_gbs = algo_bytes / (trace_ms * 1e-3) / 1e9 if trace_ms > 0 else None
+    bounces = params["max_bounces"] * args.steps
     traffic = traffic_from_profiles()
 
     # end to end through the C ABI with host buffers
@@ -524,11 +528,17 @@ def main():
             "anyhit_per_scan": st["anyhit_queries"] / args.steps,
             "bvh_build_ms_per_step": prof["build"][0] / max(prof["build"][1], 1),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "kernel_busy_ms_per_step": {k: v[2] / args.steps for k, v in prof.items()},
             "roofline": {"bound": "hbm", "kernel": "k_query (closest hit)", "achieved": achieved_gbs,
-                         "note": f"{split} azimuth ranges run on {split} streams: their launches overlap, so "
-                                 "per-launch durations include the sharing of the GPU",
                          "peak": peak, "unit": "GB/s", "frac": (achieved_gbs / peak) if achieved_gbs else None,
                          "traffic": traffic, "peak_source": peak_kind,
+                         "per": "closest-hit queries of one bounce: the launches of its azimuth ranges",
+                         "note": f"{split} azimuth ranges run on {split} streams, so the launches of a bounce "
+                                 "overlap: achieved divides their algorithmic bytes by the union of their CUDA-event "
+                                 "intervals; achieved_per_launch divides by the summed launch durations",
+                         "achieved_per_launch": per_launch_gbs,
+                         "algorithmic_bytes_per_bounce": algo_bytes / max(bounces, 1),
+                         "busy_ms_per_bounce": trace_busy / max(bounces, 1),
                          "algorithmic_bytes_per_query": bytes_per_closest,
                          "nodes_per_query": nodes_per_q, "tris_per_query": tris_per_q,
                          "launches_per_step": trace_launches / max(args.steps, 1),

@@ -180,8 +180,11 @@ typedef struct {
 #define RR_K_VIS 5   /* air-path candidates and their visibility queries */
 #define RR_K_COUNT 6
 typedef struct {
-  double ms[RR_K_COUNT];
+  double ms[RR_K_COUNT];        /* sum of the launches' event durations */
   uint64_t launches[RR_K_COUNT];
+  double busy_ms[RR_K_COUNT];   /* length of the union of the launches' event intervals: the time during
+                                   which at least one launch of the kind ran.  Launches on several streams
+                                   (split scans) overlap, so ms can exceed busy_ms. */
 } rr_profile;
 
 /* ---------------------------------------------------------------------- */
@@ -510,7 +513,9 @@ int rr_serve_stats_get(rr_server* server, rr_serve_stats* out, int reset);
 int rr_scene_stats(rr_scene* scene, rr_stats* stats, int reset);
 
 /* Per-kernel device time with CUDA events on the scene's launches.  While
-   enabled, each launch is bracketed by two events on its stream. */
+   enabled, each launch is bracketed by two events on its stream; the events
+   are placed on one time line by a base event recorded on the calling
+   thread's stream when profiling is switched on. */
 int rr_profile_enable(rr_scene* scene, int on);
 int rr_profile_read(rr_scene* scene, rr_profile* out, int reset);
 

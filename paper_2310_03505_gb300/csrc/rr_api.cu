@@ -81,15 +81,37 @@ void prof_end(rr_scene* s, cudaEvent_t stop, cudaStream_t st) {
 
 static void prof_collect(rr_scene* s) {
   for (ProfEvent& ev : s->prof_pending) {
-    float ms = 0.f;
+    float ms = 0.f, t0 = 0.f, t1 = 0.f;
     if (cudaEventSynchronize(ev.stop) == cudaSuccess && cudaEventElapsedTime(&ms, ev.start, ev.stop) == cudaSuccess) {
       s->prof_ms[ev.kind] += ms;
       s->prof_launches[ev.kind] += 1;
+      if (s->prof_base && cudaEventElapsedTime(&t0, s->prof_base, ev.start) == cudaSuccess &&
+          cudaEventElapsedTime(&t1, s->prof_base, ev.stop) == cudaSuccess)
+        s->prof_iv[ev.kind].push_back({t0, t1});
     }
     s->prof_pool.push_back(ev.start);
     s->prof_pool.push_back(ev.stop);
   }
   s->prof_pending.clear();
+}
+
+// length of the union of the collected intervals of one kind
+static double prof_union(std::vector<std::pair<double, double>>& iv) {
+  std::sort(iv.begin(), iv.end());
+  double total = 0.0, a = 0.0, b = -1.0;
+  bool open = false;
+  for (const auto& x : iv) {
+    if (open && x.first <= b) {
+      b = std::max(b, x.second);
+      continue;
+    }
+    if (open) total += b - a;
+    a = x.first;
+    b = x.second;
+    open = true;
+  }
+  if (open) total += b - a;
+  return total;
 }
 
 // ---------------------------------------------------------------------------
@@ -242,6 +264,7 @@ int rr_scene_destroy(rr_scene* s) {
     cudaEventDestroy(ev.stop);
   }
   for (auto e : s->prof_pool) cudaEventDestroy(e);
+  if (s->prof_base) cudaEventDestroy(s->prof_base);
   delete s;
   return RR_OK;
 }
@@ -599,6 +622,16 @@ int rr_scene_stats(rr_scene* s, rr_stats* out, int reset) {
 
 int rr_profile_enable(rr_scene* s, int on) {
   if (!s) return fail(RR_ERR_INVALID_ARG, "NULL scene");
+  if (on && !s->prof) {
+    // a new time origin: fold the intervals measured against the old one
+    prof_collect(s);
+    for (int k = 0; k < RR_K_COUNT; ++k) {
+      s->prof_busy_done[k] += prof_union(s->prof_iv[k]);
+      s->prof_iv[k].clear();
+    }
+    if (!s->prof_base) RR_CHECK_CUDA(cudaEventCreate(&s->prof_base), "profile event");
+    RR_CHECK_CUDA(cudaEventRecord(s->prof_base, t_stream), "profile event");
+  }
   s->prof = on != 0;
   return RR_OK;
 }
@@ -609,9 +642,12 @@ int rr_profile_read(rr_scene* s, rr_profile* out, int reset) {
   for (int k = 0; k < RR_K_COUNT; ++k) {
     out->ms[k] = s->prof_ms[k];
     out->launches[k] = s->prof_launches[k];
+    out->busy_ms[k] = s->prof_busy_done[k] + prof_union(s->prof_iv[k]);
     if (reset) {
       s->prof_ms[k] = 0.0;
       s->prof_launches[k] = 0;
+      s->prof_busy_done[k] = 0.0;
+      s->prof_iv[k].clear();
     }
   }
   return RR_OK;

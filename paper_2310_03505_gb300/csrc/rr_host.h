@@ -123,6 +123,9 @@ struct rr_scene {
   std::vector<cudaEvent_t> prof_pool;
   double prof_ms[RR_K_COUNT] = {0};
   uint64_t prof_launches[RR_K_COUNT] = {0};
+  cudaEvent_t prof_base = nullptr;                               // time origin of the intervals
+  std::vector<std::pair<double, double>> prof_iv[RR_K_COUNT];    // [start, stop] ms after prof_base
+  double prof_busy_done[RR_K_COUNT] = {0};                       // unions folded in before a new base
   std::atomic<uint64_t> launches{0};  // kernels launched for this scene (any stream)
 };
 

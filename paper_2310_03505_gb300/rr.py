@@ -79,7 +79,8 @@ class rr_stats(C.Structure):
 
 
 class rr_profile(C.Structure):
-    _fields_ = [("ms", C.c_double * RR_K_COUNT), ("launches", C.c_uint64 * RR_K_COUNT)]
+    _fields_ = [("ms", C.c_double * RR_K_COUNT), ("launches", C.c_uint64 * RR_K_COUNT),
+                ("busy_ms", C.c_double * RR_K_COUNT)]
 
 
 class rr_batch_config(C.Structure):
@@ -488,10 +489,12 @@ def rr_scene_stats(scene, reset: bool = False) -> dict:
 
 
 def rr_profile_enable(scene, on: bool) -> None:
+    _use_torch_stream()
     _check(load().rr_profile_enable(scene, 1 if on else 0))
 
 
 def rr_profile_read(scene, reset: bool = False) -> dict:
+    """Per kernel kind: (summed launch ms, launches, busy ms = union of the launch intervals)."""
     pr = rr_profile()
     _check(load().rr_profile_read(scene, C.byref(pr), 1 if reset else 0))
-    return {KERNEL_NAMES[k]: (pr.ms[k], pr.launches[k]) for k in range(RR_K_COUNT)}
+    return {KERNEL_NAMES[k]: (pr.ms[k], pr.launches[k], pr.busy_ms[k]) for k in range(RR_K_COUNT)}

@@ -246,3 +246,33 @@ def test_split_scan_equals_whole(tiny_scene, variant):
             rr.rr_scene_stats(h, reset=True)
     finally:
         rr.rr_batch_config_set(h, **saved)
+
+
+def test_profile_busy_time(tiny_scene):
+    """rr_profile_read's busy_ms is the union of a kind's launch intervals: on
+    one stream the launches of a kind never overlap, so it equals the summed
+    durations; split scans overlap their ranges' launches, so it is at most
+    that sum."""
+    _, pz, base, h = tiny_scene
+    p = scenes.sensor(**{**base, "rays_per_beam": 16})
+    saved = rr.rr_batch_config_get(h)
+    try:
+        for k in (1, 3):
+            rr.rr_batch_config_set(h, split_streams=k)
+            alone(h, pz, p)
+            rr.rr_profile_read(h, reset=True)
+            rr.rr_profile_enable(h, True)
+            for i in range(3):
+                alone(h, pz, {**p, "scan_id": i})
+            rr.rr_profile_enable(h, False)
+            prof = rr.rr_profile_read(h, reset=True)
+            ms, launches, busy = prof["trace"]
+            assert launches == 3 * k * p["max_bounces"]
+            tol = 2e-3 * launches + 1e-3   # event times are kept to about a microsecond
+            assert 0.0 < busy <= ms + tol, (k, ms, busy)
+            if k == 1:
+                for name, (m, n, b) in prof.items():
+                    assert abs(b - m) <= 2e-3 * n + 1e-3, (name, m, b)
+            assert rr.rr_profile_read(h)["trace"] == (0.0, 0, 0.0)   # the reset cleared it
+    finally:
+        rr.rr_batch_config_set(h, **saved)
