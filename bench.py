@@ -2,9 +2,12 @@
 
 One step = one pass of the whole hot path on the medium campus workload
 (about 200k triangles, 400 beams x 200 rays, at most 5 bounces, refraction
-and multipath on, 2000 range bins): LBVH rebuild from the resident vertices
-(ingest, Morton, radix sort, Karras hierarchy, refit) followed by one polar
+and multipath on, 2000 range bins): BVH rebuild from the resident vertices
+(ingest, Morton, radix sort, Karras hierarchy, refit, and with --step-bvh
+sah_top the binned-SAH top over the LBVH's subtrees) followed by one polar
 scan (raygen, trace / shade per bounce, range-bin accumulation, post pass).
+The batched and served scenes are built once, with --scene-bvh (default: the
+SAH top).
 Each step uses a new scan id, so every step traces new rays.
 
 Metric: Mrays/s = closest-hit queries over all bounces / device time of the
@@ -168,7 +171,13 @@ def oracle_sample(sc, pz, params, budget_s: float = 12.0, min_cols: int = 2):
 BATCHED_WORKLOAD = "campus_1M_tris_256_poses_random_walk_400_beams_32_512_rays_5_bounces_2000_bins"
 
 
-def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: int = 0):
+def set_bvh(rr, h, bvh: str):
+    """Scene BVH build: 'sah_top' (the library default) or 'lbvh'."""
+    if bvh != "sah_top":
+        rr.rr_batch_config_set(h, bvh_build=rr.RR_BVH_LBVH)
+
+
+def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: int = 0, bvh: str = "sah_top"):
     """The batched workload: 256 poses along a random walk through a ~1M
     triangle campus, rays per beam uneven per pose (32..512).  One step = the
     256 scans through rr_scan_batch_async after the autotuner chose the launch
@@ -179,6 +188,7 @@ def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: 
     from paper_2310_03505_gb300 import rr, scenes
     sc, poses, params = scenes.config_batched()
     h = rr.rr_scene_create(torch.from_numpy(sc.vertices).to(device), sc.triangles, sc.material_ids, sc.materials)
+    set_bvh(rr, h, bvh)
     n = len(params)
     outs = [torch.zeros(p["n_azimuth"], p["n_bins"], device=device) for p in params]
     n0 = sum(p["n_azimuth"] * p["rays_per_beam"] for p in params)
@@ -231,7 +241,7 @@ def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: 
         "config": {"triangles": sc.n_triangles, "n_scans": n, "n_azimuth": 400,
                    "rays_per_beam": {"min": int(min(ns)), "max": int(max(ns)), "mean": float(np.mean(ns))},
                    "initial_rays_per_step": n0, "max_bounces": 5, "n_bins": 2000, "node_format": "wide8_q8" if tuned_cfg["node_format"] == rr.RR_NODES_WIDE8 else "binary_fp32",
-                   "step": "256 scans, resident BVH (no rebuild)",
+                   "step": "256 scans, resident BVH (no rebuild)", "bvh": bvh,
                    "l2": "flushed between steps (256 MiB write, outside the timed events)"},
         "steps": steps, "warmup": warmup,
         "launch_sequences": int(len(first)), "workspace_bytes": int(ws_bytes),
@@ -245,7 +255,7 @@ def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: 
 SERVED_WORKLOAD = "4_scenes_50k_200k_1M_5M_tris_64_robots_poisson_16_512_rays_3_8_bounces_500_4000_bins"
 
 
-def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: int = 0):
+def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: int = 0, bvh: str = "sah_top"):
     """Scan requests from 64 simulated robots over 4 resident scenes (50k and
     200k-triangle campuses, the 1M-triangle campus, the 5M-triangle city),
     Poisson arrivals at each rate for `seconds`; every request draws a free
@@ -262,6 +272,8 @@ def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: 
            (scenes.campus(), 140.0), (scenes.campus(target_tris=1_000_000), 140.0), (scenes.city(), 290.0)]
     hs = [rr.rr_scene_create(torch.from_numpy(sc.vertices).to(device), sc.triangles, sc.material_ids, sc.materials)
           for sc, _ in scs]
+    for h in hs:
+        set_bvh(rr, h, bvh)
     torch.cuda.synchronize()
     max_img = 400 * 4000
     pool = torch.zeros(256, max_img, device=device)
@@ -331,7 +343,7 @@ def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: 
     served = dict(slots=4, memory_budget=96 << 30, max_batch_scans=64, max_batch_rays=8 << 20)
     plain = dict(slots=1, memory_budget=24 << 30, max_batch_scans=1)
     out = {"workload": SERVED_WORKLOAD, "seconds_per_rate": seconds,
-           "scenes_triangles": [sc.n_triangles for sc, _ in scs], "robots": 64,
+           "scenes_triangles": [sc.n_triangles for sc, _ in scs], "robots": 64, "bvh": bvh,
            "server": {k: int(v) for k, v in served.items()}, "rates": [], "per_scan_path": []}
     for k, rate in enumerate(rates):
         out["rates"].append(run(served, rate, 1000 + k))
@@ -354,6 +366,12 @@ def main():
     ap.add_argument("--node-format", default="auto", choices=["auto", "wide", "binary"],
                     help="BVH node format of the plain scan (auto: the library default)")
     ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--step-bvh", default="lbvh", choices=["sah_top", "lbvh"],
+                    help="BVH build of the main line, rebuilt every step: the LBVH alone (default) or with the "
+                         "binned-SAH top")
+    ap.add_argument("--scene-bvh", default="sah_top", choices=["sah_top", "lbvh"],
+                    help="BVH build of the batched and served scenes, built once: with the binned-SAH top "
+                         "(default) or the LBVH alone")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=10.0,
                     help="arrival window per request rate of the served workload")
@@ -408,6 +426,7 @@ def main():
 
     d_vtx = torch.from_numpy(sc.vertices).to(device)
     h = rr.rr_scene_create(d_vtx, sc.triangles, sc.material_ids, sc.materials)
+    set_bvh(rr, h, args.step_bvh)
     if args.node_format != "auto":
         rr.rr_batch_config_set(h, node_format=rr.RR_NODES_WIDE8 if args.node_format == "wide" else rr.RR_NODES_BINARY)
     node_format = "wide8_q8" if rr.rr_batch_config_get(h)["node_format"] == rr.RR_NODES_WIDE8 else "binary_fp32"
@@ -499,10 +518,10 @@ def main():
 
     batched = None
     if not args.no_batched:
-        batched = batched_bench(device, stream, flush, steps=args.batched_steps, rank=rank)
+        batched = batched_bench(device, stream, flush, steps=args.batched_steps, rank=rank, bvh=args.scene_bvh)
     served = None
     if not args.no_served and rank == 0:
-        served = served_bench(device, seconds=args.served_seconds, rank=rank)
+        served = served_bench(device, seconds=args.served_seconds, rank=rank, bvh=args.scene_bvh)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -518,7 +537,9 @@ def main():
             "config": {"workload": WORKLOAD, "triangles": sc.n_triangles, "n_azimuth": params["n_azimuth"],
                        "rays_per_beam": params["rays_per_beam"], "max_bounces": params["max_bounces"],
                        "n_bins": params["n_bins"], "node_format": node_format, "split_streams": split,
-                       "wide_nodes": info["n_wide_nodes"], "step": "LBVH rebuild + polar scan",
+                       "bvh": ("LBVH + binned-SAH top over its subtrees of <= 32 triangles"
+                               if args.step_bvh == "sah_top" else "LBVH"),
+                       "wide_nodes": info["n_wide_nodes"], "step": "BVH rebuild + polar scan",
                        "l2": "flushed between steps (256 MiB write, outside the timed events)",
                        "parallelism": f"replicas x{world}"},
             "scans_per_s": scans_per_s,

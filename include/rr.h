@@ -322,9 +322,20 @@ int rr_scan_batch_async(rr_scene* scene, uint32_t n, const rr_pose* poses, const
                         slow queries closing one range's bounce overlap the
                         other ranges' work (1..4; 0: the default, 3).  Scans
                         with a beam pattern run whole.  The image is the same
-                        up to the rounding of the bin sums. */
+                        up to the rounding of the bin sums.
+   bvh_build            RR_BVH_SAH_TOP (default): the LBVH (Morton codes,
+                        radix sort, Karras hierarchy, refit) with the part
+                        above its subtrees of at most 32 triangles rebuilt
+                        top down by binned SAH over those subtrees (HLBVH);
+                        RR_BVH_LBVH: the LBVH alone.  Every build of the
+                        scene (creation, rr_scene_update_vertices) uses it;
+                        setting a different value rebuilds the BVH (blocking).
+                        Both give the same closest hit for every query; the
+                        SAH top needs fewer node visits. */
 #define RR_NODES_WIDE8 0u
 #define RR_NODES_BINARY 1u
+#define RR_BVH_LBVH 0u
+#define RR_BVH_SAH_TOP 1u
 typedef struct {
   uint32_t wavefront_rays;
   uint32_t trace_block;
@@ -334,13 +345,14 @@ typedef struct {
   uint32_t refill_threshold;
   uint64_t workspace_limit;
   uint32_t split_streams;
-  uint32_t reserved;
+  uint32_t bvh_build;
 } rr_batch_config;
 
 int rr_batch_config_get(const rr_scene* scene, rr_batch_config* out);
 /* RR_ERR_INVALID_ARG for a trace_block other than 64/128/256, more than 64
-   blocks per SM, use_graph > 1, an unknown node_format, a refill_threshold
-   above 32, split_streams above 4 or a workspace limit below 1 MiB. */
+   blocks per SM, use_graph > 1, an unknown node_format or bvh_build, a
+   refill_threshold above 32, split_streams above 4 or a workspace limit
+   below 1 MiB. */
 int rr_batch_config_set(rr_scene* scene, const rr_batch_config* config);
 
 /* How rr_scan_batch would cut scans params[0..n) into launch sequences under

@@ -173,7 +173,7 @@ int device_status(ExecCtx* x, cudaStream_t st) {
     char msg[256];
     if (err & rr::kErrBadVertex)
       return fail(RR_ERR_INVALID_ARG, "a rebuild saw an invalid vertex index or a non-finite vertex");
-    if (err & rr::kErrBvh) return fail(RR_ERR_CUDA, "the wide BVH build failed; nothing was traced");
+    if (err & rr::kErrBvh) return fail(RR_ERR_CUDA, "the BVH build failed; nothing was traced");
     if (err & rr::kErrStack) return fail(RR_ERR_CAPACITY, "BVH deeper than the traversal stack");
     if (err & rr::kErrTimeout) return fail(RR_ERR_TIMEOUT, "a bounded device wait gave up");
     if (err & (rr::kErrCapacityRays | rr::kErrCapacityRecs)) {
@@ -222,11 +222,25 @@ void ctx_free(ExecCtx* x) {
 
 using namespace rr_host;
 
+int rr_host::rebuild_bvh(rr_scene* s, cudaStream_t st) {
+  if (s->nt == 0) return RR_OK;
+  RR_CHECK_CUDA(build_lbvh(s, st, true), "rebuilding the BVH");
+  uint32_t misc[8];
+  RR_CHECK_CUDA(cudaMemcpyAsync(misc, s->d_misc, sizeof misc, cudaMemcpyDeviceToHost, st), "reading the build status");
+  RR_CHECK_CUDA(cudaStreamSynchronize(st), "rebuilding the BVH");
+  if (misc[6] & rr::kErrTopBuild) return fail(RR_ERR_CUDA, "the SAH top of the BVH could not be built");
+  if (misc[6]) return fail(RR_ERR_INVALID_ARG, "the scene's vertices are invalid");
+  s->depth = misc[7];
+  if (s->depth > (uint32_t)rr::kStack)
+    return fail(RR_ERR_CAPACITY, "BVH depth " + std::to_string(s->depth) + " exceeds the traversal stack");
+  return RR_OK;
+}
+
 // one-thread kernel folding the build status into the scan status word
 __global__ void k_fold_build_status(const uint32_t* misc, const uint32_t* wctr, ScanCounters* ctr) {
   uint32_t e = 0;
-  if (misc[6]) e |= rr::kErrBadVertex;
-  if (wctr[4]) e |= rr::kErrBvh;
+  if (misc[6] & ~rr::kErrTopBuild) e |= rr::kErrBadVertex;
+  if ((misc[6] & rr::kErrTopBuild) || wctr[4]) e |= rr::kErrBvh;
   if (e) atomicOr(&ctr->error, e);
 }
 
@@ -248,7 +262,8 @@ int rr_scene_destroy(rr_scene* s) {
                   s->d_tri, s->d_nodes, s->d_centroid, s->d_keys[0], s->d_keys[1], s->d_vals[0], s->d_vals[1],
                   s->d_hist, s->d_parent, s->d_child, s->d_nbox, s->d_visit, s->d_misc,
                   s->d_cut, s->d_wnodes, s->d_wtri, s->d_wsrc, s->d_wrec, s->d_wctr, s->d_lobe_kind,
-                  s->d_lobe_samples};
+                  s->d_lobe_samples, s->d_range, s->d_cl_at, s->d_cl_bsum, s->d_cl_rec, s->d_cl_idx,
+                  s->d_top_slot, s->d_top_task, s->d_top_ready, s->d_top_small, s->d_top_ctr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ctx_free(&s->main);
@@ -367,6 +382,7 @@ int rr_scene_create(const float* vertices, uint32_t n_vertices, const uint32_t* 
     if (misc[6] & 1u) return bail(fail(RR_ERR_INVALID_ARG, "a triangle references a vertex index >= n_vertices"));
     if (misc[6] & 2u) return bail(fail(RR_ERR_INVALID_ARG, "a material id is >= n_materials"));
     if (misc[6] & rr::kErrBadVertex) return bail(fail(RR_ERR_INVALID_ARG, "non-finite vertex coordinates"));
+    if (misc[6] & rr::kErrTopBuild) return bail(fail(RR_ERR_CUDA, "the SAH top of the BVH could not be built"));
     s->depth = misc[7];
     if (s->depth > (uint32_t)rr::kStack)
       return bail(fail(RR_ERR_CAPACITY, "BVH depth " + std::to_string(s->depth) + " exceeds the traversal stack"));

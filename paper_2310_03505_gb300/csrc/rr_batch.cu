@@ -387,6 +387,7 @@ int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor
   a.wide = wide ? 1u : 0u;
   a.node_cap = wide ? s->wcap : (s->nt > 1 ? s->nt - 1 : 0u);
   a.bvh_status = wide ? s->d_wctr + 4 : nullptr;
+  a.build_status = s->d_misc + 6;
   a.desc = (const ScanDesc*)(w + L.off_desc);
   a.ray0 = (const uint32_t*)(w + L.off_desc + (size_t)n * sizeof(ScanDesc));
   a.col0 = a.ray0 + (n + 1);
@@ -515,6 +516,8 @@ static int cfg_check(const rr_batch_config* c) {
   if (c->split_streams > kMaxSplit) return fail(RR_ERR_INVALID_ARG, "split_streams must be in [0, 4]");
   if (c->workspace_limit != 0 && c->workspace_limit < (uint64_t(1) << 20))
     return fail(RR_ERR_INVALID_ARG, "workspace_limit must be 0 or at least 1 MiB");
+  if (c->bvh_build != RR_BVH_LBVH && c->bvh_build != RR_BVH_SAH_TOP)
+    return fail(RR_ERR_INVALID_ARG, "bvh_build must be RR_BVH_LBVH or RR_BVH_SAH_TOP");
   return RR_OK;
 }
 
@@ -528,6 +531,7 @@ static void cfg_to_abi(const LaunchCfg& c, rr_batch_config* o) {
   o->refill_threshold = c.refill;
   o->workspace_limit = c.ws_limit;
   o->split_streams = c.split;
+  o->bvh_build = c.bvh_build;
 }
 
 static LaunchCfg cfg_from_abi(const rr_batch_config* c) {
@@ -540,6 +544,7 @@ static LaunchCfg cfg_from_abi(const rr_batch_config* c) {
   o.refill = c->refill_threshold ? c->refill_threshold : 8u;
   if (c->workspace_limit) o.ws_limit = c->workspace_limit;
   o.split = c->split_streams ? c->split_streams : 3u;
+  o.bvh_build = c->bvh_build;
   return o;
 }
 
@@ -615,8 +620,9 @@ int rr_batch_config_set(rr_scene* s, const rr_batch_config* c) {
   if (!s || !c) return fail(RR_ERR_INVALID_ARG, "NULL argument");
   const int rc = cfg_check(c);
   if (rc != RR_OK) return rc;
+  const bool rebuild = c->bvh_build != s->cfg.bvh_build;
   s->cfg = cfg_from_abi(c);
-  return RR_OK;
+  return rebuild ? rebuild_bvh(s, current_stream()) : RR_OK;
 }
 
 int rr_batch_plan(uint32_t n, const rr_sensor_params* params, const rr_batch_config* config, uint32_t* first,

@@ -8,6 +8,9 @@
 //                (Karras, "Maximizing parallelism in the construction of BVHs,
 //                octrees, and k-d trees", HPG 2012), equal codes ordered by index
 //   a5 refit     bottom-up child boxes, the second child to arrive merges
+//   a5b SAH top  (RR_BVH_SAH_TOP) the part of the tree above its subtrees of
+//                at most kClusterMax leaves rebuilt top down by binned SAH
+//                over those subtrees, in the node slots it frees
 // plus the per-material lobe table of Eq. 5 used by the beam window (Eq. 4).
 //
 // The hierarchy is a binary BVH with one triangle per leaf.  Internal node i
@@ -36,6 +39,25 @@ __device__ __forceinline__ uint32_t enc_f(float f) {
 }
 __device__ __forceinline__ float dec_f(uint32_t e) {
   return __uint_as_float((e & 0x80000000u) ? (e & 0x7FFFFFFFu) : ~e);
+}
+
+// device-scope acquire loads and release stores of the bounded producer /
+// consumer waits in the SAH top and the wide collapse
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -269,7 +291,7 @@ __device__ __forceinline__ int delta(const uint32_t* __restrict__ k, int n, int 
 // a4: internal node i covers a key range that starts or ends at i; its split
 // is the highest position where the common prefix shrinks
 __global__ void k_karras(const uint32_t* __restrict__ keys, int n, uint32_t* __restrict__ child,
-                         uint32_t* __restrict__ parent, uint32_t* __restrict__ visit) {
+                         uint32_t* __restrict__ parent, uint32_t* __restrict__ visit, uint2* __restrict__ range) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   const int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -292,6 +314,7 @@ __global__ void k_karras(const uint32_t* __restrict__ keys, int n, uint32_t* __r
   const uint32_t right = (hi == gamma + 1) ? ((uint32_t)(gamma + 1) | kLeafBit) : (uint32_t)(gamma + 1);
   child[2 * i] = left;
   child[2 * i + 1] = right;
+  range[i] = make_uint2((uint32_t)lo, (uint32_t)hi);
   parent[(left & kLeafBit) ? (n - 1 + (left & ~kLeafBit)) : left] = (uint32_t)i;
   parent[(right & kLeafBit) ? (n - 1 + (right & ~kLeafBit)) : right] = (uint32_t)i;
   visit[i] = 0;
@@ -345,6 +368,674 @@ __global__ void k_depth(uint32_t n, const uint32_t* __restrict__ parent, uint32_
     p = parent[p];
   }
   atomicMax(&misc[7], d);
+}
+
+// ---------------------------------------------------------------------------
+// a5b: SAH top (HLBVH: Pantaleoni and Luebke, HPG 2010; Garanzha, Pantaleoni
+// and McAllister, HPG 2011).  The clusters are the LBVH's maximal subtrees of
+// at most kClusterMax leaves, in leaf order; the C - 1 internal nodes above
+// them are rebuilt top down by binned SAH over the clusters (box = union of
+// the subtree, weight = its leaves), reusing exactly their node slots with
+// the root kept at 0.  A task over clusters [b, e) at depth d:
+//   centroid c = 0.5 (lo + hi); bounds cmin, cmax; per axis with
+//   ext = cmax - cmin > 0: scale = kTopBins / ext, bin
+//   q = min(kTopBins - 1, trunc((c - cmin) scale)), each step rounded to float;
+//   a split after bin q with both sides non-empty costs
+//   area(L) weight(L) + area(R) weight(R) (float, area = dx dy + dy dz + dz dx);
+//   the lowest cost wins, ties to the lower axis, then the lower q; without a
+//   split, or at depth >= kTopMedianDepth, the first n / 2 clusters go left.
+//   The partition keeps the order on each side; a side of one cluster is that
+//   cluster's subtree, otherwise a new task at d + 1.
+// Every operation is exactly rounded, so a host restatement of these rules
+// builds the same tree.  Tasks of more than kTopSmall clusters are worked by
+// whole blocks (k_top_sah), smaller ones by one warp each (k_top_small).
+constexpr uint32_t kClusterMax = 32;
+constexpr int kTopBins = 32;
+constexpr uint32_t kTopMedianDepth = 32;
+constexpr int kTopBlock = 256;
+constexpr uint32_t kTopSmall = 32;            // a warp task: at most one cluster per lane
+constexpr int kClTile = 2048;                 // compaction: 256 threads x 8 leaves
+constexpr uint32_t kTopSpinLimit = 1u << 22;  // x <= 256 ns naps: about a second
+// counters of the SAH top
+constexpr int kCtrHead = 0;       // next block task to take
+constexpr int kCtrSlots = 1;      // node slots handed out after the root
+constexpr int kCtrMarked = 2;     // top slots found after the root (k_top_mark)
+constexpr int kCtrClusters = 3;   // C
+constexpr int kCtrTasks = 4;      // block tasks created
+constexpr int kCtrPending = 5;    // block tasks created and not finished
+constexpr int kCtrSmall = 6;      // warp tasks created
+constexpr int kCtrSmallHead = 7;  // next warp task to take
+
+// top part and clusters: internal node i is a top node when it has more than
+// kClusterMax leaves; a child of a top node with at most kClusterMax leaves
+// is a cluster root, recorded at its first leaf
+__global__ void k_top_mark(uint32_t n, const uint32_t* __restrict__ child, const uint2* __restrict__ range,
+                           uint32_t* __restrict__ cl_at, uint32_t* __restrict__ slot, uint32_t* __restrict__ ctr) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i + 1 >= n) return;
+  const uint2 r = range[i];
+  if (r.y - r.x + 1u <= kClusterMax) return;
+  if (i == 0) slot[0] = 0u;
+  else slot[1u + atomicAdd(&ctr[kCtrMarked], 1u)] = i;
+  for (int k = 0; k < 2; ++k) {
+    const uint32_t c = child[2 * i + k];
+    uint32_t first, size;
+    if (c & kLeafBit) {
+      first = c & ~kLeafBit;
+      size = 1u;
+    } else {
+      const uint2 rc = range[c];
+      first = rc.x;
+      size = rc.y - rc.x + 1u;
+    }
+    if (size <= kClusterMax) cl_at[first] = c;
+  }
+}
+
+// clusters of each block of kClTile leaves
+__global__ void __launch_bounds__(256) k_top_count(uint32_t n, const uint32_t* __restrict__ cl_at,
+                                                   uint32_t* __restrict__ bsum) {
+  __shared__ uint32_t s_w[8];
+  const uint32_t base = blockIdx.x * kClTile + threadIdx.x * 8u;
+  uint32_t c = 0;
+  for (uint32_t k = 0; k < 8; ++k)
+    if (base + k < n && cl_at[base + k] != kNone) ++c;
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < 8; ++w) t += s_w[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+// clusters in leaf order (bsum holds the exclusive block offsets): record,
+// starting order, and the root task over all of them
+__global__ void __launch_bounds__(256) k_top_compact(uint32_t n, const uint32_t* __restrict__ cl_at,
+                                                     const uint32_t* __restrict__ bsum, const uint2* __restrict__ range,
+                                                     const float* __restrict__ nbox, float4* __restrict__ rec,
+                                                     uint32_t* __restrict__ order, uint4* __restrict__ task,
+                                                     uint32_t* __restrict__ ready, uint4* __restrict__ small,
+                                                     uint32_t* __restrict__ ctr) {
+  __shared__ uint32_t s_w[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t base = blockIdx.x * kClTile + threadIdx.x * 8u;
+  uint32_t c = 0;
+  for (uint32_t k = 0; k < 8; ++k)
+    if (base + k < n && cl_at[base + k] != kNone) ++c;
+  uint32_t x = c;   // inclusive scan over the warp
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  uint32_t pos = bsum[blockIdx.x] + x - c;
+  for (int w = 0; w < warp; ++w) pos += s_w[w];
+  for (uint32_t k = 0; k < 8; ++k) {
+    const uint32_t j = base + k;
+    if (j >= n) break;
+    const uint32_t ref = cl_at[j];
+    if (ref != kNone) {
+      const uint32_t slot = (ref & kLeafBit) ? (n - 1 + (ref & ~kLeafBit)) : ref;
+      const float* b = nbox + 6 * (size_t)slot;
+      uint32_t weight = 1u;
+      if (!(ref & kLeafBit)) {
+        const uint2 r = range[ref];
+        weight = r.y - r.x + 1u;
+      }
+      rec[2 * (size_t)pos] = make_float4(b[0], b[1], b[2], __uint_as_float(weight));
+      rec[2 * (size_t)pos + 1] = make_float4(b[3], b[4], b[5], __uint_as_float(ref));
+      order[pos] = pos;
+      ++pos;
+    }
+    if (j == n - 1) {   // the last leaf: pos is now the number of clusters
+      ctr[kCtrClusters] = pos;
+      if (pos > kTopSmall) {
+        task[0] = make_uint4(0u, pos, 0u, 0u);
+        ready[0] = 1u;
+        ctr[kCtrTasks] = 1u;
+        ctr[kCtrPending] = 1u;
+      } else {
+        small[0] = make_uint4(0u, pos, 0u, 0u);
+        ctr[kCtrSmall] = 1u;
+      }
+    }
+  }
+}
+
+struct TopArgs {
+  const float4* rec;      // [C][2]
+  uint32_t* order[2];     // ping-pong cluster orders
+  const uint32_t* slot;   // [C - 1] node slots of the top part, root first
+  uint4* task;            // [C - 1] block tasks (more than kTopSmall clusters)
+  uint32_t* ready;        // [C - 1] block task published
+  uint4* small;           // [C - 1] warp tasks (2 to kTopSmall clusters)
+  uint32_t* ctr;          // kCtr*
+  float4* nodes;
+  uint32_t* child;
+  uint32_t* parent;
+  float* nbox;
+  uint32_t* misc;
+  uint32_t n;
+};
+
+__device__ __forceinline__ float box_area_rn(float3 lo, float3 hi) {
+  const float dx = __fsub_rn(hi.x, lo.x), dy = __fsub_rn(hi.y, lo.y), dz = __fsub_rn(hi.z, lo.z);
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dy), __fmul_rn(dy, dz)), __fmul_rn(dz, dx));
+}
+__device__ __forceinline__ float3 cl_centroid(float4 lo, float4 hi) {
+  return make_float3(__fmul_rn(0.5f, __fadd_rn(lo.x, hi.x)), __fmul_rn(0.5f, __fadd_rn(lo.y, hi.y)),
+                     __fmul_rn(0.5f, __fadd_rn(lo.z, hi.z)));
+}
+__device__ __forceinline__ int top_bin(float c, float cmin, float scale) {
+  return min(__float2int_rz(__fmul_rn(__fsub_rn(c, cmin), scale)), kTopBins - 1);
+}
+__device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+constexpr uint32_t kEncPosInf = 0xFF800000u, kEncNegInf = 0x007FFFFFu;   // enc_f(+inf), enc_f(-inf)
+constexpr int kBinWords = 8;   // per bin: clusters, weight, lo xyz, hi xyz (encoded)
+
+__device__ __forceinline__ void bins_clear(uint32_t* bins, int i0, int stride) {
+  for (int i = i0; i < 3 * kTopBins; i += stride) {
+    uint32_t* q = bins + kBinWords * i;
+    q[0] = 0u;
+    q[1] = 0u;
+    q[2] = q[3] = q[4] = kEncPosInf;
+    q[5] = q[6] = q[7] = kEncNegInf;
+  }
+}
+__device__ __forceinline__ void bins_add(uint32_t* bins, int k, int q, uint32_t w, float4 lo, float4 hi) {
+  uint32_t* b = bins + kBinWords * (k * kTopBins + q);
+  atomicAdd(&b[0], 1u);
+  atomicAdd(&b[1], w);
+  atomicMin(&b[2], enc_f(lo.x));
+  atomicMin(&b[3], enc_f(lo.y));
+  atomicMin(&b[4], enc_f(lo.z));
+  atomicMax(&b[5], enc_f(hi.x));
+  atomicMax(&b[6], enc_f(hi.y));
+  atomicMax(&b[7], enc_f(hi.z));
+}
+
+struct Split {
+  bool valid;
+  float cost;
+  int q;
+  uint32_t nl;   // clusters left of the split
+};
+
+// Best split after one of the bins of one axis (bins: [kTopBins][kBinWords]),
+// evaluated by a full warp, lane q = bin q, with prefix (left) and suffix
+// (right) sweeps; the result is the same in every lane.  Lowest cost, ties
+// to the lower bin.
+__device__ Split warp_best_split(const uint32_t* bins, int lane) {
+  const uint32_t* b = bins + kBinWords * lane;
+  uint32_t pn = b[0], pw = b[1];
+  float3 plo = make_float3(dec_f(b[2]), dec_f(b[3]), dec_f(b[4]));
+  float3 phi = make_float3(dec_f(b[5]), dec_f(b[6]), dec_f(b[7]));
+  uint32_t sn = pn, sw = pw;
+  float3 slo = plo, shi = phi;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t yn = __shfl_up_sync(0xFFFFFFFFu, pn, off), yw = __shfl_up_sync(0xFFFFFFFFu, pw, off);
+    const float ylx = __shfl_up_sync(0xFFFFFFFFu, plo.x, off), yly = __shfl_up_sync(0xFFFFFFFFu, plo.y, off),
+                ylz = __shfl_up_sync(0xFFFFFFFFu, plo.z, off);
+    const float yhx = __shfl_up_sync(0xFFFFFFFFu, phi.x, off), yhy = __shfl_up_sync(0xFFFFFFFFu, phi.y, off),
+                yhz = __shfl_up_sync(0xFFFFFFFFu, phi.z, off);
+    const uint32_t zn = __shfl_down_sync(0xFFFFFFFFu, sn, off), zw = __shfl_down_sync(0xFFFFFFFFu, sw, off);
+    const float zlx = __shfl_down_sync(0xFFFFFFFFu, slo.x, off), zly = __shfl_down_sync(0xFFFFFFFFu, slo.y, off),
+                zlz = __shfl_down_sync(0xFFFFFFFFu, slo.z, off);
+    const float zhx = __shfl_down_sync(0xFFFFFFFFu, shi.x, off), zhy = __shfl_down_sync(0xFFFFFFFFu, shi.y, off),
+                zhz = __shfl_down_sync(0xFFFFFFFFu, shi.z, off);
+    if (lane >= off) {
+      pn += yn;
+      pw += yw;
+      plo = make_float3(fminf(plo.x, ylx), fminf(plo.y, yly), fminf(plo.z, ylz));
+      phi = make_float3(fmaxf(phi.x, yhx), fmaxf(phi.y, yhy), fmaxf(phi.z, yhz));
+    }
+    if (lane + off < 32) {
+      sn += zn;
+      sw += zw;
+      slo = make_float3(fminf(slo.x, zlx), fminf(slo.y, zly), fminf(slo.z, zlz));
+      shi = make_float3(fmaxf(shi.x, zhx), fmaxf(shi.y, zhy), fmaxf(shi.z, zhz));
+    }
+  }
+  // split after bin lane - 1: left = prefix of lane - 1, right = suffix of lane
+  const uint32_t ln = __shfl_up_sync(0xFFFFFFFFu, pn, 1), lw = __shfl_up_sync(0xFFFFFFFFu, pw, 1);
+  const float llx = __shfl_up_sync(0xFFFFFFFFu, plo.x, 1), lly = __shfl_up_sync(0xFFFFFFFFu, plo.y, 1),
+              llz = __shfl_up_sync(0xFFFFFFFFu, plo.z, 1);
+  const float lhx = __shfl_up_sync(0xFFFFFFFFu, phi.x, 1), lhy = __shfl_up_sync(0xFFFFFFFFu, phi.y, 1),
+              lhz = __shfl_up_sync(0xFFFFFFFFu, phi.z, 1);
+  Split r;
+  r.valid = lane >= 1 && ln > 0u && sn > 0u;
+  r.cost = 0.0f;
+  r.q = lane;
+  r.nl = ln;
+  if (r.valid) {
+    const float al = box_area_rn(make_float3(llx, lly, llz), make_float3(lhx, lhy, lhz));
+    const float ar = box_area_rn(slo, shi);
+    r.cost = __fadd_rn(__fmul_rn(al, __uint2float_rn(lw)), __fmul_rn(ar, __uint2float_rn(sw)));
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const bool ov = __shfl_xor_sync(0xFFFFFFFFu, r.valid, off);
+    const float oc = __shfl_xor_sync(0xFFFFFFFFu, r.cost, off);
+    const int oq = __shfl_xor_sync(0xFFFFFFFFu, r.q, off);
+    const uint32_t onl = __shfl_xor_sync(0xFFFFFFFFu, r.nl, off);
+    if (ov && (!r.valid || oc < r.cost || (oc == r.cost && oq < r.q))) {
+      r.valid = true;
+      r.cost = oc;
+      r.q = oq;
+      r.nl = onl;
+    }
+  }
+  return r;
+}
+
+// the node of a task: child boxes (encoded lo xyz, hi xyz) and references
+__device__ __forceinline__ void write_top_node(const TopArgs& a, uint32_t slot, const uint32_t (&eb)[2][6],
+                                               const uint32_t (&ref)[2]) {
+  float bx[2][6];
+  for (int side = 0; side < 2; ++side)
+    for (int q = 0; q < 6; ++q) bx[side][q] = dec_f(eb[side][q]);
+  float4* nd = a.nodes + 4 * (size_t)slot;
+  nd[0] = make_float4(bx[0][0], bx[0][3], bx[0][1], bx[0][4]);
+  nd[1] = make_float4(bx[1][0], bx[1][3], bx[1][1], bx[1][4]);
+  nd[2] = make_float4(bx[0][2], bx[0][5], bx[1][2], bx[1][5]);
+  nd[3] = make_float4(__uint_as_float(ref[0]), __uint_as_float(ref[1]), 0.f, 0.f);
+  a.child[2 * slot] = ref[0];
+  a.child[2 * slot + 1] = ref[1];
+  for (int side = 0; side < 2; ++side) a.parent[node_slot(ref[side], a.n)] = slot;
+  float* nb = a.nbox + 6 * (size_t)slot;
+  for (int q = 0; q < 3; ++q) {
+    nb[q] = fminf(bx[0][q], bx[1][q]);
+    nb[3 + q] = fmaxf(bx[0][3 + q], bx[1][3 + q]);
+  }
+}
+
+// Block tasks (more than kTopSmall clusters), persistent: each block takes
+// the next task number and waits (bounded) until that task is published.
+// Tasks are numbered in the order they are created, a task by the block
+// working on its parent, which took a smaller number earlier and is running;
+// so the smallest number any block waits for belongs to a parent in
+// progress, and every wait ends -- with the task, or with the count of
+// pending tasks at zero when no task of that number will come.  Children of
+// at most kTopSmall clusters go to the warp-task list.
+__global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
+  __shared__ uint32_t s_bins[3 * kTopBins * kBinWords];
+  __shared__ uint32_t s_cb[6], s_side[2][6];
+  __shared__ uint32_t s_task[4], s_stop;
+  __shared__ Split s_split[3];
+  __shared__ uint32_t s_wl[kTopBlock / 32], s_wr[kTopBlock / 32], s_base[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t C = a.ctr[kCtrClusters];
+  if (C <= kTopSmall) return;   // no block task: the warp tasks do it all
+  const uint32_t n_nodes = C - 1;
+  if (a.ctr[kCtrMarked] + 1u != n_nodes) {   // the marked top part and the clusters disagree: leave the LBVH as it is
+    if (blockIdx.x == 0 && tid == 0) atomicOr(&a.misc[6], kErrTopBuild);
+    return;
+  }
+  while (true) {
+    if (tid == 0) {
+      s_stop = 0u;
+      const uint32_t ti = atomicAdd(&a.ctr[kCtrHead], 1u);
+      if (ti >= n_nodes) {
+        s_stop = 1u;
+      } else {
+        uint32_t spins = 0, nap = 32;
+        while (ld_acquire_u32(&a.ready[ti]) == 0u) {
+          if (ld_acquire_u32(&a.ctr[kCtrPending]) == 0u) {   // all tasks done: none numbered ti will come
+            s_stop = 1u;
+            break;
+          }
+          if (++spins > kTopSpinLimit || (ld_acquire_u32(&a.misc[6]) & kErrTopBuild)) {
+            atomicOr(&a.misc[6], kErrTopBuild);
+            s_stop = 1u;
+            break;
+          }
+          __nanosleep(nap);
+          if (nap < 256) nap <<= 1;
+        }
+        if (!s_stop) {
+          const uint4 t = __ldcg(&a.task[ti]);
+          s_task[0] = t.x;
+          s_task[1] = t.y;
+          s_task[2] = t.z;
+          s_task[3] = t.w;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const uint32_t b = s_task[0], n = s_task[1] - s_task[0], slot = s_task[2];
+    const uint32_t depth = s_task[3] & 0x7FFFFFFFu, src = s_task[3] >> 31;
+    const uint32_t* in = a.order[src] + b;
+    uint32_t* out = a.order[src ^ 1u] + b;
+    bins_clear(s_bins, tid, kTopBlock);
+    if (tid < 6) {
+      s_cb[tid] = tid < 3 ? kEncPosInf : kEncNegInf;
+      s_side[0][tid] = tid < 3 ? kEncPosInf : kEncNegInf;
+      s_side[1][tid] = tid < 3 ? kEncPosInf : kEncNegInf;
+    }
+    if (tid < 2) s_base[tid] = 0u;
+    __syncthreads();
+    // centroid bounds
+    {
+      float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (uint32_t i = tid; i < n; i += kTopBlock) {
+        const uint32_t c = __ldcg(in + i);
+        const float3 cc = cl_centroid(__ldg(&a.rec[2 * (size_t)c]), __ldg(&a.rec[2 * (size_t)c + 1]));
+        for (int k = 0; k < 3; ++k) {
+          mn[k] = fminf(mn[k], comp(cc, k));
+          mx[k] = fmaxf(mx[k], comp(cc, k));
+        }
+      }
+      for (int k = 0; k < 3; ++k)
+        for (int off = 16; off > 0; off >>= 1) {
+          mn[k] = fminf(mn[k], __shfl_xor_sync(0xFFFFFFFFu, mn[k], off));
+          mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xFFFFFFFFu, mx[k], off));
+        }
+      if (lane == 0)
+        for (int k = 0; k < 3; ++k) {
+          atomicMin(&s_cb[k], enc_f(mn[k]));
+          atomicMax(&s_cb[3 + k], enc_f(mx[k]));
+        }
+    }
+    __syncthreads();
+    float cmin[3], scale[3];
+    bool axis_ok[3];
+    for (int k = 0; k < 3; ++k) {
+      cmin[k] = dec_f(s_cb[k]);
+      const float ext = __fsub_rn(dec_f(s_cb[3 + k]), cmin[k]);
+      axis_ok[k] = ext > 0.0f && depth < kTopMedianDepth;
+      scale[k] = axis_ok[k] ? __fdiv_rn((float)kTopBins, ext) : 0.0f;
+    }
+    if (axis_ok[0] || axis_ok[1] || axis_ok[2]) {
+      for (uint32_t i = tid; i < n; i += kTopBlock) {
+        const uint32_t c = __ldcg(in + i);
+        const float4 lo = __ldg(&a.rec[2 * (size_t)c]), hi = __ldg(&a.rec[2 * (size_t)c + 1]);
+        const float3 cc = cl_centroid(lo, hi);
+        for (int k = 0; k < 3; ++k)
+          if (axis_ok[k]) bins_add(s_bins, k, top_bin(comp(cc, k), cmin[k], scale[k]), __float_as_uint(lo.w), lo, hi);
+      }
+    }
+    __syncthreads();
+    if (warp < 3) {
+      Split r;
+      r.valid = false;
+      if (axis_ok[warp]) r = warp_best_split(s_bins + kBinWords * kTopBins * warp, lane);
+      if (lane == 0) s_split[warp] = r;
+    }
+    __syncthreads();
+    int axis = -1, split = 0;
+    uint32_t nl = n / 2u;
+    for (int k = 0; k < 3; ++k)
+      if (s_split[k].valid && (axis < 0 || s_split[k].cost < s_split[axis].cost)) axis = k;
+    if (axis >= 0) {
+      split = s_split[axis].q;
+      nl = s_split[axis].nl;
+    }
+    // stable partition into the other order buffer, 8 clusters per thread per round
+    for (uint32_t t0 = 0; t0 < n; t0 += 8u * kTopBlock) {
+      const uint32_t i0 = t0 + 8u * tid;
+      uint32_t cs[8], lmask = 0u, hmask = 0u;
+      float v[2][6] = {{INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY},
+                       {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY}};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t i = i0 + k;
+        cs[k] = 0u;
+        if (i < n) {
+          const uint32_t c = __ldcg(in + i);
+          const float4 lo = __ldg(&a.rec[2 * (size_t)c]), hi = __ldg(&a.rec[2 * (size_t)c + 1]);
+          const bool left =
+              axis >= 0 ? top_bin(comp(cl_centroid(lo, hi), axis), cmin[axis], scale[axis]) < split : i < nl;
+          cs[k] = c;
+          hmask |= 1u << k;
+          if (left) lmask |= 1u << k;
+          const int side = left ? 0 : 1;
+          v[side][0] = fminf(v[side][0], lo.x);
+          v[side][1] = fminf(v[side][1], lo.y);
+          v[side][2] = fminf(v[side][2], lo.z);
+          v[side][3] = fmaxf(v[side][3], hi.x);
+          v[side][4] = fmaxf(v[side][4], hi.y);
+          v[side][5] = fmaxf(v[side][5], hi.z);
+        }
+      }
+      const uint32_t cl = __popc(lmask), cr = __popc(hmask & ~lmask);
+      // side boxes
+      for (int side = 0; side < 2; ++side) {
+        for (int off = 16; off > 0; off >>= 1)
+          for (int q = 0; q < 6; ++q) {
+            const float o = __shfl_xor_sync(0xFFFFFFFFu, v[side][q], off);
+            v[side][q] = q < 3 ? fminf(v[side][q], o) : fmaxf(v[side][q], o);
+          }
+        if (lane == 0 && v[side][0] <= v[side][3])
+          for (int q = 0; q < 6; ++q) {
+            if (q < 3) atomicMin(&s_side[side][q], enc_f(v[side][q]));
+            else atomicMax(&s_side[side][q], enc_f(v[side][q]));
+          }
+      }
+      // exclusive offsets of the threads' left and right counts
+      uint32_t xl = cl, xr = cr;
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t yl = __shfl_up_sync(0xFFFFFFFFu, xl, off), yr = __shfl_up_sync(0xFFFFFFFFu, xr, off);
+        if (lane >= off) {
+          xl += yl;
+          xr += yr;
+        }
+      }
+      if (lane == 31) {
+        s_wl[warp] = xl;
+        s_wr[warp] = xr;
+      }
+      __syncthreads();
+      uint32_t offl = s_base[0] + xl - cl, offr = s_base[1] + xr - cr, totl = 0, totr = 0;
+      for (int w = 0; w < kTopBlock / 32; ++w) {
+        if (w < warp) {
+          offl += s_wl[w];
+          offr += s_wr[w];
+        }
+        totl += s_wl[w];
+        totr += s_wr[w];
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (!(hmask >> k & 1u)) continue;
+        const bool left = lmask >> k & 1u;
+        // the bins and this pass classify with the same arithmetic, so the
+        // left side holds exactly nl clusters; refuse anything else
+        const uint32_t pos = left ? offl++ : nl + offr++;
+        if (left ? pos < nl : pos < n) out[pos] = cs[k];
+        else atomicOr(&a.misc[6], kErrTopBuild);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        s_base[0] += totl;
+        s_base[1] += totr;
+      }
+      __syncthreads();
+    }
+    __threadfence();   // the new order is visible before the children are published
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t ref[2] = {kNone, kNone}, pend[2] = {kNone, kNone}, n_pend = 0;
+      bool ok = true;
+      for (int side = 0; side < 2 && ok; ++side) {
+        const uint32_t first = side ? nl : 0u, cnt = side ? n - nl : nl;
+        if (cnt == 1u) {
+          ref[side] = __float_as_uint(__ldg(&a.rec[2 * (size_t)__ldcg(out + first) + 1]).w);
+          continue;
+        }
+        const uint32_t si = 1u + atomicAdd(&a.ctr[kCtrSlots], 1u);
+        if (si >= n_nodes) {   // cannot happen for a consistent marking; refuse rather than write past the slots
+          ok = false;
+          break;
+        }
+        ref[side] = a.slot[si];
+        const uint4 t = make_uint4(b + first, b + first + cnt, ref[side], (depth + 1u) | ((src ^ 1u) << 31));
+        const uint32_t ti = atomicAdd(cnt <= kTopSmall ? &a.ctr[kCtrSmall] : &a.ctr[kCtrTasks], 1u);
+        if (ti >= n_nodes) {
+          ok = false;
+          break;
+        }
+        if (cnt <= kTopSmall) {
+          a.small[ti] = t;
+        } else {
+          a.task[ti] = t;
+          pend[side] = ti;
+          ++n_pend;
+        }
+      }
+      if (!ok) {
+        atomicOr(&a.misc[6], kErrTopBuild);
+      } else {
+        uint32_t eb[2][6];
+        for (int side = 0; side < 2; ++side)
+          for (int q = 0; q < 6; ++q) eb[side][q] = s_side[side][q];
+        write_top_node(a, slot, eb, ref);
+        if (n_pend) atomicAdd(&a.ctr[kCtrPending], n_pend);   // counted before they can finish
+        __threadfence();
+        for (int side = 0; side < 2; ++side)
+          if (pend[side] != kNone) st_release_u32(&a.ready[pend[side]], 1u);
+      }
+      atomicSub(&a.ctr[kCtrPending], 1u);   // this task is done
+    }
+    __syncthreads();
+  }
+}
+
+// Warp tasks (2 to kTopSmall clusters), after the block tasks: a warp builds
+// the whole subtree of a task, a cluster per lane; a sub-task is the mask of
+// its lanes (the lane order is the cluster order, so a partition by mask is
+// stable).  The same rules and arithmetic as the block tasks.
+constexpr int kSmallWarps = 8;
+__global__ void __launch_bounds__(32 * kSmallWarps) k_top_small(TopArgs a) {
+  __shared__ uint32_t s_bins[kSmallWarps][3 * kTopBins * kBinWords];
+  __shared__ uint4 s_stack[kSmallWarps][kTopSmall];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t* bins = s_bins[warp];
+  const uint32_t C = a.ctr[kCtrClusters];
+  if (C < 2 || (a.misc[6] & kErrTopBuild)) return;
+  if (a.ctr[kCtrMarked] + 2u != C) {   // the marked top part and the clusters disagree: leave the LBVH as it is
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.misc[6], kErrTopBuild);
+    return;
+  }
+  const uint32_t n_nodes = C - 1, n_small = min(a.ctr[kCtrSmall], n_nodes);
+  while (true) {
+    uint32_t si = 0;
+    if (lane == 0) si = atomicAdd(&a.ctr[kCtrSmallHead], 1u);
+    si = __shfl_sync(0xFFFFFFFFu, si, 0);
+    if (si >= n_small) return;
+    const uint4 t = a.small[si];
+    const uint32_t n = t.y - t.x;
+    if (n < 2u || n > kTopSmall) {   // cannot happen: only such tasks are listed
+      if (lane == 0) atomicOr(&a.misc[6], kErrTopBuild);
+      return;
+    }
+    const bool mine = (uint32_t)lane < n;
+    const uint32_t c = mine ? __ldcg(a.order[t.w >> 31] + t.x + lane) : 0u;
+    const float4 lo = mine ? __ldg(&a.rec[2 * (size_t)c]) : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+    const float4 hi = mine ? __ldg(&a.rec[2 * (size_t)c + 1]) : make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+    const float3 cc = cl_centroid(lo, hi);
+    const uint32_t w = __float_as_uint(lo.w), my_ref = __float_as_uint(hi.w);
+    if (lane == 0) s_stack[warp][0] = make_uint4(n == 32u ? 0xFFFFFFFFu : (1u << n) - 1u, t.z, t.w & 0x7FFFFFFFu, 0u);
+    int sp = 1;
+    __syncwarp();
+    while (sp > 0) {
+      const uint4 e = s_stack[warp][--sp];
+      __syncwarp();
+      const uint32_t mask = e.x, slot = e.y, depth = e.z;
+      const bool in = mask >> lane & 1u;
+      const uint32_t n_s = __popc(mask);
+      float mn[3], mx[3];
+      for (int k = 0; k < 3; ++k) {
+        mn[k] = in ? comp(cc, k) : INFINITY;
+        mx[k] = in ? comp(cc, k) : -INFINITY;
+        for (int off = 16; off > 0; off >>= 1) {
+          mn[k] = fminf(mn[k], __shfl_xor_sync(0xFFFFFFFFu, mn[k], off));
+          mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xFFFFFFFFu, mx[k], off));
+        }
+      }
+      float scale[3];
+      bool axis_ok[3];
+      for (int k = 0; k < 3; ++k) {
+        const float ext = __fsub_rn(mx[k], mn[k]);
+        axis_ok[k] = ext > 0.0f && depth < kTopMedianDepth;
+        scale[k] = axis_ok[k] ? __fdiv_rn((float)kTopBins, ext) : 0.0f;
+      }
+      bins_clear(bins, lane, 32);
+      __syncwarp();
+      if (in)
+        for (int k = 0; k < 3; ++k)
+          if (axis_ok[k]) bins_add(bins, k, top_bin(comp(cc, k), mn[k], scale[k]), w, lo, hi);
+      __syncwarp();
+      int axis = -1, split = 0;
+      Split best;
+      best.valid = false;
+      best.cost = 0.0f;
+      best.q = 0;
+      best.nl = 0u;
+      for (int k = 0; k < 3; ++k) {
+        if (!axis_ok[k]) continue;
+        const Split r = warp_best_split(bins + kBinWords * kTopBins * k, lane);
+        if (r.valid && (axis < 0 || r.cost < best.cost)) {
+          axis = k;
+          best = r;
+        }
+      }
+      uint32_t nl = n_s / 2u;
+      if (axis >= 0) {
+        split = best.q;
+        nl = best.nl;
+      }
+      const bool left = in && (axis >= 0 ? top_bin(comp(cc, axis), mn[axis], scale[axis]) < split
+                                         : (uint32_t)__popc(mask & lt) < nl);
+      const uint32_t lmask = __ballot_sync(0xFFFFFFFFu, left), rmask = mask & ~lmask;
+      if ((uint32_t)__popc(lmask) != nl || lmask == 0u || rmask == 0u) {   // cannot happen: same classification
+        if (lane == 0) atomicOr(&a.misc[6], kErrTopBuild);
+        return;
+      }
+      uint32_t eb[2][6];
+      uint32_t ref[2];
+      bool fail = false;
+      for (int side = 0; side < 2; ++side) {
+        const uint32_t m = side ? rmask : lmask;
+        const bool on = m >> lane & 1u;
+        float v[6] = {on ? lo.x : INFINITY, on ? lo.y : INFINITY, on ? lo.z : INFINITY,
+                      on ? hi.x : -INFINITY, on ? hi.y : -INFINITY, on ? hi.z : -INFINITY};
+        for (int off = 16; off > 0; off >>= 1)
+          for (int q = 0; q < 6; ++q) {
+            const float o = __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+            v[q] = q < 3 ? fminf(v[q], o) : fmaxf(v[q], o);
+          }
+        for (int q = 0; q < 6; ++q) eb[side][q] = enc_f(v[q]);
+        if (__popc(m) == 1) {
+          ref[side] = __shfl_sync(0xFFFFFFFFu, my_ref, __ffs(m) - 1);
+        } else {
+          uint32_t sl = 0;
+          if (lane == 0) {
+            const uint32_t si2 = 1u + atomicAdd(&a.ctr[kCtrSlots], 1u);
+            sl = si2 < n_nodes ? a.slot[si2] : kNone;
+          }
+          sl = __shfl_sync(0xFFFFFFFFu, sl, 0);
+          if (sl == kNone || sp >= (int)kTopSmall) {   // cannot happen for a consistent marking
+            fail = true;
+            break;
+          }
+          ref[side] = sl;
+          if (lane == 0) s_stack[warp][sp] = make_uint4(m, sl, depth + 1u, 0u);
+          ++sp;
+        }
+      }
+      if (fail) {
+        if (lane == 0) atomicOr(&a.misc[6], kErrTopBuild);
+        return;
+      }
+      if (lane == 0) write_top_node(a, slot, eb, ref);
+      __syncwarp();
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -442,20 +1133,6 @@ __global__ void k_wide_cut(uint32_t n, const uint32_t* __restrict__ child, const
   uint4* o = reinterpret_cast<uint4*>(cut + 8 * (size_t)b);
   o[0] = make_uint4(out[0], out[1], out[2], out[3]);
   o[1] = make_uint4(out[4], out[5], out[6], out[7]);
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // members of the cut of binary node b in slot order (kNone: empty slot); a
@@ -773,6 +1450,8 @@ cudaError_t build_alloc(rr_scene* s) {
   RR_TRY(alloc((void**)&s->d_nbox, (T ? 2 * T - 1 : 1) * 6 * sizeof(float)));
   RR_TRY(alloc((void**)&s->d_visit, (T > 1 ? T - 1 : 1) * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_misc, 8 * sizeof(uint32_t)));
+  RR_TRY(cudaMemset(s->d_misc, 0, 8 * sizeof(uint32_t)));   // status of an empty scene: no error
+  RR_TRY(alloc((void**)&s->d_range, (T > 1 ? T - 1 : 1) * sizeof(uint2)));
   // wide BVH: at most T - 1 wide nodes (each owns a distinct binary internal node)
   s->wcap = T > 1 ? (uint32_t)(T - 1) : 1u;
   if (T) {
@@ -802,15 +1481,88 @@ cudaError_t build_materials(rr_scene* s, cudaStream_t st) {
   return cudaStreamSynchronize(st);   // the host copy of the kinds must outlive the upload
 }
 
+// buffers of the SAH top, allocated with the first build that uses it
+static cudaError_t top_alloc(rr_scene* s) {
+  if (s->d_top_ctr) return cudaSuccess;
+  const size_t T = s->nt;
+  s->cl_blocks = (uint32_t)((T + kClTile - 1) / kClTile);
+  const size_t nb4 = (s->cl_blocks + 3u) & ~3u;
+  size_t bytes = 0;
+  auto alloc = [&](void** p, size_t n) -> cudaError_t {
+    bytes += n;
+    return cudaMalloc(p, n);
+  };
+  RR_TRY(alloc((void**)&s->d_cl_at, T * sizeof(uint32_t)));
+  RR_TRY(alloc((void**)&s->d_cl_bsum, nb4 * sizeof(uint32_t)));
+  RR_TRY(alloc((void**)&s->d_cl_rec, T * 2 * sizeof(float4)));
+  RR_TRY(alloc((void**)&s->d_cl_idx, 2 * T * sizeof(uint32_t)));
+  RR_TRY(alloc((void**)&s->d_top_slot, T * sizeof(uint32_t)));
+  RR_TRY(alloc((void**)&s->d_top_task, T * sizeof(uint4)));
+  RR_TRY(alloc((void**)&s->d_top_ready, T * sizeof(uint32_t)));
+  RR_TRY(alloc((void**)&s->d_top_small, T * sizeof(uint4)));
+  RR_TRY(alloc((void**)&s->d_top_ctr, 8 * sizeof(uint32_t)));
+  s->scene_bytes += bytes;
+  return cudaSuccess;
+}
+
+// a5b on the refitted LBVH (more than kClusterMax triangles)
+static cudaError_t build_sah_top(rr_scene* s, cudaStream_t st) {
+  const uint32_t n = s->nt;
+  RR_TRY(top_alloc(s));
+  const uint32_t nb4 = (s->cl_blocks + 3u) & ~3u;
+  RR_TRY(cudaMemsetAsync(s->d_cl_at, 0xFF, (size_t)n * sizeof(uint32_t), st));
+  RR_TRY(cudaMemsetAsync(s->d_cl_bsum, 0, (size_t)nb4 * sizeof(uint32_t), st));
+  RR_TRY(cudaMemsetAsync(s->d_top_ready, 0, (size_t)n * sizeof(uint32_t), st));
+  RR_TRY(cudaMemsetAsync(s->d_top_ctr, 0, 8 * sizeof(uint32_t), st));
+  k_top_mark<<<(n - 1 + 255) / 256, 256, 0, st>>>(n, s->d_child, s->d_range, s->d_cl_at, s->d_top_slot, s->d_top_ctr);
+  RR_TRY(cudaGetLastError());
+  k_top_count<<<s->cl_blocks, 256, 0, st>>>(n, s->d_cl_at, s->d_cl_bsum);
+  RR_TRY(cudaGetLastError());
+  k_scan_single<<<1, 1024, 0, st>>>(s->d_cl_bsum, nb4);
+  RR_TRY(cudaGetLastError());
+  k_top_compact<<<s->cl_blocks, 256, 0, st>>>(n, s->d_cl_at, s->d_cl_bsum, s->d_range, s->d_nbox, s->d_cl_rec,
+                                               s->d_cl_idx, s->d_top_task, s->d_top_ready, s->d_top_small,
+                                               s->d_top_ctr);
+  RR_TRY(cudaGetLastError());
+  TopArgs a;
+  a.rec = s->d_cl_rec;
+  a.order[0] = s->d_cl_idx;
+  a.order[1] = s->d_cl_idx + n;
+  a.slot = s->d_top_slot;
+  a.task = s->d_top_task;
+  a.ready = s->d_top_ready;
+  a.small = s->d_top_small;
+  a.ctr = s->d_top_ctr;
+  a.nodes = s->d_nodes;
+  a.child = s->d_child;
+  a.parent = s->d_parent;
+  a.nbox = s->d_nbox;
+  a.misc = s->d_misc;
+  a.n = n;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  // persistent blocks; a block that finds no task left returns at once
+  k_top_sah<<<std::min<uint32_t>((uint32_t)sms * 4u, n / 64u + 1u), kTopBlock, 0, st>>>(a);
+  RR_TRY(cudaGetLastError());
+  k_top_small<<<std::min<uint32_t>((uint32_t)sms * 4u, n / 256u + 1u), 32 * kSmallWarps, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth) {
   const uint32_t n = s->nt;
-  if (n == 0) return cudaSuccess;
   // bounds reset: min slots to all ones, max slots, error and depth to zero
   RR_TRY(cudaMemsetAsync(s->d_misc, 0xFF, 3 * sizeof(uint32_t), st));
   RR_TRY(cudaMemsetAsync(s->d_misc + 3, 0, 5 * sizeof(uint32_t), st));
+  if (n == 0) return cudaSuccess;
   const int B = 256;
   const uint32_t g = (n + B - 1) / B;
-  s->launches += (n > 1) ? (with_depth ? 18u : 17u) : 15u;
+  const bool sah_top = s->cfg.bvh_build == RR_BVH_SAH_TOP && n > kClusterMax;
+  s->launches += ((n > 1) ? (with_depth ? 18u : 17u) : 15u) + (sah_top ? 6u : 0u);
   k_ingest<<<g, B, 0, st>>>(s->d_vtx, s->d_idx, s->d_mat_id, s->nv, n, s->nm, s->d_centroid, s->d_misc);
   RR_TRY(cudaGetLastError());
   k_morton<<<g, B, 0, st>>>(s->d_centroid, s->d_misc, n, s->d_keys[0], s->d_vals[0]);
@@ -832,10 +1584,12 @@ cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth) {
   k_gather<<<g, B, 0, st>>>(s->d_vtx, s->d_idx, s->d_mat_id, s->d_vals[cur], s->nv, n, s->d_tri, s->d_nbox);
   RR_TRY(cudaGetLastError());
   if (n > 1) {
-    k_karras<<<(n - 1 + B - 1) / B, B, 0, st>>>(s->d_keys[cur], (int)n, s->d_child, s->d_parent, s->d_visit);
+    k_karras<<<(n - 1 + B - 1) / B, B, 0, st>>>(s->d_keys[cur], (int)n, s->d_child, s->d_parent, s->d_visit,
+                                                s->d_range);
     RR_TRY(cudaGetLastError());
     k_refit<<<g, B, 0, st>>>(n, s->d_child, s->d_parent, s->d_visit, s->d_nbox, s->d_nodes);
     RR_TRY(cudaGetLastError());
+    if (sah_top) RR_TRY(build_sah_top(s, st));
     if (with_depth) {
       // the stack bound is checked once at creation; on rebuilds the
       // traversal's own stack check reports a deeper tree

@@ -32,6 +32,7 @@ struct LaunchCfg {
   uint32_t refill = 8;                // idle lanes that trigger a refill (1..32)
   uint32_t split = 3;                 // a single scan as this many azimuth ranges on their own streams
   uint64_t ws_limit = uint64_t(24) << 30;
+  uint32_t bvh_build = RR_BVH_SAH_TOP;
 };
 
 constexpr uint32_t kMaxSplit = 4;
@@ -105,6 +106,18 @@ struct rr_scene {
   float* d_nbox = nullptr;         // [2T-1][6]
   uint32_t* d_visit = nullptr;     // [T-1]
   uint32_t* d_misc = nullptr;      // [8]: bounds (6, encoded), error bits, depth
+  uint2* d_range = nullptr;        // [T-1] leaf range (first, last) of every internal node
+  // SAH top over the LBVH's subtrees (allocated with the first such build)
+  uint32_t* d_cl_at = nullptr;     // [T] cluster root reference at the cluster's first leaf, else kNone
+  uint32_t* d_cl_bsum = nullptr;   // [cl_blocks rounded up to 4] clusters per compaction block, then offsets
+  float4* d_cl_rec = nullptr;      // [T][2] cluster (lo xyz, weight) (hi xyz, root reference)
+  uint32_t* d_cl_idx = nullptr;    // [2][T] cluster order of the top-down build (ping-pong)
+  uint32_t* d_top_slot = nullptr;  // [T] node slots of the LBVH's top part (root first)
+  uint4* d_top_task = nullptr;     // [T] block tasks (first, end, node slot, depth | source << 31)
+  uint32_t* d_top_ready = nullptr; // [T] block task published
+  uint4* d_top_small = nullptr;    // [T] warp tasks, same fields
+  uint32_t* d_top_ctr = nullptr;   // [8] counters of the build
+  uint32_t cl_blocks = 0;
   uint32_t sort_tiles = 0;
   uint32_t depth = 0;
   float build_ms = 0.f;
@@ -149,6 +162,9 @@ cudaError_t launch_shade(const rr::ScanArgs& a, uint32_t bounce, cudaStream_t st
 void init_image_attrs();
 cudaError_t launch_image(const rr::ScanArgs& a, bool pattern, cudaStream_t st);
 cudaError_t launch_db_u8(const float* polar, uint64_t n, float cutoff_db, uint8_t* out, cudaStream_t st);
+
+// rebuild with the scene's configuration, wait, check status and depth (rr_api.cu)
+int rebuild_bvh(rr_scene* s, cudaStream_t st);
 
 // profiling helpers (rr_api.cu)
 void prof_begin(rr_scene* s, int kind, cudaStream_t st, cudaEvent_t* stop_out);

@@ -29,6 +29,7 @@ constexpr uint32_t kErrCapacitySegs = 8u;
 constexpr uint32_t kErrBadVertex = 16u;
 constexpr uint32_t kErrStack = 32u;
 constexpr uint32_t kErrBvh = 64u;      // the BVH build failed (traversal refused)
+constexpr uint32_t kErrTopBuild = 0x100u;   // build status word: the SAH top build was abandoned
 
 // ---------------------------------------------------------------------------
 // device material record (derived at scene creation)
@@ -121,6 +122,7 @@ struct ScanArgs {
   uint32_t wide;             // nodes are 8-wide quantised (tri in wide-leaf order), else binary
   uint32_t node_cap;         // nodes in the node array (traversal bound)
   const uint32_t* bvh_status;   // non-zero: the last build failed, nothing may be traced
+  const uint32_t* build_status; // the scene's build status word (kErrTopBuild: nothing may be traced)
   // batch
   const ScanDesc* desc;      // [n_scans]
   const uint32_t* ray0;      // [n_scans + 1] prefix of n_az * ns

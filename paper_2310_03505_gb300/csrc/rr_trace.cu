@@ -239,7 +239,13 @@ __device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const Scan
   const uint32_t node = s.node;
   if (!(node & kLeafBit)) {
     if (count) ++n_nodes;
-    ++s.visits;
+    // depth-first traversal of a tree visits each of its n_tris - 1 internal
+    // nodes at most once: more visits mean a malformed hierarchy
+    if (++s.visits > a.n_tris) {
+      atomicOr(&a.ctr->error, kErrBvh);
+      s.node = kNone;
+      return;
+    }
     const float3 o = s.w.o, id = s.id;
     const float4* np = a.nodes + 4 * (size_t)node;
     const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
@@ -323,7 +329,11 @@ __device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs&
       return;
     }
     if (count) ++n_nodes;
-    ++s.visits;
+    if (++s.visits > a.n_tris) {   // more visits than wide nodes: a malformed hierarchy
+      atomicOr(&a.ctr->error, kErrBvh);
+      s.node = kNone;
+      return;
+    }
     const float3 o = s.w.o, id = s.id;
     const bool neg_x = id.x < 0.0f, neg_y = id.y < 0.0f, neg_z = id.z < 0.0f;
     const uint4* np = reinterpret_cast<const uint4*>(a.nodes) + kWideNodeWords * (size_t)node;
@@ -396,7 +406,8 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
   const RayRec* __restrict__ q = a.rays[bounce & 1];
   const uint2* __restrict__ jobs = reinterpret_cast<const uint2*>(a.rays[(bounce + 1) & 1]);
   // after a failed build every query ends at once as a miss and the scan fails
-  const bool bvh_ok = a.bvh_status == nullptr || *a.bvh_status == 0u;
+  const bool bvh_ok = (a.bvh_status == nullptr || *a.bvh_status == 0u) &&
+                      (a.build_status == nullptr || (*a.build_status & kErrTopBuild) == 0u);
   if (!bvh_ok && gtid == 0) atomicOr(&C->error, kErrBvh);
   const bool count = (a.any_flags & RR_COUNT_TRAVERSAL) != 0u;
   const int lane = threadIdx.x & 31;

@@ -122,4 +122,6 @@ def test_invalid_config_and_params(lib):
     with pytest.raises(rr.RRError):
         rr.rr_batch_plan([params()], dict(workspace_limit=1000))
     with pytest.raises(rr.RRError):
+        rr.rr_batch_plan([params()], dict(bvh_build=2))
+    with pytest.raises(rr.RRError):
         rr.rr_batch_plan([params(), params(bins=0)])
