@@ -262,8 +262,8 @@ int rr_scene_destroy(rr_scene* s) {
                   s->d_tri, s->d_nodes, s->d_centroid, s->d_keys[0], s->d_keys[1], s->d_vals[0], s->d_vals[1],
                   s->d_hist, s->d_parent, s->d_child, s->d_nbox, s->d_visit, s->d_misc,
                   s->d_cut, s->d_wnodes, s->d_wtri, s->d_wsrc, s->d_wrec, s->d_wctr, s->d_lobe_kind,
-                  s->d_lobe_samples, s->d_range, s->d_cl_at, s->d_cl_bsum, s->d_cl_rec, s->d_cl_idx,
-                  s->d_top_slot, s->d_top_task, s->d_top_ready, s->d_top_small, s->d_top_ctr};
+                  s->d_lobe_samples, s->d_range, s->d_cl_at, s->d_cl_bsum, s->d_cl_rec,
+                  s->d_top_slot, s->d_top_task, s->d_top_ready, s->d_top_small, s->d_top_ctr, s->d_top_cb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ctx_free(&s->main);

@@ -410,13 +410,21 @@ constexpr int kCtrSmallHead = 7;  // next warp task to take
 // kClusterMax leaves; a child of a top node with at most kClusterMax leaves
 // is a cluster root, recorded at its first leaf
 __global__ void k_top_mark(uint32_t n, const uint32_t* __restrict__ child, const uint2* __restrict__ range,
-                           uint32_t* __restrict__ cl_at, uint32_t* __restrict__ slot, uint32_t* __restrict__ ctr) {
+                           uint32_t* __restrict__ cl_at, uint32_t* __restrict__ slot, uint32_t* __restrict__ ctr,
+                           uint32_t* __restrict__ cb) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i + 1 >= n) return;
   const uint2 r = range[i];
   if (r.y - r.x + 1u <= kClusterMax) return;
-  if (i == 0) slot[0] = 0u;
-  else slot[1u + atomicAdd(&ctr[kCtrMarked], 1u)] = i;
+  if (i == 0) {
+    slot[0] = 0u;
+    for (int k = 0; k < 3; ++k) {   // the root task's centroid bounds, filled by k_top_compact
+      cb[k] = 0xFF800000u;          // enc_f(+inf)
+      cb[3 + k] = 0x007FFFFFu;      // enc_f(-inf)
+    }
+  } else {
+    slot[1u + atomicAdd(&ctr[kCtrMarked], 1u)] = i;
+  }
   for (int k = 0; k < 2; ++k) {
     const uint32_t c = child[2 * i + k];
     uint32_t first, size;
@@ -450,14 +458,14 @@ __global__ void __launch_bounds__(256) k_top_count(uint32_t n, const uint32_t* _
   }
 }
 
-// clusters in leaf order (bsum holds the exclusive block offsets): record,
-// starting order, and the root task over all of them
+// clusters in leaf order (bsum holds the exclusive block offsets): their
+// records, and the root task over all of them
 __global__ void __launch_bounds__(256) k_top_compact(uint32_t n, const uint32_t* __restrict__ cl_at,
                                                      const uint32_t* __restrict__ bsum, const uint2* __restrict__ range,
                                                      const float* __restrict__ nbox, float4* __restrict__ rec,
-                                                     uint32_t* __restrict__ order, uint4* __restrict__ task,
+                                                     uint4* __restrict__ task,
                                                      uint32_t* __restrict__ ready, uint4* __restrict__ small,
-                                                     uint32_t* __restrict__ ctr) {
+                                                     uint32_t* __restrict__ ctr, uint32_t* __restrict__ cb) {
   __shared__ uint32_t s_w[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t base = blockIdx.x * kClTile + threadIdx.x * 8u;
@@ -473,6 +481,7 @@ __global__ void __launch_bounds__(256) k_top_compact(uint32_t n, const uint32_t*
   __syncthreads();
   uint32_t pos = bsum[blockIdx.x] + x - c;
   for (int w = 0; w < warp; ++w) pos += s_w[w];
+  float cmn[3] = {INFINITY, INFINITY, INFINITY}, cmx[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (uint32_t k = 0; k < 8; ++k) {
     const uint32_t j = base + k;
     if (j >= n) break;
@@ -487,7 +496,11 @@ __global__ void __launch_bounds__(256) k_top_compact(uint32_t n, const uint32_t*
       }
       rec[2 * (size_t)pos] = make_float4(b[0], b[1], b[2], __uint_as_float(weight));
       rec[2 * (size_t)pos + 1] = make_float4(b[3], b[4], b[5], __uint_as_float(ref));
-      order[pos] = pos;
+      for (int q = 0; q < 3; ++q) {
+        const float c = __fmul_rn(0.5f, __fadd_rn(b[q], b[3 + q]));
+        cmn[q] = fminf(cmn[q], c);
+        cmx[q] = fmaxf(cmx[q], c);
+      }
       ++pos;
     }
     if (j == n - 1) {   // the last leaf: pos is now the number of clusters
@@ -503,16 +516,26 @@ __global__ void __launch_bounds__(256) k_top_compact(uint32_t n, const uint32_t*
       }
     }
   }
+  for (int q = 0; q < 3; ++q)
+    for (int off = 16; off > 0; off >>= 1) {
+      cmn[q] = fminf(cmn[q], __shfl_xor_sync(0xFFFFFFFFu, cmn[q], off));
+      cmx[q] = fmaxf(cmx[q], __shfl_xor_sync(0xFFFFFFFFu, cmx[q], off));
+    }
+  if (lane == 0 && cmn[0] <= cmx[0])
+    for (int q = 0; q < 3; ++q) {
+      atomicMin(&cb[q], enc_f(cmn[q]));
+      atomicMax(&cb[3 + q], enc_f(cmx[q]));
+    }
 }
 
 struct TopArgs {
-  const float4* rec;      // [C][2]
-  uint32_t* order[2];     // ping-pong cluster orders
+  float4* rec[2];         // [C][2] cluster records, ping-pong between a task and its children
   const uint32_t* slot;   // [C - 1] node slots of the top part, root first
   uint4* task;            // [C - 1] block tasks (more than kTopSmall clusters)
   uint32_t* ready;        // [C - 1] block task published
   uint4* small;           // [C - 1] warp tasks (2 to kTopSmall clusters)
   uint32_t* ctr;          // kCtr*
+  uint32_t* cb;           // [T - 1][6] centroid bounds (encoded) of the block task at each node slot
   float4* nodes;
   uint32_t* child;
   uint32_t* parent;
@@ -536,6 +559,7 @@ __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (
 
 constexpr uint32_t kEncPosInf = 0xFF800000u, kEncNegInf = 0x007FFFFFu;   // enc_f(+inf), enc_f(-inf)
 constexpr int kBinWords = 8;   // per bin: clusters, weight, lo xyz, hi xyz (encoded)
+constexpr int kTopItems = 4;   // records per thread per round of a block pass
 
 __device__ __forceinline__ void bins_clear(uint32_t* bins, int i0, int stride) {
   for (int i = i0; i < 3 * kTopBins; i += stride) {
@@ -546,18 +570,6 @@ __device__ __forceinline__ void bins_clear(uint32_t* bins, int i0, int stride) {
     q[5] = q[6] = q[7] = kEncNegInf;
   }
 }
-__device__ __forceinline__ void bins_add(uint32_t* bins, int k, int q, uint32_t w, float4 lo, float4 hi) {
-  uint32_t* b = bins + kBinWords * (k * kTopBins + q);
-  atomicAdd(&b[0], 1u);
-  atomicAdd(&b[1], w);
-  atomicMin(&b[2], enc_f(lo.x));
-  atomicMin(&b[3], enc_f(lo.y));
-  atomicMin(&b[4], enc_f(lo.z));
-  atomicMax(&b[5], enc_f(hi.x));
-  atomicMax(&b[6], enc_f(hi.y));
-  atomicMax(&b[7], enc_f(hi.z));
-}
-
 struct Split {
   bool valid;
   float cost;
@@ -631,12 +643,9 @@ __device__ Split warp_best_split(const uint32_t* bins, int lane) {
   return r;
 }
 
-// the node of a task: child boxes (encoded lo xyz, hi xyz) and references
-__device__ __forceinline__ void write_top_node(const TopArgs& a, uint32_t slot, const uint32_t (&eb)[2][6],
+// the node of a task: child boxes (lo xyz, hi xyz) and references
+__device__ __forceinline__ void write_top_node(const TopArgs& a, uint32_t slot, const float (&bx)[2][6],
                                                const uint32_t (&ref)[2]) {
-  float bx[2][6];
-  for (int side = 0; side < 2; ++side)
-    for (int q = 0; q < 6; ++q) bx[side][q] = dec_f(eb[side][q]);
   float4* nd = a.nodes + 4 * (size_t)slot;
   nd[0] = make_float4(bx[0][0], bx[0][3], bx[0][1], bx[0][4]);
   nd[1] = make_float4(bx[1][0], bx[1][3], bx[1][1], bx[1][4]);
@@ -658,12 +667,15 @@ __device__ __forceinline__ void write_top_node(const TopArgs& a, uint32_t slot, 
 // working on its parent, which took a smaller number earlier and is running;
 // so the smallest number any block waits for belongs to a parent in
 // progress, and every wait ends -- with the task, or with the count of
-// pending tasks at zero when no task of that number will come.  Children of
-// at most kTopSmall clusters go to the warp-task list.
+// pending tasks at zero when no task of that number will come.  A block
+// goes on with one large child itself (no number, no wait; it stays counted
+// as pending), publishes the other; children of at most kTopSmall clusters
+// go to the warp-task list.  The cluster records move with the partition, so
+// every pass reads its task's records contiguously, kTopItems per thread.
 __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
   __shared__ uint32_t s_bins[3 * kTopBins * kBinWords];
-  __shared__ uint32_t s_cb[6], s_side[2][6];
-  __shared__ uint32_t s_task[4], s_stop;
+  __shared__ uint32_t s_cb[6], s_side[2][6], s_cside[2][6];
+  __shared__ uint32_t s_task[4], s_stop, s_cont;
   __shared__ Split s_split[3];
   __shared__ uint32_t s_wl[kTopBlock / 32], s_wr[kTopBlock / 32], s_base[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -674,20 +686,30 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
     if (blockIdx.x == 0 && tid == 0) atomicOr(&a.misc[6], kErrTopBuild);
     return;
   }
+  if (tid == 0) s_cont = 0u;
+  __syncthreads();
   while (true) {
-    if (tid == 0) {
+    if (tid == 0 && !s_cont) {
       s_stop = 0u;
       const uint32_t ti = atomicAdd(&a.ctr[kCtrHead], 1u);
       if (ti >= n_nodes) {
         s_stop = 1u;
       } else {
+        // poll the own flag; the shared counters only now and then, so that
+        // waiting blocks do not crowd the lines the working blocks update
         uint32_t spins = 0, nap = 32;
         while (ld_acquire_u32(&a.ready[ti]) == 0u) {
-          if (ld_acquire_u32(&a.ctr[kCtrPending]) == 0u) {   // all tasks done: none numbered ti will come
-            s_stop = 1u;
-            break;
+          if ((spins & 15u) == 15u) {
+            if (ld_acquire_u32(&a.ctr[kCtrPending]) == 0u) {   // all tasks done: none numbered ti will come
+              s_stop = 1u;
+              break;
+            }
+            if (ld_acquire_u32(&a.misc[6]) & kErrTopBuild) {
+              s_stop = 1u;
+              break;
+            }
           }
-          if (++spins > kTopSpinLimit || (ld_acquire_u32(&a.misc[6]) & kErrTopBuild)) {
+          if (++spins > kTopSpinLimit) {
             atomicOr(&a.misc[6], kErrTopBuild);
             s_stop = 1u;
             break;
@@ -704,42 +726,20 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
         }
       }
     }
+    if (tid == 0 && (s_cont || !s_stop))
+      for (int q = 0; q < 6; ++q) s_cb[q] = __ldcg(&a.cb[6 * (size_t)s_task[2] + q]);
     __syncthreads();
-    if (s_stop) return;
+    if (!s_cont && s_stop) return;
     const uint32_t b = s_task[0], n = s_task[1] - s_task[0], slot = s_task[2];
     const uint32_t depth = s_task[3] & 0x7FFFFFFFu, src = s_task[3] >> 31;
-    const uint32_t* in = a.order[src] + b;
-    uint32_t* out = a.order[src ^ 1u] + b;
+    const float4* in = a.rec[src] + 2 * (size_t)b;
+    float4* out = a.rec[src ^ 1u] + 2 * (size_t)b;
     bins_clear(s_bins, tid, kTopBlock);
     if (tid < 6) {
-      s_cb[tid] = tid < 3 ? kEncPosInf : kEncNegInf;
-      s_side[0][tid] = tid < 3 ? kEncPosInf : kEncNegInf;
-      s_side[1][tid] = tid < 3 ? kEncPosInf : kEncNegInf;
+      s_side[0][tid] = s_cside[0][tid] = tid < 3 ? kEncPosInf : kEncNegInf;
+      s_side[1][tid] = s_cside[1][tid] = tid < 3 ? kEncPosInf : kEncNegInf;
     }
     if (tid < 2) s_base[tid] = 0u;
-    __syncthreads();
-    // centroid bounds
-    {
-      float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-      for (uint32_t i = tid; i < n; i += kTopBlock) {
-        const uint32_t c = __ldcg(in + i);
-        const float3 cc = cl_centroid(__ldg(&a.rec[2 * (size_t)c]), __ldg(&a.rec[2 * (size_t)c + 1]));
-        for (int k = 0; k < 3; ++k) {
-          mn[k] = fminf(mn[k], comp(cc, k));
-          mx[k] = fmaxf(mx[k], comp(cc, k));
-        }
-      }
-      for (int k = 0; k < 3; ++k)
-        for (int off = 16; off > 0; off >>= 1) {
-          mn[k] = fminf(mn[k], __shfl_xor_sync(0xFFFFFFFFu, mn[k], off));
-          mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xFFFFFFFFu, mx[k], off));
-        }
-      if (lane == 0)
-        for (int k = 0; k < 3; ++k) {
-          atomicMin(&s_cb[k], enc_f(mn[k]));
-          atomicMax(&s_cb[3 + k], enc_f(mx[k]));
-        }
-    }
     __syncthreads();
     float cmin[3], scale[3];
     bool axis_ok[3];
@@ -749,14 +749,71 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
       axis_ok[k] = ext > 0.0f && depth < kTopMedianDepth;
       scale[k] = axis_ok[k] ? __fdiv_rn((float)kTopBins, ext) : 0.0f;
     }
+    // bins: each thread takes a contiguous chunk of the task (Morton order,
+    // so neighbours mostly share bins) and adds runs of one bin at a time
     if (axis_ok[0] || axis_ok[1] || axis_ok[2]) {
-      for (uint32_t i = tid; i < n; i += kTopBlock) {
-        const uint32_t c = __ldcg(in + i);
-        const float4 lo = __ldg(&a.rec[2 * (size_t)c]), hi = __ldg(&a.rec[2 * (size_t)c + 1]);
+      const uint32_t chunk = (n + kTopBlock - 1) / kTopBlock;
+      const uint32_t i0 = min(n, chunk * tid), i1 = min(n, i0 + chunk);
+      int run_q[3] = {-1, -1, -1};
+      uint32_t run_n[3] = {0u, 0u, 0u}, run_w[3] = {0u, 0u, 0u};
+      float run_b[3][6];
+      for (uint32_t ib = i0; ib < i1; ib += kTopItems) {
+        float4 blo[kTopItems], bhi[kTopItems];
+#pragma unroll
+        for (int k = 0; k < kTopItems; ++k)
+          if (ib + k < i1) {
+            blo[k] = __ldcg(in + 2 * (ib + k));
+            bhi[k] = __ldcg(in + 2 * (ib + k) + 1);
+          }
+#pragma unroll
+        for (int k = 0; k < kTopItems; ++k) {
+        if (ib + k >= i1) break;
+        const float4 lo = blo[k], hi = bhi[k];
         const float3 cc = cl_centroid(lo, hi);
-        for (int k = 0; k < 3; ++k)
-          if (axis_ok[k]) bins_add(s_bins, k, top_bin(comp(cc, k), cmin[k], scale[k]), __float_as_uint(lo.w), lo, hi);
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          if (!axis_ok[ax]) continue;
+          const int q = top_bin(comp(cc, ax), cmin[ax], scale[ax]);
+          if (q != run_q[ax]) {
+            if (run_q[ax] >= 0) {
+              uint32_t* bb = s_bins + kBinWords * (ax * kTopBins + run_q[ax]);
+              atomicAdd(&bb[0], run_n[ax]);
+              atomicAdd(&bb[1], run_w[ax]);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                atomicMin(&bb[2 + c], enc_f(run_b[ax][c]));
+                atomicMax(&bb[5 + c], enc_f(run_b[ax][3 + c]));
+              }
+            }
+            run_q[ax] = q;
+            run_n[ax] = 0u;
+            run_w[ax] = 0u;
+            run_b[ax][0] = run_b[ax][1] = run_b[ax][2] = INFINITY;
+            run_b[ax][3] = run_b[ax][4] = run_b[ax][5] = -INFINITY;
+          }
+          ++run_n[ax];
+          run_w[ax] += __float_as_uint(lo.w);
+          run_b[ax][0] = fminf(run_b[ax][0], lo.x);
+          run_b[ax][1] = fminf(run_b[ax][1], lo.y);
+          run_b[ax][2] = fminf(run_b[ax][2], lo.z);
+          run_b[ax][3] = fmaxf(run_b[ax][3], hi.x);
+          run_b[ax][4] = fmaxf(run_b[ax][4], hi.y);
+          run_b[ax][5] = fmaxf(run_b[ax][5], hi.z);
+        }
+        }
       }
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax)
+        if (run_q[ax] >= 0) {
+          uint32_t* bb = s_bins + kBinWords * (ax * kTopBins + run_q[ax]);
+          atomicAdd(&bb[0], run_n[ax]);
+          atomicAdd(&bb[1], run_w[ax]);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            atomicMin(&bb[2 + c], enc_f(run_b[ax][c]));
+            atomicMax(&bb[5 + c], enc_f(run_b[ax][3 + c]));
+          }
+        }
     }
     __syncthreads();
     if (warp < 3) {
@@ -774,45 +831,78 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
       split = s_split[axis].q;
       nl = s_split[axis].nl;
     }
-    // stable partition into the other order buffer, 8 clusters per thread per round
-    for (uint32_t t0 = 0; t0 < n; t0 += 8u * kTopBlock) {
-      const uint32_t i0 = t0 + 8u * tid;
-      uint32_t cs[8], lmask = 0u, hmask = 0u;
+    const float a_min = axis == 0 ? cmin[0] : (axis == 1 ? cmin[1] : cmin[2]);
+    const float a_scale = axis == 0 ? scale[0] : (axis == 1 ? scale[1] : scale[2]);
+    // stable partition of the records into the other buffer
+    for (uint32_t t0 = 0; t0 < n; t0 += kTopItems * kTopBlock) {
+      const uint32_t i0 = t0 + kTopItems * tid;
+      float4 lo[kTopItems], hi[kTopItems];
+      uint32_t lmask = 0u, hmask = 0u;
       float v[2][6] = {{INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY},
                        {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY}};
+      float cv[2][6] = {{INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY},
+                        {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY}};
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < kTopItems; ++k)
+        if (i0 + k < n) {
+          lo[k] = __ldcg(in + 2 * (i0 + k));
+          hi[k] = __ldcg(in + 2 * (i0 + k) + 1);
+        }
+#pragma unroll
+      for (int k = 0; k < kTopItems; ++k) {
         const uint32_t i = i0 + k;
-        cs[k] = 0u;
         if (i < n) {
-          const uint32_t c = __ldcg(in + i);
-          const float4 lo = __ldg(&a.rec[2 * (size_t)c]), hi = __ldg(&a.rec[2 * (size_t)c + 1]);
-          const bool left =
-              axis >= 0 ? top_bin(comp(cl_centroid(lo, hi), axis), cmin[axis], scale[axis]) < split : i < nl;
-          cs[k] = c;
+          const float3 cc = cl_centroid(lo[k], hi[k]);
+          const bool left = axis >= 0 ? top_bin(comp(cc, axis), a_min, a_scale) < split : i < nl;
           hmask |= 1u << k;
           if (left) lmask |= 1u << k;
-          const int side = left ? 0 : 1;
-          v[side][0] = fminf(v[side][0], lo.x);
-          v[side][1] = fminf(v[side][1], lo.y);
-          v[side][2] = fminf(v[side][2], lo.z);
-          v[side][3] = fmaxf(v[side][3], hi.x);
-          v[side][4] = fmaxf(v[side][4], hi.y);
-          v[side][5] = fmaxf(v[side][5], hi.z);
+          // both sides' accumulators by select: static indices keep them in registers
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            const bool on = left == (sd == 0);
+            const float inf = INFINITY;
+            v[sd][0] = fminf(v[sd][0], on ? lo[k].x : inf);
+            v[sd][1] = fminf(v[sd][1], on ? lo[k].y : inf);
+            v[sd][2] = fminf(v[sd][2], on ? lo[k].z : inf);
+            v[sd][3] = fmaxf(v[sd][3], on ? hi[k].x : -inf);
+            v[sd][4] = fmaxf(v[sd][4], on ? hi[k].y : -inf);
+            v[sd][5] = fmaxf(v[sd][5], on ? hi[k].z : -inf);
+            cv[sd][0] = fminf(cv[sd][0], on ? cc.x : inf);
+            cv[sd][1] = fminf(cv[sd][1], on ? cc.y : inf);
+            cv[sd][2] = fminf(cv[sd][2], on ? cc.z : inf);
+            cv[sd][3] = fmaxf(cv[sd][3], on ? cc.x : -inf);
+            cv[sd][4] = fmaxf(cv[sd][4], on ? cc.y : -inf);
+            cv[sd][5] = fmaxf(cv[sd][5], on ? cc.z : -inf);
+          }
         }
       }
       const uint32_t cl = __popc(lmask), cr = __popc(hmask & ~lmask);
-      // side boxes
+#pragma unroll
       for (int side = 0; side < 2; ++side) {
+#pragma unroll
         for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
           for (int q = 0; q < 6; ++q) {
             const float o = __shfl_xor_sync(0xFFFFFFFFu, v[side][q], off);
             v[side][q] = q < 3 ? fminf(v[side][q], o) : fmaxf(v[side][q], o);
           }
-        if (lane == 0 && v[side][0] <= v[side][3])
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
           for (int q = 0; q < 6; ++q) {
-            if (q < 3) atomicMin(&s_side[side][q], enc_f(v[side][q]));
-            else atomicMax(&s_side[side][q], enc_f(v[side][q]));
+            const float o = __shfl_xor_sync(0xFFFFFFFFu, cv[side][q], off);
+            cv[side][q] = q < 3 ? fminf(cv[side][q], o) : fmaxf(cv[side][q], o);
+          }
+        if (lane == 0 && v[side][0] <= v[side][3])
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            if (q < 3) {
+              atomicMin(&s_side[side][q], enc_f(v[side][q]));
+              atomicMin(&s_cside[side][q], enc_f(cv[side][q]));
+            } else {
+              atomicMax(&s_side[side][q], enc_f(v[side][q]));
+              atomicMax(&s_cside[side][q], enc_f(cv[side][q]));
+            }
           }
       }
       // exclusive offsets of the threads' left and right counts
@@ -839,14 +929,18 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
         totr += s_wr[w];
       }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < kTopItems; ++k) {
         if (!(hmask >> k & 1u)) continue;
-        const bool left = lmask >> k & 1u;
+        const bool left = lmask >> k & 1u;   // (k is static here: the records stay in registers)
         // the bins and this pass classify with the same arithmetic, so the
         // left side holds exactly nl clusters; refuse anything else
         const uint32_t pos = left ? offl++ : nl + offr++;
-        if (left ? pos < nl : pos < n) out[pos] = cs[k];
-        else atomicOr(&a.misc[6], kErrTopBuild);
+        if (left ? pos < nl : pos < n) {
+          out[2 * pos] = lo[k];
+          out[2 * pos + 1] = hi[k];
+        } else {
+          atomicOr(&a.misc[6], kErrTopBuild);
+        }
       }
       __syncthreads();
       if (tid == 0) {
@@ -859,62 +953,97 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
     __syncthreads();
     if (tid == 0) {
       uint32_t ref[2] = {kNone, kNone}, pend[2] = {kNone, kNone}, n_pend = 0;
-      bool ok = true;
+      bool ok = true, cont = false;
+      uint4 next = make_uint4(0u, 0u, 0u, 0u);
+      // what each side needs: a leaf reference, a node and a warp task, or a
+      // node and a block task (the first large side continues in this block)
+      const uint32_t cnt[2] = {nl, n - nl}, first[2] = {0u, nl};
+      uint32_t n_int = 0, n_sm = 0, n_big = 0;
+      int keep = -1;
+      for (int side = 0; side < 2; ++side) {
+        if (cnt[side] < 2u) continue;
+        ++n_int;
+        if (cnt[side] <= kTopSmall) ++n_sm;
+        else if (keep < 0) keep = side;
+        else ++n_big;
+      }
+      // independent counter updates, in flight together
+      const uint32_t sbase = n_int ? 1u + atomicAdd(&a.ctr[kCtrSlots], n_int) : 0u;
+      const uint32_t mbase = n_sm ? atomicAdd(&a.ctr[kCtrSmall], n_sm) : 0u;
+      const uint32_t tbase = n_big ? atomicAdd(&a.ctr[kCtrTasks], n_big) : 0u;
+      // cannot fail for a consistent marking; refuse rather than write past the arrays
+      ok = sbase + n_int <= n_nodes && mbase + n_sm <= n_nodes && tbase + n_big <= n_nodes;
+      uint32_t k_int = 0, k_sm = 0, k_big = 0;
       for (int side = 0; side < 2 && ok; ++side) {
-        const uint32_t first = side ? nl : 0u, cnt = side ? n - nl : nl;
-        if (cnt == 1u) {
-          ref[side] = __float_as_uint(__ldg(&a.rec[2 * (size_t)__ldcg(out + first) + 1]).w);
+        if (cnt[side] == 1u) {
+          ref[side] = __float_as_uint(__ldcg(out + 2 * first[side] + 1).w);
           continue;
         }
-        const uint32_t si = 1u + atomicAdd(&a.ctr[kCtrSlots], 1u);
-        if (si >= n_nodes) {   // cannot happen for a consistent marking; refuse rather than write past the slots
-          ok = false;
-          break;
-        }
-        ref[side] = a.slot[si];
-        const uint4 t = make_uint4(b + first, b + first + cnt, ref[side], (depth + 1u) | ((src ^ 1u) << 31));
-        const uint32_t ti = atomicAdd(cnt <= kTopSmall ? &a.ctr[kCtrSmall] : &a.ctr[kCtrTasks], 1u);
-        if (ti >= n_nodes) {
-          ok = false;
-          break;
-        }
-        if (cnt <= kTopSmall) {
-          a.small[ti] = t;
+        ref[side] = a.slot[sbase + k_int++];
+        const uint4 t = make_uint4(b + first[side], b + first[side] + cnt[side], ref[side],
+                                   (depth + 1u) | ((src ^ 1u) << 31));
+        if (cnt[side] > kTopSmall)
+          for (int q = 0; q < 6; ++q) a.cb[6 * (size_t)ref[side] + q] = s_cside[side][q];
+        if (side == keep) {   // this block goes on with it
+          cont = true;
+          next = t;
+        } else if (cnt[side] <= kTopSmall) {
+          a.small[mbase + k_sm++] = t;
         } else {
-          a.task[ti] = t;
-          pend[side] = ti;
+          pend[side] = tbase + k_big++;
+          a.task[pend[side]] = t;
           ++n_pend;
         }
       }
       if (!ok) {
         atomicOr(&a.misc[6], kErrTopBuild);
+        cont = false;
       } else {
-        uint32_t eb[2][6];
+        float bx[2][6];
         for (int side = 0; side < 2; ++side)
-          for (int q = 0; q < 6; ++q) eb[side][q] = s_side[side][q];
-        write_top_node(a, slot, eb, ref);
+          for (int q = 0; q < 6; ++q) bx[side][q] = dec_f(s_side[side][q]);
+        write_top_node(a, slot, bx, ref);
         if (n_pend) atomicAdd(&a.ctr[kCtrPending], n_pend);   // counted before they can finish
         __threadfence();
         for (int side = 0; side < 2; ++side)
           if (pend[side] != kNone) st_release_u32(&a.ready[pend[side]], 1u);
       }
-      atomicSub(&a.ctr[kCtrPending], 1u);   // this task is done
+      if (cont) {   // still pending: the task continues as its child
+        s_task[0] = next.x;
+        s_task[1] = next.y;
+        s_task[2] = next.z;
+        s_task[3] = next.w;
+        s_cont = 1u;
+      } else {
+        s_cont = 0u;
+        atomicSub(&a.ctr[kCtrPending], 1u);   // this task is done
+      }
     }
     __syncthreads();
   }
 }
 
 // Warp tasks (2 to kTopSmall clusters), after the block tasks: a warp builds
-// the whole subtree of a task, a cluster per lane; a sub-task is the mask of
-// its lanes (the lane order is the cluster order, so a partition by mask is
-// stable).  The same rules and arithmetic as the block tasks.
+// the whole subtree of a task, a cluster per lane, one tree level at a time.
+// The sub-tasks of a level are disjoint sets of lanes (segments, kept as lane
+// masks; the lane order is the cluster order, so splitting a mask keeps the
+// order on both sides), and all of them are worked at once: each lane
+// evaluates, for its own segment, the split after its own bin on every axis
+// -- a partition {bin < q} is reached first (lowest q) at q = 1 + the largest
+// bin on its left, so these are exactly the splits the bin sweep of a block
+// task can choose, each with its lowest q -- and the segment takes the lowest
+// (cost, axis, q).  The same rules and arithmetic as the block tasks.
 constexpr int kSmallWarps = 8;
 __global__ void __launch_bounds__(32 * kSmallWarps) k_top_small(TopArgs a) {
-  __shared__ uint32_t s_bins[kSmallWarps][3 * kTopBins * kBinWords];
-  __shared__ uint4 s_stack[kSmallWarps][kTopSmall];
+  __shared__ float s_box[kSmallWarps][kTopSmall][6];
+  __shared__ float s_cen[kSmallWarps][kTopSmall][3];
+  __shared__ uint32_t s_w[kSmallWarps][kTopSmall], s_ref[kSmallWarps][kTopSmall];
+  __shared__ int s_bin[kSmallWarps][3][kTopSmall];
+  __shared__ float s_cost[kSmallWarps][kTopSmall];
+  __shared__ uint32_t s_key[kSmallWarps][kTopSmall];   // valid << 31 | nl << 10 | axis << 8 | q
+  __shared__ uint32_t s_slot[kSmallWarps][kTopSmall], s_child[kSmallWarps][kTopSmall][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t* bins = s_bins[warp];
   const uint32_t C = a.ctr[kCtrClusters];
   if (C < 2 || (a.misc[6] & kErrTopBuild)) return;
   if (a.ctr[kCtrMarked] + 2u != C) {   // the marked top part and the clusters disagree: leave the LBVH as it is
@@ -934,106 +1063,179 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_top_small(TopArgs a) {
       return;
     }
     const bool mine = (uint32_t)lane < n;
-    const uint32_t c = mine ? __ldcg(a.order[t.w >> 31] + t.x + lane) : 0u;
-    const float4 lo = mine ? __ldg(&a.rec[2 * (size_t)c]) : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-    const float4 hi = mine ? __ldg(&a.rec[2 * (size_t)c + 1]) : make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+    const float4* in = a.rec[t.w >> 31] + 2 * (size_t)t.x;
+    const float4 lo = mine ? __ldcg(in + 2 * lane) : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+    const float4 hi = mine ? __ldcg(in + 2 * lane + 1) : make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
     const float3 cc = cl_centroid(lo, hi);
-    const uint32_t w = __float_as_uint(lo.w), my_ref = __float_as_uint(hi.w);
-    if (lane == 0) s_stack[warp][0] = make_uint4(n == 32u ? 0xFFFFFFFFu : (1u << n) - 1u, t.z, t.w & 0x7FFFFFFFu, 0u);
-    int sp = 1;
+    s_box[warp][lane][0] = lo.x;
+    s_box[warp][lane][1] = lo.y;
+    s_box[warp][lane][2] = lo.z;
+    s_box[warp][lane][3] = hi.x;
+    s_box[warp][lane][4] = hi.y;
+    s_box[warp][lane][5] = hi.z;
+    s_cen[warp][lane][0] = cc.x;
+    s_cen[warp][lane][1] = cc.y;
+    s_cen[warp][lane][2] = cc.z;
+    s_w[warp][lane] = __float_as_uint(lo.w);
+    s_ref[warp][lane] = __float_as_uint(hi.w);
+    // the subtree of n clusters has n - 1 internal nodes; its root has its slot
+    uint32_t sbase = 0;
+    if (lane == 0 && n > 2u) sbase = 1u + atomicAdd(&a.ctr[kCtrSlots], n - 2u);
+    sbase = __shfl_sync(0xFFFFFFFFu, sbase, 0);
+    if (n > 2u && sbase + (n - 2u) > n_nodes) {   // cannot happen for a consistent marking
+      if (lane == 0) atomicOr(&a.misc[6], kErrTopBuild);
+      return;
+    }
+    if ((uint32_t)lane + 2u < n) s_slot[warp][lane] = a.slot[sbase + lane];
+    uint32_t next_slot = 0;   // new nodes taken so far (warp-uniform)
+    // the lane's segment (0: none, or a single cluster), its node slot and depth
+    uint32_t seg = mine ? (n == 32u ? 0xFFFFFFFFu : (1u << n) - 1u) : 0u;
+    uint32_t seg_slot = t.z, depth = t.w & 0x7FFFFFFFu;
     __syncwarp();
-    while (sp > 0) {
-      const uint4 e = s_stack[warp][--sp];
-      __syncwarp();
-      const uint32_t mask = e.x, slot = e.y, depth = e.z;
-      const bool in = mask >> lane & 1u;
-      const uint32_t n_s = __popc(mask);
-      float mn[3], mx[3];
-      for (int k = 0; k < 3; ++k) {
-        mn[k] = in ? comp(cc, k) : INFINITY;
-        mx[k] = in ? comp(cc, k) : -INFINITY;
-        for (int off = 16; off > 0; off >>= 1) {
-          mn[k] = fminf(mn[k], __shfl_xor_sync(0xFFFFFFFFu, mn[k], off));
-          mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xFFFFFFFFu, mx[k], off));
+    bool fail = false;
+    while (true) {
+      const bool act = __popc(seg) >= 2;
+      if (!__any_sync(0xFFFFFFFFu, act)) break;
+      // segment centroid bounds, bins
+      float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (uint32_t m = act ? seg : 0u; m; m &= m - 1u) {
+        const int j = __ffs(m) - 1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          mn[k] = fminf(mn[k], s_cen[warp][j][k]);
+          mx[k] = fmaxf(mx[k], s_cen[warp][j][k]);
         }
       }
-      float scale[3];
       bool axis_ok[3];
+      int my_bin[3];
+#pragma unroll
       for (int k = 0; k < 3; ++k) {
         const float ext = __fsub_rn(mx[k], mn[k]);
-        axis_ok[k] = ext > 0.0f && depth < kTopMedianDepth;
-        scale[k] = axis_ok[k] ? __fdiv_rn((float)kTopBins, ext) : 0.0f;
+        axis_ok[k] = act && ext > 0.0f && depth < kTopMedianDepth;
+        my_bin[k] = axis_ok[k] ? top_bin(comp(cc, k), mn[k], __fdiv_rn((float)kTopBins, ext)) : kTopBins;
+        s_bin[warp][k][lane] = my_bin[k];
       }
-      bins_clear(bins, lane, 32);
       __syncwarp();
-      if (in)
-        for (int k = 0; k < 3; ++k)
-          if (axis_ok[k]) bins_add(bins, k, top_bin(comp(cc, k), mn[k], scale[k]), w, lo, hi);
-      __syncwarp();
-      int axis = -1, split = 0;
-      Split best;
-      best.valid = false;
-      best.cost = 0.0f;
-      best.q = 0;
-      best.nl = 0u;
+      // this lane's best split over the axes: lowest cost, ties to the lower axis
+      bool valid = false;
+      float cost = 0.0f;
+      int b_axis = 0, b_q = 0;
+      uint32_t b_nl = 0;
+#pragma unroll
       for (int k = 0; k < 3; ++k) {
         if (!axis_ok[k]) continue;
-        const Split r = warp_best_split(bins + kBinWords * kTopBins * k, lane);
-        if (r.valid && (axis < 0 || r.cost < best.cost)) {
-          axis = k;
-          best = r;
+        const int q = my_bin[k] + 1;
+        float3 llo = make_float3(INFINITY, INFINITY, INFINITY), lhi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+        float3 rlo = llo, rhi = lhi;
+        uint32_t lw = 0, rw = 0, lc = 0, rc = 0;
+        for (uint32_t m = seg; m; m &= m - 1u) {
+          const int j = __ffs(m) - 1;
+          const float* bj = s_box[warp][j];
+          const uint32_t wj = s_w[warp][j];
+          if (s_bin[warp][k][j] < q) {
+            llo = make_float3(fminf(llo.x, bj[0]), fminf(llo.y, bj[1]), fminf(llo.z, bj[2]));
+            lhi = make_float3(fmaxf(lhi.x, bj[3]), fmaxf(lhi.y, bj[4]), fmaxf(lhi.z, bj[5]));
+            lw += wj;
+            ++lc;
+          } else {
+            rlo = make_float3(fminf(rlo.x, bj[0]), fminf(rlo.y, bj[1]), fminf(rlo.z, bj[2]));
+            rhi = make_float3(fmaxf(rhi.x, bj[3]), fmaxf(rhi.y, bj[4]), fmaxf(rhi.z, bj[5]));
+            rw += wj;
+            ++rc;
+          }
+        }
+        if (lc == 0u || rc == 0u) continue;
+        const float c = __fadd_rn(__fmul_rn(box_area_rn(llo, lhi), __uint2float_rn(lw)),
+                                  __fmul_rn(box_area_rn(rlo, rhi), __uint2float_rn(rw)));
+        if (!valid || c < cost) {
+          valid = true;
+          cost = c;
+          b_axis = k;
+          b_q = q;
+          b_nl = lc;
         }
       }
-      uint32_t nl = n_s / 2u;
-      if (axis >= 0) {
-        split = best.q;
-        nl = best.nl;
-      }
-      const bool left = in && (axis >= 0 ? top_bin(comp(cc, axis), mn[axis], scale[axis]) < split
-                                         : (uint32_t)__popc(mask & lt) < nl);
-      const uint32_t lmask = __ballot_sync(0xFFFFFFFFu, left), rmask = mask & ~lmask;
-      if ((uint32_t)__popc(lmask) != nl || lmask == 0u || rmask == 0u) {   // cannot happen: same classification
-        if (lane == 0) atomicOr(&a.misc[6], kErrTopBuild);
-        return;
-      }
-      uint32_t eb[2][6];
-      uint32_t ref[2];
-      bool fail = false;
-      for (int side = 0; side < 2; ++side) {
-        const uint32_t m = side ? rmask : lmask;
-        const bool on = m >> lane & 1u;
-        float v[6] = {on ? lo.x : INFINITY, on ? lo.y : INFINITY, on ? lo.z : INFINITY,
-                      on ? hi.x : -INFINITY, on ? hi.y : -INFINITY, on ? hi.z : -INFINITY};
-        for (int off = 16; off > 0; off >>= 1)
-          for (int q = 0; q < 6; ++q) {
-            const float o = __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
-            v[q] = q < 3 ? fminf(v[q], o) : fmaxf(v[q], o);
-          }
-        for (int q = 0; q < 6; ++q) eb[side][q] = enc_f(v[q]);
-        if (__popc(m) == 1) {
-          ref[side] = __shfl_sync(0xFFFFFFFFu, my_ref, __ffs(m) - 1);
-        } else {
-          uint32_t sl = 0;
-          if (lane == 0) {
-            const uint32_t si2 = 1u + atomicAdd(&a.ctr[kCtrSlots], 1u);
-            sl = si2 < n_nodes ? a.slot[si2] : kNone;
-          }
-          sl = __shfl_sync(0xFFFFFFFFu, sl, 0);
-          if (sl == kNone || sp >= (int)kTopSmall) {   // cannot happen for a consistent marking
-            fail = true;
-            break;
-          }
-          ref[side] = sl;
-          if (lane == 0) s_stack[warp][sp] = make_uint4(m, sl, depth + 1u, 0u);
-          ++sp;
-        }
-      }
-      if (fail) {
-        if (lane == 0) atomicOr(&a.misc[6], kErrTopBuild);
-        return;
-      }
-      if (lane == 0) write_top_node(a, slot, eb, ref);
+      s_cost[warp][lane] = cost;
+      s_key[warp][lane] = (valid ? 0x80000000u : 0u) | (b_nl << 10) | ((uint32_t)b_axis << 8) | (uint32_t)b_q;
       __syncwarp();
+      // the segment's split: lowest (cost, axis, q) over its lanes
+      bool s_valid = false;
+      float s_c = 0.0f;
+      uint32_t s_k = 0;
+      for (uint32_t m = act ? seg : 0u; m; m &= m - 1u) {
+        const int j = __ffs(m) - 1;
+        const uint32_t key = s_key[warp][j];
+        if (!(key & 0x80000000u)) continue;
+        const float c = s_cost[warp][j];
+        if (!s_valid || c < s_c || (c == s_c && (key & 0x3FFu) < (s_k & 0x3FFu))) {
+          s_valid = true;
+          s_c = c;
+          s_k = key;
+        }
+      }
+      const uint32_t n_seg = __popc(seg);
+      const int axis = s_valid ? (int)((s_k >> 8) & 3u) : -1;
+      const int split = (int)(s_k & 0xFFu);
+      const uint32_t nl = s_valid ? (s_k >> 10) & 0x3Fu : n_seg / 2u;
+      const int a_bin = axis == 0 ? my_bin[0] : (axis == 1 ? my_bin[1] : my_bin[2]);
+      const bool left = act && (axis >= 0 ? a_bin < split : (uint32_t)__popc(seg & lt) < nl);
+      const uint32_t lmask = __ballot_sync(0xFFFFFFFFu, left);
+      const uint32_t lseg = seg & lmask, rseg = seg & ~lmask;
+      if (act && ((uint32_t)__popc(lseg) != nl || lseg == 0u || rseg == 0u)) fail = true;   // cannot happen
+      if (__any_sync(0xFFFFFFFFu, fail)) {
+        fail = true;
+        break;
+      }
+      // the segment's leader (its lowest lane) writes the node; new nodes take
+      // slots in lane order of their leaders
+      const bool leader = act && (seg & lt) == 0u;
+      const uint32_t need = leader ? (uint32_t)(__popc(lseg) >= 2) + (uint32_t)(__popc(rseg) >= 2) : 0u;
+      uint32_t x = need;
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+        if (lane >= off) x += y;
+      }
+      const uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
+      if (next_slot + total + 2u > n) fail = true;   // cannot happen: n - 2 new nodes at most
+      if (__any_sync(0xFFFFFFFFu, fail)) {
+        fail = true;
+        break;
+      }
+      if (leader) {
+        uint32_t k_new = next_slot + x - need;
+        float bx[2][6];
+        uint32_t ref[2];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const uint32_t sm = side ? rseg : lseg;
+          float v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+          for (uint32_t m = sm; m; m &= m - 1u) {
+            const float* bj = s_box[warp][__ffs(m) - 1];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              v[q] = fminf(v[q], bj[q]);
+              v[3 + q] = fmaxf(v[3 + q], bj[3 + q]);
+            }
+          }
+          for (int q = 0; q < 6; ++q) bx[side][q] = v[q];
+          ref[side] = __popc(sm) == 1 ? s_ref[warp][__ffs(sm) - 1] : s_slot[warp][k_new++];
+          s_child[warp][lane][side] = ref[side];
+        }
+        write_top_node(a, seg_slot, bx, ref);
+      }
+      next_slot += total;
+      __syncwarp();
+      if (act) {   // into the own half: its node (from the leader), one level deeper
+        const uint32_t half = left ? lseg : rseg;
+        seg_slot = s_child[warp][__ffs(seg) - 1][left ? 0 : 1];
+        seg = __popc(half) >= 2 ? half : 0u;
+        ++depth;
+      }
+      __syncwarp();
+    }
+    if (fail) {
+      if (lane == 0) atomicOr(&a.misc[6], kErrTopBuild);
+      return;
     }
   }
 }
@@ -1494,13 +1696,13 @@ static cudaError_t top_alloc(rr_scene* s) {
   };
   RR_TRY(alloc((void**)&s->d_cl_at, T * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_cl_bsum, nb4 * sizeof(uint32_t)));
-  RR_TRY(alloc((void**)&s->d_cl_rec, T * 2 * sizeof(float4)));
-  RR_TRY(alloc((void**)&s->d_cl_idx, 2 * T * sizeof(uint32_t)));
+  RR_TRY(alloc((void**)&s->d_cl_rec, 2 * T * 2 * sizeof(float4)));
   RR_TRY(alloc((void**)&s->d_top_slot, T * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_top_task, T * sizeof(uint4)));
   RR_TRY(alloc((void**)&s->d_top_ready, T * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_top_small, T * sizeof(uint4)));
   RR_TRY(alloc((void**)&s->d_top_ctr, 8 * sizeof(uint32_t)));
+  RR_TRY(alloc((void**)&s->d_top_cb, T * 6 * sizeof(uint32_t)));
   s->scene_bytes += bytes;
   return cudaSuccess;
 }
@@ -1514,25 +1716,26 @@ static cudaError_t build_sah_top(rr_scene* s, cudaStream_t st) {
   RR_TRY(cudaMemsetAsync(s->d_cl_bsum, 0, (size_t)nb4 * sizeof(uint32_t), st));
   RR_TRY(cudaMemsetAsync(s->d_top_ready, 0, (size_t)n * sizeof(uint32_t), st));
   RR_TRY(cudaMemsetAsync(s->d_top_ctr, 0, 8 * sizeof(uint32_t), st));
-  k_top_mark<<<(n - 1 + 255) / 256, 256, 0, st>>>(n, s->d_child, s->d_range, s->d_cl_at, s->d_top_slot, s->d_top_ctr);
+  k_top_mark<<<(n - 1 + 255) / 256, 256, 0, st>>>(n, s->d_child, s->d_range, s->d_cl_at, s->d_top_slot, s->d_top_ctr,
+                                                  s->d_top_cb);
   RR_TRY(cudaGetLastError());
   k_top_count<<<s->cl_blocks, 256, 0, st>>>(n, s->d_cl_at, s->d_cl_bsum);
   RR_TRY(cudaGetLastError());
   k_scan_single<<<1, 1024, 0, st>>>(s->d_cl_bsum, nb4);
   RR_TRY(cudaGetLastError());
   k_top_compact<<<s->cl_blocks, 256, 0, st>>>(n, s->d_cl_at, s->d_cl_bsum, s->d_range, s->d_nbox, s->d_cl_rec,
-                                               s->d_cl_idx, s->d_top_task, s->d_top_ready, s->d_top_small,
-                                               s->d_top_ctr);
+                                               s->d_top_task, s->d_top_ready, s->d_top_small, s->d_top_ctr,
+                                               s->d_top_cb);
   RR_TRY(cudaGetLastError());
   TopArgs a;
-  a.rec = s->d_cl_rec;
-  a.order[0] = s->d_cl_idx;
-  a.order[1] = s->d_cl_idx + n;
+  a.rec[0] = s->d_cl_rec;
+  a.rec[1] = s->d_cl_rec + 2 * (size_t)n;
   a.slot = s->d_top_slot;
   a.task = s->d_top_task;
   a.ready = s->d_top_ready;
   a.small = s->d_top_small;
   a.ctr = s->d_top_ctr;
+  a.cb = s->d_top_cb;
   a.nodes = s->d_nodes;
   a.child = s->d_child;
   a.parent = s->d_parent;

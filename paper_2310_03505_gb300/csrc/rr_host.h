@@ -110,13 +110,13 @@ struct rr_scene {
   // SAH top over the LBVH's subtrees (allocated with the first such build)
   uint32_t* d_cl_at = nullptr;     // [T] cluster root reference at the cluster's first leaf, else kNone
   uint32_t* d_cl_bsum = nullptr;   // [cl_blocks rounded up to 4] clusters per compaction block, then offsets
-  float4* d_cl_rec = nullptr;      // [T][2] cluster (lo xyz, weight) (hi xyz, root reference)
-  uint32_t* d_cl_idx = nullptr;    // [2][T] cluster order of the top-down build (ping-pong)
+  float4* d_cl_rec = nullptr;      // [2][T][2] cluster (lo xyz, weight) (hi xyz, root reference), ping-pong
   uint32_t* d_top_slot = nullptr;  // [T] node slots of the LBVH's top part (root first)
   uint4* d_top_task = nullptr;     // [T] block tasks (first, end, node slot, depth | source << 31)
   uint32_t* d_top_ready = nullptr; // [T] block task published
   uint4* d_top_small = nullptr;    // [T] warp tasks, same fields
   uint32_t* d_top_ctr = nullptr;   // [8] counters of the build
+  uint32_t* d_top_cb = nullptr;    // [T][6] centroid bounds of the block task at each node slot (encoded)
   uint32_t cl_blocks = 0;
   uint32_t sort_tiles = 0;
   uint32_t depth = 0;
