@@ -373,6 +373,7 @@ def main():
                     help="BVH build of the batched and served scenes, built once: with the binned-SAH top "
                          "(default) or the LBVH alone")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-scan-only", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=10.0,
                     help="arrival window per request rate of the served workload")
     args = ap.parse_args()
@@ -496,6 +497,35 @@ def main():
     bounces = params["max_bounces"] * args.steps
     traffic = traffic_from_profiles()
 
+    # the scans alone on a resident BVH (built once, with the SAH top): the
+    # metric with the build excluded, the build reported beside it
+    scan_only = None
+    if not args.no_scan_only:
+        rr.rr_batch_config_set(h, bvh_build=rr.RR_BVH_SAH_TOP)   # one build, untimed
+        for i in range(3):
+            rr.rr_scan_async(h, pz, {**params, "scan_id": 5000 + i}, img)
+        rr.rr_scene_sync(h)
+        rr.rr_scene_stats(h, reset=True)
+        n_so = min(args.steps, 100)
+        t_so = []
+        for i in range(n_so):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rr.rr_scan_async(h, pz, {**params, "scan_id": 6000 + rank * 1000 + i}, img)
+            e1.record(stream)
+            t_so.append((e0, e1))
+        torch.cuda.synchronize()
+        so_ms = float(np.sum([a.elapsed_time(b) for a, b in t_so]))
+        so_rc = rr.rr_scene_sync(h)
+        so_q = float(rr.rr_scene_stats(h, reset=True)["closest_queries"])
+        job_so_ms, job_so_q = reduce_timing(so_ms, so_q, world, device)
+        scan_only = {"value": job_so_q / (job_so_ms * 1e-3) / 1e6, "unit": "Mrays/s",
+                     "scans_per_s": world * n_so / (job_so_ms * 1e-3), "ms_per_scan": job_so_ms / n_so,
+                     "steps": n_so, "bvh": "LBVH + binned-SAH top, built once (untimed)",
+                     "status": "ok" if so_rc is None else str(so_rc)}
+        set_bvh(rr, h, args.step_bvh)
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -558,6 +588,8 @@ def main():
                                  "overlap: achieved divides their algorithmic bytes by the union of their CUDA-event "
                                  "intervals; achieved_per_launch divides by the summed launch durations",
                          "achieved_per_launch": per_launch_gbs,
+                         "dram_gbs": (traffic / (trace_busy / max(bounces, 1) * 1e-3) / 1e9)
+                                     if traffic and trace_busy > 0 else None,
                          "algorithmic_bytes_per_bounce": algo_bytes / max(bounces, 1),
                          "busy_ms_per_bounce": trace_busy / max(bounces, 1),
                          "algorithmic_bytes_per_query": bytes_per_closest,
@@ -565,6 +597,7 @@ def main():
                          "launches_per_step": trace_launches / max(args.steps, 1),
                          "ms_per_launch": trace_ms / max(trace_launches, 1)},
             "visibility_queries": {"nodes_per_query": any_nodes_per_q, "tris_per_query": any_tris_per_q},
+            "scan_only": scan_only,
             "batched": batched, "served": served,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["kernel_launches"]),
             "kernels_per_step": kernels_per_step, "clocks": clk, "wall_s_timed": wall,

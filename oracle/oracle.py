@@ -47,7 +47,8 @@ class Params(C.Structure):
                 ("blur_sigma_bins", C.c_double), ("az_pattern_sigma", C.c_double), ("noise_sys", C.c_double),
                 ("noise_amb", C.c_double),
                 ("flags", C.c_uint32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("scan_id", C.c_uint32),
-                ("beam_aspect", C.c_double), ("noise_cell_az", C.c_double), ("noise_cell_bins", C.c_double)]
+                ("beam_aspect", C.c_double), ("noise_cell_az", C.c_double), ("noise_cell_bins", C.c_double),
+                ("ray_stride", C.c_uint32)]
 
 
 class Pose(C.Structure):
@@ -164,7 +165,8 @@ def make_params(s: dict) -> Params:
                   s["beam_width"], s["beam_prob"], s["elevation"], s["bin_size"], s["t_min"], s["min_energy"],
                   s["freq_hz"], s["blur_sigma_bins"], s["az_pattern_sigma"], s["noise_sys"], s["noise_amb"],
                   flags, seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(s["scan_id"]),
-                  s.get("beam_aspect") or 1.0, s.get("noise_cell_az") or 8.0, s.get("noise_cell_bins") or 32.0)
+                  s.get("beam_aspect") or 1.0, s.get("noise_cell_az") or 8.0, s.get("noise_cell_bins") or 32.0,
+                  int(s.get("ray_stride") or 1))
 
 
 def make_pose(pz: dict) -> Pose:

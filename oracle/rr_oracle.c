@@ -88,6 +88,8 @@ typedef struct {
   uint32_t flags, seed_lo, seed_hi, scan_id;
   double beam_aspect;                   /* elevation / azimuth spread of the D3 cone (1: circular) */
   double noise_cell_az, noise_cell_bins; /* Perlin lattice spacing (beams, bins) */
+  uint32_t ray_stride;                  /* trace the initial rays k = 0, s, 2s, ... of each column (0, 1: all);
+                                           a sample: each ray is independent of the others */
 } orc_params;
 
 typedef struct {
@@ -669,7 +671,8 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
   size_t cap = 64;
   oray_t* stack = (oray_t*)malloc(cap * sizeof(oray_t));
 
-  for (uint32_t k = 0; k < p->rays_per_beam; ++k) {
+  const uint32_t stride = p->ray_stride > 1 ? p->ray_stride : 1u;
+  for (uint32_t k = 0; k < p->rays_per_beam; k += stride) {
     double* tal = col->tally + 4 * (size_t)k;
     int flagged = 0;
     size_t sp = 0;

@@ -69,7 +69,12 @@ E_FLOOR = 1e-30
 def compare_segment_energies(gpu_segs, ora_segs, ora_flags, az_list, rel=1e-3, abs_rel_E=1e-6):
     """Per segment of every unflagged ray: energy entering, cos theta0 and the
     two return energies, within rel of the oracle plus abs_rel_E of the
-    segment's energy plus E_FLOOR.  Returns a list of mismatch descriptions."""
+    energies along the path down to the segment (its own and every
+    ancestor's) plus E_FLOOR.  The path term: a child's energy is E R minus
+    the returns (reading 8), a difference whose FP32 rounding is relative to
+    the energies it is taken from -- when the returns take nearly all of E R
+    the child is a residue far below them -- and that error then moves down
+    the tree scaled by factors <= 1.  Returns a list of mismatch descriptions."""
     az_index = {az: i for i, az in enumerate(az_list)}
     def table(segs):
         out = {}
@@ -79,6 +84,10 @@ def compare_segment_energies(gpu_segs, ora_segs, ora_flags, az_list, rel=1e-3, a
                 out[(az, int(s["k"]), int(s["path"]), int(s["bounce"]))] = s
         return out
     g, o = table(gpu_segs), table(ora_segs)
+    along = {}   # sum of the oracle energies from the initial ray down to the segment
+    for key in sorted(o, key=lambda x: x[3]):
+        az, k, path, b = key
+        along[key] = float(o[key]["E"]) + (along.get((az, k, path >> 1, b - 1), 0.0) if b > 0 else 0.0)
     bad = []
     for key, os_ in o.items():
         az, k = key[0], key[1]
@@ -87,7 +96,8 @@ def compare_segment_energies(gpu_segs, ora_segs, ora_flags, az_list, rel=1e-3, a
         gs = g[key]
         for f in ("E", "cos_i", "ret_t", "ret_a"):
             a, b = float(gs[f]), float(os_[f])
-            if abs(a - b) > rel * abs(b) + abs_rel_E * float(os_["E"]) + E_FLOOR:
+            scale = float(os_["E"]) if f == "cos_i" else along[key]
+            if abs(a - b) > rel * abs(b) + abs_rel_E * scale + E_FLOOR:
                 bad.append(f"ray {key[:2]} seg {key[2:]} {f}: gpu {a:.9g} oracle {b:.9g} (cos_i {float(os_['cos_i']):.7f})")
     return bad
 

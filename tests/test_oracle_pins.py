@@ -706,3 +706,30 @@ def test_bin_returns_is_the_exactly_rounded_sum():
     # a cancelling sum that naive left-to-right addition gets wrong
     vals = np.array([1e16, 1.0, -1e16, 1.0], np.float64)
     assert orc.bin_returns(np.zeros(4, np.uint32), np.zeros(4, np.uint32), vals, 1, 1)[0, 0] == 2.0
+
+
+def test_ray_stride_traces_exactly_the_sampled_rays():
+    """A sample of every s-th initial ray of a column traces those rays as the
+    full scan does (each initial ray's tree depends only on its own counter):
+    the same segments and tallies for them, nothing for the others, and the
+    sample's image is the full scan's image of those rays alone."""
+    from paper_2310_03505_gb300 import scenes
+    sc, pz, s = scenes.config_tiny()
+    cols = [3, 77, 200, 391]
+    full = orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, s, az_list=cols, post=False)
+    stride = 3
+    part = orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, {**s, "ray_stride": stride},
+                    az_list=cols, post=False)
+    keep = np.arange(s["rays_per_beam"]) % stride == 0
+    assert np.array_equal(part["tallies"][:, keep], full["tallies"][:, keep])
+    assert not part["tallies"][:, ~keep].any() and not part["flags"][:, ~keep].any()
+    fs = full["segments"][full["segments"]["k"] % stride == 0]
+    ps = part["segments"]
+    assert len(ps) == len(fs) > 0
+    key = lambda a: np.lexsort((a["path"], a["bounce"], a["k"], a["az"]))
+    assert np.array_equal(ps[key(ps)], fs[key(fs)])
+    # a stride of the whole beam traces ray 0 alone: the image holds at most its returned energy
+    one = orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz,
+                   {**s, "ray_stride": s["rays_per_beam"]}, az_list=[77], post=False)
+    assert not one["tallies"][0, 1:].any()
+    assert 0 < one["image"].sum() <= one["tallies"][0, 0, 0] * (1 + 1e-12)
