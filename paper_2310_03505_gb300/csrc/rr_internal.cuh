@@ -55,7 +55,7 @@ struct __align__(16) HitRec {
   float t;
   uint32_t leaf;   // sorted leaf index or kNone
   uint32_t flags;  // bit 0: visibility test ran, bit 1: visible
-  float wa_g;      // W(omega_a) * g_rx of a visible air-path candidate, else 0
+  float wa_g;      // W(omega_a) of a visible air-path candidate, else 0 (the receive weight is applied by the shading)
 };
 
 // device counters of one scene

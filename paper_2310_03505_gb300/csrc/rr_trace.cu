@@ -392,6 +392,31 @@ __device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs&
 // so the lanes stay busy however uneven the query lengths are.
 constexpr uint32_t kClaim = 32;
 
+// Receive-beam weight of a return from p (Sec. III-A air path): g =
+// exp(-delta^2 / 2 sigma^2), delta the angle between p - sensor and the beam
+// axis of azimuth az; an elliptic beam scales the spread along the offset's
+// direction around the axis.
+__device__ __forceinline__ float rx_weight(const ScanDesc* sd, uint32_t az, float3 p) {
+  const float4 beam = __ldg(&sd->beam);
+  const float sigma = d3_sigma(beam.x, beam.y);
+  const float3 v = p - f3(__ldg(&sd->pos_rmax));
+  const float delta = angle_between(v, beam_axis(sd, az));
+  float q = (delta / sigma) * (delta / sigma);
+  const float aspect = __ldg(&sd->ext.x);
+  if (aspect != 1.0f) {
+    const float2 cs = beam_angle(az, __ldg(&sd->dims.x));
+    float se, ce;
+    sincosf(beam.z, &se, &ce);
+    const float4 qt = __ldg(&sd->quat);
+    const float3 ea = qrot(qt, make_float3(-cs.y, cs.x, 0.0f));
+    const float3 ee = qrot(qt, make_float3(-se * cs.x, -se * cs.y, ce));
+    const float c_a = dot(v, ea), c_e = dot(v, ee);
+    const float perp2 = c_a * c_a + c_e * c_e;
+    if (perp2 > 0.0f) q *= (c_a * c_a + c_e * c_e / (aspect * aspect)) / perp2;
+  }
+  return sigma > 0.0f ? expf(-0.5f * q) : 0.0f;
+}
+
 template <bool kAny, int kBlock, bool kWide>
 __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
   typedef typename std::conditional<kWide, uint2, uint32_t>::type StackEntry;
@@ -417,7 +442,6 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
   s.node = kNone;
   StackEntry stack[kStack];
   uint32_t ray_i = kNone;   // ray of the lane's query (kNone: idle)
-  uint32_t tag = 0u;        // any hit: azimuth << 16 | scan
   float wa = 0.0f;          // any hit: W(omega_a) of the candidate
   uint32_t c_base = 0u, c_end = 0u;   // claimed, unassigned jobs (warp-uniform)
   bool exhausted = false;             // the job list is used up (warp-uniform)
@@ -461,7 +485,6 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
           const float3 v = f3(__ldg(&sd->pos_rmax)) - p;
           const float dist = length(v);
           trav_begin(s, p, (1.0f / dist) * v, __ldg(&sd->phys.x), dist, h.leaf, a.n_tris, kWide);
-          tag = (ray.meta.y & 0xFFFF0000u) | sm.x;
         } else {
           ray_i = job;
           const RayRec ray = q[ray_i];
@@ -490,31 +513,9 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
           HitRec* hp = a.hits + ray_i;
           uint32_t fl = hp->flags | 1u;
           float wag = 0.0f;
-          if (s.best == kNone) {   // the sensor is visible from the hit point
-            fl |= 2u;
-            const ScanDesc* sd = a.desc + (tag & 0xFFFFu);
-            const float4 beam = __ldg(&sd->beam);
-            const float sigma = d3_sigma(beam.x, beam.y);
-            const float3 p = s.w.o;
-            const float3 v = p - f3(__ldg(&sd->pos_rmax));
-            const uint32_t az = tag >> 16;
-            const float delta = angle_between(v, beam_axis(sd, az));
-            float q = (delta / sigma) * (delta / sigma);
-            const float aspect = __ldg(&sd->ext.x);
-            if (aspect != 1.0f) {
-              // elliptic beam: the spread along the offset's direction around the axis
-              const float2 cs = beam_angle(az, __ldg(&sd->dims.x));
-              float se, ce;
-              sincosf(beam.z, &se, &ce);
-              const float4 qt = __ldg(&sd->quat);
-              const float3 ea = qrot(qt, make_float3(-cs.y, cs.x, 0.0f));
-              const float3 ee = qrot(qt, make_float3(-se * cs.x, -se * cs.y, ce));
-              const float c_a = dot(v, ea), c_e = dot(v, ee);
-              const float perp2 = c_a * c_a + c_e * c_e;
-              if (perp2 > 0.0f) q *= (c_a * c_a + c_e * c_e / (aspect * aspect)) / perp2;
-            }
-            const float g = sigma > 0.0f ? expf(-0.5f * q) : 0.0f;
-            wag = wa * g;
+          if (s.best == kNone) {   // the sensor is visible from the hit point: its window W
+            fl |= 2u;               // (the receive weight g is applied where the return is made)
+            wag = wa;
           }
           hp->flags = fl;
           hp->wa_g = wag;
@@ -777,7 +778,8 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
         const float ret_t = E1 * R * fminf(brdf_window(m, lut, 2.0f * theta0, beam.x), 1.0f);
         float ret_a = 0.0f, range_a = 0.0f;
         bool air_T = false;
-        if (h.wa_g > 0.0f) {
+        const float wag = h.wa_g > 0.0f ? h.wa_g * rx_weight(sd, az, p) : 0.0f;
+        if (wag > 0.0f) {
           float base, cap;
           if (entering && medium == kAir) {
             base = E1 * R;
@@ -787,7 +789,7 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
             base = E1 * T;
             cap = E1 * T;
           }
-          ret_a = fmaxf(fminf(base * h.wa_g, cap), 0.0f);
+          ret_a = fmaxf(fminf(base * wag, cap), 0.0f);
           range_a = 0.5f * (L1 + length(s_pos - p));
         }
         tal[0] = ret_t + ret_a;
