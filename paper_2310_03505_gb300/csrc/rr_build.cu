@@ -163,17 +163,65 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n, int 
 }
 
 // exclusive scan of n counters (n a multiple of 4, 16-byte aligned) with one
-// block: chunks of blockDim x 4 counters, one coalesced uint4 per thread,
-// carried from chunk to chunk
+// block.  Up to 8 uint4 per thread: each thread loads its contiguous run at
+// once (one round trip), one block scan of the run sums.  More: chunks of
+// blockDim x 4 counters, one coalesced uint4 per thread, carried from chunk
+// to chunk.
 __global__ void k_scan_single(uint32_t* __restrict__ data, uint32_t n) {
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
   const uint32_t t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
-  if (t == 0) s_carry = 0u;
-  __syncthreads();
   uint4* d4 = reinterpret_cast<uint4*>(data);
   const uint32_t n4 = n / 4u;
+  const uint32_t per = (n4 + blockDim.x - 1) / blockDim.x;
+  if (per <= 8u) {
+    const uint32_t b0 = t * per;
+    uint4 v[8];
+    uint32_t sum = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < 8u; ++k) {
+      v[k] = make_uint4(0u, 0u, 0u, 0u);
+      if (k < per && b0 + k < n4) v[k] = d4[b0 + k];
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < 8u; ++k) sum += v[k].x + v[k].y + v[k].z + v[k].w;
+    uint32_t x = sum;
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = lane < nw ? s_warp[lane] : 0u;
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, off);
+        if (lane >= off) w += y;
+      }
+      s_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = x - sum + (warp > 0 ? s_warp[warp - 1] : 0u);
+#pragma unroll
+    for (uint32_t k = 0; k < 8u; ++k) {
+      if (k < per && b0 + k < n4) {
+        uint4 o;
+        o.x = run;
+        run += v[k].x;
+        o.y = run;
+        run += v[k].y;
+        o.z = run;
+        run += v[k].z;
+        o.w = run;
+        run += v[k].w;
+        d4[b0 + k] = o;
+      }
+    }
+    return;
+  }
+  if (t == 0) s_carry = 0u;
+  __syncthreads();
   for (uint32_t base = 0; base < n4; base += blockDim.x) {
     const uint32_t i = base + t;
     uint4 v = i < n4 ? d4[i] : make_uint4(0u, 0u, 0u, 0u);
@@ -326,23 +374,32 @@ __device__ __forceinline__ uint32_t node_slot(uint32_t c, uint32_t n) {
 }
 
 // a5: each leaf walks to the root; at every internal node the first arrival
-// stops and the second merges both child boxes (they are final by then)
+// stops and the second merges both child boxes (they are final by then).
+// The walker carries the box of the child it comes from, so it reads only
+// the sibling's; the node's children and parent are read alongside the
+// arrival atomic (they do not depend on it).
 __global__ void k_refit(uint32_t n, const uint32_t* __restrict__ child, const uint32_t* __restrict__ parent,
                         uint32_t* __restrict__ visit, float* __restrict__ nbox, float4* __restrict__ nodes) {
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  uint32_t p = parent[n - 1 + j];
+  uint32_t cur = j | kLeafBit;
+  float own[6];
+  for (int k = 0; k < 6; ++k) own[k] = __ldcg(nbox + 6 * (size_t)(n - 1 + j) + k);
+  uint32_t p = __ldg(&parent[n - 1 + j]);
   while (p != kNone) {
+    const uint32_t c0 = __ldg(&child[2 * p]), c1 = __ldg(&child[2 * p + 1]);
+    const uint32_t pp = __ldg(&parent[p]);
     // acquire-release: the second arrival sees the first one's box
     cuda::atomic_ref<uint32_t, cuda::thread_scope_device> cnt(visit[p]);
     if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == 0u) return;
-    const uint32_t c0 = child[2 * p], c1 = child[2 * p + 1];
-    const float* b0p = nbox + 6 * (size_t)node_slot(c0, n);
-    const float* b1p = nbox + 6 * (size_t)node_slot(c1, n);
+    const bool first_is_own = c0 == cur;
+    const float* sp = nbox + 6 * (size_t)node_slot(first_is_own ? c1 : c0, n);
+    float sib[6];
+    for (int k = 0; k < 6; ++k) sib[k] = __ldcg(sp + k);
     float b0[6], b1[6];
     for (int k = 0; k < 6; ++k) {
-      b0[k] = __ldcg(b0p + k);
-      b1[k] = __ldcg(b1p + k);
+      b0[k] = first_is_own ? own[k] : sib[k];
+      b1[k] = first_is_own ? sib[k] : own[k];
     }
     float4* nd = nodes + 4 * (size_t)p;
     nd[0] = make_float4(b0[0], b0[3], b0[1], b0[4]);
@@ -351,10 +408,13 @@ __global__ void k_refit(uint32_t n, const uint32_t* __restrict__ child, const ui
     nd[3] = make_float4(__uint_as_float(c0), __uint_as_float(c1), 0.f, 0.f);
     float* bp = nbox + 6 * (size_t)p;
     for (int k = 0; k < 3; ++k) {
-      __stcg(bp + k, fminf(b0[k], b1[k]));
-      __stcg(bp + 3 + k, fmaxf(b0[3 + k], b1[3 + k]));
+      own[k] = fminf(b0[k], b1[k]);
+      own[3 + k] = fmaxf(b0[3 + k], b1[3 + k]);
+      __stcg(bp + k, own[k]);
+      __stcg(bp + 3 + k, own[3 + k]);
     }
-    p = parent[p];
+    cur = p;
+    p = pp;
   }
 }
 
