@@ -452,7 +452,7 @@ __global__ void k_depth(uint32_t n, const uint32_t* __restrict__ parent, uint32_
 constexpr uint32_t kClusterMax = 32;
 constexpr int kTopBins = 32;
 constexpr uint32_t kTopMedianDepth = 32;
-constexpr int kTopBlock = 256;
+constexpr int kTopBlock = 512;
 constexpr uint32_t kTopSmall = 32;            // a warp task: at most one cluster per lane
 constexpr int kClTile = 2048;                 // compaction: 256 threads x 8 leaves
 constexpr uint32_t kTopSpinLimit = 1u << 22;  // x <= 256 ns naps: about a second
@@ -619,7 +619,7 @@ __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (
 
 constexpr uint32_t kEncPosInf = 0xFF800000u, kEncNegInf = 0x007FFFFFu;   // enc_f(+inf), enc_f(-inf)
 constexpr int kBinWords = 8;   // per bin: clusters, weight, lo xyz, hi xyz (encoded)
-constexpr int kTopItems = 4;   // records per thread per round of a block pass
+constexpr int kTopItems = 2;   // records per thread per round of a block pass
 
 __device__ __forceinline__ void bins_clear(uint32_t* bins, int i0, int stride) {
   for (int i = i0; i < 3 * kTopBins; i += stride) {
@@ -733,7 +733,7 @@ __device__ __forceinline__ void write_top_node(const TopArgs& a, uint32_t slot, 
 // go to the warp-task list.  The cluster records move with the partition, so
 // every pass reads its task's records contiguously, kTopItems per thread.
 __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
-  __shared__ uint32_t s_bins[3 * kTopBins * kBinWords];
+  __shared__ uint32_t s_bins[8][3 * kTopBins * kBinWords];   // one copy per 1 / 8 of the warps, summed into [0]
   __shared__ uint32_t s_cb[6], s_side[2][6], s_cside[2][6];
   __shared__ uint32_t s_task[4], s_stop, s_cont;
   __shared__ Split s_split[3];
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
     const uint32_t depth = s_task[3] & 0x7FFFFFFFu, src = s_task[3] >> 31;
     const float4* in = a.rec[src] + 2 * (size_t)b;
     float4* out = a.rec[src ^ 1u] + 2 * (size_t)b;
-    bins_clear(s_bins, tid, kTopBlock);
+    for (int w = 0; w < 8; ++w) bins_clear(s_bins[w], tid, kTopBlock);
     if (tid < 6) {
       s_side[0][tid] = s_cside[0][tid] = tid < 3 ? kEncPosInf : kEncNegInf;
       s_side[1][tid] = s_cside[1][tid] = tid < 3 ? kEncPosInf : kEncNegInf;
@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
           const int q = top_bin(comp(cc, ax), cmin[ax], scale[ax]);
           if (q != run_q[ax]) {
             if (run_q[ax] >= 0) {
-              uint32_t* bb = s_bins + kBinWords * (ax * kTopBins + run_q[ax]);
+              uint32_t* bb = s_bins[warp & 7] + kBinWords * (ax * kTopBins + run_q[ax]);
               atomicAdd(&bb[0], run_n[ax]);
               atomicAdd(&bb[1], run_w[ax]);
 #pragma unroll
@@ -865,7 +865,7 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax)
         if (run_q[ax] >= 0) {
-          uint32_t* bb = s_bins + kBinWords * (ax * kTopBins + run_q[ax]);
+          uint32_t* bb = s_bins[warp & 7] + kBinWords * (ax * kTopBins + run_q[ax]);
           atomicAdd(&bb[0], run_n[ax]);
           atomicAdd(&bb[1], run_w[ax]);
 #pragma unroll
@@ -876,10 +876,22 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
         }
     }
     __syncthreads();
+    // the warps' copies into copy 0: sums of counts and weights, min / max of
+    // the (order-preserving) encoded bounds
+    for (int i = tid; i < 3 * kTopBins * kBinWords; i += kTopBlock) {
+      const int word = i % kBinWords;
+      uint32_t v = s_bins[0][i];
+      for (int w = 1; w < 8; ++w) {
+        const uint32_t u = s_bins[w][i];
+        v = word < 2 ? v + u : (word < 5 ? min(v, u) : max(v, u));
+      }
+      s_bins[0][i] = v;
+    }
+    __syncthreads();
     if (warp < 3) {
       Split r;
       r.valid = false;
-      if (axis_ok[warp]) r = warp_best_split(s_bins + kBinWords * kTopBins * warp, lane);
+      if (axis_ok[warp]) r = warp_best_split(s_bins[0] + kBinWords * kTopBins * warp, lane);
       if (lane == 0) s_split[warp] = r;
     }
     __syncthreads();
@@ -1095,10 +1107,8 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
 // (cost, axis, q).  The same rules and arithmetic as the block tasks.
 constexpr int kSmallWarps = 8;
 __global__ void __launch_bounds__(32 * kSmallWarps) k_top_small(TopArgs a) {
-  __shared__ float s_box[kSmallWarps][kTopSmall][6];
-  __shared__ float s_cen[kSmallWarps][kTopSmall][3];
-  __shared__ uint32_t s_w[kSmallWarps][kTopSmall], s_ref[kSmallWarps][kTopSmall];
-  __shared__ int s_bin[kSmallWarps][3][kTopSmall];
+  __shared__ float4 s_rec[kSmallWarps][kTopSmall][2];     // (lo xyz, weight) (hi xyz, reference)
+  __shared__ uint32_t s_bin[kSmallWarps][kTopSmall];     // the three bins, 8 bits each
   __shared__ float s_cost[kSmallWarps][kTopSmall];
   __shared__ uint32_t s_key[kSmallWarps][kTopSmall];   // valid << 31 | nl << 10 | axis << 8 | q
   __shared__ uint32_t s_slot[kSmallWarps][kTopSmall], s_child[kSmallWarps][kTopSmall][2];
@@ -1127,17 +1137,8 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_top_small(TopArgs a) {
     const float4 lo = mine ? __ldcg(in + 2 * lane) : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
     const float4 hi = mine ? __ldcg(in + 2 * lane + 1) : make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
     const float3 cc = cl_centroid(lo, hi);
-    s_box[warp][lane][0] = lo.x;
-    s_box[warp][lane][1] = lo.y;
-    s_box[warp][lane][2] = lo.z;
-    s_box[warp][lane][3] = hi.x;
-    s_box[warp][lane][4] = hi.y;
-    s_box[warp][lane][5] = hi.z;
-    s_cen[warp][lane][0] = cc.x;
-    s_cen[warp][lane][1] = cc.y;
-    s_cen[warp][lane][2] = cc.z;
-    s_w[warp][lane] = __float_as_uint(lo.w);
-    s_ref[warp][lane] = __float_as_uint(hi.w);
+    s_rec[warp][lane][0] = lo;
+    s_rec[warp][lane][1] = hi;
     // the subtree of n clusters has n - 1 internal nodes; its root has its slot
     uint32_t sbase = 0;
     if (lane == 0 && n > 2u) sbase = 1u + atomicAdd(&a.ctr[kCtrSlots], n - 2u);
@@ -1160,10 +1161,11 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_top_small(TopArgs a) {
       float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
       for (uint32_t m = act ? seg : 0u; m; m &= m - 1u) {
         const int j = __ffs(m) - 1;
+        const float3 cj = cl_centroid(s_rec[warp][j][0], s_rec[warp][j][1]);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          mn[k] = fminf(mn[k], s_cen[warp][j][k]);
-          mx[k] = fmaxf(mx[k], s_cen[warp][j][k]);
+          mn[k] = fminf(mn[k], comp(cj, k));
+          mx[k] = fmaxf(mx[k], comp(cj, k));
         }
       }
       bool axis_ok[3];
@@ -1173,46 +1175,57 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_top_small(TopArgs a) {
         const float ext = __fsub_rn(mx[k], mn[k]);
         axis_ok[k] = act && ext > 0.0f && depth < kTopMedianDepth;
         my_bin[k] = axis_ok[k] ? top_bin(comp(cc, k), mn[k], __fdiv_rn((float)kTopBins, ext)) : kTopBins;
-        s_bin[warp][k][lane] = my_bin[k];
       }
+      s_bin[warp][lane] = (uint32_t)my_bin[0] | ((uint32_t)my_bin[1] << 8) | ((uint32_t)my_bin[2] << 16);
       __syncwarp();
-      // this lane's best split over the axes: lowest cost, ties to the lower axis
+      // this lane's best split over the axes: lowest cost, ties to the lower axis;
+      // the split after the lane's own bin on each axis, all three in one pass
+      // over the segment's members
       bool valid = false;
       float cost = 0.0f;
       int b_axis = 0, b_q = 0;
       uint32_t b_nl = 0;
+      if (act && (axis_ok[0] || axis_ok[1] || axis_ok[2])) {
+        float3 llo[3], lhi[3], rlo[3], rhi[3];
+        uint32_t lw[3], rw[3], lc[3], rc[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        if (!axis_ok[k]) continue;
-        const int q = my_bin[k] + 1;
-        float3 llo = make_float3(INFINITY, INFINITY, INFINITY), lhi = make_float3(-INFINITY, -INFINITY, -INFINITY);
-        float3 rlo = llo, rhi = lhi;
-        uint32_t lw = 0, rw = 0, lc = 0, rc = 0;
+        for (int k = 0; k < 3; ++k) {
+          llo[k] = rlo[k] = make_float3(INFINITY, INFINITY, INFINITY);
+          lhi[k] = rhi[k] = make_float3(-INFINITY, -INFINITY, -INFINITY);
+          lw[k] = rw[k] = lc[k] = rc[k] = 0u;
+        }
         for (uint32_t m = seg; m; m &= m - 1u) {
           const int j = __ffs(m) - 1;
-          const float* bj = s_box[warp][j];
-          const uint32_t wj = s_w[warp][j];
-          if (s_bin[warp][k][j] < q) {
-            llo = make_float3(fminf(llo.x, bj[0]), fminf(llo.y, bj[1]), fminf(llo.z, bj[2]));
-            lhi = make_float3(fmaxf(lhi.x, bj[3]), fmaxf(lhi.y, bj[4]), fmaxf(lhi.z, bj[5]));
-            lw += wj;
-            ++lc;
-          } else {
-            rlo = make_float3(fminf(rlo.x, bj[0]), fminf(rlo.y, bj[1]), fminf(rlo.z, bj[2]));
-            rhi = make_float3(fmaxf(rhi.x, bj[3]), fmaxf(rhi.y, bj[4]), fmaxf(rhi.z, bj[5]));
-            rw += wj;
-            ++rc;
+          const float4 jlo = s_rec[warp][j][0], jhi = s_rec[warp][j][1];
+          const uint32_t jb = s_bin[warp][j], wj = __float_as_uint(jlo.w);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const bool lft = (int)((jb >> (8 * k)) & 0xFFu) <= my_bin[k];   // bin < my_bin + 1
+            if (lft) {
+              llo[k] = make_float3(fminf(llo[k].x, jlo.x), fminf(llo[k].y, jlo.y), fminf(llo[k].z, jlo.z));
+              lhi[k] = make_float3(fmaxf(lhi[k].x, jhi.x), fmaxf(lhi[k].y, jhi.y), fmaxf(lhi[k].z, jhi.z));
+              lw[k] += wj;
+              ++lc[k];
+            } else {
+              rlo[k] = make_float3(fminf(rlo[k].x, jlo.x), fminf(rlo[k].y, jlo.y), fminf(rlo[k].z, jlo.z));
+              rhi[k] = make_float3(fmaxf(rhi[k].x, jhi.x), fmaxf(rhi[k].y, jhi.y), fmaxf(rhi[k].z, jhi.z));
+              rw[k] += wj;
+              ++rc[k];
+            }
           }
         }
-        if (lc == 0u || rc == 0u) continue;
-        const float c = __fadd_rn(__fmul_rn(box_area_rn(llo, lhi), __uint2float_rn(lw)),
-                                  __fmul_rn(box_area_rn(rlo, rhi), __uint2float_rn(rw)));
-        if (!valid || c < cost) {
-          valid = true;
-          cost = c;
-          b_axis = k;
-          b_q = q;
-          b_nl = lc;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (!axis_ok[k] || lc[k] == 0u || rc[k] == 0u) continue;
+          const float c = __fadd_rn(__fmul_rn(box_area_rn(llo[k], lhi[k]), __uint2float_rn(lw[k])),
+                                    __fmul_rn(box_area_rn(rlo[k], rhi[k]), __uint2float_rn(rw[k])));
+          if (!valid || c < cost) {
+            valid = true;
+            cost = c;
+            b_axis = k;
+            b_q = my_bin[k] + 1;
+            b_nl = lc[k];
+          }
         }
       }
       s_cost[warp][lane] = cost;
@@ -1270,15 +1283,16 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_top_small(TopArgs a) {
           const uint32_t sm = side ? rseg : lseg;
           float v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
           for (uint32_t m = sm; m; m &= m - 1u) {
-            const float* bj = s_box[warp][__ffs(m) - 1];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              v[q] = fminf(v[q], bj[q]);
-              v[3 + q] = fmaxf(v[3 + q], bj[3 + q]);
-            }
+            const float4 jlo = s_rec[warp][__ffs(m) - 1][0], jhi = s_rec[warp][__ffs(m) - 1][1];
+            v[0] = fminf(v[0], jlo.x);
+            v[1] = fminf(v[1], jlo.y);
+            v[2] = fminf(v[2], jlo.z);
+            v[3] = fmaxf(v[3], jhi.x);
+            v[4] = fmaxf(v[4], jhi.y);
+            v[5] = fmaxf(v[5], jhi.z);
           }
           for (int q = 0; q < 6; ++q) bx[side][q] = v[q];
-          ref[side] = __popc(sm) == 1 ? s_ref[warp][__ffs(sm) - 1] : s_slot[warp][k_new++];
+          ref[side] = __popc(sm) == 1 ? __float_as_uint(s_rec[warp][__ffs(sm) - 1][1].w) : s_slot[warp][k_new++];
           s_child[warp][lane][side] = ref[side];
         }
         write_top_node(a, seg_slot, bx, ref);
