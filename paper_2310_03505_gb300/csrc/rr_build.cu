@@ -620,6 +620,7 @@ __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (
 constexpr uint32_t kEncPosInf = 0xFF800000u, kEncNegInf = 0x007FFFFFu;   // enc_f(+inf), enc_f(-inf)
 constexpr int kBinWords = 8;   // per bin: clusters, weight, lo xyz, hi xyz (encoded)
 constexpr int kTopItems = 2;   // records per thread per round of a block pass
+constexpr int kBinCopy = 3 * kTopBins * kBinWords + 1;   // words per copy of a block task's bins (+1: copies in different banks)
 
 __device__ __forceinline__ void bins_clear(uint32_t* bins, int i0, int stride) {
   for (int i = i0; i < 3 * kTopBins; i += stride) {
@@ -733,11 +734,11 @@ __device__ __forceinline__ void write_top_node(const TopArgs& a, uint32_t slot, 
 // go to the warp-task list.  The cluster records move with the partition, so
 // every pass reads its task's records contiguously, kTopItems per thread.
 __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
-  __shared__ uint32_t s_bins[8][3 * kTopBins * kBinWords];   // one copy per 1 / 8 of the warps, summed into [0]
+  __shared__ uint32_t s_bins[8][kBinCopy];   // one copy per lane mod 8, summed into [0]
   __shared__ uint32_t s_cb[6], s_side[2][6], s_cside[2][6];
   __shared__ uint32_t s_task[4], s_stop, s_cont;
   __shared__ Split s_split[3];
-  __shared__ uint32_t s_wl[kTopBlock / 32], s_wr[kTopBlock / 32], s_base[2];
+  __shared__ uint32_t s_wl[2][kTopBlock / 32], s_wr[2][kTopBlock / 32];   // by round parity
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t C = a.ctr[kCtrClusters];
   if (C <= kTopSmall) return;   // no block task: the warp tasks do it all
@@ -799,7 +800,6 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
       s_side[0][tid] = s_cside[0][tid] = tid < 3 ? kEncPosInf : kEncNegInf;
       s_side[1][tid] = s_cside[1][tid] = tid < 3 ? kEncPosInf : kEncNegInf;
     }
-    if (tid < 2) s_base[tid] = 0u;
     __syncthreads();
     float cmin[3], scale[3];
     bool axis_ok[3];
@@ -810,13 +810,16 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
       scale[k] = axis_ok[k] ? __fdiv_rn((float)kTopBins, ext) : 0.0f;
     }
     // bins: each thread takes a contiguous chunk of the task (Morton order,
-    // so neighbours mostly share bins) and adds runs of one bin at a time
+    // so neighbours mostly share bins) and adds runs of one bin at a time to
+    // the copy of its lane mod 8: the lanes of a warp hold neighbouring chunks,
+    // mostly in the same bins, and same-address shared atomics of one warp
+    // serialise, so at most 4 lanes share an address
     if (axis_ok[0] || axis_ok[1] || axis_ok[2]) {
-      const uint32_t chunk = (n + kTopBlock - 1) / kTopBlock;
-      const uint32_t i0 = min(n, chunk * tid), i1 = min(n, i0 + chunk);
       int run_q[3] = {-1, -1, -1};
       uint32_t run_n[3] = {0u, 0u, 0u}, run_w[3] = {0u, 0u, 0u};
       float run_b[3][6];
+      const uint32_t chunk = (n + kTopBlock - 1) / kTopBlock;
+      const uint32_t i0 = min(n, chunk * tid), i1 = min(n, i0 + chunk);
       for (uint32_t ib = i0; ib < i1; ib += kTopItems) {
         float4 blo[kTopItems], bhi[kTopItems];
 #pragma unroll
@@ -827,45 +830,45 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
           }
 #pragma unroll
         for (int k = 0; k < kTopItems; ++k) {
-        if (ib + k >= i1) break;
-        const float4 lo = blo[k], hi = bhi[k];
-        const float3 cc = cl_centroid(lo, hi);
+          if (ib + k >= i1) break;
+          const float4 lo = blo[k], hi = bhi[k];
+          const float3 cc = cl_centroid(lo, hi);
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-          if (!axis_ok[ax]) continue;
-          const int q = top_bin(comp(cc, ax), cmin[ax], scale[ax]);
-          if (q != run_q[ax]) {
-            if (run_q[ax] >= 0) {
-              uint32_t* bb = s_bins[warp & 7] + kBinWords * (ax * kTopBins + run_q[ax]);
-              atomicAdd(&bb[0], run_n[ax]);
-              atomicAdd(&bb[1], run_w[ax]);
+          for (int ax = 0; ax < 3; ++ax) {
+            if (!axis_ok[ax]) continue;
+            const int q = top_bin(comp(cc, ax), cmin[ax], scale[ax]);
+            if (q != run_q[ax]) {
+              if (run_q[ax] >= 0) {
+                uint32_t* bb = s_bins[lane & 7] + kBinWords * (ax * kTopBins + run_q[ax]);
+                atomicAdd(&bb[0], run_n[ax]);
+                atomicAdd(&bb[1], run_w[ax]);
 #pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                atomicMin(&bb[2 + c], enc_f(run_b[ax][c]));
-                atomicMax(&bb[5 + c], enc_f(run_b[ax][3 + c]));
+                for (int c = 0; c < 3; ++c) {
+                  atomicMin(&bb[2 + c], enc_f(run_b[ax][c]));
+                  atomicMax(&bb[5 + c], enc_f(run_b[ax][3 + c]));
+                }
               }
+              run_q[ax] = q;
+              run_n[ax] = 0u;
+              run_w[ax] = 0u;
+              run_b[ax][0] = run_b[ax][1] = run_b[ax][2] = INFINITY;
+              run_b[ax][3] = run_b[ax][4] = run_b[ax][5] = -INFINITY;
             }
-            run_q[ax] = q;
-            run_n[ax] = 0u;
-            run_w[ax] = 0u;
-            run_b[ax][0] = run_b[ax][1] = run_b[ax][2] = INFINITY;
-            run_b[ax][3] = run_b[ax][4] = run_b[ax][5] = -INFINITY;
+            ++run_n[ax];
+            run_w[ax] += __float_as_uint(lo.w);
+            run_b[ax][0] = fminf(run_b[ax][0], lo.x);
+            run_b[ax][1] = fminf(run_b[ax][1], lo.y);
+            run_b[ax][2] = fminf(run_b[ax][2], lo.z);
+            run_b[ax][3] = fmaxf(run_b[ax][3], hi.x);
+            run_b[ax][4] = fmaxf(run_b[ax][4], hi.y);
+            run_b[ax][5] = fmaxf(run_b[ax][5], hi.z);
           }
-          ++run_n[ax];
-          run_w[ax] += __float_as_uint(lo.w);
-          run_b[ax][0] = fminf(run_b[ax][0], lo.x);
-          run_b[ax][1] = fminf(run_b[ax][1], lo.y);
-          run_b[ax][2] = fminf(run_b[ax][2], lo.z);
-          run_b[ax][3] = fmaxf(run_b[ax][3], hi.x);
-          run_b[ax][4] = fmaxf(run_b[ax][4], hi.y);
-          run_b[ax][5] = fmaxf(run_b[ax][5], hi.z);
-        }
         }
       }
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax)
         if (run_q[ax] >= 0) {
-          uint32_t* bb = s_bins[warp & 7] + kBinWords * (ax * kTopBins + run_q[ax]);
+          uint32_t* bb = s_bins[lane & 7] + kBinWords * (ax * kTopBins + run_q[ax]);
           atomicAdd(&bb[0], run_n[ax]);
           atomicAdd(&bb[1], run_w[ax]);
 #pragma unroll
@@ -876,7 +879,7 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
         }
     }
     __syncthreads();
-    // the warps' copies into copy 0: sums of counts and weights, min / max of
+    // the lanes' copies into copy 0: sums of counts and weights, min / max of
     // the (order-preserving) encoded bounds
     for (int i = tid; i < 3 * kTopBins * kBinWords; i += kTopBlock) {
       const int word = i % kBinWords;
@@ -905,15 +908,19 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
     }
     const float a_min = axis == 0 ? cmin[0] : (axis == 1 ? cmin[1] : cmin[2]);
     const float a_scale = axis == 0 ? scale[0] : (axis == 1 ? scale[1] : scale[2]);
-    // stable partition of the records into the other buffer
-    for (uint32_t t0 = 0; t0 < n; t0 += kTopItems * kTopBlock) {
+    // stable partition of the records into the other buffer; each thread
+    // keeps its sides' boxes and centroid bounds over all rounds, reduced once
+    float v[2][6] = {{INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY},
+                     {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY}};
+    float cv[2][6] = {{INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY},
+                      {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY}};
+    // one barrier a round: the warps' counts are kept by round parity, and
+    // every thread keeps the running offsets of both sides itself
+    uint32_t base_l = 0u, base_r = 0u, rnd = 0u;
+    for (uint32_t t0 = 0; t0 < n; t0 += kTopItems * kTopBlock, ++rnd) {
       const uint32_t i0 = t0 + kTopItems * tid;
       float4 lo[kTopItems], hi[kTopItems];
       uint32_t lmask = 0u, hmask = 0u;
-      float v[2][6] = {{INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY},
-                       {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY}};
-      float cv[2][6] = {{INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY},
-                        {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY}};
 #pragma unroll
       for (int k = 0; k < kTopItems; ++k)
         if (i0 + k < n) {
@@ -949,34 +956,6 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
         }
       }
       const uint32_t cl = __popc(lmask), cr = __popc(hmask & ~lmask);
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            const float o = __shfl_xor_sync(0xFFFFFFFFu, v[side][q], off);
-            v[side][q] = q < 3 ? fminf(v[side][q], o) : fmaxf(v[side][q], o);
-          }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            const float o = __shfl_xor_sync(0xFFFFFFFFu, cv[side][q], off);
-            cv[side][q] = q < 3 ? fminf(cv[side][q], o) : fmaxf(cv[side][q], o);
-          }
-        if (lane == 0 && v[side][0] <= v[side][3])
-#pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            if (q < 3) {
-              atomicMin(&s_side[side][q], enc_f(v[side][q]));
-              atomicMin(&s_cside[side][q], enc_f(cv[side][q]));
-            } else {
-              atomicMax(&s_side[side][q], enc_f(v[side][q]));
-              atomicMax(&s_cside[side][q], enc_f(cv[side][q]));
-            }
-          }
-      }
       // exclusive offsets of the threads' left and right counts
       uint32_t xl = cl, xr = cr;
       for (int off = 1; off < 32; off <<= 1) {
@@ -986,19 +965,21 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
           xr += yr;
         }
       }
+      const uint32_t par = rnd & 1u;
       if (lane == 31) {
-        s_wl[warp] = xl;
-        s_wr[warp] = xr;
+        s_wl[par][warp] = xl;
+        s_wr[par][warp] = xr;
       }
       __syncthreads();
-      uint32_t offl = s_base[0] + xl - cl, offr = s_base[1] + xr - cr, totl = 0, totr = 0;
+      uint32_t offl = base_l + xl - cl, offr = base_r + xr - cr, totl = 0, totr = 0;
       for (int w = 0; w < kTopBlock / 32; ++w) {
+        const uint32_t wl = s_wl[par][w], wr = s_wr[par][w];
         if (w < warp) {
-          offl += s_wl[w];
-          offr += s_wr[w];
+          offl += wl;
+          offr += wr;
         }
-        totl += s_wl[w];
-        totr += s_wr[w];
+        totl += wl;
+        totr += wr;
       }
 #pragma unroll
       for (int k = 0; k < kTopItems; ++k) {
@@ -1014,12 +995,31 @@ __global__ void __launch_bounds__(kTopBlock) k_top_sah(TopArgs a) {
           atomicOr(&a.misc[6], kErrTopBuild);
         }
       }
-      __syncthreads();
-      if (tid == 0) {
-        s_base[0] += totl;
-        s_base[1] += totr;
-      }
-      __syncthreads();
+      base_l += totl;
+      base_r += totr;
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const float o = __shfl_xor_sync(0xFFFFFFFFu, v[side][q], off);
+          const float oc = __shfl_xor_sync(0xFFFFFFFFu, cv[side][q], off);
+          v[side][q] = q < 3 ? fminf(v[side][q], o) : fmaxf(v[side][q], o);
+          cv[side][q] = q < 3 ? fminf(cv[side][q], oc) : fmaxf(cv[side][q], oc);
+        }
+      if (lane == 0 && v[side][0] <= v[side][3])
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          if (q < 3) {
+            atomicMin(&s_side[side][q], enc_f(v[side][q]));
+            atomicMin(&s_cside[side][q], enc_f(cv[side][q]));
+          } else {
+            atomicMax(&s_side[side][q], enc_f(v[side][q]));
+            atomicMax(&s_cside[side][q], enc_f(cv[side][q]));
+          }
+        }
     }
     __threadfence();   // the new order is visible before the children are published
     __syncthreads();
