@@ -200,6 +200,31 @@ const char* rr_last_error(void);
    legacy default stream). */
 int rr_set_stream(void* cuda_stream);
 
+/* Failure detection without a GPU fault.  Every spin-wait in this library's
+   kernels is bounded: when the flag it waits for is not set within about a
+   second, the kernel raises an error bit, stops waiting and returns, the
+   call that launched it reports RR_ERR_TIMEOUT (or a failed build), and the
+   CUDA context stays usable.  This call proves it for one wait: it runs the
+   real kernel (or device function) of that wait, on one block, over
+   counters arranged so that the awaited flag is never set, on its own
+   scratch memory (no scene involved):
+     RR_WAIT_TOP_TASK     a block task of the SAH-top build (k_top_sah) waits
+                          for a task number that is never published while one
+                          task stays pending;
+     RR_WAIT_WIDE_NODE    the wide-BVH collapse (k_wide_alloc) waits for a
+                          wide node that is allocated but never published;
+     RR_WAIT_SHADE_PREFIX the decoupled look-back of the shading pass waits
+                          for a preceding tile that never publishes.
+   Returns RR_ERR_TIMEOUT when the wait gave up and raised its error bit (the
+   expected outcome), RR_ERR_CUDA if the wait ended otherwise or a CUDA call
+   failed, RR_ERR_INVALID_ARG for an unknown `which`.  *waited_ms (may be
+   NULL) receives the wall time of the call.  Blocking; runs on the stream of
+   rr_set_stream. */
+#define RR_WAIT_TOP_TASK 0u
+#define RR_WAIT_WIDE_NODE 1u
+#define RR_WAIT_SHADE_PREFIX 2u
+int rr_selftest_wait(uint32_t which, double* waited_ms);
+
 /* ---------------------------------------------------------------------- */
 /* scene: ingest + LBVH (Sec. III-D: the scene mesh with per-triangle      */
 /* materials; the hierarchy is this library's own, 30-bit Morton codes,    */

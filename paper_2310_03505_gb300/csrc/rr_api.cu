@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -253,6 +254,32 @@ const char* rr_last_error(void) { return t_error.c_str(); }
 int rr_set_stream(void* cuda_stream) {
   t_stream = (cudaStream_t)cuda_stream;
   return RR_OK;
+}
+
+int rr_selftest_wait(uint32_t which, double* waited_ms) {
+  if (which > RR_WAIT_SHADE_PREFIX) return fail(RR_ERR_INVALID_ARG, "rr_selftest_wait: unknown wait");
+  const cudaStream_t st = t_stream;
+  const size_t bytes = 256 + sizeof(ScanCounters);   // the largest arrangement, zeroed
+  void* scratch = nullptr;
+  RR_CHECK_CUDA(cudaMalloc(&scratch, bytes), "allocating the self-test scratch");
+  const auto t0 = std::chrono::steady_clock::now();
+  bool gave_up = false;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, bytes, st);
+  if (e == cudaSuccess) {
+    if (which == RR_WAIT_TOP_TASK) e = selftest_top_wait(static_cast<uint32_t*>(scratch), st, &gave_up);
+    else if (which == RR_WAIT_WIDE_NODE) e = selftest_wide_wait(static_cast<uint32_t*>(scratch), st, &gave_up);
+    else e = selftest_look_back_wait(scratch, st, &gave_up);
+  }
+  const auto t1 = std::chrono::steady_clock::now();
+  if (waited_ms) *waited_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(scratch);
+    return cuda_fail(e, "running the self-test wait");
+  }
+  RR_CHECK_CUDA(cudaFree(scratch), "freeing the self-test scratch");
+  if (!gave_up) return fail(RR_ERR_CUDA, "rr_selftest_wait: the wait ended without its error bit");
+  return fail(RR_ERR_TIMEOUT, "a bounded device wait gave up (self-test: expected)");
 }
 
 int rr_scene_destroy(rr_scene* s) {

@@ -21,6 +21,7 @@
 // Leaves are the triangles in sorted order: tri[3j..3j+2] = v0, v1, v2 with
 // v0.w = original triangle id, v1.w = material id (bit patterns).
 #include <algorithm>
+#include <cstring>
 #include <cuda/atomic>
 #include <cuda_runtime.h>
 
@@ -1900,6 +1901,48 @@ cudaError_t build_wide(rr_scene* s, cudaStream_t st) {
   k_wide_write<<<std::min<uint32_t>((s->wcap + 127u) / 128u, 8u * (uint32_t)sms), 128, 0, st>>>(
       n, s->d_cut, s->d_nbox, s->d_tri, s->d_wrec, s->d_wctr, s->wcap, s->d_wnodes, s->d_wtri);
   return cudaGetLastError();
+}
+
+// Failure detection: the bounded waits of the top build and of the wide
+// collapse, each run by its own kernel on counters arranged so that the flag
+// it waits for is never set.  `scratch` holds at least 32 zeroed words.
+// Returns whether the wait gave up and raised its error bit.
+cudaError_t selftest_top_wait(uint32_t* scratch, cudaStream_t st, bool* gave_up) {
+  // block task 0 taken and never published, one task pending forever:
+  // C = 64 clusters, the marked top part consistent (C - 2 slots after the root)
+  uint32_t* ctr = scratch;        // [8]
+  uint32_t* ready = scratch + 8;  // [1]
+  uint32_t* misc = scratch + 16;  // [8]
+  const uint32_t init[8] = {0u, 0u, 62u, 64u, 1u, 1u, 0u, 0u};   // head, slots, marked, clusters, tasks, pending, small, small head
+  RR_TRY(cudaMemcpyAsync(ctr, init, sizeof init, cudaMemcpyHostToDevice, st));
+  TopArgs a;
+  memset(&a, 0, sizeof a);
+  a.ready = ready;
+  a.ctr = ctr;
+  a.misc = misc;
+  a.n = 64u;
+  k_top_sah<<<1, kTopBlock, 0, st>>>(a);
+  RR_TRY(cudaGetLastError());
+  uint32_t err = 0;
+  RR_TRY(cudaMemcpyAsync(&err, misc + 6, sizeof err, cudaMemcpyDeviceToHost, st));
+  RR_TRY(cudaStreamSynchronize(st));
+  *gave_up = (err & kErrTopBuild) != 0u;
+  return cudaSuccess;
+}
+
+cudaError_t selftest_wide_wait(uint32_t* scratch, cudaStream_t st, bool* gave_up) {
+  // ticket 1 handed out, wide node 1 allocated but never published (epoch 1)
+  uint32_t* wctr = scratch;                                                       // [8]
+  unsigned long long* wsrc = reinterpret_cast<unsigned long long*>(scratch + 8);   // [2]
+  const uint32_t init[8] = {1u, 2u, 0u, 0u, 0u, 0u, 0u, 0u};   // ticket, allocated, done, triangles, error
+  RR_TRY(cudaMemcpyAsync(wctr, init, sizeof init, cudaMemcpyHostToDevice, st));
+  k_wide_alloc<<<1, 1, 0, st>>>(1u, nullptr, wsrc, nullptr, wctr, 1u, 2u);
+  RR_TRY(cudaGetLastError());
+  uint32_t err = 0;
+  RR_TRY(cudaMemcpyAsync(&err, wctr + 4, sizeof err, cudaMemcpyDeviceToHost, st));
+  RR_TRY(cudaStreamSynchronize(st));
+  *gave_up = (err & kWideErr) != 0u;
+  return cudaSuccess;
 }
 
 }  // namespace rr_host

@@ -158,6 +158,12 @@ cudaError_t launch_query(const rr::ScanArgs& a, uint32_t bounce, bool any, const
 cudaError_t launch_vis_prep(const rr::ScanArgs& a, uint32_t bounce, cudaStream_t st);
 cudaError_t launch_shade(const rr::ScanArgs& a, uint32_t bounce, cudaStream_t st);
 
+// failure detection (rr_selftest_wait): each runs one bounded device wait on
+// a flag that nothing sets and reports whether it gave up as designed
+cudaError_t selftest_top_wait(uint32_t* scratch, cudaStream_t st, bool* gave_up);    // rr_build.cu
+cudaError_t selftest_wide_wait(uint32_t* scratch, cudaStream_t st, bool* gave_up);   // rr_build.cu
+cudaError_t selftest_look_back_wait(void* scratch, cudaStream_t st, bool* gave_up);  // rr_trace.cu
+
 // rr_image.cu
 void init_image_attrs();
 cudaError_t launch_image(const rr::ScanArgs& a, bool pattern, cudaStream_t st);

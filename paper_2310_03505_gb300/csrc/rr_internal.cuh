@@ -19,7 +19,7 @@ constexpr uint32_t kLobeEq5 = 0, kLobeCookTorrance = 1, kLobeTable = 2;
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kHalfPi = 1.57079632679489661923f;
 constexpr float kC0 = 299792458.0f;   // speed of light (m/s)
-constexpr uint32_t kSpinLimit = 1u << 24;  // bounded device waits
+constexpr uint32_t kSpinLimit = 1u << 21;  // bounded device waits (each spin re-reads a flag from L2: about a second)
 
 // status bits of the sticky device error word
 constexpr uint32_t kErrCapacityRays = 1u;

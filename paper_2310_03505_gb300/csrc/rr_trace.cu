@@ -21,6 +21,7 @@
 // sequence of launches with no host round trip between bounces.
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <type_traits>
 
 #include "rr_host.h"
@@ -675,6 +676,10 @@ __device__ __forceinline__ uint2 look_back(const ScanArgs& a, uint32_t tile, uin
   return make_uint2(ex_k, ex_r);
 }
 
+// failure detection: one warp runs the look-back of tile 1 while tile 0
+// never publishes (its status word stays 0), so the bounded wait gives up
+__global__ void k_selftest_look_back(ScanArgs a) { look_back(a, 1u, 0u, 0u); }
+
 // ---------------------------------------------------------------------------
 // shade
 __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t bounce) {
@@ -1008,6 +1013,24 @@ cudaError_t launch_shade(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
   init_dims();
   k_shade<<<g_num_sms * g_shade_occ, kShadeBlock, 0, st>>>(a, bounce);
   return cudaGetLastError();
+}
+
+cudaError_t selftest_look_back_wait(void* scratch, cudaStream_t st, bool* gave_up) {
+  // scratch: a zeroed ScanCounters, then two zeroed tile status words
+  ScanArgs a;
+  memset(&a, 0, sizeof a);
+  a.ctr = static_cast<ScanCounters*>(scratch);
+  a.tile_status = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + sizeof(ScanCounters));
+  k_selftest_look_back<<<1, 32, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  uint32_t err = 0;
+  e = cudaMemcpyAsync(&err, &a.ctr->error, sizeof err, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  *gave_up = (err & kErrTimeout) != 0u;
+  return cudaSuccess;
 }
 
 }  // namespace rr_host

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "librr.so")
 RR_OK, RR_ERR_INVALID_ARG, RR_ERR_OOM, RR_ERR_CAPACITY, RR_ERR_TIMEOUT, RR_ERR_CUDA, RR_ERR_BUSY = range(7)
 RR_MULTIPATH, RR_REFRACTION, RR_SPECKLE, RR_NOISE, RR_COUNT_TRAVERSAL, RR_NOISE_PERLIN = 1, 2, 4, 8, 16, 32
 RR_MAT_PERFECT_CONDUCTOR, RR_MAT_COOK_TORRANCE, RR_MAT_TABULATED_LOBE = 1, 2, 4
+RR_WAIT_TOP_TASK, RR_WAIT_WIDE_NODE, RR_WAIT_SHADE_PREFIX = 0, 1, 2
 RR_LOBE_SAMPLES = 4097
 RR_NO_HIT = 0xFFFFFFFF
 RR_K_RAYGEN, RR_K_TRACE, RR_K_SHADE, RR_K_IMAGE, RR_K_BUILD, RR_K_VIS, RR_K_COUNT = range(7)
@@ -120,6 +121,7 @@ SIGNATURES = {
     "rr_version": ([], C.c_int),
     "rr_last_error": ([], C.c_char_p),
     "rr_set_stream": ([_P], C.c_int),
+    "rr_selftest_wait": ([C.c_uint32, C.POINTER(C.c_double)], C.c_int),
     "rr_scene_create": ([_P, C.c_uint32, _P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(_P)], C.c_int),
     "rr_scene_destroy": ([_P], C.c_int),
     "rr_scene_update_vertices": ([_P, _P], C.c_int),
@@ -246,6 +248,16 @@ def rr_last_error() -> str:
 
 def rr_set_stream(stream_handle) -> None:
     _check(load().rr_set_stream(C.c_void_p(stream_handle)))
+
+
+def rr_selftest_wait(which: int):
+    """Run one of the library's bounded device waits on a flag that nothing
+    sets.  Returns (status, wall ms); RR_ERR_TIMEOUT is the expected status
+    (the wait gave up and raised its error bit).  Never raises on a status."""
+    _use_torch_stream()
+    ms = C.c_double(0.0)
+    rc = load().rr_selftest_wait(C.c_uint32(which), C.byref(ms))
+    return rc, ms.value
 
 
 def rr_scene_create(vertices, triangles, material_ids, materials):
