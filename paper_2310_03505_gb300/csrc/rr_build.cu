@@ -129,8 +129,10 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
 }
 
 // a2: code = x9 y9 z9 x8 y8 z8 ... x0 y0 z0 of the quantised centroid
+// also counts the first sort pass's digits per tile (hist0, zeroed before)
 __global__ void k_morton(const float4* __restrict__ centroid, const uint32_t* __restrict__ misc, uint32_t nt,
-                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t tiles,
+                         uint32_t* __restrict__ hist0) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nt) return;
   const float4 c = centroid[i];
@@ -142,26 +144,18 @@ __global__ void k_morton(const float4* __restrict__ centroid, const uint32_t* __
     const float x = ext > 0.0f ? (cc[k] - lo) / ext : 0.0f;
     q[k] = (uint32_t)fminf(floorf(x * 1024.0f), 1023.0f);
   }
-  keys[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+  const uint32_t key = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+  keys[i] = key;
   vals[i] = i;
+  atomicAdd(&hist0[(key & 255u) * tiles + i / kSortTile], 1u);
 }
 
 // ---------------------------------------------------------------------------
-// a3: LSD radix sort, 8-bit digits.  hist is digit major: hist[d * tiles + t].
-__global__ void k_radix_hist(const uint32_t* __restrict__ keys, uint32_t n, int shift, uint32_t tiles,
-                             uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const uint32_t base = blockIdx.x * kSortTile;
-#pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const uint32_t i = base + r * kSortBlock + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
-}
+// a3: LSD radix sort, 8-bit digits, stable.  Each pass's digit counts per
+// tile of its input (digit major: hist[d * tiles + t]) are counted while that
+// input is written -- by k_morton for the first pass, by the previous pass's
+// scatter (a key's tile in the next pass is its output position / tile)
+// for the others -- then scanned by k_scan_single into the scatter offsets.
 
 // exclusive scan of n counters (n a multiple of 4, 16-byte aligned) with one
 // block.  Up to 8 uint4 per thread: each thread loads its contiguous run at
@@ -262,25 +256,42 @@ __global__ void k_scan_single(uint32_t* __restrict__ data, uint32_t n) {
   }
 }
 
-// stable scatter: keys of a tile are ranked in index order (round, warp, lane)
+// stable scatter: keys of a tile are ranked in index order (round, warp, lane).
+// The tile's keys and values are loaded up front (one round trip instead of
+// one per round); lanes with the same digit are found with 8 ballots.  With
+// hist_next, each key is also counted for the next pass (digit shift + 8).
 __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                 uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n, int shift,
-                                uint32_t tiles, const uint32_t* __restrict__ offs) {
+                                uint32_t tiles, const uint32_t* __restrict__ offs, uint32_t* __restrict__ hist_next) {
   __shared__ uint32_t s_base[256];
   __shared__ uint32_t s_warp[kSortBlock / 32][256];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   s_base[t] = offs[t * tiles + blockIdx.x];
   const uint32_t base = blockIdx.x * kSortTile;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t keys[kSortItems], vals[kSortItems];
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const uint32_t i = base + r * kSortBlock + t;
+    keys[r] = i < n ? kin[i] : 0u;
+    vals[r] = i < n ? vin[i] : 0u;
+  }
+#pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     for (int w = 0; w < kSortBlock / 32; ++w) s_warp[w][t] = 0;
     __syncthreads();
     const uint32_t i = base + r * kSortBlock + t;
     const bool valid = i < n;
-    const uint32_t key = valid ? kin[i] : 0u;
+    const uint32_t key = keys[r];
     const uint32_t digit = (key >> shift) & 255u;
-    const uint32_t tag = valid ? digit : 256u + (uint32_t)lane;   // invalid lanes match only themselves
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, tag);
+    // lanes holding the same digit: agree on all 8 bits; invalid lanes
+    // (only in the last tile, always the highest lanes) match nobody
+    uint32_t peers = __ballot_sync(0xFFFFFFFFu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const uint32_t ones = __ballot_sync(0xFFFFFFFFu, (digit >> b) & 1u);
+      peers &= ((digit >> b) & 1u) ? ones : ~ones;
+    }
     const uint32_t rank = __popc(peers & lt_mask);
     if (valid && rank == 0) s_warp[warp][digit] = __popc(peers);
     __syncthreads();
@@ -294,7 +305,8 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t
     if (valid) {
       const uint32_t pos = s_base[digit] + s_warp[warp][digit] + rank;
       kout[pos] = key;
-      vout[pos] = vin[i];
+      vout[pos] = vals[r];
+      if (hist_next) atomicAdd(&hist_next[((key >> (shift + 8)) & 255u) * tiles + pos / kSortTile], 1u);
     }
     __syncthreads();
     s_base[t] += acc;
@@ -1721,7 +1733,7 @@ cudaError_t build_alloc(rr_scene* s) {
     RR_TRY(alloc((void**)&s->d_keys[k], T * sizeof(uint32_t)));
     RR_TRY(alloc((void**)&s->d_vals[k], T * sizeof(uint32_t)));
   }
-  RR_TRY(alloc((void**)&s->d_hist, (size_t)256 * (s->sort_tiles ? s->sort_tiles : 1) * sizeof(uint32_t)));
+  RR_TRY(alloc((void**)&s->d_hist, (size_t)4 * 256 * (s->sort_tiles ? s->sort_tiles : 1) * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_parent, (T ? 2 * T - 1 : 1) * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_child, (T > 1 ? T - 1 : 1) * 2 * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_nbox, (T ? 2 * T - 1 : 1) * 6 * sizeof(float)));
@@ -1840,21 +1852,24 @@ cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth) {
   const int B = 256;
   const uint32_t g = (n + B - 1) / B;
   const bool sah_top = s->cfg.bvh_build == RR_BVH_SAH_TOP && n > kClusterMax;
-  s->launches += ((n > 1) ? (with_depth ? 18u : 17u) : 15u) + (sah_top ? 6u : 0u);
+  s->launches += ((n > 1) ? (with_depth ? 14u : 13u) : 11u) + (sah_top ? 6u : 0u);
   k_ingest<<<g, B, 0, st>>>(s->d_vtx, s->d_idx, s->d_mat_id, s->nv, n, s->nm, s->d_centroid, s->d_misc);
   RR_TRY(cudaGetLastError());
-  k_morton<<<g, B, 0, st>>>(s->d_centroid, s->d_misc, n, s->d_keys[0], s->d_vals[0]);
+  // the four passes' digit counts per tile, zeroed, counted as each pass's input is written
+  const size_t hist_words = (size_t)256 * s->sort_tiles;
+  RR_TRY(cudaMemsetAsync(s->d_hist, 0, 4 * hist_words * sizeof(uint32_t), st));
+  k_morton<<<g, B, 0, st>>>(s->d_centroid, s->d_misc, n, s->d_keys[0], s->d_vals[0], s->sort_tiles, s->d_hist);
   RR_TRY(cudaGetLastError());
   // 30-bit keys: passes over bits 0-7, 8-15, 16-23, 24-29
   int cur = 0;
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 8 * pass;
-    k_radix_hist<<<s->sort_tiles, kSortBlock, 0, st>>>(s->d_keys[cur], n, shift, s->sort_tiles, s->d_hist);
-    RR_TRY(cudaGetLastError());
-    k_scan_single<<<1, 1024, 0, st>>>(s->d_hist, 256u * s->sort_tiles);
+    uint32_t* hist = s->d_hist + pass * hist_words;
+    k_scan_single<<<1, 1024, 0, st>>>(hist, (uint32_t)hist_words);
     RR_TRY(cudaGetLastError());
     k_radix_scatter<<<s->sort_tiles, kSortBlock, 0, st>>>(s->d_keys[cur], s->d_vals[cur], s->d_keys[cur ^ 1],
-                                                          s->d_vals[cur ^ 1], n, shift, s->sort_tiles, s->d_hist);
+                                                          s->d_vals[cur ^ 1], n, shift, s->sort_tiles, hist,
+                                                          pass < 3 ? hist + hist_words : nullptr);
     RR_TRY(cudaGetLastError());
     cur ^= 1;
   }

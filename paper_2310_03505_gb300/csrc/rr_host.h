@@ -100,7 +100,7 @@ struct rr_scene {
   float4* d_centroid = nullptr;    // [T]
   uint32_t* d_keys[2] = {nullptr, nullptr};
   uint32_t* d_vals[2] = {nullptr, nullptr};
-  uint32_t* d_hist = nullptr;      // [256][tiles]
+  uint32_t* d_hist = nullptr;      // [4 sort passes][256][tiles]
   uint32_t* d_parent = nullptr;    // [2T-1]
   uint32_t* d_child = nullptr;     // [T-1][2]
   float* d_nbox = nullptr;         // [2T-1][6]
