@@ -390,29 +390,58 @@ __device__ __forceinline__ uint32_t node_slot(uint32_t c, uint32_t n) {
 // stops and the second merges both child boxes (they are final by then).
 // The walker carries the box of the child it comes from, so it reads only
 // the sibling's; the node's children and parent are read alongside the
-// arrival atomic (they do not depend on it).
-__global__ void k_refit(uint32_t n, const uint32_t* __restrict__ child, const uint32_t* __restrict__ parent,
-                        uint32_t* __restrict__ visit, float* __restrict__ nbox, float4* __restrict__ nodes) {
-  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+// arrival atomic (they do not depend on it).  A node whose leaf range lies
+// inside the block's own leaves (so does its index: a Karras node is one end
+// of its range) is merged through shared memory -- arrival counter and child
+// boxes -- so the bottom levels of every walk cost no L2 round trips; the
+// others through the global counters and nbox.
+constexpr int kRefitBlock = 256;
+__global__ void __launch_bounds__(kRefitBlock) k_refit(uint32_t n, const uint32_t* __restrict__ child,
+                                                       const uint32_t* __restrict__ parent,
+                                                       const uint2* __restrict__ range, uint32_t* __restrict__ visit,
+                                                       float* __restrict__ nbox, float4* __restrict__ nodes) {
+  __shared__ float s_box[2][kRefitBlock][6];   // [0] the block's leaves, [1] its local internal nodes
+  __shared__ uint32_t s_visit[kRefitBlock];
+  const uint32_t base = blockIdx.x * kRefitBlock, end = min(base + kRefitBlock, n);
+  const uint32_t j = base + threadIdx.x;
+  s_visit[threadIdx.x] = 0u;
+  float own[6];
+  if (j < n)
+    for (int k = 0; k < 6; ++k) {
+      own[k] = __ldcg(nbox + 6 * (size_t)(n - 1 + j) + k);
+      s_box[0][threadIdx.x][k] = own[k];
+    }
+  __syncthreads();
   if (j >= n) return;
   uint32_t cur = j | kLeafBit;
-  float own[6];
-  for (int k = 0; k < 6; ++k) own[k] = __ldcg(nbox + 6 * (size_t)(n - 1 + j) + k);
   uint32_t p = __ldg(&parent[n - 1 + j]);
   while (p != kNone) {
     const uint32_t c0 = __ldg(&child[2 * p]), c1 = __ldg(&child[2 * p + 1]);
     const uint32_t pp = __ldg(&parent[p]);
-    // acquire-release: the second arrival sees the first one's box
-    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> cnt(visit[p]);
-    if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == 0u) return;
+    const uint2 rg = __ldg(&range[p]);
+    const bool local = rg.x >= base && rg.y < end;
     const bool first_is_own = c0 == cur;
-    const float* sp = nbox + 6 * (size_t)node_slot(first_is_own ? c1 : c0, n);
-    float sib[6];
-    for (int k = 0; k < 6; ++k) sib[k] = __ldcg(sp + k);
+    const uint32_t sib = first_is_own ? c1 : c0;
+    float sb[6];
+    if (local) {
+      // fence - atomic - fence: the sibling's box, written before its
+      // walker arrived, is visible to the second arrival
+      __threadfence_block();
+      if (atomicAdd(&s_visit[p - base], 1u) == 0u) return;
+      __threadfence_block();
+      const float* q = (sib & kLeafBit) ? s_box[0][(sib & ~kLeafBit) - base] : s_box[1][sib - base];
+      for (int k = 0; k < 6; ++k) sb[k] = q[k];
+    } else {
+      // acquire-release: the second arrival sees the first one's box
+      cuda::atomic_ref<uint32_t, cuda::thread_scope_device> cnt(visit[p]);
+      if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == 0u) return;
+      const float* q = nbox + 6 * (size_t)node_slot(sib, n);
+      for (int k = 0; k < 6; ++k) sb[k] = __ldcg(q + k);
+    }
     float b0[6], b1[6];
     for (int k = 0; k < 6; ++k) {
-      b0[k] = first_is_own ? own[k] : sib[k];
-      b1[k] = first_is_own ? sib[k] : own[k];
+      b0[k] = first_is_own ? own[k] : sb[k];
+      b1[k] = first_is_own ? sb[k] : own[k];
     }
     float4* nd = nodes + 4 * (size_t)p;
     nd[0] = make_float4(b0[0], b0[3], b0[1], b0[4]);
@@ -426,6 +455,8 @@ __global__ void k_refit(uint32_t n, const uint32_t* __restrict__ child, const ui
       __stcg(bp + k, own[k]);
       __stcg(bp + 3 + k, own[3 + k]);
     }
+    if (local)
+      for (int k = 0; k < 6; ++k) s_box[1][p - base][k] = own[k];
     cur = p;
     p = pp;
   }
@@ -1880,7 +1911,8 @@ cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth) {
     k_karras<<<(n - 1 + B - 1) / B, B, 0, st>>>(s->d_keys[cur], (int)n, s->d_child, s->d_parent, s->d_visit,
                                                 s->d_range);
     RR_TRY(cudaGetLastError());
-    k_refit<<<g, B, 0, st>>>(n, s->d_child, s->d_parent, s->d_visit, s->d_nbox, s->d_nodes);
+    k_refit<<<(n + kRefitBlock - 1) / kRefitBlock, kRefitBlock, 0, st>>>(n, s->d_child, s->d_parent, s->d_range,
+                                                                           s->d_visit, s->d_nbox, s->d_nodes);
     RR_TRY(cudaGetLastError());
     if (sah_top) RR_TRY(build_sah_top(s, st));
     if (with_depth) {
