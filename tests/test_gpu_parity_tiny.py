@@ -65,14 +65,14 @@ def test_tiny_parity_lobes(rrlib, variant):
         rr.rr_scene_destroy(h)
 
 
-def check_parity(sc, pz, params, h):
+def check_parity(sc, pz, params, h, max_flagged=0.02, seg_capacity=None):
     ora = P.oracle_scan(sc, pz, params)
     flags = ora["flags"]
-    assert flags.mean() < 0.02, f"{flags.sum()} of {flags.size} rays flagged"
+    assert flags.mean() < max_flagged, f"{flags.sum()} of {flags.size} rays flagged"
     # ray paths and hit distances (no mask: every ray traced)
-    img_all, segs, tal = P.gpu_debug(h, pz, params)
+    img_all, segs, tal = P.gpu_debug(h, pz, params, seg_capacity=seg_capacity)
     n, bad, max_rel = P.compare_paths(segs, ora["segments"], flags, range(params["n_azimuth"]))
-    assert n > 0.95 * flags.size
+    assert n >= (~flags.astype(bool)).sum()
     assert not bad, f"{len(bad)} mismatches, first: {bad[:5]}"
     assert len(segs) == len(ora["segments"]) or flags.any()
     ebad = P.compare_segment_energies(segs, ora["segments"], flags, range(params["n_azimuth"]))
@@ -89,11 +89,54 @@ def check_parity(sc, pz, params, h):
         raise AssertionError(f"tallies of ray {(az, k)}: gpu {tal[worst]} oracle {ora['tallies'][worst]}\n"
                              f"gpu segments {g}\noracle segments {o}")
     # image with the flagged rays masked on both sides
-    img, _, _ = P.gpu_debug(h, pz, params, mask=flags)
+    img, _, _ = P.gpu_debug(h, pz, params, mask=flags, seg_capacity=seg_capacity)
     slack = P.slack_after_post(ora, params)
     excess, mx = P.image_excess(img, ora["image_masked"], slack)
     assert mx > 0
     assert excess <= P.IMG_REL, f"image excess {excess:.3g} of max {mx:.3g}"
+
+
+def test_tiny_parity_at_the_bounce_and_bin_limits(tiny_scene):
+    """The largest path depth and image the ABI accepts: RR_MAX_BOUNCES
+    reflections per path (refraction off, so each hit spawns one child and
+    the tree stays one path per ray) into RR_MAX_BINS range bins (717 m of
+    range: no path is cut by the range limit), every ray of 64 columns."""
+    sc, pz, params, h = tiny_scene
+    params = scenes.sensor(**{**params, "n_azimuth": 64, "max_bounces": 16, "n_bins": 16384,
+                              "refraction": False})
+    # one path per ray: at most 16 segments each
+    check_parity(sc, pz, params, h, max_flagged=0.1, seg_capacity=2 * 64 * 8 * 16)
+
+
+def test_tiny_parity_at_the_ray_limit(tiny_scene):
+    """RR_MAX_RAYS_PER_BEAM (65,535) rays in each of 2 beams: the GPU traces
+    all 131,070 initial rays; the oracle traces every 257th ray of both
+    columns (255 rays with all their bounces), compared ray by ray, segment
+    by segment and, with every other ray masked on the GPU, bin by bin;
+    energy is conserved for every initial ray."""
+    sc, pz, params, h = tiny_scene
+    stride = 257
+    params = scenes.sensor(**{**params, "n_azimuth": 2, "rays_per_beam": 65535})
+    cols = [0, 1]
+    ns = params["rays_per_beam"]
+    ora = P.oracle_scan(sc, pz, {**params, "ray_stride": stride}, az_list=cols)
+    keep = np.arange(ns) % stride == 0
+    flags = ora["flags"].astype(bool)
+    skip = flags | ~keep[None, :]
+    assert flags[:, keep].mean() < 0.05
+    img_all, segs, tal = P.gpu_debug(h, pz, params, seg_capacity=4 << 20)
+    segs = segs[segs["k"] % stride == 0]
+    n, bad, _ = P.compare_paths(segs, ora["segments"], skip.astype(np.uint8), cols)
+    assert n == int((~skip).sum()) > 400
+    assert not bad, f"{len(bad)} mismatches of {n} rays, first: {bad[:5]}"
+    ebad = P.compare_segment_energies(segs, ora["segments"], skip.astype(np.uint8), cols)
+    assert not ebad, f"{len(ebad)} energy mismatches, first: {ebad[:3]}"
+    img, _, _ = P.gpu_debug(h, pz, params, mask=skip.astype(np.uint8), seg_capacity=4 << 20)
+    slack = P.slack_after_post(ora, params, cols)
+    excess, mx = P.image_excess(img, ora["image_masked"], slack)
+    assert mx > 0
+    assert excess <= P.IMG_REL, f"image excess {excess:.3g} of max {mx:.3g}"
+    assert np.max(np.abs(tal.sum(-1) - 1.0 / ns)) < 1e-4 / ns
 
 
 def test_tiny_scan_entry_points_agree(tiny_scene):
