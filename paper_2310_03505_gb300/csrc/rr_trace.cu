@@ -240,13 +240,7 @@ __device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const Scan
   const uint32_t node = s.node;
   if (!(node & kLeafBit)) {
     if (count) ++n_nodes;
-    // depth-first traversal of a tree visits each of its n_tris - 1 internal
-    // nodes at most once: more visits mean a malformed hierarchy
-    if (++s.visits > a.n_tris) {
-      atomicOr(&a.ctr->error, kErrBvh);
-      s.node = kNone;
-      return;
-    }
+    ++s.visits;   // bounded where the query loop looks at its lanes
     const float3 o = s.w.o, id = s.id;
     const float4* np = a.nodes + 4 * (size_t)node;
     const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
@@ -330,11 +324,7 @@ __device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs&
       return;
     }
     if (count) ++n_nodes;
-    if (++s.visits > a.n_tris) {   // more visits than wide nodes: a malformed hierarchy
-      atomicOr(&a.ctr->error, kErrBvh);
-      s.node = kNone;
-      return;
-    }
+    ++s.visits;   // bounded where the query loop looks at its lanes
     const float3 o = s.w.o, id = s.id;
     const bool neg_x = id.x < 0.0f, neg_y = id.y < 0.0f, neg_z = id.z < 0.0f;
     const uint4* np = reinterpret_cast<const uint4*>(a.nodes) + kWideNodeWords * (size_t)node;
@@ -424,7 +414,9 @@ __device__ __forceinline__ float rx_weight(const ScanDesc* sd, uint32_t az, floa
 // kSteps steps lets a lane whose query ended idle for at most kSteps steps
 // (campus bench step: 1.85 ms at 1, 1.77 at 4, 1.73 from 12 to 64).
 constexpr int kSteps = 16;
-template <bool kAny, int kBlock, bool kWide>
+// kCount: the traversal counters (RR_COUNT_TRAVERSAL) are compiled only into
+// the kernels of the scans that ask for them
+template <bool kAny, int kBlock, bool kWide, bool kCount>
 __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
   typedef typename std::conditional<kWide, uint2, uint32_t>::type StackEntry;
   ScanCounters* C = a.ctr;
@@ -441,7 +433,7 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
   const bool bvh_ok = (a.bvh_status == nullptr || *a.bvh_status == 0u) &&
                       (a.build_status == nullptr || (*a.build_status & kErrTopBuild) == 0u);
   if (!bvh_ok && gtid == 0) atomicOr(&C->error, kErrBvh);
-  const bool count = (a.any_flags & RR_COUNT_TRAVERSAL) != 0u;
+  constexpr bool count = kCount;
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t refill = a.refill;
@@ -515,6 +507,13 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
       for (int u = 0; u < kSteps && s.node != kNone; ++u) {
         if (kWide) step_wide<kAny>(s, reinterpret_cast<uint2*>(stack), a, n_nodes, n_tris, count);
         else step_binary<kAny>(s, reinterpret_cast<uint32_t*>(stack), a, n_nodes, n_tris, count);
+      }
+      // depth-first traversal of a tree visits each of its internal nodes
+      // (fewer than n_tris, binary or wide) at most once: more visits mean a
+      // malformed hierarchy (checked here, at most kSteps visits late)
+      if (s.node != kNone && s.visits > a.n_tris) {
+        atomicOr(&a.ctr->error, kErrBvh);
+        s.node = kNone;
       }
       if (s.node == kNone) {   // the query has ended
         if (kAny) {
@@ -944,7 +943,7 @@ static int block_index(uint32_t block) { return block <= 64u ? 0 : (block <= 128
 
 template <bool kAny, int kBlock, bool kWide>
 static void occ_of(int* out) {
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_query<kAny, kBlock, kWide>, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_query<kAny, kBlock, kWide, false>, kBlock, 0);
   if (*out < 1) *out = 1;
 }
 
@@ -986,11 +985,18 @@ cudaError_t launch_raygen(const ScanArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <bool kAny, bool kWide, bool kCount>
+static void query_launch_c(const ScanArgs& a, uint32_t bounce, int bi, int grid, cudaStream_t st) {
+  if (bi == 0) k_query<kAny, 64, kWide, kCount><<<grid, 64, 0, st>>>(a, bounce);
+  else if (bi == 1) k_query<kAny, 128, kWide, kCount><<<grid, 128, 0, st>>>(a, bounce);
+  else k_query<kAny, 256, kWide, kCount><<<grid, 256, 0, st>>>(a, bounce);
+}
 template <bool kAny, bool kWide>
 static void query_launch(const ScanArgs& a, uint32_t bounce, int bi, int grid, cudaStream_t st) {
-  if (bi == 0) k_query<kAny, 64, kWide><<<grid, 64, 0, st>>>(a, bounce);
-  else if (bi == 1) k_query<kAny, 128, kWide><<<grid, 128, 0, st>>>(a, bounce);
-  else k_query<kAny, 256, kWide><<<grid, 256, 0, st>>>(a, bounce);
+  // a counting kernel may hold more registers: its blocks beyond the
+  // residency start later and find no work left
+  if (a.any_flags & RR_COUNT_TRAVERSAL) query_launch_c<kAny, kWide, true>(a, bounce, bi, grid, st);
+  else query_launch_c<kAny, kWide, false>(a, bounce, bi, grid, st);
 }
 
 cudaError_t launch_query(const ScanArgs& a, uint32_t bounce, bool any, const LaunchCfg& c, cudaStream_t st) {
