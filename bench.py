@@ -217,6 +217,57 @@ def set_bvh(rr, h, bvh: str):
         rr.rr_batch_config_set(h, bvh_build=rr.RR_BVH_LBVH)
 
 
+LARGE_WORKLOAD = "city_5M_tris_400x1000_rays_8_bounces_4000_bins"
+
+
+def large_bench(device, stream, flush, bvh: str, steps: int = 10, warmup: int = 2, rebuilds: int = 5):
+    """The large plain scan (~5M-triangle city, 400 x 1000 rays, <= 8
+    bounces, 4000 bins) as steps of the same kind as the headline: BVH
+    rebuild + scan, L2 flushed between steps, CUDA events on the stream;
+    then the rebuild alone, timed the same way."""
+    import torch
+    from paper_2310_03505_gb300 import rr, scenes
+    sc, pz, params = scenes.config_large()
+    d_vtx = torch.from_numpy(sc.vertices).to(device)
+    h = rr.rr_scene_create(d_vtx, sc.triangles, sc.material_ids, sc.materials)
+    try:
+        set_bvh(rr, h, bvh)
+        img = torch.zeros(params["n_azimuth"], params["n_bins"], device=device)
+
+        def step(sid):
+            rr.rr_scene_update_vertices(h, d_vtx)
+            rr.rr_scan_async(h, pz, {**params, "scan_id": sid}, img)
+
+        def timed(fn, n):
+            ev = []
+            for i in range(n):
+                flush.fill_(float(i))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn(i)
+                e1.record(stream)
+                ev.append((e0, e1))
+            torch.cuda.synchronize()
+            return float(np.sum([a.elapsed_time(b) for a, b in ev]))
+
+        for i in range(warmup):
+            step(90000 + i)
+        rr.rr_scene_sync(h)
+        rr.rr_scene_stats(h, reset=True)
+        ms = timed(lambda i: step(91000 + i), steps)
+        rc = rr.rr_scene_sync(h)
+        q = float(rr.rr_scene_stats(h, reset=True)["closest_queries"])
+        build_ms = timed(lambda i: rr.rr_scene_update_vertices(h, d_vtx), rebuilds) / rebuilds
+        rr.rr_scene_sync(h)
+        return {"workload": LARGE_WORKLOAD, "triangles": sc.n_triangles, "value": q / (ms * 1e-3) / 1e6,
+                "unit": "Mrays/s", "scans_per_s": steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                "steps": steps, "warmup": warmup, "bvh": "LBVH" if bvh == "lbvh" else "LBVH + binned-SAH top",
+                "bvh_rebuild_ms": build_ms, "queries_per_scan": q / steps,
+                "step": "BVH rebuild + polar scan", "status": "ok" if rc is None else str(rc)}
+    finally:
+        rr.rr_scene_destroy(h)
+
+
 def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: int = 0, bvh: str = "sah_top"):
     """The batched workload: 256 poses along a random walk through a ~1M
     triangle campus, rays per beam uneven per pose (32..512).  One step = the
@@ -414,6 +465,7 @@ def main():
                          "(default) or the LBVH alone")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-scan-only", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the large (5M-triangle city) scan object")
     ap.add_argument("--served-seconds", type=float, default=10.0,
                     help="arrival window per request rate of the served workload")
     args = ap.parse_args()
@@ -556,6 +608,11 @@ def main():
                      "status": "ok" if so_rc is None else str(so_rc)}
         set_bvh(rr, h, args.step_bvh)
 
+    # the large plain scan: rank 0 only, an extra object beside the headline
+    large = None
+    if rank == 0 and not args.no_large:
+        large = large_bench(device, stream, flush, args.step_bvh)
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -627,7 +684,7 @@ def main():
                          "launches_per_step": trace_launches / max(args.steps, 1),
                          "ms_per_launch": trace_ms / max(trace_launches, 1)},
             "visibility_queries": {"nodes_per_query": any_nodes_per_q, "tris_per_query": any_tris_per_q},
-            "scan_only": scan_only,
+            "scan_only": scan_only, "large": large,
             "batched": batched, "served": served,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["kernel_launches"]),
             "kernels_per_step": kernels_per_step, "clocks": clk, "wall_s_timed": wall,
