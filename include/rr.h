@@ -121,7 +121,13 @@ typedef struct {
                   the same elliptic Gaussian; 0 or 1: circular
    noise_cell_az, noise_cell_bins  Perlin lattice spacing in azimuth beams and
                   range bins (0: 8 and 32); the lattice wraps around the circle
-                  with round(n_azimuth / noise_cell_az) cells */
+                  with round(n_azimuth / noise_cell_az) cells
+   range_falloff  exponent k of an optional range weight of the returns: a
+                  return at range r > 1 m adds its energy times (1 m / r)^k to
+                  the image (Eq. 1's R^-4 power falloff with k = 4, made
+                  explicit; returns nearer than 1 m are not scaled).  0 (the
+                  default): the image follows the ray density alone, as
+                  Sec. III-A describes.  In [0, 16]. */
 typedef struct {
   uint32_t n_azimuth, rays_per_beam, max_bounces, n_bins;
   float beam_width_rad, beam_prob, elevation_rad, bin_size_m, t_min_m, min_energy, freq_hz;
@@ -131,6 +137,7 @@ typedef struct {
   uint32_t scan_id;
   float beam_aspect;
   float noise_cell_az, noise_cell_bins;
+  float range_falloff;
 } rr_sensor_params;
 
 /* One traced segment (debug dump): initial ray (az, k), branch path (bit i =

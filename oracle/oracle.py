@@ -48,7 +48,7 @@ class Params(C.Structure):
                 ("noise_amb", C.c_double),
                 ("flags", C.c_uint32), ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("scan_id", C.c_uint32),
                 ("beam_aspect", C.c_double), ("noise_cell_az", C.c_double), ("noise_cell_bins", C.c_double),
-                ("ray_stride", C.c_uint32)]
+                ("ray_stride", C.c_uint32), ("range_falloff", C.c_double)]
 
 
 class Pose(C.Structure):
@@ -120,6 +120,10 @@ def _load(path):
             L.orc_receive_weight.argtypes = [p, p, u32, p]
             L.orc_receive_weight.restype = d
             L.orc_max_threads.restype = C.c_int
+            L.orc_speckle_factor.argtypes = [p, u32, u32, u32, u32, C.c_int]
+            L.orc_speckle_factor.restype = d
+            L.orc_range_weight.argtypes = [p, d]
+            L.orc_range_weight.restype = d
     return L
 
 
@@ -166,7 +170,7 @@ def make_params(s: dict) -> Params:
                   s["freq_hz"], s["blur_sigma_bins"], s["az_pattern_sigma"], s["noise_sys"], s["noise_amb"],
                   flags, seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, int(s["scan_id"]),
                   s.get("beam_aspect") or 1.0, s.get("noise_cell_az") or 8.0, s.get("noise_cell_bins") or 32.0,
-                  int(s.get("ray_stride") or 1))
+                  int(s.get("ray_stride") or 1), float(s.get("range_falloff") or 0.0))
 
 
 def make_pose(pz: dict) -> Pose:
@@ -393,6 +397,17 @@ def db_u8(image, cutoff_db: float):
     out = np.zeros(img.shape, np.uint8)
     lib().orc_db_u8(_ptr(img), img.size, float(cutoff_db), _ptr(out))
     return out
+
+
+def speckle_factor(params: dict, a: int, k: int, path: int, bounce: int, which: int) -> float:
+    """Sec. III-C speckle factor of the return `which` (0 traveled path, 1 air
+    path) of segment (a, k, path, bounce)."""
+    return lib().orc_speckle_factor(C.byref(make_params(params)), a, k, path, bounce, which)
+
+
+def range_weight(params: dict, r: float) -> float:
+    """Optional range weight (1 m / r)^range_falloff of a return at range r."""
+    return lib().orc_range_weight(C.byref(make_params(params)), float(r))
 
 
 def max_threads() -> int:

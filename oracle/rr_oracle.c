@@ -90,6 +90,8 @@ typedef struct {
   double noise_cell_az, noise_cell_bins; /* Perlin lattice spacing (beams, bins) */
   uint32_t ray_stride;                  /* trace the initial rays k = 0, s, 2s, ... of each column (0, 1: all);
                                            a sample: each ray is independent of the others */
+  double range_falloff;                 /* exponent k of the optional range weight (1 m / r)^k of a
+                                           return at range r > 1 m (Eq. 1's R^-4 with k = 4; 0: off) */
 } orc_params;
 
 typedef struct {
@@ -653,10 +655,25 @@ double orc_receive_weight(const orc_params* p, const orc_pose* pose, uint32_t a,
   return receive_weight(p, pose, a, axis, pose->p, pt);
 }
 
-static double speckle_factor(const orc_params* p, uint32_t a, uint32_t k, uint32_t path, uint32_t bounce, int which) {
+/* Speckle (Sec. III-C noise model): the energy of one return is multiplied
+   by an Exp(1) factor -ln u (fully developed speckle: exponential intensity
+   with mean one, so the expected image is unchanged).  u is word `which` of
+   the Philox block of counter (scan_id, a, k, 1 | (path << 8 | bounce) << 8):
+   one block per segment, word 0 for its traveled-path return, word 1 for its
+   air-path return. */
+double orc_speckle_factor(const orc_params* p, uint32_t a, uint32_t k, uint32_t path, uint32_t bounce, int which) {
   uint32_t x[4];
   draw(p, a, k, 1u | (((path << 8) | bounce) << 8), x);
   return -log(orc_u24(x[which]));
+}
+
+/* Optional range weight of a return at range r (metres): Eq. 1's power
+   falloff R^-k made explicit, normalised at 1 m and never above one:
+   (1 / r)^k for r > 1 m, 1 otherwise.  k = 0 (the default) leaves the image
+   to the ray density alone, as Sec. III-A describes. */
+double orc_range_weight(const orc_params* p, double r) {
+  if (p->range_falloff == 0.0 || !(r > 1.0)) return 1.0;
+  return pow(r, -p->range_falloff);
 }
 
 /* Sec. III-A: trace the ray tree of every initial ray of azimuth a. */
@@ -825,12 +842,14 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
       seg.ret_a = ret_a;
       if (ret_t > 0.0) {
         double e = ret_t;
-        if (p->flags & ORC_SPECKLE) e *= speckle_factor(p, a, k, ray.path, ray.bounce, 0);
+        if (p->flags & ORC_SPECKLE) e *= orc_speckle_factor(p, a, k, ray.path, ray.bounce, 0);
+        e *= orc_range_weight(p, L1);
         push_ret(col, k, L1, e);
       }
       if (ret_a > 0.0) {
         double e = ret_a;
-        if (p->flags & ORC_SPECKLE) e *= speckle_factor(p, a, k, ray.path, ray.bounce, 1);
+        if (p->flags & ORC_SPECKLE) e *= orc_speckle_factor(p, a, k, ray.path, ray.bounce, 1);
+        e *= orc_range_weight(p, range_a);
         push_ret(col, k, range_a, e);
       }
 

@@ -131,7 +131,7 @@ int check_params(const rr_pose* pose, const rr_sensor_params* p) {
     return fail(RR_ERR_INVALID_ARG, "n_azimuth * rays_per_beam exceeds 2^30");
   const float fs[] = {p->beam_width_rad, p->beam_prob, p->elevation_rad, p->bin_size_m, p->t_min_m, p->min_energy,
                       p->freq_hz, p->blur_sigma_bins, p->az_pattern_sigma, p->noise_sys, p->noise_amb,
-                      p->beam_aspect, p->noise_cell_az, p->noise_cell_bins};
+                      p->beam_aspect, p->noise_cell_az, p->noise_cell_bins, p->range_falloff};
   for (float f : fs)
     if (!finite_f(f)) return fail(RR_ERR_INVALID_ARG, "sensor parameters must be finite");
   if (p->beam_width_rad < 0.f || p->beam_width_rad > 3.14159265f)
@@ -150,6 +150,8 @@ int check_params(const rr_pose* pose, const rr_sensor_params* p) {
   if ((p->noise_cell_az != 0.f && p->noise_cell_az < 1.f) || (p->noise_cell_bins != 0.f && p->noise_cell_bins < 1.f) ||
       p->noise_cell_az > 1e6f || p->noise_cell_bins > 1e6f)
     return fail(RR_ERR_INVALID_ARG, "noise cells must be 0 (default) or in [1, 1e6]");
+  if (p->range_falloff < 0.f || p->range_falloff > 16.f)
+    return fail(RR_ERR_INVALID_ARG, "range_falloff must be in [0, 16]");
   for (int i = 0; i < 3; ++i)
     if (!finite_f(pose->p[i])) return fail(RR_ERR_INVALID_ARG, "pose position must be finite");
   double qn = 0.0;

@@ -215,7 +215,7 @@ static void fill_desc(ScanDesc& d, const rr_pose& pose, const rr_sensor_params& 
   d.rng = make_uint4((uint32_t)(p.seed & 0xFFFFFFFFu), (uint32_t)(p.seed >> 32), p.scan_id, p.flags);
   d.offs = make_uint4(ray0, col0, tmp0, az_begin);
   d.ext = make_float4(p.beam_aspect > 0.f ? p.beam_aspect : 1.0f, p.noise_cell_az > 0.f ? p.noise_cell_az : 8.0f,
-                      p.noise_cell_bins > 0.f ? p.noise_cell_bins : 32.0f, 0.0f);
+                      p.noise_cell_bins > 0.f ? p.noise_cell_bins : 32.0f, p.range_falloff);
   d.image = image;
 }
 

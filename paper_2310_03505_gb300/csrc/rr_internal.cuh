@@ -106,7 +106,7 @@ struct __align__(16) ScanDesc {
   float4 post;       // blur_sigma, az_sigma, noise_sys, noise_amb
   uint4 rng;         // seed_lo, seed_hi, scan_id, flags
   uint4 offs;        // first initial ray, first column, first float of image_tmp (or kNone), first azimuth
-  float4 ext;        // beam aspect (elliptic beams), Perlin cell in beams, Perlin cell in bins, 0
+  float4 ext;        // beam aspect (elliptic beams), Perlin cell in beams, Perlin cell in bins, range falloff k
   float* image;      // [n_az][n_bins] output (device)
   unsigned long long pad;
 };

@@ -688,6 +688,14 @@ __global__ void k_selftest_look_back(ScanArgs a) { look_back(a, 1u, 0u, 0u); }
 
 // ---------------------------------------------------------------------------
 // shade
+
+// optional range weight of a return at range r (metres): (1 / r)^k for
+// r > 1 m, k = the scan's range_falloff (Eq. 1's power falloff; 0: off)
+__device__ __forceinline__ float range_weight(const ScanDesc* sd, float r) {
+  const float k = __ldg(&sd->ext.w);
+  return (k != 0.0f && r > 1.0f) ? powf(r, -k) : 1.0f;
+}
+
 __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t bounce) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wsum[kShadeBlock / 32];
@@ -813,6 +821,7 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
             if (bin < (float)dims.w) {
               float e = ret_t;
               if (rng.w & RR_SPECKLE) e *= -logf(u01(draw(rng, az, k, 1u | (((path << 8) | bounce) << 8)).x));
+              e *= range_weight(sd, L1);
               rec[nr++] = make_uint2(((offs.y + az - offs.w) << kBinBits) | (uint32_t)bin, __float_as_uint(e));
             }
           }
@@ -821,6 +830,7 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
             if (bin < (float)dims.w) {
               float e = ret_a;
               if (rng.w & RR_SPECKLE) e *= -logf(u01(draw(rng, az, k, 1u | (((path << 8) | bounce) << 8)).y));
+              e *= range_weight(sd, range_a);
               rec[nr++] = make_uint2(((offs.y + az - offs.w) << kBinBits) | (uint32_t)bin, __float_as_uint(e));
             }
           }

@@ -52,7 +52,7 @@ class rr_sensor_params(C.Structure):
                 ("min_energy", C.c_float), ("freq_hz", C.c_float), ("blur_sigma_bins", C.c_float),
                 ("az_pattern_sigma", C.c_float), ("noise_sys", C.c_float), ("noise_amb", C.c_float),
                 ("flags", C.c_uint32), ("seed", C.c_uint64), ("scan_id", C.c_uint32), ("beam_aspect", C.c_float),
-                ("noise_cell_az", C.c_float), ("noise_cell_bins", C.c_float)]
+                ("noise_cell_az", C.c_float), ("noise_cell_bins", C.c_float), ("range_falloff", C.c_float)]
 
 
 class rr_segment(C.Structure):
@@ -214,7 +214,8 @@ def make_params(s: dict) -> rr_sensor_params:
                             s["beam_prob"], s["elevation"], s["bin_size"], s["t_min"], s["min_energy"], s["freq_hz"],
                             s["blur_sigma_bins"], s["az_pattern_sigma"], s["noise_sys"], s["noise_amb"], flags,
                             int(s["seed"]), int(s["scan_id"]), s.get("beam_aspect", 0.0),
-                            s.get("noise_cell_az", 0.0), s.get("noise_cell_bins", 0.0))
+                            s.get("noise_cell_az", 0.0), s.get("noise_cell_bins", 0.0),
+                            s.get("range_falloff", 0.0))
 
 
 def make_pose(pz: dict) -> rr_pose:

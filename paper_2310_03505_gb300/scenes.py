@@ -448,11 +448,12 @@ def sensor(**kw) -> dict:
              beam_width=math.radians(10.0), beam_prob=0.9, elevation=0.0, bin_size=0.0438,
              t_min=1e-4, min_energy=0.0, freq_hz=76.5e9, blur_sigma_bins=0.0, az_pattern_sigma=0.0,
              noise_sys=0.0, noise_amb=0.0, multipath=True, refraction=True, speckle=False, noise=False,
-             perlin=False, beam_aspect=1.0, noise_cell_az=8.0, noise_cell_bins=32.0, seed=0x5EED, scan_id=0)
+             perlin=False, beam_aspect=1.0, noise_cell_az=8.0, noise_cell_bins=32.0, range_falloff=0.0,
+             seed=0x5EED, scan_id=0)
     p.update(kw)
     for k in ("beam_width", "beam_prob", "elevation", "bin_size", "t_min", "min_energy", "freq_hz",
               "blur_sigma_bins", "az_pattern_sigma", "noise_sys", "noise_amb", "beam_aspect", "noise_cell_az",
-              "noise_cell_bins"):
+              "noise_cell_bins", "range_falloff"):
         p[k] = f32(p[k])
     for k in ("n_azimuth", "rays_per_beam", "max_bounces", "n_bins", "seed", "scan_id"):
         p[k] = int(p[k])

@@ -31,6 +31,7 @@ VARIANTS = {
     "other_seed": dict(seed=0xABCDEF12345, scan_id=7),
     "min_energy": dict(min_energy=1e-4),
     "elliptic": dict(beam_aspect=2.5),
+    "range_falloff": dict(range_falloff=2.0),
     "perlin_noise": dict(noise=True, perlin=True, noise_sys=1e-4, noise_amb=5e-5, noise_cell_az=8.0,
                          noise_cell_bins=16.0, blur_sigma_bins=1.0),
 }

@@ -58,6 +58,14 @@ MUTANTS = {
     "bin_off_by_one": ("img[(size_t)fb] += r->E;", "img[(size_t)fb + 1] += r->E;"),
     "index_is_permittivity": ("    n2 = sqrt(m->eps_r);", "    n2 = m->eps_r;"),
     "reflected_child_medium": ("        c.medium = ray.medium;", "        c.medium = next_medium;"),
+    "speckle_mean_two": ("return -log(orc_u24(x[which]));", "return 1.0 - log(orc_u24(x[which]));"),
+    "speckle_shared_word": ("orc_speckle_factor(p, a, k, ray.path, ray.bounce, 1)",
+                            "orc_speckle_factor(p, a, k, ray.path, ray.bounce, 0)"),
+    "speckle_counter_swapped": ("draw(p, a, k, 1u | (((path << 8) | bounce) << 8), x);",
+                                "draw(p, a, k, 1u | (((bounce << 8) | path) << 8), x);"),
+    "min_energy_doubled": ("int spawn_refl = deeper && in_range && e_refl >= p->min_energy;",
+                           "int spawn_refl = deeper && in_range && e_refl >= 2.0 * p->min_energy;"),
+    "range_weight_round_trip": ("return pow(r, -p->range_falloff);", "return pow(2.0 * r, -p->range_falloff);"),
     "azimuth_step": ("double phi = 2.0 * M_PI * (double)a / (double)p->n_azimuth + r * cos(omega);",
                      "double phi = M_PI * (double)a / (double)p->n_azimuth + r * cos(omega);"),
 }

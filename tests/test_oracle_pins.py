@@ -671,11 +671,170 @@ def check_tabulated_lobe():
             assert abs(orc.brdf_window(tab, w, b) - orc.brdf_window(eq5, w, b)) < 1e-7, (w, b)
 
 
+# ----------------------------------------------------------------- speckle
+def _speckle_direct(p, a, k, path, bounce, word):
+    """The speckle factor from its definition: -ln u of word `word` of the
+    Philox4x32-10 block (pinned by the known-answer vectors) of counter
+    (scan_id, a, k, 1 | (path << 8 | bounce) << 8), key (seed_lo, seed_hi)."""
+    seed = int(p["seed"])
+    x = orc.philox([int(p["scan_id"]), a, k, 1 | (((path << 8) | bounce) << 8)],
+                   [seed & 0xFFFFFFFF, seed >> 32])
+    return -math.log(orc.u24(int(x[word])))
+
+
+def check_speckle_statistics():
+    """Sec. III-C speckle: the factor is Exp(1) (fully developed speckle has
+    an exponential intensity; mean one keeps the expected image): mean and
+    variance within 4 standard errors of 1 over 100,000 factors of distinct
+    counters, and a Kolmogorov-Smirnov test against Exp(1).  The two words
+    of one segment's block are independent draws (correlation ~ 0)."""
+    import ctypes as C
+    p = base_params(speckle=True, seed=0x1234ABCD9876, scan_id=3)
+    pr = orc.make_params(p)
+    L = orc.lib()
+    f0 = np.array([L.orc_speckle_factor(C.byref(pr), a, k, 5, 2, 0) for a in range(250) for k in range(200)])
+    f1 = np.array([L.orc_speckle_factor(C.byref(pr), a, k, 5, 2, 1) for a in range(250) for k in range(200)])
+    f = np.concatenate([f0, f1])
+    n = f.size
+    assert abs(f.mean() - 1.0) < 4.0 / math.sqrt(n), f.mean()
+    # Var of the sample variance of Exp(1): (mu4 - sigma^4) / n = 8 / n
+    assert abs(f.var() - 1.0) < 4.0 * math.sqrt(8.0 / n), f.var()
+    assert stats.kstest(f, "expon").pvalue > 1e-3
+    assert abs(np.corrcoef(f0, f1)[0, 1]) < 4.0 / math.sqrt(f0.size)
+    # the counter of the definition, for both words and several segments
+    for (a, k, path, bounce) in ((0, 0, 0, 0), (17, 3, 2, 1), (399, 199, 0b1011, 4), (65534, 65534, 0x7FFF, 15)):
+        for w in (0, 1):
+            got = L.orc_speckle_factor(C.byref(pr), a, k, path, bounce, w)
+            assert got == _speckle_direct(p, a, k, path, bounce, w), (a, k, path, bounce, w)
+
+
+def check_speckle_in_the_scan():
+    """Speckle at the scan level.  (1) A normal-incidence metal plane, one
+    ray: the speckled return is the plain return times the factor of
+    segment (0, 0, path 0, bounce 0), word 0.  (2) The eps_r = 4 slab on
+    metal with multipath: every return is its segment's return times that
+    segment's factor, word 0 for the traveled path and word 1 for the air
+    path (the air-path return of the exit hit, bounce 2, shares its bin with
+    the metal's traveled-path return).  (3) Averaged over many seeds, the
+    speckled return of the plane equals the plain one."""
+    p = base_params(seed=0xC0FFEE, scan_id=11)
+    _, d, _, _ = orc.d3_ray(p, POSE0, 0, 0)
+    u, v = frame(d)
+    D = 10.013
+    s = Soup()
+    s.quad(D * d, u, v, 2.0, -d, 0)
+    mats = [make_material(pec=True, **METAL_LOBE)]
+    plain = _scan(s, mats, p)["image"][0]
+    b = int(D / p["bin_size"])
+    spk = _scan(s, mats, {**p, "speckle": True})["image"][0]
+    assert list(np.nonzero(spk)[0]) == [b]
+    f = _speckle_direct(p, 0, 0, 0, 0, 0)
+    assert abs(spk[b] - plain[b] * f) <= 1e-12 * plain[b] * f
+    # (2) the slab with multipath
+    p2 = base_params(max_bounces=3, multipath=True, seed=0x5EED77, scan_id=5)
+    _, d, _, _ = orc.d3_ray(p2, POSE0, 0, 0)
+    u, v = frame(d)
+    D2, th = 5.0134, 0.0512
+    s2 = Soup()
+    s2.quad(D2 * d, u, v, 2.0, -d, 0)
+    s2.quad((D2 + th) * d, u, v, 2.0, -d, 1)
+    mats2 = [make_material(eps_r=4.0, tan_d=0.01, **WALL), make_material(pec=True, **METAL_LOBE)]
+    r_plain = _scan(s2, mats2, p2)
+    r_spk = _scan(s2, mats2, {**p2, "speckle": True})
+    bins = {0: int(D2 / 0.01), 1: int((D2 + 2 * th) / 0.01), 2: int((D2 + 4 * th) / 0.01)}
+    expect = np.zeros_like(r_spk["image"][0])
+    for sg in r_plain["segments"]:
+        if sg["ret_t"] > 0:
+            expect[bins[int(sg["bounce"])]] += sg["ret_t"] * _speckle_direct(p2, 0, 0, int(sg["path"]),
+                                                                             int(sg["bounce"]), 0)
+        if sg["ret_a"] > 0:
+            assert int(sg["bounce"]) == 2
+            expect[bins[1]] += sg["ret_a"] * _speckle_direct(p2, 0, 0, int(sg["path"]), 2, 1)
+    assert (r_plain["segments"]["ret_a"] > 0).sum() == 1
+    assert np.array_equal(np.nonzero(r_spk["image"][0])[0], np.nonzero(expect)[0])
+    assert np.allclose(r_spk["image"][0], expect, rtol=1e-12, atol=0.0)
+    # (3) the mean over seeds: a wide wall across the beam axis, so that every
+    # seed's ray (a new D3 draw) returns energy; speckled / plain per seed
+    s3 = Soup()
+    s3.quad((8.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0), 20.0, (-1.0, 0.0, 0.0), 0)
+    wall = [make_material(eps_r=4.0, **WALL)]
+    n, vals = 1500, []
+    for i in range(n):
+        q = {**p, "seed": 1000 + i}
+        e_plain = _scan(s3, wall, q)["image"][0].sum()
+        e_spk = _scan(s3, wall, {**q, "speckle": True})["image"][0].sum()
+        assert e_plain > 0
+        vals.append(e_spk / e_plain)
+    assert abs(np.mean(vals) - 1.0) < 4.0 / math.sqrt(n), np.mean(vals)
+
+
+# ----------------------------------------------------------------- termination
+def check_min_energy():
+    """Sec. III-A termination ("energy below detectability"): the eps_r = 4
+    slab on metal at normal incidence.  The front face's reflected child
+    carries E R - ret_t = (1 - W_wall(0)) / 9 (closed form).  With min_energy
+    just below that energy the child is spawned (and escapes back past the
+    sensor); just above it, it is not, and its energy moves from the escaped
+    to the terminated tally -- by exactly that closed-form amount -- with one
+    segment fewer and the same image.  min_energy = 0 spawns every child."""
+    p = base_params(max_bounces=3)
+    _, d, _, _ = orc.d3_ray(p, POSE0, 0, 0)
+    u, v = frame(d)
+    D, th = 5.0134, 0.0512
+    s = Soup()
+    s.quad(D * d, u, v, 2.0, -d, 0)
+    s.quad((D + th) * d, u, v, 2.0, -d, 1)
+    mats = [make_material(eps_r=4.0, tan_d=0.01, **WALL), make_material(pec=True, **METAL_LOBE)]
+    e_child = (1.0 - scipy_window(0.6, 0.1, 30, 0.0, p["beam_width"])) / 9.0
+    below = _scan(s, mats, {**p, "min_energy": e_child * (1 - 1e-4)})
+    above = _scan(s, mats, {**p, "min_energy": e_child * (1 + 1e-4)})
+    zero = _scan(s, mats, {**p, "min_energy": 0.0})
+    tb, ta = below["tallies"][0, 0], above["tallies"][0, 0]
+    assert abs((ta[3] - tb[3]) - e_child) < 1e-9 * e_child, (ta, tb, e_child)
+    assert abs((tb[2] - ta[2]) - e_child) < 1e-9 * e_child
+    assert ta[0] == tb[0] and ta[1] == tb[1]
+    assert len(below["segments"]) == len(above["segments"]) + 1
+    extra = below["segments"][(below["segments"]["bounce"] == 1) & (below["segments"]["path"] == 0)]
+    assert len(extra) == 1 and extra[0]["tri"] == orc.NONE
+    assert abs(extra[0]["E"] - e_child) < 1e-9 * e_child
+    assert np.array_equal(below["image"], above["image"])
+    # with no threshold the deeper, weaker children are spawned too
+    assert len(zero["segments"]) > len(below["segments"])
+    assert abs(zero["tallies"][0, 0].sum() - 1.0) < 1e-12 and abs(ta.sum() - 1.0) < 1e-12
+
+
+# ----------------------------------------------------------------- range weight
+def check_range_falloff():
+    """The optional range weight of Eq. 1's power falloff: with exponent k a
+    return at range r > 1 m is scaled by r^-k (1 m reference), so the
+    normal-incidence metal plane at distance D gives W(0) D^-k; below 1 m
+    nothing changes; k = 0 is the plain image; the energy tallies (physics
+    of the ray tree) are unchanged."""
+    p = base_params(n_bins=4000)
+    _, d, _, _ = orc.d3_ray(p, POSE0, 0, 0)
+    u, v = frame(d)
+    mats = [make_material(pec=True, **METAL_LOBE)]
+    w0 = scipy_window(0, 0, 2000, 0.0, p["beam_width"])
+    for D, k in ((10.013, 4.0), (23.456, 2.0), (0.7013, 4.0)):
+        s = Soup()
+        s.quad(D * d, u, v, 2.0, -d, 0)
+        t = plane_distance(s, 0, np.zeros(3), d)
+        r = _scan(s, mats, {**p, "range_falloff": k})
+        nz, e = single_return(r["image"][0])
+        assert list(nz) == [int(D / p["bin_size"])]
+        expect = w0 * (t ** -k if t > 1.0 else 1.0)
+        assert abs(e[0] - expect) < 1e-9 * expect, (D, k, e[0], expect)
+        assert abs(r["tallies"][0, 0, 0] - w0) < 1e-9 * w0
+        r0 = _scan(s, mats, {**p, "range_falloff": 0.0})
+        assert abs(single_return(r0["image"][0])[1][0] - w0) < 1e-9 * w0
+
+
 ALL_CHECKS = [check_philox_kat, check_u24, check_d3_sigma, check_d3_pose_and_azimuth, check_fresnel_closed_forms,
               check_snell, check_brdf_normalisation, check_brdf_window_pins, check_closest_brute_force,
               check_normal_incidence_plane, check_oblique_plane, check_slab, check_slab_multipath,
               check_corner_reflector, check_lidar_like, check_conservation_tiny, check_post_pass, check_db_map,
-              check_elliptic_beam, check_perlin, check_cook_torrance_lobe, check_tabulated_lobe]
+              check_elliptic_beam, check_perlin, check_cook_torrance_lobe, check_tabulated_lobe,
+              check_speckle_statistics, check_speckle_in_the_scan, check_min_energy, check_range_falloff]
 
 
 @pytest.mark.parametrize("check", ALL_CHECKS, ids=lambda f: f.__name__[6:])
