@@ -441,8 +441,13 @@ int rr_scan_debug(rr_scene* scene, const rr_pose* pose, const rr_sensor_params* 
    needs about 4 MiB.  The first call on each device, with that device current,
    looks up the array's device address once.  All calls share the array
    (it keeps the last call's contents; the scan writes everything before it
-   reads it), so calls that overlap on the GPU race.  Blocking; returns the
-   device status of the scan. */
+   reads it), so calls that overlap on the GPU race; a call also shares the
+   scene's status counters with rr_scan, so it must not overlap any other
+   scan of the same scene either.  It always traverses the binary BVH (the
+   same closest hits as the 8-wide one, without its lazy collapse), whatever
+   node format rr_batch_config_set chose.  The scene must live on the
+   current device (else RR_ERR_INVALID_ARG).  Blocking; returns the device
+   status of the scan. */
 int rr_scan_static(rr_scene* scene, const rr_pose* pose, const rr_sensor_params* params, float* out_polar);
 
 /* Range-bin accumulation alone (Sec. III-B): the image pass of a scan run on

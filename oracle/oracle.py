@@ -108,6 +108,11 @@ def _load(path):
             L.orc_scan.argtypes = [p, u32, p, u32, p, p, u32, p, p, p, u32, p, p, p, p, p, p, C.c_uint64, p,
                                    p, C.c_int]
             L.orc_scan.restype = C.c_int
+            L.orc_scan_accel.argtypes = L.orc_scan.argtypes + [p, C.c_int]
+            L.orc_scan_accel.restype = C.c_int
+            L.orc_bvh_build.argtypes = [p, u32, p, u32, p, u32, p]
+            L.orc_bvh_build.restype = p
+            L.orc_bvh_free.argtypes = [p]
             L.orc_post.argtypes = [p, p, p, u32]
             L.orc_post.restype = C.c_int
             L.orc_db_u8.argtypes = [p, C.c_uint64, d, p]
@@ -293,9 +298,38 @@ def restore_library(handle):
         _lib = handle
 
 
+# ---------------------------------------------------------------- CPU BVH
+class Bvh:
+    """CPU BVH of a scene for ``scan(..., bvh=...)`` (the timed CPU baseline):
+    binned-SAH binary tree over grown triangle boxes, plus the window tables
+    of the materials for the fast mode.  Built with all host cores."""
+
+    def __init__(self, vertices, triangles, materials):
+        self._lib = lib()
+        v = np.ascontiguousarray(vertices, np.float32)
+        t = np.ascontiguousarray(triangles, np.uint32)
+        made = [make_material(x) for x in materials]
+        mats = (Material * len(materials))(*made)
+        depth = C.c_uint32()
+        self.handle = self._lib.orc_bvh_build(_ptr(v), v.shape[0], _ptr(t), t.shape[0], mats, len(materials),
+                                              C.byref(depth))
+        del made
+        if not self.handle:
+            raise RuntimeError("orc_bvh_build failed (bad indices, no triangles or a tree deeper than its stack)")
+        self.depth = depth.value
+
+    def close(self):
+        if self.handle:
+            self._lib.orc_bvh_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
 # ---------------------------------------------------------------- full scan
 def scan(vertices, triangles, material_ids, materials, pz: dict, params: dict, az_list=None, post: bool = True,
-         threads: int = 0, want_segments: bool = True):
+         threads: int = 0, want_segments: bool = True, bvh: Bvh | None = None, fast: bool = False):
     """Run the brute-force scan on the azimuth columns az_list (all if None).
 
     Returns a dict with ``image`` [n_cols, n_bins] (every return, post pass
@@ -305,7 +339,12 @@ def scan(vertices, triangles, material_ids, materials, pz: dict, params: dict, a
     before the post pass), ``flags`` [n_cols, Ns] (1 = initial ray flagged
     for parity), ``tallies`` [n_cols, Ns, 4] (returned, absorbed, escaped,
     terminated), ``segments`` (structured array, SEGMENT_DTYPE) and
-    ``counts`` (closest-hit queries, shadow queries, returns)."""
+    ``counts`` (closest-hit queries, shadow queries, returns).
+
+    With ``bvh`` the queries go through that CPU BVH instead of brute force
+    (the same results); ``fast`` then selects the timing mode (tabulated
+    beam windows, strict pruning; ``flags``, ``image_masked`` and ``slack``
+    are not meaningful)."""
     L = lib()
     v = np.ascontiguousarray(vertices, np.float32)
     t = np.ascontiguousarray(triangles, np.uint32)
@@ -329,9 +368,10 @@ def scan(vertices, triangles, material_ids, materials, pz: dict, params: dict, a
     segs = np.zeros(cap, SEGMENT_DTYPE) if want_segments else None
     n_segs = C.c_uint64()
     counts = np.zeros(3, np.uint64)
-    rc = L.orc_scan(_ptr(v), v.shape[0], _ptr(t), t.shape[0], _ptr(m), mats, len(materials), C.byref(po),
-                    C.byref(pr), _ptr(cols), n_cols, _ptr(image), _ptr(image_m), _ptr(slack), _ptr(flags),
-                    _ptr(tallies), _ptr(segs), cap, C.byref(n_segs), _ptr(counts), int(threads))
+    rc = L.orc_scan_accel(_ptr(v), v.shape[0], _ptr(t), t.shape[0], _ptr(m), mats, len(materials), C.byref(po),
+                          C.byref(pr), _ptr(cols), n_cols, _ptr(image), _ptr(image_m), _ptr(slack), _ptr(flags),
+                          _ptr(tallies), _ptr(segs), cap, C.byref(n_segs), _ptr(counts), int(threads),
+                          bvh.handle if bvh is not None else None, 1 if fast else 0)
     del made
     if rc != 0:
         raise RuntimeError(f"orc_scan failed with code {rc}")

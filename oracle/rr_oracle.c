@@ -11,7 +11,10 @@
  *
  * Plain and slow on purpose:
  *   - every quantity is a double;
- *   - the closest hit is a loop over every triangle (Moller-Trumbore), no BVH;
+ *   - the closest hit is a loop over every triangle (Moller-Trumbore), no BVH
+ *     (orc_scan; orc_scan_accel answers the same queries through a CPU BVH
+ *     for the timed CPU baseline, pinned to give the same segments, flags,
+ *     tallies and images as the loops);
  *   - each initial ray's tree is expanded depth first with an explicit stack;
  *   - returns are collected in a list and then summed into the polar image by
  *     a lookup, as Sec. III-B describes.
@@ -462,12 +465,16 @@ int orc_tri_plane(const double o[3], const double d[3], const double v0[3], cons
 /* ------------------------------------------------------------------------ */
 /* scene                                                                    */
 /* ------------------------------------------------------------------------ */
+typedef struct orc_bvh orc_bvh;
+
 typedef struct {
   const float* vtx;
   const uint32_t* tri;
   const uint16_t* mat_id;
   const orc_material* mat;
   uint32_t nv, nt, nm;
+  const orc_bvh* bvh; /* NULL: brute force over all triangles (the oracle) */
+  int fast;           /* with a BVH: no parity flags, strict pruning, tabulated windows */
 } scene_t;
 
 static void tri_vertices(const scene_t* s, uint32_t j, double v0[3], double v1[3], double v2[3]) {
@@ -496,46 +503,82 @@ typedef struct {
   uint32_t flags;
 } hit_t;
 
+/* running state of a closest-hit query: the best hit so far, the second
+   closest valid hit, the nearest near-edge candidate, a hit next to t_min */
+typedef struct {
+  hit_t h;
+  double t2, t_edge;
+  int near_tmin;
+} hit_acc;
+
+static void hit_begin(hit_acc* a) {
+  a->h.tri = ORC_NONE;
+  a->h.t = INFINITY;
+  a->h.margin = 0.0;
+  a->h.flags = 0u;
+  a->t2 = INFINITY;
+  a->t_edge = INFINITY;
+  a->near_tmin = 0;
+}
+
+/* one triangle of a closest-hit query (t > t_min; ties on t go to the
+   smaller triangle id) */
+static void hit_consider(const scene_t* s, uint32_t j, const double o[3], const double d[3], double t_min,
+                         hit_acc* a) {
+  double v0[3], v1[3], v2[3], t, b1, b2;
+  tri_vertices(s, j, v0, v1, v2);
+  if (!orc_tri_plane(o, d, v0, v1, v2, &t, &b1, &b2)) return;
+  double b0 = 1.0 - b1 - b2;
+  double m = b0 < b1 ? b0 : b1;
+  if (b2 < m) m = b2;
+  if (m > -FLAG_BARY && m < FLAG_BARY && t > t_min - FLAG_TABS && t < a->t_edge) a->t_edge = t;
+  if (m >= 0.0 && fabs(t - t_min) < FLAG_TABS) a->near_tmin = 1;
+  if (m < 0.0 || !(t > t_min)) return;
+  if (t < a->h.t || (t == a->h.t && j < a->h.tri)) {
+    if (a->h.tri != ORC_NONE) a->t2 = a->h.t;
+    a->h.t = t;
+    a->h.tri = j;
+    a->h.margin = m;
+  } else if (t < a->t2) {
+    a->t2 = t;
+  }
+}
+
+/* parity flags of the finished query: a near-edge candidate that could be
+   the closest, a near tie with the second closest triangle, a hit next to
+   t_min */
+static hit_t hit_finish(const hit_acc* a) {
+  hit_t h = a->h;
+  if (a->t_edge < INFINITY && a->t_edge <= h.t * (1.0 + FLAG_TREL)) h.flags |= SEG_EDGE;
+  if (a->near_tmin) h.flags |= SEG_TMIN;
+  if (h.tri != ORC_NONE && a->t2 - h.t <= FLAG_TREL * h.t) h.flags |= SEG_TIE;
+  return h;
+}
+
+static hit_t closest_hit_bvh(const scene_t* s, const double o[3], const double d[3], double t_min, uint32_t skip);
+static int occluded_bvh(const scene_t* s, const double p[3], const double dir[3], double t_min, double dist,
+                        uint32_t skip, int* flag);
+
 /* Closest hit by brute force over all triangles: t > t_min, triangle != skip,
    ties on t go to the smaller triangle id.  Flags near-edge candidates (hit or
    miss within FLAG_BARY of an edge) that could be the closest, a near tie with
    the second closest triangle, and hits next to t_min. */
 static hit_t closest_hit(const scene_t* s, const double o[3], const double d[3], double t_min, uint32_t skip) {
-  hit_t h = {ORC_NONE, INFINITY, 0.0, 0u};
-  double t2 = INFINITY;         /* second closest valid hit */
-  double t_edge = INFINITY;     /* nearest near-edge candidate */
-  int near_tmin = 0;
+  if (s->bvh) return closest_hit_bvh(s, o, d, t_min, skip);
+  hit_acc a;
+  hit_begin(&a);
   for (uint32_t j = 0; j < s->nt; ++j) {
     if (j == skip) continue;
-    double v0[3], v1[3], v2[3], t, b1, b2;
-    tri_vertices(s, j, v0, v1, v2);
-    if (!orc_tri_plane(o, d, v0, v1, v2, &t, &b1, &b2)) continue;
-    double b0 = 1.0 - b1 - b2;
-    double m = b0 < b1 ? b0 : b1;
-    if (b2 < m) m = b2;
-    if (m > -FLAG_BARY && m < FLAG_BARY && t > t_min - FLAG_TABS && t < t_edge) t_edge = t;
-    if (m >= 0.0 && fabs(t - t_min) < FLAG_TABS) near_tmin = 1;
-    if (m < 0.0 || !(t > t_min)) continue;
-    if (t < h.t || (t == h.t && j < h.tri)) {
-      if (h.tri != ORC_NONE) t2 = h.t;
-      h.t = t;
-      h.tri = j;
-      h.margin = m;
-    } else if (t < t2) {
-      t2 = t;
-    }
+    hit_consider(s, j, o, d, t_min, &a);
   }
-  if (t_edge < INFINITY && t_edge <= h.t * (1.0 + FLAG_TREL)) h.flags |= SEG_EDGE;
-  if (near_tmin) h.flags |= SEG_TMIN;
-  if (h.tri != ORC_NONE && t2 - h.t <= FLAG_TREL * h.t) h.flags |= SEG_TIE;
-  return h;
+  return hit_finish(&a);
 }
 
 /* exported for the tests: closest hit of one ray by brute force */
 int orc_closest(const float* vertices, uint32_t n_vertices, const uint32_t* triangles, uint32_t n_triangles,
                 const double o[3], const double d[3], double t_min, uint32_t skip, uint32_t* tri, double* t,
                 uint32_t* flags) {
-  scene_t s = {vertices, triangles, NULL, NULL, n_vertices, n_triangles, 0};
+  scene_t s = {vertices, triangles, NULL, NULL, n_vertices, n_triangles, 0, NULL, 0};
   hit_t h = closest_hit(&s, o, d, t_min, skip);
   *tri = h.tri;
   *t = h.t;
@@ -543,24 +586,435 @@ int orc_closest(const float* vertices, uint32_t n_vertices, const uint32_t* tria
   return h.tri != ORC_NONE;
 }
 
+/* one triangle of an any-hit query on the open segment (t_min, dist) */
+static void occ_consider(const scene_t* s, uint32_t j, const double p[3], const double dir[3], double t_min,
+                         double dist, int* occ, int* flag) {
+  double v0[3], v1[3], v2[3], t, b1, b2;
+  tri_vertices(s, j, v0, v1, v2);
+  if (!orc_tri_plane(p, dir, v0, v1, v2, &t, &b1, &b2)) return;
+  double b0 = 1.0 - b1 - b2;
+  double m = b0 < b1 ? b0 : b1;
+  if (b2 < m) m = b2;
+  int inside_t = t > t_min && t < dist;
+  int near_t = fabs(t - t_min) < FLAG_TABS || fabs(t - dist) < FLAG_TREL * dist;
+  if (m > -FLAG_BARY && m < FLAG_BARY && (inside_t || near_t)) *flag = 1;
+  if (m >= 0.0 && near_t) *flag = 1;
+  if (m >= 0.0 && inside_t) *occ = 1;
+}
+
 /* Any hit on the open segment from p (on triangle skip) to the sensor at
    distance dist.  Sets *flag when a triangle lies within the flag margins. */
 static int occluded(const scene_t* s, const double p[3], const double dir[3], double t_min, double dist, uint32_t skip,
                     int* flag) {
+  if (s->bvh) return occluded_bvh(s, p, dir, t_min, dist, skip, flag);
   int occ = 0;
   for (uint32_t j = 0; j < s->nt; ++j) {
     if (j == skip) continue;
-    double v0[3], v1[3], v2[3], t, b1, b2;
-    tri_vertices(s, j, v0, v1, v2);
-    if (!orc_tri_plane(p, dir, v0, v1, v2, &t, &b1, &b2)) continue;
-    double b0 = 1.0 - b1 - b2;
-    double m = b0 < b1 ? b0 : b1;
-    if (b2 < m) m = b2;
-    int inside_t = t > t_min && t < dist;
-    int near_t = fabs(t - t_min) < FLAG_TABS || fabs(t - dist) < FLAG_TREL * dist;
-    if (m > -FLAG_BARY && m < FLAG_BARY && (inside_t || near_t)) *flag = 1;
-    if (m >= 0.0 && near_t) *flag = 1;
-    if (m >= 0.0 && inside_t) occ = 1;
+    occ_consider(s, j, p, dir, t_min, dist, &occ, flag);
+  }
+  return occ;
+}
+
+/* ------------------------------------------------------------------------ */
+/* CPU BVH: the timed CPU baseline traces with the oracle's physics through  */
+/* a bounding volume hierarchy instead of the brute-force loops above.       */
+/* Binary tree, binned SAH (16 bins per axis over the centroids), leaves of  */
+/* at most 4 triangles, float boxes rounded outward.  Every triangle's box    */
+/* is grown by 1e-4 of its largest extent plus 1e-6 m, which holds every      */
+/* point of its plane within barycentric margin FLAG_BARY of the triangle:    */
+/* so a query that keeps visiting boxes up to (1 + 1e-5) times the best t     */
+/* sees every triangle the brute-force loops would count (the closest hit,   */
+/* the second closest, near-edge candidates, hits next to t_min) and gives   */
+/* the same hit and the same flags.  In the fast mode (timing) the pruning   */
+/* is strict, any-hit queries stop at the first occluder and the flags are   */
+/* not meaningful; the hits are the same.                                    */
+/* ------------------------------------------------------------------------ */
+#define BVH_BINS 16
+#define BVH_LEAF 4
+#define BVH_STACK 128
+#define WTAB_CELLS 8192
+
+typedef struct {
+  float lo[3], hi[3];
+  uint32_t first; /* leaf: first index into idx; internal: left child (right = first + 1) */
+  uint32_t count; /* leaf: number of triangles (> 0); internal: 0 */
+} bnode_t;
+
+struct orc_bvh {
+  bnode_t* nodes;
+  uint32_t* idx;
+  uint32_t n_nodes, depth;
+  /* tabulated lobe integrals for the fast mode: per material the integral of
+     the density from 0 to x_k = k (pi/2) / WTAB_CELLS and the density there */
+  double* wtab;
+  uint32_t nm;
+};
+
+typedef struct {
+  double lo[3], hi[3];
+} box_t;
+
+static void box_empty(box_t* b) {
+  for (int i = 0; i < 3; ++i) {
+    b->lo[i] = INFINITY;
+    b->hi[i] = -INFINITY;
+  }
+}
+
+static void box_grow(box_t* b, const box_t* c) {
+  for (int i = 0; i < 3; ++i) {
+    if (c->lo[i] < b->lo[i]) b->lo[i] = c->lo[i];
+    if (c->hi[i] > b->hi[i]) b->hi[i] = c->hi[i];
+  }
+}
+
+static double box_area(const box_t* b) {
+  double e0 = b->hi[0] - b->lo[0], e1 = b->hi[1] - b->lo[1], e2 = b->hi[2] - b->lo[2];
+  if (!(e0 >= 0.0)) return 0.0;
+  return 2.0 * (e0 * e1 + e1 * e2 + e2 * e0);
+}
+
+typedef struct {
+  box_t* tbox; /* grown triangle boxes */
+  double* cen; /* [T][3] centroids of the grown boxes */
+  uint32_t* idx;
+  bnode_t* nodes;
+  uint32_t n_nodes, cap, depth;
+} build_t;
+
+/* two consecutive node slots (left and right child) */
+static uint32_t node_alloc2(build_t* B) {
+  uint32_t i;
+#ifdef _OPENMP
+#pragma omp atomic capture
+#endif
+  {
+    i = B->n_nodes;
+    B->n_nodes += 2;
+  }
+  return i;
+}
+
+static void set_node_box(bnode_t* n, const box_t* b) {
+  for (int i = 0; i < 3; ++i) {
+    n->lo[i] = nextafterf((float)b->lo[i], -INFINITY);
+    n->hi[i] = nextafterf((float)b->hi[i], INFINITY);
+  }
+}
+
+/* builds the subtree of idx[first, first + count) into node ni */
+static void build_node(build_t* B, uint32_t ni, uint32_t first, uint32_t count, uint32_t depth) {
+  box_t bb, cb;
+  box_empty(&bb);
+  box_empty(&cb);
+  for (uint32_t i = first; i < first + count; ++i) {
+    const uint32_t j = B->idx[i];
+    box_grow(&bb, &B->tbox[j]);
+    box_t c = {{B->cen[3 * j], B->cen[3 * j + 1], B->cen[3 * j + 2]}, {B->cen[3 * j], B->cen[3 * j + 1], B->cen[3 * j + 2]}};
+    box_grow(&cb, &c);
+  }
+  bnode_t* n = &B->nodes[ni];
+  set_node_box(n, &bb);
+  if (depth > B->depth) B->depth = depth;
+  if (count <= BVH_LEAF) {
+    n->first = first;
+    n->count = count;
+    return;
+  }
+  /* binned SAH over the centroid bounds */
+  int best_axis = -1, best_split = 0;
+  double best_cost = INFINITY;
+  for (int ax = 0; ax < 3; ++ax) {
+    double ext = cb.hi[ax] - cb.lo[ax];
+    if (!(ext > 0.0)) continue;
+    box_t bin_box[BVH_BINS];
+    uint32_t bin_n[BVH_BINS] = {0};
+    for (int k = 0; k < BVH_BINS; ++k) box_empty(&bin_box[k]);
+    const double scale = BVH_BINS / ext;
+    for (uint32_t i = first; i < first + count; ++i) {
+      const uint32_t j = B->idx[i];
+      int k = (int)((B->cen[3 * j + ax] - cb.lo[ax]) * scale);
+      if (k >= BVH_BINS) k = BVH_BINS - 1;
+      if (k < 0) k = 0;
+      bin_n[k]++;
+      box_grow(&bin_box[k], &B->tbox[j]);
+    }
+    double right_area[BVH_BINS];
+    uint32_t right_n[BVH_BINS];
+    box_t acc;
+    box_empty(&acc);
+    uint32_t cnt = 0;
+    for (int k = BVH_BINS - 1; k > 0; --k) {
+      box_grow(&acc, &bin_box[k]);
+      cnt += bin_n[k];
+      right_area[k] = box_area(&acc);
+      right_n[k] = cnt;
+    }
+    box_empty(&acc);
+    cnt = 0;
+    for (int k = 0; k < BVH_BINS - 1; ++k) {
+      box_grow(&acc, &bin_box[k]);
+      cnt += bin_n[k];
+      if (cnt == 0 || right_n[k + 1] == 0) continue;
+      double cost = box_area(&acc) * cnt + right_area[k + 1] * right_n[k + 1];
+      if (cost < best_cost) {
+        best_cost = cost;
+        best_axis = ax;
+        best_split = k + 1;
+      }
+    }
+  }
+  uint32_t mid;
+  if (best_axis < 0) {
+    mid = first + count / 2; /* all centroids equal: split the list */
+  } else {
+    const double scale = BVH_BINS / (cb.hi[best_axis] - cb.lo[best_axis]);
+    uint32_t i = first, e = first + count;
+    while (i < e) {
+      const uint32_t j = B->idx[i];
+      int k = (int)((B->cen[3 * j + best_axis] - cb.lo[best_axis]) * scale);
+      if (k >= BVH_BINS) k = BVH_BINS - 1;
+      if (k < best_split) {
+        ++i;
+      } else {
+        B->idx[i] = B->idx[--e];
+        B->idx[e] = j;
+      }
+    }
+    mid = i;
+    if (mid == first || mid == first + count) mid = first + count / 2;
+  }
+  const uint32_t left = node_alloc2(B);
+  n->first = left;
+  n->count = 0;
+  const uint32_t nl = mid - first, nr = first + count - mid;
+#ifdef _OPENMP
+  if (count > 65536) {
+#pragma omp task
+    build_node(B, left, first, nl, depth + 1);
+#pragma omp task
+    build_node(B, left + 1, mid, nr, depth + 1);
+#pragma omp taskwait
+    return;
+  }
+#endif
+  build_node(B, left, first, nl, depth + 1);
+  build_node(B, left + 1, mid, nr, depth + 1);
+}
+
+/* Builds the BVH of a triangle soup (and, for the fast mode, the window
+   tables of the materials).  Returns NULL on bad input. */
+orc_bvh* orc_bvh_build(const float* vertices, uint32_t n_vertices, const uint32_t* triangles, uint32_t n_triangles,
+                       const orc_material* materials, uint32_t n_materials, uint32_t* depth_out) {
+  if (n_triangles == 0) return NULL;
+  for (size_t i = 0; i < 3 * (size_t)n_triangles; ++i)
+    if (triangles[i] >= n_vertices) return NULL;
+  build_t B;
+  memset(&B, 0, sizeof B);
+  B.tbox = (box_t*)malloc(sizeof(box_t) * n_triangles);
+  B.cen = (double*)malloc(sizeof(double) * 3 * n_triangles);
+  B.idx = (uint32_t*)malloc(sizeof(uint32_t) * n_triangles);
+  B.cap = 2 * n_triangles;
+  B.nodes = (bnode_t*)calloc(B.cap, sizeof(bnode_t));
+  scene_t s = {vertices, triangles, NULL, NULL, n_vertices, n_triangles, 0, NULL, 0};
+  for (uint32_t j = 0; j < n_triangles; ++j) {
+    double v0[3], v1[3], v2[3];
+    tri_vertices(&s, j, v0, v1, v2);
+    box_t b;
+    double ext = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      b.lo[i] = fmin(v0[i], fmin(v1[i], v2[i]));
+      b.hi[i] = fmax(v0[i], fmax(v1[i], v2[i]));
+      ext = fmax(ext, b.hi[i] - b.lo[i]);
+    }
+    const double grow = 1e-4 * ext + 1e-6;
+    for (int i = 0; i < 3; ++i) {
+      b.lo[i] -= grow;
+      b.hi[i] += grow;
+      B.cen[3 * (size_t)j + i] = 0.5 * (b.lo[i] + b.hi[i]);
+    }
+    B.tbox[j] = b;
+    B.idx[j] = j;
+  }
+  B.n_nodes = 1;
+#ifdef _OPENMP
+#pragma omp parallel
+#pragma omp single
+#endif
+  build_node(&B, 0, 0, n_triangles, 1);
+  free(B.tbox);
+  free(B.cen);
+  orc_bvh* h = (orc_bvh*)calloc(1, sizeof(orc_bvh));
+  h->nodes = B.nodes;
+  h->idx = B.idx;
+  h->n_nodes = B.n_nodes;
+  h->depth = B.depth;
+  if (depth_out) *depth_out = B.depth;
+  if (B.depth + 1 >= BVH_STACK) {
+    free(h->nodes);
+    free(h->idx);
+    free(h);
+    return NULL;
+  }
+  /* window tables: G_k = integral of the density over [0, x_k], summed cell by
+     cell with the oracle's own window integral, and the density f_k */
+  h->nm = n_materials;
+  if (materials && n_materials) {
+    const double hx = 0.5 * M_PI / WTAB_CELLS;
+    h->wtab = (double*)malloc(sizeof(double) * 2 * (WTAB_CELLS + 1) * n_materials);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int mi = 0; mi < (int)n_materials; ++mi) {
+      double* G = h->wtab + (size_t)mi * 2 * (WTAB_CELLS + 1);
+      double* F = G + (WTAB_CELLS + 1);
+      G[0] = 0.0;
+      for (int k = 0; k <= WTAB_CELLS; ++k) {
+        F[k] = orc_brdf_density(&materials[mi], k * hx);
+        if (k < WTAB_CELLS) G[k + 1] = G[k] + orc_brdf_window(&materials[mi], (k + 0.5) * hx, hx);
+      }
+    }
+  }
+  return h;
+}
+
+void orc_bvh_free(orc_bvh* h) {
+  if (!h) return;
+  free(h->nodes);
+  free(h->idx);
+  free(h->wtab);
+  free(h);
+}
+
+/* integral of material mi's density over [0, x], 0 <= x <= pi/2: cubic
+   Hermite interpolation of the tabulated integral (its derivative is the
+   density) */
+static double wtab_prim(const orc_bvh* h, uint32_t mi, double x) {
+  const double hx = 0.5 * M_PI / WTAB_CELLS;
+  const double* G = h->wtab + (size_t)mi * 2 * (WTAB_CELLS + 1);
+  const double* F = G + (WTAB_CELLS + 1);
+  double u = x / hx;
+  if (!(u > 0.0)) return 0.0;
+  if (u >= WTAB_CELLS) return G[WTAB_CELLS];
+  int k = (int)u;
+  double t = u - k, t2 = t * t, t3 = t2 * t;
+  return (2 * t3 - 3 * t2 + 1) * G[k] + (t3 - 2 * t2 + t) * hx * F[k] + (-2 * t3 + 3 * t2) * G[k + 1] +
+         (t3 - t2) * hx * F[k + 1];
+}
+
+/* W(w) of Eq. 4: the oracle's quadrature, or in the fast mode the table */
+static double window(const scene_t* s, uint32_t mi, double w, double b) {
+  const orc_material* m = &s->mat[mi];
+  if (!(s->fast && s->bvh && s->bvh->wtab)) return orc_brdf_window(m, w, b);
+  double lo = w - 0.5 * b, hi = w + 0.5 * b;
+  if (lo < -M_PI / 2) lo = -M_PI / 2;
+  if (hi > M_PI / 2) hi = M_PI / 2;
+  if (!(hi > lo)) return 0.0;
+  double gh = hi >= 0.0 ? wtab_prim(s->bvh, mi, hi) : -wtab_prim(s->bvh, mi, -hi);
+  double gl = lo >= 0.0 ? wtab_prim(s->bvh, mi, lo) : -wtab_prim(s->bvh, mi, -lo);
+  return gh - gl;
+}
+
+/* entry and exit distance of the ray through a node box; 0 if it misses
+   [t_lo, t_hi] */
+static int node_range(const bnode_t* n, const double o[3], const double inv[3], double t_lo, double t_hi,
+                      double* t_in) {
+  double a = t_lo, b = t_hi;
+  for (int i = 0; i < 3; ++i) {
+    double x0, x1;
+    if (isinf(inv[i])) {
+      if (o[i] < (double)n->lo[i] || o[i] > (double)n->hi[i]) return 0;
+      continue;
+    }
+    x0 = ((double)n->lo[i] - o[i]) * inv[i];
+    x1 = ((double)n->hi[i] - o[i]) * inv[i];
+    if (x0 > x1) {
+      double t = x0;
+      x0 = x1;
+      x1 = t;
+    }
+    if (x0 > a) a = x0;
+    if (x1 < b) b = x1;
+    if (a > b) return 0;
+  }
+  *t_in = a;
+  return 1;
+}
+
+static void inv_dir(const double d[3], double inv[3]) {
+  for (int i = 0; i < 3; ++i) inv[i] = d[i] != 0.0 ? 1.0 / d[i] : INFINITY;
+}
+
+static hit_t closest_hit_bvh(const scene_t* s, const double o[3], const double d[3], double t_min, uint32_t skip) {
+  const orc_bvh* B = s->bvh;
+  hit_acc a;
+  hit_begin(&a);
+  double inv[3];
+  inv_dir(d, inv);
+  const double t_lo = s->fast ? t_min : t_min - 1e-5;
+  uint32_t stack[BVH_STACK];
+  double stack_t[BVH_STACK];
+  int sp = 0;
+  double t0;
+  if (!node_range(&B->nodes[0], o, inv, t_lo, INFINITY, &t0)) return hit_finish(&a);
+  stack[sp] = 0;
+  stack_t[sp++] = t0;
+  while (sp > 0) {
+    --sp;
+    const double limit = s->fast ? a.h.t : fmax(a.h.t * (1.0 + 1e-5), t_min + 1e-5) + 1e-9;
+    if (stack_t[sp] > limit) continue;
+    const bnode_t* n = &B->nodes[stack[sp]];
+    if (n->count) {
+      for (uint32_t i = n->first; i < n->first + n->count; ++i) {
+        const uint32_t j = B->idx[i];
+        if (j != skip) hit_consider(s, j, o, d, t_min, &a);
+      }
+      continue;
+    }
+    double tl, tr;
+    const int hl = node_range(&B->nodes[n->first], o, inv, t_lo, limit, &tl);
+    const int hr = node_range(&B->nodes[n->first + 1], o, inv, t_lo, limit, &tr);
+    if (hl && hr) {
+      const int near_left = tl <= tr;
+      stack[sp] = near_left ? n->first + 1 : n->first;
+      stack_t[sp++] = near_left ? tr : tl;
+      stack[sp] = near_left ? n->first : n->first + 1;
+      stack_t[sp++] = near_left ? tl : tr;
+    } else if (hl) {
+      stack[sp] = n->first;
+      stack_t[sp++] = tl;
+    } else if (hr) {
+      stack[sp] = n->first + 1;
+      stack_t[sp++] = tr;
+    }
+  }
+  return hit_finish(&a);
+}
+
+static int occluded_bvh(const scene_t* s, const double p[3], const double dir[3], double t_min, double dist,
+                        uint32_t skip, int* flag) {
+  const orc_bvh* B = s->bvh;
+  double inv[3];
+  inv_dir(dir, inv);
+  const double t_lo = s->fast ? t_min : t_min - 1e-5;
+  const double t_hi = s->fast ? dist : dist * (1.0 + 1e-5) + 1e-5;
+  uint32_t stack[BVH_STACK];
+  int sp = 0, occ = 0;
+  double t0;
+  if (!node_range(&B->nodes[0], p, inv, t_lo, t_hi, &t0)) return 0;
+  stack[sp++] = 0;
+  while (sp > 0) {
+    const bnode_t* n = &B->nodes[stack[--sp]];
+    if (n->count) {
+      for (uint32_t i = n->first; i < n->first + n->count; ++i) {
+        const uint32_t j = B->idx[i];
+        if (j != skip) occ_consider(s, j, p, dir, t_min, dist, &occ, flag);
+      }
+      if (occ && s->fast) return 1;
+      continue;
+    }
+    for (uint32_t c = n->first; c < n->first + 2; ++c)
+      if (node_range(&B->nodes[c], p, inv, t_lo, t_hi, &t0)) stack[sp++] = c;
   }
   return occ;
 }
@@ -587,6 +1041,7 @@ typedef struct {
   uint8_t* flagged;   /* [Ns] */
   double* tally;      /* [Ns][4]: returned, absorbed, escaped, terminated */
   uint64_t queries, shadow_queries;
+  int keep_segs;      /* store the segments (else only count them) */
 } column_t;
 
 static void push_ret(column_t* c, uint32_t k, double range, double E) {
@@ -601,6 +1056,10 @@ static void push_ret(column_t* c, uint32_t k, double range, double E) {
 }
 
 static void push_seg(column_t* c, const orc_segment* s) {
+  if (!c->keep_segs) {
+    c->n_seg++;
+    return;
+  }
   if (c->n_seg == c->cap_seg) {
     c->cap_seg = c->cap_seg ? 2 * c->cap_seg : 256;
     c->seg = (orc_segment*)realloc(c->seg, c->cap_seg * sizeof(orc_segment));
@@ -788,7 +1247,7 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
       double dn[3];
       for (int i = 0; i < 3; ++i) dn[i] = -n[i];
       double theta0 = orc_angle(ray.d, dn);
-      double ret_t = E1 * R * orc_brdf_window(m, 2.0 * theta0, b);
+      double ret_t = E1 * R * window(s, mid, 2.0 * theta0, b);
 
       /* air-path return (multipath), bounce >= 1 only */
       double ret_a = 0.0, range_a = 0.0;
@@ -818,7 +1277,7 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
           if (side >= 0.0) candidate = 0;
         }
         if (candidate) {
-          double w_a = orc_brdf_window(m, orc_angle(dir_out, v), b);
+          double w_a = window(s, mid, orc_angle(dir_out, v), b);
           if (w_a > 0.0) {
             double dir[3] = {v[0] / dist, v[1] / dist, v[2] / dist};
             int vflag = 0;
@@ -939,21 +1398,29 @@ static void bin_column(const orc_params* p, const column_t* col, double* img, do
 /* ------------------------------------------------------------------------ */
 /* public scan entry                                                        */
 /* ------------------------------------------------------------------------ */
-int orc_scan(const float* vertices, uint32_t n_vertices, const uint32_t* triangles, uint32_t n_triangles,
-             const uint16_t* material_ids, const orc_material* materials, uint32_t n_materials, const orc_pose* pose,
-             const orc_params* p, const uint32_t* az_list, uint32_t n_cols, double* image, double* image_masked,
-             double* slack, uint8_t* ray_flags, double* tallies, orc_segment* segs, uint64_t seg_cap,
-             uint64_t* n_segs, uint64_t* counts, int n_threads) {
+/* The scan with the closest-hit and any-hit queries answered through a CPU
+   BVH built by orc_bvh_build (bvh != NULL) instead of brute force; fast != 0
+   selects the timing mode (strict pruning, tabulated windows, no parity
+   flags).  bvh == NULL is the oracle itself. */
+int orc_scan_accel(const float* vertices, uint32_t n_vertices, const uint32_t* triangles, uint32_t n_triangles,
+                   const uint16_t* material_ids, const orc_material* materials, uint32_t n_materials,
+                   const orc_pose* pose, const orc_params* p, const uint32_t* az_list, uint32_t n_cols, double* image,
+                   double* image_masked, double* slack, uint8_t* ray_flags, double* tallies, orc_segment* segs,
+                   uint64_t seg_cap, uint64_t* n_segs, uint64_t* counts, int n_threads, const orc_bvh* bvh,
+                   int fast) {
   if (p->n_azimuth == 0 || p->rays_per_beam == 0 || p->n_bins == 0 || p->max_bounces == 0) return 1;
   for (uint32_t j = 0; j < n_triangles; ++j) {
     for (int i = 0; i < 3; ++i)
       if (triangles[3 * (size_t)j + i] >= n_vertices) return 2;
     if (material_ids[j] >= n_materials) return 2;
   }
-  scene_t s = {vertices, triangles, material_ids, materials, n_vertices, n_triangles, n_materials};
+  if (bvh && bvh->wtab && bvh->nm != n_materials) return 2;
+  scene_t s = {vertices, triangles, material_ids, materials, n_vertices, n_triangles, n_materials, bvh,
+               bvh ? fast : 0};
   column_t* cols = (column_t*)calloc(n_cols, sizeof(column_t));
   const uint32_t ns = p->rays_per_beam;
   for (uint32_t c = 0; c < n_cols; ++c) {
+    cols[c].keep_segs = segs != NULL;
     cols[c].flagged = ray_flags + (size_t)c * ns;
     cols[c].tally = tallies + (size_t)c * ns * 4;
     memset(cols[c].tally, 0, sizeof(double) * 4 * ns);
@@ -971,8 +1438,9 @@ int orc_scan(const float* vertices, uint32_t n_vertices, const uint32_t* triangl
   }
   uint64_t ns_out = 0, q = 0, sq = 0, nret = 0;
   for (uint32_t c = 0; c < n_cols; ++c) {
-    for (size_t i = 0; i < cols[c].n_seg; ++i) {
-      if (segs && ns_out < seg_cap) segs[ns_out] = cols[c].seg[i];
+    if (!segs) ns_out += cols[c].n_seg;
+    for (size_t i = 0; segs && i < cols[c].n_seg; ++i) {
+      if (ns_out < seg_cap) segs[ns_out] = cols[c].seg[i];
       ns_out++;
     }
     q += cols[c].queries;
@@ -989,6 +1457,16 @@ int orc_scan(const float* vertices, uint32_t n_vertices, const uint32_t* triangl
     counts[2] = nret;
   }
   return (segs && ns_out > seg_cap) ? 3 : 0;
+}
+
+int orc_scan(const float* vertices, uint32_t n_vertices, const uint32_t* triangles, uint32_t n_triangles,
+             const uint16_t* material_ids, const orc_material* materials, uint32_t n_materials, const orc_pose* pose,
+             const orc_params* p, const uint32_t* az_list, uint32_t n_cols, double* image, double* image_masked,
+             double* slack, uint8_t* ray_flags, double* tallies, orc_segment* segs, uint64_t seg_cap,
+             uint64_t* n_segs, uint64_t* counts, int n_threads) {
+  return orc_scan_accel(vertices, n_vertices, triangles, n_triangles, material_ids, materials, n_materials, pose, p,
+                        az_list, n_cols, image, image_masked, slack, ray_flags, tallies, segs, seg_cap, n_segs, counts,
+                        n_threads, NULL, 0);
 }
 
 /* number of threads an OpenMP region would use */

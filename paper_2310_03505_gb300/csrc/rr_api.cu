@@ -163,6 +163,23 @@ int check_params(const rr_pose* pose, const rr_sensor_params* p) {
   return RR_OK;
 }
 
+// The scene's buffers live on the device that was current when it was
+// created; its kernels must be launched there.  A call made with another
+// device current is refused before anything is queued: without peer access
+// the kernels would fault on the scene's pointers.
+int check_device(const rr_scene* s, const char* who) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RR_ERR_CUDA, std::string(who) + ": no usable current device");
+  }
+  if (dev != s->device)
+    return fail(RR_ERR_INVALID_ARG, std::string(who) + ": the scene lives on device " + std::to_string(s->device) +
+                                        " but device " + std::to_string(dev) + " is current");
+  return RR_OK;
+}
+
 // read (and clear) the sticky device status of a context; waits for the stream
 int device_status(ExecCtx* x, cudaStream_t st) {
   RR_CHECK_CUDA(cudaMemcpyAsync(x->h_ctr, x->d_ctr, sizeof(ScanCounters), cudaMemcpyDeviceToHost, st),
@@ -422,6 +439,7 @@ int rr_scene_create(const float* vertices, uint32_t n_vertices, const uint32_t* 
 
 int rr_scene_update_vertices(rr_scene* s, const float* vertices) {
   if (!s || !vertices) return fail(RR_ERR_INVALID_ARG, "scene and vertices must not be NULL");
+  if (int rc = check_device(s, "rr_scene_update_vertices")) return rc;
   cudaStream_t st = t_stream;
   cudaEvent_t ev;
   if (s->nv)
@@ -483,6 +501,7 @@ int rr_scene_export_bvh(const rr_scene* s, uint32_t* morton, uint32_t* perm, uin
 int rr_scene_set_lobe(rr_scene* s, uint32_t material, const float* density) {
   if (!s || !density) return fail(RR_ERR_INVALID_ARG, "scene and density must not be NULL");
   if (material >= s->nm) return fail(RR_ERR_INVALID_ARG, "material index out of range");
+  if (int rc = check_device(s, "rr_scene_set_lobe")) return rc;
   if (!(s->raw_flags[material] & RR_MAT_TABULATED_LOBE))
     return fail(RR_ERR_INVALID_ARG, "the material was not created with RR_MAT_TABULATED_LOBE");
   std::vector<float> h(rr::kLobeSamples);
@@ -509,6 +528,7 @@ int rr_scene_set_lobe(rr_scene* s, uint32_t material, const float* density) {
 
 int rr_scene_export_wide(rr_scene* s, void* nodes, uint32_t cap, uint32_t* n_nodes, float* tris) {
   if (!s) return fail(RR_ERR_INVALID_ARG, "scene must not be NULL");
+  if (int rc = check_device(s, "rr_scene_export_wide")) return rc;
   if (s->nt && s->wide_stale) RR_CHECK_CUDA(build_wide(s, t_stream), "collapsing the wide BVH");
   RR_CHECK_CUDA(cudaStreamSynchronize(t_stream), "synchronising");
   uint32_t wctr[8] = {0};
@@ -528,6 +548,7 @@ int rr_scan_async(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, f
   if (!s || !out_polar) return fail(RR_ERR_INVALID_ARG, "scene and out_polar must not be NULL");
   int rc = check_params(pose, p);
   if (rc != RR_OK) return rc;
+  if ((rc = check_device(s, "rr_scan_async")) != RR_OK) return rc;
   if (!is_device_ptr(out_polar)) return fail(RR_ERR_INVALID_ARG, "rr_scan_async needs a device output");
   return scan_split(s, pose, p, out_polar, t_stream, true);
 }
@@ -541,6 +562,7 @@ int rr_scan(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, float* 
   if (!s || !out_polar) return fail(RR_ERR_INVALID_ARG, "scene and out_polar must not be NULL");
   int rc = check_params(pose, p);
   if (rc != RR_OK) return rc;
+  if ((rc = check_device(s, "rr_scan")) != RR_OK) return rc;
   cudaStream_t st = t_stream;
   const size_t img_bytes = (size_t)p->n_azimuth * p->n_bins * sizeof(float);
   const bool dev = is_device_ptr(out_polar);
@@ -562,6 +584,7 @@ int rr_scan_debug(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, c
   if (!s || !out_polar) return fail(RR_ERR_INVALID_ARG, "scene and out_polar must not be NULL");
   int rc = check_params(pose, p);
   if (rc != RR_OK) return rc;
+  if ((rc = check_device(s, "rr_scan_debug")) != RR_OK) return rc;
   cudaStream_t st = t_stream;
   const size_t n0 = (size_t)p->n_azimuth * p->rays_per_beam;
   const size_t img_bytes = (size_t)p->n_azimuth * p->n_bins * sizeof(float);

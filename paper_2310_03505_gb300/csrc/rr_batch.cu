@@ -502,7 +502,7 @@ static int check_batch(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_s
     if (rc != RR_OK) return fail(rc, "scan " + std::to_string(i) + ": " + rr_last_error());
     if (!out[i]) return fail(RR_ERR_INVALID_ARG, "scan " + std::to_string(i) + ": NULL output");
   }
-  return RR_OK;
+  return check_device(s, "rr_scan_batch");
 }
 
 static int cfg_check(const rr_batch_config* c) {
@@ -658,6 +658,7 @@ int rr_autotune(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor_p
     const int rc = check_params(&poses[i], &params[i]);
     if (rc != RR_OK) return rc;
   }
+  if (int rc = check_device(s, "rr_autotune")) return rc;
   cudaStream_t st = current_stream();
   size_t total = 0;
   uint64_t rays = 0;

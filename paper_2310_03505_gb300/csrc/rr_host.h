@@ -198,6 +198,8 @@ int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 bool is_device_ptr(const void* p);
 int check_params(const rr_pose* pose, const rr_sensor_params* p);
+// RR_ERR_INVALID_ARG unless the current device is the scene's (who: caller name for the message)
+int check_device(const rr_scene* s, const char* who);
 // worst-case workspace of scans ps[0..n) traced together, clamped to limit
 WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit, const uint32_t* az_count = nullptr);
 // split n scans into launch sequences that respect the limits of cfg

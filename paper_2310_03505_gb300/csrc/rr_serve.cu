@@ -344,6 +344,9 @@ int rr_serve_submit(rr_server* sv, rr_scene* scene, const rr_pose* pose, const r
   if (!sv || !scene || !out_polar || !ticket) return fail(RR_ERR_INVALID_ARG, "NULL argument");
   int rc = check_params(pose, params);
   if (rc != RR_OK) return rc;
+  if (scene->device != sv->device)
+    return fail(RR_ERR_INVALID_ARG, "rr_serve_submit: the scene lives on device " + std::to_string(scene->device) +
+                                        ", the server on device " + std::to_string(sv->device));
   Request r;
   r.scene = scene;
   r.pose = *pose;

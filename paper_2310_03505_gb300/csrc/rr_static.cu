@@ -18,7 +18,14 @@
 // The scan reads nothing from it before writing: the kernels write the ray
 // queues, hits and return records before they read them, and the trace kernel
 // clears every tile flag a bounce uses.  Calls that overlap on the GPU
-// (several streams, threads or scenes at once) race on the array.
+// (several streams, threads or scenes at once) race on the array.  The scan's
+// status counters are the scene's own (those of its rr_scan path), so a
+// static call that overlaps any other scan of the same scene also races on
+// them.
+//
+// The static path always traverses the binary BVH, which every build makes:
+// both node formats give the same closest hit for every query, and the
+// binary nodes never need the lazy collapse of the 8-wide BVH.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -65,6 +72,7 @@ extern "C" int rr_scan_static(rr_scene* s, const rr_pose* pose, const rr_sensor_
   if (!s || !out_polar) return fail(RR_ERR_INVALID_ARG, "scene and out_polar must not be NULL");
   int rc = check_params(pose, p);
   if (rc != RR_OK) return rc;
+  if ((rc = check_device(s, "rr_scan_static")) != RR_OK) return rc;
   if (!is_device_ptr(out_polar)) return fail(RR_ERR_INVALID_ARG, "rr_scan_static needs a device output");
   const WsLayout L = plan_workspace(p, 1, kStaticScratchBytes);
   if (L.total > kStaticScratchBytes || L.clamped)
@@ -81,6 +89,7 @@ extern "C" int rr_scan_static(rr_scene* s, const rr_pose* pose, const rr_sensor_
   float* const images[1] = {out_polar};
   LaunchCfg cfg = s->cfg;
   cfg.use_graph = 0;
+  cfg.node_format = RR_NODES_BINARY;
   rc = batch_enqueue(s, &s->main, pose, p, images, 1, nullptr, st, scratch, L, false, false, cfg, desc);
   if (rc != RR_OK) return rc;
   return device_status(&s->main, st);

@@ -42,3 +42,30 @@ def test_bounded_waits_give_up_and_context_survives(rrlib):
 def test_unknown_wait_is_refused(rrlib):
     rc, _ = rr.rr_selftest_wait(7)
     assert rc == rr.RR_ERR_INVALID_ARG
+
+
+def test_scene_used_from_another_device_is_refused(rrlib):
+    """A scene's buffers live on the device that was current at creation;
+    every call that would launch its kernels with another device current is
+    refused before anything is queued (nothing runs on the wrong device).
+    Needs two GPUs."""
+    import torch
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs")
+    sc, pz, params = scenes.config_tiny()
+    params = scenes.sensor(**{**params, "n_azimuth": 16})
+    torch.cuda.set_device(0)
+    h = rr.rr_scene_create(sc.vertices, sc.triangles, sc.material_ids, sc.materials)
+    try:
+        torch.cuda.set_device(1)
+        img = np.zeros((params["n_azimuth"], params["n_bins"]), np.float32)
+        with pytest.raises(rr.RRError) as e:
+            rr.rr_scan(h, pz, params, img)
+        assert e.value.code == rr.RR_ERR_INVALID_ARG and "device" in str(e.value)
+        out = torch.zeros(params["n_azimuth"], params["n_bins"], device="cuda:1")
+        with pytest.raises(rr.RRError) as e:
+            rr.rr_scan_static(h, pz, params, out)
+        assert e.value.code == rr.RR_ERR_INVALID_ARG
+    finally:
+        torch.cuda.set_device(0)
+        rr.rr_scene_destroy(h)

@@ -29,7 +29,7 @@ MUTANTS = {
     "brdf_norm_drop_B": ("return m->A * M_PI + 2.0 * m->B + S * sqrt(M_PI) * gr;",
                          "return m->A * M_PI + S * sqrt(M_PI) * gr;"),
     "brdf_window_B_term": ("m->B * (sin(hi) - sin(lo))", "m->B * (cos(lo) - cos(hi))"),
-    "traveled_angle": ("orc_brdf_window(m, 2.0 * theta0, b)", "orc_brdf_window(m, theta0, b)"),
+    "traveled_angle": ("window(s, mid, 2.0 * theta0, b)", "window(s, mid, theta0, b)"),
     "attenuation_factor": ("exp(-2.0 * alpha_np(", "exp(-alpha_np("),
     "geometric_range": ("double L1 = ray.L + n_cur * h.t;", "double L1 = ray.L + h.t;"),
     "air_range_half": ("range_a = 0.5 * (L1 + dist);", "range_a = L1 + dist;"),
