@@ -1,21 +1,23 @@
 """Benchmark of the radar scan hot path on GB300.
 
-One step = one pass of the whole hot path on the medium campus workload
-(about 200k triangles, 400 beams x 200 rays, at most 5 bounces, refraction
-and multipath on, 2000 range bins): BVH rebuild from the resident vertices
-(ingest, Morton, radix sort, Karras hierarchy, refit, and with --step-bvh
-sah_top the binned-SAH top over the LBVH's subtrees) followed by one polar
+One step = one pass of the whole hot path on the large plain scan (the
+~5M-triangle city, 400 beams x 1000 rays, at most 8 bounces, refraction and
+multipath on, 4000 range bins): BVH rebuild from the resident vertices
+(ingest, Morton, radix sort, Karras hierarchy, refit) followed by one polar
 scan (raygen, trace / shade per bounce, range-bin accumulation, post pass).
-The batched and served scenes are built once, with --scene-bvh (default: the
-SAH top).
-Each step uses a new scan id, so every step traces new rays.
+Each step uses a new scan id, so every step traces new rays.  The city's BVH
+and triangles (~0.56 GB) do not fit in L2.
 
 Metric: Mrays/s = closest-hit queries over all bounces / device time of the
 steps (CUDA events on the library's stream; L2 flushed between steps with a
 256 MiB write, outside the timed events).  Also reported: scans/s, per-step
-latency p50/p99, the roofline of the dominant kernel (trace), the oracle
-timed on the host cores, an end-to-end figure through the C ABI with host
-buffers, and GPU clocks sampled during the timed region.
+latency p50/p99, the scans alone on a resident BVH, the roofline of the
+dominant kernel (closest-hit queries) against HBM and L2, the CPU-BVH
+baseline (the oracle's physics through a CPU BVH, full scan, all host
+cores), an end-to-end figure through the C ABI with host buffers, and GPU
+clocks sampled during the timed region.  Extra objects: the medium campus
+(~200k triangles) as the same kind of step, the batched and the served
+workloads.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -38,11 +40,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "campus_200k_tris_400x200_rays_5_bounces_2000_bins"
+LARGE_WORKLOAD = "city_5M_tris_400x1000_rays_8_bounces_4000_bins"
+MEDIUM_WORKLOAD = "campus_200k_tris_400x200_rays_5_bounces_2000_bins"
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "Mrays/s (all bounces) & scans/s on 1 GB300; p50/p99 served scan latency"
 RAY_IO_BYTES = 48 + 16          # ray record read + hit record written per closest-hit query
 NODE_BYTES, TRI_BYTES = 64, 48  # BVH node and triangle record
+L2_FLUSH_NOTE = "flushed between steps (256 MiB write, outside the timed events)"
 
 
 # ------------------------------------------------------------------ helpers
@@ -130,12 +134,34 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_from_profiles():
-    """DRAM bytes of the closest-hit query kernel per bounce (all azimuth
-    ranges of the bounce) from the committed ncu summary, valid only while the
-    kernel source matches the hash it was taken on."""
+def l2_copy_gbs(device) -> float:
+    """L2 bandwidth as a device-to-device copy of an L2-resident buffer
+    (24 MiB read + 24 MiB written, 20 copies per timing, best of 10): the
+    denominator of the L2 fraction (no measured L2 peak exists)."""
+    import torch
+    n = (24 << 20) // 4
+    a = torch.ones(n, device=device)
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    best = float("inf")
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 20 * 2 * a.numel() * 4 / (best * 1e-3) / 1e9
+
+
+def profile_counters(name: str):
+    """ncu counters of the closest-hit query kernel from the committed
+    summary ``profiles/<name>.txt``, valid only while the kernel source
+    matches the hash they were taken on (else None)."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "query_kernel_campus_ncu.txt")
+    p = os.path.join(ROOT, "profiles", name + ".txt")
     src = os.path.join(ROOT, "paper_2310_03505_gb300", "csrc", "rr_trace.cu")
     if not (os.path.exists(p) and os.path.exists(src)):
         return None
@@ -143,67 +169,83 @@ def traffic_from_profiles():
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if d.get("source_sha256_16") != h:
         return None
-    return d.get("dram_bytes_per_closest_bounce")
+    return d
 
 
-# ------------------------------------------------------------------ oracle arm
-def oracle_sample(sc, pz, params, budget_s: float = 12.0, min_cols: int = 2):
-    """Time the FP64 oracle (as it stands) on a bounded sample of azimuth
-    columns of the same workload; returns (Mrays/s, cores, sample text, queries, seconds)."""
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+# ------------------------------------------------------------------ CPU arms
+def cpu_bvh_baseline(sc, pz, params):
+    """The CPU-BVH baseline: the oracle's physics (FP64) with its queries
+    answered through its own binned-SAH CPU BVH, beam windows from tables,
+    OpenMP over azimuth columns on all host cores; one full scan of the
+    workload, timed (the CPU BVH build is reported beside it)."""
     from oracle import oracle as orc
-    cores = orc.max_threads()
-    cols, q_tot, t_tot = [], 0, 0.0
-    order = list(np.random.default_rng(12345).permutation(params["n_azimuth"]))
-    while order and (t_tot < budget_s or len(cols) < min_cols):
-        batch = [int(order.pop()) for _ in range(min(cores, len(order)))]
+    orc.build()
+    t0 = time.perf_counter()
+    bvh = orc.Bvh(sc.vertices, sc.triangles, sc.materials)
+    build_s = time.perf_counter() - t0
+    try:
         t0 = time.perf_counter()
-        r = orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, params, az_list=batch,
+        r = orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, params, bvh=bvh, fast=True,
                      want_segments=False)
-        t_tot += time.perf_counter() - t0
-        q_tot += int(r["counts"][0])
-        cols += batch
-    sample = (f"{len(cols)} of {params['n_azimuth']} azimuth columns ({len(cols) * params['rays_per_beam']} "
-              f"initial rays, all bounces), FP64 brute force over all {sc.n_triangles} triangles")
-    return q_tot / t_tot / 1e6, cores, sample, q_tot, t_tot
+        t = time.perf_counter() - t0
+    finally:
+        bvh.close()
+    q = int(r["counts"][0])
+    return {"value": q / t / 1e6, "unit": "Mrays/s", "cores": orc.max_threads(), "kind": "cpu_bvh",
+            "sample": (f"the full scan ({params['n_azimuth']} x {params['rays_per_beam']} rays, <= "
+                       f"{params['max_bounces']} bounces, {params['n_bins']} bins; {q} closest-hit queries), the "
+                       f"oracle's FP64 physics through a binned-SAH CPU BVH over all {sc.n_triangles} triangles, "
+                       "tabulated beam windows, OpenMP over azimuth columns"),
+            "scans_per_s": 1.0 / t, "seconds": t, "cpu_bvh_build_s": build_s, "cpu": cpu_model()}
 
 
-def oracle_reference_steps(sc, pz, params, steps: int, warmup: int, total_s: float = 120.0):
-    """The oracle arm of `--impl reference`: each step traces, in one call on
-    all host cores, one azimuth column per core, every `stride`-th initial ray
-    of each (with all its bounces), the stride chosen once from a full-column
-    call so that the K timed steps take about total_s together.  Returns
-    (Mrays/s, cores, sample text, seconds per step)."""
+def oracle_reference_steps(sc, pz, params, steps: int, warmup: int):
+    """The oracle arm of `--impl reference`: the FP64 brute-force oracle as it
+    stands.  Each step traces, in one call on all host cores, one azimuth
+    column per core (new columns every step), the first initial ray of each
+    with all its bounces -- a ray tree is the smallest unit the oracle traces,
+    and on the 5M-triangle city one tree takes seconds.  Returns (Mrays/s,
+    cores, sample text, seconds per step)."""
     from oracle import oracle as orc
     cores = orc.max_threads()
     n_az, ns = params["n_azimuth"], params["rays_per_beam"]
     order = list(np.random.default_rng(12345).permutation(n_az))
+    per = min(cores, n_az)
     pos = 0
 
-    def columns():
+    def run(n_cols):
         nonlocal pos
-        c = [int(order[(pos + i) % n_az]) for i in range(min(cores, n_az))]
-        pos += len(c)
-        return c
-
-    def run(stride):
+        cols = [int(order[(pos + i) % n_az]) for i in range(n_cols)]
+        pos += n_cols
         t0 = time.perf_counter()
-        r = orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, {**params, "ray_stride": stride},
-                     az_list=columns(), want_segments=False)
+        r = orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, {**params, "ray_stride": ns},
+                     az_list=cols, want_segments=False)
         return int(r["counts"][0]), time.perf_counter() - t0
 
-    _, t_full = run(1)   # calibration (untimed)
-    per_step = total_s / max(steps, 1)
-    stride = int(min(ns, max(1, math.ceil(t_full / per_step))))
+    # warm-up steps (untimed) trace one ray tree each: a CPU program has no
+    # state to warm beyond its first call
     for _ in range(warmup):
-        run(stride)
+        run(1)
     q_all, t_all = 0, 0.0
     for _ in range(steps):
-        q, t = run(stride)
+        q, t = run(per)
         q_all += q
         t_all += t
-    rays = min(cores, n_az) * len(range(0, ns, stride))
-    sample = (f"per step {min(cores, n_az)} of {n_az} azimuth columns, every {stride}th of their {ns} rays "
-              f"({rays} initial rays, all bounces), FP64 brute force over all {sc.n_triangles} triangles")
+    sample = (f"per step {per} of {n_az} azimuth columns (new ones every step), the first of their {ns} initial "
+              f"rays with all its bounces, FP64 brute force over all {sc.n_triangles} triangles; each warm-up "
+              "step one such ray tree")
     return q_all / t_all / 1e6, cores, sample, t_all / max(steps, 1)
 
 
@@ -215,57 +257,6 @@ def set_bvh(rr, h, bvh: str):
     """Scene BVH build: 'sah_top' (the library default) or 'lbvh'."""
     if bvh != "sah_top":
         rr.rr_batch_config_set(h, bvh_build=rr.RR_BVH_LBVH)
-
-
-LARGE_WORKLOAD = "city_5M_tris_400x1000_rays_8_bounces_4000_bins"
-
-
-def large_bench(device, stream, flush, bvh: str, steps: int = 10, warmup: int = 2, rebuilds: int = 5):
-    """The large plain scan (~5M-triangle city, 400 x 1000 rays, <= 8
-    bounces, 4000 bins) as steps of the same kind as the headline: BVH
-    rebuild + scan, L2 flushed between steps, CUDA events on the stream;
-    then the rebuild alone, timed the same way."""
-    import torch
-    from paper_2310_03505_gb300 import rr, scenes
-    sc, pz, params = scenes.config_large()
-    d_vtx = torch.from_numpy(sc.vertices).to(device)
-    h = rr.rr_scene_create(d_vtx, sc.triangles, sc.material_ids, sc.materials)
-    try:
-        set_bvh(rr, h, bvh)
-        img = torch.zeros(params["n_azimuth"], params["n_bins"], device=device)
-
-        def step(sid):
-            rr.rr_scene_update_vertices(h, d_vtx)
-            rr.rr_scan_async(h, pz, {**params, "scan_id": sid}, img)
-
-        def timed(fn, n):
-            ev = []
-            for i in range(n):
-                flush.fill_(float(i))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                fn(i)
-                e1.record(stream)
-                ev.append((e0, e1))
-            torch.cuda.synchronize()
-            return float(np.sum([a.elapsed_time(b) for a, b in ev]))
-
-        for i in range(warmup):
-            step(90000 + i)
-        rr.rr_scene_sync(h)
-        rr.rr_scene_stats(h, reset=True)
-        ms = timed(lambda i: step(91000 + i), steps)
-        rc = rr.rr_scene_sync(h)
-        q = float(rr.rr_scene_stats(h, reset=True)["closest_queries"])
-        build_ms = timed(lambda i: rr.rr_scene_update_vertices(h, d_vtx), rebuilds) / rebuilds
-        rr.rr_scene_sync(h)
-        return {"workload": LARGE_WORKLOAD, "triangles": sc.n_triangles, "value": q / (ms * 1e-3) / 1e6,
-                "unit": "Mrays/s", "scans_per_s": steps / (ms * 1e-3), "ms_per_step": ms / steps,
-                "steps": steps, "warmup": warmup, "bvh": "LBVH" if bvh == "lbvh" else "LBVH + binned-SAH top",
-                "bvh_rebuild_ms": build_ms, "queries_per_scan": q / steps,
-                "step": "BVH rebuild + polar scan", "status": "ok" if rc is None else str(rc)}
-    finally:
-        rr.rr_scene_destroy(h)
 
 
 def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: int = 0, bvh: str = "sah_top"):
@@ -346,7 +337,8 @@ def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: 
 SERVED_WORKLOAD = "4_scenes_50k_200k_1M_5M_tris_64_robots_poisson_16_512_rays_3_8_bounces_500_4000_bins"
 
 
-def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: int = 0, bvh: str = "sah_top"):
+def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: int = 0, bvh: str = "sah_top",
+                 city=None):
     """Scan requests from 64 simulated robots over 4 resident scenes (50k and
     200k-triangle campuses, the 1M-triangle campus, the 5M-triangle city),
     Poisson arrivals at each rate for `seconds`; every request draws a free
@@ -360,7 +352,7 @@ def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: 
     import torch
     from paper_2310_03505_gb300 import rr, scenes
     scs = [(scenes.campus(target_tris=50_000, seed=0x5EED0004, n_buildings=60, n_cylinders=150, extent=80.0), 70.0),
-           (scenes.campus(), 140.0), (scenes.campus(target_tris=1_000_000), 140.0), (scenes.city(), 290.0)]
+           (scenes.campus(), 140.0), (scenes.campus(target_tris=1_000_000), 140.0), (city if city is not None else scenes.city(), 290.0)]
     hs = [rr.rr_scene_create(torch.from_numpy(sc.vertices).to(device), sc.triangles, sc.material_ids, sc.materials)
           for sc, _ in scs]
     for h in hs:
@@ -444,35 +436,216 @@ def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: 
     return out
 
 
-# ------------------------------------------------------------------ main
+# ------------------------------------------------------------------ plain scan steps
+def headline_config(sc, params, node_format: str, split: int, step_bvh: str, world: int) -> dict:
+    """The `config` of the line (the same for both arms)."""
+    return {"workload": LARGE_WORKLOAD, "triangles": sc.n_triangles, "n_azimuth": params["n_azimuth"],
+            "rays_per_beam": params["rays_per_beam"], "max_bounces": params["max_bounces"],
+            "n_bins": params["n_bins"], "node_format": node_format, "split_streams": split,
+            "bvh": ("LBVH + binned-SAH top over its subtrees of <= 32 triangles" if step_bvh == "sah_top" else "LBVH"),
+            "step": "BVH rebuild + polar scan", "l2": L2_FLUSH_NOTE, "parallelism": f"replicas x{world}"}
+
+
+def plain_bench(rr, device, stream, flush, sc, pz, params, steps, warmup, *, rank=0, world=1, step_bvh="lbvh",
+                node_format="auto", ws_limit_gb=0.0, e2e=True, scan_only=True, clocks=False):
+    """Steps of BVH rebuild + polar scan on one scene (CUDA events on the
+    stream, L2 flushed between steps), with the per-kernel profile of the
+    timed steps, the traversal counters of one untimed scan, and optionally
+    the same metric end to end through the C ABI with host buffers and the
+    scans alone on a resident SAH-top BVH."""
+    import torch
+    d_vtx = torch.from_numpy(sc.vertices).to(device)
+    h = rr.rr_scene_create(d_vtx, sc.triangles, sc.material_ids, sc.materials)
+    out = {}
+    try:
+        set_bvh(rr, h, step_bvh)
+        if node_format != "auto":
+            rr.rr_batch_config_set(h, node_format=rr.RR_NODES_WIDE8 if node_format == "wide" else rr.RR_NODES_BINARY)
+        if ws_limit_gb > 0:
+            rr.rr_batch_config_set(h, workspace_limit=int(ws_limit_gb * (1 << 30)))
+        cfg = rr.rr_batch_config_get(h)
+        nf = "wide8_q8" if cfg["node_format"] == rr.RR_NODES_WIDE8 else "binary_fp32"
+        out.update(node_format=nf, split_streams=cfg["split_streams"], workspace_limit=cfg["workspace_limit"])
+        img = torch.zeros(params["n_azimuth"], params["n_bins"], device=device)
+        warm_ids, step_ids = shard_scan_ids(rank, steps, warmup)
+
+        def step(scan_id):
+            rr.rr_scene_update_vertices(h, d_vtx)
+            rr.rr_scan_async(h, pz, {**params, "scan_id": scan_id}, img)
+
+        for sid in warm_ids:
+            step(sid)
+        rr.rr_scene_sync(h)
+        # traversal counters of one untimed scan (per-query algorithmic bytes)
+        rr.rr_scene_stats(h, reset=True)
+        rr.rr_scan(h, pz, {**params, "scan_id": 10 ** 6 + rank, "count_traversal": True}, img)
+        cst = rr.rr_scene_stats(h, reset=True)
+        node_bytes = rr.WIDE_NODE_BYTES if nf == "wide8_q8" else NODE_BYTES
+        nq = max(cst["closest_queries"], 1)
+        out["nodes_per_query"] = cst["nodes_visited"] / nq
+        out["tris_per_query"] = cst["tris_tested"] / nq
+        out["bytes_per_query"] = out["nodes_per_query"] * node_bytes + out["tris_per_query"] * TRI_BYTES + RAY_IO_BYTES
+        out["visibility"] = {"nodes_per_query": cst["anyhit_nodes_visited"] / max(cst["anyhit_queries"], 1),
+                             "tris_per_query": cst["anyhit_tris_tested"] / max(cst["anyhit_queries"], 1)}
+
+        # timed region
+        rr.rr_profile_read(h, reset=True)
+        rr.rr_profile_enable(h, True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in step_ids]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in step_ids]
+        clock_csv = os.environ.get("RR_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(), f"rr_clocks_rank{rank}.csv")
+        sampler = ClockSampler(device.index or 0, clock_csv) if clocks else None
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i, sid in enumerate(step_ids):
+            flush.fill_(float(i))                      # evict the scene from L2 (outside the events)
+            starts[i].record(stream)
+            step(sid)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        out["wall_s_timed"] = time.perf_counter() - wall0
+        if world > 1:
+            torch.distributed.barrier()
+        rc = rr.rr_scene_sync(h)
+        out["clocks"] = sampler.stop() if sampler else None
+        rr.rr_profile_enable(h, False)
+        prof = rr.rr_profile_read(h, reset=True)
+        st = rr.rr_scene_stats(h, reset=True)
+        per_step = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        local_ms = float(np.sum(per_step))
+        job_ms, job_q = reduce_timing(local_ms, float(st["closest_queries"]), world, device)
+        out.update(value=job_q / (job_ms * 1e-3) / 1e6, unit="Mrays/s", ms_per_step=job_ms / steps,
+                   scans_per_s=world * steps / (job_ms * 1e-3), steps=steps, warmup=warmup,
+                   latency_ms={"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
+                               "kind": "plain scan (rebuild + scan), not served"},
+                   queries_per_scan=st["closest_queries"] / steps, anyhit_per_scan=st["anyhit_queries"] / steps,
+                   closest_queries=st["closest_queries"], gpu_launches=int(st["kernel_launches"]),
+                   kernels_per_step=st["kernel_launches"] / max(steps, 1),
+                   bvh_build_ms_per_step=prof["build"][0] / max(prof["build"][1], 1),
+                   kernel_ms_per_step={k: v[0] / steps for k, v in prof.items()},
+                   kernel_busy_ms_per_step={k: v[2] / steps for k, v in prof.items()},
+                   trace=prof["trace"], status="ok" if rc is None else str(rc))
+
+        # the scans alone on a resident BVH (built once, with the SAH top): the
+        # metric with the build excluded, the build reported beside it
+        if scan_only:
+            rr.rr_batch_config_set(h, bvh_build=rr.RR_BVH_SAH_TOP)   # one build, untimed
+            for i in range(3):
+                rr.rr_scan_async(h, pz, {**params, "scan_id": 5000 + i}, img)
+            rr.rr_scene_sync(h)
+            rr.rr_scene_stats(h, reset=True)
+            n_so = max(3, min(steps, 100))
+            t_so = []
+            for i in range(n_so):
+                flush.fill_(float(i))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rr.rr_scan_async(h, pz, {**params, "scan_id": 6000 + rank * 1000 + i}, img)
+                e1.record(stream)
+                t_so.append((e0, e1))
+            torch.cuda.synchronize()
+            so_ms = float(np.sum([a.elapsed_time(b) for a, b in t_so]))
+            so_rc = rr.rr_scene_sync(h)
+            so_q = float(rr.rr_scene_stats(h, reset=True)["closest_queries"])
+            job_so_ms, job_so_q = reduce_timing(so_ms, so_q, world, device)
+            out["scan_only"] = {"value": job_so_q / (job_so_ms * 1e-3) / 1e6, "unit": "Mrays/s",
+                                "scans_per_s": world * n_so / (job_so_ms * 1e-3), "ms_per_scan": job_so_ms / n_so,
+                                "steps": n_so, "bvh": "LBVH + binned-SAH top, built once (untimed)",
+                                "status": "ok" if so_rc is None else str(so_rc)}
+            set_bvh(rr, h, step_bvh)
+            if step_bvh != "sah_top":
+                rr.rr_batch_config_set(h, bvh_build=rr.RR_BVH_LBVH)
+
+        # end to end through the C ABI with host buffers
+        if e2e:
+            h_vtx = torch.from_numpy(sc.vertices).pin_memory()
+            h_img = torch.zeros(params["n_azimuth"], params["n_bins"]).pin_memory()
+            rr.rr_scene_stats(h, reset=True)
+            t_e2e = 0.0
+            for i, sid in enumerate(step_ids):
+                flush.fill_(float(i))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rr.rr_scene_update_vertices(h, h_vtx)
+                rr.rr_scan(h, pz, {**params, "scan_id": sid}, h_img)     # blocking: D2H included
+                t_e2e += time.perf_counter() - t0
+            st2 = rr.rr_scene_stats(h, reset=True)
+            e2e_ms, e2e_q = reduce_timing(1e3 * t_e2e, float(st2["closest_queries"]), world, device)
+            out["e2e"] = {"value": e2e_q / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
+                          "h2d_bytes_per_step": int(sc.vertices.nbytes + 28 + 96),
+                          "d2h_bytes_per_step": int(h_img.numel() * 4),
+                          "scans_per_s": world * steps / (e2e_ms * 1e-3)}
+    finally:
+        rr.rr_scene_destroy(h)
+    return out
+
+
+def roofline(res: dict, peak: float, peak_kind: str, counters, l2_peak: float | None, bound: str, note: str):
+    """Roofline of the closest-hit query kernel from a plain_bench result:
+    achieved = algorithmic bytes per launch (node and triangle fetches, ray
+    and hit records, from the device traversal counters) / average launch
+    duration (CUDA events around each launch), against the measured HBM copy
+    bandwidth; traffic and the L2 bytes per launch from the committed ncu
+    summary of the same kernel source."""
+    trace_ms, launches, busy = res["trace"]
+    algo = res["bytes_per_query"] * res["closest_queries"]
+    ms_launch = trace_ms / max(launches, 1)
+    bytes_launch = algo / max(launches, 1)
+    achieved = bytes_launch / (ms_launch * 1e-3) / 1e9 if ms_launch > 0 else None
+    traffic = counters.get("dram_bytes_per_launch") if counters else None
+    lts = counters.get("lts_bytes_per_launch") if counters else None
+    r = {"bound": bound, "kernel": "k_query (closest hit)", "achieved": achieved, "peak": peak, "unit": "GB/s",
+         "frac": achieved / peak if achieved else None, "traffic": traffic, "peak_source": peak_kind,
+         "per": "one launch: the closest-hit queries of one azimuth range of one bounce", "note": note,
+         "algorithmic_bytes_per_launch": bytes_launch, "ms_per_launch": ms_launch,
+         "launches_per_step": launches / max(res["steps"], 1), "algorithmic_bytes_per_query": res["bytes_per_query"],
+         "nodes_per_query": res["nodes_per_query"], "tris_per_query": res["tris_per_query"],
+         "busy_ms_per_step": busy / max(res["steps"], 1),
+         "dram_gbs": traffic / (ms_launch * 1e-3) / 1e9 if traffic and ms_launch > 0 else None}
+    r["dram_frac"] = r["dram_gbs"] / peak if r["dram_gbs"] else None
+    if counters:
+        r["counters"] = {k: counters[k] for k in ("profile", "launches_captured", "scaling") if k in counters}
+    if l2_peak:
+        l2 = lts / (ms_launch * 1e-3) / 1e9 if lts is not None and ms_launch > 0 else None
+        r["l2"] = {"achieved": l2, "peak": l2_peak, "unit": "GB/s", "frac": l2 / l2_peak if l2 else None,
+                   "bytes_per_launch": lts, "peak_source": "measured in this run: copy of an L2-resident buffer"}
+    return r
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-medium", action="store_true", help="skip the medium (200k-triangle campus) object")
     ap.add_argument("--node-format", default="auto", choices=["auto", "wide", "binary"],
-                    help="BVH node format of the plain scan (auto: the library default)")
+                    help="BVH node format of the plain scans (auto: the library default)")
     ap.add_argument("--batched-steps", type=int, default=3)
     ap.add_argument("--step-bvh", default="lbvh", choices=["sah_top", "lbvh"],
-                    help="BVH build of the main line, rebuilt every step: the LBVH alone (default) or with the "
-                         "binned-SAH top")
+                    help="BVH build of the plain-scan steps, rebuilt every step: the LBVH alone (default) or with "
+                         "the binned-SAH top")
     ap.add_argument("--scene-bvh", default="sah_top", choices=["sah_top", "lbvh"],
                     help="BVH build of the batched and served scenes, built once: with the binned-SAH top "
                          "(default) or the LBVH alone")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-scan-only", action="store_true")
-    ap.add_argument("--no-large", action="store_true", help="skip the large (5M-triangle city) scan object")
+    ap.add_argument("--workspace-limit-gb", type=float, default=0.0,
+                    help="scan workspace limit of the headline scene (0: the library default); the profile "
+                         "commands use 1 GiB so that the captured process holds a few GB")
     ap.add_argument("--served-seconds", type=float, default=10.0,
                     help="arrival window per request rate of the served workload")
     args = ap.parse_args()
     world, rank, local = dist_env()
 
     from paper_2310_03505_gb300 import scenes
-    sc, pz, params = scenes.config_medium()
+    sc, pz, params = scenes.config_large()
+    split_default = 3
 
     if args.impl == "reference":
         # the oracle arm: rank 0 only, on the host cores
@@ -481,10 +654,12 @@ def main():
         import oracle.oracle as orc
         orc.build()
         value, cores, sample, t_step = oracle_reference_steps(sc, pz, params, args.steps, args.warmup)
+        nf = {"auto": "binary_fp32", "binary": "binary_fp32", "wide": "wide8_q8"}[args.node_format]
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": WORKLOAD, "triangles": sc.n_triangles},
+                "data": "synthetic",
+                "config": headline_config(sc, params, nf, split_default, args.step_bvh, args.gpus),
                 "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
                                  "sample": sample},
                 "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -506,192 +681,65 @@ def main():
     rr.load()
     torch.cuda.init()
     stream = torch.cuda.current_stream()
-
-    d_vtx = torch.from_numpy(sc.vertices).to(device)
-    h = rr.rr_scene_create(d_vtx, sc.triangles, sc.material_ids, sc.materials)
-    set_bvh(rr, h, args.step_bvh)
-    if args.node_format != "auto":
-        rr.rr_batch_config_set(h, node_format=rr.RR_NODES_WIDE8 if args.node_format == "wide" else rr.RR_NODES_BINARY)
-    node_format = "wide8_q8" if rr.rr_batch_config_get(h)["node_format"] == rr.RR_NODES_WIDE8 else "binary_fp32"
-    split = rr.rr_batch_config_get(h)["split_streams"]
-    node_bytes = rr.WIDE_NODE_BYTES if node_format == "wide8_q8" else NODE_BYTES
-    info = rr.rr_scene_info_get(h)
-    img = torch.zeros(params["n_azimuth"], params["n_bins"], device=device)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
-    warm_ids, step_ids = shard_scan_ids(rank, args.steps, args.warmup)
-
-    def step(scan_id):
-        rr.rr_scene_update_vertices(h, d_vtx)
-        rr.rr_scan_async(h, pz, {**params, "scan_id": scan_id}, img)
-
-    for sid in warm_ids:
-        step(sid)
-    rr.rr_scene_sync(h)
-
-    # traversal counters of one untimed scan (per-query algorithmic bytes)
-    rr.rr_scene_stats(h, reset=True)
-    rr.rr_scan(h, pz, {**params, "scan_id": 10 ** 6 + rank, "count_traversal": True}, img)
-    cst = rr.rr_scene_stats(h, reset=True)
-    # the dominant kernel is the closest-hit query: its algorithmic bytes are
-    # the nodes and triangles it fetches plus its ray and hit records
-    nodes_per_q = cst["nodes_visited"] / max(cst["closest_queries"], 1)
-    tris_per_q = cst["tris_tested"] / max(cst["closest_queries"], 1)
-    any_nodes_per_q = cst["anyhit_nodes_visited"] / max(cst["anyhit_queries"], 1)
-    any_tris_per_q = cst["anyhit_tris_tested"] / max(cst["anyhit_queries"], 1)
-    bytes_per_closest = nodes_per_q * node_bytes + tris_per_q * TRI_BYTES + RAY_IO_BYTES
-
-    # timed region
-    rr.rr_profile_read(h, reset=True)
-    rr.rr_profile_enable(h, True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in step_ids]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in step_ids]
-    clock_csv = os.environ.get("RR_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(), f"rr_clocks_rank{rank}.csv")
-    clocks = ClockSampler(local, clock_csv) if rank == 0 else None
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    for i, sid in enumerate(step_ids):
-        flush.fill_(float(i))                      # evict the scene from L2 (outside the events)
-        starts[i].record(stream)
-        step(sid)
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    rc_status = rr.rr_scene_sync(h)
-    clk = clocks.stop() if clocks else None
-    rr.rr_profile_enable(h, False)
-    prof = rr.rr_profile_read(h, reset=True)
-    st = rr.rr_scene_stats(h, reset=True)
-    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    local_ms = float(np.sum(per_step))
-    job_ms, job_queries = reduce_timing(local_ms, float(st["closest_queries"]), world, device)
-
-    mrays = job_queries / (job_ms * 1e-3) / 1e6
-    scans_per_s = world * args.steps / (job_ms * 1e-3)
-    trace_ms, trace_launches, trace_busy = prof["trace"]
     peak, peak_kind = measured_peaks()
-    algo_bytes = bytes_per_closest * st["closest_queries"]
-    # the split ranges' closest-hit launches of a bounce run at the same time on
-    # their streams: the kernel's rate is its bytes over the time any of them ran
-    achieved_gbs = algo_bytes / (trace_busy * 1e-3) / 1e9 if trace_busy > 0 else None
-    per_launch_gbs = algo_bytes / (trace_ms * 1e-3) / 1e9 if trace_ms > 0 else None
-    bounces = params["max_bounces"] * args.steps
-    traffic = traffic_from_profiles()
+    l2_peak = l2_copy_gbs(device)
 
-    # the scans alone on a resident BVH (built once, with the SAH top): the
-    # metric with the build excluded, the build reported beside it
-    scan_only = None
-    if not args.no_scan_only:
-        rr.rr_batch_config_set(h, bvh_build=rr.RR_BVH_SAH_TOP)   # one build, untimed
-        for i in range(3):
-            rr.rr_scan_async(h, pz, {**params, "scan_id": 5000 + i}, img)
-        rr.rr_scene_sync(h)
-        rr.rr_scene_stats(h, reset=True)
-        n_so = min(args.steps, 100)
-        t_so = []
-        for i in range(n_so):
-            flush.fill_(float(i))
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rr.rr_scan_async(h, pz, {**params, "scan_id": 6000 + rank * 1000 + i}, img)
-            e1.record(stream)
-            t_so.append((e0, e1))
-        torch.cuda.synchronize()
-        so_ms = float(np.sum([a.elapsed_time(b) for a, b in t_so]))
-        so_rc = rr.rr_scene_sync(h)
-        so_q = float(rr.rr_scene_stats(h, reset=True)["closest_queries"])
-        job_so_ms, job_so_q = reduce_timing(so_ms, so_q, world, device)
-        scan_only = {"value": job_so_q / (job_so_ms * 1e-3) / 1e6, "unit": "Mrays/s",
-                     "scans_per_s": world * n_so / (job_so_ms * 1e-3), "ms_per_scan": job_so_ms / n_so,
-                     "steps": n_so, "bvh": "LBVH + binned-SAH top, built once (untimed)",
-                     "status": "ok" if so_rc is None else str(so_rc)}
-        set_bvh(rr, h, args.step_bvh)
+    head = plain_bench(rr, device, stream, flush, sc, pz, params, args.steps, args.warmup, rank=rank, world=world,
+                       step_bvh=args.step_bvh, node_format=args.node_format, ws_limit_gb=args.workspace_limit_gb,
+                       e2e=not args.no_e2e, scan_only=not args.no_scan_only, clocks=rank == 0)
+    rl = roofline(head, peak, peak_kind, profile_counters("query_kernel_city_ncu"), l2_peak, "hbm",
+                  "the city's BVH and triangles (~0.56 GB) exceed the 129 MB L2; achieved counts the algorithmic "
+                  "node/triangle/record bytes of a launch over its CUDA-event duration (launches of the 3 azimuth "
+                  "ranges overlap on their streams); dram_gbs is the DRAM traffic ncu measured for the same "
+                  "kernel source over that duration")
 
-    # the large plain scan: rank 0 only, an extra object beside the headline
-    large = None
-    if rank == 0 and not args.no_large:
-        large = large_bench(device, stream, flush, args.step_bvh)
-
-    # end to end through the C ABI with host buffers
-    e2e = None
-    if not args.no_e2e:
-        h_vtx = torch.from_numpy(sc.vertices).pin_memory()
-        h_img = torch.zeros(params["n_azimuth"], params["n_bins"]).pin_memory()
-        rr.rr_scene_stats(h, reset=True)
-        t_e2e = 0.0
-        for i, sid in enumerate(step_ids):
-            flush.fill_(float(i))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rr.rr_scene_update_vertices(h, h_vtx)
-            rr.rr_scan(h, pz, {**params, "scan_id": sid}, h_img)     # blocking: D2H included
-            t_e2e += time.perf_counter() - t0
-        st2 = rr.rr_scene_stats(h, reset=True)
-        e2e_ms, e2e_q = reduce_timing(1e3 * t_e2e, float(st2["closest_queries"]), world, device)
-        e2e = {"value": e2e_q / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
-               "h2d_bytes_per_step": int(sc.vertices.nbytes + 28 + 80),
-               "d2h_bytes_per_step": int(h_img.numel() * 4), "scans_per_s": world * args.steps / (e2e_ms * 1e-3)}
+    medium = None
+    if not args.no_medium:
+        msc, mpz, mparams = scenes.config_medium()
+        m_steps = max(args.steps, 50)
+        medium = plain_bench(rr, device, stream, flush, msc, mpz, mparams, m_steps, args.warmup, rank=rank,
+                             world=world, step_bvh=args.step_bvh, node_format=args.node_format, e2e=False,
+                             scan_only=not args.no_scan_only)
+        medium["roofline"] = roofline(medium, peak, peak_kind, profile_counters("query_kernel_campus_ncu"), l2_peak,
+                                      "latency",
+                                      "cache-resident: the campus BVH and triangles (~22 MB) stay in L2, so the "
+                                      "algorithmic bytes come from L1/L2 and the launches are bound by the latency "
+                                      "of dependent node fetches, not by HBM")
+        medium = {"workload": MEDIUM_WORKLOAD, "triangles": msc.n_triangles,
+                  **{k: v for k, v in medium.items() if k not in ("trace", "closest_queries")}}
 
     batched = None
     if not args.no_batched:
         batched = batched_bench(device, stream, flush, steps=args.batched_steps, rank=rank, bvh=args.scene_bvh)
     served = None
     if not args.no_served and rank == 0:
-        served = served_bench(device, seconds=args.served_seconds, rank=rank, bvh=args.scene_bvh)
+        served = served_bench(device, seconds=args.served_seconds, rank=rank, bvh=args.scene_bvh, city=sc)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample, _, _ = oracle_sample(sc, pz, params)
-        cpu = {"value": v, "unit": "Mrays/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = cpu_bvh_baseline(sc, pz, params)
 
     if rank == 0:
-        kernels_per_step = st["kernel_launches"] / max(args.steps, 1)
+        config = headline_config(sc, params, head["node_format"], head["split_streams"], args.step_bvh, world)
+        if args.workspace_limit_gb > 0:
+            config["workspace_limit"] = head["workspace_limit"]
         line = {
-            "metric": METRIC, "value": mrays, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": job_ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": head["value"], "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "triangles": sc.n_triangles, "n_azimuth": params["n_azimuth"],
-                       "rays_per_beam": params["rays_per_beam"], "max_bounces": params["max_bounces"],
-                       "n_bins": params["n_bins"], "node_format": node_format, "split_streams": split,
-                       "bvh": ("LBVH + binned-SAH top over its subtrees of <= 32 triangles"
-                               if args.step_bvh == "sah_top" else "LBVH"),
-                       "wide_nodes": info["n_wide_nodes"], "step": "BVH rebuild + polar scan",
-                       "l2": "flushed between steps (256 MiB write, outside the timed events)",
-                       "parallelism": f"replicas x{world}"},
-            "scans_per_s": scans_per_s,
-            "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
-                           "kind": "plain scan (rebuild + scan), not served"},
-            "queries_per_scan": st["closest_queries"] / args.steps,
-            "anyhit_per_scan": st["anyhit_queries"] / args.steps,
-            "bvh_build_ms_per_step": prof["build"][0] / max(prof["build"][1], 1),
-            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-            "kernel_busy_ms_per_step": {k: v[2] / args.steps for k, v in prof.items()},
-            "roofline": {"bound": "hbm", "kernel": "k_query (closest hit)", "achieved": achieved_gbs,
-                         "peak": peak, "unit": "GB/s", "frac": (achieved_gbs / peak) if achieved_gbs else None,
-                         "traffic": traffic, "peak_source": peak_kind,
-                         "per": "closest-hit queries of one bounce: the launches of its azimuth ranges",
-                         "note": f"{split} azimuth ranges run on {split} streams, so the launches of a bounce "
-                                 "overlap: achieved divides their algorithmic bytes by the union of their CUDA-event "
-                                 "intervals; achieved_per_launch divides by the summed launch durations",
-                         "achieved_per_launch": per_launch_gbs,
-                         "dram_gbs": (traffic / (trace_busy / max(bounces, 1) * 1e-3) / 1e9)
-                                     if traffic and trace_busy > 0 else None,
-                         "algorithmic_bytes_per_bounce": algo_bytes / max(bounces, 1),
-                         "busy_ms_per_bounce": trace_busy / max(bounces, 1),
-                         "algorithmic_bytes_per_query": bytes_per_closest,
-                         "nodes_per_query": nodes_per_q, "tris_per_query": tris_per_q,
-                         "launches_per_step": trace_launches / max(args.steps, 1),
-                         "ms_per_launch": trace_ms / max(trace_launches, 1)},
-            "visibility_queries": {"nodes_per_query": any_nodes_per_q, "tris_per_query": any_tris_per_q},
-            "scan_only": scan_only, "large": large,
-            "batched": batched, "served": served,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["kernel_launches"]),
-            "kernels_per_step": kernels_per_step, "clocks": clk, "wall_s_timed": wall,
-            "status": "ok" if rc_status is None else str(rc_status),
+            "config": config, "scans_per_s": head["scans_per_s"], "latency_ms": head["latency_ms"],
+            "queries_per_scan": head["queries_per_scan"], "anyhit_per_scan": head["anyhit_per_scan"],
+            "bvh_build_ms_per_step": head["bvh_build_ms_per_step"],
+            "kernel_ms_per_step": head["kernel_ms_per_step"],
+            "kernel_busy_ms_per_step": head["kernel_busy_ms_per_step"],
+            "roofline": rl, "visibility_queries": head["visibility"], "scan_only": head.get("scan_only"),
+            "medium": medium, "batched": batched, "served": served,
+            "cpu_baseline": cpu, "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"],
+            "kernels_per_step": head["kernels_per_step"], "clocks": head["clocks"],
+            "wall_s_timed": head["wall_s_timed"], "status": head["status"],
         }
         print(json.dumps(line))
-    rr.rr_scene_destroy(h)
     if world > 1:
         torch.distributed.destroy_process_group()
 

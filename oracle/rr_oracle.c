@@ -55,8 +55,10 @@
 #define FLAG_TABS 1e-6    /* absolute distance next to t_min (metres)          */
 #define FLAG_TIR 1e-6     /* |eta^2 sin^2 - 1| next to the critical angle      */
 #define FLAG_COS 1e-6     /* grazing incidence |cos theta0|                    */
-#define FLAG_COST 0.05    /* refraction next to grazing: cos theta2 below it  */
-#define FLAG_TALLY 1e-6   /* energy a tally may move by (half its tolerance)  */
+#define FLAG_TDIR 1e-5    /* angle error (rad) of a refracted direction: the  */
+                          /* relative hit-distance tolerance of the parity   */
+#define FLAG_TALLY 8e-6   /* energy a tally may move by, relative to the      */
+                          /* initial ray's energy (half its tolerance)       */
 
 /* segment flag bits (diagnostics) */
 #define SEG_EDGE 1u
@@ -1202,10 +1204,11 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
          1 / |cos theta0|, and the energy the medium absorbs over it by
          2 alpha E_end as much; flagged for the per-ray tallies when that can
          reach half their tolerance */
-      if (ray.medium != ORC_AIR && fabs(cos_i) < FLAG_COST) {
+      if (ray.medium != ORC_AIR) {
         double omax = fmax(fmax(fabs(ray.o[0]), fabs(ray.o[1])), fmax(fabs(ray.o[2]), 1.0));
         double dt = 8.0 * omax * 0x1p-24 / fmax(fabs(cos_i), 1e-12);
-        if (2.0 * alpha_np(s, ray.medium, p->freq_hz) * E1 * dt > FLAG_TALLY) seg.flags |= SEG_TALLY;
+        if (2.0 * alpha_np(s, ray.medium, p->freq_hz) * E1 * dt > FLAG_TALLY / (double)p->rays_per_beam)
+          seg.flags |= SEG_TALLY;
       }
       int entering = cos_i > 0.0;
       double n1 = n_cur, n2;
@@ -1227,10 +1230,18 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
       } else {
         tir = orc_fresnel(n1, n2, cos_i, &R, &cos_t, &sin2_t);
         if (fabs(sin2_t - 1.0) < FLAG_TIR) seg.flags |= SEG_TIR;
-        /* Snell's law is ill-conditioned next to the critical angle: the
-           refracted direction moves by d(sin^2)/(2 cos theta2), so float32
-           rounding there bends the refracted child measurably */
-        if (!tir && cos_t < FLAG_COST && (p->flags & ORC_REFRACTION)) seg.flags |= SEG_SNELL;
+        /* Snell's law is ill-conditioned next to the critical angle.  In
+           float32, sin^2 theta2 = eta^2 (1 - cos^2 theta0) carries an error
+           of at most (6 eta^2 + 5) 2^-24 (cos theta0 itself off by 3 ulps,
+           twice amplified by eta^2, plus the roundings of the products), and
+           theta2 moves by that over 2 cos theta2 sin theta2 ~ 2 cos theta2:
+           the refracted child is flagged when this angle error exceeds the
+           relative hit-distance tolerance (a direction off by d theta moves
+           the next hit distance by about d theta of itself) */
+        if (!tir && (p->flags & ORC_REFRACTION)) {
+          double eta = n1 / n2;
+          if ((6.0 * eta * eta + 5.0) * 0x1p-24 > FLAG_TDIR * 2.0 * cos_t) seg.flags |= SEG_SNELL;
+        }
       }
       double T = (m->pec || tir) ? 0.0 : 1.0 - R;
       int can_refract = !m->pec && !tir;

@@ -8,9 +8,23 @@ Tolerances (the parity contract):
     1e-5 relative -- single segments deep in a path cannot: their end
     points carry the float32 resolution of coordinates ~100 m from the
     origin (7.6e-6 m);
+  * every single hit distance t agrees within 1e-5 of itself plus
+    K_ULP ulps of the scene's largest coordinate over the cosine of the
+    incidence: the segment starts at its parent's hit point, which float32
+    holds to within 2.5 ulps per coordinate (the rounding of o + t d and the
+    parent's own t error), i.e. 4.3 ulps in length, and an origin moved by
+    dx moves the distance to the next plane by at most dx / cos theta0;
+    K_ULP = 8 allows twice that;
+  * per-segment energies, cos theta0 and return energies as described in
+    compare_segment_energies; per-ray energy tallies within TALLY_REL of the
+    initial ray's energy;
   * image bins agree within 1e-3 of the oracle image's maximum plus the
     oracle's per-bin slack (returns next to a bin edge), after masking the
     flagged rays on both sides.
+
+The oracle side is the FP64 brute-force oracle, or, for the full-size scans,
+the same oracle with its queries answered through its CPU BVH, which gives
+exactly the brute-force results (pinned on the CPU in test_cpu_bvh.py).
 """
 from __future__ import annotations
 
@@ -21,6 +35,10 @@ from paper_2310_03505_gb300 import rr
 
 T_REL = 1e-5
 IMG_REL = 1e-3
+K_ULP = 8.0
+TALLY_REL = 1.6e-5
+FLAG_BITS = {"EDGE": 1, "TMIN": 2, "TIE": 4, "TLIM": 8, "TIR": 16, "GRAZE": 32, "RMAX": 64, "VIS": 128,
+             "EMIN": 256, "SNELL": 512, "TALLY": 1024}
 
 
 def gpu_scene(sc):
@@ -36,8 +54,71 @@ def gpu_scene(sc):
     return h
 
 
-def oracle_scan(sc, pz, params, az_list=None, post=True):
-    return orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, params, az_list=az_list, post=post)
+_BVH = {}
+
+
+def oracle_scan(sc, pz, params, az_list=None, post=True, accel=False):
+    """The oracle's scan; accel: through its CPU BVH (flag-exact mode, the
+    brute-force results), built once per scene."""
+    bvh = None
+    if accel:
+        key = (sc.name, sc.n_triangles, id(sc.vertices))
+        if key not in _BVH:
+            _BVH.clear()
+            _BVH[key] = orc.Bvh(sc.vertices, sc.triangles, sc.materials)
+        bvh = _BVH[key]
+    return orc.scan(sc.vertices, sc.triangles, sc.material_ids, sc.materials, pz, params, az_list=az_list, post=post,
+                    bvh=bvh)
+
+
+def flag_census(ora, keep=None):
+    """Initial rays removed from the comparisons, by flag kind (a ray counts
+    under every kind its tree holds)."""
+    segs, fl, tf = ora["segments"], ora["flags"].astype(bool), ora["tally_flags"].astype(bool)
+    if keep is not None:
+        fl, tf = fl[:, keep], tf[:, keep]
+    out = {"rays": int(fl.size), "flagged": int(fl.sum()), "tally_only": int((tf & ~fl).sum())}
+    for name, b in FLAG_BITS.items():
+        sel = (segs["flags"] & b) != 0
+        out[name] = len(set(zip(segs["az"][sel].tolist(), segs["k"][sel].tolist())))
+    return out
+
+
+def compare_tallies(tal_gpu, ora, az_list, rays_per_beam):
+    """Per-ray energy tallies (returned, absorbed, escaped, terminated) of the
+    rays the oracle does not flag for them, within TALLY_REL of the initial
+    ray's energy.  Returns (worst excess over the tolerance, its (column
+    index, k))."""
+    ok = ora["tally_flags"] == 0
+    diff = np.abs(tal_gpu[list(az_list)] - ora["tallies"]).max(-1) * ok
+    worst = np.unravel_index(np.argmax(diff), diff.shape)
+    return float(diff[worst]) / (TALLY_REL / rays_per_beam), worst
+
+
+def compare_segment_distances(gpu_segs, ora_segs, ora_flags, az_list, coord_max):
+    """Every single hit distance of every unflagged ray (see the module
+    notes).  Returns (segments compared, mismatches, largest error over its
+    tolerance)."""
+    ulp = 2.0 ** (np.floor(np.log2(max(coord_max, 1.0))) - 23)
+    az_list = list(az_list)
+    ns = ora_flags.shape[1]
+    o, g = _Segs(ora_segs, az_list, ora_flags), _Segs(gpu_segs, az_list, ora_flags)
+    gi = np.searchsorted(g.key, o.key)
+    gi = np.minimum(gi, max(len(g.key) - 1, 0))
+    ok = ((g.key[gi] == o.key) if len(g.key) else np.zeros(len(o.key), bool)) & (o.tri != orc.NONE)
+    ok &= g.tri[gi] == o.tri if len(g.key) else ok
+    t_o = o.s["t"].astype(np.float64)[ok]
+    t_g = g.s["t"].astype(np.float64)[gi][ok]
+    cos = o.s["cos_i"].astype(np.float64)[ok]
+    tol = T_REL * t_o + K_ULP * ulp / np.maximum(cos, 1e-6)
+    r = np.abs(t_g - t_o) / tol
+    idx = np.nonzero(ok)[0]
+    bad = []
+    for j in np.nonzero(r > 1.0)[0][:20]:
+        i = idx[j]
+        bad.append(f"ray {(az_list[int(o.ray[i]) // ns], int(o.ray[i]) % ns)} seg {(int(o.path[i]), int(o.bounce[i]))}: "
+                   f"t {t_g[j]:.9g} vs {t_o[j]:.9g} (tol {tol[j]:.3g}, cos {cos[j]:.4f})")
+    return int(ok.sum()), bad, float(r.max()) if r.size else 0.0
 
 
 def gpu_debug(h, pz, params, mask=None, seg_capacity=None):
@@ -66,6 +147,46 @@ def seg_table(segs, az_set=None):
 E_FLOOR = 1e-30
 
 
+class _Segs:
+    """Segments of the rays of az_list that the oracle does not flag, sorted by
+    a key (initial ray, path, bounce), with the index of each segment's parent
+    and, per segment, the distance along the path from the sensor to its hit
+    and the sum of the energies from the initial ray down to it."""
+
+    def __init__(self, segs, az_list, ora_flags):
+        az_list = np.asarray(list(az_list), np.int64)
+        col = np.full(int(max(az_list.max(), int(segs["az"].max()) if len(segs) else 0)) + 1, -1, np.int64)
+        col[az_list] = np.arange(len(az_list))
+        ci = col[segs["az"].astype(np.int64)] if len(segs) else np.zeros(0, np.int64)
+        keep = ci >= 0
+        k = segs["k"].astype(np.int64)
+        keep[keep] &= ora_flags[ci[keep], k[keep]] == 0
+        s = segs[keep]
+        self.ray = ci[keep] * ora_flags.shape[1] + k[keep]
+        self.path = s["path"].astype(np.int64)
+        self.bounce = s["bounce"].astype(np.int64)
+        self.key = (self.ray << 22) | (self.path << 5) | self.bounce
+        order = np.argsort(self.key, kind="stable")
+        self.key, self.ray, self.path, self.bounce = self.key[order], self.ray[order], self.path[order], self.bounce[order]
+        self.s = s[order]
+        self.tri = self.s["tri"].astype(np.int64)
+        t = self.s["t"].astype(np.float64)
+        E = self.s["E"].astype(np.float64)
+        pkey = (self.ray << 22) | ((self.path >> 1) << 5) | (self.bounce - 1)
+        pi = np.searchsorted(self.key, pkey)
+        pi = np.minimum(pi, len(self.key) - 1) if len(self.key) else pi
+        has_parent = (self.bounce > 0) & (len(self.key) > 0)
+        if len(self.key):
+            has_parent &= self.key[pi] == pkey
+        self.parent = np.where(has_parent, pi, -1)
+        self.length = np.where(self.tri != orc.NONE, t, 0.0)
+        self.along = E.copy()
+        for b in range(1, int(self.bounce.max()) + 1 if len(self.bounce) else 0):
+            sel = np.nonzero((self.bounce == b) & (self.parent >= 0))[0]
+            self.length[sel] += self.length[self.parent[sel]]
+            self.along[sel] += self.along[self.parent[sel]]
+
+
 def compare_segment_energies(gpu_segs, ora_segs, ora_flags, az_list, rel=1e-3, abs_rel_E=1e-6):
     """Per segment of every unflagged ray: energy entering, cos theta0 and the
     two return energies, within rel of the oracle plus abs_rel_E of the
@@ -75,43 +196,24 @@ def compare_segment_energies(gpu_segs, ora_segs, ora_flags, az_list, rel=1e-3, a
     the energies it is taken from -- when the returns take nearly all of E R
     the child is a residue far below them -- and that error then moves down
     the tree scaled by factors <= 1.  Returns a list of mismatch descriptions."""
-    az_index = {az: i for i, az in enumerate(az_list)}
-    def table(segs):
-        out = {}
-        for s in segs:
-            az = int(s["az"])
-            if az in az_index:
-                out[(az, int(s["k"]), int(s["path"]), int(s["bounce"]))] = s
-        return out
-    g, o = table(gpu_segs), table(ora_segs)
-    along = {}   # sum of the oracle energies from the initial ray down to the segment
-    for key in sorted(o, key=lambda x: x[3]):
-        az, k, path, b = key
-        along[key] = float(o[key]["E"]) + (along.get((az, k, path >> 1, b - 1), 0.0) if b > 0 else 0.0)
+    az_list = list(az_list)
+    o, g = _Segs(ora_segs, az_list, ora_flags), _Segs(gpu_segs, az_list, ora_flags)
+    gi = np.searchsorted(g.key, o.key)
+    gi = np.minimum(gi, max(len(g.key) - 1, 0))
+    present = (g.key[gi] == o.key) if len(g.key) else np.zeros(len(o.key), bool)
     bad = []
-    for key, os_ in o.items():
-        az, k = key[0], key[1]
-        if ora_flags[az_index[az], k] or key not in g:
-            continue
-        gs = g[key]
-        for f in ("E", "cos_i", "ret_t", "ret_a"):
-            a, b = float(gs[f]), float(os_[f])
-            scale = float(os_["E"]) if f == "cos_i" else along[key]
-            if abs(a - b) > rel * abs(b) + abs_rel_E * scale + E_FLOOR:
-                bad.append(f"ray {key[:2]} seg {key[2:]} {f}: gpu {a:.9g} oracle {b:.9g} (cos_i {float(os_['cos_i']):.7f})")
+    for f in ("E", "cos_i", "ret_t", "ret_a"):
+        a = g.s[f][gi].astype(np.float64)
+        b = o.s[f].astype(np.float64)
+        scale = o.s["E"].astype(np.float64) if f == "cos_i" else o.along
+        off = present & (np.abs(a - b) > rel * np.abs(b) + abs_rel_E * scale + E_FLOOR)
+        for i in np.nonzero(off)[0][:20]:
+            az, k = az_list[int(o.ray[i]) // ora_flags.shape[1]], int(o.ray[i]) % ora_flags.shape[1]
+            bad.append(f"ray {(az, k)} seg {(int(o.path[i]), int(o.bounce[i]))} {f}: gpu {a[i]:.9g} oracle "
+                       f"{b[i]:.9g} (cos_i {float(o.s['cos_i'][i]):.7f})")
+        if off.sum() > 20:
+            bad.append(f"... {int(off.sum()) - 20} more {f} mismatches")
     return bad
-
-
-def path_lengths(table):
-    """Distance along the path from the sensor to every hit: the sum of the
-    segment lengths from the initial ray down to this segment."""
-    out = {}
-    for ray, segs in table.items():
-        for (path, bounce) in sorted(segs, key=lambda x: x[1]):
-            tri, t = segs[(path, bounce)]
-            prev = out.get((ray, path >> 1, bounce - 1), 0.0) if bounce else 0.0
-            out[(ray, path, bounce)] = prev + t
-    return out
 
 
 def compare_paths(gpu_segs, ora_segs, ora_flags, az_list):
@@ -119,31 +221,26 @@ def compare_paths(gpu_segs, ora_segs, ora_flags, az_list):
     the path to every hit within T_REL relative.  Returns (n_rays_compared,
     mismatches[list of str], max relative path-length error)."""
     az_list = list(az_list)
-    g = seg_table(gpu_segs, set(az_list))
-    o = seg_table(ora_segs, set(az_list))
-    gl, ol = path_lengths(g), path_lengths(o)
+    ns = ora_flags.shape[1]
+    o, g = _Segs(ora_segs, az_list, ora_flags), _Segs(gpu_segs, az_list, ora_flags)
+    n = int((ora_flags == 0).sum())
+    name = lambda r: (az_list[int(r) // ns], int(r) % ns)
     bad = []
-    max_rel = 0.0
-    n = 0
-    for ci, az in enumerate(az_list):
-        for k in range(ora_flags.shape[1]):
-            if ora_flags[ci, k]:
-                continue
-            n += 1
-            gs, os_ = g.get((az, k), {}), o.get((az, k), {})
-            if set(gs) != set(os_):
-                bad.append(f"ray {(az, k)}: segments differ {sorted(set(gs) ^ set(os_))[:4]}")
-                continue
-            for key, (otri, ot) in os_.items():
-                gtri, gt = gs[key]
-                if gtri != otri:
-                    bad.append(f"ray {(az, k)} seg {key}: tri {gtri} vs {otri}")
-                elif otri != orc.NONE:
-                    od, gd = ol[((az, k),) + key], gl[((az, k),) + key]
-                    rel = abs(gd - od) / od
-                    max_rel = max(max_rel, rel)
-                    if rel > T_REL:
-                        bad.append(f"ray {(az, k)} seg {key}: path length {gd} vs {od}")
+    if len(o.key) != len(g.key) or not np.array_equal(o.key, g.key):
+        diff = np.setxor1d(o.key, g.key)
+        for r in np.unique(diff >> 22)[:20]:
+            bad.append(f"ray {name(r)}: segments differ")
+        return n, bad, 0.0
+    tri_off = np.nonzero(o.tri != g.tri)[0]
+    for i in tri_off[:20]:
+        bad.append(f"ray {name(o.ray[i])} seg {(int(o.path[i]), int(o.bounce[i]))}: tri {int(g.tri[i])} vs "
+                   f"{int(o.tri[i])}")
+    hit = (o.tri == g.tri) & (o.tri != orc.NONE)
+    rel = np.abs(g.length[hit] - o.length[hit]) / o.length[hit]
+    max_rel = float(rel.max()) if rel.size else 0.0
+    for i in np.nonzero(hit)[0][rel > T_REL][:20]:
+        bad.append(f"ray {name(o.ray[i])} seg {(int(o.path[i]), int(o.bounce[i]))}: path length {g.length[i]} vs "
+                   f"{o.length[i]}")
     return n, bad, max_rel
 
 

@@ -1,11 +1,13 @@
 """Parity at the full size of the large city workload (about 5M triangles,
 400 beams x 1000 rays, at most 8 bounces, 4000 bins): the GPU traces the
-whole scan; the FP64 brute-force oracle recomputes a sample of initial rays
--- every 100th ray of 16 azimuth columns, 160 rays with all their bounces,
-each ray's tree being independent of the others -- and the two are compared
-ray by ray, segment by segment and, through the GPU's ray mask, bin by bin
-on the image of exactly those rays.  Properties that hold at any size are
-checked on the whole image.  Needs a GPU."""
+whole scan; the FP64 oracle recomputes a sample of initial rays -- every
+10th ray of 40 azimuth columns, 4,000 rays with all their bounces, each
+ray's tree being independent of the others; its queries go through its CPU
+BVH, which gives exactly the brute-force results -- and the two are compared
+ray by ray, segment by segment (triangle, hit distance, energies), per-ray
+energy tallies and, through the GPU's ray mask, bin by bin on the image of
+exactly those rays.  Properties that hold at any size are checked on the
+whole image.  Needs a GPU."""
 import numpy as np
 import pytest
 
@@ -14,8 +16,8 @@ from tests import parity as P
 
 pytestmark = pytest.mark.gpu
 
-COLS = list(range(0, 400, 25))
-STRIDE = 100
+COLS = list(range(0, 400, 10))
+STRIDE = 10
 
 
 @pytest.fixture(scope="module")
@@ -29,10 +31,11 @@ def large(rrlib):
 def test_large_sampled_rays(large):
     sc, pz, params, h = large
     ns = params["rays_per_beam"]
-    ora = P.oracle_scan(sc, pz, {**params, "ray_stride": STRIDE}, az_list=COLS)
+    ora = P.oracle_scan(sc, pz, {**params, "ray_stride": STRIDE}, az_list=COLS, accel=True)
     keep = np.arange(ns) % STRIDE == 0
     flags = ora["flags"].astype(bool)
-    assert flags[:, keep].mean() < 0.05, f"{flags.sum()} of {keep.sum() * len(COLS)} sampled rays flagged"
+    census = P.flag_census(ora, keep)
+    assert flags[:, keep].mean() < 0.05, census
     skip = flags | ~keep[None, :]   # flagged, or not in the sample
     # every segment is one closest-hit query: size the dump from a plain scan's count
     out = np.zeros((params["n_azimuth"], params["n_bins"]), np.float32)
@@ -43,10 +46,17 @@ def test_large_sampled_rays(large):
     assert np.allclose(img_all, out, rtol=0, atol=1e-5 * float(out.max()))   # the debug scan is the scan
     segs = segs[np.isin(segs["az"], COLS) & (segs["k"] % STRIDE == 0)]
     n, bad, max_rel = P.compare_paths(segs, ora["segments"], skip.astype(np.uint8), COLS)
-    assert n == int((~skip).sum()) > 120
+    assert n == int((~skip).sum()) > 3500
     assert not bad, f"{len(bad)} mismatches of {n} rays, first: {bad[:5]}"
     ebad = P.compare_segment_energies(segs, ora["segments"], skip.astype(np.uint8), COLS)
     assert not ebad, f"{len(ebad)} energy mismatches, first: {ebad[:3]}"
+    coord_max = float(max(np.abs(sc.vertices).max(), np.abs(np.asarray(pz["p"])).max()))
+    nd, dbad, worst = P.compare_segment_distances(segs, ora["segments"], skip.astype(np.uint8), COLS, coord_max)
+    assert nd > 50_000 and not dbad, f"{len(dbad)} of {nd} hit distances off (worst {worst:.3g}), first: {dbad[:5]}"
+    # per-ray tallies of the sampled rays (the others are zero on the oracle side)
+    ora_k = {**ora, "tally_flags": ora["tally_flags"] | ~keep[None, :]}
+    excess, w = P.compare_tallies(tal, ora_k, COLS, ns)
+    assert excess <= 1.0, f"tallies of ray {w}: gpu {tal[COLS][w]} oracle {ora['tallies'][w]}"
     # the image of the sampled, unflagged rays alone: every other ray masked
     mask = np.ones((params["n_azimuth"], ns), np.uint8)
     mask[COLS] = skip

@@ -78,12 +78,14 @@ def check_parity(sc, pz, params, h, max_flagged=0.02, seg_capacity=None):
     assert len(segs) == len(ora["segments"]) or flags.any()
     ebad = P.compare_segment_energies(segs, ora["segments"], flags, range(params["n_azimuth"]))
     assert not ebad, f"{len(ebad)} segment energy mismatches, first: {ebad[:6]}"
+    # every single hit distance
+    coord_max = float(max(np.abs(sc.vertices).max(), np.abs(np.asarray(pz["p"])).max()))
+    nd, dbad, _ = P.compare_segment_distances(segs, ora["segments"], flags, range(params["n_azimuth"]), coord_max)
+    assert nd > 0 and not dbad, f"{len(dbad)} of {nd} hit distances off, first: {dbad[:5]}"
     # energy bookkeeping per initial ray
     assert np.max(np.abs(tal.sum(-1) - 1.0 / params["rays_per_beam"])) < 1e-5 / params["rays_per_beam"] * 10
-    ok = ora["tally_flags"] == 0
-    diff = np.abs(tal - ora["tallies"]).max(-1) * ok
-    worst = np.unravel_index(np.argmax(diff), diff.shape)
-    if diff[worst] >= 2e-6:
+    excess, worst = P.compare_tallies(tal, ora, range(params["n_azimuth"]), params["rays_per_beam"])
+    if excess > 1.0:
         az, k = int(worst[0]), int(worst[1])
         g = segs[(segs["az"] == az) & (segs["k"] == k)]
         o = ora["segments"][(ora["segments"]["az"] == az) & (ora["segments"]["k"] == k)]
