@@ -193,7 +193,7 @@ def cpu_bvh_baseline(sc, pz, params):
     from oracle import oracle as orc
     orc.build()
     t0 = time.perf_counter()
-    bvh = orc.Bvh(sc.vertices, sc.triangles, sc.materials)
+    bvh = orc.Bvh(sc.vertices, sc.triangles, sc.materials, flags=False)
     build_s = time.perf_counter() - t0
     try:
         t0 = time.perf_counter()

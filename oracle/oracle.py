@@ -57,7 +57,7 @@ class Pose(C.Structure):
 
 SEGMENT_DTYPE = np.dtype([("az", "<u4"), ("k", "<u4"), ("path", "<u4"), ("bounce", "<u4"), ("tri", "<u4"),
                           ("flags", "<u4"), ("t", "<f8"), ("E", "<f8"), ("cos_i", "<f8"), ("ret_t", "<f8"),
-                          ("ret_a", "<f8")])
+                          ("ret_a", "<f8"), ("e_org", "<f8"), ("e_dir", "<f8")])
 
 
 def build(force: bool = False) -> str:
@@ -110,7 +110,7 @@ def _load(path):
             L.orc_scan.restype = C.c_int
             L.orc_scan_accel.argtypes = L.orc_scan.argtypes + [p, C.c_int]
             L.orc_scan_accel.restype = C.c_int
-            L.orc_bvh_build.argtypes = [p, u32, p, u32, p, u32, p]
+            L.orc_bvh_build.argtypes = [p, u32, p, u32, p, u32, p, C.c_int]
             L.orc_bvh_build.restype = p
             L.orc_bvh_free.argtypes = [p]
             L.orc_post.argtypes = [p, p, p, u32]
@@ -302,9 +302,11 @@ def restore_library(handle):
 class Bvh:
     """CPU BVH of a scene for ``scan(..., bvh=...)`` (the timed CPU baseline):
     binned-SAH binary tree over grown triangle boxes, plus the window tables
-    of the materials for the fast mode.  Built with all host cores."""
+    of the materials for the fast mode.  Built with all host cores.  With
+    ``flags`` (default) the boxes are grown so that the scan reproduces the
+    brute-force parity flags; without, only the fast mode may use it."""
 
-    def __init__(self, vertices, triangles, materials):
+    def __init__(self, vertices, triangles, materials, flags: bool = True):
         self._lib = lib()
         v = np.ascontiguousarray(vertices, np.float32)
         t = np.ascontiguousarray(triangles, np.uint32)
@@ -312,7 +314,7 @@ class Bvh:
         mats = (Material * len(materials))(*made)
         depth = C.c_uint32()
         self.handle = self._lib.orc_bvh_build(_ptr(v), v.shape[0], _ptr(t), t.shape[0], mats, len(materials),
-                                              C.byref(depth))
+                                              C.byref(depth), 1 if flags else 0)
         del made
         if not self.handle:
             raise RuntimeError("orc_bvh_build failed (bad indices, no triangles or a tree deeper than its stack)")

@@ -55,6 +55,10 @@
 #define FLAG_TABS 1e-6    /* absolute distance next to t_min (metres)          */
 #define FLAG_TIR 1e-6     /* |eta^2 sin^2 - 1| next to the critical angle      */
 #define FLAG_COS 1e-6     /* grazing incidence |cos theta0|                    */
+#define FLAG_EMAX 1e-2    /* largest edge distance (m) a hit point's error    */
+                          /* estimate flags; above it the segment is flagged */
+                          /* outright (the CPU BVH's boxes are grown by more */
+                          /* than this)                                      */
 #define FLAG_TDIR 1e-5    /* angle error (rad) of a refracted direction: the  */
                           /* relative hit-distance tolerance of the parity   */
 #define FLAG_TALLY 8e-6   /* energy a tally may move by, relative to the      */
@@ -72,6 +76,7 @@
 #define SEG_EMIN 256u
 #define SEG_SNELL 512u
 #define SEG_TALLY 1024u   /* affects only the per-ray energy tallies */
+#define SEG_ERR 2048u     /* FLAG_SIGMAS times a hit point's float32 error exceeds FLAG_EMAX */
 
 /* lobe kinds of a material (Sec. III-A: user-defined BRDFs per material) */
 #define ORC_LOBE_EQ5 0           /* Eq. 5 with A, B, C                                  */
@@ -108,6 +113,8 @@ typedef struct {
   uint32_t az, k, path, bounce, tri, flags;
   double t, E;
   double cos_i, ret_t, ret_a;
+  double e_org, e_dir; /* float32 error estimate (standard deviations) of the segment's origin (m) and
+                          direction (rad) */
 } orc_segment;
 
 /* ------------------------------------------------------------------------ */
@@ -499,6 +506,51 @@ static void tri_normal(const scene_t* s, uint32_t j, double n[3]) {
   normalize3(n);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Float32 error estimate.  The CUDA path holds ray origins, directions and */
+/* hit points in float32, so its hit points drift from this oracle's by an  */
+/* amount that grows along the path.  Each rounding moves a value by a      */
+/* uniform fraction of half an ulp (standard deviation 0.29 ulp); the many  */
+/* independent roundings along a path add up like a random walk, so each   */
+/* ray carries standard deviations: e_org (m) of its origin and e_dir (rad) */
+/* of its direction, combined in quadrature.  Ray generation starts at      */
+/* e_org = 0 (the pose position is a float) and e_dir = ERR_DIR0 ulps (the  */
+/* beam angle, the angle sum, the elevation, the pose rotation and the      */
+/* normalisation: about a dozen roundings); the hit point at distance t     */
+/* adds t e_dir, half an ulp of its largest coordinate (the rounding of     */
+/* o + t d) and one ulp of t (the watertight test's division); a reflection */
+/* adds ERR_REFL ulps to the direction (the normal from float vertices,     */
+/* cos theta0, the mirror formula, the normalisation); a refraction scales  */
+/* the incoming direction error by the derivative of Snell's law            */
+/* eta cos theta0 / cos theta2 and adds a third of the bound (6 eta^2 + 5)  */
+/* 2^-24 / (2 cos theta2) of the rounding of sin^2 theta2, plus ERR_REFR    */
+/* ulps.  A hit or near miss within FLAG_SIGMAS standard deviations of a    */
+/* triangle edge is a decision float32 can take the other way and flags the */
+/* ray; the parity tests take the same estimate for the hit distances.      */
+/* ------------------------------------------------------------------------ */
+#define ULP32 0x1p-24
+#define ERR_DIR0 2.0     /* ulps of the generated direction */
+#define ERR_REFL 2.0     /* ulps a reflection adds */
+#define ERR_REFR 1.0     /* ulps a refraction adds besides the Snell term */
+#define FLAG_SIGMAS 4.0  /* standard deviations of a hit point that flag an edge */
+
+/* one float32 ulp of x (the spacing of floats around |x|, at least 2^-149) */
+static double ulp32(double x) {
+  x = fabs(x);
+  if (!(x >= 0x1p-126)) return 0x1p-149;
+  int e;
+  frexp(x, &e); /* x = f 2^e, 0.5 <= f < 1: floats in [2^(e-1), 2^e) are 2^(e-24) apart */
+  return ldexp(1.0, e - 24);
+}
+
+/* standard deviation of the float32 point at distance t along (o, d) */
+static double point_err(double e_org, double e_dir, double t, const double o[3], const double d[3]) {
+  double m = 0.0;
+  for (int i = 0; i < 3; ++i) m = fmax(m, fabs(o[i] + t * d[i]));
+  const double r = 0.5 * ulp32(m), u = ulp32(t);
+  return sqrt(e_org * e_org + t * t * e_dir * e_dir + r * r + u * u);
+}
+
 typedef struct {
   uint32_t tri;
   double t, margin;
@@ -511,7 +563,28 @@ typedef struct {
   hit_t h;
   double t2, t_edge;
   int near_tmin;
+  double e_org, e_dir; /* the ray's float32 error estimate */
 } hit_acc;
+
+/* Is the plane point of triangle (v0, v1, v2) with barycentrics (b0, b1, b2)
+   within barycentric margin FLAG_BARY of an edge, or closer to an edge than
+   `err` metres (inside or outside)?  The signed distance to the edge
+   opposite vertex i is b_i times the altitude over that edge. */
+static int near_edge(const double v0[3], const double v1[3], const double v2[3], double b0, double b1, double b2,
+                     double m, double err) {
+  if (m > -FLAG_BARY && m < FLAG_BARY) return 1;
+  if (!(m > -0.5 && m < 0.5)) return 0;
+  double e1[3], e2[3], e3[3], c[3];
+  sub3(v1, v0, e1);
+  sub3(v2, v0, e2);
+  sub3(v2, v1, e3);
+  cross3(e1, e2, c);
+  const double twice_area = norm3(c);
+  const double s0 = b0 * twice_area / norm3(e3), s1 = b1 * twice_area / norm3(e2), s2 = b2 * twice_area / norm3(e1);
+  double smin = s0 < s1 ? s0 : s1;
+  if (s2 < smin) smin = s2;
+  return smin > -err && smin < err;
+}
 
 static void hit_begin(hit_acc* a) {
   a->h.tri = ORC_NONE;
@@ -521,6 +594,8 @@ static void hit_begin(hit_acc* a) {
   a->t2 = INFINITY;
   a->t_edge = INFINITY;
   a->near_tmin = 0;
+  a->e_org = 0.0;
+  a->e_dir = 0.0;
 }
 
 /* one triangle of a closest-hit query (t > t_min; ties on t go to the
@@ -533,7 +608,9 @@ static void hit_consider(const scene_t* s, uint32_t j, const double o[3], const 
   double b0 = 1.0 - b1 - b2;
   double m = b0 < b1 ? b0 : b1;
   if (b2 < m) m = b2;
-  if (m > -FLAG_BARY && m < FLAG_BARY && t > t_min - FLAG_TABS && t < a->t_edge) a->t_edge = t;
+  if (t > t_min - FLAG_TABS && t < a->t_edge &&
+      near_edge(v0, v1, v2, b0, b1, b2, m, fmin(FLAG_SIGMAS * point_err(a->e_org, a->e_dir, t, o, d), FLAG_EMAX)))
+    a->t_edge = t;
   if (m >= 0.0 && fabs(t - t_min) < FLAG_TABS) a->near_tmin = 1;
   if (m < 0.0 || !(t > t_min)) return;
   if (t < a->h.t || (t == a->h.t && j < a->h.tri)) {
@@ -557,18 +634,22 @@ static hit_t hit_finish(const hit_acc* a) {
   return h;
 }
 
-static hit_t closest_hit_bvh(const scene_t* s, const double o[3], const double d[3], double t_min, uint32_t skip);
+static hit_t closest_hit_bvh(const scene_t* s, const double o[3], const double d[3], double t_min, uint32_t skip,
+                             double e_org, double e_dir);
 static int occluded_bvh(const scene_t* s, const double p[3], const double dir[3], double t_min, double dist,
-                        uint32_t skip, int* flag);
+                        uint32_t skip, int* flag, double e_org, double e_dir);
 
 /* Closest hit by brute force over all triangles: t > t_min, triangle != skip,
    ties on t go to the smaller triangle id.  Flags near-edge candidates (hit or
    miss within FLAG_BARY of an edge) that could be the closest, a near tie with
    the second closest triangle, and hits next to t_min. */
-static hit_t closest_hit(const scene_t* s, const double o[3], const double d[3], double t_min, uint32_t skip) {
-  if (s->bvh) return closest_hit_bvh(s, o, d, t_min, skip);
+static hit_t closest_hit(const scene_t* s, const double o[3], const double d[3], double t_min, uint32_t skip,
+                         double e_org, double e_dir) {
+  if (s->bvh) return closest_hit_bvh(s, o, d, t_min, skip, e_org, e_dir);
   hit_acc a;
   hit_begin(&a);
+  a.e_org = e_org;
+  a.e_dir = e_dir;
   for (uint32_t j = 0; j < s->nt; ++j) {
     if (j == skip) continue;
     hit_consider(s, j, o, d, t_min, &a);
@@ -581,16 +662,28 @@ int orc_closest(const float* vertices, uint32_t n_vertices, const uint32_t* tria
                 const double o[3], const double d[3], double t_min, uint32_t skip, uint32_t* tri, double* t,
                 uint32_t* flags) {
   scene_t s = {vertices, triangles, NULL, NULL, n_vertices, n_triangles, 0, NULL, 0};
-  hit_t h = closest_hit(&s, o, d, t_min, skip);
+  hit_t h = closest_hit(&s, o, d, t_min, skip, 0.0, 0.0);
   *tri = h.tri;
   *t = h.t;
   *flags = h.flags;
   return h.tri != ORC_NONE;
 }
 
+/* Standard deviation of the float32 point at distance t along the
+   visibility segment from a hit point (error e_org) to the sensor (a float:
+   no error) at distance dist: the segment is fixed by its two end points,
+   so the error shrinks linearly toward the sensor. */
+static double seg_err(double e_org, double t, double dist, const double p[3], const double dir[3]) {
+  double m = 0.0;
+  for (int i = 0; i < 3; ++i) m = fmax(m, fabs(p[i] + t * dir[i]));
+  const double e = e_org * fmax(1.0 - t / dist, 0.0), r = 0.5 * ulp32(m), u = ulp32(t);
+  return sqrt(e * e + r * r + u * u);
+}
+
 /* one triangle of an any-hit query on the open segment (t_min, dist) */
 static void occ_consider(const scene_t* s, uint32_t j, const double p[3], const double dir[3], double t_min,
-                         double dist, int* occ, int* flag) {
+                         double dist, int* occ, int* flag, double e_org, double e_dir) {
+  (void)e_dir;
   double v0[3], v1[3], v2[3], t, b1, b2;
   tri_vertices(s, j, v0, v1, v2);
   if (!orc_tri_plane(p, dir, v0, v1, v2, &t, &b1, &b2)) return;
@@ -599,7 +692,9 @@ static void occ_consider(const scene_t* s, uint32_t j, const double p[3], const 
   if (b2 < m) m = b2;
   int inside_t = t > t_min && t < dist;
   int near_t = fabs(t - t_min) < FLAG_TABS || fabs(t - dist) < FLAG_TREL * dist;
-  if (m > -FLAG_BARY && m < FLAG_BARY && (inside_t || near_t)) *flag = 1;
+  if ((inside_t || near_t) &&
+      near_edge(v0, v1, v2, b0, b1, b2, m, fmin(FLAG_SIGMAS * seg_err(e_org, t, dist, p, dir), FLAG_EMAX)))
+    *flag = 1;
   if (m >= 0.0 && near_t) *flag = 1;
   if (m >= 0.0 && inside_t) *occ = 1;
 }
@@ -607,12 +702,12 @@ static void occ_consider(const scene_t* s, uint32_t j, const double p[3], const 
 /* Any hit on the open segment from p (on triangle skip) to the sensor at
    distance dist.  Sets *flag when a triangle lies within the flag margins. */
 static int occluded(const scene_t* s, const double p[3], const double dir[3], double t_min, double dist, uint32_t skip,
-                    int* flag) {
-  if (s->bvh) return occluded_bvh(s, p, dir, t_min, dist, skip, flag);
+                    int* flag, double e_org, double e_dir) {
+  if (s->bvh) return occluded_bvh(s, p, dir, t_min, dist, skip, flag, e_org, e_dir);
   int occ = 0;
   for (uint32_t j = 0; j < s->nt; ++j) {
     if (j == skip) continue;
-    occ_consider(s, j, p, dir, t_min, dist, &occ, flag);
+    occ_consider(s, j, p, dir, t_min, dist, &occ, flag, e_org, e_dir);
   }
   return occ;
 }
@@ -622,8 +717,10 @@ static int occluded(const scene_t* s, const double p[3], const double dir[3], do
 /* a bounding volume hierarchy instead of the brute-force loops above.       */
 /* Binary tree, binned SAH (16 bins per axis over the centroids), leaves of  */
 /* at most 4 triangles, float boxes rounded outward.  Every triangle's box    */
-/* is grown by 1e-4 of its largest extent plus 1e-6 m, which holds every      */
-/* point of its plane within barycentric margin FLAG_BARY of the triangle:    */
+/* is grown by 1e-4 of its largest extent plus 2 FLAG_EMAX, which holds every */
+/* point of its plane within barycentric margin FLAG_BARY, or within the      */
+/* largest edge distance FLAG_EMAX that flags, of the triangle (built for    */
+/* the flags; the fast mode's tree grows them by 1e-6 m only):               */
 /* so a query that keeps visiting boxes up to (1 + 1e-5) times the best t     */
 /* sees every triangle the brute-force loops would count (the closest hit,   */
 /* the second closest, near-edge candidates, hits next to t_min) and gives   */
@@ -646,6 +743,7 @@ struct orc_bvh {
   bnode_t* nodes;
   uint32_t* idx;
   uint32_t n_nodes, depth;
+  int exact; /* boxes grown for the parity flags */
   /* tabulated lobe integrals for the fast mode: per material the integral of
      the density from 0 to x_k = k (pi/2) / WTAB_CELLS and the density there */
   double* wtab;
@@ -807,7 +905,7 @@ static void build_node(build_t* B, uint32_t ni, uint32_t first, uint32_t count, 
 /* Builds the BVH of a triangle soup (and, for the fast mode, the window
    tables of the materials).  Returns NULL on bad input. */
 orc_bvh* orc_bvh_build(const float* vertices, uint32_t n_vertices, const uint32_t* triangles, uint32_t n_triangles,
-                       const orc_material* materials, uint32_t n_materials, uint32_t* depth_out) {
+                       const orc_material* materials, uint32_t n_materials, uint32_t* depth_out, int exact) {
   if (n_triangles == 0) return NULL;
   for (size_t i = 0; i < 3 * (size_t)n_triangles; ++i)
     if (triangles[i] >= n_vertices) return NULL;
@@ -829,7 +927,7 @@ orc_bvh* orc_bvh_build(const float* vertices, uint32_t n_vertices, const uint32_
       b.hi[i] = fmax(v0[i], fmax(v1[i], v2[i]));
       ext = fmax(ext, b.hi[i] - b.lo[i]);
     }
-    const double grow = 1e-4 * ext + 1e-6;
+    const double grow = exact ? 1e-4 * ext + 2.0 * FLAG_EMAX : 1e-6;
     for (int i = 0; i < 3; ++i) {
       b.lo[i] -= grow;
       b.hi[i] += grow;
@@ -851,6 +949,7 @@ orc_bvh* orc_bvh_build(const float* vertices, uint32_t n_vertices, const uint32_
   h->idx = B.idx;
   h->n_nodes = B.n_nodes;
   h->depth = B.depth;
+  h->exact = exact;
   if (depth_out) *depth_out = B.depth;
   if (B.depth + 1 >= BVH_STACK) {
     free(h->nodes);
@@ -947,10 +1046,13 @@ static void inv_dir(const double d[3], double inv[3]) {
   for (int i = 0; i < 3; ++i) inv[i] = d[i] != 0.0 ? 1.0 / d[i] : INFINITY;
 }
 
-static hit_t closest_hit_bvh(const scene_t* s, const double o[3], const double d[3], double t_min, uint32_t skip) {
+static hit_t closest_hit_bvh(const scene_t* s, const double o[3], const double d[3], double t_min, uint32_t skip,
+                             double e_org, double e_dir) {
   const orc_bvh* B = s->bvh;
   hit_acc a;
   hit_begin(&a);
+  a.e_org = e_org;
+  a.e_dir = e_dir;
   double inv[3];
   inv_dir(d, inv);
   const double t_lo = s->fast ? t_min : t_min - 1e-5;
@@ -994,7 +1096,7 @@ static hit_t closest_hit_bvh(const scene_t* s, const double o[3], const double d
 }
 
 static int occluded_bvh(const scene_t* s, const double p[3], const double dir[3], double t_min, double dist,
-                        uint32_t skip, int* flag) {
+                        uint32_t skip, int* flag, double e_org, double e_dir) {
   const orc_bvh* B = s->bvh;
   double inv[3];
   inv_dir(dir, inv);
@@ -1010,7 +1112,7 @@ static int occluded_bvh(const scene_t* s, const double p[3], const double dir[3]
     if (n->count) {
       for (uint32_t i = n->first; i < n->first + n->count; ++i) {
         const uint32_t j = B->idx[i];
-        if (j != skip) occ_consider(s, j, p, dir, t_min, dist, &occ, flag);
+        if (j != skip) occ_consider(s, j, p, dir, t_min, dist, &occ, flag, e_org, e_dir);
       }
       if (occ && s->fast) return 1;
       continue;
@@ -1028,6 +1130,7 @@ typedef struct {
   double o[3], d[3], E, L;
   int32_t medium;
   uint32_t prev, path, bounce;
+  double e_org, e_dir; /* float32 error estimate (see above) */
 } oray_t;
 
 typedef struct {
@@ -1162,14 +1265,17 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
     root.prev = ORC_NONE;
     root.path = 0;
     root.bounce = 0;
+    root.e_org = 0.0;
+    root.e_dir = ERR_DIR0 * ULP32;
     stack[sp++] = root;
 
     while (sp > 0) {
       oray_t ray = stack[--sp];
-      orc_segment seg = {a, k, ray.path, ray.bounce, ORC_NONE, 0u, INFINITY, ray.E, 0.0, 0.0, 0.0};
+      orc_segment seg = {a, k, ray.path, ray.bounce, ORC_NONE, 0u, INFINITY, ray.E, 0.0, 0.0, 0.0,
+                         ray.e_org, ray.e_dir};
       double n_cur = refr_index(s, ray.medium);
       double t_lim = (r_lim - ray.L) / n_cur; /* past it no return can reach the image */
-      hit_t h = closest_hit(s, ray.o, ray.d, p->t_min, ray.prev);
+      hit_t h = closest_hit(s, ray.o, ray.d, p->t_min, ray.prev, ray.e_org, ray.e_dir);
       col->queries++;
       seg.flags = h.flags;
       if (h.tri != ORC_NONE && fabs(h.t - t_lim) <= FLAG_TREL * t_lim) seg.flags |= SEG_TLIM;
@@ -1182,6 +1288,8 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
       }
       seg.tri = h.tri;
       seg.t = h.t;
+      const double e_hit = point_err(ray.e_org, ray.e_dir, h.t, ray.o, ray.d);
+      if (FLAG_SIGMAS * e_hit > FLAG_EMAX) seg.flags |= SEG_ERR;
 
       double pt[3];
       for (int i = 0; i < 3; ++i) pt[i] = ray.o[i] + h.t * ray.d[i];
@@ -1223,7 +1331,7 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
         next_medium = ORC_AIR;
       }
 
-      double R, cos_t = 0.0, sin2_t = 0.0;
+      double R, cos_t = 0.0, sin2_t = 0.0, e_refr_dir = 0.0;
       int tir = 0;
       if (m->pec) {
         R = 1.0;
@@ -1240,7 +1348,10 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
            the next hit distance by about d theta of itself) */
         if (!tir && (p->flags & ORC_REFRACTION)) {
           double eta = n1 / n2;
-          if ((6.0 * eta * eta + 5.0) * 0x1p-24 > FLAG_TDIR * 2.0 * cos_t) seg.flags |= SEG_SNELL;
+          const double snell = (6.0 * eta * eta + 5.0) * ULP32 / (2.0 * cos_t);
+          const double amp = ray.e_dir * eta * cos_i / cos_t;
+          e_refr_dir = sqrt(amp * amp + snell * snell / 9.0 + ERR_REFR * ERR_REFR * ULP32 * ULP32);
+          if (!(snell <= FLAG_TDIR)) seg.flags |= SEG_SNELL;
         }
       }
       double T = (m->pec || tir) ? 0.0 : 1.0 - R;
@@ -1292,7 +1403,7 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
           if (w_a > 0.0) {
             double dir[3] = {v[0] / dist, v[1] / dist, v[2] / dist};
             int vflag = 0;
-            int occ = occluded(s, pt, dir, p->t_min, dist, h.tri, &vflag);
+            int occ = occluded(s, pt, dir, p->t_min, dist, h.tri, &vflag, e_hit, hypot(e_hit / dist, ULP32));
             col->shadow_queries++;
             if (vflag) seg.flags |= SEG_VIS;
             if (!occ) {
@@ -1358,6 +1469,8 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
         c.prev = h.tri;
         c.path = (ray.path << 1) | 1u;
         c.bounce = ray.bounce + 1;
+        c.e_org = e_hit;
+        c.e_dir = e_refr_dir;
         stack[sp++] = c;
       }
       if (spawn_refl) {
@@ -1370,6 +1483,8 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
         c.prev = h.tri;
         c.path = ray.path << 1;
         c.bounce = ray.bounce + 1;
+        c.e_org = e_hit;
+        c.e_dir = sqrt(ray.e_dir * ray.e_dir + ERR_REFL * ERR_REFL * ULP32 * ULP32);
         stack[sp++] = c;
       }
     }
@@ -1426,6 +1541,7 @@ int orc_scan_accel(const float* vertices, uint32_t n_vertices, const uint32_t* t
     if (material_ids[j] >= n_materials) return 2;
   }
   if (bvh && bvh->wtab && bvh->nm != n_materials) return 2;
+  if (bvh && !fast && !bvh->exact) return 4; /* the flags need the grown boxes */
   scene_t s = {vertices, triangles, material_ids, materials, n_vertices, n_triangles, n_materials, bvh,
                bvh ? fast : 0};
   column_t* cols = (column_t*)calloc(n_cols, sizeof(column_t));

@@ -36,13 +36,13 @@ def test_medium_full_scan_every_ray(medium, variant):
     census = P.flag_census(ora)
     assert flags.mean() < 0.05, census
     img_all, segs, tal = P.gpu_debug(h, pz, params)
-    n, bad, _ = P.compare_paths(segs, ora["segments"], flags, cols)
+    cmax = P.coord_max(sc, pz)
+    n, bad, _ = P.compare_paths(segs, ora["segments"], flags, cols, cmax)
     assert n == int((flags == 0).sum())
     assert not bad, f"{len(bad)} mismatches of {n} rays, first: {bad[:5]}"
     ebad = P.compare_segment_energies(segs, ora["segments"], flags, cols)
     assert not ebad, f"{len(ebad)} segment energy mismatches, first: {ebad[:5]}"
-    coord_max = float(max(np.abs(sc.vertices).max(), np.abs(np.asarray(pz["p"])).max()))
-    nd, dbad, worst = P.compare_segment_distances(segs, ora["segments"], flags, cols, coord_max)
+    nd, dbad, worst = P.compare_segment_distances(segs, ora["segments"], flags, cols, cmax)
     assert nd > 500_000 and not dbad, f"{len(dbad)} of {nd} hit distances off (worst {worst:.3g}), first: {dbad[:5]}"
     excess, w = P.compare_tallies(tal, ora, cols, ns)
     assert excess <= 1.0, f"tallies of ray {w}: gpu {tal[w]} oracle {ora['tallies'][w]}"

@@ -72,15 +72,15 @@ def check_parity(sc, pz, params, h, max_flagged=0.02, seg_capacity=None):
     assert flags.mean() < max_flagged, f"{flags.sum()} of {flags.size} rays flagged"
     # ray paths and hit distances (no mask: every ray traced)
     img_all, segs, tal = P.gpu_debug(h, pz, params, seg_capacity=seg_capacity)
-    n, bad, max_rel = P.compare_paths(segs, ora["segments"], flags, range(params["n_azimuth"]))
+    cmax = P.coord_max(sc, pz)
+    n, bad, max_rel = P.compare_paths(segs, ora["segments"], flags, range(params["n_azimuth"]), cmax)
     assert n >= (~flags.astype(bool)).sum()
     assert not bad, f"{len(bad)} mismatches, first: {bad[:5]}"
     assert len(segs) == len(ora["segments"]) or flags.any()
     ebad = P.compare_segment_energies(segs, ora["segments"], flags, range(params["n_azimuth"]))
     assert not ebad, f"{len(ebad)} segment energy mismatches, first: {ebad[:6]}"
     # every single hit distance
-    coord_max = float(max(np.abs(sc.vertices).max(), np.abs(np.asarray(pz["p"])).max()))
-    nd, dbad, _ = P.compare_segment_distances(segs, ora["segments"], flags, range(params["n_azimuth"]), coord_max)
+    nd, dbad, _ = P.compare_segment_distances(segs, ora["segments"], flags, range(params["n_azimuth"]), cmax)
     assert nd > 0 and not dbad, f"{len(dbad)} of {nd} hit distances off, first: {dbad[:5]}"
     # energy bookkeeping per initial ray
     assert np.max(np.abs(tal.sum(-1) - 1.0 / params["rays_per_beam"])) < 1e-5 / params["rays_per_beam"] * 10
@@ -129,7 +129,7 @@ def test_tiny_parity_at_the_ray_limit(tiny_scene):
     assert flags[:, keep].mean() < 0.05
     img_all, segs, tal = P.gpu_debug(h, pz, params, seg_capacity=4 << 20)
     segs = segs[segs["k"] % stride == 0]
-    n, bad, _ = P.compare_paths(segs, ora["segments"], skip.astype(np.uint8), cols)
+    n, bad, _ = P.compare_paths(segs, ora["segments"], skip.astype(np.uint8), cols, P.coord_max(sc, pz))
     assert n == int((~skip).sum()) > 400
     assert not bad, f"{len(bad)} mismatches of {n} rays, first: {bad[:5]}"
     ebad = P.compare_segment_energies(segs, ora["segments"], skip.astype(np.uint8), cols)
