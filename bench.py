@@ -47,6 +47,7 @@ METRIC = "Mrays/s (all bounces) & scans/s on 1 GB300; p50/p99 served scan latenc
 RAY_IO_BYTES = 48 + 16          # ray record read + hit record written per closest-hit query
 NODE_BYTES, TRI_BYTES = 64, 48  # BVH node and triangle record
 L2_FLUSH_NOTE = "flushed between steps (256 MiB write, outside the timed events)"
+ORDER_DEFAULT = "queue"         # the library's default query order (rr_batch_config.query_order)
 
 
 # ------------------------------------------------------------------ helpers
@@ -437,17 +438,17 @@ def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: 
 
 
 # ------------------------------------------------------------------ plain scan steps
-def headline_config(sc, params, node_format: str, split: int, step_bvh: str, world: int) -> dict:
+def headline_config(sc, params, node_format: str, split: int, step_bvh: str, world: int, order: str) -> dict:
     """The `config` of the line (the same for both arms)."""
     return {"workload": LARGE_WORKLOAD, "triangles": sc.n_triangles, "n_azimuth": params["n_azimuth"],
             "rays_per_beam": params["rays_per_beam"], "max_bounces": params["max_bounces"],
-            "n_bins": params["n_bins"], "node_format": node_format, "split_streams": split,
+            "n_bins": params["n_bins"], "node_format": node_format, "split_streams": split, "query_order": order,
             "bvh": ("LBVH + binned-SAH top over its subtrees of <= 32 triangles" if step_bvh == "sah_top" else "LBVH"),
             "step": "BVH rebuild + polar scan", "l2": L2_FLUSH_NOTE, "parallelism": f"replicas x{world}"}
 
 
 def plain_bench(rr, device, stream, flush, sc, pz, params, steps, warmup, *, rank=0, world=1, step_bvh="lbvh",
-                node_format="auto", ws_limit_gb=0.0, e2e=True, scan_only=True, clocks=False):
+                node_format="auto", ws_limit_gb=0.0, e2e=True, scan_only=True, clocks=False, order="auto"):
     """Steps of BVH rebuild + polar scan on one scene (CUDA events on the
     stream, L2 flushed between steps), with the per-kernel profile of the
     timed steps, the traversal counters of one untimed scan, and optionally
@@ -463,9 +464,13 @@ def plain_bench(rr, device, stream, flush, sc, pz, params, steps, warmup, *, ran
             rr.rr_batch_config_set(h, node_format=rr.RR_NODES_WIDE8 if node_format == "wide" else rr.RR_NODES_BINARY)
         if ws_limit_gb > 0:
             rr.rr_batch_config_set(h, workspace_limit=int(ws_limit_gb * (1 << 30)))
+        if order != "auto":
+            rr.rr_batch_config_set(h, query_order=rr.RR_ORDER_CELL_OCTANT if order == "cell_octant"
+                                   else rr.RR_ORDER_QUEUE)
         cfg = rr.rr_batch_config_get(h)
         nf = "wide8_q8" if cfg["node_format"] == rr.RR_NODES_WIDE8 else "binary_fp32"
-        out.update(node_format=nf, split_streams=cfg["split_streams"], workspace_limit=cfg["workspace_limit"])
+        out.update(node_format=nf, split_streams=cfg["split_streams"], workspace_limit=cfg["workspace_limit"],
+                   query_order="cell_octant" if cfg["query_order"] == rr.RR_ORDER_CELL_OCTANT else "queue")
         img = torch.zeros(params["n_azimuth"], params["n_bins"], device=device)
         warm_ids, step_ids = shard_scan_ids(rank, steps, warmup)
 
@@ -627,6 +632,8 @@ def main():
     ap.add_argument("--node-format", default="auto", choices=["auto", "wide", "binary"],
                     help="BVH node format of the plain scans (auto: the library default)")
     ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--query-order", default="auto", choices=["auto", "queue", "cell_octant"],
+                    help="order of the closest-hit queries of bounces >= 1 (auto: the library default)")
     ap.add_argument("--step-bvh", default="lbvh", choices=["sah_top", "lbvh"],
                     help="BVH build of the plain-scan steps, rebuilt every step: the LBVH alone (default) or with "
                          "the binned-SAH top")
@@ -659,7 +666,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": headline_config(sc, params, nf, split_default, args.step_bvh, args.gpus),
+                "config": headline_config(sc, params, nf, split_default, args.step_bvh, args.gpus,
+                                          ORDER_DEFAULT if args.query_order == "auto" else args.query_order),
                 "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
                                  "sample": sample},
                 "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -687,7 +695,8 @@ def main():
 
     head = plain_bench(rr, device, stream, flush, sc, pz, params, args.steps, args.warmup, rank=rank, world=world,
                        step_bvh=args.step_bvh, node_format=args.node_format, ws_limit_gb=args.workspace_limit_gb,
-                       e2e=not args.no_e2e, scan_only=not args.no_scan_only, clocks=rank == 0)
+                       e2e=not args.no_e2e, scan_only=not args.no_scan_only, clocks=rank == 0,
+                       order=args.query_order)
     rl = roofline(head, peak, peak_kind, profile_counters("query_kernel_city_ncu"), l2_peak, "hbm",
                   "the city's BVH and triangles (~0.56 GB) exceed the 129 MB L2; achieved counts the algorithmic "
                   "node/triangle/record bytes of a launch over its CUDA-event duration (launches of the 3 azimuth "
@@ -700,7 +709,7 @@ def main():
         m_steps = max(args.steps, 50)
         medium = plain_bench(rr, device, stream, flush, msc, mpz, mparams, m_steps, args.warmup, rank=rank,
                              world=world, step_bvh=args.step_bvh, node_format=args.node_format, e2e=False,
-                             scan_only=not args.no_scan_only)
+                             scan_only=not args.no_scan_only, order=args.query_order)
         medium["roofline"] = roofline(medium, peak, peak_kind, profile_counters("query_kernel_campus_ncu"), l2_peak,
                                       "latency",
                                       "cache-resident: the campus BVH and triangles (~22 MB) stay in L2, so the "
@@ -721,7 +730,8 @@ def main():
         cpu = cpu_bvh_baseline(sc, pz, params)
 
     if rank == 0:
-        config = headline_config(sc, params, head["node_format"], head["split_streams"], args.step_bvh, world)
+        config = headline_config(sc, params, head["node_format"], head["split_streams"], args.step_bvh, world,
+                                 head["query_order"])
         if args.workspace_limit_gb > 0:
             config["workspace_limit"] = head["workspace_limit"]
         line = {

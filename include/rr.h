@@ -363,11 +363,22 @@ int rr_scan_batch_async(rr_scene* scene, uint32_t n, const rr_pose* poses, const
                         scene (creation, rr_scene_update_vertices) uses it;
                         setting a different value rebuilds the BVH (blocking).
                         Both give the same closest hit for every query; the
-                        SAH top needs fewer node visits. */
+                        SAH top needs fewer node visits.
+   query_order          order in which the closest-hit queries of bounces >= 1
+                        are handed to the query kernel: RR_ORDER_QUEUE (the
+                        queue order: children of neighbouring rays together,
+                        reflected and refracted interleaved) or
+                        RR_ORDER_CELL_OCTANT (bucketed by the ray's direction
+                        octant and a cell of its origin around the sensor, so
+                        that the lanes of a warp trace rays that go the same
+                        way from the same region).  Every query's result is
+                        the same in either order. */
 #define RR_NODES_WIDE8 0u
 #define RR_NODES_BINARY 1u
 #define RR_BVH_LBVH 0u
 #define RR_BVH_SAH_TOP 1u
+#define RR_ORDER_QUEUE 0u
+#define RR_ORDER_CELL_OCTANT 1u
 typedef struct {
   uint32_t wavefront_rays;
   uint32_t trace_block;
@@ -378,12 +389,15 @@ typedef struct {
   uint64_t workspace_limit;
   uint32_t split_streams;
   uint32_t bvh_build;
+  uint32_t query_order;
+  uint32_t reserved;
 } rr_batch_config;
 
 int rr_batch_config_get(const rr_scene* scene, rr_batch_config* out);
 /* RR_ERR_INVALID_ARG for a trace_block other than 64/128/256, more than 64
    blocks per SM, use_graph > 1, an unknown node_format or bvh_build, a
-   refill_threshold above 32, split_streams above 4 or a workspace limit
+   refill_threshold above 32, split_streams above 4, an unknown query_order
+   (reserved must be 0) or a workspace limit
    below 1 MiB. */
 int rr_batch_config_set(rr_scene* scene, const rr_batch_config* config);
 

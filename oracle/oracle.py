@@ -57,7 +57,7 @@ class Pose(C.Structure):
 
 SEGMENT_DTYPE = np.dtype([("az", "<u4"), ("k", "<u4"), ("path", "<u4"), ("bounce", "<u4"), ("tri", "<u4"),
                           ("flags", "<u4"), ("t", "<f8"), ("E", "<f8"), ("cos_i", "<f8"), ("ret_t", "<f8"),
-                          ("ret_a", "<f8"), ("e_org", "<f8"), ("e_dir", "<f8")])
+                          ("ret_a", "<f8"), ("e_org", "<f8"), ("e_dir", "<f8"), ("alpha2", "<f8")])
 
 
 def build(force: bool = False) -> str:

@@ -115,6 +115,7 @@ typedef struct {
   double cos_i, ret_t, ret_a;
   double e_org, e_dir; /* float32 error estimate (standard deviations) of the segment's origin (m) and
                           direction (rad) */
+  double alpha2;       /* power attenuation constant 2 alpha (1/m) of the medium the segment crosses (0: air) */
 } orc_segment;
 
 /* ------------------------------------------------------------------------ */
@@ -1272,7 +1273,7 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
     while (sp > 0) {
       oray_t ray = stack[--sp];
       orc_segment seg = {a, k, ray.path, ray.bounce, ORC_NONE, 0u, INFINITY, ray.E, 0.0, 0.0, 0.0,
-                         ray.e_org, ray.e_dir};
+                         ray.e_org, ray.e_dir, 2.0 * alpha_np(s, ray.medium, p->freq_hz)};
       double n_cur = refr_index(s, ray.medium);
       double t_lim = (r_lim - ray.L) / n_cur; /* past it no return can reach the image */
       hit_t h = closest_hit(s, ray.o, ray.d, p->t_min, ray.prev, ray.e_org, ray.e_dir);
@@ -1307,14 +1308,13 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
       tri_normal(s, h.tri, n);
       double cos_i = -dot3(ray.d, n);
       if (fabs(cos_i) < FLAG_COS) seg.flags |= SEG_GRAZE;
-      /* a segment inside a medium that ends at grazing incidence: its length
-         moves by the float32 resolution of its start point amplified by
-         1 / |cos theta0|, and the energy the medium absorbs over it by
+      /* a segment inside a medium: its length may move by FLAG_SIGMAS
+         standard deviations of its float32 hit point over |cos theta0|, and
+         the energy the medium absorbs over it (and every energy after it) by
          2 alpha E_end as much; flagged for the per-ray tallies when that can
          reach half their tolerance */
       if (ray.medium != ORC_AIR) {
-        double omax = fmax(fmax(fabs(ray.o[0]), fabs(ray.o[1])), fmax(fabs(ray.o[2]), 1.0));
-        double dt = 8.0 * omax * 0x1p-24 / fmax(fabs(cos_i), 1e-12);
+        double dt = FLAG_SIGMAS * e_hit / fmax(fabs(cos_i), 1e-12);
         if (2.0 * alpha_np(s, ray.medium, p->freq_hz) * E1 * dt > FLAG_TALLY / (double)p->rays_per_beam)
           seg.flags |= SEG_TALLY;
       }

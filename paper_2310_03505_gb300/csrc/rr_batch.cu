@@ -52,7 +52,9 @@ static size_t desc_bytes(uint64_t n) { return (size_t)n * sizeof(ScanDesc) + 2 *
 static uint64_t bytes_of(uint64_t q, uint64_t r, const Need& nd) {
   const uint64_t tiles = (q + 255) / 256 + 1;
   return align256(q * sizeof(rr::RayRec)) * 2 + align256(q * sizeof(rr::HitRec)) + align256(r * 8) +
-         align256(tiles * 8) + align256(nd.tmp * 4) + align256(desc_bytes(nd.n));
+         align256(tiles * 8) + align256(nd.tmp * 4) + align256(desc_bytes(nd.n)) + align256(q * 2) +
+         align256(q * 4) + align256((RR_MAX_BOUNCES + 1) * (uint64_t)rr::kOrderBuckets * 4) +
+         align256((uint64_t)rr::kOrderBuckets * 4);
 }
 
 static WsLayout layout_of(const Need& nd, uint64_t limit) {
@@ -62,7 +64,9 @@ static WsLayout layout_of(const Need& nd, uint64_t limit) {
   WsLayout L;
   L.clamped = false;
   if (bytes_of(q, r, nd) > limit) {
-    const double f = (double)limit / (double)bytes_of(q, r, nd);
+    // scale the queues and records; the parts that do not grow with them stay
+    const double fixed = (double)bytes_of(0, 0, nd);
+    const double f = std::max(0.0, (double)limit - fixed) / std::max(1.0, (double)bytes_of(q, r, nd) - fixed);
     q = std::max<uint64_t>(nd.n0, (uint64_t)(q * f));
     r = std::max<uint64_t>(2 * nd.n0, (uint64_t)(r * f));
     L.clamped = true;
@@ -87,6 +91,10 @@ static WsLayout layout_of(const Need& nd, uint64_t limit) {
   off += align256((size_t)nd.tmp * 4);
   L.off_desc = off;
   off += align256(desc_bytes(nd.n));
+  // query order: keys, permutation, per-bounce bucket counts, bucket cursors
+  L.off_order = off;
+  off += align256((size_t)q * 2) + align256((size_t)q * 4) +
+         align256((size_t)(RR_MAX_BOUNCES + 1) * rr::kOrderBuckets * 4) + align256((size_t)rr::kOrderBuckets * 4);
   L.total = off;
   return L;
 }
@@ -240,6 +248,7 @@ static cudaError_t launch_sequence(rr_scene* s, const ScanArgs& a, bool pattern,
     }
     if (profile) prof_begin(s, RR_K_SHADE, st, &ev);
     if ((e = launch_shade(a, b, st)) != cudaSuccess) return e;
+    if (a.order_perm && b + 1 < a.max_bounces && (e = launch_order(a, b + 1, st)) != cudaSuccess) return e;
     if (profile) prof_end(s, ev, st);
   }
   if (profile) prof_begin(s, RR_K_IMAGE, st, &ev);
@@ -405,6 +414,16 @@ int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor
   a.tile_status = (unsigned long long*)(w + L.off_status);
   a.ctr = x->d_ctr;
   a.image_tmp = pattern ? (float*)(w + L.off_tmp) : nullptr;
+  if (cfg.order == RR_ORDER_CELL_OCTANT && maxb > 1) {
+    char* o = w + L.off_order;
+    a.order_key = (uint16_t*)o;
+    o += align256((size_t)L.ray_cap * 2);
+    a.order_perm = (uint32_t*)o;
+    o += align256((size_t)L.ray_cap * 4);
+    a.order_hist = (uint32_t*)o;
+    o += align256((size_t)(RR_MAX_BOUNCES + 1) * rr::kOrderBuckets * 4);
+    a.order_off = (uint32_t*)o;
+  }
   a.ray_cap = L.ray_cap;
   a.rec_cap = L.rec_cap;
   if (dbg) {
@@ -414,7 +433,7 @@ int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor
     a.mask = dbg->mask;
   }
   s->launches += 2u + 2u * maxb + ((any_flags & RR_MULTIPATH) && maxb > 1 ? 2u * (maxb - 1u) : 0u) +
-                 (pattern ? 1u : 0u);
+                 (pattern ? 1u : 0u) + (a.order_perm ? 2u * (maxb - 1u) : 0u);
   const bool prof = profile && s->prof;
   if (!prof && allow_graph && cfg.use_graph && !dbg) return graph_launch(s, x, a, pattern, cfg, st);
   e = launch_sequence(s, a, pattern, cfg, prof, st);
@@ -518,6 +537,8 @@ static int cfg_check(const rr_batch_config* c) {
     return fail(RR_ERR_INVALID_ARG, "workspace_limit must be 0 or at least 1 MiB");
   if (c->bvh_build != RR_BVH_LBVH && c->bvh_build != RR_BVH_SAH_TOP)
     return fail(RR_ERR_INVALID_ARG, "bvh_build must be RR_BVH_LBVH or RR_BVH_SAH_TOP");
+  if (c->query_order > RR_ORDER_CELL_OCTANT)
+    return fail(RR_ERR_INVALID_ARG, "query_order must be RR_ORDER_QUEUE or RR_ORDER_CELL_OCTANT");
   return RR_OK;
 }
 
@@ -532,6 +553,7 @@ static void cfg_to_abi(const LaunchCfg& c, rr_batch_config* o) {
   o->workspace_limit = c.ws_limit;
   o->split_streams = c.split;
   o->bvh_build = c.bvh_build;
+  o->query_order = c.order;
 }
 
 static LaunchCfg cfg_from_abi(const rr_batch_config* c) {
@@ -545,6 +567,7 @@ static LaunchCfg cfg_from_abi(const rr_batch_config* c) {
   if (c->workspace_limit) o.ws_limit = c->workspace_limit;
   o.split = c->split_streams ? c->split_streams : 3u;
   o.bvh_build = c->bvh_build;
+  o.order = c->query_order;
   return o;
 }
 

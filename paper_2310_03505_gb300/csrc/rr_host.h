@@ -33,6 +33,7 @@ struct LaunchCfg {
   uint32_t split = 3;                 // a single scan as this many azimuth ranges on their own streams
   uint64_t ws_limit = uint64_t(24) << 30;
   uint32_t bvh_build = RR_BVH_SAH_TOP;
+  uint32_t order = 0;                 // RR_ORDER_*: query order of the closest-hit queries of bounces >= 1
 };
 
 constexpr uint32_t kMaxSplit = 4;
@@ -157,6 +158,7 @@ cudaError_t launch_raygen(const rr::ScanArgs& a, cudaStream_t st);
 cudaError_t launch_query(const rr::ScanArgs& a, uint32_t bounce, bool any, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_vis_prep(const rr::ScanArgs& a, uint32_t bounce, cudaStream_t st);
 cudaError_t launch_shade(const rr::ScanArgs& a, uint32_t bounce, cudaStream_t st);
+cudaError_t launch_order(const rr::ScanArgs& a, uint32_t bounce, cudaStream_t st);   // query order of a bounce
 
 // failure detection (rr_selftest_wait): each runs one bounded device wait on
 // a flag that nothing sets and reports whether it gave up as designed
@@ -179,7 +181,7 @@ void prof_end(rr_scene* s, cudaEvent_t stop, cudaStream_t st);
 // scan orchestration shared by the entry points (rr_batch.cu)
 struct WsLayout {
   uint32_t ray_cap, rec_cap, tiles, n_desc;
-  size_t off_rays0, off_rays1, off_hits, off_recs, off_status, off_tmp, off_desc, total;
+  size_t off_rays0, off_rays1, off_hits, off_recs, off_status, off_tmp, off_desc, off_order, total;
   size_t tmp_floats;
   bool clamped;
 };

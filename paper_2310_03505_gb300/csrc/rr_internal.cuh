@@ -95,6 +95,11 @@ constexpr uint32_t kMaxColumns = 1u << (32 - kBinBits);   // columns of one laun
 constexpr uint32_t kMaxBatchScans = 0xFFFFu;       // scan index lives in 16 bits of RayRec.meta.w
 constexpr uint32_t kMediumMask = 0xFFFFu;
 
+// Buckets of the closest-hit query order: direction octant (3 bits), height
+// cell (2 bits) and an 8 x 8 grid of horizontal cells (6 bits, Morton order)
+// around the scan's sensor
+constexpr uint32_t kOrderBuckets = 1u << 11;
+
 // Per-scan constants of a batch (one pose and sensor model), 160 bytes.
 // Kernels read the fields of the scan each ray belongs to.
 struct __align__(16) ScanDesc {
@@ -140,6 +145,11 @@ struct ScanArgs {
   ScanCounters* ctr;
   float* image_tmp;          // images before the azimuth pattern (or null)
   uint32_t ray_cap, rec_cap;
+  // query order of the closest-hit queries of bounces >= 1 (null: queue order)
+  uint16_t* order_key;       // [ray_cap] bucket of every queued ray (written by the shading pass)
+  uint32_t* order_perm;      // [ray_cap] queue index of the j-th query
+  uint32_t* order_hist;      // [RR_MAX_BOUNCES + 1][kOrderBuckets] rays per bucket
+  uint32_t* order_off;       // [kOrderBuckets] next free position of every bucket
   // debug (may be null)
   rr_segment* segs;
   uint32_t seg_cap;
@@ -202,7 +212,13 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 __device__ __forceinline__ float length(float3 a) { return sqrtf(dot(a, a)); }
-__device__ __forceinline__ float3 normalize(float3 a) { return rsqrtf(dot(a, a)) * a; }
+// a / |a| with correctly rounded square root and divisions: no systematic
+// bias (an approximate reciprocal square root has one, and a ray reflected
+// many times between parallel walls accumulates it into its direction)
+__device__ __forceinline__ float3 normalize(float3 a) {
+  const float n = sqrtf(dot(a, a));
+  return make_float3(__fdiv_rn(a.x, n), __fdiv_rn(a.y, n), __fdiv_rn(a.z, n));
+}
 // angle between two vectors, well conditioned at 0 and pi
 __device__ __forceinline__ float angle_between(float3 a, float3 b) { return atan2f(length(cross(a, b)), dot(a, b)); }
 

@@ -233,6 +233,15 @@ __device__ __forceinline__ bool trav_tri(Trav& s, const ScanArgs& a, uint32_t j,
   return false;
 }
 
+// two float4 of read-only memory with one 256-bit load (p 32-byte aligned):
+// a node is two such loads instead of four 128-bit ones, half the load
+// instructions and L1 wavefronts of the divergent node fetches
+__device__ __forceinline__ void ldg256(const float4* p, float4& a, float4& b) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+
 // one step over the binary LBVH (both children tested, nearer first)
 template <bool kAny>
 __device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const ScanArgs& a, uint32_t& n_nodes,
@@ -243,7 +252,9 @@ __device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const Scan
     ++s.visits;   // bounded where the query loop looks at its lanes
     const float3 o = s.w.o, id = s.id;
     const float4* np = a.nodes + 4 * (size_t)node;
-    const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+    float4 n0, n1, n2, n3;   // 64-byte nodes from a 256-byte aligned allocation
+    ldg256(np, n0, n1);
+    ldg256(np + 2, n2, n3);
     // child 0
     float t0 = (n0.x - o.x) * id.x, t1 = (n0.y - o.x) * id.x;
     float lo0 = fminf(t0, t1), hi0 = fmaxf(t0, t1);
@@ -426,7 +437,11 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
   if (!kAny) {
     const uint32_t tiles = (n + kShadeBlock - 1) / kShadeBlock;
     for (uint32_t t = gtid; t < tiles; t += gsz) a.tile_status[t] = 0ull;
+    // the shading pass of this bounce counts the next bounce's rays per order bucket
+    if (a.order_hist != nullptr && bounce + 1 <= RR_MAX_BOUNCES)
+      for (uint32_t t = gtid; t < kOrderBuckets; t += gsz) a.order_hist[(bounce + 1) * kOrderBuckets + t] = 0u;
   }
+  const uint32_t* __restrict__ perm = (!kAny && bounce > 0) ? a.order_perm : nullptr;
   const RayRec* __restrict__ q = a.rays[bounce & 1];
   const uint2* __restrict__ jobs = reinterpret_cast<const uint2*>(a.rays[(bounce + 1) & 1]);
   // after a failed build every query ends at once as a miss and the scan fails
@@ -485,7 +500,8 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
           const float dist = length(v);
           trav_begin(s, p, (1.0f / dist) * v, __ldg(&sd->phys.x), dist, h.leaf, a.n_tris, kWide);
         } else {
-          ray_i = job;
+          ray_i = perm ? perm[job] : job;
+          if (ray_i >= n) ray_i = job;   // only after a failed shading pass (the scan reports it)
           const RayRec ray = q[ray_i];
           const uint2 sm = ray_scan_medium(a, ray.meta.w);
           const float4 phys = __ldg(&a.desc[sm.x].phys);   // t_min, min_energy, freq, r_lim
@@ -687,6 +703,75 @@ __device__ __forceinline__ uint2 look_back(const ScanArgs& a, uint32_t tile, uin
 __global__ void k_selftest_look_back(ScanArgs a) { look_back(a, 1u, 0u, 0u); }
 
 // ---------------------------------------------------------------------------
+// query order: bucket of a queued ray (direction octant, then a 4 x 64 grid of
+// cells of its origin around the sensor: height in r_max / 16 steps from one
+// below the sensor, horizontal r_max / 4 cells in Morton order)
+__device__ __forceinline__ uint32_t order_key(const ScanArgs& a, const RayRec& r) {
+  const ScanDesc* sd = a.desc + ray_scan_medium(a, r.meta.w).x;
+  const float4 pr = __ldg(&sd->pos_rmax);
+  const float inv = 4.0f / fmaxf(pr.w, 1e-3f);
+  const int cx = min(max((int)floorf((r.o_L.x - pr.x) * inv) + 4, 0), 7);
+  const int cy = min(max((int)floorf((r.o_L.y - pr.y) * inv) + 4, 0), 7);
+  const int cz = min(max((int)floorf((r.o_L.z - pr.z) * (4.0f * inv)) + 1, 0), 3);
+  uint32_t xy = 0;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) xy |= (((uint32_t)cx >> b) & 1u) << (2 * b) | (((uint32_t)cy >> b) & 1u) << (2 * b + 1);
+  const uint32_t oct = (r.d_E.x < 0.0f ? 1u : 0u) | (r.d_E.y < 0.0f ? 2u : 0u) | (r.d_E.z < 0.0f ? 4u : 0u);
+  return oct << 8 | (uint32_t)cz << 6 | xy;
+}
+
+// exclusive prefix of the bucket counts of a bounce (one block of 1024 threads, two buckets each)
+__global__ void __launch_bounds__(1024) k_order_scan(ScanArgs a, uint32_t bounce) {
+  __shared__ uint32_t s_w[32];
+  const uint32_t* h = a.order_hist + bounce * kOrderBuckets;
+  const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+  const uint32_t c0 = h[2 * t], c1 = h[2 * t + 1];
+  uint32_t x = c0 + c1;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+    if ((int)lane >= off) x += y;
+  }
+  if (lane == 31u) s_w[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = s_w[lane];
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, v, off);
+      if ((int)lane >= off) v += y;
+    }
+    s_w[lane] = v;
+  }
+  __syncthreads();
+  const uint32_t excl = x - (c0 + c1) + (warp ? s_w[warp - 1] : 0u);
+  a.order_off[2 * t] = excl;
+  a.order_off[2 * t + 1] = excl + c0;
+}
+
+// the permutation: every queued ray of the bounce to the next free position
+// of its bucket (rays of one bucket in any order: every query's result is
+// independent of the order)
+__global__ void k_order_scatter(ScanArgs a, uint32_t bounce) {
+  const uint32_t n = min(a.ctr->count[bounce], a.ray_cap);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+    const uint32_t i = i0 + threadIdx.x;
+    const bool has = i < n;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, has);
+    if (has) {
+      const uint32_t key = a.order_key[i] & (kOrderBuckets - 1u);
+      const uint32_t peers = __match_any_sync(m, key);
+      const uint32_t leader = __ffs(peers) - 1u;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&a.order_off[key], (uint32_t)__popc(peers));
+      base = __shfl_sync(peers, base, leader);
+      const uint32_t pos = base + __popc(peers & ((1u << lane) - 1u));
+      if (pos < a.ray_cap) a.order_perm[pos] = i;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // shade
 
 // optional range weight of a return at range r (metres): (1 / r)^k for
@@ -696,7 +781,7 @@ __device__ __forceinline__ float range_weight(const ScanDesc* sd, float r) {
   return (k != 0.0f && r > 1.0f) ? powf(r, -k) : 1.0f;
 }
 
-__global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t bounce) {
+__global__ void __launch_bounds__(kShadeBlock, 3) k_shade(ScanArgs a, uint32_t bounce) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wsum[kShadeBlock / 32];
   __shared__ uint2 s_excl;
@@ -911,6 +996,21 @@ __global__ void __launch_bounds__(kShadeBlock) k_shade(ScanArgs a, uint32_t boun
       const uint32_t pos = kbase + c;
       if (pos < a.ray_cap) qout[pos] = kid[c];
     }
+    if (a.order_key != nullptr && bounce + 1 < a.max_bounces) {
+      // order buckets of the children, counted with one atomic per bucket and warp
+      for (uint32_t c = 0; c < 2u; ++c) {
+        const uint32_t pos = kbase + c;
+        const bool has = c < nk && pos < a.ray_cap;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, has);
+        if (has) {
+          const uint32_t key = order_key(a, kid[c]);
+          a.order_key[pos] = (uint16_t)key;
+          const uint32_t peers = __match_any_sync(m, key);
+          if (lane == __ffs(peers) - 1)
+            atomicAdd(&a.order_hist[(bounce + 1) * kOrderBuckets + key], (uint32_t)__popc(peers));
+        }
+      }
+    }
     for (uint32_t c = 0; c < nr; ++c) {
       const uint32_t pos = rec0 + rbase + c;
       if (pos < a.rec_cap) a.recs[pos] = rec[c];
@@ -1029,6 +1129,13 @@ cudaError_t launch_query(const ScanArgs& a, uint32_t bounce, bool any, const Lau
 cudaError_t launch_vis_prep(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
   init_dims();
   k_vis_prep<<<g_num_sms * 8, 256, 0, st>>>(a, bounce);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
+  init_dims();
+  k_order_scan<<<1, 1024, 0, st>>>(a, bounce);
+  k_order_scatter<<<g_num_sms * 4, 256, 0, st>>>(a, bounce);
   return cudaGetLastError();
 }
 

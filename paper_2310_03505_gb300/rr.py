@@ -87,11 +87,13 @@ class rr_profile(C.Structure):
 class rr_batch_config(C.Structure):
     _fields_ = [("wavefront_rays", C.c_uint32), ("trace_block", C.c_uint32), ("trace_blocks_per_sm", C.c_uint32),
                 ("use_graph", C.c_uint32), ("node_format", C.c_uint32), ("refill_threshold", C.c_uint32),
-                ("workspace_limit", C.c_uint64), ("split_streams", C.c_uint32), ("bvh_build", C.c_uint32)]
+                ("workspace_limit", C.c_uint64), ("split_streams", C.c_uint32), ("bvh_build", C.c_uint32),
+                ("query_order", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 RR_NODES_WIDE8, RR_NODES_BINARY = 0, 1
 RR_BVH_LBVH, RR_BVH_SAH_TOP = 0, 1
+RR_ORDER_QUEUE, RR_ORDER_CELL_OCTANT = 0, 1
 WIDE_NODE_BYTES = 80
 RR_REQ_QUEUED, RR_REQ_RUNNING, RR_REQ_DONE, RR_REQ_FAILED = range(4)
 
@@ -376,7 +378,7 @@ def rr_scan_batch_async(scene, poses, params, outs) -> None:
 def rr_batch_config_get(scene) -> dict:
     c = rr_batch_config()
     _check(load().rr_batch_config_get(scene, C.byref(c)))
-    return {k: getattr(c, k) for k, _ in rr_batch_config._fields_}
+    return {k: getattr(c, k) for k, _ in rr_batch_config._fields_ if k != "reserved"}
 
 
 def rr_batch_config_set(scene, **cfg) -> None:
@@ -386,7 +388,7 @@ def rr_batch_config_set(scene, **cfg) -> None:
     if unknown:
         raise ValueError(f"unknown batch config keys {sorted(unknown)}")
     cur.update(cfg)
-    c = rr_batch_config(*[int(cur[k]) for k, _ in rr_batch_config._fields_])
+    c = rr_batch_config(*[int(cur.get(k, 0)) for k, _ in rr_batch_config._fields_])
     _check(load().rr_batch_config_set(scene, C.byref(c)))
 
 
@@ -397,7 +399,7 @@ def rr_batch_plan(params, config: dict | None = None):
     cfg = None
     if config is not None:
         full = dict(wavefront_rays=0, trace_block=128, trace_blocks_per_sm=0, use_graph=1, node_format=1,
-                    refill_threshold=8, workspace_limit=0, split_streams=3, bvh_build=1)
+                    refill_threshold=8, workspace_limit=0, split_streams=3, bvh_build=1, query_order=0, reserved=0)
         full.update(config)
         cfg = C.byref(rr_batch_config(*[int(full[k]) for k, _ in rr_batch_config._fields_]))
     cap = max(n, 1)

@@ -200,24 +200,34 @@ class _Segs:
             cos = np.maximum(self.s["cos_i"].astype(np.float64), 1e-3)
             self.allow = np.where(hit, K_SIG * sig / cos, 0.0)
         self.allow_path = self.allow.copy()
+        # relative energy allowance from attenuation: a segment inside a lossy
+        # medium whose length may move by its distance allowance changes the
+        # energy it delivers by 2 alpha times that; the children inherit it
+        self.att_own = self.s["alpha2"] * self.allow if "alpha2" in (s.dtype.names or ()) else np.zeros(len(self.key))
+        self.att_path = np.zeros(len(self.key))   # over the strict ancestors
         for b in range(1, int(self.bounce.max()) + 1 if len(self.bounce) else 0):
             sel = np.nonzero((self.bounce == b) & (self.parent >= 0))[0]
             self.length[sel] += self.length[self.parent[sel]]
             self.along[sel] += self.along[self.parent[sel]]
             self.allow_path[sel] += self.allow_path[self.parent[sel]]
+            self.att_path[sel] = self.att_path[self.parent[sel]] + self.att_own[self.parent[sel]]
 
 
-def compare_segment_energies(gpu_segs, ora_segs, ora_flags, az_list, rel=1e-3, abs_rel_E=1e-6):
+def compare_segment_energies(gpu_segs, ora_segs, ora_flags, az_list, rel=1e-3, abs_rel_E=1e-6, coord_max=1.0):
     """Per segment of every unflagged ray: energy entering, cos theta0 and the
     two return energies, within rel of the oracle plus abs_rel_E of the
     energies along the path down to the segment (its own and every
-    ancestor's) plus E_FLOOR.  The path term: a child's energy is E R minus
-    the returns (reading 8), a difference whose FP32 rounding is relative to
-    the energies it is taken from -- when the returns take nearly all of E R
-    the child is a residue far below them -- and that error then moves down
-    the tree scaled by factors <= 1.  Returns a list of mismatch descriptions."""
+    ancestor's) plus E_FLOOR, plus the attenuation allowance: inside a lossy
+    medium the energy a segment delivers is E exp(-2 alpha t), so a length
+    that may move by its distance allowance dt (module notes) moves the
+    energy by 2 alpha dt of itself, for the segment's returns and for every
+    descendant.  The path term: a child's energy is E R minus the returns
+    (reading 8), a difference whose FP32 rounding is relative to the
+    energies it is taken from -- when the returns take nearly all of E R the
+    child is a residue far below them -- and that error then moves down the
+    tree scaled by factors <= 1.  Returns a list of mismatch descriptions."""
     az_list = list(az_list)
-    o, g = _Segs(ora_segs, az_list, ora_flags), _Segs(gpu_segs, az_list, ora_flags)
+    o, g = _Segs(ora_segs, az_list, ora_flags, coord_max), _Segs(gpu_segs, az_list, ora_flags)
     gi = np.searchsorted(g.key, o.key)
     gi = np.minimum(gi, max(len(g.key) - 1, 0))
     present = (g.key[gi] == o.key) if len(g.key) else np.zeros(len(o.key), bool)
@@ -226,7 +236,8 @@ def compare_segment_energies(gpu_segs, ora_segs, ora_flags, az_list, rel=1e-3, a
         a = g.s[f][gi].astype(np.float64)
         b = o.s[f].astype(np.float64)
         scale = o.s["E"].astype(np.float64) if f == "cos_i" else o.along
-        off = present & (np.abs(a - b) > rel * np.abs(b) + abs_rel_E * scale + E_FLOOR)
+        att = 0.0 if f == "cos_i" else (o.att_path if f == "E" else o.att_path + o.att_own)
+        off = present & (np.abs(a - b) > (rel + att) * np.abs(b) + abs_rel_E * scale + E_FLOOR)
         for i in np.nonzero(off)[0][:20]:
             az, k = az_list[int(o.ray[i]) // ora_flags.shape[1]], int(o.ray[i]) % ora_flags.shape[1]
             bad.append(f"ray {(az, k)} seg {(int(o.path[i]), int(o.bounce[i]))} {f}: gpu {a[i]:.9g} oracle "

@@ -51,7 +51,7 @@ def test_large_sampled_rays(large):
     n, bad, max_rel = P.compare_paths(segs, ora["segments"], skip.astype(np.uint8), COLS, cmax)
     assert n == int((~skip).sum()) > 3400
     assert not bad, f"{len(bad)} mismatches of {n} rays, first: {bad[:5]}"
-    ebad = P.compare_segment_energies(segs, ora["segments"], skip.astype(np.uint8), COLS)
+    ebad = P.compare_segment_energies(segs, ora["segments"], skip.astype(np.uint8), COLS, coord_max=cmax)
     assert not ebad, f"{len(ebad)} energy mismatches, first: {ebad[:3]}"
     nd, dbad, worst = P.compare_segment_distances(segs, ora["segments"], skip.astype(np.uint8), COLS, cmax)
     assert nd > 50_000 and not dbad, f"{len(dbad)} of {nd} hit distances off (worst {worst:.3g}), first: {dbad[:5]}"

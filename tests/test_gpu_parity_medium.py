@@ -40,7 +40,7 @@ def test_medium_full_scan_every_ray(medium, variant):
     n, bad, _ = P.compare_paths(segs, ora["segments"], flags, cols, cmax)
     assert n == int((flags == 0).sum())
     assert not bad, f"{len(bad)} mismatches of {n} rays, first: {bad[:5]}"
-    ebad = P.compare_segment_energies(segs, ora["segments"], flags, cols)
+    ebad = P.compare_segment_energies(segs, ora["segments"], flags, cols, coord_max=cmax)
     assert not ebad, f"{len(ebad)} segment energy mismatches, first: {ebad[:5]}"
     nd, dbad, worst = P.compare_segment_distances(segs, ora["segments"], flags, cols, cmax)
     assert nd > 500_000 and not dbad, f"{len(dbad)} of {nd} hit distances off (worst {worst:.3g}), first: {dbad[:5]}"

@@ -77,7 +77,7 @@ def check_parity(sc, pz, params, h, max_flagged=0.02, seg_capacity=None):
     assert n >= (~flags.astype(bool)).sum()
     assert not bad, f"{len(bad)} mismatches, first: {bad[:5]}"
     assert len(segs) == len(ora["segments"]) or flags.any()
-    ebad = P.compare_segment_energies(segs, ora["segments"], flags, range(params["n_azimuth"]))
+    ebad = P.compare_segment_energies(segs, ora["segments"], flags, range(params["n_azimuth"]), coord_max=cmax)
     assert not ebad, f"{len(ebad)} segment energy mismatches, first: {ebad[:6]}"
     # every single hit distance
     nd, dbad, _ = P.compare_segment_distances(segs, ora["segments"], flags, range(params["n_azimuth"]), cmax)
@@ -132,7 +132,8 @@ def test_tiny_parity_at_the_ray_limit(tiny_scene):
     n, bad, _ = P.compare_paths(segs, ora["segments"], skip.astype(np.uint8), cols, P.coord_max(sc, pz))
     assert n == int((~skip).sum()) > 400
     assert not bad, f"{len(bad)} mismatches of {n} rays, first: {bad[:5]}"
-    ebad = P.compare_segment_energies(segs, ora["segments"], skip.astype(np.uint8), cols)
+    ebad = P.compare_segment_energies(segs, ora["segments"], skip.astype(np.uint8), cols,
+                                      coord_max=P.coord_max(sc, pz))
     assert not ebad, f"{len(ebad)} energy mismatches, first: {ebad[:3]}"
     img, _, _ = P.gpu_debug(h, pz, params, mask=skip.astype(np.uint8), seg_capacity=4 << 20)
     slack = P.slack_after_post(ora, params, cols)

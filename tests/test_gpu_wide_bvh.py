@@ -203,3 +203,26 @@ def test_refill_threshold_does_not_change_hits(rrlib, fmt):
     finally:
         rr.rr_batch_config_set(h, **saved)
         rr.rr_scene_destroy(h)
+
+
+@pytest.mark.parametrize("config", ["tiny", "campus"])
+def test_query_order_does_not_change_hits(rrlib, config):
+    """The closest-hit queries of bounces >= 1 handed out in bucket order
+    (direction octant and origin cell) instead of queue order: every segment
+    (triangle, distance, energies, visits) is the same, the image the same
+    up to the rounding of the bin sums."""
+    sc, pz, params = scenes.config_tiny() if config == "tiny" else scenes.config_medium()
+    h = P.gpu_scene(sc)
+    saved = rr.rr_batch_config_get(h)
+    try:
+        out = []
+        for order in (rr.RR_ORDER_QUEUE, rr.RR_ORDER_CELL_OCTANT):
+            rr.rr_batch_config_set(h, query_order=order)
+            img, segs, _ = P.gpu_debug(h, pz, params)
+            out.append((img, sorted_segments(segs)))
+        assert_same_hits(out[1][1], out[0][1])
+        assert np.array_equal(out[1][1]["visits"], out[0][1]["visits"])
+        assert np.max(np.abs(out[1][0] - out[0][0])) <= 1e-6 * out[0][0].max()
+    finally:
+        rr.rr_batch_config_set(h, **saved)
+        rr.rr_scene_destroy(h)
