@@ -338,8 +338,8 @@ def batched_bench(device, stream, flush, steps: int = 3, warmup: int = 2, rank: 
 SERVED_WORKLOAD = "4_scenes_50k_200k_1M_5M_tris_64_robots_poisson_16_512_rays_3_8_bounces_500_4000_bins"
 
 
-def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: int = 0, bvh: str = "sah_top",
-                 city=None):
+def served_bench(device, seconds: float = 60.0, rates=(30, 60, 120, 240), rank: int = 0, bvh: str = "sah_top",
+                 city=None, short_seconds: float = 10.0):
     """Scan requests from 64 simulated robots over 4 resident scenes (50k and
     200k-triangle campuses, the 1M-triangle campus, the 5M-triangle city),
     Poisson arrivals at each rate for `seconds`; every request draws a free
@@ -348,8 +348,9 @@ def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: 
     (4 slots) and, for comparison, by a server that runs one request at a time
     (the plain per-scan path).  Latency = submit to completion as the server
     records it; Mrays/s = closest-hit queries / window (arrivals + drain).
-    The configured rates are 30, 60 and 120 requests/s; 240 is added to show
-    the servers near saturation."""
+    The configured rates are 30, 60 and 120 requests/s, served for `seconds`
+    each; 240 is added to show the servers near saturation, and the
+    one-at-a-time comparison, both for `short_seconds`."""
     import torch
     from paper_2310_03505_gb300 import rr, scenes
     scs = [(scenes.campus(target_tris=50_000, seed=0x5EED0004, n_buildings=60, n_cylinders=150, extent=80.0), 70.0),
@@ -370,7 +371,7 @@ def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: 
                           bin_size=0.0438, beam_width=math.radians(10.0), seed=0x5EED0005 + robot, scan_id=sid)
         return si, scenes.random_pose(sc, rng, 1.8, ext), p
 
-    def run(cfg, rate, seed):
+    def run(cfg, rate, seed, seconds):
         sv = rr.rr_serve_create(**cfg)
         rng = np.random.default_rng(seed)
         try:
@@ -422,16 +423,18 @@ def served_bench(device, seconds: float = 10.0, rates=(30, 60, 120, 240), rank: 
                 "p50_ms": st["latency_p50_ms"], "p99_ms": st["latency_p99_ms"], "mean_ms": st["latency_mean_ms"],
                 "max_ms": st["latency_max_ms"], "mrays_per_s": st["closest_queries"] / win / 1e6,
                 "busy_fraction": st["busy_ms"] / max(st["elapsed_ms"], 1e-9), "batches": int(st["batches"]),
+                "requests_per_batch": st["completed"] / max(st["batches"], 1), "retried": int(st["retried"]),
                 "window_s": win}
 
     served = dict(slots=4, memory_budget=96 << 30, max_batch_scans=64, max_batch_rays=8 << 20)
     plain = dict(slots=1, memory_budget=24 << 30, max_batch_scans=1)
-    out = {"workload": SERVED_WORKLOAD, "seconds_per_rate": seconds,
+    out = {"workload": SERVED_WORKLOAD, "seconds_per_rate": seconds, "seconds_short": short_seconds,
+           "admission": "estimate of the ray tree per scene (x2), worst case on the first batch and on overflow",
            "scenes_triangles": [sc.n_triangles for sc, _ in scs], "robots": 64, "bvh": bvh,
            "server": {k: int(v) for k, v in served.items()}, "rates": [], "per_scan_path": []}
     for k, rate in enumerate(rates):
-        out["rates"].append(run(served, rate, 1000 + k))
-        out["per_scan_path"].append(run(plain, rate, 1000 + k))
+        out["rates"].append(run(served, rate, 1000 + k, seconds if rate <= 120 else short_seconds))
+        out["per_scan_path"].append(run(plain, rate, 1000 + k, short_seconds))
     for h in hs:
         rr.rr_scene_destroy(h)
     return out
@@ -645,8 +648,8 @@ def main():
     ap.add_argument("--workspace-limit-gb", type=float, default=0.0,
                     help="scan workspace limit of the headline scene (0: the library default); the profile "
                          "commands use 1 GiB so that the captured process holds a few GB")
-    ap.add_argument("--served-seconds", type=float, default=10.0,
-                    help="arrival window per request rate of the served workload")
+    ap.add_argument("--served-seconds", type=float, default=60.0,
+                    help="arrival window per configured request rate (30, 60, 120/s) of the served workload")
     args = ap.parse_args()
     world, rank, local = dist_env()
 

@@ -496,7 +496,19 @@ typedef struct rr_server rr_server; /* opaque */
                     single larger request still runs alone
    max_queue        most requests waiting for a slot (0: 4096); beyond it
                     rr_serve_submit returns RR_ERR_BUSY
-   node_format, refill_threshold   as in rr_batch_config */
+   node_format, refill_threshold   as in rr_batch_config
+   admission        RR_ADMIT_ESTIMATE (default): a batch's workspace is sized
+                    by an estimate of its ray tree -- the largest queue and
+                    return counts per initial ray seen at every bounce of
+                    the scene's earlier batches (bounces not seen yet: twice
+                    the previous bounce), times estimate_factor; the scene's
+                    first batch, and any batch that outgrows its estimate
+                    (rerun, never dropped: rr_serve_stats.retried), are sized
+                    for the worst case.  RR_ADMIT_WORST_CASE: always the
+                    worst case (every hit spawning both children).
+   estimate_factor  safety factor of the estimate (0: 2; must be >= 0) */
+#define RR_ADMIT_ESTIMATE 0u
+#define RR_ADMIT_WORST_CASE 1u
 typedef struct {
   uint64_t memory_budget;
   uint32_t slots;
@@ -505,6 +517,8 @@ typedef struct {
   uint32_t max_queue;
   uint32_t node_format;
   uint32_t refill_threshold;
+  uint32_t admission;
+  float estimate_factor;
 } rr_serve_config;
 
 /* request states */
@@ -536,6 +550,8 @@ typedef struct {
   uint64_t queued;
   double busy_ms, elapsed_ms;
   double latency_p50_ms, latency_p99_ms, latency_mean_ms, latency_max_ms;
+  uint64_t retried;   /* requests rerun at worst-case size after their estimated batch overflowed */
+  uint64_t reserved;
 } rr_serve_stats;
 
 /* Starts a server (its worker thread and slots) on the current device.

@@ -524,7 +524,8 @@ static void tri_normal(const scene_t* s, uint32_t j, double n[3]) {
 /* cos theta0, the mirror formula, the normalisation); a refraction scales  */
 /* the incoming direction error by the derivative of Snell's law            */
 /* eta cos theta0 / cos theta2 and adds a third of the bound (6 eta^2 + 5)  */
-/* 2^-24 / (2 cos theta2) of the rounding of sin^2 theta2, plus ERR_REFR    */
+/* 2^-24 / (2 cos theta2) of the rounding of sin^2 theta2, the normal's     */
+/* ERR_NRM ulps turned by (A - 1) (A the same derivative), plus ERR_REFR    */
 /* ulps.  A hit or near miss within FLAG_SIGMAS standard deviations of a    */
 /* triangle edge is a decision float32 can take the other way and flags the */
 /* ray; the parity tests take the same estimate for the hit distances.      */
@@ -533,6 +534,7 @@ static void tri_normal(const scene_t* s, uint32_t j, double n[3]) {
 #define ERR_DIR0 2.0     /* ulps of the generated direction */
 #define ERR_REFL 2.0     /* ulps a reflection adds */
 #define ERR_REFR 1.0     /* ulps a refraction adds besides the Snell term */
+#define ERR_NRM 1.5      /* ulps of a triangle normal computed from float vertices */
 #define FLAG_SIGMAS 4.0  /* standard deviations of a hit point that flag an edge */
 
 /* one float32 ulp of x (the spacing of floats around |x|, at least 2^-149) */
@@ -1349,8 +1351,11 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
         if (!tir && (p->flags & ORC_REFRACTION)) {
           double eta = n1 / n2;
           const double snell = (6.0 * eta * eta + 5.0) * ULP32 / (2.0 * cos_t);
-          const double amp = ray.e_dir * eta * cos_i / cos_t;
-          e_refr_dir = sqrt(amp * amp + snell * snell / 9.0 + ERR_REFR * ERR_REFR * ULP32 * ULP32);
+          /* Snell's derivative scales the incoming direction's error; a normal
+             turned by dn turns the refracted direction by (A - 1) dn */
+          const double A = eta * cos_i / cos_t;
+          const double amp = ray.e_dir * A, nrm = ERR_NRM * ULP32 * fabs(A - 1.0);
+          e_refr_dir = sqrt(amp * amp + nrm * nrm + snell * snell / 9.0 + ERR_REFR * ERR_REFR * ULP32 * ULP32);
           if (!(snell <= FLAG_TDIR)) seg.flags |= SEG_SNELL;
         }
       }

@@ -105,6 +105,17 @@ WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit, 
   return layout_of(nd, limit);
 }
 
+WsLayout plan_workspace_caps(const rr_sensor_params* ps, uint32_t n, uint64_t q_cap, uint64_t r_cap) {
+  Need nd;
+  for (uint32_t i = 0; i < n; ++i) nd.add(ps[i]);
+  Need e = nd;
+  e.q = std::min(nd.q, std::max(q_cap, nd.n0));
+  e.r = std::min(nd.r, std::max(r_cap, 2 * nd.n0));
+  WsLayout L = layout_of(e, ~uint64_t(0));
+  L.clamped = e.q < nd.q || e.r < nd.r;
+  return L;
+}
+
 std::vector<Group> plan_groups(const rr_sensor_params* ps, uint32_t n, const LaunchCfg& cfg) {
   std::vector<Group> out;
   uint32_t i = 0;

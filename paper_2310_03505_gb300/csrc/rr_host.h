@@ -204,6 +204,9 @@ int check_params(const rr_pose* pose, const rr_sensor_params* p);
 int check_device(const rr_scene* s, const char* who);
 // worst-case workspace of scans ps[0..n) traced together, clamped to limit
 WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit, const uint32_t* az_count = nullptr);
+// the same with the queues and records sized to given capacities (an estimate of the
+// ray tree; clamped = smaller than the worst case), never below the initial rays
+WsLayout plan_workspace_caps(const rr_sensor_params* ps, uint32_t n, uint64_t q_cap, uint64_t r_cap);
 // split n scans into launch sequences that respect the limits of cfg
 std::vector<Group> plan_groups(const rr_sensor_params* ps, uint32_t n, const LaunchCfg& cfg);
 // queue the launch sequence of scans poses/ps[0..n) writing images[i]

@@ -8,8 +8,15 @@
 // budget when the server is created (nothing is allocated while serving).
 // Whenever a slot is free the worker forms the next batch: the oldest waiting
 // request's scene, then every other waiting request for that scene in
-// arrival order whose worst-case ray tree still fits the slot's arena (and
-// the scan / ray limits of a batch).  The batch runs as one launch sequence
+// arrival order whose ray tree still fits the slot's arena (and the scan /
+// ray limits of a batch).  A ray tree is sized by an estimate once the scene
+// has run a batch: the largest queue and record counts per initial ray seen
+// on that scene at every bounce (bounces not seen yet: twice the previous
+// one), times the configured safety factor -- far below the worst
+// case (every hit spawning both children), so more requests share a launch
+// sequence.  A batch that outgrows its estimate (the device reports
+// RR_ERR_CAPACITY, nothing is dropped silently) goes back to the front of the
+// queue and its requests are rerun at worst-case size.  The batch runs as one launch sequence
 // of rr_scan_batch's kernels, so requests that arrive while others are on the
 // GPU join the next batch as soon as a slot and its memory free up, and the
 // batches of different slots overlap on the device.  A finished batch's
@@ -51,6 +58,15 @@ struct Request {
   double submit_ms = 0, start_ms = 0, done_ms = 0;
   uint32_t batch_size = 0;
   uint64_t rays0 = 0;
+  bool worst = false;   // size its batch for the worst-case tree (a retry after an overflow)
+};
+
+// largest queue length and return records per initial ray seen at every
+// bounce of a scene's batches
+struct Growth {
+  uint32_t depth = 0;   // bounces seen (0: no batch yet)
+  double q[RR_MAX_BOUNCES + 1] = {0};
+  double r[RR_MAX_BOUNCES + 1] = {0};
 };
 
 struct Slot {
@@ -62,6 +78,9 @@ struct Slot {
   std::vector<uint64_t> batch;   // tickets in flight (empty: free)
   std::vector<float*> images;    // device image of each
   unsigned long long closest0 = 0, anyhit0 = 0;   // counters before the batch
+  bool estimated = false;        // the batch was sized by the growth estimate
+  uint64_t n0 = 0;               // initial rays of the batch
+  uint32_t max_bounces = 0;
 };
 
 }  // namespace rr_host
@@ -76,11 +95,12 @@ struct rr_server {
   std::condition_variable cv_work, cv_done;
   std::deque<uint64_t> pending;                                  // waiting tickets, arrival order
   std::unordered_map<uint64_t, rr_host::Request> reqs;          // live and finished, until read
+  std::unordered_map<const rr_scene*, rr_host::Growth> growth;  // ray-tree statistics per scene
   uint64_t next_ticket = 1;
   bool stop = false;
   std::thread worker;
   // statistics since the last reset
-  uint64_t submitted = 0, completed = 0, failed = 0, rejected = 0, batches = 0;
+  uint64_t submitted = 0, completed = 0, failed = 0, rejected = 0, batches = 0, retried = 0;
   uint64_t closest = 0, anyhit = 0, rays0 = 0;
   double stats_t0 = 0, busy_ms = 0;
   std::vector<double> latencies;
@@ -94,15 +114,48 @@ static double now_ms(const rr_server* sv) {
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// worst-case arena bytes of a batch: workspace plus device images of host outputs
-static size_t batch_bytes(const std::vector<const Request*>& b, WsLayout* L_out) {
+// arena bytes of a batch (requests of one scene): workspace plus device
+// images of host outputs.  The workspace is sized by the scene's growth
+// estimate when there is one and no request asks for the worst case
+// (*estimated says which), else for the worst-case tree.
+static size_t batch_bytes(const rr_server* sv, const std::vector<const Request*>& b, WsLayout* L_out,
+                          bool* estimated) {
   std::vector<rr_sensor_params> ps(b.size());
   size_t img = 0;
+  bool est = sv != nullptr && !b.empty();
   for (size_t i = 0; i < b.size(); ++i) {
     ps[i] = b[i]->params;
     if (!b[i]->out_on_device) img += align256(b[i]->image_bytes);
+    if (b[i]->worst) est = false;
   }
-  const WsLayout L = plan_workspace(ps.data(), (uint32_t)ps.size(), ~uint64_t(0));
+  const Growth* g = nullptr;
+  if (est && sv->cfg.admission == RR_ADMIT_WORST_CASE) est = false;
+  if (est) {
+    auto it = sv->growth.find(b[0]->scene);
+    if (it == sv->growth.end() || it->second.depth == 0) est = false;
+    else g = &it->second;
+  }
+  WsLayout L;
+  if (est) {
+    const double f = sv->cfg.estimate_factor;
+    double qe = 0.0, re = 0.0;
+    for (const Request* r : b) {
+      double qmax = 0.0, rsum = 0.0, q = 1.0, rr_ = 2.0;
+      for (uint32_t k = 0; k < r->params.max_bounces && k <= RR_MAX_BOUNCES; ++k) {
+        // a bounce the scene has not reached yet: twice the previous one
+        q = k < g->depth ? g->q[k] : 2.0 * q;
+        rr_ = k < g->depth ? g->r[k] : 2.0 * rr_;
+        qmax = std::max(qmax, q);
+        rsum += rr_;
+      }
+      qe += (double)r->rays0 * qmax;
+      re += (double)r->rays0 * rsum;
+    }
+    L = plan_workspace_caps(ps.data(), (uint32_t)ps.size(), (uint64_t)(f * qe) + 1, (uint64_t)(f * re) + 1);
+  } else {
+    L = plan_workspace(ps.data(), (uint32_t)ps.size(), ~uint64_t(0));
+  }
+  if (estimated) *estimated = est;
   if (L_out) *L_out = L;
   return align256(L.total) + img;
 }
@@ -113,6 +166,33 @@ static void finish_slot(rr_server* sv, Slot& sl) {
   const double t = now_ms(sv);
   sv->closest += sl.ctx.h_ctr->stat_closest - sl.closest0;
   sv->anyhit += sl.ctx.h_ctr->stat_anyhit - sl.anyhit0;
+  const rr_scene* scene = sl.batch.empty() ? nullptr : sv->reqs[sl.batch.front()].scene;
+  if (status == RR_OK && scene && sl.n0) {
+    // the batch's queue and record counts per initial ray feed the scene's estimate
+    Growth& g = sv->growth[scene];
+    const rr::ScanCounters* c = sl.ctx.h_ctr;
+    for (uint32_t k = 0; k < sl.max_bounces && k <= RR_MAX_BOUNCES; ++k) {
+      g.q[k] = std::max(g.q[k], (double)c->count[k] / (double)sl.n0);
+      const uint32_t r0 = c->rec_start[k], r1 = k < RR_MAX_BOUNCES ? c->rec_start[k + 1] : r0;
+      g.r[k] = std::max(g.r[k], (double)(r1 >= r0 ? r1 - r0 : 0u) / (double)sl.n0);
+    }
+    g.depth = std::max(g.depth, std::min<uint32_t>(sl.max_bounces, RR_MAX_BOUNCES + 1));
+  }
+  if (status == RR_ERR_CAPACITY && sl.estimated) {
+    // the batch outgrew its estimate: its requests go back to the front of the
+    // queue, in their order, to run again sized for the worst case
+    for (size_t k = sl.batch.size(); k-- > 0;) {
+      auto it = sv->reqs.find(sl.batch[k]);
+      if (it == sv->reqs.end()) continue;
+      it->second.state = RR_REQ_QUEUED;
+      it->second.worst = true;
+      sv->pending.push_front(sl.batch[k]);
+      ++sv->retried;
+    }
+    sl.batch.clear();
+    sl.images.clear();
+    return;
+  }
   for (size_t k = 0; k < sl.batch.size(); ++k) {
     auto it = sv->reqs.find(sl.batch[k]);
     if (it == sv->reqs.end()) continue;
@@ -154,7 +234,7 @@ static bool launch_slot(rr_server* sv, Slot& sl) {
     if (b.size() >= sv->cfg.max_batch_scans) break;
     if (!b.empty() && rays + r.rays0 > sv->cfg.max_batch_rays) continue;
     b.push_back(&r);
-    if (!b.empty() && batch_bytes(b, nullptr) > sl.arena_bytes) {
+    if (!b.empty() && batch_bytes(sv, b, nullptr, nullptr) > sl.arena_bytes) {
       b.pop_back();
       continue;
     }
@@ -163,7 +243,8 @@ static bool launch_slot(rr_server* sv, Slot& sl) {
   }
   if (b.empty()) return false;   // cannot happen: every request fits a slot alone (checked at submit)
   WsLayout L;
-  batch_bytes(b, &L);
+  bool estimated = false;
+  batch_bytes(sv, b, &L, &estimated);
   // device images: caller's device buffers, or arena space after the workspace
   std::vector<float*> images(b.size());
   std::vector<rr_pose> poses(b.size());
@@ -211,6 +292,10 @@ static bool launch_slot(rr_server* sv, Slot& sl) {
   }
   sl.batch = tickets;
   sl.images = images;
+  sl.estimated = estimated;
+  sl.n0 = rays;
+  sl.max_bounces = 0;
+  for (const Request* r : b) sl.max_bounces = std::max(sl.max_bounces, r->params.max_bounces);
   ++sv->batches;
   sv->rays0 += rays;
   return true;
@@ -265,6 +350,10 @@ static int serve_check(const rr_serve_config* c) {
   if (c->node_format != RR_NODES_WIDE8 && c->node_format != RR_NODES_BINARY)
     return fail(RR_ERR_INVALID_ARG, "node_format must be RR_NODES_WIDE8 or RR_NODES_BINARY");
   if (c->refill_threshold > 32) return fail(RR_ERR_INVALID_ARG, "refill_threshold must be in [0, 32]");
+  if (c->admission > RR_ADMIT_WORST_CASE)
+    return fail(RR_ERR_INVALID_ARG, "admission must be RR_ADMIT_ESTIMATE or RR_ADMIT_WORST_CASE");
+  if (!(c->estimate_factor >= 0.0f) || !std::isfinite(c->estimate_factor))
+    return fail(RR_ERR_INVALID_ARG, "estimate_factor must be finite and >= 0 (0: 2)");
   return RR_OK;
 }
 
@@ -288,6 +377,7 @@ int rr_serve_create(const rr_serve_config* config, rr_server** out) {
   if (!c.max_batch_rays) c.max_batch_rays = 4u << 20;
   if (!c.max_queue) c.max_queue = 4096;
   if (!c.refill_threshold) c.refill_threshold = 8;
+  if (c.estimate_factor == 0.0f) c.estimate_factor = 2.0f;
   if (c.memory_budget / c.slots < (uint64_t(16) << 20))
     return fail(RR_ERR_INVALID_ARG, "memory_budget must give every slot at least 16 MiB");
   rr_server* sv = new rr_server();
@@ -356,7 +446,7 @@ int rr_serve_submit(rr_server* sv, rr_scene* scene, const rr_pose* pose, const r
   r.image_bytes = (size_t)params->n_azimuth * params->n_bins * sizeof(float);
   r.rays0 = (uint64_t)params->n_azimuth * params->rays_per_beam;
   std::vector<const Request*> alone = {&r};
-  const size_t need = batch_bytes(alone, nullptr);
+  const size_t need = batch_bytes(nullptr, alone, nullptr, nullptr);   // worst case: a retry must fit
   if (need > sv->slots[0].arena_bytes)
     return fail(RR_ERR_INVALID_ARG, "the request needs " + std::to_string(need) + " bytes of worst-case scratch, " +
                                         "more than a slot's " + std::to_string(sv->slots[0].arena_bytes) +
@@ -435,6 +525,7 @@ int rr_serve_stats_get(rr_server* sv, rr_serve_stats* out, int reset) {
   out->busy_ms = sv->busy_ms;
   out->elapsed_ms = now_ms(sv) - sv->stats_t0;
   out->queued = sv->pending.size();
+  out->retried = sv->retried;
   std::vector<double> l = sv->latencies;
   if (!l.empty()) {
     std::sort(l.begin(), l.end());
@@ -450,7 +541,7 @@ int rr_serve_stats_get(rr_server* sv, rr_serve_stats* out, int reset) {
     out->latency_max_ms = l.back();
   }
   if (reset) {
-    sv->submitted = sv->completed = sv->failed = sv->rejected = sv->batches = 0;
+    sv->submitted = sv->completed = sv->failed = sv->rejected = sv->batches = sv->retried = 0;
     sv->closest = sv->anyhit = sv->rays0 = 0;
     sv->busy_ms = 0;
     sv->stats_t0 = now_ms(sv);

@@ -96,12 +96,13 @@ RR_BVH_LBVH, RR_BVH_SAH_TOP = 0, 1
 RR_ORDER_QUEUE, RR_ORDER_CELL_OCTANT = 0, 1
 WIDE_NODE_BYTES = 80
 RR_REQ_QUEUED, RR_REQ_RUNNING, RR_REQ_DONE, RR_REQ_FAILED = range(4)
+RR_ADMIT_ESTIMATE, RR_ADMIT_WORST_CASE = 0, 1
 
 
 class rr_serve_config(C.Structure):
     _fields_ = [("memory_budget", C.c_uint64), ("slots", C.c_uint32), ("max_batch_scans", C.c_uint32),
                 ("max_batch_rays", C.c_uint32), ("max_queue", C.c_uint32), ("node_format", C.c_uint32),
-                ("refill_threshold", C.c_uint32)]
+                ("refill_threshold", C.c_uint32), ("admission", C.c_uint32), ("estimate_factor", C.c_float)]
 
 
 class rr_serve_record(C.Structure):
@@ -114,7 +115,8 @@ class rr_serve_stats(C.Structure):
                 ("rejected_busy", C.c_uint64), ("batches", C.c_uint64), ("closest_queries", C.c_uint64),
                 ("anyhit_queries", C.c_uint64), ("initial_rays", C.c_uint64), ("queued", C.c_uint64),
                 ("busy_ms", C.c_double), ("elapsed_ms", C.c_double), ("latency_p50_ms", C.c_double),
-                ("latency_p99_ms", C.c_double), ("latency_mean_ms", C.c_double), ("latency_max_ms", C.c_double)]
+                ("latency_p99_ms", C.c_double), ("latency_mean_ms", C.c_double), ("latency_max_ms", C.c_double),
+                ("retried", C.c_uint64), ("reserved", C.c_uint64)]
 
 
 # every symbol declared in include/rr.h with its ctypes signature
@@ -428,7 +430,7 @@ def rr_serve_create(**config):
     if unknown:
         raise ValueError(f"unknown server config keys {sorted(unknown)}")
     _use_torch_stream()
-    c = rr_serve_config(**{k: int(v) for k, v in config.items()})
+    c = rr_serve_config(**{k: (float(v) if k == "estimate_factor" else int(v)) for k, v in config.items()})
     h = C.c_void_p()
     _check(load().rr_serve_create(C.byref(c), C.byref(h)))
     return h

@@ -187,3 +187,72 @@ def test_full_queue_refuses(two_scenes):
         assert st["completed"] == len(tickets)
     finally:
         rr.rr_serve_destroy(sv)
+
+
+def test_estimated_batch_that_overflows_is_rerun(two_scenes):
+    """Admission by the scene's growth estimate: with an estimate factor far
+    too small the second batch on a scene outgrows its workspace; the device
+    reports the overflow, the server reruns those requests sized for the
+    worst case, and each result still equals the scan alone."""
+    import torch
+    hs, base = two_scenes
+    sv = rr.rr_serve_create(slots=1, memory_budget=2 << 30, estimate_factor=0.01)
+    try:
+        p = scenes.sensor(**{**base, "rays_per_beam": 8, "max_bounces": 4, "refraction": True, "scan_id": 1})
+        pz = scenes.pose(0.3, -0.2, 0.5, yaw=0.4)
+        outs = []
+        for i in range(3):
+            q = {**p, "scan_id": 10 + i}
+            out = torch.zeros(q["n_azimuth"], q["n_bins"], device="cuda")
+            t = rr.rr_serve_submit(sv, hs[0], pz, q, out)
+            rr.rr_serve_wait(sv, t, 60_000)
+            assert rr.rr_serve_result(sv, t)["state"] == rr.RR_REQ_DONE
+            outs.append((q, out))
+        st = rr.rr_serve_stats_get(sv)
+        # the first batch seeded the estimate at worst-case size; the next ones overflowed and were rerun
+        assert st["retried"] >= 2 and st["failed"] == 0
+        for q, out in outs:
+            assert_close(out.cpu().numpy(), alone(hs[0], pz, q), f"scan {q['scan_id']}")
+    finally:
+        rr.rr_serve_destroy(sv)
+
+
+def test_estimated_admission_batches_more_requests(two_scenes):
+    """Requests queued behind a busy slot: sized by the estimate, more of
+    them share a launch sequence than under worst-case sizing with the same
+    arena, and every result equals the scan alone."""
+    import torch
+    hs, base = two_scenes
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(24):
+        p = scenes.sensor(**{**base, "rays_per_beam": 512, "max_bounces": 6, "refraction": True,
+                             "multipath": True, "scan_id": 100 + i})
+        pz = scenes.pose(float(rng.uniform(-2, 2)), float(rng.uniform(-2, 2)), 0.5, yaw=float(rng.uniform(-3, 3)))
+        reqs.append((pz, p))
+    sizes = {}
+    for admission in (rr.RR_ADMIT_WORST_CASE, rr.RR_ADMIT_ESTIMATE):
+        sv = rr.rr_serve_create(slots=1, memory_budget=6 << 30, admission=admission, max_batch_rays=64 << 20)
+        try:
+            # one request seeds the estimate
+            seed = torch.zeros(base["n_azimuth"], base["n_bins"], device="cuda")
+            t0 = rr.rr_serve_submit(sv, hs[0], reqs[0][0], reqs[0][1], seed)
+            rr.rr_serve_wait(sv, t0, 60_000)
+            rr.rr_serve_result(sv, t0)
+            rr.rr_serve_stats_get(sv, reset=True)
+            outs, tickets = [], []
+            for pz, p in reqs:
+                out = torch.zeros(p["n_azimuth"], p["n_bins"], device="cuda")
+                tickets.append(rr.rr_serve_submit(sv, hs[0], pz, p, out))
+                outs.append(out)
+            for t in tickets:
+                rr.rr_serve_wait(sv, t, 120_000)
+            sizes[admission] = [rr.rr_serve_result(sv, t)["batch_size"] for t in tickets]
+            st = rr.rr_serve_stats_get(sv)
+            assert st["completed"] == len(reqs) and st["failed"] == 0
+            if admission == rr.RR_ADMIT_ESTIMATE:
+                for (pz, p), out in zip(reqs, outs):
+                    assert_close(out.cpu().numpy(), alone(hs[0], pz, p), f"scan {p['scan_id']}")
+        finally:
+            rr.rr_serve_destroy(sv)
+    assert max(sizes[rr.RR_ADMIT_ESTIMATE]) > max(sizes[rr.RR_ADMIT_WORST_CASE]), sizes
