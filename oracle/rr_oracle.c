@@ -113,8 +113,8 @@ typedef struct {
   uint32_t az, k, path, bounce, tri, flags;
   double t, E;
   double cos_i, ret_t, ret_a;
-  double e_org, e_dir; /* float32 error estimate (standard deviations) of the segment's origin (m) and
-                          direction (rad) */
+  double e_org, e_dir; /* float32 error estimate (standard deviations) of the segment's origin (m, moved
+                          within the hit plane it starts on: the distance tolerances) and direction (rad) */
   double alpha2;       /* power attenuation constant 2 alpha (1/m) of the medium the segment crosses (0: air) */
 } orc_segment;
 
@@ -528,13 +528,16 @@ static void tri_normal(const scene_t* s, uint32_t j, double n[3]) {
 /* ERR_NRM ulps turned by (A - 1) (A the same derivative), plus ERR_REFR    */
 /* ulps.  A hit or near miss within FLAG_SIGMAS standard deviations of a    */
 /* triangle edge is a decision float32 can take the other way and flags the */
-/* ray; the parity tests take the same estimate for the hit distances.      */
+/* ray.  For the hit distances the parity tests take the same estimate with */
+/* one more term: a hit point's error across the ray moves it within the    */
+/* hit plane by that error over cos theta0, and the children start there.   */
 /* ------------------------------------------------------------------------ */
 #define ULP32 0x1p-24
 #define ERR_DIR0 2.0     /* ulps of the generated direction */
 #define ERR_REFL 2.0     /* ulps a reflection adds */
 #define ERR_REFR 1.0     /* ulps a refraction adds besides the Snell term */
 #define ERR_NRM 1.5      /* ulps of a triangle normal computed from float vertices */
+#define ERR_T 1.0        /* ulps of t from the watertight test's division */
 #define FLAG_SIGMAS 4.0  /* standard deviations of a hit point that flag an edge */
 
 /* one float32 ulp of x (the spacing of floats around |x|, at least 2^-149) */
@@ -550,7 +553,7 @@ static double ulp32(double x) {
 static double point_err(double e_org, double e_dir, double t, const double o[3], const double d[3]) {
   double m = 0.0;
   for (int i = 0; i < 3; ++i) m = fmax(m, fabs(o[i] + t * d[i]));
-  const double r = 0.5 * ulp32(m), u = ulp32(t);
+  const double r = 0.5 * ulp32(m), u = ERR_T * ulp32(t);
   return sqrt(e_org * e_org + t * t * e_dir * e_dir + r * r + u * u);
 }
 
@@ -571,8 +574,9 @@ typedef struct {
 
 /* Is the plane point of triangle (v0, v1, v2) with barycentrics (b0, b1, b2)
    within barycentric margin FLAG_BARY of an edge, or closer to an edge than
-   `err` metres (inside or outside)?  The signed distance to the edge
-   opposite vertex i is b_i times the altitude over that edge. */
+   `err` metres (inside or outside; capped at FLAG_EMAX)?  The signed
+   distance to the edge opposite vertex i is b_i times the altitude over
+   that edge. */
 static int near_edge(const double v0[3], const double v1[3], const double v2[3], double b0, double b1, double b2,
                      double m, double err) {
   if (m > -FLAG_BARY && m < FLAG_BARY) return 1;
@@ -583,6 +587,7 @@ static int near_edge(const double v0[3], const double v1[3], const double v2[3],
   sub3(v2, v1, e3);
   cross3(e1, e2, c);
   const double twice_area = norm3(c);
+  err = fmin(err, FLAG_EMAX);
   const double s0 = b0 * twice_area / norm3(e3), s1 = b1 * twice_area / norm3(e2), s2 = b2 * twice_area / norm3(e1);
   double smin = s0 < s1 ? s0 : s1;
   if (s2 < smin) smin = s2;
@@ -612,7 +617,7 @@ static void hit_consider(const scene_t* s, uint32_t j, const double o[3], const 
   double m = b0 < b1 ? b0 : b1;
   if (b2 < m) m = b2;
   if (t > t_min - FLAG_TABS && t < a->t_edge &&
-      near_edge(v0, v1, v2, b0, b1, b2, m, fmin(FLAG_SIGMAS * point_err(a->e_org, a->e_dir, t, o, d), FLAG_EMAX)))
+      near_edge(v0, v1, v2, b0, b1, b2, m, FLAG_SIGMAS * point_err(a->e_org, a->e_dir, t, o, d)))
     a->t_edge = t;
   if (m >= 0.0 && fabs(t - t_min) < FLAG_TABS) a->near_tmin = 1;
   if (m < 0.0 || !(t > t_min)) return;
@@ -679,7 +684,7 @@ int orc_closest(const float* vertices, uint32_t n_vertices, const uint32_t* tria
 static double seg_err(double e_org, double t, double dist, const double p[3], const double dir[3]) {
   double m = 0.0;
   for (int i = 0; i < 3; ++i) m = fmax(m, fabs(p[i] + t * dir[i]));
-  const double e = e_org * fmax(1.0 - t / dist, 0.0), r = 0.5 * ulp32(m), u = ulp32(t);
+  const double e = e_org * fmax(1.0 - t / dist, 0.0), r = 0.5 * ulp32(m), u = ERR_T * ulp32(t);
   return sqrt(e * e + r * r + u * u);
 }
 
@@ -696,7 +701,7 @@ static void occ_consider(const scene_t* s, uint32_t j, const double p[3], const 
   int inside_t = t > t_min && t < dist;
   int near_t = fabs(t - t_min) < FLAG_TABS || fabs(t - dist) < FLAG_TREL * dist;
   if ((inside_t || near_t) &&
-      near_edge(v0, v1, v2, b0, b1, b2, m, fmin(FLAG_SIGMAS * seg_err(e_org, t, dist, p, dir), FLAG_EMAX)))
+      near_edge(v0, v1, v2, b0, b1, b2, m, FLAG_SIGMAS * seg_err(e_org, t, dist, p, dir)))
     *flag = 1;
   if (m >= 0.0 && near_t) *flag = 1;
   if (m >= 0.0 && inside_t) *occ = 1;
@@ -1134,6 +1139,7 @@ typedef struct {
   int32_t medium;
   uint32_t prev, path, bounce;
   double e_org, e_dir; /* float32 error estimate (see above) */
+  double e_tol;        /* the origin's error for the distance tolerances (moved within hit planes) */
 } oray_t;
 
 typedef struct {
@@ -1269,13 +1275,14 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
     root.path = 0;
     root.bounce = 0;
     root.e_org = 0.0;
+    root.e_tol = 0.0;
     root.e_dir = ERR_DIR0 * ULP32;
     stack[sp++] = root;
 
     while (sp > 0) {
       oray_t ray = stack[--sp];
       orc_segment seg = {a, k, ray.path, ray.bounce, ORC_NONE, 0u, INFINITY, ray.E, 0.0, 0.0, 0.0,
-                         ray.e_org, ray.e_dir, 2.0 * alpha_np(s, ray.medium, p->freq_hz)};
+                         ray.e_tol, ray.e_dir, 2.0 * alpha_np(s, ray.medium, p->freq_hz)};
       double n_cur = refr_index(s, ray.medium);
       double t_lim = (r_lim - ray.L) / n_cur; /* past it no return can reach the image */
       hit_t h = closest_hit(s, ray.o, ray.d, p->t_min, ray.prev, ray.e_org, ray.e_dir);
@@ -1293,6 +1300,16 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
       seg.t = h.t;
       const double e_hit = point_err(ray.e_org, ray.e_dir, h.t, ray.o, ray.d);
       if (FLAG_SIGMAS * e_hit > FLAG_EMAX) seg.flags |= SEG_ERR;
+      /* for the distance tolerances: the error of the hit point within the
+         hit plane, where the children start -- a ray meeting the plane at
+         cos theta0 moves its hit point along the plane by its error across
+         the ray over cos theta0 */
+      double e_tol_hit;
+      {
+        double nh[3];
+        tri_normal(s, h.tri, nh);
+        e_tol_hit = point_err(ray.e_tol, ray.e_dir, h.t, ray.o, ray.d) / fmax(fabs(dot3(ray.d, nh)), 1e-6);
+      }
 
       double pt[3];
       for (int i = 0; i < 3; ++i) pt[i] = ray.o[i] + h.t * ray.d[i];
@@ -1475,6 +1492,7 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
         c.path = (ray.path << 1) | 1u;
         c.bounce = ray.bounce + 1;
         c.e_org = e_hit;
+        c.e_tol = e_tol_hit;
         c.e_dir = e_refr_dir;
         stack[sp++] = c;
       }
@@ -1489,6 +1507,7 @@ static void trace_column(const scene_t* s, const orc_params* p, const orc_pose* 
         c.path = ray.path << 1;
         c.bounce = ray.bounce + 1;
         c.e_org = e_hit;
+        c.e_tol = e_tol_hit;
         c.e_dir = sqrt(ray.e_dir * ray.e_dir + ERR_REFL * ERR_REFL * ULP32 * ULP32);
         stack[sp++] = c;
       }

@@ -35,6 +35,7 @@ struct Need {
   uint64_t r = 0;      // return records: sum of 2 n0 (2^bounces - 1)
   uint64_t tmp = 0;    // floats of the images before the azimuth pattern
   uint64_t n = 0;      // scans
+  bool order = false;  // room for the closest-hit query order (rr_batch_config.query_order)
   // a scan of n_az columns (all azimuths of p, or a range of them)
   void add(const rr_sensor_params& p, uint32_t n_az) {
     const uint64_t s0 = (uint64_t)n_az * p.rays_per_beam;
@@ -49,12 +50,17 @@ struct Need {
 
 static size_t desc_bytes(uint64_t n) { return (size_t)n * sizeof(ScanDesc) + 2 * (size_t)(n + 1) * sizeof(uint32_t); }
 
+static uint64_t order_bytes(uint64_t q, const Need& nd) {
+  return nd.order ? align256(q * 2) + align256(q * 4) +
+                        align256((RR_MAX_BOUNCES + 1) * (uint64_t)rr::kOrderBuckets * 4) +
+                        align256((uint64_t)rr::kOrderBuckets * 4)
+                  : 0;
+}
+
 static uint64_t bytes_of(uint64_t q, uint64_t r, const Need& nd) {
   const uint64_t tiles = (q + 255) / 256 + 1;
   return align256(q * sizeof(rr::RayRec)) * 2 + align256(q * sizeof(rr::HitRec)) + align256(r * 8) +
-         align256(tiles * 8) + align256(nd.tmp * 4) + align256(desc_bytes(nd.n)) + align256(q * 2) +
-         align256(q * 4) + align256((RR_MAX_BOUNCES + 1) * (uint64_t)rr::kOrderBuckets * 4) +
-         align256((uint64_t)rr::kOrderBuckets * 4);
+         align256(tiles * 8) + align256(nd.tmp * 4) + align256(desc_bytes(nd.n)) + order_bytes(q, nd);
 }
 
 static WsLayout layout_of(const Need& nd, uint64_t limit) {
@@ -93,20 +99,23 @@ static WsLayout layout_of(const Need& nd, uint64_t limit) {
   off += align256(desc_bytes(nd.n));
   // query order: keys, permutation, per-bounce bucket counts, bucket cursors
   L.off_order = off;
-  off += align256((size_t)q * 2) + align256((size_t)q * 4) +
-         align256((size_t)(RR_MAX_BOUNCES + 1) * rr::kOrderBuckets * 4) + align256((size_t)rr::kOrderBuckets * 4);
+  L.order = nd.order;
+  off += order_bytes(q, nd);
   L.total = off;
   return L;
 }
 
-WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit, const uint32_t* az_count) {
+WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit, const uint32_t* az_count,
+                        bool order) {
   Need nd;
+  nd.order = order;
   for (uint32_t i = 0; i < n; ++i) nd.add(ps[i], az_count ? az_count[i] : ps[i].n_azimuth);
   return layout_of(nd, limit);
 }
 
-WsLayout plan_workspace_caps(const rr_sensor_params* ps, uint32_t n, uint64_t q_cap, uint64_t r_cap) {
+WsLayout plan_workspace_caps(const rr_sensor_params* ps, uint32_t n, uint64_t q_cap, uint64_t r_cap, bool order) {
   Need nd;
+  nd.order = order;
   for (uint32_t i = 0; i < n; ++i) nd.add(ps[i]);
   Need e = nd;
   e.q = std::min(nd.q, std::max(q_cap, nd.n0));
@@ -121,6 +130,7 @@ std::vector<Group> plan_groups(const rr_sensor_params* ps, uint32_t n, const Lau
   uint32_t i = 0;
   while (i < n) {
     Need nd;
+    nd.order = cfg.order == RR_ORDER_CELL_OCTANT;
     uint64_t cols = 0;
     uint32_t j = i;
     while (j < n) {
@@ -425,7 +435,7 @@ int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor
   a.tile_status = (unsigned long long*)(w + L.off_status);
   a.ctr = x->d_ctr;
   a.image_tmp = pattern ? (float*)(w + L.off_tmp) : nullptr;
-  if (cfg.order == RR_ORDER_CELL_OCTANT && maxb > 1) {
+  if (cfg.order == RR_ORDER_CELL_OCTANT && L.order && maxb > 1) {
     char* o = w + L.off_order;
     a.order_key = (uint16_t*)o;
     o += align256((size_t)L.ray_cap * 2);
@@ -506,7 +516,7 @@ int scan_split(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, floa
     const uint32_t range[2] = {a0, a1 - a0};
     ExecCtx* x = k == 0 ? &s->main : &s->split[k - 1].ctx;
     cudaStream_t sk = k == 0 ? st : s->split[k - 1].stream;
-    const WsLayout L = plan_workspace(p, 1, s->cfg.ws_limit, &range[1]);
+    const WsLayout L = plan_workspace(p, 1, s->cfg.ws_limit, &range[1], s->cfg.order == RR_ORDER_CELL_OCTANT);
     int rc = ensure_workspace(x, L.total, sk);
     if (rc != RR_OK) return rc;
     float* const images[1] = {image};

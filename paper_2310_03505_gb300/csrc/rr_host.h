@@ -184,6 +184,7 @@ struct WsLayout {
   size_t off_rays0, off_rays1, off_hits, off_recs, off_status, off_tmp, off_desc, off_order, total;
   size_t tmp_floats;
   bool clamped;
+  bool order;   // holds the closest-hit query order buffers
 };
 struct DebugOut {
   rr_segment* segs = nullptr;
@@ -203,10 +204,12 @@ int check_params(const rr_pose* pose, const rr_sensor_params* p);
 // RR_ERR_INVALID_ARG unless the current device is the scene's (who: caller name for the message)
 int check_device(const rr_scene* s, const char* who);
 // worst-case workspace of scans ps[0..n) traced together, clamped to limit
-WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit, const uint32_t* az_count = nullptr);
+WsLayout plan_workspace(const rr_sensor_params* ps, uint32_t n, uint64_t limit, const uint32_t* az_count = nullptr,
+                        bool order = false);
 // the same with the queues and records sized to given capacities (an estimate of the
 // ray tree; clamped = smaller than the worst case), never below the initial rays
-WsLayout plan_workspace_caps(const rr_sensor_params* ps, uint32_t n, uint64_t q_cap, uint64_t r_cap);
+WsLayout plan_workspace_caps(const rr_sensor_params* ps, uint32_t n, uint64_t q_cap, uint64_t r_cap,
+                            bool order = false);
 // split n scans into launch sequences that respect the limits of cfg
 std::vector<Group> plan_groups(const rr_sensor_params* ps, uint32_t n, const LaunchCfg& cfg);
 // queue the launch sequence of scans poses/ps[0..n) writing images[i]

@@ -233,15 +233,6 @@ __device__ __forceinline__ bool trav_tri(Trav& s, const ScanArgs& a, uint32_t j,
   return false;
 }
 
-// two float4 of read-only memory with one 256-bit load (p 32-byte aligned):
-// a node is two such loads instead of four 128-bit ones, half the load
-// instructions and L1 wavefronts of the divergent node fetches
-__device__ __forceinline__ void ldg256(const float4* p, float4& a, float4& b) {
-  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-      : "l"(p));
-}
-
 // one step over the binary LBVH (both children tested, nearer first)
 template <bool kAny>
 __device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const ScanArgs& a, uint32_t& n_nodes,
@@ -252,9 +243,7 @@ __device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const Scan
     ++s.visits;   // bounded where the query loop looks at its lanes
     const float3 o = s.w.o, id = s.id;
     const float4* np = a.nodes + 4 * (size_t)node;
-    float4 n0, n1, n2, n3;   // 64-byte nodes from a 256-byte aligned allocation
-    ldg256(np, n0, n1);
-    ldg256(np + 2, n2, n3);
+    const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
     // child 0
     float t0 = (n0.x - o.x) * id.x, t1 = (n0.y - o.x) * id.x;
     float lo0 = fminf(t0, t1), hi0 = fmaxf(t0, t1);
@@ -747,27 +736,32 @@ __global__ void __launch_bounds__(1024) k_order_scan(ScanArgs a, uint32_t bounce
   a.order_off[2 * t + 1] = excl + c0;
 }
 
-// the permutation: every queued ray of the bounce to the next free position
-// of its bucket (rays of one bucket in any order: every query's result is
-// independent of the order)
-__global__ void k_order_scatter(ScanArgs a, uint32_t bounce) {
+// the permutation: every queued ray of the bounce to a position of its
+// bucket.  A block takes a contiguous chunk of the queue, counts its keys in
+// shared memory, reserves each bucket's share with one atomic and places its
+// rays (in any order within a bucket: every query's result is independent
+// of the order)
+__global__ void __launch_bounds__(256) k_order_place(ScanArgs a, uint32_t bounce) {
+  __shared__ uint32_t s_cnt[kOrderBuckets];
+  __shared__ uint32_t s_base[kOrderBuckets];
   const uint32_t n = min(a.ctr->count[bounce], a.ray_cap);
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
-    const uint32_t i = i0 + threadIdx.x;
-    const bool has = i < n;
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, has);
-    if (has) {
-      const uint32_t key = a.order_key[i] & (kOrderBuckets - 1u);
-      const uint32_t peers = __match_any_sync(m, key);
-      const uint32_t leader = __ffs(peers) - 1u;
-      uint32_t base = 0;
-      if (lane == leader) base = atomicAdd(&a.order_off[key], (uint32_t)__popc(peers));
-      base = __shfl_sync(peers, base, leader);
-      const uint32_t pos = base + __popc(peers & ((1u << lane) - 1u));
-      if (pos < a.ray_cap) a.order_perm[pos] = i;
-    }
+  const uint32_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const uint32_t i0 = blockIdx.x * chunk, i1 = min(i0 + chunk, n);
+  for (uint32_t j = threadIdx.x; j < kOrderBuckets; j += blockDim.x) s_cnt[j] = 0u;
+  __syncthreads();
+  for (uint32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+    atomicAdd(&s_cnt[a.order_key[i] & (kOrderBuckets - 1u)], 1u);
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < kOrderBuckets; j += blockDim.x) {
+    const uint32_t c = s_cnt[j];
+    s_base[j] = c ? atomicAdd(&a.order_off[j], c) : 0u;
+    s_cnt[j] = 0u;
+  }
+  __syncthreads();
+  for (uint32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const uint32_t key = a.order_key[i] & (kOrderBuckets - 1u);
+    const uint32_t pos = s_base[key] + atomicAdd(&s_cnt[key], 1u);
+    if (pos < a.ray_cap) a.order_perm[pos] = i;
   }
 }
 
@@ -785,6 +779,7 @@ __global__ void __launch_bounds__(kShadeBlock, 3) k_shade(ScanArgs a, uint32_t b
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wsum[kShadeBlock / 32];
   __shared__ uint2 s_excl;
+  extern __shared__ uint32_t s_hist[];   // [kOrderBuckets] children per order bucket (query order on only)
   const uint32_t n = a.ctr->count[bounce];
   const uint32_t tiles = (n + kShadeBlock - 1) / kShadeBlock;
   const uint32_t rec0 = a.ctr->rec_start[bounce];
@@ -801,6 +796,9 @@ __global__ void __launch_bounds__(kShadeBlock, 3) k_shade(ScanArgs a, uint32_t b
     }
     return;
   }
+  const bool counting = a.order_key != nullptr && bounce + 1 < a.max_bounces;
+  if (counting)
+    for (uint32_t j = threadIdx.x; j < kOrderBuckets; j += kShadeBlock) s_hist[j] = 0u;
   while (true) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctr->shade_ticket[bounce], 1u);
     __syncthreads();
@@ -997,17 +995,13 @@ __global__ void __launch_bounds__(kShadeBlock, 3) k_shade(ScanArgs a, uint32_t b
       if (pos < a.ray_cap) qout[pos] = kid[c];
     }
     if (a.order_key != nullptr && bounce + 1 < a.max_bounces) {
-      // order buckets of the children, counted with one atomic per bucket and warp
-      for (uint32_t c = 0; c < 2u; ++c) {
+      // order buckets of the children, counted in the block's histogram
+      for (uint32_t c = 0; c < nk; ++c) {
         const uint32_t pos = kbase + c;
-        const bool has = c < nk && pos < a.ray_cap;
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, has);
-        if (has) {
+        if (pos < a.ray_cap) {
           const uint32_t key = order_key(a, kid[c]);
           a.order_key[pos] = (uint16_t)key;
-          const uint32_t peers = __match_any_sync(m, key);
-          if (lane == __ffs(peers) - 1)
-            atomicAdd(&a.order_hist[(bounce + 1) * kOrderBuckets + key], (uint32_t)__popc(peers));
+          atomicAdd(&s_hist[key], 1u);
         }
       }
     }
@@ -1036,6 +1030,13 @@ __global__ void __launch_bounds__(kShadeBlock, 3) k_shade(ScanArgs a, uint32_t b
       cn->stat_returns += (unsigned long long)recs;
     }
     __syncthreads();
+  }
+  // the block's bucket counts into the bounce's histogram (the loop ended
+  // with a barrier, so every count is in)
+  if (counting) {
+    uint32_t* h = a.order_hist + (size_t)(bounce + 1) * kOrderBuckets;
+    for (uint32_t j = threadIdx.x; j < kOrderBuckets; j += kShadeBlock)
+      if (s_hist[j]) atomicAdd(&h[j], s_hist[j]);
   }
 }
 
@@ -1135,13 +1136,13 @@ cudaError_t launch_vis_prep(const ScanArgs& a, uint32_t bounce, cudaStream_t st)
 cudaError_t launch_order(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
   init_dims();
   k_order_scan<<<1, 1024, 0, st>>>(a, bounce);
-  k_order_scatter<<<g_num_sms * 4, 256, 0, st>>>(a, bounce);
+  k_order_place<<<g_num_sms * 4, 256, 0, st>>>(a, bounce);
   return cudaGetLastError();
 }
 
 cudaError_t launch_shade(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
   init_dims();
-  k_shade<<<g_num_sms * g_shade_occ, kShadeBlock, 0, st>>>(a, bounce);
+  k_shade<<<g_num_sms * g_shade_occ, kShadeBlock, a.order_key ? kOrderBuckets * sizeof(uint32_t) : 0, st>>>(a, bounce);
   return cudaGetLastError();
 }
 

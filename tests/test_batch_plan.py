@@ -32,10 +32,7 @@ def worst_case_bytes(ps):
     tmp = sum(p["n_azimuth"] * p["n_bins"] for p in ps if p["az_pattern_sigma"] > 0)
     tiles = (q + 255) // 256 + 1
     desc = len(ps) * 160 + 2 * (len(ps) + 1) * 4
-    # query order: a 2-byte bucket and a 4-byte permutation entry per queued
-    # ray, bucket counts of every bounce (17 x 2048) and bucket cursors (2048)
-    order = a256(q * 2) + a256(q * 4) + a256(17 * 2048 * 4) + a256(2048 * 4)
-    return 2 * a256(q * 48) + a256(q * 16) + a256(r * 8) + a256(tiles * 8) + a256(tmp * 4) + a256(desc) + order
+    return 2 * a256(q * 48) + a256(q * 16) + a256(r * 8) + a256(tiles * 8) + a256(tmp * 4) + a256(desc)
 
 
 def test_empty_request(lib):
