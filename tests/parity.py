@@ -10,10 +10,12 @@ Tolerances (the parity contract):
     estimate of the segment (its origin's e_org and direction's e_dir, which
     it carries along the path: the rounding of every hit point, reflection
     and refraction), combined with half an ulp of the scene's largest
-    coordinate and an ulp of t.  A full-size test compares about a million
-    segments, so the bound must hold far out in the tail: K_SIG = 8 (a
-    Gaussian exceeds 8 standard deviations with probability 1e-15; the
-    error terms are sums of roundings, not exactly Gaussian);
+    coordinate and an ulp of t, and, for a segment that starts on an
+    earlier hit, that hit point's error moved within its plane (its error
+    across the ray over the cosine of its incidence).  K_SIG = 4 is the
+    oracle's edge-flag threshold (FLAG_SIGMAS); over the full campus scan
+    and 4,000 city rays (1.4M segments) the largest GPU deviation measured
+    1.7 of these standard deviations, the 99.99th percentile 1.1;
   * the distance along the path from the sensor to every hit (the sum of
     the segment lengths, what the radar's range measures) agrees within
     1e-5 relative plus the sum of those per-segment terms along the path;
@@ -37,7 +39,7 @@ from paper_2310_03505_gb300 import rr
 
 T_REL = 1e-5
 IMG_REL = 1e-3
-K_SIG = 8.0
+K_SIG = 4.0
 TALLY_REL = 1.6e-5
 FLAG_BITS = {"EDGE": 1, "TMIN": 2, "TIE": 4, "TLIM": 8, "TIR": 16, "GRAZE": 32, "RMAX": 64, "VIS": 128,
              "EMIN": 256, "SNELL": 512, "TALLY": 1024, "ERR": 2048}
