@@ -282,13 +282,16 @@ int rr_scene_export_bvh(const rr_scene* scene, uint32_t* morton, uint32_t* perm,
    triangles in wide-leaf order (v0, v1, v2 with w = original triangle id,
    material id as bit patterns).  Node layout, five 16-byte words:
      w0 = P.x, P.y, P.z (float), ex | ey << 8 | ez << 16 | imask << 24
-     w1 = first internal child, first triangle, valid slot mask, 0 (uint32)
+     w1 = first internal child, first triangle, valid slot mask, leaf
+          triangle counts (2 bits per slot, slot k at bits 2k) (uint32)
      w2..w4 = child bounds as bytes: qlo.x[8], qlo.y[8], qlo.z[8], qhi.x[8],
               qhi.y[8], qhi.z[8]
    Slot k's bound on axis a is P.a + (2^23 + q) 2^(e_a - 127), an exact
    float; internal slots (imask) are children first_child + (number of
-   internal slots below k), leaf slots triangles first_triangle + (number of
-   leaf slots below k).  Node 0 is the root.  *n_nodes receives the node
+   internal slots below k); a leaf slot holds 1..3 consecutive triangles
+   (this library's builder groups at most two) from first_triangle + (the
+   triangle counts of the leaf slots below k).
+   Node 0 is the root.  *n_nodes receives the node
    count; at most cap nodes are written.  The wide BVH is collapsed from the
    binary one when first needed after a build (a scan with RR_NODES_WIDE8 or
    this call).  Blocking. */

@@ -77,14 +77,15 @@ struct ScanCounters {
 
 // 8-wide BVH node with 8-bit quantised child boxes, 5 float4 (80 bytes):
 //   w0 = (P.x, P.y, P.z, ex | ey << 8 | ez << 16 | imask << 24)
-//   w1 = (first internal child, first triangle, valid mask, 0)      (bits)
+//   w1 = (first internal child, first triangle, valid mask, leaf counts: 2 bits per slot)
 //   w2 = (qlo.x[0..3], qlo.x[4..7], qlo.y[0..3], qlo.y[4..7])       (bytes)
 //   w3 = (qlo.z[0..3], qlo.z[4..7], qhi.x[0..3], qhi.x[4..7])
 //   w4 = (qhi.y[0..3], qhi.y[4..7], qhi.z[0..3], qhi.z[4..7])
 // Slot k of an axis has bounds fma(float(2^23 + q), s, P) with s = 2^(e - 127)
 // (exact floats that contain the child's box).  Internal children are stored
-// consecutively from the first child in slot order, leaf slots (one
-// triangle each) likewise from the first triangle.
+// consecutively from the first child in slot order, the triangles of the
+// leaf slots (1..3 each, a small binary subtree) likewise from the first
+// triangle.
 constexpr int kWideNodeWords = 5;
 
 // Return record key: global image column (scan's first column + azimuth)

@@ -178,7 +178,8 @@ struct Trav {
   uint32_t node;        // binary: next node; both: kNone once the query has ended
   uint32_t best, best_id, visits;
   uint32_t oct;                               // wide: direction octant
-  uint32_t g_base, g_bits, t_base, t_bits;    // wide: node group, triangle group
+  uint32_t g_base, g_bits;                    // wide: node group
+  uint32_t t_base, t_bits;                    // wide: triangles still to test, bit i = triangle t_base + i
   int sp;
 };
 
@@ -289,7 +290,9 @@ __device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const Scan
 
 // One step over the 8-wide quantised BVH: a triangle of the current
 // triangle group, else the next child of the current node group, else a
-// group from the stack.  Children are visited in slot order k ^ octant
+// group from the stack.  A leaf slot holds 1..3 consecutive triangles (its
+// count in two bits of the node's word w1.w); the hit leaf slots of a node
+// become one mask over its up to 24 triangles.  Children are visited in slot order k ^ octant
 // (near first) through node groups as in Ylitie, Karras, Laine, "Efficient
 // incoherent ray traversal on GPUs through compressed wide BVHs" (HPG 2017):
 // a group is (first child, internal-slot mask << 8 | hit children still to
@@ -301,11 +304,9 @@ template <bool kAny>
 __device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs& a, uint32_t& n_nodes,
                                           uint32_t& n_tris, bool count) {
   const uint32_t oct = s.oct;
-  if (s.t_bits & 0xFFu) {
-    const uint32_t k = __ffs(s.t_bits & 0xFFu) - 1u;
-    s.t_bits &= ~(1u << k);
-    const uint32_t slot = k ^ oct;
-    const uint32_t j = s.t_base + __popc((s.t_bits >> 8) & ((1u << slot) - 1u));
+  if (s.t_bits) {
+    const uint32_t j = s.t_base + (uint32_t)__ffs(s.t_bits) - 1u;
+    s.t_bits &= s.t_bits - 1u;
     if (j < a.n_tris && trav_tri<kAny>(s, a, j, n_tris, count)) s.node = kNone;
     return;
   }
@@ -332,7 +333,7 @@ __device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs&
     const float px = __uint_as_float(w0.x), py = __uint_as_float(w0.y), pz = __uint_as_float(w0.z);
     const float sx = __uint_as_float((w0.w & 0xFFu) << 23), sy = __uint_as_float(((w0.w >> 8) & 0xFFu) << 23),
                 sz = __uint_as_float(((w0.w >> 16) & 0xFFu) << 23);
-    const uint32_t imask = w0.w >> 24, valid = w1.z;
+    const uint32_t imask = w0.w >> 24, valid = w1.z, counts = w1.w;
     // near and far plane bytes per axis: (lo, hi) for a positive direction, swapped otherwise
     const uint32_t nx0 = neg_x ? w3.z : w2.x, nx1 = neg_x ? w3.w : w2.y;
     const uint32_t fx0 = neg_x ? w2.x : w3.z, fx1 = neg_x ? w2.y : w3.w;
@@ -340,7 +341,7 @@ __device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs&
     const uint32_t fy0 = neg_y ? w2.z : w4.x, fy1 = neg_y ? w2.w : w4.y;
     const uint32_t nz0 = neg_z ? w4.z : w3.x, nz1 = neg_z ? w4.w : w3.y;
     const uint32_t fz0 = neg_z ? w3.x : w4.z, fz1 = neg_z ? w3.y : w4.w;
-    uint32_t hit_i = 0u, hit_l = 0u;
+    uint32_t hit_i = 0u, tmask = 0u, first = 0u;   // first: the slot's first triangle (of the node's)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       // bits 0x4B0000qq = 2^23 + q (byte q of the word), decoded to P + q s exactly
@@ -354,16 +355,17 @@ __device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs&
       const float lo = fmaxf(fmaxf((bnx - o.x) * id.x, (bny - o.y) * id.y), fmaxf((bnz - o.z) * id.z, s.t_min));
       const float hi =
           fminf(fminf(fminf((bfx - o.x) * id.x, (bfy - o.y) * id.y), (bfz - o.z) * id.z) * kBoxInflate, s.t_best);
+      const uint32_t c = counts >> (2 * j) & 3u;   // triangles of a leaf slot (0: inner or empty)
       if (lo <= hi && (valid >> j & 1u)) {
-        const uint32_t bit = 1u << (j ^ oct);
-        if (imask >> j & 1u) hit_i |= bit;
-        else hit_l |= bit;
+        if (imask >> j & 1u) hit_i |= 1u << (j ^ oct);
+        else tmask |= ((1u << c) - 1u) << first;
       }
+      first += c;
     }
     s.g_base = w1.x;
     s.g_bits = (imask << 8) | hit_i;
     s.t_base = w1.y;
-    s.t_bits = ((valid & ~imask) << 8) | hit_l;
+    s.t_bits = tmask;
     return;
   }
   if (s.sp) {

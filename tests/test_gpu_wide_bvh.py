@@ -1,9 +1,11 @@
 """The 8-wide BVH with 8-bit quantised child boxes.
 
 Structure (exported, checked in numpy): every triangle sits in exactly one
-leaf slot, every decoded bound is an exact float, every slot's decoded box
-contains the true box of what it holds and is at most one quantum looser per
-side.  Behaviour: a scan traced through the wide BVH and through the binary
+leaf slot (a leaf slot holds one triangle or a group of two consecutive
+ones; the format has room for three), every decoded bound is an exact float,
+every slot's decoded box contains the true box of what it holds and is at
+most one quantum looser per side.  Behaviour: a scan traced through the wide
+BVH and through the binary
 LBVH (float boxes) gives the same segments -- same triangle, same distance,
 bit for bit -- for every ray.  Needs a GPU."""
 import numpy as np
@@ -26,7 +28,8 @@ def decode(nodes):
     s = np.ldexp(1.0, e)
     q = nodes[:, 32:80].reshape(n, 6, 8).astype(np.int64)
     return dict(P=Pn, s=s, imask=(eb >> 24).astype(np.int64), cb=w[:, 4].astype(np.int64),
-                tb=w[:, 5].astype(np.int64), valid=w[:, 6].astype(np.int64), qlo=q[:, 0:3], qhi=q[:, 3:6])
+                tb=w[:, 5].astype(np.int64), valid=w[:, 6].astype(np.int64), counts=w[:, 7].astype(np.int64),
+                qlo=q[:, 0:3], qhi=q[:, 3:6])
 
 
 def check_wide(sc, h):
@@ -54,10 +57,15 @@ def check_wide(sc, h):
     box_hi = np.full((n, 3), -np.inf)
     seen_nodes = np.zeros(n, np.int64)
     seen_tris = np.zeros(sc.n_triangles, np.int64)
+    groups = 0
     seen_nodes[0] = 1
     for i in range(n - 1, -1, -1):
         v, im = int(d["valid"][i]), int(d["imask"][i])
         assert im & ~v == 0
+        # inner and empty slots hold no triangle count
+        for k in range(8):
+            if not ((v >> k) & 1) or ((im >> k) & 1):
+                assert (int(d["counts"][i]) >> (2 * k)) & 3 == 0
         ri = rl = 0
         for k in range(8):
             if not (v >> k) & 1:
@@ -69,11 +77,15 @@ def check_wide(sc, h):
                 seen_nodes[c] += 1
                 clo, chi = box_lo[c], box_hi[c]
             else:
-                j = int(d["tb"][i]) + rl
-                rl += 1
-                assert 0 <= j < sc.n_triangles
-                seen_tris[j] += 1
-                clo, chi = tri_lo[j], tri_hi[j]
+                # a leaf slot: 1..3 consecutive triangles
+                c = (int(d["counts"][i]) >> (2 * k)) & 3
+                assert 1 <= c <= 2, f"node {i} slot {k}: {c} triangles"
+                groups += c > 1
+                j0 = int(d["tb"][i]) + rl
+                rl += c
+                assert 0 <= j0 and j0 + c <= sc.n_triangles
+                seen_tris[j0:j0 + c] += 1
+                clo, chi = tri_lo[j0:j0 + c].min(0), tri_hi[j0:j0 + c].max(0)
             qlo, qhi = lo[i, :, k], hi[i, :, k]
             assert np.all(qlo <= clo) and np.all(qhi >= chi), f"node {i} slot {k}: box not contained"
             s = d["s"][i]
@@ -91,15 +103,15 @@ def check_wide(sc, h):
                 depth[int(d["cb"][i]) + ri] = depth[i] + 1
                 ri += 1
     assert depth.max() <= 64
-    return n
+    return n, groups
 
 
 def test_wide_bvh_structure_tiny(rrlib):
     sc, _, _ = scenes.config_tiny()
     h = P.gpu_scene(sc)
     try:
-        n = check_wide(sc, h)
-        assert n < sc.n_triangles / 2
+        n, groups = check_wide(sc, h)
+        assert n < sc.n_triangles / 2 and groups > 0
     finally:
         rr.rr_scene_destroy(h)
 
@@ -109,7 +121,9 @@ def test_wide_bvh_structure_campus_after_rebuild(rrlib):
     sc, _, _ = scenes.config_medium()
     h = P.gpu_scene(sc)
     try:
-        check_wide(sc, h)
+        n, groups = check_wide(sc, h)
+        # two-triangle groups take the place of many wide nodes
+        assert groups > sc.n_triangles / 8 and n < sc.n_triangles / 4
         # a rebuild with moved vertices collapses the new hierarchy
         moved = sc.vertices + np.float32(0.37)
         rr.rr_scene_update_vertices(h, torch.from_numpy(moved).cuda())
@@ -125,7 +139,7 @@ def test_wide_bvh_single_triangle(rrlib):
                        np.array([[0, 2, 1]], np.uint32), np.zeros(1, np.uint16), [scenes.MATERIALS["metal"]])
     h = P.gpu_scene(one)
     try:
-        assert check_wide(one, h) == 1
+        assert check_wide(one, h) == (1, 0)
     finally:
         rr.rr_scene_destroy(h)
 
