@@ -348,7 +348,7 @@ int rr_scan_batch_async(rr_scene* scene, uint32_t n, const rr_pose* poses, const
                         rounded outward onto exact float bounds).
    refill_threshold     the query kernels keep their lanes busy by handing a
                         warp's idle lanes new queries once at least this many
-                        of its 32 lanes are idle (1..32; 0 = 8)
+                        of its 32 lanes are idle (1..32; 0 = 16)
    workspace_limit      bytes of scan workspace; a launch sequence is sized
                         for its worst-case ray tree (every hit spawning both
                         children) within this limit (0: 24 GiB)

@@ -584,7 +584,7 @@ static LaunchCfg cfg_from_abi(const rr_batch_config* c) {
   o.trace_blocks_per_sm = c->trace_blocks_per_sm;
   o.use_graph = c->use_graph;
   o.node_format = c->node_format;
-  o.refill = c->refill_threshold ? c->refill_threshold : 8u;
+  o.refill = c->refill_threshold ? c->refill_threshold : 16u;
   if (c->workspace_limit) o.ws_limit = c->workspace_limit;
   o.split = c->split_streams ? c->split_streams : 3u;
   o.bvh_build = c->bvh_build;

@@ -29,7 +29,7 @@ struct LaunchCfg {
   uint32_t trace_blocks_per_sm = 0;   // 0: occupancy maximum
   uint32_t use_graph = 1;             // capture each launch sequence once and replay it
   uint32_t node_format = RR_NODES_BINARY;
-  uint32_t refill = 8;                // idle lanes that trigger a refill (1..32)
+  uint32_t refill = 16;               // idle lanes that trigger a refill (1..32)
   uint32_t split = 3;                 // a single scan as this many azimuth ranges on their own streams
   uint64_t ws_limit = uint64_t(24) << 30;
   uint32_t bvh_build = RR_BVH_SAH_TOP;

@@ -376,7 +376,7 @@ int rr_serve_create(const rr_serve_config* config, rr_server** out) {
   if (!c.max_batch_scans) c.max_batch_scans = 64;
   if (!c.max_batch_rays) c.max_batch_rays = 4u << 20;
   if (!c.max_queue) c.max_queue = 4096;
-  if (!c.refill_threshold) c.refill_threshold = 8;
+  if (!c.refill_threshold) c.refill_threshold = 16;
   if (c.estimate_factor == 0.0f) c.estimate_factor = 2.0f;
   if (c.memory_budget / c.slots < (uint64_t(16) << 20))
     return fail(RR_ERR_INVALID_ARG, "memory_budget must give every slot at least 16 MiB");

@@ -401,7 +401,7 @@ def rr_batch_plan(params, config: dict | None = None):
     cfg = None
     if config is not None:
         full = dict(wavefront_rays=0, trace_block=128, trace_blocks_per_sm=0, use_graph=1, node_format=1,
-                    refill_threshold=8, workspace_limit=0, split_streams=3, bvh_build=1, query_order=0, reserved=0)
+                    refill_threshold=16, workspace_limit=0, split_streams=3, bvh_build=1, query_order=0, reserved=0)
         full.update(config)
         cfg = C.byref(rr_batch_config(*[int(full[k]) for k, _ in rr_batch_config._fields_]))
     cap = max(n, 1)
