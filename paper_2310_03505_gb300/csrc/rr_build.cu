@@ -256,6 +256,90 @@ __global__ void k_scan_single(uint32_t* __restrict__ data, uint32_t n) {
   }
 }
 
+// Exclusive scan of counter arrays too long for one block to scan in one
+// round trip (the 5M-triangle sort has 625k counters per pass): the counters
+// are split into tiles of kScanTile, 16 consecutive counters per thread;
+// k_scan_tiles_up writes each tile's sum, k_scan_single scans the sums,
+// k_scan_tiles_down scans each tile from its offset.  Three launches of about
+// one block per SM instead of one block walking the whole array.
+constexpr int kScanBlock = 256;
+constexpr uint32_t kScanTile = kScanBlock * 16u;
+// counters k_scan_single scans in one round trip (8 uint4 per thread, 1024 threads)
+constexpr uint32_t kScanSingleMax = 8u * 4u * 1024u;
+
+__host__ __device__ constexpr uint32_t scan_tiles(size_t n) { return (uint32_t)((n + kScanTile - 1) / kScanTile); }
+// words of tile sums (a multiple of 4, as k_scan_single wants)
+__host__ __device__ constexpr uint32_t scan_tile_words(size_t n) { return (scan_tiles(n) + 3u) & ~3u; }
+
+// block-wide sum of one value per thread (every thread gets the sum)
+__device__ __forceinline__ uint32_t block_sum(uint32_t x, uint32_t* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, off);
+  if (lane == 0) s_warp[warp] = x;
+  __syncthreads();
+  uint32_t t = 0;
+  for (int w = 0; w < kScanBlock / 32; ++w) t += s_warp[w];
+  return t;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_tiles_up(const uint32_t* __restrict__ data, uint32_t n4,
+                                                              uint32_t* __restrict__ tsum, uint32_t tsum_words) {
+  __shared__ uint32_t s_warp[kScanBlock / 32];
+  const uint4* d4 = reinterpret_cast<const uint4*>(data);
+  const uint32_t b4 = blockIdx.x * (kScanTile / 4u) + threadIdx.x * 4u;
+  uint32_t sum = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < 4u; ++k)
+    if (b4 + k < n4) {
+      const uint4 v = d4[b4 + k];
+      sum += v.x + v.y + v.z + v.w;
+    }
+  const uint32_t t = block_sum(sum, s_warp);
+  if (threadIdx.x == 0) tsum[blockIdx.x] = t;
+  // the padding words after the last tile's sum
+  if (blockIdx.x == 0 && gridDim.x + threadIdx.x < tsum_words) tsum[gridDim.x + threadIdx.x] = 0u;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_tiles_down(uint32_t* __restrict__ data, uint32_t n4,
+                                                                const uint32_t* __restrict__ tsum) {
+  __shared__ uint32_t s_warp[kScanBlock / 32];
+  uint4* d4 = reinterpret_cast<uint4*>(data);
+  const uint32_t b4 = blockIdx.x * (kScanTile / 4u) + threadIdx.x * 4u;
+  uint4 v[4];
+  uint32_t sum = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < 4u; ++k) {
+    v[k] = b4 + k < n4 ? d4[b4 + k] : make_uint4(0u, 0u, 0u, 0u);
+    sum += v[k].x + v[k].y + v[k].z + v[k].w;
+  }
+  // exclusive prefix of the per-thread sums within the tile
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = sum;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  uint32_t run = tsum[blockIdx.x] + x - sum;
+  for (int w = 0; w < warp; ++w) run += s_warp[w];
+#pragma unroll
+  for (uint32_t k = 0; k < 4u; ++k) {
+    if (b4 + k < n4) {
+      uint4 o;
+      o.x = run;
+      run += v[k].x;
+      o.y = run;
+      run += v[k].y;
+      o.z = run;
+      run += v[k].z;
+      o.w = run;
+      run += v[k].w;
+      d4[b4 + k] = o;
+    }
+  }
+}
+
 // stable scatter: keys of a tile are ranked in index order (round, warp, lane).
 // The tile's keys and values are loaded up front (one round trip instead of
 // one per round); lanes with the same digit are found with 8 ballots.  With
@@ -1824,7 +1908,9 @@ cudaError_t build_alloc(rr_scene* s) {
     RR_TRY(alloc((void**)&s->d_keys[k], T * sizeof(uint32_t)));
     RR_TRY(alloc((void**)&s->d_vals[k], T * sizeof(uint32_t)));
   }
-  RR_TRY(alloc((void**)&s->d_hist, (size_t)4 * 256 * (s->sort_tiles ? s->sort_tiles : 1) * sizeof(uint32_t)));
+  // the four passes' counters, then the tile sums of the multi-block counter scan
+  const size_t hist_words = (size_t)256 * (s->sort_tiles ? s->sort_tiles : 1);
+  RR_TRY(alloc((void**)&s->d_hist, (4 * hist_words + scan_tile_words(hist_words)) * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_parent, (T ? 2 * T - 1 : 1) * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_child, (T > 1 ? T - 1 : 1) * 2 * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_nbox, (T ? 2 * T - 1 : 1) * 6 * sizeof(float)));
@@ -1943,7 +2029,8 @@ cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth) {
   const int B = 256;
   const uint32_t g = (n + B - 1) / B;
   const bool sah_top = s->cfg.bvh_build == RR_BVH_SAH_TOP && n > kClusterMax;
-  s->launches += ((n > 1) ? (with_depth ? 14u : 13u) : 11u) + (sah_top ? 6u : 0u);
+  s->launches += ((n > 1) ? (with_depth ? 14u : 13u) : 11u) + (sah_top ? 6u : 0u) +
+                 ((size_t)256 * s->sort_tiles > kScanSingleMax ? 8u : 0u);   // 3 launches per pass's counter scan
   k_ingest<<<g, B, 0, st>>>(s->d_vtx, s->d_idx, s->d_mat_id, s->nv, n, s->nm, s->d_centroid, s->d_misc);
   RR_TRY(cudaGetLastError());
   // the four passes' digit counts per tile, zeroed, counted as each pass's input is written
@@ -1956,7 +2043,17 @@ cudaError_t build_lbvh(rr_scene* s, cudaStream_t st, bool with_depth) {
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 8 * pass;
     uint32_t* hist = s->d_hist + pass * hist_words;
-    k_scan_single<<<1, 1024, 0, st>>>(hist, (uint32_t)hist_words);
+    if (hist_words <= kScanSingleMax) {
+      k_scan_single<<<1, 1024, 0, st>>>(hist, (uint32_t)hist_words);
+    } else {
+      uint32_t* tsum = s->d_hist + 4 * hist_words;
+      const uint32_t nb = scan_tiles(hist_words), n4 = (uint32_t)(hist_words / 4);
+      k_scan_tiles_up<<<nb, kScanBlock, 0, st>>>(hist, n4, tsum, scan_tile_words(hist_words));
+      RR_TRY(cudaGetLastError());
+      k_scan_single<<<1, 1024, 0, st>>>(tsum, scan_tile_words(hist_words));
+      RR_TRY(cudaGetLastError());
+      k_scan_tiles_down<<<nb, kScanBlock, 0, st>>>(hist, n4, tsum);
+    }
     RR_TRY(cudaGetLastError());
     k_radix_scatter<<<s->sort_tiles, kSortBlock, 0, st>>>(s->d_keys[cur], s->d_vals[cur], s->d_keys[cur ^ 1],
                                                           s->d_vals[cur ^ 1], n, shift, s->sort_tiles, hist,

@@ -1,6 +1,7 @@
 """LBVH rows on the GPU (ingest, Morton, radix sort, Karras hierarchy,
 refit) and the SAH top over the LBVH's subtrees against the CPU reference,
-bit for bit.  Needs a GPU."""
+bit for bit, from 2 to 600,000 triangles (the largest with more sort
+counters than one block scans in one round trip).  Needs a GPU."""
 import numpy as np
 import pytest
 
@@ -31,6 +32,8 @@ CASES = {
     "soup_dup": lambda: soup(5000, 2, dup=True),
     "soup_ragged": lambda: soup(2049, 3),
     "two": lambda: soup(2, 4),
+    # 293 sort tiles: 75,008 counters per pass, scanned by the multi-block counter scan
+    "soup_600k": lambda: soup(600000, 9),
 }
 
 
@@ -86,7 +89,7 @@ def soup_flat(n, seed):
                         np.zeros(n, np.uint16), [scenes.MATERIALS["metal"]])
 
 
-SAH_CASES = dict(CASES, soup_40=lambda: soup(40, 8), soup_flat=lambda: soup_flat(30000, 7),
+SAH_CASES = dict({k: f for k, f in CASES.items() if k != "soup_600k"}, soup_40=lambda: soup(40, 8), soup_flat=lambda: soup_flat(30000, 7),
                  campus=lambda: scenes.campus())
 
 
