@@ -157,17 +157,31 @@ def l2_copy_gbs(device) -> float:
     return 20 * 2 * a.numel() * 4 / (best * 1e-3) / 1e9
 
 
+# the query kernels' source, their shared definitions and the launch defaults
+KERNEL_SOURCES = ("rr_trace.cu", "rr_internal.cuh", "rr_host.h")
+
+
+def kernel_source_hash() -> str:
+    """sha256 prefix over the files that decide what the query kernels do."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2310_03505_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profile_counters(name: str):
     """ncu counters of the closest-hit query kernel from the committed
-    summary ``profiles/<name>.txt``, valid only while the kernel source
-    matches the hash they were taken on (else None)."""
-    import hashlib
+    summary ``profiles/<name>.txt``, valid only while the kernel sources
+    match the hash they were taken on (else None)."""
     p = os.path.join(ROOT, "profiles", name + ".txt")
-    src = os.path.join(ROOT, "paper_2310_03505_gb300", "csrc", "rr_trace.cu")
-    if not (os.path.exists(p) and os.path.exists(src)):
+    if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    try:
+        h = kernel_source_hash()
+    except OSError:
+        return None
     if d.get("source_sha256_16") != h:
         return None
     return d

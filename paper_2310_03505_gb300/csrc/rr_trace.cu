@@ -777,7 +777,17 @@ __device__ __forceinline__ float range_weight(const ScanDesc* sd, float r) {
   return (k != 0.0f && r > 1.0f) ? powf(r, -k) : 1.0f;
 }
 
-__global__ void __launch_bounds__(kShadeBlock, 3) k_shade(ScanArgs a, uint32_t bounce) {
+// The shading pass runs with 3 resident blocks per SM (80 registers) or 4
+// (64 registers, a few spilled).  Launch sequences with many rays take 4: the
+// more warps hide more of the random triangle and material loads (5M-triangle
+// city, 133k initial rays per sequence: 1.9 % per step).  Small ones take 3:
+// there the launch holds fewer tiles than the SMs have room for, each tile's
+// chain of dependent loads sets the time and the spills lengthen it (200k-
+// triangle campus, 27k initial rays per sequence: 1.4 %).
+constexpr uint32_t kShadeManyRays = 1u << 16;   // initial rays of a launch sequence
+
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kShadeBlock, kMinBlocks) k_shade(ScanArgs a, uint32_t bounce) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wsum[kShadeBlock / 32];
   __shared__ uint2 s_excl;
@@ -1050,7 +1060,7 @@ using namespace rr;
 
 static int g_num_sms = 0;
 static int g_query_occ[2][2][3] = {{{0}}};   // [wide][any][block 64 / 128 / 256]
-static int g_shade_occ = 0;
+static int g_shade_occ[2] = {0, 0};   // resident blocks of k_shade<3>, k_shade<4>
 
 static int block_index(uint32_t block) { return block <= 64u ? 0 : (block <= 128u ? 1 : 2); }
 
@@ -1077,8 +1087,10 @@ void init_dims() {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   occ_all<false>(g_query_occ[0]);
   occ_all<true>(g_query_occ[1]);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_shade_occ, k_shade, kShadeBlock, 0);
-  if (g_shade_occ < 1) g_shade_occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_shade_occ[0], k_shade<3>, kShadeBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_shade_occ[1], k_shade<4>, kShadeBlock, 0);
+  for (int& o : g_shade_occ)
+    if (o < 1) o = 1;
   g_num_sms = sms < 1 ? 1 : sms;
 }
 
@@ -1144,7 +1156,11 @@ cudaError_t launch_order(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
 
 cudaError_t launch_shade(const ScanArgs& a, uint32_t bounce, cudaStream_t st) {
   init_dims();
-  k_shade<<<g_num_sms * g_shade_occ, kShadeBlock, a.order_key ? kOrderBuckets * sizeof(uint32_t) : 0, st>>>(a, bounce);
+  const size_t smem = a.order_key ? kOrderBuckets * sizeof(uint32_t) : 0;
+  if (a.n_rays0 >= kShadeManyRays)
+    k_shade<4><<<g_num_sms * g_shade_occ[1], kShadeBlock, smem, st>>>(a, bounce);
+  else
+    k_shade<3><<<g_num_sms * g_shade_occ[0], kShadeBlock, smem, st>>>(a, bounce);
   return cudaGetLastError();
 }
 
