@@ -270,17 +270,24 @@ __device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const Scan
     hi1 = fminf(fminf(hi1, fmaxf(t0, t1)) * kBoxInflate, s.t_best);
     const bool h0 = lo0 <= hi0, h1 = lo1 <= hi1;
     const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
-    if (h0 && h1) {
-      const bool first0 = lo0 <= lo1;
-      s.node = first0 ? c0 : c1;
-      if (s.sp < kStack) stack[s.sp++] = first0 ? c1 : c0;
-      else atomicOr(&a.ctr->error, kErrStack);
-      return;
-    }
+    // the nearer hit child next, the farther one pushed when both are hit,
+    // else the next stack entry: selects and a predicated store instead of
+    // branches, so that the lanes of a warp take the same path here
+    const bool both = h0 && h1;
+    const bool first0 = !h1 || (h0 && lo0 <= lo1);
+    const uint32_t near = first0 ? c0 : c1, far = first0 ? c1 : c0;
+    const int sp = s.sp;
+    if (sp < kStack) stack[sp] = far;   // above the top unless both are hit
+    if (both && sp >= kStack) atomicOr(&a.ctr->error, kErrStack);
+    const int sp1 = sp + ((both && sp < kStack) ? 1 : 0);
     if (h0 || h1) {
-      s.node = h0 ? c0 : c1;
-      return;
+      s.sp = sp1;
+      s.node = near;
+    } else {
+      s.node = sp1 ? stack[sp1 - 1] : kNone;
+      s.sp = sp1 ? sp1 - 1 : 0;
     }
+    return;
   } else if (trav_tri<kAny>(s, a, node & ~kLeafBit, n_tris, count)) {
     s.node = kNone;
     return;
@@ -510,7 +517,7 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
       continue;
     }
     if (busy) {
-#pragma unroll 1
+#pragma unroll 2
       for (int u = 0; u < kSteps && s.node != kNone; ++u) {
         if (kWide) step_wide<kAny>(s, reinterpret_cast<uint2*>(stack), a, n_nodes, n_tris, count);
         else step_binary<kAny>(s, reinterpret_cast<uint32_t*>(stack), a, n_nodes, n_tris, count);
