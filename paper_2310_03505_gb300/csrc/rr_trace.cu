@@ -277,7 +277,7 @@ __device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const Scan
     const bool first0 = !h1 || (h0 && lo0 <= lo1);
     const uint32_t near = first0 ? c0 : c1, far = first0 ? c1 : c0;
     const int sp = s.sp;
-    if (sp < kStack) stack[sp] = far;   // above the top unless both are hit
+    if (both && sp < kStack) stack[sp] = far;   // a predicated store: every local store costs an L2 sector
     if (both && sp >= kStack) atomicOr(&a.ctr->error, kErrStack);
     const int sp1 = sp + ((both && sp < kStack) ? 1 : 0);
     if (h0 || h1) {
