@@ -723,8 +723,8 @@ def main():
                        order=args.query_order)
     rl = roofline(head, peak, peak_kind, profile_counters("query_kernel_city_ncu"), l2_peak, "latency",
                   "the city's BVH and triangles (~0.56 GB) exceed the 129 MB L2, yet the dependent node fetches "
-                  "are served by L1 (80 % hit) and L2 (77-79 %): the kernel is bound by their latency, with L1 "
-                  "throughput the nearest limit (68-77 % of peak) and DRAM under 3 %.  achieved counts the "
+                  "are served by L1 (81-83 % hit) and L2 (73-75 %): the kernel is bound by their latency, with L1 "
+                  "throughput the nearest limit (70-78 % of peak) and DRAM under 3 %.  achieved counts the "
                   "algorithmic node/triangle/record bytes of a launch over its CUDA-event duration (the launches "
                   "of the 3 azimuth ranges overlap on their streams), against the HBM copy peak; dram_gbs and "
                   "l2.achieved divide the bytes ncu measured for the same kernel source by that duration")
