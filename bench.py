@@ -462,9 +462,10 @@ def served_bench(device, seconds: float = 60.0, rates=(30, 60, 120, 240), rank: 
 
 
 # ------------------------------------------------------------------ plain scan steps
-def headline_config(sc, params, node_format: str, split: int, step_bvh: str, world: int, order: str) -> dict:
+def headline_config(sc, params, node_format: str, split: int, step_bvh: str, world: int, order: str,
+                    workload: str = LARGE_WORKLOAD) -> dict:
     """The `config` of the line (the same for both arms)."""
-    return {"workload": LARGE_WORKLOAD, "triangles": sc.n_triangles, "n_azimuth": params["n_azimuth"],
+    return {"workload": workload, "triangles": sc.n_triangles, "n_azimuth": params["n_azimuth"],
             "rays_per_beam": params["rays_per_beam"], "max_bounces": params["max_bounces"],
             "n_bins": params["n_bins"], "node_format": node_format, "split_streams": split, "query_order": order,
             "bvh": ("LBVH + binned-SAH top over its subtrees of <= 32 triangles" if step_bvh == "sah_top" else "LBVH"),
@@ -653,6 +654,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-medium", action="store_true", help="skip the medium (200k-triangle campus) object")
+    ap.add_argument("--no-large", action="store_true",
+                    help="profiling runs of the campus: its step is the line's step, the city is not run")
     ap.add_argument("--node-format", default="auto", choices=["auto", "wide", "binary"],
                     help="BVH node format of the plain scans (auto: the library default)")
     ap.add_argument("--batched-steps", type=int, default=3)
@@ -675,7 +678,8 @@ def main():
     world, rank, local = dist_env()
 
     from paper_2310_03505_gb300 import scenes
-    sc, pz, params = scenes.config_large()
+    sc, pz, params = scenes.config_medium() if args.no_large else scenes.config_large()
+    workload = MEDIUM_WORKLOAD if args.no_large else LARGE_WORKLOAD
     split_default = 3
 
     if args.impl == "reference":
@@ -691,7 +695,8 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
                 "config": headline_config(sc, params, nf, split_default, args.step_bvh, args.gpus,
-                                          ORDER_DEFAULT if args.query_order == "auto" else args.query_order),
+                                          ORDER_DEFAULT if args.query_order == "auto" else args.query_order,
+                                          workload),
                 "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
                                  "sample": sample},
                 "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -721,7 +726,11 @@ def main():
                        step_bvh=args.step_bvh, node_format=args.node_format, ws_limit_gb=args.workspace_limit_gb,
                        e2e=not args.no_e2e, scan_only=not args.no_scan_only, clocks=rank == 0,
                        order=args.query_order)
-    rl = roofline(head, peak, peak_kind, profile_counters("query_kernel_city_ncu"), l2_peak, "latency",
+    campus_note = ("cache-resident: the campus BVH and triangles (~22 MB) stay in L2, so the algorithmic bytes "
+                   "come from L1/L2 and the launches are bound by the latency of dependent node fetches, not by HBM")
+    rl = roofline(head, peak, peak_kind, profile_counters("query_kernel_campus_ncu"), l2_peak, "latency",
+                  campus_note) if args.no_large else \
+        roofline(head, peak, peak_kind, profile_counters("query_kernel_city_ncu"), l2_peak, "latency",
                   "the city's BVH and triangles (~0.56 GB) exceed the 129 MB L2, yet the dependent node fetches "
                   "are served by L1 (81-83 % hit) and L2 (73-75 %): the kernel is bound by their latency, with L1 "
                   "throughput the nearest limit (70-78 % of peak) and DRAM under 3 %.  achieved counts the "
@@ -730,17 +739,14 @@ def main():
                   "l2.achieved divide the bytes ncu measured for the same kernel source by that duration")
 
     medium = None
-    if not args.no_medium:
+    if not args.no_medium and not args.no_large:
         msc, mpz, mparams = scenes.config_medium()
         m_steps = max(args.steps, 50)
         medium = plain_bench(rr, device, stream, flush, msc, mpz, mparams, m_steps, args.warmup, rank=rank,
                              world=world, step_bvh=args.step_bvh, node_format=args.node_format, e2e=False,
                              scan_only=not args.no_scan_only, order=args.query_order)
         medium["roofline"] = roofline(medium, peak, peak_kind, profile_counters("query_kernel_campus_ncu"), l2_peak,
-                                      "latency",
-                                      "cache-resident: the campus BVH and triangles (~22 MB) stay in L2, so the "
-                                      "algorithmic bytes come from L1/L2 and the launches are bound by the latency "
-                                      "of dependent node fetches, not by HBM")
+                                      "latency", campus_note)
         medium = {"workload": MEDIUM_WORKLOAD, "triangles": msc.n_triangles,
                   **{k: v for k, v in medium.items() if k not in ("trace", "closest_queries")}}
 
@@ -749,7 +755,8 @@ def main():
         batched = batched_bench(device, stream, flush, steps=args.batched_steps, rank=rank, bvh=args.scene_bvh)
     served = None
     if not args.no_served and rank == 0:
-        served = served_bench(device, seconds=args.served_seconds, rank=rank, bvh=args.scene_bvh, city=sc)
+        served = served_bench(device, seconds=args.served_seconds, rank=rank, bvh=args.scene_bvh,
+                              city=None if args.no_large else sc)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -757,7 +764,7 @@ def main():
 
     if rank == 0:
         config = headline_config(sc, params, head["node_format"], head["split_streams"], args.step_bvh, world,
-                                 head["query_order"])
+                                 head["query_order"], workload)
         if args.workspace_limit_gb > 0:
             config["workspace_limit"] = head["workspace_limit"]
         line = {
