@@ -409,6 +409,7 @@ int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor
     }
   }
   a.tri = wide ? s->d_wtri : s->d_tri;
+  a.tri_copy = 3 * (size_t)s->nt;
   a.nodes = wide ? s->d_wnodes : s->d_nodes;
   a.mats = s->d_mats;
   a.lut = s->d_lut;

@@ -413,9 +413,14 @@ __global__ void k_gather(const float* __restrict__ vtx, const uint32_t* __restri
     // an invalid index was flagged by the ingest step; never read past the vertices
     v[c] = vi < nv ? make_float3(vtx[3 * vi], vtx[3 * vi + 1], vtx[3 * vi + 2]) : make_float3(0.f, 0.f, 0.f);
   }
-  tri[3 * j + 0] = make_float4(v[0].x, v[0].y, v[0].z, __uint_as_float(t));
-  tri[3 * j + 1] = make_float4(v[1].x, v[1].y, v[1].z, __uint_as_float((uint32_t)mat_id[t]));
-  tri[3 * j + 2] = make_float4(v[2].x, v[2].y, v[2].z, 0.0f);
+  const float w[3] = {__uint_as_float(t), __uint_as_float((uint32_t)mat_id[t]), 0.0f};
+#pragma unroll
+  for (uint32_t r = 0; r < (uint32_t)kTriCopies; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float3 u = tri_rotate(v[c], r);
+      tri[(size_t)r * 3 * nt + 3 * (size_t)j + c] = make_float4(u.x, u.y, u.z, w[c]);
+    }
   float* b = nbox + 6 * (size_t)(nt - 1 + j);
   b[0] = fminf(fminf(v[0].x, v[1].x), v[2].x);
   b[1] = fminf(fminf(v[0].y, v[1].y), v[2].y);
@@ -1756,9 +1761,12 @@ __global__ void __launch_bounds__(128) k_wide_write(uint32_t n, const uint32_t* 
         if (x & kLeafBit) {
           const uint32_t j = x & ~kLeafBit;
           const size_t dst = 3 * (size_t)(rec.z + r++);
-          wtri[dst] = tri[3 * (size_t)j];
-          wtri[dst + 1] = tri[3 * (size_t)j + 1];
-          wtri[dst + 2] = tri[3 * (size_t)j + 2];
+          for (int c = 0; c < kTriCopies; ++c) {   // every rotated copy
+            const size_t off = (size_t)c * 3 * n;
+            wtri[off + dst] = tri[off + 3 * (size_t)j];
+            wtri[off + dst + 1] = tri[off + 3 * (size_t)j + 1];
+            wtri[off + dst + 2] = tri[off + 3 * (size_t)j + 2];
+          }
         } else if (sp + 2 <= kGroupMax + 1) {   // always: a group has at most kGroupMax triangles
           stack[sp++] = __ldg(&child[2 * x + 1]);
           stack[sp++] = __ldg(&child[2 * x]);
@@ -1901,7 +1909,7 @@ cudaError_t build_alloc(rr_scene* s) {
   RR_TRY(alloc((void**)&s->d_lut, M * (kLutCells + 1) * sizeof(float4)));
   RR_TRY(alloc((void**)&s->d_lut_cells, M * kLutCells * sizeof(float)));
   RR_TRY(alloc((void**)&s->d_lobe_kind, M * sizeof(uint8_t)));
-  RR_TRY(alloc((void**)&s->d_tri, T * 3 * sizeof(float4)));
+  RR_TRY(alloc((void**)&s->d_tri, kTriCopies * T * 3 * sizeof(float4)));
   RR_TRY(alloc((void**)&s->d_nodes, (T > 1 ? T - 1 : 0) * 4 * sizeof(float4)));
   RR_TRY(alloc((void**)&s->d_centroid, T * sizeof(float4)));
   for (int k = 0; k < 2; ++k) {
@@ -1923,7 +1931,7 @@ cudaError_t build_alloc(rr_scene* s) {
   if (T) {
     RR_TRY(alloc((void**)&s->d_cut, (size_t)s->wcap * 8 * sizeof(uint32_t)));
     RR_TRY(alloc((void**)&s->d_wnodes, (size_t)s->wcap * kWideNodeWords * sizeof(float4)));
-    RR_TRY(alloc((void**)&s->d_wtri, T * 3 * sizeof(float4)));
+    RR_TRY(alloc((void**)&s->d_wtri, kTriCopies * T * 3 * sizeof(float4)));
     RR_TRY(alloc((void**)&s->d_wsrc, (size_t)s->wcap * sizeof(unsigned long long)));
     RR_TRY(alloc((void**)&s->d_wrec, (size_t)s->wcap * sizeof(uint4)));
     RR_TRY(alloc((void**)&s->d_wctr, 8 * sizeof(uint32_t)));

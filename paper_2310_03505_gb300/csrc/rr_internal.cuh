@@ -42,6 +42,17 @@ struct __align__(16) MatDev {
   uint32_t pec;     // perfect conductor
 };
 
+// Triangle vertices are stored three times, with their coordinates rotated
+// by 0, 1 and 2 places: copy r holds (v[k], v[k+1 mod 3], v[k+2 mod 3]) for
+// k = r.  The watertight ray/triangle test works in a frame whose third axis
+// is the ray's dominant axis kz and whose first two axes follow it cyclically;
+// that frame is copy r = (kz + 1) mod 3, so the test reads the vertices in its
+// own order instead of selecting each coordinate at run time.
+constexpr int kTriCopies = 3;
+__device__ __forceinline__ float3 tri_rotate(float3 v, uint32_t r) {
+  return r == 0 ? v : (r == 1 ? make_float3(v.y, v.z, v.x) : make_float3(v.z, v.x, v.y));
+}
+
 // ray record, 48 bytes
 struct __align__(16) RayRec {
   float4 o_L;   // origin, one-way optical path so far
@@ -120,7 +131,9 @@ struct __align__(16) ScanDesc {
 // Launch-sequence constants of one batch (passed by value)
 struct ScanArgs {
   // scene
-  const float4* tri;         // [T][3] sorted: v0 (w: orig id bits), v1 (w: material bits), v2
+  const float4* tri;         // [3][T][3] sorted: v0 (w: orig id bits), v1 (w: material bits), v2; copy r holds
+                             // the coordinates rotated by r (tri_rotate), so copy 0 is (x, y, z)
+  size_t tri_copy;           // float4s from one rotated copy to the next (3 T)
   const float4* nodes;       // [T-1][4] Aila-Laine layout
   const MatDev* mats;
   const float4* lut;         // [M][kLutCells + 1]: (G(x_k), Gc(x_k), cos^C(x_k), 0)

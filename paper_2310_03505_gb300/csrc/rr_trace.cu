@@ -114,43 +114,43 @@ __global__ void k_raygen(ScanArgs a) {
 // ---------------------------------------------------------------------------
 // traversal
 struct WoopRay {
-  float3 o;
-  int kx, ky, kz;
-  float Sx, Sy, Sz;
+  float3 o;            // origin in the frame (kx, ky, kz)
+  float Sx, Sy, Sz;    // shear: d_kx / d_kz, d_ky / d_kz, 1 / d_kz
+  uint32_t rot;        // the rotated triangle copy whose coordinates are in that frame
 };
 
-__device__ __forceinline__ float sel(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
-
+// The frame's third axis kz is the dominant axis of d; kx and ky follow it
+// cyclically (kx = kz + 1, ky = kz + 2 mod 3), which is the triangle copy
+// rotated by (kz + 1) mod 3.  Woop et al. swap kx and ky when d_kz < 0 to keep
+// the winding; the test below accepts both windings, and swapping the two
+// axes negates U, V, W, det and T exactly (each is a difference of the same
+// rounded products, or a sum of such terms), so t and the decision are the
+// same bit for bit without the swap.
 __device__ __forceinline__ WoopRay make_woop(float3 o, float3 d) {
   WoopRay w;
-  w.o = o;
   const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
-  w.kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
-  w.kx = w.kz == 2 ? 0 : w.kz + 1;
-  w.ky = w.kx == 2 ? 0 : w.kx + 1;
-  const float dz = sel(d, w.kz);
-  if (dz < 0.0f) {
-    const int t = w.kx;
-    w.kx = w.ky;
-    w.ky = t;
-  }
-  w.Sx = sel(d, w.kx) / dz;
-  w.Sy = sel(d, w.ky) / dz;
-  w.Sz = 1.0f / dz;
+  const uint32_t kz = (ax >= ay && ax >= az) ? 0u : (ay >= az ? 1u : 2u);
+  w.rot = kz == 2u ? 0u : kz + 1u;
+  const float3 dr = tri_rotate(d, w.rot);
+  w.o = tri_rotate(o, w.rot);
+  w.Sx = dr.x / dr.z;
+  w.Sy = dr.y / dr.z;
+  w.Sz = 1.0f / dr.z;
   return w;
 }
 
 // watertight test; returns t (or -1) -- products are kept unfused so that a
 // shared edge evaluates to exactly opposite values in both triangles
+// (the vertices in the ray's frame: the triangle copy w.rot)
 __device__ __forceinline__ float woop_hit(const WoopRay& w, float3 v0, float3 v1, float3 v2) {
   const float3 A = v0 - w.o, B = v1 - w.o, C = v2 - w.o;
-  const float Az_ = sel(A, w.kz), Bz_ = sel(B, w.kz), Cz_ = sel(C, w.kz);
-  const float Ax = __fsub_rn(sel(A, w.kx), __fmul_rn(w.Sx, Az_));
-  const float Ay = __fsub_rn(sel(A, w.ky), __fmul_rn(w.Sy, Az_));
-  const float Bx = __fsub_rn(sel(B, w.kx), __fmul_rn(w.Sx, Bz_));
-  const float By = __fsub_rn(sel(B, w.ky), __fmul_rn(w.Sy, Bz_));
-  const float Cx = __fsub_rn(sel(C, w.kx), __fmul_rn(w.Sx, Cz_));
-  const float Cy = __fsub_rn(sel(C, w.ky), __fmul_rn(w.Sy, Cz_));
+  const float Az_ = A.z, Bz_ = B.z, Cz_ = C.z;
+  const float Ax = __fsub_rn(A.x, __fmul_rn(w.Sx, Az_));
+  const float Ay = __fsub_rn(A.y, __fmul_rn(w.Sy, Az_));
+  const float Bx = __fsub_rn(B.x, __fmul_rn(w.Sx, Bz_));
+  const float By = __fsub_rn(B.y, __fmul_rn(w.Sy, Bz_));
+  const float Cx = __fsub_rn(C.x, __fmul_rn(w.Sx, Cz_));
+  const float Cy = __fsub_rn(C.y, __fmul_rn(w.Sy, Cz_));
   const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
   const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
   const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
@@ -171,7 +171,9 @@ __device__ __forceinline__ float woop_hit(const WoopRay& w, float3 v0, float3 v1
 // lexicographically smallest.  Any hit: the first t_min < t < t_best.  The
 // leaf `skip` (the one the ray starts on) is never reported.
 struct Trav {
-  WoopRay w;            // origin and the watertight-test frame
+  float3 c0, c1;        // slab offsets (trav_begin): binary nodes, of the lower / upper box planes;
+                        // wide nodes, of the near / far planes
+  WoopRay w;            // the watertight-test frame
   float3 id;            // 1 / direction, zero components replaced by +-1e-30
   float t_min, t_best;
   uint32_t skip;
@@ -189,6 +191,25 @@ __device__ __forceinline__ void trav_begin(Trav& s, float3 o, float3 d, float t_
   s.id = make_float3(1.0f / (fabsf(d.x) > 1e-30f ? d.x : copysignf(1e-30f, d.x)),
                      1.0f / (fabsf(d.y) > 1e-30f ? d.y : copysignf(1e-30f, d.y)),
                      1.0f / (fabsf(d.z) > 1e-30f ? d.z : copysignf(1e-30f, d.z)));
+  // Slab test with one fma per plane: plane b is reached at t = fma(b, id, c)
+  // with c = -(o id) -+ eps, where the robust form (b - o) id needs two
+  // operations.  The fma form errs against (b - o) id by at most u |o id|
+  // (o id rounded) + u |c| (c rounded) + u |t| (the fma itself), u = 2^-24.
+  // eps = 4 u |o id| moves every near plane down and every far plane up by
+  // more than the first two; the last is relative, like the errors of the
+  // robust form, and the far-plane inflation kBoxInflate covers it.  So a box
+  // the robust test accepts is accepted here too.
+  {
+    const float ox = __fmul_rn(o.x, s.id.x), oy = __fmul_rn(o.y, s.id.y), oz = __fmul_rn(o.z, s.id.z);
+    float ex = 0x1p-22f * fabsf(ox), ey = 0x1p-22f * fabsf(oy), ez = 0x1p-22f * fabsf(oz);
+    if (!wide) {   // the lower plane is the near one for a positive direction component
+      ex = copysignf(ex, s.id.x);
+      ey = copysignf(ey, s.id.y);
+      ez = copysignf(ez, s.id.z);
+    }
+    s.c0 = make_float3(-ox - ex, -oy - ey, -oz - ez);
+    s.c1 = make_float3(-ox + ex, -oy + ey, -oz + ez);
+  }
   s.t_min = t_min;
   s.t_best = t_best;
   s.skip = skip;
@@ -213,7 +234,7 @@ template <bool kAny>
 __device__ __forceinline__ bool trav_tri(Trav& s, const ScanArgs& a, uint32_t j, uint32_t& n_tris, bool count) {
   if (j == s.skip) return false;
   if (count) ++n_tris;
-  const float4* tp = a.tri + 3 * (size_t)j;
+  const float4* tp = a.tri + a.tri_copy * s.w.rot + 3 * (size_t)j;
   const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
   const float t = woop_hit(s.w, f3(v0), f3(v1), f3(v2));
   if (t > s.t_min) {
@@ -242,30 +263,30 @@ __device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const Scan
   if (!(node & kLeafBit)) {
     if (count) ++n_nodes;
     ++s.visits;   // bounded where the query loop looks at its lanes
-    const float3 o = s.w.o, id = s.id;
+    const float3 id = s.id, cl = s.c0, ch = s.c1;
     const float4* np = a.nodes + 4 * (size_t)node;
     const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
     // child 0
-    float t0 = (n0.x - o.x) * id.x, t1 = (n0.y - o.x) * id.x;
+    float t0 = fmaf(n0.x, id.x, cl.x), t1 = fmaf(n0.y, id.x, ch.x);
     float lo0 = fminf(t0, t1), hi0 = fmaxf(t0, t1);
-    t0 = (n0.z - o.y) * id.y;
-    t1 = (n0.w - o.y) * id.y;
+    t0 = fmaf(n0.z, id.y, cl.y);
+    t1 = fmaf(n0.w, id.y, ch.y);
     lo0 = fmaxf(lo0, fminf(t0, t1));
     hi0 = fminf(hi0, fmaxf(t0, t1));
-    t0 = (n2.x - o.z) * id.z;
-    t1 = (n2.y - o.z) * id.z;
+    t0 = fmaf(n2.x, id.z, cl.z);
+    t1 = fmaf(n2.y, id.z, ch.z);
     lo0 = fmaxf(fmaxf(lo0, fminf(t0, t1)), s.t_min);
     hi0 = fminf(fminf(hi0, fmaxf(t0, t1)) * kBoxInflate, s.t_best);
     // child 1
-    t0 = (n1.x - o.x) * id.x;
-    t1 = (n1.y - o.x) * id.x;
+    t0 = fmaf(n1.x, id.x, cl.x);
+    t1 = fmaf(n1.y, id.x, ch.x);
     float lo1 = fminf(t0, t1), hi1 = fmaxf(t0, t1);
-    t0 = (n1.z - o.y) * id.y;
-    t1 = (n1.w - o.y) * id.y;
+    t0 = fmaf(n1.z, id.y, cl.y);
+    t1 = fmaf(n1.w, id.y, ch.y);
     lo1 = fmaxf(lo1, fminf(t0, t1));
     hi1 = fminf(hi1, fmaxf(t0, t1));
-    t0 = (n2.z - o.z) * id.z;
-    t1 = (n2.w - o.z) * id.z;
+    t0 = fmaf(n2.z, id.z, cl.z);
+    t1 = fmaf(n2.w, id.z, ch.z);
     lo1 = fmaxf(fmaxf(lo1, fminf(t0, t1)), s.t_min);
     hi1 = fminf(fminf(hi1, fmaxf(t0, t1)) * kBoxInflate, s.t_best);
     const bool h0 = lo0 <= hi0, h1 = lo1 <= hi1;
@@ -304,9 +325,10 @@ __device__ __forceinline__ void step_binary(Trav& s, uint32_t* stack, const Scan
 // incoherent ray traversal on GPUs through compressed wide BVHs" (HPG 2017):
 // a group is (first child, internal-slot mask << 8 | hit children still to
 // visit, bit k for slot k ^ octant), so one stack entry stands for up to 7
-// pending children.  Slot boxes are decoded exactly (see kWideNodeWords) and
-// tested with the same slab test as the binary nodes, so a query finds the
-// same closest hit in either BVH.
+// pending children.  Slot boxes are decoded exactly (see kWideNodeWords);
+// each contains the box of the binary node it stands for, and both node
+// formats take the conservative slab test of trav_begin, so a query reaches
+// every triangle it can hit in either BVH and finds the same closest hit.
 template <bool kAny>
 __device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs& a, uint32_t& n_nodes,
                                           uint32_t& n_tris, bool count) {
@@ -333,7 +355,7 @@ __device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs&
     }
     if (count) ++n_nodes;
     ++s.visits;   // bounded where the query loop looks at its lanes
-    const float3 o = s.w.o, id = s.id;
+    const float3 id = s.id, cn = s.c0, cf = s.c1;
     const bool neg_x = id.x < 0.0f, neg_y = id.y < 0.0f, neg_z = id.z < 0.0f;
     const uint4* np = reinterpret_cast<const uint4*>(a.nodes) + kWideNodeWords * (size_t)node;
     const uint4 w0 = __ldg(np), w1 = __ldg(np + 1), w2 = __ldg(np + 2), w3 = __ldg(np + 3), w4 = __ldg(np + 4);
@@ -359,9 +381,10 @@ __device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs&
       const float bfy = fmaf(__uint_as_float(__byte_perm(j < 4 ? fy0 : fy1, 0x4B000000u, sel)), sy, py);
       const float bnz = fmaf(__uint_as_float(__byte_perm(j < 4 ? nz0 : nz1, 0x4B000000u, sel)), sz, pz);
       const float bfz = fmaf(__uint_as_float(__byte_perm(j < 4 ? fz0 : fz1, 0x4B000000u, sel)), sz, pz);
-      const float lo = fmaxf(fmaxf((bnx - o.x) * id.x, (bny - o.y) * id.y), fmaxf((bnz - o.z) * id.z, s.t_min));
-      const float hi =
-          fminf(fminf(fminf((bfx - o.x) * id.x, (bfy - o.y) * id.y), (bfz - o.z) * id.z) * kBoxInflate, s.t_best);
+      const float lo =
+          fmaxf(fmaxf(fmaf(bnx, id.x, cn.x), fmaf(bny, id.y, cn.y)), fmaxf(fmaf(bnz, id.z, cn.z), s.t_min));
+      const float hi = fminf(
+          fminf(fminf(fmaf(bfx, id.x, cf.x), fmaf(bfy, id.y, cf.y)), fmaf(bfz, id.z, cf.z)) * kBoxInflate, s.t_best);
       const uint32_t c = counts >> (2 * j) & 3u;   // triangles of a leaf slot (0: inner or empty)
       if (lo <= hi && (valid >> j & 1u)) {
         if (imask >> j & 1u) hit_i |= 1u << (j ^ oct);
