@@ -413,6 +413,10 @@ __global__ void k_gather(const float* __restrict__ vtx, const uint32_t* __restri
     // an invalid index was flagged by the ingest step; never read past the vertices
     v[c] = vi < nv ? make_float3(vtx[3 * vi], vtx[3 * vi + 1], vtx[3 * vi + 2]) : make_float3(0.f, 0.f, 0.f);
   }
+  {   // the unit normal (and the material) after the three copies
+    const float3 nr = normalize(cross(v[1] - v[0], v[2] - v[0]));
+    tri[(size_t)kTriCopies * 3 * nt + j] = make_float4(nr.x, nr.y, nr.z, __uint_as_float((uint32_t)mat_id[t]));
+  }
   const float w[3] = {__uint_as_float(t), __uint_as_float((uint32_t)mat_id[t]), 0.0f};
 #pragma unroll
   for (uint32_t r = 0; r < (uint32_t)kTriCopies; ++r)
@@ -1767,6 +1771,7 @@ __global__ void __launch_bounds__(128) k_wide_write(uint32_t n, const uint32_t* 
             wtri[off + dst + 1] = tri[off + 3 * (size_t)j + 1];
             wtri[off + dst + 2] = tri[off + 3 * (size_t)j + 2];
           }
+          wtri[(size_t)kTriCopies * 3 * n + dst / 3] = tri[(size_t)kTriCopies * 3 * n + j];
         } else if (sp + 2 <= kGroupMax + 1) {   // always: a group has at most kGroupMax triangles
           stack[sp++] = __ldg(&child[2 * x + 1]);
           stack[sp++] = __ldg(&child[2 * x]);
@@ -1909,7 +1914,7 @@ cudaError_t build_alloc(rr_scene* s) {
   RR_TRY(alloc((void**)&s->d_lut, M * (kLutCells + 1) * sizeof(float4)));
   RR_TRY(alloc((void**)&s->d_lut_cells, M * kLutCells * sizeof(float)));
   RR_TRY(alloc((void**)&s->d_lobe_kind, M * sizeof(uint8_t)));
-  RR_TRY(alloc((void**)&s->d_tri, kTriCopies * T * 3 * sizeof(float4)));
+  RR_TRY(alloc((void**)&s->d_tri, (kTriCopies * 3 + 1) * T * sizeof(float4)));
   RR_TRY(alloc((void**)&s->d_nodes, (T > 1 ? T - 1 : 0) * 4 * sizeof(float4)));
   RR_TRY(alloc((void**)&s->d_centroid, T * sizeof(float4)));
   for (int k = 0; k < 2; ++k) {
@@ -1931,7 +1936,7 @@ cudaError_t build_alloc(rr_scene* s) {
   if (T) {
     RR_TRY(alloc((void**)&s->d_cut, (size_t)s->wcap * 8 * sizeof(uint32_t)));
     RR_TRY(alloc((void**)&s->d_wnodes, (size_t)s->wcap * kWideNodeWords * sizeof(float4)));
-    RR_TRY(alloc((void**)&s->d_wtri, kTriCopies * T * 3 * sizeof(float4)));
+    RR_TRY(alloc((void**)&s->d_wtri, (kTriCopies * 3 + 1) * T * sizeof(float4)));
     RR_TRY(alloc((void**)&s->d_wsrc, (size_t)s->wcap * sizeof(unsigned long long)));
     RR_TRY(alloc((void**)&s->d_wrec, (size_t)s->wcap * sizeof(uint4)));
     RR_TRY(alloc((void**)&s->d_wctr, 8 * sizeof(uint32_t)));

@@ -85,7 +85,7 @@ struct rr_scene {
   std::vector<uint8_t> lobe_kind;  // host copy
   std::vector<uint32_t> raw_flags; // rr_material.flags of every material
   float* d_lobe_samples = nullptr; // [M][kLobeSamples] tabulated lobes (allocated on first use)
-  float4* d_tri = nullptr;         // [T][3] sorted leaves
+  float4* d_tri = nullptr;         // [3][T][3] sorted leaves in three rotated copies, then [T] unit normals
   float4* d_nodes = nullptr;       // [T-1][4]
   // 8-wide quantised BVH (collapsed from the binary one at every build)
   uint32_t wcap = 0;               // wide node capacity (T - 1, at least 1)
@@ -93,7 +93,7 @@ struct rr_scene {
   bool wide_stale = true;          // the binary LBVH changed since the last collapse
   uint32_t* d_cut = nullptr;       // [T-1][8] cut of every binary internal node, slot order
   float4* d_wnodes = nullptr;      // [wcap][kWideNodeWords]
-  float4* d_wtri = nullptr;        // [T][3] triangles in wide-leaf order
+  float4* d_wtri = nullptr;        // the same in wide-leaf order
   unsigned long long* d_wsrc = nullptr;   // [wcap] epoch << 32 | binary node of each wide node
   uint4* d_wrec = nullptr;         // [wcap] (binary node, first child, first triangle, 0)
   uint32_t* d_wctr = nullptr;      // [8] ticket, allocated, done, triangles, error

@@ -132,7 +132,8 @@ struct __align__(16) ScanDesc {
 struct ScanArgs {
   // scene
   const float4* tri;         // [3][T][3] sorted: v0 (w: orig id bits), v1 (w: material bits), v2; copy r holds
-                             // the coordinates rotated by r (tri_rotate), so copy 0 is (x, y, z)
+                             // the coordinates rotated by r (tri_rotate), so copy 0 is (x, y, z); then [T]
+                             // (unit geometric normal, material bits) at tri + 3 tri_copy
   size_t tri_copy;           // float4s from one rotated copy to the next (3 T)
   const float4* nodes;       // [T-1][4] Aila-Laine layout
   const MatDev* mats;

@@ -620,10 +620,10 @@ __global__ void __launch_bounds__(256) k_vis_prep(ScanArgs a, uint32_t bounce) {
         if (__ldg(&sd->rng.w) & RR_MULTIPATH) {
           const float3 o = f3(ray.o_L), d = f3(ray.d_E);
           const float n_cur = medium == kAir ? 1.0f : __ldg(&a.mats[medium].n);
-          const float4* tp = a.tri + 3 * (size_t)h.leaf;
-          const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-          const MatDev m = a.mats[__float_as_uint(v1.w)];
-          float3 nrm = normalize(cross(f3(v1) - f3(v0), f3(v2) - f3(v0)));
+          const float4 nr = __ldg(a.tri + (size_t)kTriCopies * a.tri_copy + h.leaf);   // unit normal, material
+          const uint32_t mid = __float_as_uint(nr.w);
+          const MatDev m = a.mats[mid];
+          float3 nrm = f3(nr);
           float cos_i = -dot(d, nrm);
           const bool entering = cos_i > 0.0f;
           float n2 = m.n;
@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(256) k_vis_prep(ScanArgs a, uint32_t bounce) {
             }
           }
           if (cand) {
-            wa = brdf_window(m, a.lut + (size_t)__float_as_uint(v1.w) * (kLutCells + 1), angle_between(dir_out, v),
+            wa = brdf_window(m, a.lut + (size_t)mid * (kLutCells + 1), angle_between(dir_out, v),
                              __ldg(&sd->beam.x));
             want = wa > 0.0f;
           }
@@ -885,13 +885,12 @@ __global__ void __launch_bounds__(kShadeBlock, kMinBlocks) k_shade(ScanArgs a, u
           E1 = E * expf(-2.0f * alpha * t);
           tal[1] = E - E1;
         }
-        const float4* tp = a.tri + 3 * (size_t)h.leaf;
-        const float4 v0 = tp[0], v1 = tp[1], v2 = tp[2];
-        orig = __float_as_uint(v0.w);
-        const uint32_t mid = __float_as_uint(v1.w);
+        const float4 nrw = __ldg(a.tri + (size_t)kTriCopies * a.tri_copy + h.leaf);   // unit normal, material
+        orig = __float_as_uint(__ldg(&a.tri[3 * (size_t)h.leaf].w));
+        const uint32_t mid = __float_as_uint(nrw.w);
         const MatDev m = a.mats[mid];
         const float4* lut = a.lut + (size_t)mid * (kLutCells + 1);
-        float3 nrm = normalize(cross(f3(v1) - f3(v0), f3(v2) - f3(v0)));
+        float3 nrm = f3(nrw);
         float cos_i = -dot(d, nrm);
         const bool entering = cos_i > 0.0f;
         float n2 = m.n;
