@@ -235,6 +235,11 @@ void ctx_free(ExecCtx* x) {
   if (x->stage_ev) cudaEventDestroy(x->stage_ev);
   if (x->gexec) cudaGraphExecDestroy(x->gexec);
   if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
+  for (int b = 0; b < RR_MAX_BOUNCES; ++b) {
+    if (x->fork[b]) cudaEventDestroy(x->fork[b]);
+    if (x->join[b]) cudaEventDestroy(x->join[b]);
+  }
+  if (x->side) cudaStreamDestroy(x->side);
   *x = ExecCtx();
 }
 

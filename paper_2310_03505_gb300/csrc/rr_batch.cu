@@ -59,7 +59,7 @@ static uint64_t order_bytes(uint64_t q, const Need& nd) {
 
 static uint64_t bytes_of(uint64_t q, uint64_t r, const Need& nd) {
   const uint64_t tiles = (q + 255) / 256 + 1;
-  return align256(q * sizeof(rr::RayRec)) * 2 + align256(q * sizeof(rr::HitRec)) + align256(r * 8) +
+  return align256(q * sizeof(rr::RayRec)) * 2 + align256(q * sizeof(rr::HitRec)) + align256(q * 4) + align256(r * 8) +
          align256(tiles * 8) + align256(nd.tmp * 4) + align256(desc_bytes(nd.n)) + order_bytes(q, nd);
 }
 
@@ -89,6 +89,8 @@ static WsLayout layout_of(const Need& nd, uint64_t limit) {
   off += align256((size_t)q * sizeof(rr::RayRec));
   L.off_hits = off;
   off += align256((size_t)q * sizeof(rr::HitRec));
+  L.off_vis = off;   // deferred visibility: the candidates of a bounce
+  off += align256((size_t)q * 4);
   L.off_recs = off;
   off += align256((size_t)L.rec_cap * 8);
   L.off_status = off;
@@ -248,11 +250,28 @@ static void fill_desc(ScanDesc& d, const rr_pose& pose, const rr_sensor_params& 
   d.image = image;
 }
 
-// the kernels of one launch sequence on stream st
-static cudaError_t launch_sequence(rr_scene* s, const ScanArgs& a, bool pattern, const LaunchCfg& cfg,
+// the side stream and events of deferred visibility (made outside any capture)
+static cudaError_t ensure_side(ExecCtx* x) {
+  if (x->side_ready) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (!x->side) e = cudaStreamCreateWithFlags(&x->side, cudaStreamNonBlocking);
+  for (int b = 0; b < RR_MAX_BOUNCES && e == cudaSuccess; ++b) {
+    if (!x->fork[b]) e = cudaEventCreateWithFlags(&x->fork[b], cudaEventDisableTiming);
+    if (e == cudaSuccess && !x->join[b]) e = cudaEventCreateWithFlags(&x->join[b], cudaEventDisableTiming);
+  }
+  x->side_ready = e == cudaSuccess;
+  return e;
+}
+
+// the kernels of one launch sequence on stream st (with deferred visibility,
+// each bounce's visibility queries on x->side, overlapping the next bounce's
+// closest-hit queries; the next shading pass waits for them)
+static cudaError_t launch_sequence(rr_scene* s, ExecCtx* x, const ScanArgs& a, bool pattern, const LaunchCfg& cfg,
                                    bool profile, cudaStream_t st) {
   cudaEvent_t ev;
   cudaError_t e;
+  const bool overlap = a.defer_vis && x->side_ready;
+  int pending = -1;   // bounce whose visibility queries run on the side stream
   if (profile) prof_begin(s, RR_K_RAYGEN, st, &ev);
   if ((e = launch_raygen(a, st)) != cudaSuccess) return e;
   if (profile) prof_end(s, ev, st);
@@ -261,17 +280,37 @@ static cudaError_t launch_sequence(rr_scene* s, const ScanArgs& a, bool pattern,
     if (profile) prof_begin(s, RR_K_TRACE, st, &ev);
     if ((e = launch_query(a, b, false, cfg, st)) != cudaSuccess) return e;
     if (profile) prof_end(s, ev, st);
-    if (b >= 1 && vis) {   // air-path visibility (Sec. III-A) from bounce 1 on
+    if (b >= 1 && vis && !a.defer_vis) {   // air-path visibility (Sec. III-A) from bounce 1 on
       if (profile) prof_begin(s, RR_K_VIS, st, &ev);
       if ((e = launch_vis_prep(a, b, st)) != cudaSuccess) return e;
       if ((e = launch_query(a, b, true, cfg, st)) != cudaSuccess) return e;
       if (profile) prof_end(s, ev, st);
     }
+    if (pending >= 0) {
+      if ((e = cudaStreamWaitEvent(st, x->join[pending], 0)) != cudaSuccess) return e;
+      pending = -1;
+    }
     if (profile) prof_begin(s, RR_K_SHADE, st, &ev);
     if ((e = launch_shade(a, b, st)) != cudaSuccess) return e;
     if (a.order_perm && b + 1 < a.max_bounces && (e = launch_order(a, b + 1, st)) != cudaSuccess) return e;
     if (profile) prof_end(s, ev, st);
+    if (b >= 1 && vis && a.defer_vis) {   // the candidates the shading pass listed, settled when visible
+      cudaStream_t sv = st;
+      if (overlap) {
+        if ((e = cudaEventRecord(x->fork[b], st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(x->side, x->fork[b], 0)) != cudaSuccess) return e;
+        sv = x->side;
+      }
+      if (profile) prof_begin(s, RR_K_VIS, sv, &ev);
+      if ((e = launch_query(a, b, true, cfg, sv)) != cudaSuccess) return e;
+      if (profile) prof_end(s, ev, sv);
+      if (overlap) {
+        if ((e = cudaEventRecord(x->join[b], x->side)) != cudaSuccess) return e;
+        pending = (int)b;
+      }
+    }
   }
+  if (pending >= 0 && (e = cudaStreamWaitEvent(st, x->join[pending], 0)) != cudaSuccess) return e;
   if (profile) prof_begin(s, RR_K_IMAGE, st, &ev);
   if ((e = launch_image(a, pattern, st)) != cudaSuccess) return e;
   if (profile) prof_end(s, ev, st);
@@ -301,7 +340,7 @@ static int graph_launch(rr_scene* s, ExecCtx* x, const ScanArgs& a, bool pattern
       cudaGetLastError();
       return cuda_fail(e, "beginning the graph capture");
     }
-    const cudaError_t le = launch_sequence(s, a, pattern, cfg, false, x->cap_stream);
+    const cudaError_t le = launch_sequence(s, x, a, pattern, cfg, false, x->cap_stream);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(x->cap_stream, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
@@ -356,7 +395,7 @@ int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor
   uint32_t* C0 = R0 + (n + 1);
   uint32_t rays = 0, cols = 0, maxb = 0, maxbins = 0, any_flags = 0;
   uint64_t tmp = 0;
-  bool pattern = false;
+  bool pattern = false, min_energy = false;
   for (uint32_t i = 0; i < n; ++i) {
     const rr_sensor_params& p = ps[i];
     const bool pat = p.az_pattern_sigma > 0.f;
@@ -371,6 +410,7 @@ int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor
     maxbins = std::max(maxbins, p.n_bins);
     any_flags |= p.flags;
     pattern = pattern || pat;
+    min_energy = min_energy || p.min_energy > 0.f;
   }
   R0[n] = rays;
   C0[n] = cols;
@@ -428,6 +468,10 @@ int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor
   a.max_bounces = maxb;
   a.max_bins = maxbins;
   a.any_flags = any_flags;
+  // deferred visibility needs the children spawned whatever their air-path
+  // return: with a min_energy cut the return decides, so the query runs first
+  a.defer_vis = (any_flags & RR_MULTIPATH) && maxb > 1 && !min_energy ? 1u : 0u;
+  a.vis_list = (uint32_t*)(w + L.off_vis);
   a.refill = cfg.refill;
   a.rays[0] = (rr::RayRec*)(w + L.off_rays0);
   a.rays[1] = (rr::RayRec*)(w + L.off_rays1);
@@ -454,11 +498,15 @@ int batch_enqueue(rr_scene* s, ExecCtx* x, const rr_pose* poses, const rr_sensor
     a.tallies = dbg->tallies;
     a.mask = dbg->mask;
   }
-  s->launches += 2u + 2u * maxb + ((any_flags & RR_MULTIPATH) && maxb > 1 ? 2u * (maxb - 1u) : 0u) +
+  s->launches += 2u + 2u * maxb + ((any_flags & RR_MULTIPATH) && maxb > 1 ? (a.defer_vis ? 1u : 2u) * (maxb - 1u) : 0u) +
                  (pattern ? 1u : 0u) + (a.order_perm ? 2u * (maxb - 1u) : 0u);
+  // without its side stream, deferred visibility runs on the launch stream
+  // (the allocation-free entry point, which stages its descriptors from the
+  // caller's stack, never creates one)
+  if (a.defer_vis && !x->side_ready && !host_desc && ensure_side(x) != cudaSuccess) cudaGetLastError();
   const bool prof = profile && s->prof;
   if (!prof && allow_graph && cfg.use_graph && !dbg) return graph_launch(s, x, a, pattern, cfg, st);
-  e = launch_sequence(s, a, pattern, cfg, prof, st);
+  e = launch_sequence(s, x, a, pattern, cfg, prof, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(e, "scan launch");

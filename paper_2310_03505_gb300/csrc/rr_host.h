@@ -57,6 +57,12 @@ struct ExecCtx {
   cudaStream_t cap_stream = nullptr;   // stream used only to capture graphs
   cudaGraphExec_t gexec = nullptr;     // last captured launch sequence
   std::vector<unsigned char> gkey;     // what gexec was captured for
+  // deferred visibility: the visibility queries of bounce b run on `side`
+  // while the closest-hit queries of bounce b + 1 run on the launch stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork[RR_MAX_BOUNCES] = {};
+  cudaEvent_t join[RR_MAX_BOUNCES] = {};
+  bool side_ready = false;
 };
 cudaError_t ctx_init(ExecCtx* x, cudaStream_t st);   // counters (zeroed)
 void ctx_free(ExecCtx* x);
@@ -181,7 +187,7 @@ void prof_end(rr_scene* s, cudaEvent_t stop, cudaStream_t st);
 // scan orchestration shared by the entry points (rr_batch.cu)
 struct WsLayout {
   uint32_t ray_cap, rec_cap, tiles, n_desc;
-  size_t off_rays0, off_rays1, off_hits, off_recs, off_status, off_tmp, off_desc, off_order, total;
+  size_t off_rays0, off_rays1, off_hits, off_vis, off_recs, off_status, off_tmp, off_desc, off_order, total;
   size_t tmp_floats;
   bool clamped;
   bool order;   // holds the closest-hit query order buffers

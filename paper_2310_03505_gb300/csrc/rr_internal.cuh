@@ -61,6 +61,20 @@ struct __align__(16) RayRec {
                 // z: path (bit 31: masked), w: scan << 16 | (medium material or kAir)
 };
 
+// An air-path candidate whose visibility is still open (Sec. III-A): what the
+// visibility query needs and what it changes once the sensor is visible.  It
+// is written over the candidate's ray record of the bounce, which the shading
+// pass has consumed (48 bytes, the size of a RayRec).
+struct __align__(16) VisJob {
+  float4 p_leaf;   // hit point, the hit leaf (bits): the query starts there
+  uint4 idx;       // scan; queue position of the child the air-path return depletes (kNone: not spawned);
+                   // position of its reserved return record (kNone: none); tally slot (kNone: no tallies)
+  float4 val;      // x: the child energy before the return is taken, y: the return, z: its image energy
+                   // (speckle and range weight applied), w: segment slot (bits; kNone: no dump)
+};
+
+static_assert(sizeof(VisJob) == sizeof(RayRec), "a VisJob takes the place of a RayRec");
+
 // hit record, 16 bytes
 struct __align__(16) HitRec {
   float t;
@@ -165,6 +179,11 @@ struct ScanArgs {
   uint32_t* order_perm;      // [ray_cap] queue index of the j-th query
   uint32_t* order_hist;      // [RR_MAX_BOUNCES + 1][kOrderBuckets] rays per bucket
   uint32_t* order_off;       // [kOrderBuckets] next free position of every bucket
+  // deferred visibility (defer_vis != 0): the shading pass lists the air-path
+  // candidates of its bounce (queue indices in vis_list, a VisJob written over
+  // each candidate's spent ray record) and the visibility query settles them
+  uint32_t defer_vis;
+  uint32_t* vis_list;        // [ray_cap]
   // debug (may be null)
   rr_segment* segs;
   uint32_t seg_cap;

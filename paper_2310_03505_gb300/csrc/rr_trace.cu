@@ -410,7 +410,9 @@ __device__ __forceinline__ void step_wide(Trav& s, uint2* stack, const ScanArgs&
 // ---------------------------------------------------------------------------
 // Queries of one bounce.  kAny = false: the closest hit of every queued ray.
 // kAny = true: the visibility test of the air-path return (Sec. III-A) for the
-// jobs k_vis_prep listed.  Persistent: a warp claims jobs in chunks and hands
+// candidates the shading pass listed (deferred visibility, which then settles
+// the visible ones), or, with a min_energy cut, for the jobs k_vis_prep listed
+// ahead of the shading pass.  Persistent: a warp claims jobs in chunks and hands
 // them to its idle lanes once at least `refill` lanes are idle (or all are),
 // so the lanes stay busy however uneven the query lengths are.
 constexpr uint32_t kClaim = 32;
@@ -438,6 +440,30 @@ __device__ __forceinline__ float rx_weight(const ScanDesc* sd, uint32_t az, floa
     if (perp2 > 0.0f) q *= (c_a * c_a + c_e * c_e / (aspect * aspect)) / perp2;
   }
   return sigma > 0.0f ? expf(-0.5f * q) : 0.0f;
+}
+
+// Deferred visibility: the sensor is visible from candidate i of a bounce,
+// so its air-path return is taken (Sec. III-A; returns deplete the ray): the
+// reserved record gets its energy and the child it depletes (or, when the
+// child was not spawned, the terminated tally) loses it; the debug dump and
+// tallies are patched like the shading pass would have written them.
+__device__ __noinline__ void settle_air_path(const ScanArgs& a, uint32_t bounce, uint32_t i) {
+  const VisJob* jp = reinterpret_cast<const VisJob*>(a.rays[bounce & 1]) + i;
+  const uint4 ix = jp->idx;
+  const float4 v = jp->val;
+  const float e_child = fmaxf(v.x - v.y, 0.0f);
+  if (ix.y != kNone) a.rays[(bounce + 1) & 1][ix.y].d_E.w = e_child;
+  if (ix.z != kNone) a.recs[ix.z].y = __float_as_uint(v.z);
+  if (ix.w != kNone && a.tallies != nullptr) {
+    float* tp = a.tallies + 4 * (size_t)ix.w;
+    atomicAdd(tp, v.y);
+    if (ix.y == kNone) atomicAdd(tp + 3, e_child - fmaxf(v.x, 0.0f));
+  }
+  const uint32_t si = __float_as_uint(v.w);
+  if (si != kNone && a.segs != nullptr && si < a.seg_cap) {
+    a.segs[si].flags |= 2u;
+    a.segs[si].ret_a = v.y;
+  }
 }
 
 // Steps a busy lane takes between two looks at the warp's idle lanes.  The
@@ -507,7 +533,16 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
         }
       }
       if (job != kNone) {
-        if (kAny) {
+        if (kAny && a.defer_vis) {
+          ray_i = a.vis_list[job];
+          const float4 pl = reinterpret_cast<const VisJob*>(q)[ray_i].p_leaf;
+          const uint32_t scan = min(reinterpret_cast<const VisJob*>(q)[ray_i].idx.x, a.n_scans - 1u);
+          const ScanDesc* sd = a.desc + scan;
+          const float3 p = f3(pl);
+          const float3 v = f3(__ldg(&sd->pos_rmax)) - p;
+          const float dist = length(v);
+          trav_begin(s, p, (1.0f / dist) * v, __ldg(&sd->phys.x), dist, __float_as_uint(pl.w), a.n_tris, kWide);
+        } else if (kAny) {
           const uint2 jb = jobs[job];
           ray_i = jb.x;
           wa = __uint_as_float(jb.y);
@@ -553,7 +588,9 @@ __global__ void __launch_bounds__(kBlock) k_query(ScanArgs a, uint32_t bounce) {
         s.node = kNone;
       }
       if (s.node == kNone) {   // the query has ended
-        if (kAny) {
+        if (kAny && a.defer_vis) {
+          if (s.best == kNone) settle_air_path(a, bounce, ray_i);
+        } else if (kAny) {
           HitRec* hp = a.hits + ray_i;
           uint32_t fl = hp->flags | 1u;
           float wag = 0.0f;
@@ -826,7 +863,7 @@ __global__ void __launch_bounds__(kShadeBlock, kMinBlocks) k_shade(ScanArgs a, u
   const uint32_t tiles = (n + kShadeBlock - 1) / kShadeBlock;
   const uint32_t rec0 = a.ctr->rec_start[bounce];
   const uint32_t seg0 = a.ctr->seg_start[bounce];
-  const RayRec* __restrict__ qin = a.rays[bounce & 1];
+  const RayRec* qin = a.rays[bounce & 1];   // not restrict: deferred visibility writes its jobs over it
   RayRec* __restrict__ qout = a.rays[(bounce + 1) & 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (n == 0) {
@@ -850,6 +887,8 @@ __global__ void __launch_bounds__(kShadeBlock, kMinBlocks) k_shade(ScanArgs a, u
     RayRec kid[2];
     uint2 rec[2];
     uint32_t nk = 0, nr = 0;
+    bool cand = false;           // an air-path candidate left to the visibility query (deferred visibility)
+    int vj_kid = -1, vj_rec = -1;   // its child in kid[], its record in rec[] (-1: none)
     if (i < n) {
       const RayRec ray = qin[i];
       const HitRec h = a.hits[i];
@@ -919,9 +958,35 @@ __global__ void __launch_bounds__(kShadeBlock, kMinBlocks) k_shade(ScanArgs a, u
         // traveled-path return: omega = theta0 + theta1 = 2 theta0, range L1
         const float theta0 = angle_between(d, -nrm);
         const float ret_t = E1 * R * fminf(brdf_window(m, lut, 2.0f * theta0, beam.x), 1.0f);
-        float ret_a = 0.0f, range_a = 0.0f;
+        float ret_a = 0.0f, range_a = 0.0f, e_rec = 0.0f;
         bool air_T = false;
-        const float wag = h.wa_g > 0.0f ? h.wa_g * rx_weight(sd, az, p) : 0.0f;
+        // the air-path candidate (Sec. III-A): its window W is open toward the
+        // sensor; with deferred visibility it is found here, else the
+        // visibility query has run and left W in the hit record when visible
+        float wag = 0.0f;
+        if (a.defer_vis) {
+          if (bounce >= 1u && (rng.w & RR_MULTIPATH)) {
+            const float3 v = s_pos - p;
+            const float side = dot(v, nrm);
+            float3 dir_out = d_refl;
+            bool c = false;
+            if (entering && medium == kAir) {
+              c = side > 0.0f;
+            } else if (!entering && medium != kAir && can_refract) {
+              dir_out = normalize(eta * d + (eta * cos_i - cos_t) * nrm);
+              c = side < 0.0f;
+            }
+            if (c) {
+              const float wa = brdf_window(m, lut, angle_between(dir_out, v), beam.x);
+              if (wa > 0.0f) {
+                cand = true;
+                wag = wa * rx_weight(sd, az, p);
+              }
+            }
+          }
+        } else if (h.wa_g > 0.0f) {
+          wag = h.wa_g * rx_weight(sd, az, p);
+        }
         if (wag > 0.0f) {
           float base, cap;
           if (entering && medium == kAir) {
@@ -935,10 +1000,13 @@ __global__ void __launch_bounds__(kShadeBlock, kMinBlocks) k_shade(ScanArgs a, u
           ret_a = fmaxf(fminf(base * wag, cap), 0.0f);
           range_a = 0.5f * (L1 + length(s_pos - p));
         }
-        tal[0] = ret_t + ret_a;
+        // a candidate's return is taken once its visibility is known: until
+        // then the ray gives nothing to the air path
+        const float ret_a_now = cand ? 0.0f : ret_a;
+        tal[0] = ret_t + ret_a_now;
         dbg_cos = cos_i;
         dbg_ret_t = ret_t;
-        dbg_ret_a = ret_a;
+        dbg_ret_a = ret_a_now;
         if (!masked) {
           if (ret_t > 0.0f) {
             const float bin = floorf(L1 / beam.w);
@@ -955,12 +1023,17 @@ __global__ void __launch_bounds__(kShadeBlock, kMinBlocks) k_shade(ScanArgs a, u
               float e = ret_a;
               if (rng.w & RR_SPECKLE) e *= -logf(u01(draw(rng, az, k, 1u | (((path << 8) | bounce) << 8)).y));
               e *= range_weight(sd, range_a);
-              rec[nr++] = make_uint2(((offs.y + az - offs.w) << kBinBits) | (uint32_t)bin, __float_as_uint(e));
+              if (cand) {   // reserved with energy 0, written if the sensor is visible
+                e_rec = e;
+                vj_rec = (int)nr;
+              }
+              rec[nr++] =
+                  make_uint2(((offs.y + az - offs.w) << kBinBits) | (uint32_t)bin, cand ? 0u : __float_as_uint(e));
             }
           }
         }
-        const float e_refl = fmaxf(E1 * R - ret_t - (air_T ? 0.0f : ret_a), 0.0f);
-        const float e_refr = fmaxf(E1 * T - (air_T ? ret_a : 0.0f), 0.0f);
+        const float e_refl = fmaxf(E1 * R - ret_t - (air_T ? 0.0f : ret_a_now), 0.0f);
+        const float e_refr = fmaxf(E1 * T - (air_T ? ret_a_now : 0.0f), 0.0f);
         const bool in_range = L1 < pr.w;
         const bool sp_refl = deeper && in_range && e_refl >= phys.y;
         const bool sp_refr = deeper && in_range && can_refract && (rng.w & RR_REFRACTION) && e_refr >= phys.y;
@@ -980,6 +1053,16 @@ __global__ void __launch_bounds__(kShadeBlock, kMinBlocks) k_shade(ScanArgs a, u
           c.d_E = make_float4(d_refr.x, d_refr.y, d_refr.z, e_refr);
           c.meta = make_uint4(h.leaf, ray.meta.y, mbit | (path << 1) | 1u, (scan << 16) | next_med);
         }
+        if (cand) {   // the job, over this ray's record (read above, not read again)
+          vj_kid = air_T ? (sp_refr ? (sp_refl ? 1 : 0) : -1) : (sp_refl ? 0 : -1);
+          VisJob j;
+          j.p_leaf = make_float4(p.x, p.y, p.z, __uint_as_float(h.leaf));
+          j.idx = make_uint4(scan, kNone, kNone,
+                             a.tallies != nullptr ? offs.x + (az - offs.w) * dims.y + k : kNone);
+          j.val = make_float4(air_T ? E1 * T : E1 * R - ret_t, ret_a, e_rec,
+                              __uint_as_float(a.segs != nullptr ? seg0 + i : kNone));
+          reinterpret_cast<VisJob*>(a.rays[bounce & 1])[i] = j;
+        }
       }
       if (a.tallies != nullptr) {
         float* tp = a.tallies + 4 * ((size_t)offs.x + (size_t)(az - offs.w) * dims.y + k);
@@ -997,7 +1080,7 @@ __global__ void __launch_bounds__(kShadeBlock, kMinBlocks) k_shade(ScanArgs a, u
           sg.tri = orig;
           sg.t = h.leaf == kNone ? INFINITY : h.t;
           sg.E = E;
-          sg.flags = h.flags & 0xFFu;
+          sg.flags = (h.flags & 0xFFu) | (cand ? 1u : 0u);   // bit 0: visibility tested, bit 1: visible
           sg.cos_i = dbg_cos;
           sg.ret_t = dbg_ret_t;
           sg.ret_a = dbg_ret_a;
@@ -1031,6 +1114,26 @@ __global__ void __launch_bounds__(kShadeBlock, kMinBlocks) k_shade(ScanArgs a, u
     __syncthreads();
     const uint2 ex = s_excl;
     const uint32_t kbase = ex.x + (local & 0xFFFFu), rbase = ex.y + (local >> 16);
+    if (a.defer_vis) {
+      // the candidates' child and record positions, and the list of jobs
+      // (one atomic per warp; the order of the list does not matter)
+      const uint32_t vm = __ballot_sync(0xFFFFFFFFu, cand);
+      if (vm) {
+        uint32_t b0 = 0;
+        if (lane == __ffs(vm) - 1) b0 = atomicAdd(&a.ctr->vis_count[bounce], (uint32_t)__popc(vm));
+        b0 = __shfl_sync(0xFFFFFFFFu, b0, __ffs(vm) - 1);
+        if (cand) {
+          uint32_t cpos = vj_kid >= 0 ? kbase + (uint32_t)vj_kid : kNone;
+          uint32_t rpos = vj_rec >= 0 ? rec0 + rbase + (uint32_t)vj_rec : kNone;
+          if (cpos != kNone && cpos >= a.ray_cap) cpos = kNone;   // not written: the scan reports the overflow
+          if (rpos != kNone && rpos >= a.rec_cap) rpos = kNone;
+          VisJob* jw = reinterpret_cast<VisJob*>(a.rays[bounce & 1]) + i;
+          jw->idx.y = cpos;
+          jw->idx.z = rpos;
+          a.vis_list[b0 + (uint32_t)__popc(vm & ((1u << lane) - 1u))] = i;
+        }
+      }
+    }
     for (uint32_t c = 0; c < nk; ++c) {
       const uint32_t pos = kbase + c;
       if (pos < a.ray_cap) qout[pos] = kid[c];

@@ -32,7 +32,8 @@ def worst_case_bytes(ps):
     tmp = sum(p["n_azimuth"] * p["n_bins"] for p in ps if p["az_pattern_sigma"] > 0)
     tiles = (q + 255) // 256 + 1
     desc = len(ps) * 160 + 2 * (len(ps) + 1) * 4
-    return 2 * a256(q * 48) + a256(q * 16) + a256(r * 8) + a256(tiles * 8) + a256(tmp * 4) + a256(desc)
+    # ray queues (x2), hits, the list of air-path candidates, records, tile flags, images, descriptors
+    return 2 * a256(q * 48) + a256(q * 16) + a256(q * 4) + a256(r * 8) + a256(tiles * 8) + a256(tmp * 4) + a256(desc)
 
 
 def test_empty_request(lib):
