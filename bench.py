@@ -452,10 +452,15 @@ def served_bench(device, seconds: float = 60.0, rates=(30, 60, 120, 240), rank: 
     out = {"workload": SERVED_WORKLOAD, "seconds_per_rate": seconds, "seconds_short": short_seconds,
            "admission": "estimate of the ray tree per scene (x2), worst case on the first batch and on overflow",
            "scenes_triangles": [sc.n_triangles for sc, _ in scs], "robots": 64, "bvh": bvh,
-           "server": {k: int(v) for k, v in served.items()}, "rates": [], "per_scan_path": []}
+           "server": {k: int(v) for k, v in served.items()}, "rates": [], "per_scan_path": [],
+           "rates_same_window": [],
+           "same_window_note": "the batching server over the same short window and arrival trace (same seed) as "
+                               "the one-at-a-time server: the like-for-like latency comparison"}
     for k, rate in enumerate(rates):
         out["rates"].append(run(served, rate, 1000 + k, seconds if rate <= 120 else short_seconds))
         out["per_scan_path"].append(run(plain, rate, 1000 + k, short_seconds))
+        if rate <= 120 and seconds != short_seconds:
+            out["rates_same_window"].append(run(served, rate, 1000 + k, short_seconds))
     for h in hs:
         rr.rr_scene_destroy(h)
     return out
