@@ -25,7 +25,7 @@ struct ProfEvent {
 // tunables of the batched launch sequence (rr_batch_config)
 struct LaunchCfg {
   uint32_t wavefront_rays = 0;        // most initial rays per launch sequence, 0: workspace limit only
-  uint32_t trace_block = 128;         // 64, 128 or 256
+  uint32_t trace_block = 64;          // 64, 128 or 256
   uint32_t trace_blocks_per_sm = 0;   // 0: occupancy maximum
   uint32_t use_graph = 1;             // capture each launch sequence once and replay it
   uint32_t node_format = RR_NODES_BINARY;
