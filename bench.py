@@ -640,6 +640,16 @@ def roofline(res: dict, peak: float, peak_kind: str, counters, l2_peak: float | 
          "busy_ms_per_step": busy / max(res["steps"], 1),
          "dram_gbs": traffic / (ms_launch * 1e-3) / 1e9 if traffic and ms_launch > 0 else None}
     r["dram_frac"] = r["dram_gbs"] / peak if r["dram_gbs"] else None
+    step_ms = res.get("ms_per_step")
+    if step_ms:
+        # context: each closest-hit launch shares the GPU with the previous
+        # bounce's visibility queries (a second stream), which its event
+        # duration counts too; over a whole step nothing is counted twice
+        per_step = algo / max(res["steps"], 1)
+        r["per_step"] = {"achieved": per_step / (step_ms * 1e-3) / 1e9, "frac": per_step / (step_ms * 1e-3) / 1e9 / peak,
+                         "algorithmic_bytes": per_step, "ms": step_ms,
+                         "note": "the closest-hit queries' algorithmic bytes of one step over the whole step time "
+                                 "(rebuild, shading and visibility included)"}
     if counters:
         r["counters"] = {k: counters[k] for k in ("profile", "launches_captured", "scaling") if k in counters}
     if l2_peak:
@@ -737,10 +747,11 @@ def main():
                   campus_note) if args.no_large else \
         roofline(head, peak, peak_kind, profile_counters("query_kernel_city_ncu"), l2_peak, "latency",
                   "the city's BVH and triangles (~0.56 GB) exceed the 129 MB L2, yet the dependent node fetches "
-                  "are served by L1 (81-83 % hit) and L2 (73-75 %): the kernel is bound by their latency, with L1 "
-                  "throughput the nearest limit (70-78 % of peak) and DRAM under 3 %.  achieved counts the "
+                  "are served by L1 (79-81 % hit) and L2 (77-79 %): the kernel is bound by their latency, with L1 "
+                  "throughput the nearest limit (53-74 % of peak) and DRAM about 3 %.  achieved counts the "
                   "algorithmic node/triangle/record bytes of a launch over its CUDA-event duration (the launches "
-                  "of the 3 azimuth ranges overlap on their streams), against the HBM copy peak; dram_gbs and "
+                  "of the 3 azimuth ranges and the previous bounce's visibility queries overlap them), against the HBM copy "
+                  "peak; per_step divides a step's closest-hit bytes by the step time; dram_gbs and "
                   "l2.achieved divide the bytes ncu measured for the same kernel source by that duration")
 
     medium = None
