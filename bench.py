@@ -360,7 +360,7 @@ SERVED_WORKLOAD = "4_scenes_50k_200k_1M_5M_tris_64_robots_poisson_16_512_rays_3_
 
 
 def served_bench(device, seconds: float = 60.0, rates=(30, 60, 120, 240), rank: int = 0, bvh: str = "sah_top",
-                 city=None, short_seconds: float = 10.0):
+                 city=None, short_seconds: float = 10.0, served_cfg=None):
     """Scan requests from 64 simulated robots over 4 resident scenes (50k and
     200k-triangle campuses, the 1M-triangle campus, the 5M-triangle city),
     Poisson arrivals at each rate for `seconds`; every request draws a free
@@ -447,7 +447,7 @@ def served_bench(device, seconds: float = 60.0, rates=(30, 60, 120, 240), rank: 
                 "requests_per_batch": st["completed"] / max(st["batches"], 1), "retried": int(st["retried"]),
                 "window_s": win}
 
-    served = dict(slots=4, memory_budget=96 << 30, max_batch_scans=64, max_batch_rays=8 << 20)
+    served = served_cfg or dict(slots=4, memory_budget=96 << 30, max_batch_scans=64, max_batch_rays=8 << 20)
     plain = dict(slots=1, memory_budget=24 << 30, max_batch_scans=1)
     out = {"workload": SERVED_WORKLOAD, "seconds_per_rate": seconds, "seconds_short": short_seconds,
            "admission": "estimate of the ray tree per scene (x2), worst case on the first batch and on overflow",
