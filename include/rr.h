@@ -232,6 +232,19 @@ int rr_set_stream(void* cuda_stream);
 #define RR_WAIT_SHADE_PREFIX 2u
 int rr_selftest_wait(uint32_t which, double* waited_ms);
 
+/* Failure detection, host-side fault injection (no counterpart in the paper:
+   the library's own failure handling).  Every device and pinned host
+   allocation the library makes passes one gate.  fail_at >= 0 arms it: the
+   allocations go on until fail_at more have passed, and the next one fails
+   as if the device were out of memory (no CUDA call is made for it), after
+   which the gate is disarmed again; fail_at < 0 disarms it.  The call that
+   met the failure returns RR_ERR_OOM with a message naming what it was
+   allocating, frees what it had allocated and leaves the library usable.
+   *allocs_seen (may be NULL) receives the number of allocations that passed
+   the gate since the previous call, so a test can count how many an
+   operation makes.  Process-wide (all threads and devices); for tests. */
+int rr_fault_inject_alloc(int64_t fail_at, uint64_t* allocs_seen);
+
 /* ---------------------------------------------------------------------- */
 /* scene: ingest + LBVH (Sec. III-D: the scene mesh with per-triangle      */
 /* materials; the hierarchy is this library's own, 30-bit Morton codes,    */

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -30,6 +31,35 @@ cudaStream_t current_stream() { return t_stream; }
 int fail(int code, const std::string& msg) {
   set_error(msg);
   return code;
+}
+
+// host-side fault injection: the number of allocations still to let pass
+// before one fails (-1: off), and the allocations seen since the last query
+static std::atomic<int64_t> g_alloc_countdown{-1};
+static std::atomic<uint64_t> g_allocs_seen{0};
+
+static bool injected_alloc_failure() {
+  g_allocs_seen.fetch_add(1, std::memory_order_relaxed);
+  int64_t c = g_alloc_countdown.load();
+  while (c >= 0)
+    if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 0;   // the armed one fails, then off
+  return false;
+}
+
+cudaError_t dev_malloc_raw(void** p, size_t n) {
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, n);
+}
+
+cudaError_t host_malloc_raw(void** p, size_t n) {
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, n);
 }
 
 int cuda_fail(cudaError_t e, const char* what) {
@@ -219,8 +249,8 @@ int scene_status(rr_scene* s, cudaStream_t st) {
 }
 
 cudaError_t ctx_init(ExecCtx* x, cudaStream_t st) {
-  cudaError_t e = cudaMalloc((void**)&x->d_ctr, sizeof(ScanCounters));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&x->h_ctr, sizeof(ScanCounters));
+  cudaError_t e = dev_malloc((void**)&x->d_ctr, sizeof(ScanCounters));
+  if (e == cudaSuccess) e = host_malloc((void**)&x->h_ctr, sizeof(ScanCounters));
   if (e == cudaSuccess) memset(x->h_ctr, 0, sizeof(ScanCounters));   // the mirror starts equal to the device
   if (e == cudaSuccess) e = cudaMemsetAsync(x->d_ctr, 0, sizeof(ScanCounters), st);
   return e;
@@ -280,12 +310,18 @@ int rr_set_stream(void* cuda_stream) {
   return RR_OK;
 }
 
+int rr_fault_inject_alloc(int64_t fail_at, uint64_t* allocs_seen) {
+  if (allocs_seen) *allocs_seen = g_allocs_seen.exchange(0);
+  g_alloc_countdown.store(fail_at < 0 ? -1 : fail_at);
+  return RR_OK;
+}
+
 int rr_selftest_wait(uint32_t which, double* waited_ms) {
   if (which > RR_WAIT_SHADE_PREFIX) return fail(RR_ERR_INVALID_ARG, "rr_selftest_wait: unknown wait");
   const cudaStream_t st = t_stream;
   const size_t bytes = 256 + sizeof(ScanCounters);   // the largest arrangement, zeroed
   void* scratch = nullptr;
-  RR_CHECK_CUDA(cudaMalloc(&scratch, bytes), "allocating the self-test scratch");
+  RR_CHECK_CUDA(dev_malloc(&scratch, bytes), "allocating the self-test scratch");
   const auto t0 = std::chrono::steady_clock::now();
   bool gave_up = false;
   cudaError_t e = cudaMemsetAsync(scratch, 0, bytes, st);
@@ -520,7 +556,7 @@ int rr_scene_set_lobe(rr_scene* s, uint32_t material, const float* density) {
   cudaStream_t st = t_stream;
   if (!s->d_lobe_samples) {
     const size_t bytes = (size_t)s->nm * rr::kLobeSamples * sizeof(float);
-    RR_CHECK_CUDA(cudaMalloc(&s->d_lobe_samples, bytes), "allocating the lobe samples");
+    RR_CHECK_CUDA(dev_malloc(&s->d_lobe_samples, bytes), "allocating the lobe samples");
     RR_CHECK_CUDA(cudaMemsetAsync(s->d_lobe_samples, 0, bytes, st), "clearing the lobe samples");
   }
   RR_CHECK_CUDA(cudaMemcpyAsync(s->d_lobe_samples + (size_t)material * rr::kLobeSamples, h.data(),
@@ -612,15 +648,15 @@ int rr_scan_debug(rr_scene* s, const rr_pose* pose, const rr_sensor_params* p, c
     cleanup();
     return cuda_fail(e, what);
   };
-  if ((rc = check(cudaMalloc(&d_img, img_bytes), "debug image")) != RR_OK) return rc;
+  if ((rc = check(dev_malloc(&d_img, img_bytes), "debug image")) != RR_OK) return rc;
   if (segs && seg_capacity)
-    if ((rc = check(cudaMalloc(&d_segs, seg_capacity * sizeof(rr_segment)), "debug segments")) != RR_OK) return rc;
+    if ((rc = check(dev_malloc(&d_segs, seg_capacity * sizeof(rr_segment)), "debug segments")) != RR_OK) return rc;
   if (ray_tallies) {
-    if ((rc = check(cudaMalloc(&d_tal, n0 * 4 * sizeof(float)), "debug tallies")) != RR_OK) return rc;
+    if ((rc = check(dev_malloc(&d_tal, n0 * 4 * sizeof(float)), "debug tallies")) != RR_OK) return rc;
     if ((rc = check(cudaMemsetAsync(d_tal, 0, n0 * 4 * sizeof(float), st), "debug tallies")) != RR_OK) return rc;
   }
   if (ray_mask) {
-    if ((rc = check(cudaMalloc(&d_mask, n0), "debug mask")) != RR_OK) return rc;
+    if ((rc = check(dev_malloc(&d_mask, n0), "debug mask")) != RR_OK) return rc;
     if ((rc = check(cudaMemcpyAsync(d_mask, ray_mask, n0, cudaMemcpyDefault, st), "debug mask")) != RR_OK) return rc;
   }
   DebugOut dbg;

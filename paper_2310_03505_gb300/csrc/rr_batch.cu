@@ -169,7 +169,7 @@ int ensure_workspace(ExecCtx* x, size_t bytes, cudaStream_t st) {
   x->ws = nullptr;
   x->ws_bytes = 0;
   x->gkey.clear();   // a captured graph points into the old workspace
-  e = cudaMalloc(&x->ws, bytes);
+  e = dev_malloc(&x->ws, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(e, "allocating the scan workspace");
@@ -188,7 +188,7 @@ int ensure_image(ExecCtx* x, size_t bytes, cudaStream_t st) {
   if (x->d_image) cudaFree(x->d_image);
   x->d_image = nullptr;
   x->image_bytes = 0;
-  e = cudaMalloc(&x->d_image, bytes);
+  e = dev_malloc(&x->d_image, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(e, "allocating the image buffer");
@@ -220,7 +220,7 @@ static int stage_acquire(ExecCtx* x, size_t bytes) {
     x->h_stage = nullptr;
     x->stage_bytes = 0;
     const size_t want = std::max<size_t>(bytes, 4096);
-    cudaError_t e = cudaMallocHost(&x->h_stage, want);
+    cudaError_t e = host_malloc(&x->h_stage, want);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return cuda_fail(e, "allocating the descriptor staging");
@@ -760,7 +760,7 @@ int rr_autotune(rr_scene* s, uint32_t n, const rr_pose* poses, const rr_sensor_p
     rays += (uint64_t)params[i].n_azimuth * params[i].rays_per_beam;
   }
   float* d_out = nullptr;
-  cudaError_t e = cudaMalloc(&d_out, total * sizeof(float));
+  cudaError_t e = dev_malloc(&d_out, total * sizeof(float));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(e, "allocating the autotuner's images");

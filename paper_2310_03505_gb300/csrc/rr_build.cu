@@ -1903,7 +1903,7 @@ cudaError_t build_alloc(rr_scene* s) {
       return cudaSuccess;
     }
     bytes += n;
-    return cudaMalloc(p, n);
+    return dev_malloc(p, n);
   };
   s->sort_tiles = (uint32_t)((T + kSortTile - 1) / kSortTile);
   RR_TRY(alloc((void**)&s->d_vtx, V * 3 * sizeof(float)));
@@ -1969,7 +1969,7 @@ static cudaError_t top_alloc(rr_scene* s) {
   size_t bytes = 0;
   auto alloc = [&](void** p, size_t n) -> cudaError_t {
     bytes += n;
-    return cudaMalloc(p, n);
+    return dev_malloc(p, n);
   };
   RR_TRY(alloc((void**)&s->d_cl_at, T * sizeof(uint32_t)));
   RR_TRY(alloc((void**)&s->d_cl_bsum, nb4 * sizeof(uint32_t)));

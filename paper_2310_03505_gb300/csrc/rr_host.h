@@ -205,6 +205,19 @@ struct Group {
 };
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
+// Every device and pinned host allocation of the library goes through these
+// two, so that rr_fault_inject_alloc can make a chosen one fail (as
+// cudaErrorMemoryAllocation, without calling CUDA).
+cudaError_t dev_malloc_raw(void** p, size_t n);
+cudaError_t host_malloc_raw(void** p, size_t n);
+template <class T>
+cudaError_t dev_malloc(T** p, size_t n) {
+  return dev_malloc_raw(reinterpret_cast<void**>(p), n);
+}
+template <class T>
+cudaError_t host_malloc(T** p, size_t n) {
+  return host_malloc_raw(reinterpret_cast<void**>(p), n);
+}
 bool is_device_ptr(const void* p);
 int check_params(const rr_pose* pose, const rr_sensor_params* p);
 // RR_ERR_INVALID_ARG unless the current device is the scene's (who: caller name for the message)

@@ -307,15 +307,15 @@ extern "C" int rr_accumulate_returns(const uint32_t* column, const uint32_t* bin
   };
   cudaError_t e = cudaSuccess;
   const size_t nn = n ? n : 1;
-  if (e == cudaSuccess) e = cudaMalloc(&d_col, nn * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&d_bin, nn * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&d_e, nn * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&d_recs, nn * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&d_bad, 4);
-  if (e == cudaSuccess) e = cudaMalloc(&d_img, img_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&d_ctr, sizeof(ScanCounters));
-  if (e == cudaSuccess) e = cudaMalloc(&d_desc, sizeof(ScanDesc));
-  if (e == cudaSuccess) e = cudaMalloc(&d_pre, 4 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = dev_malloc(&d_col, nn * 4);
+  if (e == cudaSuccess) e = dev_malloc(&d_bin, nn * 4);
+  if (e == cudaSuccess) e = dev_malloc(&d_e, nn * 4);
+  if (e == cudaSuccess) e = dev_malloc(&d_recs, nn * 8);
+  if (e == cudaSuccess) e = dev_malloc(&d_bad, 4);
+  if (e == cudaSuccess) e = dev_malloc(&d_img, img_bytes);
+  if (e == cudaSuccess) e = dev_malloc(&d_ctr, sizeof(ScanCounters));
+  if (e == cudaSuccess) e = dev_malloc(&d_desc, sizeof(ScanDesc));
+  if (e == cudaSuccess) e = dev_malloc(&d_pre, 4 * sizeof(uint32_t));
   if (e == cudaSuccess && n) e = cudaMemcpyAsync(d_col, column, n * 4, cudaMemcpyDefault, st);
   if (e == cudaSuccess && n) e = cudaMemcpyAsync(d_bin, bin, n * 4, cudaMemcpyDefault, st);
   if (e == cudaSuccess && n) e = cudaMemcpyAsync(d_e, energy, n * 4, cudaMemcpyDefault, st);

@@ -394,7 +394,7 @@ int rr_serve_create(const rr_serve_config* config, rr_server** out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = ctx_init(&sl.ctx, sl.stream);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&sl.arena, arena);
+    if (e == cudaSuccess) e = dev_malloc((void**)&sl.arena, arena);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sl.stream);
     sl.arena_bytes = arena;
   }

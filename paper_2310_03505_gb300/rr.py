@@ -126,6 +126,7 @@ SIGNATURES = {
     "rr_last_error": ([], C.c_char_p),
     "rr_set_stream": ([_P], C.c_int),
     "rr_selftest_wait": ([C.c_uint32, C.POINTER(C.c_double)], C.c_int),
+    "rr_fault_inject_alloc": ([C.c_int64, C.POINTER(C.c_uint64)], C.c_int),
     "rr_scene_create": ([_P, C.c_uint32, _P, C.c_uint32, _P, _P, C.c_uint32, C.POINTER(_P)], C.c_int),
     "rr_scene_destroy": ([_P], C.c_int),
     "rr_scene_update_vertices": ([_P, _P], C.c_int),
@@ -253,6 +254,15 @@ def rr_last_error() -> str:
 
 def rr_set_stream(stream_handle) -> None:
     _check(load().rr_set_stream(C.c_void_p(stream_handle)))
+
+
+def rr_fault_inject_alloc(fail_at: int) -> int:
+    """Arms (fail_at >= 0: that many more allocations pass, the next fails)
+    or disarms (fail_at < 0) the library's allocation fault injection;
+    returns the allocations that passed the gate since the previous call."""
+    seen = C.c_uint64(0)
+    _check(load().rr_fault_inject_alloc(C.c_int64(int(fail_at)), C.byref(seen)))
+    return int(seen.value)
 
 
 def rr_selftest_wait(which: int):
