@@ -48,6 +48,7 @@ extern "C" {
 #define RR_ERR_TIMEOUT 4     /* a bounded device wait gave up                           */
 #define RR_ERR_CUDA 5        /* a CUDA runtime call failed                              */
 #define RR_ERR_BUSY 6        /* the request cannot be admitted now                      */
+#define RR_ERR_CANCELLED 7   /* the request was cancelled before it ran                 */
 
 /* sensor flags (rr_sensor_params.flags) */
 #define RR_MULTIPATH 1u  /* air-path returns, Sec. III-A ("multi-path reflection")   */
@@ -542,6 +543,7 @@ typedef struct {
 #define RR_REQ_RUNNING 1
 #define RR_REQ_DONE 2
 #define RR_REQ_FAILED 3
+#define RR_REQ_CANCELLED 4   /* cancelled while queued: it never ran, out_polar untouched */
 
 /* One request: state, status (RR_OK or the failure), times in ms of the
    host steady clock since the server was created: submitted, launched,
@@ -567,7 +569,7 @@ typedef struct {
   double busy_ms, elapsed_ms;
   double latency_p50_ms, latency_p99_ms, latency_mean_ms, latency_max_ms;
   uint64_t retried;   /* requests rerun at worst-case size after their estimated batch overflowed */
-  uint64_t reserved;
+  uint64_t cancelled; /* requests cancelled while queued (rr_serve_cancel) */
 } rr_serve_stats;
 
 /* Starts a server (its worker thread and slots) on the current device.
@@ -597,6 +599,18 @@ int rr_serve_wait(rr_server* server, uint64_t ticket, uint32_t timeout_ms);
 
 /* The request's record; a finished request's ticket is then forgotten. */
 int rr_serve_result(rr_server* server, uint64_t ticket, rr_serve_record* out);
+
+/* Cancels a request that is still queued: it never runs, its out_polar is
+   not written, and it finishes at once as RR_REQ_CANCELLED (rr_serve_wait
+   returns RR_ERR_CANCELLED; its record can be read as for any finished
+   request).  *cancelled = 1 then.  A request already launched (its batch
+   is on the GPU) or finished is left as it is, *cancelled = 0: a launched
+   batch is not interrupted, and its outputs are written.  A request queued
+   again to rerun at worst-case size is queued and can be cancelled.
+   RR_ERR_INVALID_ARG for an unknown ticket.  Non-blocking.  (No counterpart
+   in the paper: serving clients such as robots that move on abandon scans
+   they no longer need.) */
+int rr_serve_cancel(rr_server* server, uint64_t ticket, int* cancelled);
 
 /* Server statistics (see rr_serve_stats); reset != 0 starts a new window. */
 int rr_serve_stats_get(rr_server* server, rr_serve_stats* out, int reset);

@@ -61,6 +61,11 @@ struct Request {
   bool worst = false;   // size its batch for the worst-case tree (a retry after an overflow)
 };
 
+// completed, failed or cancelled: nothing of it is left on the device
+inline bool req_finished(const Request& r) {
+  return r.state == RR_REQ_DONE || r.state == RR_REQ_FAILED || r.state == RR_REQ_CANCELLED;
+}
+
 // largest queue length and return records per initial ray seen at every
 // bounce of a scene's batches
 struct Growth {
@@ -100,7 +105,7 @@ struct rr_server {
   bool stop = false;
   std::thread worker;
   // statistics since the last reset
-  uint64_t submitted = 0, completed = 0, failed = 0, rejected = 0, batches = 0, retried = 0;
+  uint64_t submitted = 0, completed = 0, failed = 0, rejected = 0, batches = 0, retried = 0, cancelled = 0;
   uint64_t closest = 0, anyhit = 0, rays0 = 0;
   double stats_t0 = 0, busy_ms = 0;
   std::vector<double> latencies;
@@ -469,12 +474,33 @@ int rr_serve_submit(rr_server* sv, rr_scene* scene, const rr_pose* pose, const r
   return RR_OK;
 }
 
+int rr_serve_cancel(rr_server* sv, uint64_t ticket, int* cancelled) {
+  if (!sv || !cancelled) return fail(RR_ERR_INVALID_ARG, "NULL argument");
+  *cancelled = 0;
+  {
+    std::lock_guard<std::mutex> g(sv->mu);   // the worker forms batches under this lock
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return fail(RR_ERR_INVALID_ARG, "unknown ticket");
+    Request& r = it->second;
+    if (r.state != RR_REQ_QUEUED) return RR_OK;
+    auto q = std::find(sv->pending.begin(), sv->pending.end(), ticket);
+    if (q != sv->pending.end()) sv->pending.erase(q);
+    r.state = RR_REQ_CANCELLED;
+    r.status = RR_ERR_CANCELLED;
+    r.done_ms = now_ms(sv);
+    ++sv->cancelled;
+    *cancelled = 1;
+  }
+  sv->cv_done.notify_all();
+  return RR_OK;
+}
+
 int rr_serve_poll(rr_server* sv, uint64_t ticket, int* done) {
   if (!sv || !done) return fail(RR_ERR_INVALID_ARG, "NULL argument");
   std::lock_guard<std::mutex> g(sv->mu);
   auto it = sv->reqs.find(ticket);
   if (it == sv->reqs.end()) return fail(RR_ERR_INVALID_ARG, "unknown ticket");
-  *done = (it->second.state == RR_REQ_DONE || it->second.state == RR_REQ_FAILED) ? 1 : 0;
+  *done = req_finished(it->second) ? 1 : 0;
   return RR_OK;
 }
 
@@ -483,12 +509,13 @@ int rr_serve_wait(rr_server* sv, uint64_t ticket, uint32_t timeout_ms) {
   std::unique_lock<std::mutex> lk(sv->mu);
   auto finished = [&] {
     auto it = sv->reqs.find(ticket);
-    return it == sv->reqs.end() || it->second.state == RR_REQ_DONE || it->second.state == RR_REQ_FAILED;
+    return it == sv->reqs.end() || req_finished(it->second);
   };
   if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), finished))
     return fail(RR_ERR_TIMEOUT, "the request is not finished");
   auto it = sv->reqs.find(ticket);
   if (it == sv->reqs.end()) return fail(RR_ERR_INVALID_ARG, "unknown ticket");
+  if (it->second.state == RR_REQ_CANCELLED) return fail(RR_ERR_CANCELLED, "the request was cancelled");
   if (it->second.status != RR_OK) return fail(it->second.status, "the request failed");
   return RR_OK;
 }
@@ -506,7 +533,7 @@ int rr_serve_result(rr_server* sv, uint64_t ticket, rr_serve_record* out) {
   out->start_ms = r.start_ms;
   out->done_ms = r.done_ms;
   out->batch_size = r.batch_size;
-  if (r.state == RR_REQ_DONE || r.state == RR_REQ_FAILED) sv->reqs.erase(it);
+  if (req_finished(r)) sv->reqs.erase(it);
   return RR_OK;
 }
 
@@ -526,6 +553,7 @@ int rr_serve_stats_get(rr_server* sv, rr_serve_stats* out, int reset) {
   out->elapsed_ms = now_ms(sv) - sv->stats_t0;
   out->queued = sv->pending.size();
   out->retried = sv->retried;
+  out->cancelled = sv->cancelled;
   std::vector<double> l = sv->latencies;
   if (!l.empty()) {
     std::sort(l.begin(), l.end());
@@ -541,7 +569,7 @@ int rr_serve_stats_get(rr_server* sv, rr_serve_stats* out, int reset) {
     out->latency_max_ms = l.back();
   }
   if (reset) {
-    sv->submitted = sv->completed = sv->failed = sv->rejected = sv->batches = sv->retried = 0;
+    sv->submitted = sv->completed = sv->failed = sv->rejected = sv->batches = sv->retried = sv->cancelled = 0;
     sv->closest = sv->anyhit = sv->rays0 = 0;
     sv->busy_ms = 0;
     sv->stats_t0 = now_ms(sv);

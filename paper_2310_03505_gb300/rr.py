@@ -20,7 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librr.so")
 
-RR_OK, RR_ERR_INVALID_ARG, RR_ERR_OOM, RR_ERR_CAPACITY, RR_ERR_TIMEOUT, RR_ERR_CUDA, RR_ERR_BUSY = range(7)
+RR_OK, RR_ERR_INVALID_ARG, RR_ERR_OOM, RR_ERR_CAPACITY, RR_ERR_TIMEOUT, RR_ERR_CUDA, RR_ERR_BUSY, RR_ERR_CANCELLED = range(8)
 RR_MULTIPATH, RR_REFRACTION, RR_SPECKLE, RR_NOISE, RR_COUNT_TRAVERSAL, RR_NOISE_PERLIN = 1, 2, 4, 8, 16, 32
 RR_MAT_PERFECT_CONDUCTOR, RR_MAT_COOK_TORRANCE, RR_MAT_TABULATED_LOBE = 1, 2, 4
 RR_WAIT_TOP_TASK, RR_WAIT_WIDE_NODE, RR_WAIT_SHADE_PREFIX = 0, 1, 2
@@ -95,7 +95,7 @@ RR_NODES_WIDE8, RR_NODES_BINARY = 0, 1
 RR_BVH_LBVH, RR_BVH_SAH_TOP = 0, 1
 RR_ORDER_QUEUE, RR_ORDER_CELL_OCTANT = 0, 1
 WIDE_NODE_BYTES = 80
-RR_REQ_QUEUED, RR_REQ_RUNNING, RR_REQ_DONE, RR_REQ_FAILED = range(4)
+RR_REQ_QUEUED, RR_REQ_RUNNING, RR_REQ_DONE, RR_REQ_FAILED, RR_REQ_CANCELLED = range(5)
 RR_ADMIT_ESTIMATE, RR_ADMIT_WORST_CASE = 0, 1
 
 
@@ -116,7 +116,7 @@ class rr_serve_stats(C.Structure):
                 ("anyhit_queries", C.c_uint64), ("initial_rays", C.c_uint64), ("queued", C.c_uint64),
                 ("busy_ms", C.c_double), ("elapsed_ms", C.c_double), ("latency_p50_ms", C.c_double),
                 ("latency_p99_ms", C.c_double), ("latency_mean_ms", C.c_double), ("latency_max_ms", C.c_double),
-                ("retried", C.c_uint64), ("reserved", C.c_uint64)]
+                ("retried", C.c_uint64), ("cancelled", C.c_uint64)]
 
 
 # every symbol declared in include/rr.h with its ctypes signature
@@ -151,6 +151,7 @@ SIGNATURES = {
     "rr_serve_submit": ([_P, _P, C.POINTER(rr_pose), C.POINTER(rr_sensor_params), _P, C.POINTER(C.c_uint64)],
                         C.c_int),
     "rr_serve_poll": ([_P, C.c_uint64, C.POINTER(C.c_int)], C.c_int),
+    "rr_serve_cancel": ([_P, C.c_uint64, C.POINTER(C.c_int)], C.c_int),
     "rr_serve_wait": ([_P, C.c_uint64, C.c_uint32], C.c_int),
     "rr_serve_result": ([_P, C.c_uint64, C.POINTER(rr_serve_record)], C.c_int),
     "rr_serve_stats_get": ([_P, C.POINTER(rr_serve_stats), C.c_int], C.c_int),
@@ -456,6 +457,14 @@ def rr_serve_submit(server, scene, pose: dict, params: dict, out_polar) -> int:
     t = C.c_uint64()
     _check(load().rr_serve_submit(server, scene, C.byref(P), C.byref(S), _ptr(out_polar), C.byref(t)))
     return t.value
+
+
+def rr_serve_cancel(server, ticket: int) -> bool:
+    """True if the request was still queued and is now cancelled (it never
+    runs); False if it was already launched or finished (left as it is)."""
+    c = C.c_int(0)
+    _check(load().rr_serve_cancel(server, int(ticket), C.byref(c)))
+    return bool(c.value)
 
 
 def rr_serve_poll(server, ticket: int) -> bool:

@@ -256,3 +256,46 @@ def test_estimated_admission_batches_more_requests(two_scenes):
         finally:
             rr.rr_serve_destroy(sv)
     assert max(sizes[rr.RR_ADMIT_ESTIMATE]) > max(sizes[rr.RR_ADMIT_WORST_CASE]), sizes
+
+
+def test_cancel_queued_requests(two_scenes):
+    """Requests cancelled while queued never run: their outputs stay as they
+    were and they finish as cancelled; the others complete as if alone.  A
+    request already launched or finished is not cancelled."""
+    hs, base = two_scenes
+    sv = rr.rr_serve_create(memory_budget=1 << 30, slots=1, max_batch_scans=1)
+    try:
+        p = scenes.sensor(**{**base, "rays_per_beam": 16})
+        pz = scenes.pose(0, 0, 0.5)
+        outs = [np.full((p["n_azimuth"], p["n_bins"]), -1.0, np.float32) for _ in range(24)]
+        tickets = [rr.rr_serve_submit(sv, hs[0], pz, p, o) for o in outs]
+        cancelled = {t for t in tickets[::2] if rr.rr_serve_cancel(sv, t)}
+        assert cancelled, "every request had been launched before the cancel"
+        for t in tickets:
+            if t in cancelled:
+                with pytest.raises(rr.RRError) as e:
+                    rr.rr_serve_wait(sv, t, 60_000)
+                assert e.value.code == rr.RR_ERR_CANCELLED
+                assert rr.rr_serve_poll(sv, t)
+            else:
+                rr.rr_serve_wait(sv, t, 60_000)
+        ref = alone(hs[0], pz, p)
+        for t, o in zip(tickets, outs):
+            rec = rr.rr_serve_result(sv, t)
+            if t in cancelled:
+                assert rec["state"] == rr.RR_REQ_CANCELLED and rec["status"] == rr.RR_ERR_CANCELLED
+                assert (o == -1.0).all(), "a cancelled request wrote its output"
+            else:
+                assert rec["state"] == rr.RR_REQ_DONE
+                assert_close(o, ref, "not cancelled")
+        st = rr.rr_serve_stats_get(sv)
+        assert st["cancelled"] == len(cancelled)
+        assert st["completed"] == len(tickets) - len(cancelled)
+        t = rr.rr_serve_submit(sv, hs[0], pz, p, outs[1])
+        rr.rr_serve_wait(sv, t, 60_000)
+        assert not rr.rr_serve_cancel(sv, t)   # finished: left as it is
+        assert rr.rr_serve_result(sv, t)["state"] == rr.RR_REQ_DONE
+        with pytest.raises(rr.RRError):
+            rr.rr_serve_cancel(sv, 10 ** 12)
+    finally:
+        rr.rr_serve_destroy(sv)
