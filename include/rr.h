@@ -182,10 +182,10 @@ typedef struct {
 /* kernel kinds reported by rr_profile_read */
 #define RR_K_RAYGEN 0
 #define RR_K_TRACE 1 /* closest-hit queries */
-#define RR_K_SHADE 2
+#define RR_K_SHADE 2 /* shading and compaction; with deferred visibility also the air-path candidates */
 #define RR_K_IMAGE 3
 #define RR_K_BUILD 4 /* LBVH build and the 8-wide collapse */
-#define RR_K_VIS 5   /* air-path candidates and their visibility queries */
+#define RR_K_VIS 5   /* air-path visibility queries (and, with a min_energy cut, the candidate pass) */
 #define RR_K_COUNT 6
 typedef struct {
   double ms[RR_K_COUNT];        /* sum of the launches' event durations */
