@@ -282,6 +282,26 @@ int rr_scene_info_get(const rr_scene* scene, rr_scene_info* info);
    [-pi/2, pi/2].  Rebuilds the scene's lobe tables (stream ordered). */
 int rr_scene_set_lobe(rr_scene* scene, uint32_t material, const float* density);
 
+/* Scene serialisation (no counterpart in the paper: a simulation saves the
+   scene it scans and resumes from it later, or ships it to another process).
+   rr_scene_save writes the scene's current state -- its vertices (as updated
+   by rr_scene_update_vertices), triangles, material ids, materials, the
+   densities of its tabulated lobes and its launch configuration
+   (rr_batch_config, including the BVH build) -- into blob[capacity], host
+   memory, behind a header with a format version and a checksum.  *size
+   receives the bytes the blob takes; blob may be NULL to ask for it.
+   RR_ERR_INVALID_ARG when capacity is too small (*size is still set).
+   Blocking (waits for the scene's stream). */
+int rr_scene_save(const rr_scene* scene, void* blob, uint64_t capacity, uint64_t* size);
+
+/* Creates a scene from a blob written by rr_scene_save: the same mesh,
+   materials, lobes and launch configuration.  The BVH is built again from
+   them; the build is deterministic, so the new scene's hierarchy equals the
+   saved scene's node for node and its scans give the same segments.
+   RR_ERR_INVALID_ARG for a blob that is truncated, corrupted (checksum) or of
+   another format version; otherwise as rr_scene_create.  Blocking. */
+int rr_scene_load(const void* blob, uint64_t size, rr_scene** out);
+
 /* Copies the LBVH to host arrays (each may be NULL): morton [T] sorted
    Morton codes, perm [T] triangle id of each sorted leaf, children
    [(T-1)][2] child references of the internal nodes (leaf j encoded as

@@ -567,6 +567,137 @@ int rr_scene_set_lobe(rr_scene* s, uint32_t material, const float* density) {
   return RR_OK;
 }
 
+// Scene blob: a 64-byte header, then the payload -- vertices f32[V][3],
+// triangles u32[T][3], material ids u16[T] (padded to 4 bytes), materials
+// rr_material[M], the launch configuration rr_batch_config, and for every
+// tabulated lobe its material index u32 and densities f32[RR_LOBE_SAMPLES].
+// The checksum is FNV-1a (64 bit) over the payload.
+struct SceneBlobHeader {
+  char magic[8];            // "RRSCENE" and a zero byte
+  uint32_t version, nv, nt, nm, n_tab, reserved;
+  uint64_t payload_bytes, checksum;
+  uint8_t pad[16];
+};
+static_assert(sizeof(SceneBlobHeader) == 64, "the blob header is 64 bytes");
+static const char kBlobMagic[8] = {'R', 'R', 'S', 'C', 'E', 'N', 'E', 0};
+constexpr uint32_t kBlobVersion = 1;
+
+static uint64_t fnv1a(const unsigned char* p, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+  return h;
+}
+
+static size_t blob_payload_bytes(uint32_t nv, uint32_t nt, uint32_t nm, uint32_t n_tab) {
+  return (size_t)nv * 12 + (size_t)nt * 12 + (((size_t)nt * 2 + 3) & ~(size_t)3) + (size_t)nm * sizeof(rr_material) +
+         sizeof(rr_batch_config) + (size_t)n_tab * (4 + (size_t)rr::kLobeSamples * 4);
+}
+
+int rr_scene_save(const rr_scene* s, void* blob, uint64_t capacity, uint64_t* size) {
+  if (!s || !size) return fail(RR_ERR_INVALID_ARG, "scene and size must not be NULL");
+  if (int rc = check_device(s, "rr_scene_save")) return rc;
+  uint32_t n_tab = 0;
+  for (uint32_t m = 0; m < s->nm; ++m) n_tab += s->lobe_kind[m] == rr::kLobeTable ? 1u : 0u;
+  const size_t payload = blob_payload_bytes(s->nv, s->nt, s->nm, n_tab);
+  *size = sizeof(SceneBlobHeader) + payload;
+  if (!blob) return RR_OK;
+  if (capacity < *size) return fail(RR_ERR_INVALID_ARG, "the blob needs " + std::to_string(*size) + " bytes");
+  RR_CHECK_CUDA(cudaStreamSynchronize(t_stream), "synchronising");
+  unsigned char* b = static_cast<unsigned char*>(blob) + sizeof(SceneBlobHeader);
+  unsigned char* q = b;
+  auto d2h = [&](const void* src, size_t n) -> cudaError_t {
+    cudaError_t e = n ? cudaMemcpy(q, src, n, cudaMemcpyDeviceToHost) : cudaSuccess;
+    q += n;
+    return e;
+  };
+  RR_CHECK_CUDA(d2h(s->d_vtx, (size_t)s->nv * 12), "saving the vertices");
+  RR_CHECK_CUDA(d2h(s->d_idx, (size_t)s->nt * 12), "saving the triangles");
+  RR_CHECK_CUDA(d2h(s->d_mat_id, (size_t)s->nt * 2), "saving the material ids");
+  for (size_t pad = (((size_t)s->nt * 2 + 3) & ~(size_t)3) - (size_t)s->nt * 2; pad; --pad) *q++ = 0;
+  RR_CHECK_CUDA(d2h(s->d_raw_mats, (size_t)s->nm * sizeof(rr_material)), "saving the materials");
+  rr_batch_config cfg;
+  if (int rc = rr_batch_config_get(s, &cfg)) return rc;
+  memcpy(q, &cfg, sizeof cfg);
+  q += sizeof cfg;
+  for (uint32_t m = 0; m < s->nm; ++m) {
+    if (s->lobe_kind[m] != rr::kLobeTable) continue;
+    memcpy(q, &m, 4);
+    q += 4;
+    RR_CHECK_CUDA(d2h(s->d_lobe_samples + (size_t)m * rr::kLobeSamples, (size_t)rr::kLobeSamples * 4),
+                  "saving a tabulated lobe");
+  }
+  SceneBlobHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, kBlobMagic, 8);
+  h.version = kBlobVersion;
+  h.nv = s->nv;
+  h.nt = s->nt;
+  h.nm = s->nm;
+  h.n_tab = n_tab;
+  h.payload_bytes = payload;
+  h.checksum = fnv1a(b, payload);
+  memcpy(blob, &h, sizeof h);
+  return RR_OK;
+}
+
+int rr_scene_load(const void* blob, uint64_t size, rr_scene** out) {
+  if (!blob || !out) return fail(RR_ERR_INVALID_ARG, "blob and out must not be NULL");
+  if (size < sizeof(SceneBlobHeader)) return fail(RR_ERR_INVALID_ARG, "the blob is truncated (no header)");
+  SceneBlobHeader h;
+  memcpy(&h, blob, sizeof h);
+  if (memcmp(h.magic, kBlobMagic, 8) != 0) return fail(RR_ERR_INVALID_ARG, "not a scene blob");
+  if (h.version != kBlobVersion)
+    return fail(RR_ERR_INVALID_ARG, "scene blob format " + std::to_string(h.version) + ", this library reads " +
+                                        std::to_string(kBlobVersion));
+  if (h.nm == 0 || h.nm > RR_MAX_MATERIALS || h.n_tab > h.nm || h.nt > (1u << 30))
+    return fail(RR_ERR_INVALID_ARG, "the blob header is inconsistent");
+  const size_t payload = blob_payload_bytes(h.nv, h.nt, h.nm, h.n_tab);
+  if (h.payload_bytes != payload || size < sizeof(SceneBlobHeader) + payload)
+    return fail(RR_ERR_INVALID_ARG, "the blob is truncated or its sizes disagree");
+  const unsigned char* b = static_cast<const unsigned char*>(blob) + sizeof(SceneBlobHeader);
+  if (fnv1a(b, payload) != h.checksum) return fail(RR_ERR_INVALID_ARG, "the blob is corrupted (checksum)");
+  // copies of the arrays: the payload has no alignment guarantee beyond bytes
+  std::vector<float> vtx((size_t)h.nv * 3);
+  std::vector<uint32_t> tri((size_t)h.nt * 3);
+  std::vector<uint16_t> mid(h.nt);
+  std::vector<rr_material> mats(h.nm);
+  const unsigned char* q = b;
+  memcpy(vtx.data(), q, vtx.size() * 4);
+  q += vtx.size() * 4;
+  memcpy(tri.data(), q, tri.size() * 4);
+  q += tri.size() * 4;
+  memcpy(mid.data(), q, mid.size() * 2);
+  q += ((size_t)h.nt * 2 + 3) & ~(size_t)3;
+  memcpy(mats.data(), q, mats.size() * sizeof(rr_material));
+  q += mats.size() * sizeof(rr_material);
+  rr_batch_config cfg;
+  memcpy(&cfg, q, sizeof cfg);
+  q += sizeof cfg;
+  rr_scene* s = nullptr;
+  int rc = rr_scene_create(vtx.data(), h.nv, tri.data(), h.nt, mid.data(), mats.data(), h.nm, &s);
+  if (rc != RR_OK) return rc;
+  std::vector<float> dens(rr::kLobeSamples);
+  for (uint32_t k = 0; k < h.n_tab && rc == RR_OK; ++k) {
+    uint32_t m = 0;
+    memcpy(&m, q, 4);
+    memcpy(dens.data(), q + 4, dens.size() * 4);
+    q += 4 + dens.size() * 4;
+    rc = rr_scene_set_lobe(s, m, dens.data());
+  }
+  if (rc == RR_OK) rc = rr_batch_config_set(s, &cfg);   // rebuilds when the saved BVH build differs
+  if (rc == RR_OK) {
+    cudaError_t e = cudaStreamSynchronize(t_stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "loading the scene");
+  }
+  if (rc != RR_OK) {
+    const std::string msg = rr_last_error();
+    rr_scene_destroy(s);
+    return fail(rc, msg);
+  }
+  *out = s;
+  return RR_OK;
+}
+
 int rr_scene_export_wide(rr_scene* s, void* nodes, uint32_t cap, uint32_t* n_nodes, float* tris) {
   if (!s) return fail(RR_ERR_INVALID_ARG, "scene must not be NULL");
   if (int rc = check_device(s, "rr_scene_export_wide")) return rc;

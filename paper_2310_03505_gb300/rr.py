@@ -131,6 +131,8 @@ SIGNATURES = {
     "rr_scene_destroy": ([_P], C.c_int),
     "rr_scene_update_vertices": ([_P, _P], C.c_int),
     "rr_scene_set_lobe": ([_P, C.c_uint32, _P], C.c_int),
+    "rr_scene_save": ([_P, _P, C.c_uint64, C.POINTER(C.c_uint64)], C.c_int),
+    "rr_scene_load": ([_P, C.c_uint64, C.POINTER(_P)], C.c_int),
     "rr_scene_info_get": ([_P, C.POINTER(rr_scene_info)], C.c_int),
     "rr_scene_export_bvh": ([_P, _P, _P, _P, _P, _P], C.c_int),
     "rr_scene_export_wide": ([_P, _P, C.c_uint32, C.POINTER(C.c_uint32), _P], C.c_int),
@@ -297,6 +299,26 @@ def rr_scene_destroy(scene) -> None:
 def rr_scene_update_vertices(scene, vertices) -> None:
     _use_torch_stream()
     _check(load().rr_scene_update_vertices(scene, _ptr(vertices)))
+
+
+def rr_scene_save(scene) -> bytes:
+    """The scene's mesh, materials, tabulated lobes and launch configuration
+    as a blob (see rr_scene_load)."""
+    _use_torch_stream()
+    size = C.c_uint64(0)
+    _check(load().rr_scene_save(scene, None, 0, C.byref(size)))
+    buf = np.zeros(size.value, np.uint8)
+    _check(load().rr_scene_save(scene, _ptr(buf), size.value, C.byref(size)))
+    return buf.tobytes()
+
+
+def rr_scene_load(blob: bytes):
+    """A new scene from a blob written by rr_scene_save; returns the handle."""
+    _use_torch_stream()
+    b = np.frombuffer(blob, np.uint8)
+    h = _P()
+    _check(load().rr_scene_load(_ptr(b), b.size, C.byref(h)))
+    return h
 
 
 def rr_scene_set_lobe(scene, material: int, density) -> None:
