@@ -153,7 +153,9 @@ typedef struct {
   uint32_t tri;
   float t;
   float E;
-  uint32_t flags; /* bit 0: an air-path visibility test ran, bit 1: the sensor was visible */
+  uint32_t flags; /* bit 0: an air-path visibility test ran (a candidate whose window W toward the
+                     sensor and receive weight g are both non-zero in float32: otherwise its return
+                     is 0 whatever the visibility), bit 1: the sensor was visible */
   float cos_i, ret_t, ret_a;
   float visits; /* BVH nodes the closest-hit query visited (diagnostics) */
 } rr_segment;

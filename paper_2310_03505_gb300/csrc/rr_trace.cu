@@ -686,10 +686,10 @@ __global__ void __launch_bounds__(256) k_vis_prep(ScanArgs a, uint32_t bounce) {
               cand = side < 0.0f;
             }
           }
-          if (cand) {
+          if (cand) {   // as the deferred candidates: W and the receive weight g both non-zero
             wa = brdf_window(m, a.lut + (size_t)mid * (kLutCells + 1), angle_between(dir_out, v),
                              __ldg(&sd->beam.x));
-            want = wa > 0.0f;
+            want = wa > 0.0f && wa * rx_weight(sd, ray.meta.y >> 16, p) > 0.0f;
           }
         }
       }
@@ -976,11 +976,11 @@ __global__ void __launch_bounds__(kShadeBlock, kMinBlocks) k_shade(ScanArgs a, u
               dir_out = normalize(eta * d + (eta * cos_i - cos_t) * nrm);
               c = side < 0.0f;
             }
-            if (c) {
+            if (c) {   // a window closed toward the sensor, or a receive weight that is 0, returns nothing
               const float wa = brdf_window(m, lut, angle_between(dir_out, v), beam.x);
               if (wa > 0.0f) {
-                cand = true;
                 wag = wa * rx_weight(sd, az, p);
+                cand = wag > 0.0f;
               }
             }
           }
